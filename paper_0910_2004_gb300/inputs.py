@@ -1,0 +1,242 @@
+"""Seeded synthetic input generators (graphs and coarse partitions).
+
+This module produces INPUTS only: CSR graphs with the shapes and weight
+distributions of the workloads the partitioner is measured on, and the seeded
+random coarse partition that stands in for initial partitioning.  It holds none
+of the method's arithmetic (no rating, matching, contraction, cut or gain), so
+both the CUDA path and the CPU oracle may consume what it returns.
+
+Graph layout (shared by every consumer): an undirected graph is stored as a
+symmetric CSR with int32 arrays
+    xadj   [n+1]   row offsets
+    adjncy [nnz]   neighbour ids, strictly increasing inside each row
+    ewgt   [nnz]   edge weights (>0), equal for (u,v) and (v,u)
+    vwgt   [n]     node weights (>=0)
+nnz = 2m counts directed entries (Section 2: G=(V,E,c,omega), Section 5.2:
+static adjacency array).
+
+Random numbers come from numpy's PCG64 generator, whose bit stream is
+platform independent, so the same seed gives the same graph on x86 and Arm.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "CSRGraph", "from_edges", "grid2d", "grid3d", "rgg2d", "rmat",
+    "random_small_graph", "path_graph", "star_graph", "batch_rgg_sizes",
+    "random_balanced_partition", "random_partition",
+]
+
+
+@dataclass
+class CSRGraph:
+    xadj: np.ndarray
+    adjncy: np.ndarray
+    ewgt: np.ndarray
+    vwgt: np.ndarray
+    name: str = ""
+
+    @property
+    def n(self) -> int:
+        return int(self.xadj.shape[0] - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.adjncy.shape[0])
+
+    @property
+    def m(self) -> int:
+        return self.nnz // 2
+
+    def arrays(self):
+        return self.xadj, self.adjncy, self.ewgt, self.vwgt
+
+
+def from_edges(n: int, lo: np.ndarray, hi: np.ndarray, w: np.ndarray | None = None,
+               vwgt: np.ndarray | None = None, name: str = "") -> CSRGraph:
+    """Symmetric sorted CSR from an undirected edge list.
+
+    (lo, hi) must be unique pairs with lo != hi (either orientation is fine).
+    """
+    lo = np.asarray(lo, dtype=np.int64)
+    hi = np.asarray(hi, dtype=np.int64)
+    if w is None:
+        w = np.ones(lo.shape[0], dtype=np.int64)
+    w = np.asarray(w, dtype=np.int64)
+    src = np.concatenate([lo, hi])
+    dst = np.concatenate([hi, lo])
+    ww = np.concatenate([w, w])
+    order = np.lexsort((dst, src))
+    src, dst, ww = src[order], dst[order], ww[order]
+    counts = np.bincount(src, minlength=n).astype(np.int64)
+    xadj = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=xadj[1:])
+    if vwgt is None:
+        vwgt = np.ones(n, dtype=np.int32)
+    return CSRGraph(xadj.astype(np.int32), dst.astype(np.int32), ww.astype(np.int32),
+                    np.asarray(vwgt, dtype=np.int32), name)
+
+
+def grid2d(nx: int, ny: int) -> CSRGraph:
+    """5-point grid, id = x + nx*y, unit node and edge weights."""
+    ids = np.arange(nx * ny, dtype=np.int64).reshape(ny, nx)
+    lo = [ids[:, :-1].ravel(), ids[:-1, :].ravel()]
+    hi = [ids[:, 1:].ravel(), ids[1:, :].ravel()]
+    return from_edges(nx * ny, np.concatenate(lo), np.concatenate(hi),
+                      name=f"grid2d_{nx}x{ny}")
+
+
+def grid3d(nx: int, ny: int, nz: int) -> CSRGraph:
+    """7-point grid, id = x + nx*(y + ny*z) (x fastest), unit weights.
+
+    Built row by row in sorted order directly (no global sort), so the
+    256^3 case (16.8M nodes, 100M directed entries) takes seconds.
+    """
+    n = nx * ny * nz
+    v = np.arange(n, dtype=np.int64)
+    x = v % nx
+    y = (v // nx) % ny
+    z = v // (nx * ny)
+    # neighbour offsets in increasing id order: -nx*ny, -nx, -1, +1, +nx, +nx*ny
+    offs = [(-nx * ny, z > 0), (-nx, y > 0), (-1, x > 0),
+            (1, x < nx - 1), (nx, y < ny - 1), (nx * ny, z < nz - 1)]
+    deg = np.zeros(n, dtype=np.int64)
+    for _, ok in offs:
+        deg += ok
+    xadj = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(deg, out=xadj[1:])
+    nnz = int(xadj[-1])
+    adjncy = np.empty(nnz, dtype=np.int32)
+    pos = xadj[:-1].copy()
+    for off, ok in offs:
+        idx = np.nonzero(ok)[0]
+        adjncy[pos[idx]] = (idx + off).astype(np.int32)
+        pos[idx] += 1
+        del idx
+    return CSRGraph(xadj.astype(np.int32), adjncy, np.ones(nnz, dtype=np.int32),
+                    np.ones(n, dtype=np.int32), f"grid3d_{nx}x{ny}x{nz}")
+
+
+def rgg2d(n: int, seed: int, mean_degree: float = 6.0, radius: float | None = None,
+          wmax: int = 1) -> CSRGraph:
+    """2D random geometric graph: n points uniform in [0,1)^2, edge iff the
+    Euclidean distance is below r (Section 6, instances).  Default r gives
+    expected mean degree `mean_degree` (pi r^2 n = mean_degree); ids follow
+    generation order.  Edge weights are uniform in [1, wmax] (1 = unit)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pts = rng.random((n, 2))
+    if radius is None:
+        radius = math.sqrt(mean_degree / (math.pi * n))
+    r2 = radius * radius
+    G = max(1, int(1.0 / radius))
+    cx = np.minimum((pts[:, 0] * G).astype(np.int64), G - 1)
+    cy = np.minimum((pts[:, 1] * G).astype(np.int64), G - 1)
+    cell = cx + G * cy
+    order = np.argsort(cell, kind="stable")
+    cell_sorted = cell[order]
+    start = np.searchsorted(cell_sorted, np.arange(G * G), side="left")
+    count = np.searchsorted(cell_sorted, np.arange(G * G), side="right") - start
+    maxc = int(count.max()) if n else 0
+    los, his = [], []
+    pid = np.arange(n, dtype=np.int64)
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            ncx, ncy = cx + dx, cy + dy
+            ok = (ncx >= 0) & (ncx < G) & (ncy >= 0) & (ncy < G)
+            src = pid[ok]
+            ncell = (ncx + G * ncy)[ok]
+            s0, c0 = start[ncell], count[ncell]
+            for j in range(maxc):
+                has = c0 > j
+                if not has.any():
+                    break
+                a = src[has]
+                b = order[s0[has] + j]
+                keep = a < b
+                a, b = a[keep], b[keep]
+                d = pts[a] - pts[b]
+                close = (d * d).sum(axis=1) < r2
+                los.append(a[close])
+                his.append(b[close])
+    lo = np.concatenate(los) if los else np.zeros(0, np.int64)
+    hi = np.concatenate(his) if his else np.zeros(0, np.int64)
+    if wmax > 1:
+        w = rng.integers(1, wmax + 1, size=lo.shape[0])
+    else:
+        w = None
+    return from_edges(n, lo, hi, w, name=f"rgg2d_n{n}_s{seed}")
+
+
+def rmat(scale: int, seed: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
+         c: float = 0.19) -> CSRGraph:
+    """R-MAT graph (Chakrabarti et al. 2004): edge_factor * 2^scale samples,
+    symmetrised, self loops dropped, duplicates merged into integer weights."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = 1 << scale
+    M = edge_factor * n
+    u = np.zeros(M, dtype=np.int64)
+    v = np.zeros(M, dtype=np.int64)
+    for bit in range(scale):
+        r = rng.random(M)
+        ubit = r >= a + b            # quadrants c, d -> lower half in u
+        vbit = ((r >= a) & (r < a + b)) | (r >= a + b + c)
+        u |= ubit.astype(np.int64) << bit
+        v |= vbit.astype(np.int64) << bit
+    keep = u != v
+    u, v = u[keep], v[keep]
+    lo, hi = np.minimum(u, v), np.maximum(u, v)
+    key, cnt = np.unique(lo * n + hi, return_counts=True)
+    return from_edges(n, key // n, key % n, cnt, name=f"rmat_s{scale}_seed{seed}")
+
+
+def random_small_graph(n: int, p: float, seed: int, wmax: int = 4, cmax: int = 3,
+                       allow_zero_c: bool = False) -> CSRGraph:
+    """Erdos-Renyi G(n,p) with random integer edge weights in [1,wmax] and node
+    weights in [1,cmax] (or [0,cmax])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    iu, ju = np.triu_indices(n, 1)
+    keep = rng.random(iu.shape[0]) < p
+    lo, hi = iu[keep], ju[keep]
+    w = rng.integers(1, wmax + 1, size=lo.shape[0])
+    c = rng.integers(0 if allow_zero_c else 1, cmax + 1, size=n)
+    return from_edges(n, lo, hi, w, c, name=f"gnp_n{n}_p{p}_s{seed}")
+
+
+def path_graph(n: int, increasing: bool = True) -> CSRGraph:
+    """Path 0-1-...-(n-1); edge (i,i+1) has weight i+1 (increasing) or 1."""
+    lo = np.arange(n - 1)
+    w = lo + 1 if increasing else np.ones(n - 1, dtype=np.int64)
+    return from_edges(n, lo, lo + 1, w, name=f"path_{n}")
+
+
+def star_graph(leaves: int) -> CSRGraph:
+    """Hub 0 joined to leaves 1..leaves, unit weights."""
+    return from_edges(leaves + 1, np.zeros(leaves, np.int64), np.arange(1, leaves + 1),
+                      name=f"star_{leaves}")
+
+
+def batch_rgg_sizes(count: int, seed: int, nmin: int = 1024, nmax: int = 65536) -> np.ndarray:
+    """Node counts log-uniform in [nmin, nmax] for a batch of independent RGGs."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.floor(np.exp(rng.uniform(math.log(nmin), math.log(nmax), size=count))).astype(np.int64)
+
+
+def random_balanced_partition(n: int, k: int, seed: int) -> np.ndarray:
+    """Seeded random balanced k-way partition of n nodes: a random permutation
+    of the nodes is dealt round-robin to blocks 0..k-1, so block sizes differ
+    by at most one.  Stands in for initial partitioning (Section 4)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    perm = rng.permutation(n)
+    part = np.empty(n, dtype=np.int32)
+    part[perm] = (np.arange(n) % k).astype(np.int32)
+    return part
+
+
+def random_partition(n: int, k: int, seed: int) -> np.ndarray:
+    """Uniformly random block per node (not balanced)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.integers(0, k, size=n).astype(np.int32)
