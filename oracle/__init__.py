@@ -13,6 +13,7 @@ Each function names the passage it follows.  All arithmetic is integer.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -248,9 +249,10 @@ def project(maps, coarse_part) -> np.ndarray:
 
 def l_max(total_c: int, max_c: int, k: int, eps: float) -> int:
     """Balance bound L_max = (1+eps) c(V)/k + max_v c(v) (Section 2), with eps
-    read in parts per million and the result rounded down so that the integer
-    test c(V_i) <= L_max is exact."""
-    eps_ppm = int(round(eps * 1_000_000))
+    read in parts per million (rounded half up) and the result rounded down so
+    that the integer test c(V_i) <= L_max is exact."""
+    x = eps * 1_000_000          # the same double product as the C library's
+    eps_ppm = math.floor(x) + (1 if x - math.floor(x) >= 0.5 else 0)   # round half up
     return ((1_000_000 + eps_ppm) * int(total_c) + k * 1_000_000 * int(max_c)) // (k * 1_000_000)
 
 
