@@ -1,0 +1,212 @@
+/*
+ * kp.h - C ABI of the GB300 coarsening / projection / cut-gain library.
+ *
+ * The library implements the data-parallel path of the multilevel graph
+ * partitioner of "Engineering a Scalable High Quality Graph Partitioner"
+ * (Holtgrewe, Sanders, Schulz): edge rating (Section 3.1), matching of
+ * locally heaviest edges by handshake rounds (Section 3.3, which under a
+ * strict edge order yields the Greedy matching of Section 3.2), contraction
+ * level after level (Section 2), projection of a coarse partition back to the
+ * input (uncontraction, Section 2) and the cut, block weights, balance bound
+ * and per-node FM gains of a partition (Sections 2 and 5.2).
+ *
+ * Conventions
+ *  - All arithmetic is integer: int32 node ids, node weights c and edge
+ *    weights omega; int64 sums.  Ratings are exact fractions.
+ *  - A graph is a symmetric CSR: row v lists the neighbours of v in strictly
+ *    increasing order, each undirected edge {u,v} appears as (u,v) and (v,u)
+ *    with the same weight, there are no self loops, omega > 0 and c >= 0.
+ *    nnz = 2|E| directed entries.  Section 2 requires omega > 0, c >= 0.
+ *  - Integer ranges: sum of c < 2^31, sum of omega over undirected edges
+ *    < 2^31, nnz < 2^31.  Then every coarse weight fits in int32.
+ *  - Pointers are DEVICE pointers unless a parameter says "host".
+ *    Every call is ordered on the stream passed in (NULL = legacy default
+ *    stream); calls that return host scalars synchronise that stream.
+ *  - Every call returns a kp_status.  On failure no output is valid and a
+ *    message is available from kp_last_error() (thread local).
+ *  - Ties between equal ratings are broken by a seeded splitmix64 hash of the
+ *    edge's endpoints (higher first), then by the smaller (min id, max id);
+ *    the paper leaves tie breaking open.  All results are bit-exact and do not
+ *    depend on launch shapes or scheduling.
+ */
+#ifndef KP_H
+#define KP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t / CUstream); NULL is the legacy default stream. */
+typedef struct CUstream_st *kp_stream;
+
+typedef enum {
+    KP_OK = 0,
+    KP_ERR_INVALID = 1,     /* malformed input (see each call) */
+    KP_ERR_OVERFLOW = 2,    /* input outside the integer ranges above */
+    KP_ERR_OOM = 3,         /* a device or host allocation failed */
+    KP_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    KP_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+    KP_ERR_UNSUPPORTED = 6  /* a parameter value this build does not handle */
+} kp_status;
+
+/* Edge ratings of Section 3.1, each kept as an exact fraction num/den:
+ *   EXPANSION_STAR2  omega^2 / (c(u) c(v))          (the paper's default)
+ *   INNER_OUTER      omega / (Out(u) + Out(v) - 2 omega),
+ *                    Out(v) = sum of omega over v's edges
+ *   WEIGHT           omega
+ *   EXPANSION        omega / (c(u) + c(v))
+ *   EXPANSION_STAR   omega / (c(u) c(v))
+ * A zero denominator means +infinity; two infinities are equal. */
+typedef enum {
+    KP_RATING_EXPANSION_STAR2 = 0,
+    KP_RATING_INNER_OUTER = 1,
+    KP_RATING_WEIGHT = 2,
+    KP_RATING_EXPANSION = 3,
+    KP_RATING_EXPANSION_STAR = 4
+} kp_rating;
+
+/* A graph G = (V, E, c, omega) (Section 2) as a symmetric CSR (the static
+ * adjacency array of Section 5.2).  Arrays are caller-owned:
+ *   xadj[n+1] row offsets, adjncy[nnz] neighbours, ewgt[nnz] omega,
+ *   vwgt[n] c. */
+typedef struct {
+    int32_t n;
+    int32_t nnz;
+    const int32_t *xadj;
+    const int32_t *adjncy;
+    const int32_t *ewgt;
+    const int32_t *vwgt;
+} kp_graph;
+
+/* Coarsening options.
+ *   rating               a kp_rating
+ *   seed                 tie-break hash seed
+ *   stop_size            stop before contracting a graph with <= stop_size
+ *                        nodes (Section 4: "small enough"; 20*k in the
+ *                        measured workloads)
+ *   max_levels           at most this many contractions (default 64)
+ *   min_shrink_permille  stop after a contraction that kept more than
+ *                        (1000 - this)/1000 of the nodes (default 50); a
+ *                        contraction that matches nothing is not kept
+ *   spin_limit           iteration bound of every device-side wait; a wait
+ *                        that runs out sets KP_ERR_TIMEOUT (default 1<<22)
+ *   validate             1: check the input graph on the device first */
+typedef struct {
+    int32_t rating;
+    uint64_t seed;
+    int32_t stop_size;
+    int32_t max_levels;
+    int32_t min_shrink_permille;
+    int64_t spin_limit;
+    int32_t validate;
+} kp_options;
+
+/* Fills *o with the defaults: EXPANSION_STAR2, seed 1, stop_size 40,
+ * max_levels 64, min_shrink_permille 50, spin_limit 1<<22, validate 1. */
+void kp_options_default(kp_options *o);
+
+/* A hierarchy of graphs G_0 (the input) .. G_L (the coarsest) with the maps
+ * map_l : V(G_l) -> V(G_{l+1}).  Opaque and library-owned. */
+typedef struct kp_hierarchy kp_hierarchy;
+
+/* Contraction phase (Sections 2, 3, 4).  Level after level: rate every edge,
+ * find the matching of locally heaviest edges by handshake rounds (every free
+ * node names its best free neighbour, mutual names are matched, repeated
+ * until no edge has two free ends; Section 3.3), and contract it (matched
+ * pairs become one node with c = c(u)+c(v); parallel edges are merged with
+ * summed omega; Section 2).  Coarse node ids are the ranks of each pair's
+ * smaller fine id; coarse rows are sorted.  Stops by the options' rules.
+ *   g    input graph (device arrays); BORROWED: it must stay alive and
+ *        unchanged until kp_hierarchy_free
+ *   o    options (host; NULL = defaults)
+ *   out  receives the hierarchy (host pointer to a handle)
+ * Blocks until the hierarchy is complete (level sizes are data-dependent).
+ * Errors: KP_ERR_INVALID (malformed graph, with o->validate), KP_ERR_OVERFLOW,
+ * KP_ERR_UNSUPPORTED (unknown rating), KP_ERR_OOM, KP_ERR_CUDA,
+ * KP_ERR_TIMEOUT. */
+kp_status kp_coarsen(const kp_graph *g, const kp_options *o, kp_stream s, kp_hierarchy **out);
+
+/* Number of levels L+1 including the input (host output). */
+kp_status kp_hierarchy_num_levels(const kp_hierarchy *h, int32_t *num_levels);
+
+/* Read-only device view of level l (0 = input).  *map (may be NULL) receives
+ * map_l (n_l entries, values < n_{l+1}), or NULL for the coarsest level.
+ * The arrays stay valid until kp_hierarchy_free. */
+kp_status kp_hierarchy_level(const kp_hierarchy *h, int32_t l, kp_graph *view, const int32_t **map);
+
+/* Statistics of the last kp_coarsen on h (host outputs, any may be NULL):
+ * handshake rounds summed over all levels, and the matched pairs of level l. */
+kp_status kp_hierarchy_stats(const kp_hierarchy *h, int32_t *total_rounds, int64_t *total_matched);
+
+/* Releases the hierarchy (synchronises the stream it was built on). */
+void kp_hierarchy_free(kp_hierarchy *h);
+
+/* Uncontraction (Section 2): the block of every input node is the block of
+ * the coarsest node it was contracted into, p_l(v) = p_{l+1}(map_l(v)) from
+ * the coarsest level down to level 0.
+ *   coarse_part  device int32[n_L] (values are copied through unchecked)
+ *   fine_part    device int32[n_0], caller-owned output
+ * Does not synchronise. */
+kp_status kp_project(const kp_hierarchy *h, const int32_t *coarse_part, int32_t *fine_part, kp_stream s);
+
+/* Results of kp_cut_gain.  The three pointers are caller-owned DEVICE
+ * buffers the call fills: block_w[k], gain[n], target[n]. */
+typedef struct {
+    int64_t cut;        /* sum over blocks i<j of omega(E_ij) (Section 2) */
+    int64_t total_c;    /* c(V) */
+    int64_t max_c;      /* max_v c(v) */
+    int64_t l_max;      /* floor((1+eps) c(V)/k + max_v c(v)), eps read in ppm */
+    int64_t imbalance;  /* max(0, max_i c(V_i) - L_max) (Section 5.2) */
+    int64_t *block_w;   /* c(V_i) */
+    int64_t *gain;      /* decrease of the cut when v moves to target[v] */
+    int32_t *target;    /* adjacent block with the largest connection, the
+                           smallest id on ties; -1 when v has no neighbour in
+                           another block (then gain = -sum of v's omega) */
+} kp_cut_gain_out;
+
+/* Cut, block weights, balance bound L_max = (1+eps) c(V)/k + max c(v)
+ * (Section 2, rounded down with eps taken in parts per million), imbalance,
+ * and per-node FM gains (Section 5.2; with k > 2 a node's gain is for the
+ * adjacent block it is best connected to).
+ *   part  device int32[n], values in [0,k)
+ *   out   host struct; its device buffers are filled, its scalars set
+ * Synchronises the stream (the scalars are returned on the host).
+ * Errors: KP_ERR_INVALID (k < 1, eps < 0, eps > 1000, or a block id outside
+ * [0,k)), KP_ERR_OOM, KP_ERR_CUDA. */
+kp_status kp_cut_gain(const kp_graph *g, const int32_t *part, int32_t k, double eps,
+                      kp_cut_gain_out *out, kp_stream s);
+
+/* Initial partitioning callback for kp_pipeline_host (Section 4 partitions
+ * the coarsest graph on one PE).  Receives the coarsest graph's size and its
+ * node weights (host) and writes a block id in [0,k) for every coarsest node
+ * into part (host).  Returns 0 on success. */
+typedef int (*kp_initial_partition_fn)(int32_t n_coarse, const int32_t *coarse_vwgt, int32_t k,
+                                       int32_t *part, void *user);
+
+/* End to end on HOST buffers: copies the input CSR to the device, coarsens,
+ * asks `ip` for a partition of the coarsest graph, projects it to the input,
+ * evaluates cut/gain and copies part/gain/target/block_w back.
+ *   g        host arrays of the input graph (pinned memory copies fastest)
+ *   fine_part, gain, target: host outputs of n entries; block_w host [k]
+ *   out      host scalars (its pointer fields are ignored)
+ *   num_levels (may be NULL) receives the hierarchy's level count
+ * Synchronises the stream.  Errors as kp_coarsen and kp_cut_gain, plus
+ * KP_ERR_INVALID if ip fails. */
+kp_status kp_pipeline_host(const kp_graph *g, const kp_options *o, int32_t k, double eps,
+                           kp_initial_partition_fn ip, void *user, int32_t *fine_part,
+                           int64_t *gain, int32_t *target, int64_t *block_w,
+                           kp_cut_gain_out *out, int32_t *num_levels, kp_stream s);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *kp_last_error(void);
+
+/* Library version string. */
+const char *kp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KP_H */

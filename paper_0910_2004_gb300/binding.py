@@ -1,0 +1,332 @@
+"""Thin ctypes binding of the C ABI in include/kp.h (argument marshalling only).
+
+Every computation runs in the CUDA library libkp.so.  The functions named
+kp_* mirror the C entry points one to one; the helpers below them only turn
+torch CUDA tensors into the plain pointers and sizes the ABI takes.  If the
+library has not been built, every call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libkp.so")
+
+KP_OK, KP_ERR_INVALID, KP_ERR_OVERFLOW, KP_ERR_OOM, KP_ERR_CUDA, KP_ERR_TIMEOUT, KP_ERR_UNSUPPORTED = range(7)
+STATUS_NAMES = ["KP_OK", "KP_ERR_INVALID", "KP_ERR_OVERFLOW", "KP_ERR_OOM", "KP_ERR_CUDA",
+                "KP_ERR_TIMEOUT", "KP_ERR_UNSUPPORTED"]
+RATINGS = {"expansion*2": 0, "innerOuter": 1, "weight": 2, "expansion": 3, "expansion*": 4}
+
+EXPORTED = ["kp_options_default", "kp_coarsen", "kp_hierarchy_num_levels", "kp_hierarchy_level",
+            "kp_hierarchy_stats", "kp_hierarchy_free", "kp_project", "kp_cut_gain", "kp_pipeline_host",
+            "kp_last_error", "kp_version"]
+
+
+class KpError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{where}: {name}: {msg}")
+
+
+class kp_graph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32), ("xadj", ctypes.c_void_p),
+                ("adjncy", ctypes.c_void_p), ("ewgt", ctypes.c_void_p), ("vwgt", ctypes.c_void_p)]
+
+
+class kp_options(ctypes.Structure):
+    _fields_ = [("rating", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stop_size", ctypes.c_int32),
+                ("max_levels", ctypes.c_int32), ("min_shrink_permille", ctypes.c_int32),
+                ("spin_limit", ctypes.c_int64), ("validate", ctypes.c_int32)]
+
+
+class kp_cut_gain_out(ctypes.Structure):
+    _fields_ = [("cut", ctypes.c_int64), ("total_c", ctypes.c_int64), ("max_c", ctypes.c_int64),
+                ("l_max", ctypes.c_int64), ("imbalance", ctypes.c_int64), ("block_w", ctypes.c_void_p),
+                ("gain", ctypes.c_void_p), ("target", ctypes.c_void_p)]
+
+
+kp_initial_partition_fn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Loads libkp.so; raises if it has not been built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing "
+                               "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+        L = ctypes.CDLL(path)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.kp_options_default.argtypes = [ctypes.POINTER(kp_options)]
+        L.kp_options_default.restype = None
+        L.kp_coarsen.argtypes = [ctypes.POINTER(kp_graph), ctypes.POINTER(kp_options), vp, ctypes.POINTER(vp)]
+        L.kp_coarsen.restype = ctypes.c_int
+        L.kp_hierarchy_num_levels.argtypes = [vp, ctypes.POINTER(i32)]
+        L.kp_hierarchy_num_levels.restype = ctypes.c_int
+        L.kp_hierarchy_level.argtypes = [vp, i32, ctypes.POINTER(kp_graph), ctypes.POINTER(vp)]
+        L.kp_hierarchy_level.restype = ctypes.c_int
+        L.kp_hierarchy_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
+        L.kp_hierarchy_stats.restype = ctypes.c_int
+        L.kp_hierarchy_free.argtypes = [vp]
+        L.kp_hierarchy_free.restype = None
+        L.kp_project.argtypes = [vp, vp, vp, vp]
+        L.kp_project.restype = ctypes.c_int
+        L.kp_cut_gain.argtypes = [ctypes.POINTER(kp_graph), vp, i32, ctypes.c_double,
+                                  ctypes.POINTER(kp_cut_gain_out), vp]
+        L.kp_cut_gain.restype = ctypes.c_int
+        L.kp_pipeline_host.argtypes = [ctypes.POINTER(kp_graph), ctypes.POINTER(kp_options), i32, ctypes.c_double,
+                                       kp_initial_partition_fn, vp, vp, vp, vp, vp,
+                                       ctypes.POINTER(kp_cut_gain_out), ctypes.POINTER(i32), vp]
+        L.kp_pipeline_host.restype = ctypes.c_int
+        L.kp_last_error.argtypes = []
+        L.kp_last_error.restype = ctypes.c_char_p
+        L.kp_version.argtypes = []
+        L.kp_version.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _check(status: int, where: str):
+    if status != KP_OK:
+        raise KpError(status, where, load().kp_last_error().decode(errors="replace"))
+
+
+# ---------------------------------------------------------------------------
+# one wrapper per C entry point
+# ---------------------------------------------------------------------------
+
+def kp_options_default() -> kp_options:
+    o = kp_options()
+    load().kp_options_default(ctypes.byref(o))
+    return o
+
+
+def kp_coarsen(graph: kp_graph, options: kp_options, stream: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().kp_coarsen(ctypes.byref(graph), ctypes.byref(options), ctypes.c_void_p(stream),
+                             ctypes.byref(h)), "kp_coarsen")
+    return h.value
+
+
+def kp_hierarchy_num_levels(h: int) -> int:
+    n = ctypes.c_int32()
+    _check(load().kp_hierarchy_num_levels(ctypes.c_void_p(h), ctypes.byref(n)), "kp_hierarchy_num_levels")
+    return n.value
+
+
+def kp_hierarchy_level(h: int, level: int):
+    g = kp_graph()
+    mp = ctypes.c_void_p()
+    _check(load().kp_hierarchy_level(ctypes.c_void_p(h), level, ctypes.byref(g), ctypes.byref(mp)),
+           "kp_hierarchy_level")
+    return g, mp.value
+
+
+def kp_hierarchy_stats(h: int):
+    r, m = ctypes.c_int32(), ctypes.c_int64()
+    _check(load().kp_hierarchy_stats(ctypes.c_void_p(h), ctypes.byref(r), ctypes.byref(m)), "kp_hierarchy_stats")
+    return r.value, m.value
+
+
+def kp_hierarchy_free(h: int):
+    if h:
+        load().kp_hierarchy_free(ctypes.c_void_p(h))
+
+
+def kp_project(h: int, coarse_part: int, fine_part: int, stream: int):
+    _check(load().kp_project(ctypes.c_void_p(h), ctypes.c_void_p(coarse_part), ctypes.c_void_p(fine_part),
+                             ctypes.c_void_p(stream)), "kp_project")
+
+
+def kp_cut_gain(graph: kp_graph, part: int, k: int, eps: float, out: kp_cut_gain_out, stream: int):
+    _check(load().kp_cut_gain(ctypes.byref(graph), ctypes.c_void_p(part), k, eps, ctypes.byref(out),
+                              ctypes.c_void_p(stream)), "kp_cut_gain")
+
+
+def kp_pipeline_host(graph: kp_graph, options: kp_options, k: int, eps: float, ip, user, fine_part: int,
+                     gain: int, target: int, block_w: int, out: kp_cut_gain_out, stream: int) -> int:
+    nl = ctypes.c_int32()
+    _check(load().kp_pipeline_host(ctypes.byref(graph), ctypes.byref(options), k, eps, ip, user,
+                                   ctypes.c_void_p(fine_part), ctypes.c_void_p(gain), ctypes.c_void_p(target),
+                                   ctypes.c_void_p(block_w), ctypes.byref(out), ctypes.byref(nl),
+                                   ctypes.c_void_p(stream)), "kp_pipeline_host")
+    return nl.value
+
+
+def kp_last_error() -> str:
+    return load().kp_last_error().decode(errors="replace")
+
+
+def kp_version() -> str:
+    return load().kp_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# torch helpers (marshalling only)
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def current_stream() -> int:
+    return _torch().cuda.current_stream().cuda_stream
+
+
+class _DevArray:
+    """Zero-copy view of a library-owned device array (CUDA array interface)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str = "<i4"):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr or 0, True),
+                                         "version": 3, "strides": None}
+
+
+def device_view(ptr: int, n: int, dtype: str = "<i4"):
+    torch = _torch()
+    if n == 0:
+        return torch.empty(0, dtype=torch.int32 if dtype == "<i4" else torch.int64, device="cuda")
+    return torch.as_tensor(_DevArray(ptr, n, dtype), device="cuda")
+
+
+class DeviceGraph:
+    """A CSR graph held in torch CUDA tensors (int32), with its kp_graph."""
+
+    def __init__(self, xadj, adjncy, ewgt, vwgt):
+        torch = _torch()
+        dev = torch.device("cuda")
+        self.xadj = torch.as_tensor(np.asarray(xadj, dtype=np.int32)).to(dev) if not torch.is_tensor(xadj) else xadj
+        self.adjncy = torch.as_tensor(np.asarray(adjncy, dtype=np.int32)).to(dev) if not torch.is_tensor(adjncy) else adjncy
+        self.ewgt = torch.as_tensor(np.asarray(ewgt, dtype=np.int32)).to(dev) if not torch.is_tensor(ewgt) else ewgt
+        self.vwgt = torch.as_tensor(np.asarray(vwgt, dtype=np.int32)).to(dev) if not torch.is_tensor(vwgt) else vwgt
+        for t in (self.xadj, self.adjncy, self.ewgt, self.vwgt):
+            assert t.dtype == torch.int32 and t.is_cuda and t.is_contiguous()
+        self.n = int(self.xadj.numel() - 1)
+        self.nnz = int(self.adjncy.numel())
+        self.kp = kp_graph(self.n, self.nnz, self.xadj.data_ptr(), self.adjncy.data_ptr(),
+                           self.ewgt.data_ptr(), self.vwgt.data_ptr())
+
+    @classmethod
+    def from_csr(cls, g):
+        return cls(g.xadj, g.adjncy, g.ewgt, g.vwgt)
+
+
+def make_options(rating="expansion*2", seed=1, stop_size=40, max_levels=64, min_shrink_permille=50,
+                 spin_limit=1 << 22, validate=True) -> kp_options:
+    o = kp_options_default()
+    o.rating = RATINGS[rating] if isinstance(rating, str) else int(rating)
+    o.seed = seed
+    o.stop_size = stop_size
+    o.max_levels = max_levels
+    o.min_shrink_permille = min_shrink_permille
+    o.spin_limit = spin_limit
+    o.validate = 1 if validate else 0
+    return o
+
+
+class Hierarchy:
+    """Owns a kp_hierarchy handle; level views are zero-copy tensors valid
+    until free()."""
+
+    def __init__(self, graph: DeviceGraph, handle: int):
+        self.graph = graph            # level 0 is borrowed: keep it alive
+        self.handle = handle
+
+    def num_levels(self) -> int:
+        return kp_hierarchy_num_levels(self.handle)
+
+    def level(self, l: int):
+        g, mp = kp_hierarchy_level(self.handle, l)
+        out = {"n": g.n, "nnz": g.nnz, "xadj": device_view(g.xadj, g.n + 1),
+               "adjncy": device_view(g.adjncy, g.nnz), "ewgt": device_view(g.ewgt, g.nnz),
+               "vwgt": device_view(g.vwgt, g.n), "map": device_view(mp, g.n) if mp else None}
+        out["graph"] = g
+        return out
+
+    def stats(self):
+        return kp_hierarchy_stats(self.handle)
+
+    def project(self, coarse_part, fine_part=None):
+        torch = _torch()
+        n0 = self.graph.n
+        if fine_part is None:
+            fine_part = torch.empty(n0, dtype=torch.int32, device="cuda")
+        kp_project(self.handle, coarse_part.data_ptr(), fine_part.data_ptr(), current_stream())
+        return fine_part
+
+    def free(self):
+        if self.handle:
+            kp_hierarchy_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def coarsen(graph: DeviceGraph, **opts) -> Hierarchy:
+    h = kp_coarsen(graph.kp, make_options(**opts), current_stream())
+    return Hierarchy(graph, h)
+
+
+def cut_gain(graph, part, k: int, eps: float, block_w=None, gain=None, target=None):
+    """graph: DeviceGraph or kp_graph view; part: int32 CUDA tensor."""
+    torch = _torch()
+    kg = graph.kp if isinstance(graph, DeviceGraph) else graph
+    n = kg.n
+    block_w = torch.empty(max(k, 1), dtype=torch.int64, device="cuda") if block_w is None else block_w
+    gain = torch.empty(max(n, 1), dtype=torch.int64, device="cuda") if gain is None else gain
+    target = torch.empty(max(n, 1), dtype=torch.int32, device="cuda") if target is None else target
+    out = kp_cut_gain_out()
+    out.block_w, out.gain, out.target = block_w.data_ptr(), gain.data_ptr(), target.data_ptr()
+    kp_cut_gain(kg, part.data_ptr() if n > 0 else 0, k, eps, out, current_stream())
+    return {"cut": out.cut, "total_c": out.total_c, "max_c": out.max_c, "L_max": out.l_max,
+            "imbalance": out.imbalance, "block_w": block_w[:k], "gain": gain[:n], "target": target[:n]}
+
+
+def pipeline_host(xadj, adjncy, ewgt, vwgt, k: int, eps: float, initial_partition, outputs=None, **opts):
+    """End to end from host arrays (numpy, ideally pinned): the whole path in
+    one C call.  initial_partition(n_coarse, coarse_vwgt: np.ndarray, k) ->
+    np.ndarray[int32] of block ids."""
+    n = len(xadj) - 1
+    nnz = len(adjncy)
+    arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in (xadj, adjncy, ewgt, vwgt)]
+    g = kp_graph(n, nnz, *[a.ctypes.data for a in arrs])
+    if outputs is None:
+        outputs = {"part": np.empty(n, np.int32), "gain": np.empty(n, np.int64),
+                   "target": np.empty(n, np.int32), "block_w": np.empty(k, np.int64)}
+    err = []
+
+    def _ip(nc, cw_ptr, kk, part_ptr, user):
+        try:
+            cw = np.ctypeslib.as_array(cw_ptr, shape=(max(nc, 1),))[:nc].copy()
+            p = np.asarray(initial_partition(nc, cw, kk), dtype=np.int32)
+            np.ctypeslib.as_array(part_ptr, shape=(max(nc, 1),))[:nc] = p[:nc]
+            return 0
+        except Exception as e:   # reported through the C status
+            err.append(e)
+            return 1
+
+    cb = kp_initial_partition_fn(_ip)
+    out = kp_cut_gain_out()
+    stream = current_stream()
+    levels = kp_pipeline_host(g, make_options(**opts), k, eps, cb, None, outputs["part"].ctypes.data,
+                              outputs["gain"].ctypes.data, outputs["target"].ctypes.data,
+                              outputs["block_w"].ctypes.data, out, stream)
+    if err:
+        raise err[0]
+    return {"cut": out.cut, "total_c": out.total_c, "max_c": out.max_c, "L_max": out.l_max,
+            "imbalance": out.imbalance, "num_levels": levels, **outputs}

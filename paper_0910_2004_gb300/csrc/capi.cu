@@ -1,0 +1,275 @@
+// C ABI entry points (include/kp.h), error state, allocation and the
+// device-side input check of Section 2's requirements (omega > 0, c >= 0,
+// undirected graph stored symmetrically, no self loops).
+#include <cstdio>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "kp_internal.cuh"
+
+namespace kp {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+kp_status set_error(kp_status st, const std::string &msg) {
+    g_last_error = msg;
+    return st;
+}
+
+kp_status cuda_error(cudaError_t e, const char *what) {
+    cudaGetLastError();   // clear a non-sticky error
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    return set_error(e == cudaErrorMemoryAllocation ? KP_ERR_OOM : KP_ERR_CUDA, buf);
+}
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (cached[dev] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = v > 0 ? v : 1;
+    }
+    return cached[dev];
+}
+
+kp_status dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+    static std::mutex mu;
+    static bool configured[64] = {false};
+    int dev = 0;
+    KP_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && !configured[dev]) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!configured[dev]) {
+            cudaMemPool_t pool;
+            if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+                uint64_t threshold = ~0ull;   // keep freed blocks for reuse
+                cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+            }
+            configured[dev] = true;
+        }
+    }
+    const cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_error(e, "cudaMallocAsync");
+    }
+    return KP_OK;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+// ---------------------------------------------------------------------------
+// input check
+// ---------------------------------------------------------------------------
+struct CheckAcc {
+    unsigned long long csum;
+    unsigned long long wsum;
+    int32_t err;
+    int32_t pad;
+};
+
+__global__ void k_validate(int32_t n, int32_t nnz, const int32_t *__restrict__ xadj,
+                           const int32_t *__restrict__ adjncy, const int32_t *__restrict__ ewgt,
+                           const int32_t *__restrict__ vwgt, CheckAcc *acc) {
+    constexpr int G = 8;
+    const unsigned gmask = group_mask<G>();
+    const int gl = threadIdx.x & (G - 1);
+    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+    int bad = 0;
+    unsigned long long csum = 0, wsum = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (xadj[0] != 0 || xadj[n] != nnz)) bad = 1;
+    for (int64_t v = gid; v < n; v += ngroups) {
+        const int32_t beg = xadj[v], end = xadj[v + 1];
+        if (beg < 0 || end < beg || end > nnz) {
+            bad = 1;
+            continue;
+        }
+        if (gl == 0) {
+            const int32_t c = vwgt[v];
+            if (c < 0) bad = 1;
+            else csum += (unsigned long long)c;
+        }
+        for (int32_t e = beg + gl; e < end; e += G) {
+            const int32_t u = adjncy[e];
+            const int32_t w = ewgt[e];
+            if (u < 0 || u >= n || u == v || w <= 0) {
+                bad = 1;
+                continue;
+            }
+            if (e > beg && adjncy[e - 1] >= u) bad = 1;
+            // the reverse entry (u, v) with the same weight
+            int32_t lo = xadj[u], hi = xadj[u + 1] - 1;
+            if (lo < 0 || hi >= nnz) {
+                bad = 1;
+                continue;
+            }
+            int found = -1;
+            while (lo <= hi) {
+                const int32_t mid = lo + (hi - lo) / 2;
+                const int32_t t = adjncy[mid];
+                if (t == (int32_t)v) {
+                    found = mid;
+                    break;
+                }
+                if (t < (int32_t)v) lo = mid + 1;
+                else hi = mid - 1;
+            }
+            if (found < 0 || ewgt[found] != w) bad = 1;
+            if (u > v) wsum += (unsigned long long)w;
+        }
+    }
+    (void)gmask;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        csum += __shfl_xor_sync(0xffffffffu, csum, o);
+        wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (csum) atomicAdd(&acc->csum, csum);
+        if (wsum) atomicAdd(&acc->wsum, wsum);
+    }
+    if (bad) atomicOr(&acc->err, ERR_GRAPH_INVALID);
+}
+
+kp_status validate_graph(const kp_graph *g, cudaStream_t s, int64_t) {
+    CheckAcc *acc = nullptr;
+    KP_TRY(dev_alloc_n(&acc, 1, s));
+    thread_local CheckAcc *host = nullptr;
+    if (!host && cudaMallocHost((void **)&host, sizeof(CheckAcc)) != cudaSuccess) {
+        host = nullptr;
+        dev_free(acc, s);
+        return set_error(KP_ERR_OOM, "pinned host buffer");
+    }
+    cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(CheckAcc), s);
+    if (e == cudaSuccess) {
+        const int64_t want = ((int64_t)g->n * 8 + 255) / 256;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 16));
+        k_validate<<<grid, 256, 0, s>>>(g->n, g->nnz, g->xadj, g->adjncy, g->ewgt, g->vwgt, acc);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, acc, sizeof(CheckAcc), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(acc, s);
+    if (e != cudaSuccess) return cuda_error(e, "graph check");
+    if (host->err) return set_error(KP_ERR_INVALID, "graph is not a valid symmetric sorted CSR with omega > 0, c >= 0");
+    if (host->csum >= (1ull << 31)) return set_error(KP_ERR_OVERFLOW, "sum of node weights >= 2^31");
+    if (host->wsum >= (1ull << 31)) return set_error(KP_ERR_OVERFLOW, "sum of edge weights >= 2^31");
+    return KP_OK;
+}
+
+kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, kp_hierarchy **out);
+kp_status project_impl(const kp_hierarchy *h, const int32_t *coarse_part, int32_t *fine_part, cudaStream_t s);
+kp_status cut_gain_impl(const kp_graph *g, const int32_t *part, int32_t k, double eps, kp_cut_gain_out *out,
+                        cudaStream_t s);
+kp_status pipeline_host_impl(const kp_graph *hg, const kp_options *o, int32_t k, double eps,
+                             kp_initial_partition_fn ip, void *user, int32_t *fine_part, int64_t *gain,
+                             int32_t *target, int64_t *block_w, kp_cut_gain_out *out, int32_t *num_levels,
+                             cudaStream_t s);
+
+}  // namespace kp
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+using namespace kp;
+
+#define KP_GUARD(expr)                                              \
+    try {                                                           \
+        return (expr);                                              \
+    } catch (const std::bad_alloc &) {                              \
+        return set_error(KP_ERR_OOM, "host allocation failed");     \
+    } catch (...) {                                                 \
+        return set_error(KP_ERR_CUDA, "unexpected exception");      \
+    }
+
+extern "C" {
+
+void kp_options_default(kp_options *o) {
+    if (!o) return;
+    o->rating = KP_RATING_EXPANSION_STAR2;
+    o->seed = 1;
+    o->stop_size = 40;
+    o->max_levels = 64;
+    o->min_shrink_permille = 50;
+    o->spin_limit = 1ll << 22;
+    o->validate = 1;
+}
+
+kp_status kp_coarsen(const kp_graph *g, const kp_options *o, kp_stream s, kp_hierarchy **out) {
+    if (!g || !out) return set_error(KP_ERR_INVALID, "null argument");
+    *out = nullptr;
+    kp_options def;
+    kp_options_default(&def);
+    if (o && o->max_levels > 120) return set_error(KP_ERR_UNSUPPORTED, "max_levels above 120");
+    g_last_error.clear();
+    KP_GUARD(coarsen_impl(g, o ? o : &def, (cudaStream_t)s, out));
+}
+
+kp_status kp_hierarchy_num_levels(const kp_hierarchy *h, int32_t *num_levels) {
+    if (!h || !num_levels) return set_error(KP_ERR_INVALID, "null argument");
+    *num_levels = (int32_t)h->levels.size();
+    return KP_OK;
+}
+
+kp_status kp_hierarchy_level(const kp_hierarchy *h, int32_t l, kp_graph *view, const int32_t **map) {
+    if (!h || !view) return set_error(KP_ERR_INVALID, "null argument");
+    if (l < 0 || l >= (int32_t)h->levels.size()) return set_error(KP_ERR_INVALID, "level out of range");
+    const kp_level &L = h->levels[(size_t)l];
+    view->n = L.n;
+    view->nnz = L.nnz;
+    view->xadj = L.xadj;
+    view->adjncy = L.adjncy;
+    view->ewgt = L.ewgt;
+    view->vwgt = L.vwgt;
+    if (map) *map = L.map;
+    return KP_OK;
+}
+
+kp_status kp_hierarchy_stats(const kp_hierarchy *h, int32_t *total_rounds, int64_t *total_matched) {
+    if (!h) return set_error(KP_ERR_INVALID, "null argument");
+    if (total_rounds) *total_rounds = h->total_rounds;
+    if (total_matched) *total_matched = h->total_matched;
+    return KP_OK;
+}
+
+void kp_hierarchy_free(kp_hierarchy *h) {
+    if (!h) return;
+    for (void *p : h->allocations) dev_free(p, h->stream);
+    cudaStreamSynchronize(h->stream);
+    delete h;
+}
+
+kp_status kp_project(const kp_hierarchy *h, const int32_t *coarse_part, int32_t *fine_part, kp_stream s) {
+    KP_GUARD(project_impl(h, coarse_part, fine_part, (cudaStream_t)s));
+}
+
+kp_status kp_cut_gain(const kp_graph *g, const int32_t *part, int32_t k, double eps, kp_cut_gain_out *out,
+                      kp_stream s) {
+    KP_GUARD(cut_gain_impl(g, part, k, eps, out, (cudaStream_t)s));
+}
+
+kp_status kp_pipeline_host(const kp_graph *g, const kp_options *o, int32_t k, double eps,
+                           kp_initial_partition_fn ip, void *user, int32_t *fine_part, int64_t *gain,
+                           int32_t *target, int64_t *block_w, kp_cut_gain_out *out, int32_t *num_levels,
+                           kp_stream s) {
+    kp_options def;
+    kp_options_default(&def);
+    if (o && o->max_levels > 120) return set_error(KP_ERR_UNSUPPORTED, "max_levels above 120");
+    KP_GUARD(pipeline_host_impl(g, o ? o : &def, k, eps, ip, user, fine_part, gain, target, block_w, out,
+                                num_levels, (cudaStream_t)s));
+}
+
+const char *kp_last_error(void) { return g_last_error.c_str(); }
+
+const char *kp_version(void) { return "kp-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

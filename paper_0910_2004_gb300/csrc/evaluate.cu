@@ -1,0 +1,398 @@
+// Projection of a coarse partition (uncontraction, Section 2) and evaluation
+// of a partition: cut and block weights (Section 2), balance bound L_max
+// (Section 2), imbalance and per-node FM gains (Section 5.2).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+#include "kp_internal.cuh"
+
+namespace kp {
+
+constexpr int PROJECT_MAX_LEVELS = 128;
+
+struct ProjectParams {
+    int32_t n0;
+    int32_t L;
+    const int32_t *coarse_part;
+    int32_t *fine_part;
+    const int32_t *maps[PROJECT_MAX_LEVELS];
+};
+
+// p_0(v) = p_L(map_{L-1}(...map_0(v))): every level of the uncontraction in
+// one pass, a chain of gathers per input node.
+__global__ void k_project(const __grid_constant__ ProjectParams p) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n0; v += stride) {
+        int32_t x = (int32_t)v;
+        for (int l = 0; l < p.L; l++) x = p.maps[l][x];
+        p.fine_part[v] = p.coarse_part[x];
+    }
+}
+
+// Device accumulators of one evaluation.
+struct EvalAcc {
+    unsigned long long ext_sum;   // sum over v of omega(v, other blocks) = 2 * cut
+    unsigned long long total_c;
+    long long max_c;
+    long long max_bw;
+    int32_t err;
+    int32_t pad[3];
+};
+
+constexpr int EVAL_BLOCK = 256;
+constexpr int BW_SMEM = 2048;   // block weights kept in shared memory up to this k
+
+struct CutGainParams {
+    int32_t n;
+    int32_t k;
+    const int32_t *__restrict__ xadj;
+    const int32_t *__restrict__ adjncy;
+    const int32_t *__restrict__ ewgt;
+    const int32_t *__restrict__ vwgt;
+    const int32_t *__restrict__ part;
+    unsigned long long *block_w;
+    int64_t *gain;
+    int32_t *target;
+    EvalAcc *acc;
+};
+
+// One G-lane group per node.  The adjacent blocks of v are visited in
+// increasing id order (each step finds the smallest block id above the last
+// one and sums the weight towards it), so the first block reaching the
+// largest connection is the smallest such id.
+template <int G>
+__global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p) {
+    __shared__ unsigned long long s_bw[BW_SMEM];
+    __shared__ unsigned long long s_red[EVAL_BLOCK / 32];
+    __shared__ long long s_max[EVAL_BLOCK / 32];
+    const bool smem_bw = p.k <= BW_SMEM;
+    if (smem_bw)
+        for (int i = threadIdx.x; i < p.k; i += blockDim.x) s_bw[i] = 0;
+    __syncthreads();
+    const unsigned gmask = group_mask<G>();
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+    unsigned long long ext_acc = 0, c_acc = 0;
+    long long cmax = 0;
+    int32_t bad = 0;
+    for (int64_t v = gid; v < p.n; v += ngroups) {
+        const int32_t pv = p.part[v];
+        const bool pv_ok = pv >= 0 && pv < p.k;
+        const int32_t beg = p.xadj[v], end = p.xadj[v + 1];
+        const int32_t deg = end - beg;
+        // entries held in registers when the row fits the group
+        int32_t rb = -1, rw = 0;
+        if (deg <= G && gl < deg) {
+            rb = p.part[p.adjncy[beg + gl]];
+            rw = p.ewgt[beg + gl];
+            if (rb < 0 || rb >= p.k) {
+                bad = 1;
+                rb = -1;
+            }
+        }
+        // pass over the row: internal weight, total weight, smallest other block
+        long long inw = 0, tot = 0;
+        int32_t nextb = 0x7fffffff;
+        if (deg <= G) {
+            if (rb >= 0) {
+                tot = rw;
+                if (rb == pv) inw = rw;
+                else nextb = rb;
+            }
+        } else {
+            for (int32_t e = beg + gl; e < end; e += G) {
+                const int32_t b = p.part[p.adjncy[e]];
+                const int32_t w = p.ewgt[e];
+                if (b < 0 || b >= p.k) {
+                    bad = 1;
+                    continue;
+                }
+                tot += w;
+                if (b == pv) inw += w;
+                else nextb = min(nextb, b);
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            inw += __shfl_xor_sync(gmask, inw, o);
+            tot += __shfl_xor_sync(gmask, tot, o);
+            nextb = min(nextb, __shfl_xor_sync(gmask, nextb, o));
+        }
+        int32_t best = -1;
+        long long best_conn = 0;
+        while (nextb != 0x7fffffff) {
+            const int32_t cur = nextb;
+            long long conn = 0;
+            nextb = 0x7fffffff;
+            if (deg <= G) {
+                if (rb == cur) conn = rw;
+                else if (rb > cur && rb != pv) nextb = rb;
+            } else {
+                for (int32_t e = beg + gl; e < end; e += G) {
+                    const int32_t b = p.part[p.adjncy[e]];
+                    if (b < 0 || b >= p.k) continue;
+                    if (b == cur) conn += p.ewgt[e];
+                    else if (b > cur && b != pv) nextb = min(nextb, b);
+                }
+            }
+#pragma unroll
+            for (int o = G / 2; o > 0; o >>= 1) {
+                conn += __shfl_xor_sync(gmask, conn, o);
+                nextb = min(nextb, __shfl_xor_sync(gmask, nextb, o));
+            }
+            if (conn > best_conn) {
+                best_conn = conn;
+                best = cur;
+            }
+        }
+        if (gl == 0) {
+            const int32_t c = p.vwgt[v];
+            p.gain[v] = (best >= 0 ? best_conn : 0) - inw;
+            p.target[v] = best;
+            ext_acc += (unsigned long long)(tot - inw);
+            c_acc += (unsigned long long)(long long)c;
+            cmax = max(cmax, (long long)c);
+            if (!pv_ok) {
+                bad = 1;
+            } else if (smem_bw) {
+                atomicAdd(&s_bw[pv], (unsigned long long)(long long)c);
+            } else {
+                atomicAdd(&p.block_w[pv], (unsigned long long)(long long)c);
+            }
+        }
+    }
+    // block reductions, then one atomic per block
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ext_acc += __shfl_xor_sync(0xffffffffu, ext_acc, o);
+        c_acc += __shfl_xor_sync(0xffffffffu, c_acc, o);
+        cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    }
+    const int warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_red[warp] = ext_acc;
+        s_max[warp] = cmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long e = 0;
+        long long m = 0;
+        for (int w = 0; w < EVAL_BLOCK / 32; w++) {
+            e += s_red[w];
+            m = max(m, s_max[w]);
+        }
+        atomicAdd(&p.acc->ext_sum, e);
+        atomicMax(&p.acc->max_c, m);
+    }
+    __syncthreads();
+    if (lane == 0) s_red[warp] = c_acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long c = 0;
+        for (int w = 0; w < EVAL_BLOCK / 32; w++) c += s_red[w];
+        atomicAdd(&p.acc->total_c, c);
+    }
+    if (bad) atomicOr(&p.acc->err, ERR_BAD_PART);
+    if (smem_bw)
+        for (int i = threadIdx.x; i < p.k; i += blockDim.x)
+            if (s_bw[i]) atomicAdd(&p.block_w[i], s_bw[i]);
+}
+
+__global__ void k_max_block(int32_t k, const long long *block_w, EvalAcc *acc) {
+    long long m = 0;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) m = max(m, block_w[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&acc->max_bw, m);
+}
+
+// floor((1+eps) c(V)/k + max c) with eps read as round(eps * 10^6) ppm.
+int64_t l_max_of(int64_t total_c, int64_t max_c, int32_t k, double eps) {
+    const long long eps_ppm = llround(eps * 1e6);
+    const __int128 num = (__int128)(1000000 + eps_ppm) * total_c + (__int128)k * 1000000 * max_c;
+    const __int128 den = (__int128)k * 1000000;
+    return (int64_t)(num / den);
+}
+
+namespace {
+
+kp_status check_eval_args(const kp_graph *g, const int32_t *part, int32_t k, double eps,
+                          const kp_cut_gain_out *out) {
+    if (!g || !out) return set_error(KP_ERR_INVALID, "null argument");
+    if (k < 1) return set_error(KP_ERR_INVALID, "k must be >= 1");
+    if (!(eps >= 0.0) || eps > 1000.0) return set_error(KP_ERR_INVALID, "eps must be in [0, 1000]");
+    if (g->n < 0) return set_error(KP_ERR_INVALID, "negative n");
+    if (g->n > 0 && (!part || !g->xadj || !g->vwgt || !out->gain || !out->target))
+        return set_error(KP_ERR_INVALID, "null array");
+    if (!out->block_w) return set_error(KP_ERR_INVALID, "null block_w");
+    return KP_OK;
+}
+
+}  // namespace
+
+// Evaluation with the accumulators in caller-provided device memory `acc`.
+kp_status cut_gain_with(const kp_graph *g, const int32_t *part, int32_t k, double eps, kp_cut_gain_out *out,
+                        cudaStream_t s, EvalAcc *acc, EvalAcc *host_acc) {
+    KP_TRY(check_eval_args(g, part, k, eps, out));
+    KP_CUDA(cudaMemsetAsync(acc, 0, sizeof(EvalAcc), s));
+    KP_CUDA(cudaMemsetAsync(out->block_w, 0, sizeof(int64_t) * (size_t)k, s));
+    if (g->n > 0) {
+        CutGainParams p;
+        p.n = g->n;
+        p.k = k;
+        p.xadj = g->xadj;
+        p.adjncy = g->adjncy;
+        p.ewgt = g->ewgt;
+        p.vwgt = g->vwgt;
+        p.part = part;
+        p.block_w = reinterpret_cast<unsigned long long *>(out->block_w);
+        p.gain = out->gain;
+        p.target = out->target;
+        p.acc = acc;
+        const double avg = (double)g->nnz / (double)g->n;
+        const int grid_cap = num_sms() * 8;
+        auto grid_for = [&](int G) {
+            const int64_t want = ((int64_t)g->n * G + EVAL_BLOCK - 1) / EVAL_BLOCK;
+            return (int)std::max<int64_t>(1, std::min<int64_t>(want, grid_cap));
+        };
+        if (avg <= 5.0) k_cut_gain<4><<<grid_for(4), EVAL_BLOCK, 0, s>>>(p);
+        else if (avg <= 10.0) k_cut_gain<8><<<grid_for(8), EVAL_BLOCK, 0, s>>>(p);
+        else if (avg <= 20.0) k_cut_gain<16><<<grid_for(16), EVAL_BLOCK, 0, s>>>(p);
+        else k_cut_gain<32><<<grid_for(32), EVAL_BLOCK, 0, s>>>(p);
+        KP_CUDA(cudaGetLastError());
+        k_max_block<<<1, 1024, 0, s>>>(k, reinterpret_cast<const long long *>(out->block_w), acc);
+        KP_CUDA(cudaGetLastError());
+    }
+    KP_CUDA(cudaMemcpyAsync(host_acc, acc, sizeof(EvalAcc), cudaMemcpyDeviceToHost, s));
+    KP_CUDA(cudaStreamSynchronize(s));
+    if (host_acc->err & ERR_BAD_PART) return set_error(KP_ERR_INVALID, "block id outside [0,k)");
+    out->cut = (int64_t)(host_acc->ext_sum / 2);
+    out->total_c = (int64_t)host_acc->total_c;
+    out->max_c = (int64_t)host_acc->max_c;
+    out->l_max = l_max_of(out->total_c, out->max_c, k, eps);
+    out->imbalance = std::max<int64_t>(0, (int64_t)host_acc->max_bw - out->l_max);
+    return KP_OK;
+}
+
+kp_status cut_gain_impl(const kp_graph *g, const int32_t *part, int32_t k, double eps, kp_cut_gain_out *out,
+                        cudaStream_t s) {
+    KP_TRY(check_eval_args(g, part, k, eps, out));
+    EvalAcc *acc = nullptr;
+    KP_TRY(dev_alloc_n(&acc, 1, s));
+    thread_local EvalAcc *host_acc = nullptr;
+    if (!host_acc && cudaMallocHost((void **)&host_acc, sizeof(EvalAcc)) != cudaSuccess) {
+        host_acc = nullptr;
+        dev_free(acc, s);
+        return set_error(KP_ERR_OOM, "pinned host accumulator");
+    }
+    const kp_status st = cut_gain_with(g, part, k, eps, out, s, acc, host_acc);
+    dev_free(acc, s);
+    return st;
+}
+
+kp_status project_impl(const kp_hierarchy *h, const int32_t *coarse_part, int32_t *fine_part, cudaStream_t s) {
+    if (!h || (h->levels[0].n > 0 && (!coarse_part || !fine_part))) return set_error(KP_ERR_INVALID, "null argument");
+    const int32_t L = (int32_t)h->levels.size() - 1;
+    if (L >= PROJECT_MAX_LEVELS) return set_error(KP_ERR_UNSUPPORTED, "too many levels");
+    const int32_t n0 = h->levels[0].n;
+    if (n0 == 0) return KP_OK;
+    ProjectParams p;
+    p.n0 = n0;
+    p.L = L;
+    p.coarse_part = coarse_part;
+    p.fine_part = fine_part;
+    for (int l = 0; l < L; l++) p.maps[l] = h->levels[l].map;
+    const int64_t want = ((int64_t)n0 + 255) / 256;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 16));
+    k_project<<<grid, 256, 0, s>>>(p);
+    KP_CUDA(cudaGetLastError());
+    return KP_OK;
+}
+
+kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, kp_hierarchy **out);
+
+kp_status pipeline_host_impl(const kp_graph *hg, const kp_options *o, int32_t k, double eps,
+                             kp_initial_partition_fn ip, void *user, int32_t *fine_part, int64_t *gain,
+                             int32_t *target, int64_t *block_w, kp_cut_gain_out *out, int32_t *num_levels,
+                             cudaStream_t s) {
+    if (!hg || !o || !ip || !out) return set_error(KP_ERR_INVALID, "null argument");
+    if (hg->n < 0 || hg->nnz < 0) return set_error(KP_ERR_INVALID, "negative size");
+    if (k < 1) return set_error(KP_ERR_INVALID, "k must be >= 1");
+    const int32_t n = hg->n, nnz = hg->nnz;
+    int32_t *d_xadj = nullptr, *d_adj = nullptr, *d_w = nullptr, *d_c = nullptr;
+    int32_t *d_cpart = nullptr, *d_fpart = nullptr, *d_target = nullptr;
+    int64_t *d_gain = nullptr, *d_bw = nullptr;
+    kp_hierarchy *h = nullptr;
+    std::vector<int32_t> cw, cpart;
+    kp_status st = KP_OK;
+    auto cleanup = [&]() {
+        if (h) kp_hierarchy_free(h);
+        void *ptrs[] = {d_xadj, d_adj, d_w, d_c, d_cpart, d_fpart, d_target, d_gain, d_bw};
+        for (void *q : ptrs)
+            if (q) dev_free(q, s);
+    };
+#define PH(call)                  \
+    do {                          \
+        st = (call);              \
+        if (st != KP_OK) {        \
+            cleanup();            \
+            return st;            \
+        }                         \
+    } while (0)
+#define PH_CUDA(call) PH(((call) == cudaSuccess) ? KP_OK : cuda_error(cudaGetLastError(), #call))
+    PH(dev_alloc_n(&d_xadj, (int64_t)n + 1, s));
+    PH(dev_alloc_n(&d_adj, nnz, s));
+    PH(dev_alloc_n(&d_w, nnz, s));
+    PH(dev_alloc_n(&d_c, n, s));
+    PH(dev_alloc_n(&d_fpart, n, s));
+    PH(dev_alloc_n(&d_target, n, s));
+    PH(dev_alloc_n(&d_gain, n, s));
+    PH(dev_alloc_n(&d_bw, k, s));
+    PH_CUDA(cudaMemcpyAsync(d_xadj, hg->xadj, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s));
+    if (nnz > 0) {
+        PH_CUDA(cudaMemcpyAsync(d_adj, hg->adjncy, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
+        PH_CUDA(cudaMemcpyAsync(d_w, hg->ewgt, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
+    }
+    if (n > 0) PH_CUDA(cudaMemcpyAsync(d_c, hg->vwgt, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
+    kp_graph dg = {n, nnz, d_xadj, d_adj, d_w, d_c};
+    PH(coarsen_impl(&dg, o, s, &h));
+    const kp_level &top = h->levels.back();
+    cw.resize((size_t)std::max(top.n, 1));
+    cpart.resize((size_t)std::max(top.n, 1));
+    if (top.n > 0)
+        PH_CUDA(cudaMemcpyAsync(cw.data(), top.vwgt, sizeof(int32_t) * (size_t)top.n, cudaMemcpyDeviceToHost, s));
+    PH_CUDA(cudaStreamSynchronize(s));
+    if (ip(top.n, cw.data(), k, cpart.data(), user) != 0) PH(set_error(KP_ERR_INVALID, "initial partition callback failed"));
+    PH(dev_alloc_n(&d_cpart, top.n, s));
+    if (top.n > 0)
+        PH_CUDA(cudaMemcpyAsync(d_cpart, cpart.data(), sizeof(int32_t) * (size_t)top.n, cudaMemcpyHostToDevice, s));
+    PH(project_impl(h, d_cpart, d_fpart, s));
+    kp_cut_gain_out o2;
+    o2.block_w = d_bw;
+    o2.gain = d_gain;
+    o2.target = d_target;
+    PH(cut_gain_impl(&dg, d_fpart, k, eps, &o2, s));
+    if (n > 0) {
+        if (fine_part) PH_CUDA(cudaMemcpyAsync(fine_part, d_fpart, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+        if (gain) PH_CUDA(cudaMemcpyAsync(gain, d_gain, sizeof(int64_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+        if (target) PH_CUDA(cudaMemcpyAsync(target, d_target, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    }
+    if (block_w) PH_CUDA(cudaMemcpyAsync(block_w, d_bw, sizeof(int64_t) * (size_t)k, cudaMemcpyDeviceToHost, s));
+    PH_CUDA(cudaStreamSynchronize(s));
+    out->cut = o2.cut;
+    out->total_c = o2.total_c;
+    out->max_c = o2.max_c;
+    out->l_max = o2.l_max;
+    out->imbalance = o2.imbalance;
+    if (num_levels) *num_levels = (int32_t)h->levels.size();
+#undef PH_CUDA
+#undef PH
+    cleanup();
+    return cudaStreamSynchronize(s) == cudaSuccess ? KP_OK : cuda_error(cudaGetLastError(), "final sync");
+}
+
+}  // namespace kp

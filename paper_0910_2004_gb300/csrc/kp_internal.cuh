@@ -1,0 +1,279 @@
+// Internal declarations shared by the library's translation units.
+// Device helpers: exact rating comparison, tie-break hash, a bounded grid
+// barrier for persistent kernels, and a three-phase device-wide scan.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "kp.h"
+
+namespace kp {
+
+// ---------------------------------------------------------------------------
+// error state (host)
+// ---------------------------------------------------------------------------
+kp_status set_error(kp_status st, const std::string &msg);
+kp_status cuda_error(cudaError_t e, const char *what);
+
+#define KP_CUDA(call)                                                  \
+    do {                                                               \
+        cudaError_t _e = (call);                                       \
+        if (_e != cudaSuccess) return ::kp::cuda_error(_e, #call);     \
+    } while (0)
+
+#define KP_TRY(call)                                                   \
+    do {                                                               \
+        kp_status _s = (call);                                         \
+        if (_s != KP_OK) return _s;                                    \
+    } while (0)
+
+int num_sms();
+
+// Stream-ordered device allocation from the device's default memory pool
+// (its release threshold is raised once so freed blocks are reused).
+kp_status dev_alloc(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
+template <class T>
+kp_status dev_alloc_n(T **p, int64_t count, cudaStream_t s) {
+    return dev_alloc(reinterpret_cast<void **>(p), sizeof(T) * (size_t)(count > 0 ? count : 1), s);
+}
+
+// ---------------------------------------------------------------------------
+// device-side status flags
+// ---------------------------------------------------------------------------
+enum : int32_t {
+    ERR_TIMEOUT = 1,
+    ERR_BAD_PART = 2,
+    ERR_GRAPH_INVALID = 4,
+};
+
+// ---------------------------------------------------------------------------
+// exact comparison of ratings num/den (Section 3.1)
+// ---------------------------------------------------------------------------
+// a/b against c/d by the 128-bit cross products a*d and c*b.  Numerators are
+// > 0 and denominators >= 0, so a zero denominator (rating +infinity) wins
+// against any finite rating and ties with another infinity.
+__device__ __forceinline__ int cmp_frac(uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+    const uint64_t lh = __umul64hi(a, d), ll = a * d;
+    const uint64_t rh = __umul64hi(c, b), rl = c * b;
+    if (lh != rh) return lh > rh ? 1 : -1;
+    if (ll != rl) return ll > rl ? 1 : -1;
+    return 0;
+}
+
+// splitmix64 output function (Steele, Lea, Flood, OOPSLA 2014).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t edge_hash(uint64_t seed, int32_t u, int32_t v) {
+    const uint32_t lo = (uint32_t)min(u, v), hi = (uint32_t)max(u, v);
+    return splitmix64(seed ^ (((uint64_t)lo << 32) | hi));
+}
+
+// ---------------------------------------------------------------------------
+// bounded grid barrier for cooperative (co-resident) grids
+// ---------------------------------------------------------------------------
+struct GridBarrier {
+    unsigned int count;
+    unsigned int generation;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_relaxed_i32(const int32_t *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// All blocks of the grid meet here.  Returns false (and every block returns
+// false soon after) when a wait exceeded spin_limit iterations or another
+// block already flagged an error; the error flag then holds ERR_TIMEOUT.
+__device__ __forceinline__ bool grid_sync(GridBarrier *bar, int32_t *err, long long spin_limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned int gen = ld_acquire_u32(&bar->generation);
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            st_release_u32(&bar->generation, gen + 1);
+        } else {
+            long long it = 0;
+            while (ld_acquire_u32(&bar->generation) == gen) {
+                if (ld_relaxed_i32(err) != 0) { ok = 0; break; }
+                if (++it > spin_limit) {
+                    atomicOr(err, ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        if (ok && ld_relaxed_i32(err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Mask of the G-lane group that contains this lane (G divides 32).
+template <int G>
+__device__ __forceinline__ unsigned group_mask() {
+    if constexpr (G == 32) {
+        return 0xffffffffu;
+    } else {
+        const unsigned lane = threadIdx.x & 31u;
+        return ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// three-phase device-wide exclusive scan over 64-bit values produced and
+// consumed by an operator:
+//   uint64_t Op::load(int64_t i)                          value of item i
+//   void     Op::store(int64_t i, uint64_t excl, uint64_t v)  prefix of item i
+//   void     Op::total(uint64_t t)                        sum of all items
+// Items are processed in order, so store() sees the exact prefix.
+// ---------------------------------------------------------------------------
+constexpr int SCAN_BLOCK = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+template <int BLOCK>
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *total) {
+    __shared__ uint64_t warp_sums[BLOCK / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t s = lane < BLOCK / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, s, d);
+            if (lane >= d) s += y;
+        }
+        if (lane < BLOCK / 32) warp_sums[lane] = s;
+    }
+    __syncthreads();
+    const uint64_t warp_prefix = warp > 0 ? warp_sums[warp - 1] : 0;
+    *total = warp_sums[BLOCK / 32 - 1];
+    __syncthreads();
+    return warp_prefix + x - v;
+}
+
+template <class Op>
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_up(Op op, int64_t count, uint64_t *partials) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++)
+        if (base + j < count) s += op.load(base + j);
+    uint64_t total;
+    block_exclusive_scan<SCAN_BLOCK>(s, &total);
+    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+}
+
+template <class Op>
+__global__ void __launch_bounds__(1024) k_scan_mid(Op op, int64_t tiles, uint64_t *partials) {
+    uint64_t carry = 0;
+    for (int64_t base = 0; base < tiles; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const uint64_t v = i < tiles ? partials[i] : 0;
+        uint64_t total;
+        const uint64_t ex = block_exclusive_scan<1024>(v, &total);
+        if (i < tiles) partials[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) op.total(carry);
+}
+
+template <class Op>
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_down(Op op, int64_t count, const uint64_t *partials) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint64_t v[SCAN_ITEMS];
+    uint64_t s = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        v[j] = base + j < count ? op.load(base + j) : 0;
+        s += v[j];
+    }
+    uint64_t total;
+    uint64_t p = partials[blockIdx.x] + block_exclusive_scan<SCAN_BLOCK>(s, &total);
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; j++) {
+        if (base + j < count) op.store(base + j, p, v[j]);
+        p += v[j];
+    }
+}
+
+inline int64_t scan_tiles(int64_t count) { return (count + SCAN_TILE - 1) / SCAN_TILE; }
+
+// partials must hold scan_tiles(count) entries.
+template <class Op>
+cudaError_t device_scan(const Op &op, int64_t count, uint64_t *partials, cudaStream_t s) {
+    const int64_t tiles = scan_tiles(count);
+    if (tiles > 0) k_scan_up<Op><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(op, count, partials);
+    k_scan_mid<Op><<<1, 1024, 0, s>>>(op, tiles, partials);
+    if (tiles > 0) k_scan_down<Op><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(op, count, partials);
+    return cudaGetLastError();
+}
+
+}  // namespace kp
+
+// The hierarchy handle (opaque to C callers).
+struct kp_level {
+    int32_t n = 0;
+    int32_t nnz = 0;
+    int32_t *xadj = nullptr;
+    int32_t *adjncy = nullptr;
+    int32_t *ewgt = nullptr;
+    int32_t *vwgt = nullptr;
+    int32_t *map = nullptr;   // to the next level; nullptr on the coarsest
+    bool owned = false;
+};
+
+struct kp_hierarchy {
+    std::vector<kp_level> levels;
+    std::vector<void *> allocations;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int32_t total_rounds = 0;
+    int64_t total_matched = 0;
+};
