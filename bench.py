@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark of the whole data-parallel path on one synthetic workload.
+
+A step is one pass of the path: coarsen the input level after level (rating,
+handshake matching, contraction), partition the coarsest graph (a seeded
+random balanced partition on the host, standing in for initial
+partitioning), project it back to the input, and evaluate cut, block weights
+and gains.  The metric is coarsened input edges per second (m_0 undirected
+edges per step / step time), aggregated over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rgg20]
+  python bench.py --impl reference ...   (the CPU oracle, timed on the host)
+
+Multi-GPU (torchrun): every rank coarsens its own replica of the workload
+(independent problems, no collective on the data path), rank 0 prints one
+JSON line with the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0910_2004_gb300 import inputs as I  # noqa: E402
+
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+HBM_PEAK_FALLBACK = 6800.0
+
+
+def workloads():
+    return {
+        "rgg20": dict(
+            desc="2D random geometric graph, n=2^20 uniform points, radius for mean degree 6, unit int32 "
+                 "weights, expansion*2 rating, full hierarchy to <= 20*64 nodes, cut/gain k=64 eps=0.03",
+            make=lambda: I.rgg2d(1 << 20, 1), rating="expansion*2", k=64, eps=0.03),
+        "grid64": dict(
+            desc="2D 5-point grid 64x64, unit weights, expansion*2, coarsen to <= 20*2 nodes, cut/gain k=2 eps=0.03",
+            make=lambda: I.grid2d(64, 64), rating="expansion*2", k=2, eps=0.03),
+        "grid256": dict(
+            desc="3D 7-point grid 256^3, unit weights, innerOuter, full hierarchy to <= 20*256 nodes, "
+                 "cut/gain k=256 eps=0.03",
+            make=lambda: I.grid3d(256, 256, 256), rating="innerOuter", k=256, eps=0.03),
+    }
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_PEAK_FALLBACK, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.gpu_index), "-lms", "100"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes (int32 ids/weights), per phase, from the level sizes
+# ---------------------------------------------------------------------------
+def algorithmic_bytes(sizes, rating):
+    """sizes: [(n_l, nnz_l)] for l = 0..L.  Bytes the method must move:
+    match   read the fine CSR once (xadj, adjncy, ewgt), c (and Out), write match
+    relabel read match, write map and c'
+    contract read the fine CSR again, write the coarse rows
+    csr     write the coarse xadj"""
+    out = {"match": 0, "relabel": 0, "contract": 0, "csr": 0, "out": 0}
+    if rating == "innerOuter" and sizes:
+        n0, nnz0 = sizes[0]
+        out["out"] = 4 * (n0 + 1) + 4 * nnz0 + 4 * n0
+    for (n, nnz), (n2, nnz2) in zip(sizes, sizes[1:]):
+        out["match"] += 4 * (n + 1) + 8 * nnz + 4 * n + 4 * n + (4 * n if rating == "innerOuter" else 0)
+        out["relabel"] += 4 * n + 4 * n + 4 * n2
+        out["contract"] += 4 * (n + 1) + 8 * nnz + 8 * nnz2 + (4 * n2 if rating == "innerOuter" else 0)
+        out["csr"] += 4 * (n2 + 1) + 8 * nnz2
+    return out
+
+
+def eval_bytes(n, nnz, k):
+    # cut/gain: xadj, adjncy, ewgt, part of the row ends (gathered), c, part; writes gain, target; block weights
+    return 4 * (n + 1) + 8 * nnz + 4 * nnz + 4 * n + 4 * n + 12 * n + 8 * k
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_step(g, wl, seed=1):
+    import oracle as O
+    k = wl["k"]
+    h = O.coarsen(g, wl["rating"], 1, 20 * k)
+    cpart = I.random_balanced_partition(h.levels[-1].n, k, seed)
+    part = O.project(h.maps, cpart)
+    r = O.cut_gain(g, part, k, wl["eps"])
+    return h, r
+
+
+def run_reference(args, wl, g):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_step(g, wl)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle_step(g, wl)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = g.m * args.steps / total
+    line = {
+        "impl": "reference", "metric": "coarsened edges/s (full hierarchy)", "value": value, "unit": "edges/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "n": g.n, "m": g.m},
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": f"the whole workload per step ({args.steps} steps), single-threaded C/numpy oracle"},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rgg20", choices=sorted(workloads()))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    args = ap.parse_args()
+    wl = workloads()[args.workload]
+    g = wl["make"]()
+    if args.impl == "reference":
+        return run_reference(args, wl, g)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0910_2004_gb300 import binding as B
+
+    k, eps, rating = wl["k"], wl["eps"], wl["rating"]
+    stop = 20 * k
+    dg = B.DeviceGraph.from_csr(g)
+    fine = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    bw = torch.empty(k, dtype=torch.int64, device="cuda")
+    gain = torch.empty(g.n, dtype=torch.int64, device="cuda")
+    target = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(seed):
+        h = B.coarsen(dg, rating=rating, seed=1, stop_size=stop, validate=True, profile=True)
+        L = h.num_levels()
+        top_n = h.level(L - 1)["n"]
+        cpart = torch.from_numpy(I.random_balanced_partition(top_n, k, seed)).to("cuda", non_blocking=False)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev2 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        h.project(cpart, fine)
+        ev1.record(stream)
+        res = B.cut_gain(dg, fine, k, eps, block_w=bw, gain=gain, target=target)
+        ev2.record(stream)
+        prof, launches = h.profile()
+        sizes = [(h.level(l)["n"], h.level(l)["nnz"]) for l in range(L)]
+        h.free()
+        return res, prof, launches + 3, sizes, (ev0, ev1, ev2)
+
+    # warm-up (also checks the input once more on the device)
+    for w in range(max(args.warmup, 3)):
+        step(w)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, phase_tot, launches_tot = [], {}, 0
+    proj_ms = eval_ms = 0.0
+    sizes = None
+    for s in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        res, prof, launches, sizes, evs = step(100 + s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        for kk, v in prof.items():
+            phase_tot[kk] = phase_tot.get(kk, 0.0) + v
+        proj_ms += evs[0].elapsed_time(evs[1])
+        eval_ms += evs[1].elapsed_time(evs[2])
+        launches_tot += launches
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+
+    # end to end through the host-buffer entry point
+    e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(3, min(args.steps, 20))
+    pin = {name: torch.from_numpy(np.ascontiguousarray(arr, dtype=np.int32)).pin_memory()
+           for name, arr in (("xadj", g.xadj), ("adjncy", g.adjncy), ("ewgt", g.ewgt), ("vwgt", g.vwgt))}
+    outs = {"part": torch.empty(g.n, dtype=torch.int32).pin_memory().numpy(),
+            "gain": torch.empty(g.n, dtype=torch.int64).pin_memory().numpy(),
+            "target": torch.empty(g.n, dtype=torch.int32).pin_memory().numpy(),
+            "block_w": torch.empty(k, dtype=torch.int64).pin_memory().numpy()}
+    coarse_n = []
+
+    def ip(nc, cw, kk):
+        coarse_n.append(nc)
+        return I.random_balanced_partition(nc, kk, 7)
+
+    arrs = [pin[x].numpy() for x in ("xadj", "adjncy", "ewgt", "vwgt")]
+    B.pipeline_host(*arrs, k, eps, ip, outputs=outs, rating=rating, seed=1, stop_size=stop)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e2e_ms = []
+    for s in range(e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = B.pipeline_host(*arrs, k, eps, ip, outputs=outs, rating=rating, seed=1, stop_size=stop)
+        e2e_ms.append(1000 * (time.perf_counter() - t0))
+    e2e_total = sum(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    h2d = 4 * (g.n + 1) + 8 * g.nnz + 4 * g.n + 4 * coarse_n[-1]
+    d2h = 4 * g.n + 8 * g.n + 4 * g.n + 8 * k + 4 * coarse_n[-1]
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    steps = args.steps
+    value = world * g.m * steps / (total_ms / 1000.0)
+    peak, peak_kind = load_peaks()
+    ab = algorithmic_bytes(sizes, rating)
+    phase_ms = {kk: v / steps for kk, v in phase_tot.items()}
+    cands = {kk: (ab.get(kk, 0), phase_ms.get(kk, 0.0)) for kk in ("match", "relabel", "contract", "csr")}
+    cands["cut_gain"] = (eval_bytes(g.n, g.nnz, k), eval_ms / steps)
+    dom = max(cands, key=lambda x: cands[x][1])
+    dom_bytes, dom_ms = cands[dom]
+    achieved = dom_bytes / (dom_ms / 1000.0) / 1e9 if dom_ms > 0 else 0.0
+    path_bytes = sum(ab.values()) + eval_bytes(g.n, g.nnz, k) + 8 * g.n
+    line = {
+        "metric": "coarsened edges/s (full hierarchy)",
+        "value": value, "unit": "edges/s", "n_gpus": world, "steps": steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "n": g.n, "m": g.m, "levels": len(sizes),
+                   "coarsest_n": sizes[-1][0], "level_n": [s[0] for s in sizes],
+                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_step": dom_bytes, "kernel_ms_per_step": dom_ms},
+        "path_roofline": {"bytes_per_step": path_bytes, "achieved_gbs": path_bytes / (total_ms / steps / 1000) / 1e9,
+                          "frac": path_bytes / (total_ms / steps / 1000) / 1e9 / peak},
+        "phase_ms_per_step": {**phase_ms, "project": proj_ms / steps, "cut_gain": eval_ms / steps},
+        "clocks": clocks,
+        "e2e": {"value": world * g.m * e2e_steps / (e2e_total / 1000.0), "unit": "edges/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                "api": "kp_pipeline_host (host pinned buffers, copies inside)"},
+        "gpu_launches": launches_tot,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        oracle_step(g, wl)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": g.m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                "sample": "one full step of the same workload (coarsen + project + cut/gain), "
+                                          "single-threaded C/numpy oracle"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -92,7 +92,9 @@ typedef struct {
  *                        contraction that matches nothing is not kept
  *   spin_limit           iteration bound of every device-side wait; a wait
  *                        that runs out sets KP_ERR_TIMEOUT (default 1<<22)
- *   validate             1: check the input graph on the device first */
+ *   validate             1: check the input graph on the device first
+ *   profile              1: time every phase with CUDA events on the stream
+ *                        (read with kp_hierarchy_profile) */
 typedef struct {
     int32_t rating;
     uint64_t seed;
@@ -101,10 +103,12 @@ typedef struct {
     int32_t min_shrink_permille;
     int64_t spin_limit;
     int32_t validate;
+    int32_t profile;
 } kp_options;
 
 /* Fills *o with the defaults: EXPANSION_STAR2, seed 1, stop_size 40,
- * max_levels 64, min_shrink_permille 50, spin_limit 1<<22, validate 1. */
+ * max_levels 64, min_shrink_permille 50, spin_limit 1<<22, validate 1,
+ * profile 0. */
 void kp_options_default(kp_options *o);
 
 /* A hierarchy of graphs G_0 (the input) .. G_L (the coarsest) with the maps
@@ -136,9 +140,26 @@ kp_status kp_hierarchy_num_levels(const kp_hierarchy *h, int32_t *num_levels);
  * The arrays stay valid until kp_hierarchy_free. */
 kp_status kp_hierarchy_level(const kp_hierarchy *h, int32_t l, kp_graph *view, const int32_t **map);
 
-/* Statistics of the last kp_coarsen on h (host outputs, any may be NULL):
- * handshake rounds summed over all levels, and the matched pairs of level l. */
+/* Statistics of the kp_coarsen that built h (host outputs, any may be NULL):
+ * handshake rounds summed over all levels, and matched pairs summed over all
+ * levels. */
 kp_status kp_hierarchy_stats(const kp_hierarchy *h, int32_t *total_rounds, int64_t *total_matched);
+
+/* Phases timed when kp_options.profile is set. */
+typedef enum {
+    KP_PHASE_VALIDATE = 0,   /* input check */
+    KP_PHASE_OUT = 1,        /* Out(v) of the input (innerOuter) */
+    KP_PHASE_MATCH = 2,      /* rating + handshake rounds, all levels */
+    KP_PHASE_RELABEL = 3,    /* coarse ids, map, c', row bounds */
+    KP_PHASE_CONTRACT = 4,   /* gather, sort, merge of coarse rows */
+    KP_PHASE_CSR = 5,        /* coarse xadj scan and row compaction */
+    KP_NUM_PHASES = 6
+} kp_phase;
+
+/* Device milliseconds per phase summed over all levels (host array of
+ * KP_NUM_PHASES; zeros unless built with profile = 1) and the number of
+ * kernels kp_coarsen launched (host, may be NULL). */
+kp_status kp_hierarchy_profile(const kp_hierarchy *h, double *phase_ms, int32_t *launches);
 
 /* Releases the hierarchy (synchronises the stream it was built on). */
 void kp_hierarchy_free(kp_hierarchy *h);

@@ -21,8 +21,10 @@ STATUS_NAMES = ["KP_OK", "KP_ERR_INVALID", "KP_ERR_OVERFLOW", "KP_ERR_OOM", "KP_
                 "KP_ERR_TIMEOUT", "KP_ERR_UNSUPPORTED"]
 RATINGS = {"expansion*2": 0, "innerOuter": 1, "weight": 2, "expansion": 3, "expansion*": 4}
 
+PHASES = ["validate", "out", "match", "relabel", "contract", "csr"]
+
 EXPORTED = ["kp_options_default", "kp_coarsen", "kp_hierarchy_num_levels", "kp_hierarchy_level",
-            "kp_hierarchy_stats", "kp_hierarchy_free", "kp_project", "kp_cut_gain", "kp_pipeline_host",
+            "kp_hierarchy_stats", "kp_hierarchy_profile", "kp_hierarchy_free", "kp_project", "kp_cut_gain", "kp_pipeline_host",
             "kp_last_error", "kp_version"]
 
 
@@ -41,7 +43,7 @@ class kp_graph(ctypes.Structure):
 class kp_options(ctypes.Structure):
     _fields_ = [("rating", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stop_size", ctypes.c_int32),
                 ("max_levels", ctypes.c_int32), ("min_shrink_permille", ctypes.c_int32),
-                ("spin_limit", ctypes.c_int64), ("validate", ctypes.c_int32)]
+                ("spin_limit", ctypes.c_int64), ("validate", ctypes.c_int32), ("profile", ctypes.c_int32)]
 
 
 class kp_cut_gain_out(ctypes.Structure):
@@ -78,6 +80,8 @@ def load(path: str = LIB_PATH):
         L.kp_hierarchy_level.restype = ctypes.c_int
         L.kp_hierarchy_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.kp_hierarchy_stats.restype = ctypes.c_int
+        L.kp_hierarchy_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+        L.kp_hierarchy_profile.restype = ctypes.c_int
         L.kp_hierarchy_free.argtypes = [vp]
         L.kp_hierarchy_free.restype = None
         L.kp_project.argtypes = [vp, vp, vp, vp]
@@ -137,6 +141,13 @@ def kp_hierarchy_stats(h: int):
     r, m = ctypes.c_int32(), ctypes.c_int64()
     _check(load().kp_hierarchy_stats(ctypes.c_void_p(h), ctypes.byref(r), ctypes.byref(m)), "kp_hierarchy_stats")
     return r.value, m.value
+
+
+def kp_hierarchy_profile(h: int):
+    ms = (ctypes.c_double * len(PHASES))()
+    launches = ctypes.c_int32()
+    _check(load().kp_hierarchy_profile(ctypes.c_void_p(h), ms, ctypes.byref(launches)), "kp_hierarchy_profile")
+    return dict(zip(PHASES, list(ms))), launches.value
 
 
 def kp_hierarchy_free(h: int):
@@ -223,7 +234,7 @@ class DeviceGraph:
 
 
 def make_options(rating="expansion*2", seed=1, stop_size=40, max_levels=64, min_shrink_permille=50,
-                 spin_limit=1 << 22, validate=True) -> kp_options:
+                 spin_limit=1 << 22, validate=True, profile=False) -> kp_options:
     o = kp_options_default()
     o.rating = RATINGS[rating] if isinstance(rating, str) else int(rating)
     o.seed = seed
@@ -232,6 +243,7 @@ def make_options(rating="expansion*2", seed=1, stop_size=40, max_levels=64, min_
     o.min_shrink_permille = min_shrink_permille
     o.spin_limit = spin_limit
     o.validate = 1 if validate else 0
+    o.profile = 1 if profile else 0
     return o
 
 
@@ -256,6 +268,9 @@ class Hierarchy:
 
     def stats(self):
         return kp_hierarchy_stats(self.handle)
+
+    def profile(self):
+        return kp_hierarchy_profile(self.handle)
 
     def project(self, coarse_part, fine_part=None):
         torch = _torch()

@@ -202,6 +202,7 @@ void kp_options_default(kp_options *o) {
     o->min_shrink_permille = 50;
     o->spin_limit = 1ll << 22;
     o->validate = 1;
+    o->profile = 0;
 }
 
 kp_status kp_coarsen(const kp_graph *g, const kp_options *o, kp_stream s, kp_hierarchy **out) {
@@ -238,6 +239,14 @@ kp_status kp_hierarchy_stats(const kp_hierarchy *h, int32_t *total_rounds, int64
     if (!h) return set_error(KP_ERR_INVALID, "null argument");
     if (total_rounds) *total_rounds = h->total_rounds;
     if (total_matched) *total_matched = h->total_matched;
+    return KP_OK;
+}
+
+kp_status kp_hierarchy_profile(const kp_hierarchy *h, double *phase_ms, int32_t *launches) {
+    if (!h) return set_error(KP_ERR_INVALID, "null argument");
+    if (phase_ms)
+        for (int i = 0; i < KP_NUM_PHASES; i++) phase_ms[i] = h->phase_ms[i];
+    if (launches) *launches = h->launches;
     return KP_OK;
 }
 

@@ -794,7 +794,14 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         g_coop_supported = v;
     }
     if (!g_coop_supported) return set_error(KP_ERR_UNSUPPORTED, "device lacks cooperative launch");
-    if (o->validate && g->n > 0) KP_TRY(validate_graph(g, s, o->spin_limit));
+    PhaseTimer timer(o->profile != 0, s);
+    int32_t launches = 0;
+    if (o->validate && g->n > 0) {
+        timer.mark(KP_PHASE_VALIDATE);
+        KP_TRY(validate_graph(g, s, o->spin_limit));
+        timer.mark(-1);
+        launches += 1;
+    }
 
     kp_hierarchy *h = new kp_hierarchy();
     h->stream = s;
@@ -849,8 +856,10 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     Counters *hc = pinned.h;
 
     if (rating == KP_RATING_INNER_OUTER) {
+        timer.mark(KP_PHASE_OUT);
         const int64_t threads = (int64_t)n0 * 8;
         k_out_weight<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n0, g->xadj, g->ewgt, sc.outw_a);
+        launches += 1;
     }
     int32_t *outw_cur = sc.outw_a, *outw_next = sc.outw_b;
     int32_t total_rounds = 0;
@@ -880,8 +889,10 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         mp.ctr = sc.ctr;
         mp.spin_limit = o->spin_limit;
         const int G = group_for_degree(n > 0 ? (double)cur.nnz / n : 0.0);
+        timer.mark(KP_PHASE_MATCH);
         st = launch_match(rating, mp, G, s);
         if (st != KP_OK) return fail(st);
+        launches += 1;
         // -- relabel (Section 2: pairs become one node)
         kp_level nxt;
         nxt.owned = true;
@@ -904,8 +915,11 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         rop.cvwgt = cvw;
         rop.off = sc.off;
         rop.ctr = sc.ctr;
+        timer.mark(KP_PHASE_RELABEL);
         if (device_scan(rop, n, sc.partials, s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "relabel scan"));
+        timer.mark(-1);
+        launches += 3;
         if (cudaMemcpyAsync(hc, sc.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "read counters"));
         if (cudaStreamSynchronize(s) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "sync"));
@@ -949,6 +963,8 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         cp.ctr = sc.ctr;
         const double avg_pair = n > 0 ? 2.0 * (double)cur.nnz / n : 0.0;
         const int Gs = avg_pair <= 7.0 ? 8 : (avg_pair <= 14.0 ? 16 : 32);
+        timer.mark(KP_PHASE_CONTRACT);
+        launches += (Gs < 32) ? 4 : 3;
         if (Gs == 8) launch_contract_small<8>(cp, s);
         else if (Gs == 16) launch_contract_small<16>(cp, s);
         else launch_contract_small<32>(cp, s);
@@ -963,6 +979,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
             const int passes = (bits + 7) / 8;
             k_contract_big<<<num_sms(), CONTRACT_BLOCK, 0, s>>>(cp, passes);
         }
+        timer.mark(KP_PHASE_CSR);
         DegScanOp dop;
         dop.cn = cn;
         dop.degp = sc.degp;
@@ -976,6 +993,8 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
             k_compact<<<grid, 256, 0, s>>>(cn, sc.off, sc.degp, nxt.xadj, sc.tmp_adj, sc.tmp_w, nxt.adjncy,
                                            nxt.ewgt);
         }
+        timer.mark(-1);
+        launches += 4;
         if (cudaGetLastError() != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "contraction"));
         // the coarse entry count reaches the host with the next synchronisation
         const int lvl = (int)h->levels.size();
@@ -988,9 +1007,12 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         std::swap(outw_cur, outw_next);
         if ((int64_t)cn * 1000 > (int64_t)n * (1000 - o->min_shrink_permille)) break;
     }
+    timer.mark(-1);
     h->total_rounds = total_rounds;
     h->total_matched = total_matched;
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "final sync"));
+    timer.accumulate(h->phase_ms);
+    h->launches = launches;
     for (size_t l = 1; l < h->levels.size(); l++) h->levels[l].nnz = pinned.nnz[l];
     *out = h;
     return KP_OK;

@@ -276,4 +276,46 @@ struct kp_hierarchy {
     int device = 0;
     int32_t total_rounds = 0;
     int64_t total_matched = 0;
+    int32_t launches = 0;
+    double phase_ms[KP_NUM_PHASES] = {0, 0, 0, 0, 0, 0};
 };
+
+namespace kp {
+
+// Records CUDA events at phase boundaries on one stream when enabled; the
+// elapsed times are summed per phase once the stream has been synchronised.
+class PhaseTimer {
+  public:
+    PhaseTimer(bool on, cudaStream_t s) : on_(on), s_(s) {}
+    ~PhaseTimer() {
+        for (auto &m : marks_) cudaEventDestroy(m.ev);
+    }
+    void mark(int phase_starting) {
+        if (!on_) return;
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        cudaEventRecord(e, s_);
+        marks_.push_back({e, phase_starting});
+    }
+    // After the stream is synchronised: add each interval to the phase that
+    // began at its start mark (a mark with phase -1 ends an interval only).
+    void accumulate(double *phase_ms) {
+        for (size_t i = 0; i + 1 < marks_.size(); i++) {
+            if (marks_[i].phase < 0) continue;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, marks_[i].ev, marks_[i + 1].ev) == cudaSuccess)
+                phase_ms[marks_[i].phase] += ms;
+        }
+    }
+
+  private:
+    struct Mark {
+        cudaEvent_t ev;
+        int phase;
+    };
+    bool on_;
+    cudaStream_t s_;
+    std::vector<Mark> marks_;
+};
+
+}  // namespace kp
