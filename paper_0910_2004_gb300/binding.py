@@ -200,7 +200,7 @@ class _DevArray:
     """Zero-copy view of a library-owned device array (CUDA array interface)."""
 
     def __init__(self, ptr: int, n: int, typestr: str = "<i4"):
-        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr or 0, True),
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr or 0, False),
                                          "version": 3, "strides": None}
 
 
