@@ -44,6 +44,10 @@ def workloads():
             desc="2D random geometric graph, n=2^20 uniform points, radius for mean degree 6, unit int32 "
                  "weights, expansion*2 rating, full hierarchy to <= 20*64 nodes, cut/gain k=64 eps=0.03",
             make=lambda: I.rgg2d(1 << 20, 1), rating="expansion*2", k=64, eps=0.03),
+        "rgg22": dict(
+            desc="2D random geometric graph, n=2^22 uniform points, radius for mean degree 6, unit int32 "
+                 "weights, expansion*2 rating, full hierarchy to <= 20*64 nodes, cut/gain k=64 eps=0.03",
+            make=lambda: I.rgg2d(1 << 22, 1), rating="expansion*2", k=64, eps=0.03),
         "grid64": dict(
             desc="2D 5-point grid 64x64, unit weights, expansion*2, coarsen to <= 20*2 nodes, cut/gain k=2 eps=0.03",
             make=lambda: I.grid2d(64, 64), rating="expansion*2", k=2, eps=0.03),
@@ -278,37 +282,42 @@ def main():
 
     # end to end through the host-buffer entry point
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(3, min(args.steps, 20))
-    pin = {name: torch.from_numpy(np.ascontiguousarray(arr, dtype=np.int32)).pin_memory()
-           for name, arr in (("xadj", g.xadj), ("adjncy", g.adjncy), ("ewgt", g.ewgt), ("vwgt", g.vwgt))}
-    outs = {"part": torch.empty(g.n, dtype=torch.int32).pin_memory().numpy(),
-            "gain": torch.empty(g.n, dtype=torch.int64).pin_memory().numpy(),
-            "target": torch.empty(g.n, dtype=torch.int32).pin_memory().numpy(),
-            "block_w": torch.empty(k, dtype=torch.int64).pin_memory().numpy()}
-    coarse_n = []
+    e2e_line = None
+    if e2e_steps > 0:
+        pin = {name: torch.from_numpy(np.ascontiguousarray(arr, dtype=np.int32)).pin_memory()
+               for name, arr in (("xadj", g.xadj), ("adjncy", g.adjncy), ("ewgt", g.ewgt), ("vwgt", g.vwgt))}
+        outs = {"part": torch.empty(g.n, dtype=torch.int32).pin_memory().numpy(),
+                "gain": torch.empty(g.n, dtype=torch.int64).pin_memory().numpy(),
+                "target": torch.empty(g.n, dtype=torch.int32).pin_memory().numpy(),
+                "block_w": torch.empty(k, dtype=torch.int64).pin_memory().numpy()}
+        coarse_n = []
 
-    def ip(nc, cw, kk):
-        coarse_n.append(nc)
-        return I.random_balanced_partition(nc, kk, 7)
+        def ip(nc, cw, kk):
+            coarse_n.append(nc)
+            return I.random_balanced_partition(nc, kk, 7)
 
-    arrs = [pin[x].numpy() for x in ("xadj", "adjncy", "ewgt", "vwgt")]
-    B.pipeline_host(*arrs, k, eps, ip, outputs=outs, rating=rating, seed=1, stop_size=stop)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    e2e_ms = []
-    for s in range(e2e_steps):
-        flush.zero_()
+        arrs = [pin[x].numpy() for x in ("xadj", "adjncy", "ewgt", "vwgt")]
+        B.pipeline_host(*arrs, k, eps, ip, outputs=outs, rating=rating, seed=1, stop_size=stop)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r = B.pipeline_host(*arrs, k, eps, ip, outputs=outs, rating=rating, seed=1, stop_size=stop)
-        e2e_ms.append(1000 * (time.perf_counter() - t0))
-    e2e_total = sum(e2e_ms)
-    if dist:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    h2d = 4 * (g.n + 1) + 8 * g.nnz + 4 * g.n + 4 * coarse_n[-1]
-    d2h = 4 * g.n + 8 * g.n + 4 * g.n + 8 * k + 4 * coarse_n[-1]
+        if dist:
+            dist.barrier()
+        e2e_ms = []
+        for s in range(e2e_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.pipeline_host(*arrs, k, eps, ip, outputs=outs, rating=rating, seed=1, stop_size=stop)
+            e2e_ms.append(1000 * (time.perf_counter() - t0))
+        e2e_total = sum(e2e_ms)
+        if dist:
+            t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_total = float(t.item())
+        h2d = 4 * (g.n + 1) + 8 * g.nnz + 4 * g.n + 4 * coarse_n[-1]
+        d2h = 4 * g.n + 8 * g.n + 4 * g.n + 8 * k + 4 * coarse_n[-1]
+        e2e_line = {"value": world * g.m * e2e_steps / (e2e_total / 1000.0), "unit": "edges/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                    "api": "kp_pipeline_host (host pinned buffers, copies inside)"}
 
     if rank != 0:
         if dist:
@@ -341,9 +350,7 @@ def main():
                           "frac": path_bytes / (total_ms / steps / 1000) / 1e9 / peak},
         "phase_ms_per_step": {**phase_ms, "project": proj_ms / steps, "cut_gain": eval_ms / steps},
         "clocks": clocks,
-        "e2e": {"value": world * g.m * e2e_steps / (e2e_total / 1000.0), "unit": "edges/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
-                "api": "kp_pipeline_host (host pinned buffers, copies inside)"},
+        "e2e": e2e_line,
         "gpu_launches": launches_tot,
     }
     if world == 1 and not args.no_cpu_baseline:
