@@ -199,6 +199,32 @@ typedef struct {
 kp_status kp_cut_gain(const kp_graph *g, const int32_t *part, int32_t k, double eps,
                       kp_cut_gain_out *out, kp_stream s);
 
+/* Largest k accepted by kp_cut_gain_noalloc. */
+#define KP_CUT_GAIN_NOALLOC_MAX_K 16384
+
+/* kp_cut_gain without any allocation.  The paper has no counterpart: this
+ * entry point serves callers that cannot allocate device memory (or pinned
+ * host memory) while they evaluate a partition -- serving loops that must
+ * not enter an allocator on their hot path, applications that embed the
+ * library under a fixed device-memory budget or behind their own allocator,
+ * and code paths where an allocation may block or fail.  It computes exactly
+ * what kp_cut_gain computes, with the same arguments, outputs, errors and
+ * synchronisation, and calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ * Its scratch (the accumulators and one int64 partial weight per block) is a
+ * fixed static device array of 64 + 8 * KP_CUT_GAIN_NOALLOC_MAX_K bytes
+ * (about 128 KB) that every GPU which loads the library holds until the
+ * process exits.  k above KP_CUT_GAIN_NOALLOC_MAX_K returns
+ * KP_ERR_UNSUPPORTED without touching the GPU.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the array and each call clears
+ * the part that must start at zero, so calls whose GPU work overlaps (other
+ * streams or threads) race on it: serialise them.  The scalars are read back
+ * through pageable host memory. */
+kp_status kp_cut_gain_noalloc(const kp_graph *g, const int32_t *part, int32_t k, double eps,
+                              kp_cut_gain_out *out, kp_stream s);
+
 /* Initial partitioning callback for kp_pipeline_host (Section 4 partitions
  * the coarsest graph on one PE).  Receives the coarsest graph's size and its
  * node weights (host) and writes a block id in [0,k) for every coarsest node

@@ -16,6 +16,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libkp.so")
 
+KP_CUT_GAIN_NOALLOC_MAX_K = 16384
+
 KP_OK, KP_ERR_INVALID, KP_ERR_OVERFLOW, KP_ERR_OOM, KP_ERR_CUDA, KP_ERR_TIMEOUT, KP_ERR_UNSUPPORTED = range(7)
 STATUS_NAMES = ["KP_OK", "KP_ERR_INVALID", "KP_ERR_OVERFLOW", "KP_ERR_OOM", "KP_ERR_CUDA",
                 "KP_ERR_TIMEOUT", "KP_ERR_UNSUPPORTED"]
@@ -24,7 +26,7 @@ RATINGS = {"expansion*2": 0, "innerOuter": 1, "weight": 2, "expansion": 3, "expa
 PHASES = ["validate", "out", "match", "relabel", "contract", "csr"]
 
 EXPORTED = ["kp_options_default", "kp_coarsen", "kp_hierarchy_num_levels", "kp_hierarchy_level",
-            "kp_hierarchy_stats", "kp_hierarchy_profile", "kp_hierarchy_free", "kp_project", "kp_cut_gain", "kp_pipeline_host",
+            "kp_hierarchy_stats", "kp_hierarchy_profile", "kp_hierarchy_free", "kp_project", "kp_cut_gain", "kp_cut_gain_noalloc", "kp_pipeline_host",
             "kp_last_error", "kp_version"]
 
 
@@ -89,6 +91,9 @@ def load(path: str = LIB_PATH):
         L.kp_cut_gain.argtypes = [ctypes.POINTER(kp_graph), vp, i32, ctypes.c_double,
                                   ctypes.POINTER(kp_cut_gain_out), vp]
         L.kp_cut_gain.restype = ctypes.c_int
+        L.kp_cut_gain_noalloc.argtypes = [ctypes.POINTER(kp_graph), vp, i32, ctypes.c_double,
+                                          ctypes.POINTER(kp_cut_gain_out), vp]
+        L.kp_cut_gain_noalloc.restype = ctypes.c_int
         L.kp_pipeline_host.argtypes = [ctypes.POINTER(kp_graph), ctypes.POINTER(kp_options), i32, ctypes.c_double,
                                        kp_initial_partition_fn, vp, vp, vp, vp, vp,
                                        ctypes.POINTER(kp_cut_gain_out), ctypes.POINTER(i32), vp]
@@ -163,6 +168,13 @@ def kp_project(h: int, coarse_part: int, fine_part: int, stream: int):
 def kp_cut_gain(graph: kp_graph, part: int, k: int, eps: float, out: kp_cut_gain_out, stream: int):
     _check(load().kp_cut_gain(ctypes.byref(graph), ctypes.c_void_p(part), k, eps, ctypes.byref(out),
                               ctypes.c_void_p(stream)), "kp_cut_gain")
+
+
+def kp_cut_gain_noalloc(graph: kp_graph, part: int, k: int, eps: float, out: kp_cut_gain_out, stream: int):
+    """kp_cut_gain for callers that cannot allocate: scratch in a static device
+    array (k <= KP_CUT_GAIN_NOALLOC_MAX_K); overlapping calls race."""
+    _check(load().kp_cut_gain_noalloc(ctypes.byref(graph), ctypes.c_void_p(part), k, eps, ctypes.byref(out),
+                                      ctypes.c_void_p(stream)), "kp_cut_gain_noalloc")
 
 
 def kp_pipeline_host(graph: kp_graph, options: kp_options, k: int, eps: float, ip, user, fine_part: int,

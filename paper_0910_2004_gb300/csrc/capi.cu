@@ -170,6 +170,8 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
 kp_status project_impl(const kp_hierarchy *h, const int32_t *coarse_part, int32_t *fine_part, cudaStream_t s);
 kp_status cut_gain_impl(const kp_graph *g, const int32_t *part, int32_t k, double eps, kp_cut_gain_out *out,
                         cudaStream_t s);
+kp_status cut_gain_noalloc_impl(const kp_graph *g, const int32_t *part, int32_t k, double eps,
+                                kp_cut_gain_out *out, cudaStream_t s);
 kp_status pipeline_host_impl(const kp_graph *hg, const kp_options *o, int32_t k, double eps,
                              kp_initial_partition_fn ip, void *user, int32_t *fine_part, int64_t *gain,
                              int32_t *target, int64_t *block_w, kp_cut_gain_out *out, int32_t *num_levels,
@@ -264,6 +266,11 @@ kp_status kp_project(const kp_hierarchy *h, const int32_t *coarse_part, int32_t 
 kp_status kp_cut_gain(const kp_graph *g, const int32_t *part, int32_t k, double eps, kp_cut_gain_out *out,
                       kp_stream s) {
     KP_GUARD(cut_gain_impl(g, part, k, eps, out, (cudaStream_t)s));
+}
+
+kp_status kp_cut_gain_noalloc(const kp_graph *g, const int32_t *part, int32_t k, double eps,
+                              kp_cut_gain_out *out, kp_stream s) {
+    KP_GUARD(cut_gain_noalloc_impl(g, part, k, eps, out, (cudaStream_t)s));
 }
 
 kp_status kp_pipeline_host(const kp_graph *g, const kp_options *o, int32_t k, double eps,

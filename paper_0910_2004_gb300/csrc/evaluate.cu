@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "kp_internal.cuh"
 
@@ -275,6 +276,103 @@ kp_status cut_gain_with(const kp_graph *g, const int32_t *part, int32_t k, doubl
     out->max_c = (int64_t)host_acc->max_c;
     out->l_max = l_max_of(out->total_c, out->max_c, k, eps);
     out->imbalance = std::max<int64_t>(0, (int64_t)host_acc->max_bw - out->l_max);
+    return KP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// evaluation without any allocation
+// ---------------------------------------------------------------------------
+// Scratch of kp_cut_gain_noalloc: words [0, 8) hold the accumulators
+// (EvalAcc), words [8, 8 + KP_CUT_GAIN_NOALLOC_MAX_K) one partial weight per
+// block.  Every device that loads the library holds it until the process
+// exits; all calls share it.
+constexpr int NOALLOC_HEADER_WORDS = 8;
+static_assert(sizeof(EvalAcc) <= NOALLOC_HEADER_WORDS * sizeof(unsigned long long), "accumulator header");
+static __device__ __align__(256) unsigned long long
+    g_noalloc_scratch[NOALLOC_HEADER_WORDS + KP_CUT_GAIN_NOALLOC_MAX_K];
+
+// Copies the block weights to the caller's buffer and reduces their maximum.
+__global__ void k_noalloc_finish(int32_t k, const unsigned long long *bw, long long *block_w_out, EvalAcc *acc) {
+    long long m = 0;
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        const long long v = (long long)bw[i];
+        block_w_out[i] = v;
+        m = max(m, v);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&acc->max_bw, m);
+}
+
+namespace {
+std::mutex g_noalloc_mu;
+unsigned long long *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the static scratch on the current device, looked up once
+// per device with that device current.
+kp_status noalloc_scratch(unsigned long long **out) {
+    int dev = 0;
+    KP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(KP_ERR_UNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(static scratch)");
+        g_noalloc_ptr[dev] = static_cast<unsigned long long *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return KP_OK;
+}
+}  // namespace
+
+kp_status cut_gain_noalloc_impl(const kp_graph *g, const int32_t *part, int32_t k, double eps,
+                                kp_cut_gain_out *out, cudaStream_t s) {
+    KP_TRY(check_eval_args(g, part, k, eps, out));
+    if (k > KP_CUT_GAIN_NOALLOC_MAX_K)
+        return set_error(KP_ERR_UNSUPPORTED, "kp_cut_gain_noalloc: k exceeds KP_CUT_GAIN_NOALLOC_MAX_K (16384)");
+    unsigned long long *scratch = nullptr;
+    KP_TRY(noalloc_scratch(&scratch));
+    EvalAcc *acc = reinterpret_cast<EvalAcc *>(scratch);
+    unsigned long long *bw = scratch + NOALLOC_HEADER_WORDS;
+    // the accumulators and the k partial block weights start at zero
+    KP_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * (size_t)(NOALLOC_HEADER_WORDS + k), s));
+    if (g->n > 0) {
+        CutGainParams p;
+        p.n = g->n;
+        p.k = k;
+        p.xadj = g->xadj;
+        p.adjncy = g->adjncy;
+        p.ewgt = g->ewgt;
+        p.vwgt = g->vwgt;
+        p.part = part;
+        p.block_w = bw;
+        p.gain = out->gain;
+        p.target = out->target;
+        p.acc = acc;
+        const double avg = (double)g->nnz / (double)g->n;
+        const int grid_cap = num_sms() * 8;
+        auto grid_for = [&](int G) {
+            const int64_t want = ((int64_t)g->n * G + EVAL_BLOCK - 1) / EVAL_BLOCK;
+            return (int)std::max<int64_t>(1, std::min<int64_t>(want, grid_cap));
+        };
+        if (avg <= 5.0) k_cut_gain<4><<<grid_for(4), EVAL_BLOCK, 0, s>>>(p);
+        else if (avg <= 10.0) k_cut_gain<8><<<grid_for(8), EVAL_BLOCK, 0, s>>>(p);
+        else if (avg <= 20.0) k_cut_gain<16><<<grid_for(16), EVAL_BLOCK, 0, s>>>(p);
+        else k_cut_gain<32><<<grid_for(32), EVAL_BLOCK, 0, s>>>(p);
+        KP_CUDA(cudaGetLastError());
+    }
+    k_noalloc_finish<<<1, 1024, 0, s>>>(k, bw, reinterpret_cast<long long *>(out->block_w), acc);
+    KP_CUDA(cudaGetLastError());
+    EvalAcc host_acc;   // pageable: no pinned allocation
+    KP_CUDA(cudaMemcpyAsync(&host_acc, acc, sizeof(EvalAcc), cudaMemcpyDeviceToHost, s));
+    KP_CUDA(cudaStreamSynchronize(s));
+    if (host_acc.err & ERR_BAD_PART) return set_error(KP_ERR_INVALID, "block id outside [0,k)");
+    out->cut = (int64_t)(host_acc.ext_sum / 2);
+    out->total_c = (int64_t)host_acc.total_c;
+    out->max_c = (int64_t)host_acc.max_c;
+    out->l_max = l_max_of(out->total_c, out->max_c, k, eps);
+    out->imbalance = std::max<int64_t>(0, (int64_t)host_acc.max_bw - out->l_max);
     return KP_OK;
 }
 
