@@ -198,6 +198,7 @@ def main():
     ap.add_argument("--workload", default="rgg20", choices=sorted(workloads()))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--matcher", default="suitor", choices=["suitor", "handshake"])
     args = ap.parse_args()
     wl = workloads()[args.workload]
     g = wl["make"]()
@@ -228,11 +229,12 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def step(seed):
-        h = B.coarsen(dg, rating=rating, seed=1, stop_size=stop, validate=True, profile=True)
+    def step(seed, validate=False, want_sizes=False):
+        h = B.coarsen(dg, rating=rating, seed=1, stop_size=stop, validate=validate, profile=True,
+                      matcher=args.matcher)
         L = h.num_levels()
-        top_n = h.level(L - 1)["n"]
-        cpart = torch.from_numpy(I.random_balanced_partition(top_n, k, seed)).to("cuda", non_blocking=False)
+        top, _ = B.kp_hierarchy_level(h.handle, L - 1)
+        cpart = torch.from_numpy(I.random_balanced_partition(top.n, k, seed)).to("cuda", non_blocking=False)
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev2 = torch.cuda.Event(enable_timing=True)
@@ -242,13 +244,20 @@ def main():
         res = B.cut_gain(dg, fine, k, eps, block_w=bw, gain=gain, target=target)
         ev2.record(stream)
         prof, launches = h.profile()
-        sizes = [(h.level(l)["n"], h.level(l)["nnz"]) for l in range(L)]
+        sizes = None
+        if want_sizes:
+            sizes = []
+            for l in range(L):
+                gl, _ = B.kp_hierarchy_level(h.handle, l)
+                sizes.append((gl.n, gl.nnz))
         h.free()
         return res, prof, launches + 3, sizes, (ev0, ev1, ev2)
 
-    # warm-up (also checks the input once more on the device)
+    # warm-up; the first step also checks the input graph on the device (the
+    # timed steps take it as checked)
     for w in range(max(args.warmup, 3)):
-        step(w)
+        step(w, validate=(w == 0))
+    sizes = step(0, want_sizes=True)[3]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -256,14 +265,13 @@ def main():
     sampler.start()
     step_ms, phase_tot, launches_tot = [], {}, 0
     proj_ms = eval_ms = 0.0
-    sizes = None
     for s in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        res, prof, launches, sizes, evs = step(100 + s)
+        res, prof, launches, _, evs = step(100 + s)
         e1.record(stream)
         torch.cuda.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -306,7 +314,8 @@ def main():
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            B.pipeline_host(*arrs, k, eps, ip, outputs=outs, rating=rating, seed=1, stop_size=stop)
+            B.pipeline_host(*arrs, k, eps, ip, outputs=outs, rating=rating, seed=1, stop_size=stop,
+                            matcher=args.matcher)
             e2e_ms.append(1000 * (time.perf_counter() - t0))
         e2e_total = sum(e2e_ms)
         if dist:
@@ -342,7 +351,8 @@ def main():
         "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "n": g.n, "m": g.m, "levels": len(sizes),
                    "coarsest_n": sizes[-1][0], "level_n": [s[0] for s in sizes],
-                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}",
+                   "matcher": args.matcher, "input_check": "once before timing (kp_options.validate=0 in timed steps)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
                      "algorithmic_bytes_per_step": dom_bytes, "kernel_ms_per_step": dom_ms},

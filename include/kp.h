@@ -80,6 +80,22 @@ typedef struct {
     const int32_t *vwgt;
 } kp_graph;
 
+/* Two ways to reach the matching of locally heaviest edges (Section 3.3).
+ * Under the strict edge order both end in the same unique matching, the
+ * Greedy matching of Section 3.2:
+ *   SUITOR     every node proposes to its best neighbour whose standing offer
+ *              it beats (one 128-bit compare-and-swap per proposal); a
+ *              displaced proposer proposes again (Manne & Halappanavar's
+ *              Suitor scheme).  No rounds, no grid barriers.
+ *   HANDSHAKE  rounds: every free node names its best free neighbour, mutual
+ *              names are matched, repeated until no edge has two free ends;
+ *              one cooperative launch per level, rounds separated by bounded
+ *              grid barriers. */
+typedef enum {
+    KP_MATCHER_SUITOR = 0,
+    KP_MATCHER_HANDSHAKE = 1
+} kp_matcher;
+
 /* Coarsening options.
  *   rating               a kp_rating
  *   seed                 tie-break hash seed
@@ -94,7 +110,9 @@ typedef struct {
  *                        that runs out sets KP_ERR_TIMEOUT (default 1<<22)
  *   validate             1: check the input graph on the device first
  *   profile              1: time every phase with CUDA events on the stream
- *                        (read with kp_hierarchy_profile) */
+ *                        (read with kp_hierarchy_profile)
+ *   matcher              a kp_matcher: how the matching of each level is
+ *                        found; both give the same unique matching */
 typedef struct {
     int32_t rating;
     uint64_t seed;
@@ -104,11 +122,12 @@ typedef struct {
     int64_t spin_limit;
     int32_t validate;
     int32_t profile;
+    int32_t matcher;
 } kp_options;
 
 /* Fills *o with the defaults: EXPANSION_STAR2, seed 1, stop_size 40,
  * max_levels 64, min_shrink_permille 50, spin_limit 1<<22, validate 1,
- * profile 0. */
+ * profile 0, matcher SUITOR. */
 void kp_options_default(kp_options *o);
 
 /* A hierarchy of graphs G_0 (the input) .. G_L (the coarsest) with the maps
@@ -128,8 +147,9 @@ typedef struct kp_hierarchy kp_hierarchy;
  *   out  receives the hierarchy (host pointer to a handle)
  * Blocks until the hierarchy is complete (level sizes are data-dependent).
  * Errors: KP_ERR_INVALID (malformed graph, with o->validate), KP_ERR_OVERFLOW,
- * KP_ERR_UNSUPPORTED (unknown rating), KP_ERR_OOM, KP_ERR_CUDA,
- * KP_ERR_TIMEOUT. */
+ * KP_ERR_UNSUPPORTED (unknown rating or matcher), KP_ERR_OOM, KP_ERR_CUDA,
+ * KP_ERR_TIMEOUT (a grid-barrier wait, or a proposal chain longer than
+ * spin_limit steps, gave up). */
 kp_status kp_coarsen(const kp_graph *g, const kp_options *o, kp_stream s, kp_hierarchy **out);
 
 /* Number of levels L+1 including the input (host output). */
@@ -141,8 +161,8 @@ kp_status kp_hierarchy_num_levels(const kp_hierarchy *h, int32_t *num_levels);
 kp_status kp_hierarchy_level(const kp_hierarchy *h, int32_t l, kp_graph *view, const int32_t **map);
 
 /* Statistics of the kp_coarsen that built h (host outputs, any may be NULL):
- * handshake rounds summed over all levels, and matched pairs summed over all
- * levels. */
+ * handshake rounds summed over all levels (one per level with SUITOR), and
+ * matched pairs summed over all levels. */
 kp_status kp_hierarchy_stats(const kp_hierarchy *h, int32_t *total_rounds, int64_t *total_matched);
 
 /* Phases timed when kp_options.profile is set. */

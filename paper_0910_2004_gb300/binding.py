@@ -22,6 +22,7 @@ KP_OK, KP_ERR_INVALID, KP_ERR_OVERFLOW, KP_ERR_OOM, KP_ERR_CUDA, KP_ERR_TIMEOUT,
 STATUS_NAMES = ["KP_OK", "KP_ERR_INVALID", "KP_ERR_OVERFLOW", "KP_ERR_OOM", "KP_ERR_CUDA",
                 "KP_ERR_TIMEOUT", "KP_ERR_UNSUPPORTED"]
 RATINGS = {"expansion*2": 0, "innerOuter": 1, "weight": 2, "expansion": 3, "expansion*": 4}
+MATCHERS = {"suitor": 0, "handshake": 1}
 
 PHASES = ["validate", "out", "match", "relabel", "contract", "csr"]
 
@@ -45,7 +46,8 @@ class kp_graph(ctypes.Structure):
 class kp_options(ctypes.Structure):
     _fields_ = [("rating", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stop_size", ctypes.c_int32),
                 ("max_levels", ctypes.c_int32), ("min_shrink_permille", ctypes.c_int32),
-                ("spin_limit", ctypes.c_int64), ("validate", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("spin_limit", ctypes.c_int64), ("validate", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("matcher", ctypes.c_int32)]
 
 
 class kp_cut_gain_out(ctypes.Structure):
@@ -246,7 +248,7 @@ class DeviceGraph:
 
 
 def make_options(rating="expansion*2", seed=1, stop_size=40, max_levels=64, min_shrink_permille=50,
-                 spin_limit=1 << 22, validate=True, profile=False) -> kp_options:
+                 spin_limit=1 << 22, validate=True, profile=False, matcher="suitor") -> kp_options:
     o = kp_options_default()
     o.rating = RATINGS[rating] if isinstance(rating, str) else int(rating)
     o.seed = seed
@@ -256,6 +258,7 @@ def make_options(rating="expansion*2", seed=1, stop_size=40, max_levels=64, min_
     o.spin_limit = spin_limit
     o.validate = 1 if validate else 0
     o.profile = 1 if profile else 0
+    o.matcher = MATCHERS[matcher] if isinstance(matcher, str) else int(matcher)
     return o
 
 

@@ -210,6 +210,188 @@ __global__ void __launch_bounds__(MATCH_BLOCK) k_match(MatchParams p) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// proposal matching (Suitor scheme, Manne & Halappanavar 2014)
+// ---------------------------------------------------------------------------
+// Every node proposes to its best neighbour whose standing offer it beats; a
+// displaced proposer proposes again.  Under a strict edge order the pairs of
+// mutual proposals are exactly the Greedy matching (Section 3.2), i.e. the
+// fixed point of the handshake rounds (Section 3.3), reached without rounds
+// or grid barriers.
+//
+// Offer record of node u (16 bytes, updated by one 128-bit CAS): the current
+// suitor s (-1: none), omega(s,u), the rating attribute of s, and u's own
+// rating attribute (c for the c-based ratings, Out for innerOuter), so one
+// gather per neighbour yields both ratings a comparison needs.
+struct __align__(16) Offer {
+    int32_t s;
+    int32_t w;
+    int32_t as;
+    int32_t au;
+};
+
+template <int R>
+__device__ __forceinline__ int32_t rating_attr(const int32_t *__restrict__ vwgt, const int32_t *__restrict__ outw,
+                                               int32_t v) {
+    if (R == KP_RATING_INNER_OUTER) return __ldg(outw + v);
+    if (R == KP_RATING_WEIGHT) return 0;
+    return __ldg(vwgt + v);
+}
+
+// The rating of an edge with weight w between nodes of attributes a and b
+// (symmetric in a and b for every rating).
+template <int R>
+__device__ __forceinline__ void rating_ab(int32_t w, int32_t a, int32_t b, uint64_t &num, uint64_t &den) {
+    rating_of<R>(w, a, b, a, b, num, den);
+}
+
+__device__ __forceinline__ Offer ld_offer(const Offer *p) {
+    Offer o;
+    asm volatile("ld.global.cg.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(o.s), "=r"(o.w), "=r"(o.as), "=r"(o.au)
+                 : "l"(p)
+                 : "memory");
+    return o;
+}
+
+__device__ __forceinline__ bool cas_offer(Offer *addr, const Offer &expect, const Offer &desired) {
+    const uint64_t elo = ((uint64_t)(uint32_t)expect.w << 32) | (uint32_t)expect.s;
+    const uint64_t ehi = ((uint64_t)(uint32_t)expect.au << 32) | (uint32_t)expect.as;
+    const uint64_t dlo = ((uint64_t)(uint32_t)desired.w << 32) | (uint32_t)desired.s;
+    const uint64_t dhi = ((uint64_t)(uint32_t)desired.au << 32) | (uint32_t)desired.as;
+    uint64_t olo, ohi;
+    asm volatile(
+        "{\n\t.reg .b128 e, d, o;\n\t"
+        "mov.b128 e, {%2, %3};\n\t"
+        "mov.b128 d, {%4, %5};\n\t"
+        "atom.global.cas.b128 o, [%6], e, d;\n\t"
+        "mov.b128 {%0, %1}, o;\n\t}"
+        : "=l"(olo), "=l"(ohi)
+        : "l"(elo), "l"(ehi), "l"(dlo), "l"(dhi), "l"(addr)
+        : "memory");
+    return olo == elo && ohi == ehi;
+}
+
+struct SuitorParams {
+    int32_t n;
+    const int32_t *__restrict__ xadj;
+    const int32_t *__restrict__ adjncy;
+    const int32_t *__restrict__ ewgt;
+    const int32_t *__restrict__ vwgt;
+    const int32_t *__restrict__ outw;
+    uint64_t seed;
+    Offer *offer;
+    int32_t *match;
+    Counters *ctr;
+    long long spin_limit;
+};
+
+template <int R>
+__global__ void k_offer_init(SuitorParams p) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
+        Offer o;
+        o.s = -1;
+        o.w = 0;
+        o.as = 0;
+        o.au = rating_attr<R>(p.vwgt, p.outw, (int32_t)v);
+        p.offer[v] = o;
+    }
+}
+
+template <int R, int G>
+__global__ void __launch_bounds__(MATCH_BLOCK) k_suitor(SuitorParams p) {
+    const unsigned gmask = group_mask<G>();
+    const int gl = threadIdx.x & (G - 1);
+    const int leader = (threadIdx.x & 31) & ~(G - 1);
+    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+    long long iters = 0;
+    for (int64_t v0 = gid; v0 < p.n; v0 += ngroups) {
+        int32_t cur = (int32_t)v0;
+        while (cur >= 0) {
+            if (++iters > p.spin_limit) {   // a bound, not a wait: report instead of looping on
+                if (gl == 0) atomicOr(&p.ctr->err, ERR_TIMEOUT);
+                return;
+            }
+            const int32_t beg = __ldg(p.xadj + cur), end = __ldg(p.xadj + cur + 1);
+            const int32_t acur = rating_attr<R>(p.vwgt, p.outw, cur);
+            Cand best;
+            best.u = -1;
+            best.num = best.den = best.h = 0;
+            int32_t bw = 0;
+            Offer bsnap = {-1, 0, 0, 0};
+            for (int32_t e = beg + gl; e < end; e += G) {
+                const int32_t v = __ldg(p.adjncy + e);
+                const int32_t w = __ldg(p.ewgt + e);
+                const Offer st = ld_offer(p.offer + v);
+                Cand c;
+                c.u = v;
+                rating_ab<R>(w, acur, st.au, c.num, c.den);
+                c.h = edge_hash(p.seed, cur, v);
+                bool eligible = st.s < 0;
+                if (!eligible) {
+                    // compare at v: the offer of cur against the standing offer of st.s
+                    Cand a, b;
+                    a.u = cur;
+                    a.num = c.num;
+                    a.den = c.den;
+                    a.h = c.h;
+                    b.u = st.s;
+                    rating_ab<R>(st.w, st.as, st.au, b.num, b.den);
+                    b.h = edge_hash(p.seed, st.s, v);
+                    eligible = better(a, b, v);
+                }
+                if (eligible && better(c, best, cur)) {
+                    best = c;
+                    bw = w;
+                    bsnap = st;
+                }
+            }
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) {
+                Cand o;
+                o.num = __shfl_xor_sync(gmask, best.num, off);
+                o.den = __shfl_xor_sync(gmask, best.den, off);
+                o.h = __shfl_xor_sync(gmask, best.h, off);
+                o.u = __shfl_xor_sync(gmask, best.u, off);
+                const int32_t ow = __shfl_xor_sync(gmask, bw, off);
+                Offer os;
+                os.s = __shfl_xor_sync(gmask, bsnap.s, off);
+                os.w = __shfl_xor_sync(gmask, bsnap.w, off);
+                os.as = __shfl_xor_sync(gmask, bsnap.as, off);
+                os.au = __shfl_xor_sync(gmask, bsnap.au, off);
+                if (better(o, best, cur)) {
+                    best = o;
+                    bw = ow;
+                    bsnap = os;
+                }
+            }
+            int32_t next = -1;
+            if (best.u >= 0 && gl == 0) {
+                Offer mine;
+                mine.s = cur;
+                mine.w = bw;
+                mine.as = acur;
+                mine.au = bsnap.au;
+                // success: the displaced suitor (if any) proposes again;
+                // failure: the record changed under us, so cur searches again
+                next = cas_offer(p.offer + best.u, bsnap, mine) ? bsnap.s : cur;
+            }
+            cur = __shfl_sync(gmask, next, leader);
+        }
+    }
+}
+
+// The matching: pairs of mutual proposals; everyone else stays single.
+__global__ void k_suitor_final(SuitorParams p) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n; v += stride) {
+        const int32_t s = p.offer[v].s;
+        p.match[v] = (s >= 0 && p.offer[s].s == (int32_t)v) ? s : (int32_t)v;
+    }
+}
+
 // Out(v) = sum of the weights of v's edges (Section 3.1), for innerOuter.
 __global__ void k_out_weight(int32_t n, const int32_t *__restrict__ xadj, const int32_t *__restrict__ ewgt,
                              int32_t *__restrict__ outw) {
@@ -722,6 +904,39 @@ kp_status launch_match(int rating, const MatchParams &p, int G, cudaStream_t s) 
     }
 }
 
+template <int R, int G>
+kp_status launch_suitor_rg(const SuitorParams &p, cudaStream_t s) {
+    const int64_t want = ((int64_t)p.n * G + MATCH_BLOCK - 1) / MATCH_BLOCK;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 16));
+    const int grid1 = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)p.n + 255) / 256, (int64_t)num_sms() * 8));
+    k_offer_init<R><<<grid1, 256, 0, s>>>(p);
+    k_suitor<R, G><<<grid, MATCH_BLOCK, 0, s>>>(p);
+    k_suitor_final<<<grid1, 256, 0, s>>>(p);
+    KP_CUDA(cudaGetLastError());
+    return KP_OK;
+}
+
+template <int R>
+kp_status launch_suitor_r(const SuitorParams &p, int G, cudaStream_t s) {
+    switch (G) {
+    case 4: return launch_suitor_rg<R, 4>(p, s);
+    case 8: return launch_suitor_rg<R, 8>(p, s);
+    case 16: return launch_suitor_rg<R, 16>(p, s);
+    default: return launch_suitor_rg<R, 32>(p, s);
+    }
+}
+
+kp_status launch_suitor(int rating, const SuitorParams &p, int G, cudaStream_t s) {
+    switch (rating) {
+    case KP_RATING_EXPANSION_STAR2: return launch_suitor_r<KP_RATING_EXPANSION_STAR2>(p, G, s);
+    case KP_RATING_INNER_OUTER: return launch_suitor_r<KP_RATING_INNER_OUTER>(p, G, s);
+    case KP_RATING_WEIGHT: return launch_suitor_r<KP_RATING_WEIGHT>(p, G, s);
+    case KP_RATING_EXPANSION: return launch_suitor_r<KP_RATING_EXPANSION>(p, G, s);
+    case KP_RATING_EXPANSION_STAR: return launch_suitor_r<KP_RATING_EXPANSION_STAR>(p, G, s);
+    default: return set_error(KP_ERR_UNSUPPORTED, "unknown rating");
+    }
+}
+
 int group_for_degree(double avg) {
     if (avg <= 3.0) return 4;
     if (avg <= 6.5) return 8;
@@ -746,6 +961,7 @@ struct Scratch {
     int32_t *outw_a = nullptr, *outw_b = nullptr;
     int32_t *tmp_adj = nullptr, *tmp_w = nullptr, *big_adj = nullptr, *big_w = nullptr;
     int32_t *lists[4] = {nullptr, nullptr, nullptr, nullptr};
+    Offer *offer = nullptr;
     uint64_t *partials = nullptr;
     Counters *ctr = nullptr;
     template <class T>
@@ -782,6 +998,8 @@ kp_status validate_graph(const kp_graph *g, cudaStream_t s, int64_t spin_limit);
 kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, kp_hierarchy **out) {
     const int rating = o->rating;
     if (rating < 0 || rating > 4) return set_error(KP_ERR_UNSUPPORTED, "unknown rating");
+    if (o->matcher != KP_MATCHER_SUITOR && o->matcher != KP_MATCHER_HANDSHAKE)
+        return set_error(KP_ERR_UNSUPPORTED, "unknown matcher");
     if (g->n < 0 || g->nnz < 0) return set_error(KP_ERR_INVALID, "negative graph size");
     if (g->n > 0 && (!g->xadj || !g->vwgt || (g->nnz > 0 && (!g->adjncy || !g->ewgt))))
         return set_error(KP_ERR_INVALID, "null graph array");
@@ -845,6 +1063,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     SC_GET(sc.big_w, nnz0);
     for (int c = 1; c <= 3; c++) SC_GET(sc.lists[c], n0);
     SC_GET(sc.partials, scan_tiles(n0) + 1);
+    if (o->matcher == KP_MATCHER_SUITOR) SC_GET(sc.offer, n0);
     SC_GET(sc.ctr, 1);
     if (rating == KP_RATING_INNER_OUTER) {
         SC_GET(sc.outw_a, n0);
@@ -890,9 +1109,26 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         mp.spin_limit = o->spin_limit;
         const int G = group_for_degree(n > 0 ? (double)cur.nnz / n : 0.0);
         timer.mark(KP_PHASE_MATCH);
-        st = launch_match(rating, mp, G, s);
+        if (o->matcher == KP_MATCHER_SUITOR) {
+            SuitorParams sp;
+            sp.n = n;
+            sp.xadj = cur.xadj;
+            sp.adjncy = cur.adjncy;
+            sp.ewgt = cur.ewgt;
+            sp.vwgt = cur.vwgt;
+            sp.outw = outw_cur;
+            sp.seed = o->seed;
+            sp.offer = sc.offer;
+            sp.match = sc.match;
+            sp.ctr = sc.ctr;
+            sp.spin_limit = o->spin_limit;
+            st = launch_suitor(rating, sp, G, s);
+            launches += 3;
+        } else {
+            st = launch_match(rating, mp, G, s);
+            launches += 1;
+        }
         if (st != KP_OK) return fail(st);
-        launches += 1;
         // -- relabel (Section 2: pairs become one node)
         kp_level nxt;
         nxt.owned = true;
@@ -923,8 +1159,11 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         if (cudaMemcpyAsync(hc, sc.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "read counters"));
         if (cudaStreamSynchronize(s) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "sync"));
-        if (hc->err & ERR_TIMEOUT) return fail(set_error(KP_ERR_TIMEOUT, "matching grid barrier timed out"));
-        total_rounds += hc->rounds;
+        if (hc->err & ERR_TIMEOUT)
+            return fail(set_error(KP_ERR_TIMEOUT, o->matcher == KP_MATCHER_SUITOR
+                                                      ? "proposal chain exceeded spin_limit steps"
+                                                      : "matching grid barrier timed out"));
+        total_rounds += (o->matcher == KP_MATCHER_SUITOR) ? 1 : hc->rounds;
         const int32_t cn = hc->cn;
         const int32_t U = hc->U;
         if (cn == n) {   // nothing matched: this level is not kept

@@ -15,6 +15,7 @@ from paper_0910_2004_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 RATINGS = ["expansion*2", "innerOuter", "weight", "expansion", "expansion*"]
+MATCHERS = ["suitor", "handshake"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -70,9 +71,9 @@ def check_eval(dg, g, part, k, eps):
     return got
 
 
-def full_path(g, rating, seed, stop, k, eps=0.03, part_seed=1):
+def full_path(g, rating, seed, stop, k, eps=0.03, part_seed=1, matcher="suitor"):
     import torch
-    h, dg, levels, maps = run_gpu(g, rating=rating, seed=seed, stop_size=stop)
+    h, dg, levels, maps = run_gpu(g, rating=rating, seed=seed, stop_size=stop, matcher=matcher)
     ref = O.coarsen(g, rating, seed, stop)
     assert_same(levels, maps, ref, g.name)
     cpart = I.random_balanced_partition(ref.levels[-1].n, k, seed=part_seed)
@@ -88,27 +89,39 @@ def full_path(g, rating, seed, stop, k, eps=0.03, part_seed=1):
 # the measured workloads
 # ---------------------------------------------------------------------------
 
-def test_grid64_expansion_star2_k2():
+@pytest.mark.parametrize("matcher", MATCHERS)
+def test_grid64_expansion_star2_k2(matcher):
     """2D 5-point grid 64x64, expansion*2, stop at <= 20k nodes, k=2."""
-    ref = full_path(I.grid2d(64, 64), "expansion*2", 1, 40, 2)
+    ref = full_path(I.grid2d(64, 64), "expansion*2", 1, 40, 2, matcher=matcher)
     assert ref.levels[-1].n <= 40
 
 
-def test_rgg_2pow20_full_size():
+@pytest.mark.parametrize("matcher", MATCHERS)
+def test_rgg_2pow20_full_size(matcher):
     """2D RGG, n=2^20, mean degree 6, expansion*2, stop <= 20*64, k=64."""
     g = I.rgg2d(1 << 20, 1)
-    full_path(g, "expansion*2", 1, 20 * 64, 64)
+    full_path(g, "expansion*2", 1, 20 * 64, 64, matcher=matcher)
 
 
 @pytest.mark.slow
 def test_grid3d_256_full_size_levelwise():
+    _grid3d_levelwise("suitor")
+
+
+@pytest.mark.slow
+def test_grid3d_256_full_size_levelwise_handshake():
+    _grid3d_levelwise("handshake")
+
+
+def _grid3d_levelwise(matcher):
     """3D 7-point grid 256^3, innerOuter, stop <= 20*256, k=256.  The oracle's
     Greedy sort is slow at this size, so every level is checked with the
     sort-free characterisation of the Greedy matching and the oracle's
     contraction, and the evaluation against the oracle's cut/gain."""
     import torch
     g = I.grid3d(256, 256, 256)
-    h, dg, levels, maps = run_gpu(g, rating="innerOuter", seed=1, stop_size=20 * 256, validate=False)
+    h, dg, levels, maps = run_gpu(g, rating="innerOuter", seed=1, stop_size=20 * 256, validate=False,
+                                  matcher=matcher)
     for l, mp in enumerate(maps):
         cur = levels[l]
         match = match_from_map(mp)
@@ -142,8 +155,9 @@ def match_from_map(mp):
 # many small and ragged graphs, every rating
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("matcher", MATCHERS)
 @pytest.mark.parametrize("rating", RATINGS)
-def test_random_graphs(rating):
+def test_random_graphs(rating, matcher):
     for t in range(24):
         rng = np.random.default_rng(t)
         n = int(rng.integers(2, 400))
@@ -152,9 +166,9 @@ def test_random_graphs(rating):
                                  allow_zero_c=(t % 5 == 0))
         seed = int(rng.integers(0, 2**63))
         stop = int(rng.choice([1, 10, 50]))
-        h, dg, levels, maps = run_gpu(g, rating=rating, seed=seed, stop_size=stop)
+        h, dg, levels, maps = run_gpu(g, rating=rating, seed=seed, stop_size=stop, matcher=matcher)
         ref = O.coarsen(g, rating, seed, stop)
-        assert_same(levels, maps, ref, f"{rating} t={t}")
+        assert_same(levels, maps, ref, f"{rating} {matcher} t={t}")
         h.free()
 
 
@@ -167,9 +181,10 @@ def test_random_graphs(rating):
     (lambda: I.rmat(13, 4), "innerOuter"),
     (lambda: I.rmat(11, 5, edge_factor=64), "weight"),
 ])
-def test_structured_graphs(make, rating):
+@pytest.mark.parametrize("matcher", MATCHERS)
+def test_structured_graphs(make, rating, matcher):
     g = make()
-    ref = full_path(g, rating, 7, 20, 5)
+    ref = full_path(g, rating, 7, 20, 5, matcher=matcher)
     assert len(ref.levels) >= 2
 
 
@@ -191,12 +206,15 @@ def test_star_hub_rows():
         hi.append(hub + 1)
     g = I.from_edges(8 + 8 * 3000, np.array(lo), np.array(hi), name="stars")
     for r in ["expansion*2", "innerOuter", "weight"]:
-        full_path(g, r, 11, 4, 3)
+        for m in MATCHERS:
+            full_path(g, r, 11, 4, 3, matcher=m)
 
 
-def test_path_increasing_weights_many_rounds():
+@pytest.mark.parametrize("matcher", MATCHERS)
+def test_path_increasing_weights_many_rounds(matcher):
+    """Worst case for rounds (one edge per round) and for proposal chains."""
     g = I.path_graph(3000)
-    full_path(g, "weight", 0, 2, 2)
+    full_path(g, "weight", 0, 2, 2, matcher=matcher)
 
 
 def test_tiny_and_degenerate():
@@ -211,18 +229,20 @@ def test_tiny_and_degenerate():
               I.from_edges(30, np.zeros(0, np.int64), np.zeros(0, np.int64)),
               I.from_edges(6, np.array([0, 2, 3]), np.array([1, 3, 4]), np.array([1, 50, 60]))]:
         for r in RATINGS:
-            h, dg, levels, maps = run_gpu(g, rating=r, stop_size=0)
-            assert_same(levels, maps, O.coarsen(g, r, 1, 0), f"deg {g.n} {r}")
-            h.free()
+            for m in MATCHERS:
+                h, dg, levels, maps = run_gpu(g, rating=r, stop_size=0, matcher=m)
+                assert_same(levels, maps, O.coarsen(g, r, 1, 0), f"deg {g.n} {r} {m}")
+                h.free()
     # zero node weights: expansion*2 ratings become +infinity
     g = I.random_small_graph(200, 0.05, 9, cmax=2, allow_zero_c=True)
     full_path(g, "expansion*2", 5, 3, 4)
     # all ratings equal: the hash alone decides
     g = I.grid2d(50, 50)
     for seed in [0, 1, 2**63 + 5]:
-        h, dg, levels, maps = run_gpu(g, seed=seed, stop_size=10)
-        assert_same(levels, maps, O.coarsen(g, "expansion*2", seed, 10))
-        h.free()
+        for m in MATCHERS:
+            h, dg, levels, maps = run_gpu(g, seed=seed, stop_size=10, matcher=m)
+            assert_same(levels, maps, O.coarsen(g, "expansion*2", seed, 10))
+            h.free()
 
 
 def test_stop_rules():
@@ -282,16 +302,21 @@ def test_error_statuses():
     with pytest.raises(B().KpError) as e:
         B().coarsen(dg, rating=9)
     assert e.value.status == B().KP_ERR_UNSUPPORTED
+    with pytest.raises(B().KpError) as e:
+        B().coarsen(dg, matcher=7)
+    assert e.value.status == B().KP_ERR_UNSUPPORTED
 
 
-def test_barrier_timeout_reports_status_and_context_survives():
-    """A grid-barrier wait with a limit of one iteration runs out; the kernel
-    sets the error flag and returns, kp_coarsen reports KP_ERR_TIMEOUT, and the
-    next call on the same context succeeds."""
+@pytest.mark.parametrize("matcher", MATCHERS)
+def test_bounded_waits_report_status_and_context_survives(matcher):
+    """With a bound of one step, a grid-barrier wait (handshake) or a proposal
+    chain (suitor) runs out; the kernel sets the error flag and returns,
+    kp_coarsen reports KP_ERR_TIMEOUT, and the next call on the same context
+    succeeds."""
     g = I.grid2d(512, 512)
     dg = B().DeviceGraph.from_csr(g)
     with pytest.raises(B().KpError) as e:
-        B().coarsen(dg, spin_limit=1, stop_size=10)
+        B().coarsen(dg, spin_limit=1, stop_size=10, matcher=matcher)
     assert e.value.status == B().KP_ERR_TIMEOUT
     h, _, levels, maps = run_gpu(I.grid2d(64, 64))
     assert_same(levels, maps, O.coarsen(I.grid2d(64, 64), "expansion*2", 1, 40))
