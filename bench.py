@@ -243,13 +243,21 @@ def main():
         ev1.record(stream)
         res = B.cut_gain(dg, fine, k, eps, block_w=bw, gain=gain, target=target)
         ev2.record(stream)
-        prof, launches = h.profile()
+        tot = h.profile()
+        prof, launches = tot["phase_ms"], tot["launches"]
         sizes = None
         if want_sizes:
             sizes = []
             for l in range(L):
                 gl, _ = B.kp_hierarchy_level(h.handle, l)
                 sizes.append((gl.n, gl.nnz))
+            per_level = []
+            for l in range(L - 1):
+                lp = h.profile(l)
+                per_level.append({"n": lp["n"], "nnz": lp["nnz"], "searches": lp["searches"],
+                                  "failed_cas": lp["failed_cas"], "rounds": lp["rounds"],
+                                  **{kk + "_ms": round(v, 4) for kk, v in lp["phase_ms"].items() if v}})
+            sizes = (sizes, per_level)
         h.free()
         return res, prof, launches + 3, sizes, (ev0, ev1, ev2)
 
@@ -257,7 +265,7 @@ def main():
     # timed steps take it as checked)
     for w in range(max(args.warmup, 3)):
         step(w, validate=(w == 0))
-    sizes = step(0, want_sizes=True)[3]
+    sizes, level_profile = step(0, want_sizes=True)[3]
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -359,6 +367,7 @@ def main():
         "path_roofline": {"bytes_per_step": path_bytes, "achieved_gbs": path_bytes / (total_ms / steps / 1000) / 1e9,
                           "frac": path_bytes / (total_ms / steps / 1000) / 1e9 / peak},
         "phase_ms_per_step": {**phase_ms, "project": proj_ms / steps, "cut_gain": eval_ms / steps},
+        "level_profile": level_profile,
         "clocks": clocks,
         "e2e": e2e_line,
         "gpu_launches": launches_tot,

@@ -176,10 +176,27 @@ typedef enum {
     KP_NUM_PHASES = 6
 } kp_phase;
 
-/* Device milliseconds per phase summed over all levels (host array of
- * KP_NUM_PHASES; zeros unless built with profile = 1) and the number of
- * kernels kp_coarsen launched (host, may be NULL). */
-kp_status kp_hierarchy_profile(const kp_hierarchy *h, double *phase_ms, int32_t *launches);
+/* Per-level record of a kp_coarsen run.  Times are device milliseconds
+ * measured with CUDA events (zeros unless built with profile = 1); the
+ * counters are always kept.
+ *   n, nnz         size of the level that was contracted
+ *   launches       kernels launched for this level
+ *   rounds         handshake rounds (1 with SUITOR)
+ *   searches       neighbourhood scans (rating passes over a row)
+ *   failed_cas     proposals whose compare-and-swap lost a race (SUITOR) */
+typedef struct {
+    double phase_ms[KP_NUM_PHASES];
+    int64_t n;
+    int64_t nnz;
+    int64_t searches;
+    int64_t failed_cas;
+    int32_t launches;
+    int32_t rounds;
+} kp_level_profile;
+
+/* Profile of level l (0 .. num_levels-2: the contraction of level l), or
+ * with l = -1 the sums over all levels plus the input check.  Host output. */
+kp_status kp_hierarchy_profile(const kp_hierarchy *h, int32_t l, kp_level_profile *out);
 
 /* Releases the hierarchy (synchronises the stream it was built on). */
 void kp_hierarchy_free(kp_hierarchy *h);

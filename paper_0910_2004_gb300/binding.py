@@ -56,6 +56,12 @@ class kp_cut_gain_out(ctypes.Structure):
                 ("gain", ctypes.c_void_p), ("target", ctypes.c_void_p)]
 
 
+class kp_level_profile(ctypes.Structure):
+    _fields_ = [("phase_ms", ctypes.c_double * 6), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("searches", ctypes.c_int64), ("failed_cas", ctypes.c_int64), ("launches", ctypes.c_int32),
+                ("rounds", ctypes.c_int32)]
+
+
 kp_initial_partition_fn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p)
 
@@ -84,7 +90,7 @@ def load(path: str = LIB_PATH):
         L.kp_hierarchy_level.restype = ctypes.c_int
         L.kp_hierarchy_stats.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64)]
         L.kp_hierarchy_stats.restype = ctypes.c_int
-        L.kp_hierarchy_profile.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+        L.kp_hierarchy_profile.argtypes = [vp, i32, ctypes.POINTER(kp_level_profile)]
         L.kp_hierarchy_profile.restype = ctypes.c_int
         L.kp_hierarchy_free.argtypes = [vp]
         L.kp_hierarchy_free.restype = None
@@ -150,11 +156,11 @@ def kp_hierarchy_stats(h: int):
     return r.value, m.value
 
 
-def kp_hierarchy_profile(h: int):
-    ms = (ctypes.c_double * len(PHASES))()
-    launches = ctypes.c_int32()
-    _check(load().kp_hierarchy_profile(ctypes.c_void_p(h), ms, ctypes.byref(launches)), "kp_hierarchy_profile")
-    return dict(zip(PHASES, list(ms))), launches.value
+def kp_hierarchy_profile(h: int, level: int = -1) -> dict:
+    p = kp_level_profile()
+    _check(load().kp_hierarchy_profile(ctypes.c_void_p(h), level, ctypes.byref(p)), "kp_hierarchy_profile")
+    return {"phase_ms": dict(zip(PHASES, list(p.phase_ms))), "n": p.n, "nnz": p.nnz, "searches": p.searches,
+            "failed_cas": p.failed_cas, "launches": p.launches, "rounds": p.rounds}
 
 
 def kp_hierarchy_free(h: int):
@@ -284,8 +290,8 @@ class Hierarchy:
     def stats(self):
         return kp_hierarchy_stats(self.handle)
 
-    def profile(self):
-        return kp_hierarchy_profile(self.handle)
+    def profile(self, level: int = -1) -> dict:
+        return kp_hierarchy_profile(self.handle, level)
 
     def project(self, coarse_part, fine_part=None):
         torch = _torch()

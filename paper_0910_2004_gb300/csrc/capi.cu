@@ -245,11 +245,14 @@ kp_status kp_hierarchy_stats(const kp_hierarchy *h, int32_t *total_rounds, int64
     return KP_OK;
 }
 
-kp_status kp_hierarchy_profile(const kp_hierarchy *h, double *phase_ms, int32_t *launches) {
-    if (!h) return set_error(KP_ERR_INVALID, "null argument");
-    if (phase_ms)
-        for (int i = 0; i < KP_NUM_PHASES; i++) phase_ms[i] = h->phase_ms[i];
-    if (launches) *launches = h->launches;
+kp_status kp_hierarchy_profile(const kp_hierarchy *h, int32_t l, kp_level_profile *out) {
+    if (!h || !out) return set_error(KP_ERR_INVALID, "null argument");
+    if (l == -1) {
+        *out = h->total;
+        return KP_OK;
+    }
+    if (l < 0 || l >= (int32_t)h->per_level.size()) return set_error(KP_ERR_INVALID, "level out of range");
+    *out = h->per_level[(size_t)l];
     return KP_OK;
 }
 

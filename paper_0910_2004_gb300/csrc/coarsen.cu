@@ -34,7 +34,9 @@ struct Counters {
     int32_t U;           // sum of coarse row upper bounds
     int32_t nclass[4];   // overflow lists: [1] warp rows, [2] mid rows, [3] big rows
     int32_t nnz_out;     // coarse entry count
-    int32_t pad[3];
+    int32_t pad;
+    unsigned long long searches;     // rating passes over a row
+    unsigned long long failed_cas;   // lost proposal races
 };
 
 // ---------------------------------------------------------------------------
@@ -118,6 +120,7 @@ __device__ __forceinline__ void rate_node(const MatchParams &p, int32_t v, bool 
     }
     need = __shfl_sync(gmask, need, leader);
     if (!need) return;
+    if (gl == 0) atomicAdd(&p.ctr->searches, 1ull);
     const int32_t beg = __ldg(p.xadj + v), end = __ldg(p.xadj + v + 1);
     const int32_t cv = __ldg(p.vwgt + v);
     const int32_t outv = (R == KP_RATING_INNER_OUTER) ? __ldg(p.outw + v) : 0;
@@ -307,6 +310,7 @@ __global__ void __launch_bounds__(MATCH_BLOCK) k_suitor(SuitorParams p) {
     const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
     const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
     long long iters = 0;
+    unsigned long long fails = 0;
     for (int64_t v0 = gid; v0 < p.n; v0 += ngroups) {
         int32_t cur = (int32_t)v0;
         while (cur >= 0) {
@@ -376,10 +380,19 @@ __global__ void __launch_bounds__(MATCH_BLOCK) k_suitor(SuitorParams p) {
                 mine.au = bsnap.au;
                 // success: the displaced suitor (if any) proposes again;
                 // failure: the record changed under us, so cur searches again
-                next = cas_offer(p.offer + best.u, bsnap, mine) ? bsnap.s : cur;
+                if (cas_offer(p.offer + best.u, bsnap, mine)) {
+                    next = bsnap.s;
+                } else {
+                    next = cur;
+                    fails++;
+                }
             }
             cur = __shfl_sync(gmask, next, leader);
         }
+    }
+    if (gl == 0) {
+        atomicAdd(&p.ctr->searches, (unsigned long long)iters);
+        if (fails) atomicAdd(&p.ctr->failed_cas, fails);
     }
 }
 
@@ -1088,6 +1101,11 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         kp_level &cur = h->levels.back();
         const int32_t n = cur.n;
         if (n <= o->stop_size || (int32_t)h->levels.size() - 1 >= o->max_levels) break;
+        const int lvl_idx = (int)h->levels.size() - 1;
+        h->per_level.push_back(kp_level_profile{});
+        h->per_level.back().n = n;
+        h->per_level.back().nnz = cur.nnz;
+        const int32_t launches_before = launches;
         if (cudaMemsetAsync(sc.ctr, 0, sizeof(Counters), s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "memset counters"));
         if (cudaMemsetAsync(sc.match, 0xff, sizeof(int32_t) * (size_t)n, s) != cudaSuccess)
@@ -1108,7 +1126,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         mp.ctr = sc.ctr;
         mp.spin_limit = o->spin_limit;
         const int G = group_for_degree(n > 0 ? (double)cur.nnz / n : 0.0);
-        timer.mark(KP_PHASE_MATCH);
+        timer.mark(KP_PHASE_MATCH, lvl_idx);
         if (o->matcher == KP_MATCHER_SUITOR) {
             SuitorParams sp;
             sp.n = n;
@@ -1151,7 +1169,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         rop.cvwgt = cvw;
         rop.off = sc.off;
         rop.ctr = sc.ctr;
-        timer.mark(KP_PHASE_RELABEL);
+        timer.mark(KP_PHASE_RELABEL, lvl_idx);
         if (device_scan(rop, n, sc.partials, s) != cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "relabel scan"));
         timer.mark(-1);
@@ -1164,10 +1182,14 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
                                                       ? "proposal chain exceeded spin_limit steps"
                                                       : "matching grid barrier timed out"));
         total_rounds += (o->matcher == KP_MATCHER_SUITOR) ? 1 : hc->rounds;
+        h->per_level.back().rounds = (o->matcher == KP_MATCHER_SUITOR) ? 1 : hc->rounds;
+        h->per_level.back().searches = (int64_t)hc->searches;
+        h->per_level.back().failed_cas = (int64_t)hc->failed_cas;
         const int32_t cn = hc->cn;
         const int32_t U = hc->U;
         if (cn == n) {   // nothing matched: this level is not kept
             cur.map = nullptr;
+            h->per_level.back().launches = launches - launches_before;
             break;
         }
         total_matched += n - cn;
@@ -1202,7 +1224,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         cp.ctr = sc.ctr;
         const double avg_pair = n > 0 ? 2.0 * (double)cur.nnz / n : 0.0;
         const int Gs = avg_pair <= 7.0 ? 8 : (avg_pair <= 14.0 ? 16 : 32);
-        timer.mark(KP_PHASE_CONTRACT);
+        timer.mark(KP_PHASE_CONTRACT, lvl_idx);
         launches += (Gs < 32) ? 4 : 3;
         if (Gs == 8) launch_contract_small<8>(cp, s);
         else if (Gs == 16) launch_contract_small<16>(cp, s);
@@ -1218,7 +1240,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
             const int passes = (bits + 7) / 8;
             k_contract_big<<<num_sms(), CONTRACT_BLOCK, 0, s>>>(cp, passes);
         }
-        timer.mark(KP_PHASE_CSR);
+        timer.mark(KP_PHASE_CSR, lvl_idx);
         DegScanOp dop;
         dop.cn = cn;
         dop.degp = sc.degp;
@@ -1242,6 +1264,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
             cudaSuccess)
             return fail(cuda_error(cudaGetLastError(), "read nnz"));
         nxt.nnz = U;   // upper bound until the exact count has arrived
+        h->per_level.back().launches = launches - launches_before;
         h->levels.push_back(nxt);
         std::swap(outw_cur, outw_next);
         if ((int64_t)cn * 1000 > (int64_t)n * (1000 - o->min_shrink_permille)) break;
@@ -1250,8 +1273,16 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     h->total_rounds = total_rounds;
     h->total_matched = total_matched;
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "final sync"));
-    timer.accumulate(h->phase_ms);
-    h->launches = launches;
+    if (h->per_level.size() > h->levels.size() - 1) h->per_level.resize(h->levels.size() - 1);
+    timer.accumulate(&h->total, h->per_level);
+    h->total.launches = launches;
+    h->total.rounds = total_rounds;
+    h->total.n = n0;
+    h->total.nnz = nnz0;
+    for (const auto &lp : h->per_level) {
+        h->total.searches += lp.searches;
+        h->total.failed_cas += lp.failed_cas;
+    }
     for (size_t l = 1; l < h->levels.size(); l++) h->levels[l].nnz = pinned.nnz[l];
     *out = h;
     return KP_OK;

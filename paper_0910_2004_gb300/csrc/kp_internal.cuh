@@ -276,8 +276,8 @@ struct kp_hierarchy {
     int device = 0;
     int32_t total_rounds = 0;
     int64_t total_matched = 0;
-    int32_t launches = 0;
-    double phase_ms[KP_NUM_PHASES] = {0, 0, 0, 0, 0, 0};
+    kp_level_profile total = {};
+    std::vector<kp_level_profile> per_level;
 };
 
 namespace kp {
@@ -290,21 +290,25 @@ class PhaseTimer {
     ~PhaseTimer() {
         for (auto &m : marks_) cudaEventDestroy(m.ev);
     }
-    void mark(int phase_starting) {
+    // Starts `phase_starting` (-1: only ends the running interval) of level
+    // `level` (-1: outside the level loop).
+    void mark(int phase_starting, int level = -1) {
         if (!on_) return;
         cudaEvent_t e;
         if (cudaEventCreate(&e) != cudaSuccess) return;
         cudaEventRecord(e, s_);
-        marks_.push_back({e, phase_starting});
+        marks_.push_back({e, phase_starting, level});
     }
     // After the stream is synchronised: add each interval to the phase that
-    // began at its start mark (a mark with phase -1 ends an interval only).
-    void accumulate(double *phase_ms) {
+    // began at its start mark, per level and in total.
+    void accumulate(kp_level_profile *total, std::vector<kp_level_profile> &levels) {
         for (size_t i = 0; i + 1 < marks_.size(); i++) {
             if (marks_[i].phase < 0) continue;
             float ms = 0.f;
-            if (cudaEventElapsedTime(&ms, marks_[i].ev, marks_[i + 1].ev) == cudaSuccess)
-                phase_ms[marks_[i].phase] += ms;
+            if (cudaEventElapsedTime(&ms, marks_[i].ev, marks_[i + 1].ev) != cudaSuccess) continue;
+            total->phase_ms[marks_[i].phase] += ms;
+            const int l = marks_[i].level;
+            if (l >= 0 && l < (int)levels.size()) levels[(size_t)l].phase_ms[marks_[i].phase] += ms;
         }
     }
 
@@ -312,6 +316,7 @@ class PhaseTimer {
     struct Mark {
         cudaEvent_t ev;
         int phase;
+        int level;
     };
     bool on_;
     cudaStream_t s_;
