@@ -7,8 +7,10 @@
 //   k_match                one cooperative persistent launch running all
 //                          handshake rounds, separated by grid barriers
 //   relabel scan           coarse ids, map, c', members, row upper bounds
-//   k_contract_small<G>    coarse rows with <= G gathered entries: a G-lane
-//                          group gathers, sorts (bitonic, shuffles), merges
+//   k_contract_small       coarse rows with <= 16 gathered entries: one thread
+//                          gathers, sorts (register bitonic network), merges
+//   k_contract_warp_list   rows of 17..32 entries: one warp, shuffle bitonic
+//   k_contract_warp_smem   rows of 33..128 entries: one warp, shared memory
 //   k_contract_mid         rows <= MID_MAX entries: one block, shared memory
 //   k_contract_big         longer rows: one block, LSD radix sort in global
 //   degree scan            coarse xadj
@@ -32,9 +34,8 @@ struct Counters {
     int32_t rounds;
     int32_t cn;          // coarse node count
     int32_t U;           // sum of coarse row upper bounds
-    int32_t nclass[4];   // overflow lists: [1] warp rows, [2] mid rows, [3] big rows
+    int32_t nclass[5];   // overflow lists: [1] <=32, [2] <=128, [3] <=MID_MAX, [4] longer
     int32_t nnz_out;     // coarse entry count
-    int32_t pad;
     unsigned long long searches;     // rating passes over a row
     unsigned long long failed_cas;   // lost proposal races
 };
@@ -285,6 +286,8 @@ struct SuitorParams {
     uint64_t seed;
     Offer *offer;
     int32_t *match;
+    int32_t *parked;        // nodes left to the wide pass
+    int32_t *parked_size;
     Counters *ctr;
     long long spin_limit;
 };
@@ -302,93 +305,128 @@ __global__ void k_offer_init(SuitorParams p) {
     }
 }
 
-template <int R, int G>
+// G lanes per proposing node.  Start nodes are [0, n) (FROM_LIST = false)
+// or the parked list (FROM_LIST = true).  Every warp owns one contiguous range
+// of start nodes; its 32/G groups each follow one proposal chain (a node,
+// then whoever it displaced) and take the next start node of the range as
+// soon as their chain ends, so lanes stay busy until the range is used up.
+// With HEAVY > 0 a node whose row is longer than HEAVY entries is parked on
+// p.parked instead of being scanned by so few lanes; a later FROM_LIST pass
+// with G = 32 finishes those.  The order in which nodes propose does not
+// change the final matching.
+template <int R, int G, int HEAVY, bool FROM_LIST>
 __global__ void __launch_bounds__(MATCH_BLOCK) k_suitor(SuitorParams p) {
+    constexpr int NG = 32 / G;
     const unsigned gmask = group_mask<G>();
-    const int gl = threadIdx.x & (G - 1);
-    const int leader = (threadIdx.x & 31) & ~(G - 1);
-    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int leader = lane & ~(G - 1);
+    const unsigned below_leader = (1u << leader) - 1u;
+    const int64_t count = FROM_LIST ? (int64_t)ld_relaxed_i32(p.parked_size) : (int64_t)p.n;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t chunk = (count + nwarps - 1) / nwarps;
+    int64_t pos = warp_id * chunk;
+    const int64_t stop = min(count, pos + chunk);
     long long iters = 0;
     unsigned long long fails = 0;
-    for (int64_t v0 = gid; v0 < p.n; v0 += ngroups) {
-        int32_t cur = (int32_t)v0;
-        while (cur >= 0) {
-            if (++iters > p.spin_limit) {   // a bound, not a wait: report instead of looping on
-                if (gl == 0) atomicOr(&p.ctr->err, ERR_TIMEOUT);
-                return;
-            }
-            const int32_t beg = __ldg(p.xadj + cur), end = __ldg(p.xadj + cur + 1);
-            const int32_t acur = rating_attr<R>(p.vwgt, p.outw, cur);
-            Cand best;
-            best.u = -1;
-            best.num = best.den = best.h = 0;
-            int32_t bw = 0;
-            Offer bsnap = {-1, 0, 0, 0};
-            for (int32_t e = beg + gl; e < end; e += G) {
-                const int32_t v = __ldg(p.adjncy + e);
-                const int32_t w = __ldg(p.ewgt + e);
-                const Offer st = ld_offer(p.offer + v);
-                Cand c;
-                c.u = v;
-                rating_ab<R>(w, acur, st.au, c.num, c.den);
-                c.h = edge_hash(p.seed, cur, v);
-                bool eligible = st.s < 0;
-                if (!eligible) {
-                    // compare at v: the offer of cur against the standing offer of st.s
-                    Cand a, b;
-                    a.u = cur;
-                    a.num = c.num;
-                    a.den = c.den;
-                    a.h = c.h;
-                    b.u = st.s;
-                    rating_ab<R>(st.w, st.as, st.au, b.num, b.den);
-                    b.h = edge_hash(p.seed, st.s, v);
-                    eligible = better(a, b, v);
-                }
-                if (eligible && better(c, best, cur)) {
-                    best = c;
-                    bw = w;
-                    bsnap = st;
-                }
-            }
-#pragma unroll
-            for (int off = G / 2; off > 0; off >>= 1) {
-                Cand o;
-                o.num = __shfl_xor_sync(gmask, best.num, off);
-                o.den = __shfl_xor_sync(gmask, best.den, off);
-                o.h = __shfl_xor_sync(gmask, best.h, off);
-                o.u = __shfl_xor_sync(gmask, best.u, off);
-                const int32_t ow = __shfl_xor_sync(gmask, bw, off);
-                Offer os;
-                os.s = __shfl_xor_sync(gmask, bsnap.s, off);
-                os.w = __shfl_xor_sync(gmask, bsnap.w, off);
-                os.as = __shfl_xor_sync(gmask, bsnap.as, off);
-                os.au = __shfl_xor_sync(gmask, bsnap.au, off);
-                if (better(o, best, cur)) {
-                    best = o;
-                    bw = ow;
-                    bsnap = os;
-                }
-            }
-            int32_t next = -1;
-            if (best.u >= 0 && gl == 0) {
-                Offer mine;
-                mine.s = cur;
-                mine.w = bw;
-                mine.as = acur;
-                mine.au = bsnap.au;
-                // success: the displaced suitor (if any) proposes again;
-                // failure: the record changed under us, so cur searches again
-                if (cas_offer(p.offer + best.u, bsnap, mine)) {
-                    next = bsnap.s;
-                } else {
-                    next = cur;
-                    fails++;
-                }
-            }
-            cur = __shfl_sync(gmask, next, leader);
+    int32_t cur = -1;
+    bool aborted = false;
+    for (;;) {
+        // the whole warp leaves together (full-warp votes follow)
+        if (__any_sync(0xffffffffu, aborted)) break;
+        // give every idle group the next start node of the warp's range
+        const unsigned need = __ballot_sync(0xffffffffu, cur < 0 && gl == 0);
+        if (need && pos < stop) {
+            const int64_t avail = min((int64_t)NG, stop - pos);
+            const int rank = __popc(need & below_leader);
+            if (cur < 0 && rank < avail) cur = FROM_LIST ? p.parked[pos + rank] : (int32_t)(pos + rank);
+            pos += min((int64_t)__popc(need), avail);
         }
+        if (__ballot_sync(0xffffffffu, cur >= 0) == 0) break;
+        if (cur < 0) continue;
+        if (++iters > p.spin_limit) {   // a bound, not a wait: report instead of looping on
+            if (gl == 0) atomicOr(&p.ctr->err, ERR_TIMEOUT);
+            cur = -1;
+            aborted = true;
+            continue;
+        }
+        const int32_t beg = __ldg(p.xadj + cur), end = __ldg(p.xadj + cur + 1);
+        if (HEAVY > 0 && end - beg > HEAVY) {   // park it for the wide pass
+            if (gl == 0) p.parked[atomicAdd(p.parked_size, 1)] = cur;
+            cur = -1;
+            continue;
+        }
+        const int32_t acur = rating_attr<R>(p.vwgt, p.outw, cur);
+        Cand best;
+        best.u = -1;
+        best.num = best.den = best.h = 0;
+        int32_t bw = 0;
+        Offer bsnap = {-1, 0, 0, 0};
+#pragma unroll 4
+        for (int32_t e = beg + gl; e < end; e += G) {
+            const int32_t v = __ldg(p.adjncy + e);
+            const int32_t w = __ldg(p.ewgt + e);
+            const Offer st = ld_offer(p.offer + v);
+            Cand c;
+            c.u = v;
+            rating_ab<R>(w, acur, st.au, c.num, c.den);
+            c.h = edge_hash(p.seed, cur, v);
+            bool eligible = st.s < 0;
+            if (!eligible) {
+                // compare at v: the offer of cur against the standing offer of st.s
+                Cand a, b;
+                a.u = cur;
+                a.num = c.num;
+                a.den = c.den;
+                a.h = c.h;
+                b.u = st.s;
+                rating_ab<R>(st.w, st.as, st.au, b.num, b.den);
+                b.h = edge_hash(p.seed, st.s, v);
+                eligible = better(a, b, v);
+            }
+            if (eligible && better(c, best, cur)) {
+                best = c;
+                bw = w;
+                bsnap = st;
+            }
+        }
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) {
+            Cand o;
+            o.num = __shfl_xor_sync(gmask, best.num, off);
+            o.den = __shfl_xor_sync(gmask, best.den, off);
+            o.h = __shfl_xor_sync(gmask, best.h, off);
+            o.u = __shfl_xor_sync(gmask, best.u, off);
+            const int32_t ow = __shfl_xor_sync(gmask, bw, off);
+            Offer os;
+            os.s = __shfl_xor_sync(gmask, bsnap.s, off);
+            os.w = __shfl_xor_sync(gmask, bsnap.w, off);
+            os.as = __shfl_xor_sync(gmask, bsnap.as, off);
+            os.au = __shfl_xor_sync(gmask, bsnap.au, off);
+            if (better(o, best, cur)) {
+                best = o;
+                bw = ow;
+                bsnap = os;
+            }
+        }
+        int32_t next = -1;
+        if (best.u >= 0 && gl == 0) {
+            Offer mine;
+            mine.s = cur;
+            mine.w = bw;
+            mine.as = acur;
+            mine.au = bsnap.au;
+            // success: the displaced suitor (if any) proposes next;
+            // failure: the record changed under us, so cur searches again
+            if (cas_offer(p.offer + best.u, bsnap, mine)) {
+                next = bsnap.s;
+            } else {
+                next = cur;
+                fails++;
+            }
+        }
+        cur = __shfl_sync(gmask, next, leader);
     }
     if (gl == 0) {
         atomicAdd(&p.ctr->searches, (unsigned long long)iters);
@@ -487,7 +525,7 @@ struct ContractParams {
     int32_t *big_w;
     int32_t *degp;      // coarse row length after merging
     int32_t *outw;      // Out of the coarse node (sum of its row), may be null
-    int32_t *lists[4];  // overflow lists by class (index 1..3)
+    int32_t *lists[5];  // overflow lists by class (index 1..4)
     Counters *ctr;
 };
 
@@ -560,15 +598,77 @@ __device__ __forceinline__ void contract_group(const ContractParams &p, int32_t 
     }
 }
 
-template <int G>
+// Rows with at most 16 gathered entries: one thread per coarse node.  The
+// entries (map(u), omega) are packed as (key << 32 | omega) in 16 registers,
+// sorted by a bitonic network (sentinels last), merged run by run and
+// written.  Longer rows go to the overflow lists (warp-aggregated appends).
+constexpr int TNET = 16;
+
+__device__ __forceinline__ void contract_thread(const ContractParams &p, int32_t x, int32_t xa, int32_t da,
+                                                int32_t xb, int32_t db) {
+    constexpr uint64_t SENT64 = (uint64_t)SENT << 32;
+    uint64_t r[TNET];
+#pragma unroll
+    for (int i = 0; i < TNET; i++) {
+        uint64_t v = SENT64;
+        if (i < da + db) {
+            const int32_t e = i < da ? xa + i : xb + (i - da);
+            const int32_t t = p.map[p.adjncy[e]];
+            if (t != x) v = ((uint64_t)(uint32_t)t << 32) | (uint32_t)p.ewgt[e];
+        }
+        r[i] = v;
+    }
+#pragma unroll
+    for (int k = 2; k <= TNET; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int i = 0; i < TNET; i++) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint64_t a = r[i], b = r[l];
+                    const bool sw = ((i & k) == 0) ? (a > b) : (a < b);
+                    r[i] = sw ? b : a;
+                    r[l] = sw ? a : b;
+                }
+            }
+        }
+    }
+    const int32_t o = p.off[x];
+    int32_t cnt = 0, curk = -1, sum = 0, total = 0;
+#pragma unroll
+    for (int i = 0; i < TNET; i++) {
+        const int32_t k = (int32_t)(r[i] >> 32);
+        const int32_t w = (int32_t)(uint32_t)r[i];
+        if (k != SENT) {
+            total += w;
+            if (k == curk) {
+                sum += w;
+            } else {
+                if (curk >= 0) {
+                    p.tmp_adj[o + cnt] = curk;
+                    p.tmp_w[o + cnt] = sum;
+                    cnt++;
+                }
+                curk = k;
+                sum = w;
+            }
+        }
+    }
+    if (curk >= 0) {
+        p.tmp_adj[o + cnt] = curk;
+        p.tmp_w[o + cnt] = sum;
+        cnt++;
+    }
+    p.degp[x] = cnt;
+    if (p.outw) p.outw[x] = total;
+}
+
 __global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_small(ContractParams p) {
-    constexpr int PER_WARP = 32 / G;
     const int lane = threadIdx.x & 31;
-    const int gl = lane & (G - 1);
-    const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t x0 = warp_id * PER_WARP; x0 < p.cn; x0 += nwarps * PER_WARP) {
-        const int64_t x = x0 + lane / G;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t x0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); x0 < p.cn; x0 += stride) {
+        const int64_t x = x0 + lane;
         int cls = -1;
         int32_t da = 0, db = 0, xa = 0, xb = 0;
         if (x < p.cn) {
@@ -581,13 +681,11 @@ __global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_small(ContractParam
                 db = p.xadj[b + 1] - xb;
             }
             const int32_t L = da + db;
-            cls = L <= G ? 0 : L <= 32 ? 1 : L <= MID_MAX ? 2 : 3;
+            cls = L <= TNET ? 0 : L <= 32 ? 1 : L <= 128 ? 2 : L <= MID_MAX ? 3 : 4;
         }
-        if (cls == 0) contract_group<G>(p, (int32_t)x, xa, da, xb, db);
-        // overflow appends by the group leaders, aggregated per warp
 #pragma unroll
-        for (int c = 1; c <= 3; c++) {
-            const bool mine = gl == 0 && cls == c;
+        for (int c = 1; c <= 4; c++) {
+            const bool mine = cls == c;
             const unsigned m = __ballot_sync(0xffffffffu, mine);
             if (m) {
                 int32_t pos = 0;
@@ -597,6 +695,103 @@ __global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_small(ContractParam
                 if (mine) p.lists[c][pos + __popc(m & lanemask_lt())] = (int32_t)x;
             }
         }
+        if (cls == 0) contract_thread(p, (int32_t)x, xa, da, xb, db);
+    }
+}
+
+// Rows of 33..128 gathered entries (overflow class 2): one warp each,
+// bitonic sort of up to 128 (key, omega) pairs in the warp's shared memory,
+// run indices by a warp scan of the head flags, run sums by shared atomics.
+constexpr int WSORT = 128;
+
+__global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_warp_smem(ContractParams p) {
+    constexpr int NW = CONTRACT_BLOCK / 32;
+    __shared__ int32_t sk[NW][WSORT];
+    __shared__ int32_t sv[NW][WSORT];
+    __shared__ int32_t ss[NW][WSORT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t *K = sk[warp], *V = sv[warp], *S = ss[warp];
+    const int32_t count = p.ctr->nclass[2];
+    const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t li = warp_id; li < count; li += nwarps) {
+        const int32_t x = p.lists[2][li];
+        const int32_t a = p.first[x], b = p.second[x];
+        const int32_t xa = p.xadj[a], da = p.xadj[a + 1] - xa;
+        const int32_t xb = b >= 0 ? p.xadj[b] : 0, db = b >= 0 ? p.xadj[b + 1] - xb : 0;
+        const int32_t L = da + db;
+        const int P = L <= 64 ? 64 : 128;
+        for (int i = lane; i < P; i += 32) {
+            int32_t key = SENT, val = 0;
+            if (i < L) {
+                const int32_t e = i < da ? xa + i : xb + (i - da);
+                const int32_t t = p.map[p.adjncy[e]];
+                if (t != x) {
+                    key = t;
+                    val = p.ewgt[e];
+                }
+            }
+            K[i] = key;
+            V[i] = val;
+            S[i] = 0;
+        }
+        __syncwarp();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = lane; t < P / 2; t += 32) {
+                    const int i = 2 * j * (t / j) + (t % j);
+                    const int l = i + j;
+                    const int32_t ki = K[i], kl = K[l];
+                    const bool up = (i & k) == 0;
+                    if (up ? ki > kl : ki < kl) {
+                        K[i] = kl;
+                        K[l] = ki;
+                        const int32_t tv = V[i];
+                        V[i] = V[l];
+                        V[l] = tv;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        // P/32 consecutive items per lane
+        const int per = P / 32;
+        const int base = lane * per;
+        int heads = 0;
+        for (int q = 0; q < per; q++) {
+            const int i = base + q;
+            heads += (K[i] != SENT && (i == 0 || K[i - 1] != K[i])) ? 1 : 0;
+        }
+        int incl = heads;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const int nruns = __shfl_sync(0xffffffffu, incl, 31);
+        int r = incl - heads - 1;
+        const int32_t o = p.off[x];
+        int32_t wsum = 0;
+        for (int q = 0; q < per; q++) {
+            const int i = base + q;
+            const int32_t k = K[i];
+            if (k == SENT) break;
+            if (i == 0 || K[i - 1] != k) {
+                r++;
+                p.tmp_adj[o + r] = k;
+            }
+            atomicAdd(&S[r], V[i]);
+            wsum += V[i];
+        }
+        __syncwarp();
+        for (int i = lane; i < nruns; i += 32) p.tmp_w[o + i] = S[i];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, d);
+        if (lane == 0) {
+            p.degp[x] = nruns;
+            if (p.outw) p.outw[x] = wsum;
+        }
+        __syncwarp();
     }
 }
 
@@ -617,8 +812,8 @@ __global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_warp_list(ContractP
 // Rows of 33..MID_MAX gathered entries: one block per coarse node, bitonic
 // sort in shared memory, then run heads, run sums and the merged row.
 __global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_mid(ContractParams p) {
-    const int32_t *list = p.lists[2];
-    const int32_t count = p.ctr->nclass[2];
+    const int32_t *list = p.lists[3];
+    const int32_t count = p.ctr->nclass[3];
     __shared__ int32_t keys[MID_MAX];
     __shared__ int32_t vals[MID_MAX];
     __shared__ int32_t sums[MID_MAX];
@@ -714,8 +909,8 @@ __global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_mid(ContractParams 
 //    per thread is ranked with warp match masks and per-warp digit counts
 // 3. merge equal neighbours from big back into tmp (run sums by atomics)
 __global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_big(ContractParams p, int passes) {
-    const int32_t *list = p.lists[3];
-    const int32_t count = p.ctr->nclass[3];
+    const int32_t *list = p.lists[4];
+    const int32_t count = p.ctr->nclass[4];
     constexpr int NW = CONTRACT_BLOCK / 32;
     __shared__ int32_t base[256];
     __shared__ int32_t chunk_tot[256];
@@ -917,13 +1112,23 @@ kp_status launch_match(int rating, const MatchParams &p, int G, cudaStream_t s) 
     }
 }
 
-template <int R, int G>
+// One group per start node; nodes with rows longer than HEAVY are parked and
+// finished by one warp each.
+template <int R, int G, int HEAVY>
 kp_status launch_suitor_rg(const SuitorParams &p, cudaStream_t s) {
+    // persistent grid: the blocks that fit at once, fewer for small levels
+    static int occ = -1;
+    if (occ < 0) {
+        int o = 0;
+        KP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_suitor<R, G, HEAVY, false>, MATCH_BLOCK, 0));
+        occ = o > 0 ? o : 1;
+    }
     const int64_t want = ((int64_t)p.n * G + MATCH_BLOCK - 1) / MATCH_BLOCK;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 16));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)occ * num_sms()));
     const int grid1 = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)p.n + 255) / 256, (int64_t)num_sms() * 8));
     k_offer_init<R><<<grid1, 256, 0, s>>>(p);
-    k_suitor<R, G><<<grid, MATCH_BLOCK, 0, s>>>(p);
+    k_suitor<R, G, HEAVY, false><<<grid, MATCH_BLOCK, 0, s>>>(p);
+    if (HEAVY > 0) k_suitor<R, 32, 0, true><<<num_sms() * 4, MATCH_BLOCK, 0, s>>>(p);
     k_suitor_final<<<grid1, 256, 0, s>>>(p);
     KP_CUDA(cudaGetLastError());
     return KP_OK;
@@ -932,11 +1137,19 @@ kp_status launch_suitor_rg(const SuitorParams &p, cudaStream_t s) {
 template <int R>
 kp_status launch_suitor_r(const SuitorParams &p, int G, cudaStream_t s) {
     switch (G) {
-    case 4: return launch_suitor_rg<R, 4>(p, s);
-    case 8: return launch_suitor_rg<R, 8>(p, s);
-    case 16: return launch_suitor_rg<R, 16>(p, s);
-    default: return launch_suitor_rg<R, 32>(p, s);
+    case 1: return launch_suitor_rg<R, 1, 32>(p, s);
+    case 4: return launch_suitor_rg<R, 4, 128>(p, s);
+    case 8: return launch_suitor_rg<R, 8, 512>(p, s);
+    default: return launch_suitor_rg<R, 32, 0>(p, s);
     }
+}
+
+// Lanes per proposing node from the level's mean degree.
+int suitor_group(double avg) {
+    if (avg <= 12.0) return 1;
+    if (avg <= 40.0) return 4;
+    if (avg <= 160.0) return 8;
+    return 32;
 }
 
 kp_status launch_suitor(int rating, const SuitorParams &p, int G, cudaStream_t s) {
@@ -957,13 +1170,6 @@ int group_for_degree(double avg) {
     return 32;
 }
 
-template <int G>
-void launch_contract_small(const ContractParams &p, cudaStream_t s) {
-    constexpr int per_block = (CONTRACT_BLOCK / 32) * (32 / G);
-    int64_t want = ((int64_t)p.cn + per_block - 1) / per_block;
-    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 16));
-    k_contract_small<G><<<grid, CONTRACT_BLOCK, 0, s>>>(p);
-}
 
 // Scratch reused by all levels (sized for level 0).
 struct Scratch {
@@ -973,7 +1179,7 @@ struct Scratch {
     int32_t *first = nullptr, *second = nullptr, *off = nullptr, *degp = nullptr;
     int32_t *outw_a = nullptr, *outw_b = nullptr;
     int32_t *tmp_adj = nullptr, *tmp_w = nullptr, *big_adj = nullptr, *big_w = nullptr;
-    int32_t *lists[4] = {nullptr, nullptr, nullptr, nullptr};
+    int32_t *lists[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     Offer *offer = nullptr;
     uint64_t *partials = nullptr;
     Counters *ctr = nullptr;
@@ -1074,7 +1280,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     SC_GET(sc.tmp_w, nnz0);
     SC_GET(sc.big_adj, nnz0);
     SC_GET(sc.big_w, nnz0);
-    for (int c = 1; c <= 3; c++) SC_GET(sc.lists[c], n0);
+    for (int c = 1; c <= 4; c++) SC_GET(sc.lists[c], n0);
     SC_GET(sc.partials, scan_tiles(n0) + 1);
     if (o->matcher == KP_MATCHER_SUITOR) SC_GET(sc.offer, n0);
     SC_GET(sc.ctr, 1);
@@ -1128,6 +1334,8 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         const int G = group_for_degree(n > 0 ? (double)cur.nnz / n : 0.0);
         timer.mark(KP_PHASE_MATCH, lvl_idx);
         if (o->matcher == KP_MATCHER_SUITOR) {
+            if (cudaMemsetAsync(&sc.ctr->list_size[0], 0, sizeof(int32_t), s) != cudaSuccess)
+                return fail(cuda_error(cudaGetLastError(), "memset parked"));
             SuitorParams sp;
             sp.n = n;
             sp.xadj = cur.xadj;
@@ -1138,10 +1346,13 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
             sp.seed = o->seed;
             sp.offer = sc.offer;
             sp.match = sc.match;
+            sp.parked = sc.list0;
+            sp.parked_size = &sc.ctr->list_size[0];
             sp.ctr = sc.ctr;
             sp.spin_limit = o->spin_limit;
-            st = launch_suitor(rating, sp, G, s);
-            launches += 3;
+            const int Gs = suitor_group(n > 0 ? (double)cur.nnz / n : 0.0);
+            st = launch_suitor(rating, sp, Gs, s);
+            launches += (Gs < 32) ? 4 : 3;
         } else {
             st = launch_match(rating, mp, G, s);
             launches += 1;
@@ -1220,21 +1431,19 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         cp.big_w = sc.big_w;
         cp.degp = sc.degp;
         cp.outw = (rating == KP_RATING_INNER_OUTER) ? outw_next : nullptr;
-        for (int c = 0; c < 4; c++) cp.lists[c] = sc.lists[c];
+        for (int c = 0; c < 5; c++) cp.lists[c] = sc.lists[c];
         cp.ctr = sc.ctr;
-        const double avg_pair = n > 0 ? 2.0 * (double)cur.nnz / n : 0.0;
-        const int Gs = avg_pair <= 7.0 ? 8 : (avg_pair <= 14.0 ? 16 : 32);
         timer.mark(KP_PHASE_CONTRACT, lvl_idx);
-        launches += (Gs < 32) ? 4 : 3;
-        if (Gs == 8) launch_contract_small<8>(cp, s);
-        else if (Gs == 16) launch_contract_small<16>(cp, s);
-        else launch_contract_small<32>(cp, s);
-        // overflow classes: their sizes are only known on the device, so the
-        // launches use fixed grids that stride over the lists
+        launches += 5;
         {
-            const int grid_w = num_sms() * 8;
-            if (Gs < 32) k_contract_warp_list<<<grid_w, CONTRACT_BLOCK, 0, s>>>(cp);
-            k_contract_mid<<<num_sms() * 2, CONTRACT_BLOCK, 0, s>>>(cp);
+            const int64_t want = ((int64_t)cn + CONTRACT_BLOCK - 1) / CONTRACT_BLOCK;
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)1 << 30));
+            k_contract_small<<<grid, CONTRACT_BLOCK, 0, s>>>(cp);
+            // overflow classes: their sizes are only known on the device, so the
+            // launches use fixed grids that stride over the lists
+            k_contract_warp_list<<<num_sms() * 8, CONTRACT_BLOCK, 0, s>>>(cp);
+            k_contract_warp_smem<<<num_sms() * 8, CONTRACT_BLOCK, 0, s>>>(cp);
+            k_contract_mid<<<num_sms() * 4, CONTRACT_BLOCK, 0, s>>>(cp);
             int bits = 1;
             while (bits < 31 && ((int64_t)1 << bits) < (int64_t)cn) bits++;
             const int passes = (bits + 7) / 8;
