@@ -112,7 +112,10 @@ typedef enum {
  *   profile              1: time every phase with CUDA events on the stream
  *                        (read with kp_hierarchy_profile)
  *   matcher              a kp_matcher: how the matching of each level is
- *                        found; both give the same unique matching */
+ *                        found; both give the same unique matching
+ *   arena_bytes          initial size of the device arena that holds the
+ *                        coarse levels (0: sized from the input); the
+ *                        arena grows automatically when a level does not fit */
 typedef struct {
     int32_t rating;
     uint64_t seed;
@@ -123,11 +126,12 @@ typedef struct {
     int32_t validate;
     int32_t profile;
     int32_t matcher;
+    int64_t arena_bytes;
 } kp_options;
 
 /* Fills *o with the defaults: EXPANSION_STAR2, seed 1, stop_size 40,
  * max_levels 64, min_shrink_permille 50, spin_limit 1<<22, validate 1,
- * profile 0, matcher SUITOR. */
+ * profile 0, matcher SUITOR, arena_bytes 0. */
 void kp_options_default(kp_options *o);
 
 /* A hierarchy of graphs G_0 (the input) .. G_L (the coarsest) with the maps

@@ -1,0 +1,301 @@
+// Device-side state of the coarsening engine, shared by the matching and the
+// contraction translation units.
+//
+// The level loop is driven from device memory: a table of level descriptors
+// (sizes, array pointers, flags), per-level counters and a bump arena from
+// which coarse levels are carved once their sizes are known on the device.
+// Every kernel of level l reads its sizes and pointers from the table, skips
+// itself when level l is not being contracted, and the stop rule is decided
+// on the device, so the host can enqueue levels ahead without waiting.
+#pragma once
+
+#include "kp_internal.cuh"
+
+namespace kp {
+
+constexpr int32_t SENT = 0x7fffffff;   // sorts after every node id
+constexpr int MID_MAX = 2048;          // longest row handled in shared memory
+constexpr int MATCH_BLOCK = 256;
+constexpr int CONTRACT_BLOCK = 256;
+constexpr int MAX_LEVELS = 128;        // level table size (kp_options.max_levels <= 120)
+
+// level flags
+enum : int32_t { LV_ACTIVE = 1, LV_BUILT = 2, LV_NOMATCH = 4 };
+
+struct Counters {   // one per level, zeroed before the level runs
+    GridBarrier bar;
+    int32_t err;
+    int32_t list_size[2];
+    int32_t rounds;
+    int32_t cn;            // coarse node count
+    int32_t U;             // sum of coarse row upper bounds
+    int32_t nclass[5];     // overflow lists: [1] <=32, [2] <=128, [3] <=MID_MAX, [4] longer
+    int32_t nnz_out;       // coarse entry count
+    int32_t tile_counter[2];
+    int32_t pad;
+    unsigned long long searches;     // rating passes over a row
+    unsigned long long failed_cas;   // lost proposal races
+};
+
+struct DevLevel {
+    int32_t n, nnz, U, flags;
+    int32_t *xadj, *adjncy, *ewgt, *vwgt;
+    int32_t *map;    // to level l+1
+    int32_t *outw;   // Out(v) (innerOuter only)
+};
+
+// What the host needs to steer the loop, written by the device into mapped
+// pinned host memory when a level ends (no copy on the stream).
+struct LevelSnap {
+    int32_t stop;
+    int32_t cn;
+    int32_t nnz;
+    int32_t done;
+};
+
+struct DevState {
+    DevLevel lv[MAX_LEVELS];
+    Counters ctr[MAX_LEVELS];
+    char *arena;
+    unsigned long long arena_cap, arena_used;
+    int32_t stop_size, max_levels, min_shrink_permille, inner_outer;
+    int32_t stop;       // coarsening has ended
+    int32_t overflow;   // 1 + the level whose arrays did not fit the arena
+    int32_t err;        // ERR_TIMEOUT from a bounded wait
+    int32_t pad;
+    LevelSnap *snap;    // host-mapped, one per level
+};
+
+// Ends the loop: the level is not contracted further and the host is told.
+__device__ __forceinline__ void stop_at(DevState *st, int level, int32_t err_bits) {
+    if (err_bits) atomicOr(&st->err, err_bits);
+    atomicAnd(&st->lv[level].flags, ~LV_ACTIVE);
+    st->stop = 1;
+    volatile LevelSnap *s = st->snap + level;
+    s->stop = 1;
+    s->done = 1;
+}
+
+// Offer record of node u for the proposal matching (16 bytes, one 128-bit
+// CAS): current suitor s (-1 none), omega(s,u), rating attribute of s, and
+// u's own rating attribute (c, or Out for innerOuter).
+struct __align__(16) Offer {
+    int32_t s;
+    int32_t w;
+    int32_t as;
+    int32_t au;
+};
+
+// Decoupled look-back scan status of one tile; the flag carries the scan's
+// epoch so the array never needs clearing between scans.
+struct TileStatus {
+    unsigned long long agg;
+    unsigned long long incl;
+    int32_t flag;   // (epoch << 2) | 1 aggregate ready, | 2 inclusive prefix ready
+    int32_t pad;
+};
+
+// Scratch sized for level 0 and reused by every level.
+struct Work {
+    Offer *offer;
+    int32_t *match, *cand, *list0, *list1;
+    int32_t *first, *second, *off, *degp;
+    int32_t *tmp_adj, *tmp_w, *big_adj, *big_w;
+    int32_t *lists[5];
+    TileStatus *status;
+    uint64_t seed;
+    long long spin_limit;
+};
+
+// ---------------------------------------------------------------------------
+// ratings (Section 3.1) as exact fractions
+// ---------------------------------------------------------------------------
+// The rating of an edge of weight w whose ends carry attributes a and b
+// (c for the c-based ratings, Out for innerOuter); symmetric in a and b.
+template <int R>
+__device__ __forceinline__ void rating_ab(int32_t w, int32_t a, int32_t b, uint64_t &num, uint64_t &den) {
+    const uint64_t W = (uint64_t)(uint32_t)w;
+    if (R == KP_RATING_EXPANSION_STAR2) {
+        num = W * W;
+        den = (uint64_t)(uint32_t)a * (uint64_t)(uint32_t)b;
+    } else if (R == KP_RATING_INNER_OUTER) {
+        num = W;
+        den = (uint64_t)((int64_t)a + (int64_t)b - 2 * (int64_t)w);
+    } else if (R == KP_RATING_WEIGHT) {
+        num = W;
+        den = 1;
+    } else if (R == KP_RATING_EXPANSION) {
+        num = W;
+        den = (uint64_t)(uint32_t)a + (uint64_t)(uint32_t)b;
+    } else {
+        num = W;
+        den = (uint64_t)(uint32_t)a * (uint64_t)(uint32_t)b;
+    }
+}
+
+template <int R>
+__device__ __forceinline__ int32_t rating_attr(const int32_t *vwgt, const int32_t *outw, int32_t v) {
+    if (R == KP_RATING_INNER_OUTER) return outw[v];
+    if (R == KP_RATING_WEIGHT) return 0;
+    return vwgt[v];
+}
+
+// A candidate edge {v,u} seen from v.
+struct Cand {
+    uint64_t num, den, h;
+    int32_t u;
+};
+
+// Strict order: higher rating, then higher hash, then smaller (min,max) ids.
+__device__ __forceinline__ bool better(const Cand &a, const Cand &b, int32_t v) {
+    if (b.u < 0) return a.u >= 0;
+    if (a.u < 0) return false;
+    const int c = cmp_frac(a.num, a.den, b.num, b.den);
+    if (c != 0) return c > 0;
+    if (a.h != b.h) return a.h > b.h;
+    const int32_t alo = min(v, a.u), ahi = max(v, a.u), blo = min(v, b.u), bhi = max(v, b.u);
+    if (alo != blo) return alo < blo;
+    return ahi < bhi;
+}
+
+// ---------------------------------------------------------------------------
+// memory-model helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire_i32(const int32_t *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_i32(int32_t *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Carves `bytes` (256-byte aligned) from the arena; nullptr when full.
+__device__ __forceinline__ char *arena_carve(DevState *st, unsigned long long bytes) {
+    const unsigned long long b = (bytes + 255ull) & ~255ull;
+    const unsigned long long at = st->arena_used;
+    if (at + b > st->arena_cap) return nullptr;
+    st->arena_used = at + b;
+    return st->arena + at;
+}
+
+// ---------------------------------------------------------------------------
+// single-pass exclusive scan (decoupled look-back) over 64-bit values
+//   bool     Op::prepare()                 false: the level is not active
+//   int64_t  Op::count()
+//   int32_t *Op::tile_counter()            zero before the scan
+//   uint64_t Op::load(int64_t i)
+//   void     Op::store(int64_t i, uint64_t excl, uint64_t v)
+//   void     Op::total(uint64_t t)         once, with the sum of all items
+//   void     Op::fail()                    a look-back wait ran out
+// Tiles are taken in order from a counter, so every tile's predecessors are
+// held by running blocks; each wait for a predecessor is bounded.
+// ---------------------------------------------------------------------------
+template <class Op>
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_lb(Op op, TileStatus *status, int32_t epoch,
+                                                        long long spin_limit) {
+    __shared__ int64_t s_tile;
+    __shared__ unsigned long long s_prefix;
+    __shared__ int s_abort;
+    if (!op.prepare()) return;
+    const int64_t count = op.count();
+    const int64_t tiles = (count + SCAN_TILE - 1) / SCAN_TILE;
+    if (tiles == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) op.total(0);
+        return;
+    }
+    int32_t *counter = op.tile_counter();
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t tile = s_tile;
+        if (tile >= tiles) break;
+        const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+        uint64_t v[SCAN_ITEMS];
+        uint64_t sum = 0;
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; j++) {
+            v[j] = base + j < count ? op.load(base + j) : 0;
+            sum += v[j];
+        }
+        uint64_t total;
+        const uint64_t excl = block_exclusive_scan<SCAN_BLOCK>(sum, &total);
+        if (threadIdx.x == 0) {
+            unsigned long long prefix = 0;
+            int ok = 1;
+            TileStatus *me = status + tile;
+            if (tile == 0) {
+                st_relaxed_u64(&me->incl, total);
+                st_release_i32(&me->flag, (epoch << 2) | 2);
+            } else {
+                st_relaxed_u64(&me->agg, total);
+                st_release_i32(&me->flag, (epoch << 2) | 1);
+                int64_t j = tile - 1;
+                long long it = 0;
+                while (j >= 0) {
+                    const int f = ld_acquire_i32(&status[j].flag);
+                    if ((f >> 2) != epoch || (f & 3) == 0) {
+                        if (++it > spin_limit) {
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(32);
+                        continue;
+                    }
+                    if ((f & 3) == 2) {
+                        prefix += ld_relaxed_u64(&status[j].incl);
+                        break;
+                    }
+                    prefix += ld_relaxed_u64(&status[j].agg);
+                    j--;
+                }
+                st_relaxed_u64(&me->incl, prefix + total);
+                st_release_i32(&me->flag, (epoch << 2) | 2);
+            }
+            s_prefix = prefix;
+            s_abort = !ok;
+            if (!ok) op.fail();
+            else if (tile == tiles - 1) op.total(prefix + total);
+        }
+        __syncthreads();
+        if (s_abort) return;
+        uint64_t p = s_prefix + excl;
+#pragma unroll
+        for (int j = 0; j < SCAN_ITEMS; j++) {
+            if (base + j < count) op.store(base + j, p, v[j]);
+            p += v[j];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers (host), defined in match.cu and contract.cu
+// ---------------------------------------------------------------------------
+struct LevelLaunch {
+    DevState *st;
+    Work w;
+    int level;
+    int rating;
+    int matcher;
+    int32_t n_bound;     // upper bound of the level's node count (grid sizes)
+    int64_t nnz_bound;   // upper bound of its entry count
+    int32_t epoch_relabel, epoch_degscan;
+};
+
+kp_status launch_out_weight(DevState *st, int32_t n0, const int32_t *xadj, const int32_t *ewgt, int32_t *outw,
+                            cudaStream_t s, int32_t *launches);
+kp_status launch_matching(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
+kp_status launch_relabel(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
+kp_status launch_contract(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
+kp_status launch_csr(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
+
+}  // namespace kp

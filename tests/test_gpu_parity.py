@@ -245,6 +245,16 @@ def test_tiny_and_degenerate():
             h.free()
 
 
+@pytest.mark.parametrize("matcher", MATCHERS)
+def test_arena_growth_resumes_exactly(matcher):
+    """A tiny initial arena overflows at several levels; the engine grows it
+    and resumes at the level that did not fit, with the same results."""
+    for g, r in [(I.rgg2d(30000, 9, wmax=5), "expansion*2"), (I.grid3d(20, 20, 20), "innerOuter")]:
+        h, dg, levels, maps = run_gpu(g, rating=r, seed=3, stop_size=20, matcher=matcher, arena_bytes=4096)
+        assert_same(levels, maps, O.coarsen(g, r, 3, 20), f"arena {g.name} {matcher}")
+        h.free()
+
+
 def test_stop_rules():
     g = I.grid2d(64, 64)
     for kw in [dict(max_levels=2), dict(max_levels=0), dict(min_shrink_permille=600),
