@@ -177,7 +177,8 @@ typedef enum {
     KP_PHASE_RELABEL = 3,    /* coarse ids, map, c', row bounds */
     KP_PHASE_CONTRACT = 4,   /* gather, sort, merge of coarse rows */
     KP_PHASE_CSR = 5,        /* coarse xadj scan and row compaction */
-    KP_NUM_PHASES = 6
+    KP_PHASE_TAIL = 6,       /* all remaining small levels in one launch */
+    KP_NUM_PHASES = 7
 } kp_phase;
 
 /* Per-level record of a kp_coarsen run.  Times are device milliseconds

@@ -24,7 +24,7 @@ STATUS_NAMES = ["KP_OK", "KP_ERR_INVALID", "KP_ERR_OVERFLOW", "KP_ERR_OOM", "KP_
 RATINGS = {"expansion*2": 0, "innerOuter": 1, "weight": 2, "expansion": 3, "expansion*": 4}
 MATCHERS = {"suitor": 0, "handshake": 1}
 
-PHASES = ["validate", "out", "match", "relabel", "contract", "csr"]
+PHASES = ["validate", "out", "match", "relabel", "contract", "csr", "tail"]
 
 EXPORTED = ["kp_options_default", "kp_coarsen", "kp_hierarchy_num_levels", "kp_hierarchy_level",
             "kp_hierarchy_stats", "kp_hierarchy_profile", "kp_hierarchy_free", "kp_project", "kp_cut_gain", "kp_cut_gain_noalloc", "kp_pipeline_host",
@@ -57,7 +57,7 @@ class kp_cut_gain_out(ctypes.Structure):
 
 
 class kp_level_profile(ctypes.Structure):
-    _fields_ = [("phase_ms", ctypes.c_double * 6), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+    _fields_ = [("phase_ms", ctypes.c_double * 7), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("searches", ctypes.c_int64), ("failed_cas", ctypes.c_int64), ("launches", ctypes.c_int32),
                 ("rounds", ctypes.c_int32)]
 

@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libkp.so")
-SOURCES = ["capi.cu", "coarsen.cu", "match.cu", "contract.cu", "evaluate.cu"]
-HEADERS = [os.path.join(CSRC, "kp_internal.cuh"), os.path.join(CSRC, "engine.cuh"), os.path.join(INCLUDE, "kp.h")]
+SOURCES = ["capi.cu", "coarsen.cu", "match.cu", "contract.cu", "tail.cu", "evaluate.cu"]
+HEADERS = [os.path.join(CSRC, h) for h in ("kp_internal.cuh", "engine.cuh", "match.cuh", "contract.cuh")] + [os.path.join(INCLUDE, "kp.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

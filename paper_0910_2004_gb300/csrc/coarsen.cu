@@ -20,6 +20,8 @@ namespace kp {
 namespace {
 
 constexpr int LOOKAHEAD = 2;
+// Levels with at most this many nodes run in the persistent tail launch.
+constexpr int32_t TAIL_NODES = 1 << 18;
 
 int g_coop_supported = -1;
 
@@ -219,6 +221,16 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         int32_t n_bound = start == 0 ? n0 : hs->lv[start].n;
         int64_t nnz_bound = start == 0 ? nnz0 : std::max(hs->lv[start].nnz, 1);
         for (int level = start; level < o->max_levels; level++) {
+            if (n_bound <= TAIL_NODES) {   // the rest in one persistent launch
+                timer.mark(KP_PHASE_TAIL, level);
+                const int32_t before = launches;
+                st = launch_tail(dst, w, rating, o->matcher, level, o->max_levels, n_bound, epoch, s, &launches);
+                timer.mark(-1, level);
+                if (st != KP_OK) return bail(st);
+                level_launches[(size_t)level] += launches - before;
+                epoch += 2 * (o->max_levels - level) + 2;
+                break;
+            }
             LevelLaunch LL;
             LL.st = dst;
             LL.w = w;

@@ -1,731 +1,21 @@
-// Contraction of one level (Section 2): matched pairs become one node with
-// c = c(u)+c(v), parallel edges are merged with summed omega, the contracted
-// edge disappears.  Everything is read from the device level table.
-//
-//   relabel      single-pass scan over (is representative, row bound): coarse
-//                ids, map, c', members, row offsets; its last tile carves the
-//                coarse level from the arena
-//   small rows   one thread per coarse node (<= 16 gathered entries):
-//                register bitonic network, run merge
-//   overflow     one kernel, block roles: rows <= 32 one warp (shuffle
-//                bitonic), <= 128 one warp (shared memory), <= MID_MAX one
-//                block (shared memory), longer one block (radix through global)
-//   degree scan  coarse xadj; its last tile records nnz' and decides the stop
-//                rule for the next level
-//   compaction   merged rows move to the final CSR
+// Contraction of one level (Section 2): the per-phase kernels over the
+// device functions of contract.cuh, and their launchers.
 #include <algorithm>
 
-#include "engine.cuh"
+#include "contract.cuh"
 
 namespace kp {
 
-// ---------------------------------------------------------------------------
-// relabel
-// ---------------------------------------------------------------------------
-template <bool SUITOR>
-struct RelabelOp {
-    DevState *st;
-    int level;
-    Work w;
-    // loaded by prepare()
-    int32_t n;
-    const int32_t *xadj, *vwgt;
-    int32_t *map, *cvwgt;
-
-    __device__ bool prepare() {
-        const DevLevel L = st->lv[level];
-        if (!(L.flags & LV_ACTIVE)) return false;
-        n = L.n;
-        xadj = L.xadj;
-        vwgt = L.vwgt;
-        map = L.map;
-        cvwgt = st->lv[level + 1].vwgt;
-        return true;
-    }
-    __device__ int64_t count() const { return n; }
-    __device__ int32_t *tile_counter() const { return &st->ctr[level].tile_counter[0]; }
-    __device__ void fail() const { stop_at(st, level, ERR_TIMEOUT); }
-    __device__ int32_t partner(int64_t v) const {
-        if (SUITOR) {
-            const int32_t s = w.offer[v].s;
-            return (s >= 0 && w.offer[s].s == (int32_t)v) ? s : (int32_t)v;
-        }
-        const int32_t p = w.match[v];
-        return p < 0 ? (int32_t)v : p;   // still free after a barrier gave up: single
-    }
-    __device__ uint64_t load(int64_t v) const {
-        const int32_t p = partner(v);
-        if (p < v) return 0;   // not the representative of its pair
-        int32_t ub = xadj[v + 1] - xadj[v];
-        if (p != v) ub += xadj[p + 1] - xadj[p] - 2;   // the pair's own edge is dropped
-        return (1ull << 32) | (uint32_t)ub;
-    }
-    __device__ void store(int64_t v, uint64_t excl, uint64_t val) const {
-        if (val == 0) return;
-        const int32_t x = (int32_t)(excl >> 32);
-        const int32_t p = partner(v);
-        map[v] = x;
-        w.first[x] = (int32_t)v;
-        if (p != v) {
-            map[p] = x;
-            w.second[x] = p;
-            cvwgt[x] = vwgt[v] + vwgt[p];
-        } else {
-            w.second[x] = -1;
-            cvwgt[x] = vwgt[v];
-        }
-        w.off[x] = (int32_t)(excl & 0xffffffffu);
-    }
-    // One thread: the coarse sizes are known, carve the coarse level.
-    __device__ void total(uint64_t t) const {
-        const int32_t cn = (int32_t)(t >> 32);
-        const int32_t U = (int32_t)(t & 0xffffffffu);
-        Counters *c = &st->ctr[level];
-        c->cn = cn;
-        c->U = U;
-        DevLevel *L = &st->lv[level];
-        if (cn == n) {   // nothing matched: the level is not kept
-            atomicOr(&L->flags, LV_NOMATCH);
-            stop_at(st, level, 0);
-            return;
-        }
-        const unsigned long long need_x = 4ull * ((unsigned long long)cn + 1);
-        const unsigned long long need_e = 4ull * (unsigned long long)(U > 0 ? U : 1);
-        char *px = arena_carve(st, need_x);
-        char *pa = px ? arena_carve(st, need_e) : nullptr;
-        char *pw = pa ? arena_carve(st, need_e) : nullptr;
-        char *po = (pw && st->inner_outer) ? arena_carve(st, 4ull * (unsigned long long)cn) : pw;
-        if (!po) {
-            st->overflow = level + 1;
-            stop_at(st, level, 0);
-            return;
-        }
-        DevLevel *C = &st->lv[level + 1];
-        C->n = cn;
-        C->U = U;
-        C->xadj = (int32_t *)px;
-        C->adjncy = (int32_t *)pa;
-        C->ewgt = (int32_t *)pw;
-        C->outw = st->inner_outer ? (int32_t *)po : nullptr;
-        w.off[cn] = U;
-    }
-};
-
-// ---------------------------------------------------------------------------
-// contraction view of a level, loaded from the table at kernel start
-// ---------------------------------------------------------------------------
-struct CView {
-    int32_t cn;
-    const int32_t *xadj, *adjncy, *ewgt, *map;
-    const int32_t *first, *second, *off;
-    int32_t *tmp_adj, *tmp_w, *big_adj, *big_w, *degp, *outw;
-    int32_t *const *lists;
-    Counters *ctr;
-};
-
-__device__ __forceinline__ bool load_view(DevState *st, int level, const Work &w, CView &v) {
-    const DevLevel L = st->lv[level];
-    if (!(L.flags & LV_ACTIVE)) return false;
-    v.ctr = &st->ctr[level];
-    v.cn = v.ctr->cn;
-    v.xadj = L.xadj;
-    v.adjncy = L.adjncy;
-    v.ewgt = L.ewgt;
-    v.map = L.map;
-    v.first = w.first;
-    v.second = w.second;
-    v.off = w.off;
-    v.tmp_adj = w.tmp_adj;
-    v.tmp_w = w.tmp_w;
-    v.big_adj = w.big_adj;
-    v.big_w = w.big_w;
-    v.degp = w.degp;
-    v.outw = st->lv[level + 1].outw;
-    v.lists = w.lists;
-    return true;
-}
-
-__device__ __forceinline__ void members(const CView &p, int32_t x, int32_t &xa, int32_t &da, int32_t &xb,
-                                        int32_t &db) {
-    const int32_t a = p.first[x], b = p.second[x];
-    xa = p.xadj[a];
-    da = p.xadj[a + 1] - xa;
-    xb = b >= 0 ? p.xadj[b] : 0;
-    db = b >= 0 ? p.xadj[b + 1] - xb : 0;
-}
-
-// Rows with at most 16 gathered entries: one thread.  (map(u), omega) packed
-// as (key << 32 | omega) in 16 registers, sorted by a bitonic network
-// (sentinels last), merged run by run.
-constexpr int TNET = 16;
-
-__device__ __forceinline__ void contract_thread(const CView &p, int32_t x, int32_t xa, int32_t da, int32_t xb,
-                                                int32_t db) {
-    constexpr uint64_t SENT64 = (uint64_t)SENT << 32;
-    uint64_t r[TNET];
-#pragma unroll
-    for (int i = 0; i < TNET; i++) {
-        uint64_t v = SENT64;
-        if (i < da + db) {
-            const int32_t e = i < da ? xa + i : xb + (i - da);
-            const int32_t t = p.map[p.adjncy[e]];
-            if (t != x) v = ((uint64_t)(uint32_t)t << 32) | (uint32_t)p.ewgt[e];
-        }
-        r[i] = v;
-    }
-#pragma unroll
-    for (int k = 2; k <= TNET; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-#pragma unroll
-            for (int i = 0; i < TNET; i++) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const uint64_t a = r[i], b = r[l];
-                    const bool sw = ((i & k) == 0) ? (a > b) : (a < b);
-                    r[i] = sw ? b : a;
-                    r[l] = sw ? a : b;
-                }
-            }
-        }
-    }
-    const int32_t o = p.off[x];
-    int32_t cnt = 0, curk = -1, sum = 0, total = 0;
-#pragma unroll
-    for (int i = 0; i < TNET; i++) {
-        const int32_t k = (int32_t)(r[i] >> 32);
-        const int32_t wv = (int32_t)(uint32_t)r[i];
-        if (k != SENT) {
-            total += wv;
-            if (k == curk) {
-                sum += wv;
-            } else {
-                if (curk >= 0) {
-                    p.tmp_adj[o + cnt] = curk;
-                    p.tmp_w[o + cnt] = sum;
-                    cnt++;
-                }
-                curk = k;
-                sum = wv;
-            }
-        }
-    }
-    if (curk >= 0) {
-        p.tmp_adj[o + cnt] = curk;
-        p.tmp_w[o + cnt] = sum;
-        cnt++;
-    }
-    p.degp[x] = cnt;
-    if (p.outw) p.outw[x] = total;
-}
-
 __global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_small(DevState *st, int level, Work w) {
-    CView p;
-    if (!load_view(st, level, w, p)) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t x0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); x0 < p.cn; x0 += stride) {
-        const int64_t x = x0 + lane;
-        int cls = -1;
-        int32_t da = 0, db = 0, xa = 0, xb = 0;
-        if (x < p.cn) {
-            members(p, (int32_t)x, xa, da, xb, db);
-            const int32_t L = da + db;
-            cls = L <= TNET ? 0 : L <= 32 ? 1 : L <= 128 ? 2 : L <= MID_MAX ? 3 : 4;
-        }
-#pragma unroll
-        for (int c = 1; c <= 4; c++) {
-            const bool mine = cls == c;
-            const unsigned m = __ballot_sync(0xffffffffu, mine);
-            if (m) {
-                int32_t pos = 0;
-                const int first_lane = __ffs(m) - 1;
-                if (lane == first_lane) pos = atomicAdd(&p.ctr->nclass[c], __popc(m));
-                pos = __shfl_sync(0xffffffffu, pos, first_lane);
-                if (mine) p.lists[c][pos + __popc(m & lanemask_lt())] = (int32_t)x;
-            }
-        }
-        if (cls == 0) contract_thread(p, (int32_t)x, xa, da, xb, db);
-    }
+    phase_contract_small(st, level, w);
 }
-
-// Rows of 17..32 gathered entries: one warp, bitonic sort over the lanes.
-__device__ __forceinline__ void contract_warp32(const CView &p, int32_t x) {
-    int32_t xa, da, xb, db;
-    members(p, x, xa, da, xb, db);
-    const int gl = threadIdx.x & 31;
-    const int32_t L = da + db;
-    int32_t key = SENT, val = 0;
-    if (gl < L) {
-        const int32_t e = gl < da ? xa + gl : xb + (gl - da);
-        const int32_t t = p.map[p.adjncy[e]];
-        if (t != x) {
-            key = t;
-            val = p.ewgt[e];
-        }
-    }
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const int32_t ok = __shfl_xor_sync(0xffffffffu, key, j);
-            const int32_t ov = __shfl_xor_sync(0xffffffffu, val, j);
-            const bool up = (gl & k) == 0;
-            const bool lower = (gl & j) == 0;
-            const bool take = lower ? (up ? ok < key : ok > key) : (up ? ok > key : ok < key);
-            if (take) {
-                key = ok;
-                val = ov;
-            }
-        }
-    }
-    const int32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
-    const int32_t next = __shfl_down_sync(0xffffffffu, key, 1);
-    const bool valid = key != SENT;
-    const bool head = valid && (gl == 0 || prev != key);
-    const bool tail = valid && (gl == 31 || next != key);
-    int32_t s = val;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, s, d);
-        if (gl >= d) s += y;
-    }
-    const unsigned heads = __ballot_sync(0xffffffffu, head);
-    const unsigned tails = __ballot_sync(0xffffffffu, tail);
-    const unsigned upto = (gl == 31) ? 0xffffffffu : ((2u << gl) - 1u);
-    const unsigned hb = heads & upto;
-    const int start = hb ? 31 - __clz(hb) : 0;
-    const int32_t before = __shfl_sync(0xffffffffu, s, start > 0 ? start - 1 : 0);
-    const int32_t run = s - (start > 0 ? before : 0);
-    const int32_t total = __shfl_sync(0xffffffffu, s, 31);
-    if (tail) {
-        const int32_t idx = __popc(tails & ((1u << gl) - 1u));
-        const int32_t o = p.off[x];
-        p.tmp_adj[o + idx] = key;
-        p.tmp_w[o + idx] = run;
-    }
-    if (gl == 0) {
-        p.degp[x] = __popc(tails);
-        if (p.outw) p.outw[x] = total;
-    }
-}
-
-// Rows of 33..128 gathered entries: one warp, bitonic sort of up to 128
-// (key, omega) pairs in the warp's shared memory, run indices by a warp scan
-// of the head flags, run sums by shared atomics.
-constexpr int WSORT = 128;
-
-__device__ __forceinline__ void contract_warp_smem(const CView &p, int32_t x, int32_t *K, int32_t *V, int32_t *S) {
-    const int lane = threadIdx.x & 31;
-    int32_t xa, da, xb, db;
-    members(p, x, xa, da, xb, db);
-    const int32_t L = da + db;
-    const int P = L <= 64 ? 64 : 128;
-    for (int i = lane; i < P; i += 32) {
-        int32_t key = SENT, val = 0;
-        if (i < L) {
-            const int32_t e = i < da ? xa + i : xb + (i - da);
-            const int32_t t = p.map[p.adjncy[e]];
-            if (t != x) {
-                key = t;
-                val = p.ewgt[e];
-            }
-        }
-        K[i] = key;
-        V[i] = val;
-        S[i] = 0;
-    }
-    __syncwarp();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = lane; t < P / 2; t += 32) {
-                const int i = 2 * j * (t / j) + (t % j);
-                const int l = i + j;
-                const int32_t ki = K[i], kl = K[l];
-                const bool up = (i & k) == 0;
-                if (up ? ki > kl : ki < kl) {
-                    K[i] = kl;
-                    K[l] = ki;
-                    const int32_t tv = V[i];
-                    V[i] = V[l];
-                    V[l] = tv;
-                }
-            }
-            __syncwarp();
-        }
-    }
-    const int per = P / 32;
-    const int base = lane * per;
-    int heads = 0;
-    for (int q = 0; q < per; q++) {
-        const int i = base + q;
-        heads += (K[i] != SENT && (i == 0 || K[i - 1] != K[i])) ? 1 : 0;
-    }
-    int incl = heads;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += y;
-    }
-    const int nruns = __shfl_sync(0xffffffffu, incl, 31);
-    int r = incl - heads - 1;
-    const int32_t o = p.off[x];
-    int32_t wsum = 0;
-    for (int q = 0; q < per; q++) {
-        const int i = base + q;
-        const int32_t k = K[i];
-        if (k == SENT) break;
-        if (i == 0 || K[i - 1] != k) {
-            r++;
-            p.tmp_adj[o + r] = k;
-        }
-        atomicAdd(&S[r], V[i]);
-        wsum += V[i];
-    }
-    __syncwarp();
-    for (int i = lane; i < nruns; i += 32) p.tmp_w[o + i] = S[i];
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, d);
-    if (lane == 0) {
-        p.degp[x] = nruns;
-        if (p.outw) p.outw[x] = wsum;
-    }
-    __syncwarp();
-}
-
-// Rows of 129..MID_MAX gathered entries: one block, bitonic sort in shared
-// memory, then run heads, run sums and the merged row.
-__device__ void contract_block_smem(const CView &p, int32_t x, int32_t *keys, int32_t *vals, int32_t *sums,
-                                    int32_t *s_red) {
-    constexpr int IPT = MID_MAX / CONTRACT_BLOCK;
-    int32_t xa, da, xb, db;
-    members(p, x, xa, da, xb, db);
-    const int32_t L = da + db;
-    int32_t P = 64;
-    while (P < L) P <<= 1;
-    for (int32_t i = threadIdx.x; i < P; i += blockDim.x) {
-        int32_t key = SENT, val = 0;
-        if (i < L) {
-            const int32_t e = i < da ? xa + i : xb + (i - da);
-            const int32_t t = p.map[p.adjncy[e]];
-            if (t != x) {
-                key = t;
-                val = p.ewgt[e];
-            }
-        }
-        keys[i] = key;
-        vals[i] = val;
-        sums[i] = 0;
-    }
-    __syncthreads();
-    for (int32_t k = 2; k <= P; k <<= 1) {
-        for (int32_t j = k >> 1; j > 0; j >>= 1) {
-            for (int32_t i = threadIdx.x; i < P; i += blockDim.x) {
-                const int32_t ixj = i ^ j;
-                if (ixj > i) {
-                    const bool up = (i & k) == 0;
-                    const int32_t ki = keys[i], kj = keys[ixj];
-                    if (up ? ki > kj : ki < kj) {
-                        keys[i] = kj;
-                        keys[ixj] = ki;
-                        const int32_t t = vals[i];
-                        vals[i] = vals[ixj];
-                        vals[ixj] = t;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    const int32_t base = threadIdx.x * IPT;
-    int32_t h[IPT];
-    int32_t cnt = 0;
-#pragma unroll
-    for (int j = 0; j < IPT; j++) {
-        const int32_t i = base + j;
-        h[j] = (i < P && keys[i] != SENT && (i == 0 || keys[i - 1] != keys[i])) ? 1 : 0;
-        cnt += h[j];
-    }
-    uint64_t tot;
-    int32_t r = (int32_t)block_exclusive_scan<CONTRACT_BLOCK>((uint64_t)cnt, &tot) - 1;
-    const int32_t o = p.off[x];
-    int32_t wsum = 0;
-#pragma unroll
-    for (int j = 0; j < IPT; j++) {
-        const int32_t i = base + j;
-        r += h[j];
-        if (i < P && keys[i] != SENT) {
-            atomicAdd(&sums[r], vals[i]);
-            wsum += vals[i];
-            if (h[j]) p.tmp_adj[o + r] = keys[i];
-        }
-    }
-    __syncthreads();
-    for (int32_t i = threadIdx.x; i < (int32_t)tot; i += blockDim.x) p.tmp_w[o + i] = sums[i];
-    for (int off2 = 16; off2 > 0; off2 >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off2);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = wsum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int32_t t = 0;
-        for (int wi = 0; wi < CONTRACT_BLOCK / 32; wi++) t += s_red[wi];
-        p.degp[x] = (int32_t)tot;
-        if (p.outw) p.outw[x] = t;
-    }
-    __syncthreads();
-}
-
-// Rows longer than MID_MAX gathered entries: one block.
-// 1. gather (map(u), omega) without the contracted edge into tmp at off[x]
-// 2. stable LSD radix sort by coarse neighbour, 8 bits per pass, ping-pong
-//    between tmp and big at the same offsets (an extra copy makes the number
-//    of moves odd, so the sorted row ends in big); each chunk of one element
-//    per thread is ranked with warp match masks and per-warp digit counts
-// 3. merge equal neighbours from big back into tmp (run sums by atomics)
-struct BigSmem {
-    int32_t base[256];
-    int32_t chunk_tot[256];
-    int32_t wcnt[CONTRACT_BLOCK / 32][256];
-    int32_t s_red[CONTRACT_BLOCK / 32];
-    int32_t s_carry;
-};
-
-__device__ void contract_block_radix(const CView &p, int32_t x, int passes, BigSmem &sm) {
-    constexpr int NW = CONTRACT_BLOCK / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t xa, da, xb, db;
-    members(p, x, xa, da, xb, db);
-    const int32_t L = da + db;
-    const int32_t o = p.off[x];
-    if (threadIdx.x == 0) sm.s_carry = 0;
-    __syncthreads();
-    for (int32_t c0 = 0; c0 < L; c0 += CONTRACT_BLOCK) {
-        const int32_t i = c0 + threadIdx.x;
-        int32_t t = x, wv = 0;
-        if (i < L) {
-            const int32_t e = i < da ? xa + i : xb + (i - da);
-            t = p.map[p.adjncy[e]];
-            wv = p.ewgt[e];
-        }
-        const bool keep = i < L && t != x;
-        uint64_t tot;
-        const int32_t pos = (int32_t)block_exclusive_scan<CONTRACT_BLOCK>(keep ? 1 : 0, &tot);
-        const int32_t carry = sm.s_carry;
-        if (keep) {
-            p.tmp_adj[o + carry + pos] = t;
-            p.tmp_w[o + carry + pos] = wv;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) sm.s_carry = carry + (int32_t)tot;
-        __syncthreads();
-    }
-    const int32_t M = sm.s_carry;   // == off[x+1] - off[x]
-    int32_t *src_k = p.tmp_adj + o, *src_v = p.tmp_w + o;
-    int32_t *dst_k = p.big_adj + o, *dst_v = p.big_w + o;
-    const int moves = (passes & 1) ? passes : passes + 1;
-    for (int pass = 0; pass < moves; pass++) {
-        if (pass >= passes) {
-            for (int32_t i = threadIdx.x; i < M; i += blockDim.x) {
-                dst_k[i] = src_k[i];
-                dst_v[i] = src_v[i];
-            }
-        } else {
-            const int shift = 8 * pass;
-            for (int i = threadIdx.x; i < 256; i += blockDim.x) sm.base[i] = 0;
-            __syncthreads();
-            for (int32_t i = threadIdx.x; i < M; i += blockDim.x) atomicAdd(&sm.base[(src_k[i] >> shift) & 255], 1);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int32_t run = 0;
-                for (int d = 0; d < 256; d++) {
-                    const int32_t c = sm.base[d];
-                    sm.base[d] = run;
-                    run += c;
-                }
-            }
-            __syncthreads();
-            for (int32_t c0 = 0; c0 < M; c0 += CONTRACT_BLOCK) {
-                for (int i = threadIdx.x; i < NW * 256; i += blockDim.x) (&sm.wcnt[0][0])[i] = 0;
-                __syncthreads();
-                const int32_t i = c0 + threadIdx.x;
-                const bool valid = i < M;
-                const int32_t k = valid ? src_k[i] : 0;
-                const int32_t v = valid ? src_v[i] : 0;
-                const int d = valid ? ((k >> shift) & 255) : 256 + lane;   // invalid lanes: unique
-                const unsigned peers = __match_any_sync(0xffffffffu, d);
-                const int wr = __popc(peers & lanemask_lt());
-                if (valid && wr == 0) sm.wcnt[warp][d] = __popc(peers);
-                __syncthreads();
-                if (threadIdx.x < 256) {
-                    int32_t run = 0;
-                    for (int w2 = 0; w2 < NW; w2++) {
-                        const int32_t c = sm.wcnt[w2][threadIdx.x];
-                        sm.wcnt[w2][threadIdx.x] = run;
-                        run += c;
-                    }
-                    sm.chunk_tot[threadIdx.x] = run;
-                }
-                __syncthreads();
-                if (valid) {
-                    const int32_t r = sm.base[d] + sm.wcnt[warp][d] + wr;
-                    dst_k[r] = k;
-                    dst_v[r] = v;
-                }
-                __syncthreads();
-                if (threadIdx.x < 256) sm.base[threadIdx.x] += sm.chunk_tot[threadIdx.x];
-                __syncthreads();
-            }
-        }
-        __syncthreads();
-        int32_t *tk = src_k, *tv = src_v;
-        src_k = dst_k;
-        src_v = dst_v;
-        dst_k = tk;
-        dst_v = tv;
-    }
-    // src == big now; merge into tmp
-    for (int32_t i = threadIdx.x; i < M; i += blockDim.x) p.tmp_w[o + i] = 0;
-    if (threadIdx.x == 0) sm.s_carry = 0;
-    __syncthreads();
-    int32_t wsum = 0;
-    for (int32_t c0 = 0; c0 < M; c0 += CONTRACT_BLOCK) {
-        const int32_t i = c0 + threadIdx.x;
-        const bool valid = i < M;
-        const int32_t k = valid ? src_k[i] : SENT;
-        const bool head = valid && (i == 0 || src_k[i - 1] != k);
-        uint64_t tot;
-        const int32_t pos = (int32_t)block_exclusive_scan<CONTRACT_BLOCK>(head ? 1 : 0, &tot);
-        const int32_t carry = sm.s_carry;
-        if (valid) {
-            const int32_t r = carry + pos + (head ? 1 : 0) - 1;
-            if (head) p.tmp_adj[o + r] = k;
-            atomicAdd(&p.tmp_w[o + r], src_v[i]);
-            wsum += src_v[i];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) sm.s_carry = carry + (int32_t)tot;
-        __syncthreads();
-    }
-    for (int off2 = 16; off2 > 0; off2 >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off2);
-    if (lane == 0) sm.s_red[warp] = wsum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int32_t t = 0;
-        for (int w2 = 0; w2 < NW; w2++) t += sm.s_red[w2];
-        p.degp[x] = sm.s_carry;
-        if (p.outw) p.outw[x] = t;
-    }
-    __syncthreads();
-}
-
-// All overflow classes in one launch: blocks take roles by index.
-union OverflowSmem {
-    struct {
-        int32_t K[CONTRACT_BLOCK / 32][WSORT];
-        int32_t V[CONTRACT_BLOCK / 32][WSORT];
-        int32_t S[CONTRACT_BLOCK / 32][WSORT];
-    } warp;
-    struct {
-        int32_t keys[MID_MAX];
-        int32_t vals[MID_MAX];
-        int32_t sums[MID_MAX];
-        int32_t s_red[CONTRACT_BLOCK / 32];
-    } mid;
-    BigSmem big;
-};
 
 __global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_overflow(DevState *st, int level, Work w) {
     __shared__ OverflowSmem sm;
-    CView p;
-    if (!load_view(st, level, w, p)) return;
-    const int nb = gridDim.x;
-    const int r1 = nb * 3 / 8, r2 = nb * 6 / 8, r3 = nb * 7 / 8;   // role boundaries
-    const int b = blockIdx.x;
-    const int warp = threadIdx.x >> 5;
-    constexpr int NW = CONTRACT_BLOCK / 32;
-    if (b < r2) {
-        const int cls = b < r1 ? 1 : 2;
-        const int rb = b < r1 ? b : b - r1, nrb = b < r1 ? r1 : r2 - r1;
-        const int32_t count = p.ctr->nclass[cls];
-        for (int64_t li = (int64_t)rb * NW + warp; li < count; li += (int64_t)nrb * NW) {
-            const int32_t x = p.lists[cls][li];
-            if (cls == 1) contract_warp32(p, x);
-            else contract_warp_smem(p, x, sm.warp.K[warp], sm.warp.V[warp], sm.warp.S[warp]);
-        }
-    } else if (b < r3) {
-        const int32_t count = p.ctr->nclass[3];
-        for (int32_t li = b - r2; li < count; li += r3 - r2)
-            contract_block_smem(p, p.lists[3][li], sm.mid.keys, sm.mid.vals, sm.mid.sums, sm.mid.s_red);
-    } else {
-        const int32_t count = p.ctr->nclass[4];
-        if (count == 0) return;
-        int bits = 1;
-        while (bits < 31 && ((int64_t)1 << bits) < (int64_t)p.cn) bits++;
-        const int passes = (bits + 7) / 8;
-        for (int32_t li = b - r3; li < count; li += nb - r3) contract_block_radix(p, p.lists[4][li], passes, sm.big);
-    }
+    phase_contract_overflow(st, level, w, sm);
 }
 
-// ---------------------------------------------------------------------------
-// coarse xadj and the stop rule
-// ---------------------------------------------------------------------------
-struct DegScanOp {
-    DevState *st;
-    int level;
-    Work w;
-    int32_t cn;
-    int32_t *cxadj;
-
-    __device__ bool prepare() {
-        if (!(st->lv[level].flags & LV_ACTIVE)) return false;
-        cn = st->ctr[level].cn;
-        cxadj = st->lv[level + 1].xadj;
-        return true;
-    }
-    __device__ int64_t count() const { return cn; }
-    __device__ int32_t *tile_counter() const { return &st->ctr[level].tile_counter[1]; }
-    __device__ void fail() const { stop_at(st, level, ERR_TIMEOUT); }
-    __device__ uint64_t load(int64_t x) const { return (uint64_t)(uint32_t)w.degp[x]; }
-    __device__ void store(int64_t x, uint64_t excl, uint64_t) const { cxadj[x] = (int32_t)excl; }
-    // One thread: record nnz' and decide whether level+1 is contracted
-    // (stop when small enough, after too little shrinkage, or at the level cap).
-    __device__ void total(uint64_t t) const {
-        cxadj[cn] = (int32_t)t;
-        st->ctr[level].nnz_out = (int32_t)t;
-        DevLevel *C = &st->lv[level + 1];
-        C->nnz = (int32_t)t;
-        const int64_t n = st->lv[level].n;
-        const bool small = cn <= st->stop_size;
-        const bool capped = level + 1 >= st->max_levels;
-        const bool stalled = (int64_t)cn * 1000 > n * (1000 - st->min_shrink_permille);
-        const bool next = !(small || capped || stalled || st->stop || st->err);
-        C->flags = LV_BUILT | (next ? LV_ACTIVE : 0);
-        if (!next) st->stop = 1;
-        volatile LevelSnap *s = st->snap + level;
-        s->cn = cn;
-        s->nnz = (int32_t)t;
-        s->stop = next ? 0 : 1;
-        s->done = 1;
-    }
-};
-
-// Moves every merged coarse row from its upper-bound slot to the CSR.
-__global__ void k_compact(DevState *st, int level, Work w) {
-    if (!(st->lv[level].flags & LV_ACTIVE)) return;
-    const int32_t cn = st->ctr[level].cn;
-    const int32_t *__restrict__ cxadj = st->lv[level + 1].xadj;
-    int32_t *__restrict__ cadj = st->lv[level + 1].adjncy;
-    int32_t *__restrict__ cw = st->lv[level + 1].ewgt;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int gl = threadIdx.x & 7;
-    for (int64_t g = t >> 3; g < cn; g += stride >> 3) {
-        const int32_t o = w.off[g], d = w.degp[g], s = cxadj[g];
-        for (int32_t i = gl; i < d; i += 8) {
-            cadj[s + i] = w.tmp_adj[o + i];
-            cw[s + i] = w.tmp_w[o + i];
-        }
-    }
-}
+__global__ void k_compact(DevState *st, int level, Work w) { phase_compact(st, level, w); }
 
 // ---------------------------------------------------------------------------
 // launchers

@@ -64,6 +64,7 @@ struct DevState {
     int32_t err;        // ERR_TIMEOUT from a bounded wait
     int32_t pad;
     LevelSnap *snap;    // host-mapped, one per level
+    GridBarrier tail_bar;
 };
 
 // Ends the loop: the level is not contracted further and the host is told.
@@ -199,24 +200,25 @@ __device__ __forceinline__ char *arena_carve(DevState *st, unsigned long long by
 // Tiles are taken in order from a counter, so every tile's predecessors are
 // held by running blocks; each wait for a predecessor is bounded.
 // ---------------------------------------------------------------------------
+// Returns false when a look-back wait gave up (op.fail() has been called).
 template <class Op>
-__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_lb(Op op, TileStatus *status, int32_t epoch,
-                                                        long long spin_limit) {
+__device__ bool scan_lb_phase(Op &op, TileStatus *status, int32_t epoch, long long spin_limit) {
     __shared__ int64_t s_tile;
     __shared__ unsigned long long s_prefix;
     __shared__ int s_abort;
-    if (!op.prepare()) return;
+    if (!op.prepare()) return true;
     const int64_t count = op.count();
     const int64_t tiles = (count + SCAN_TILE - 1) / SCAN_TILE;
     if (tiles == 0) {
         if (blockIdx.x == 0 && threadIdx.x == 0) op.total(0);
-        return;
+        return true;
     }
     int32_t *counter = op.tile_counter();
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1);
         __syncthreads();
         const int64_t tile = s_tile;
+        __syncthreads();
         if (tile >= tiles) break;
         const int64_t base = tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
         uint64_t v[SCAN_ITEMS];
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scan_lb(Op op, TileStatus *statu
             else if (tile == tiles - 1) op.total(prefix + total);
         }
         __syncthreads();
-        if (s_abort) return;
+        if (s_abort) return false;
         uint64_t p = s_prefix + excl;
 #pragma unroll
         for (int j = 0; j < SCAN_ITEMS; j++) {
@@ -275,6 +277,13 @@ __global__ void __launch_bounds__(SCAN_BLOCK) k_scan_lb(Op op, TileStatus *statu
         }
         __syncthreads();
     }
+    return true;
+}
+
+template <class Op>
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_lb(Op op, TileStatus *status, int32_t epoch,
+                                                        long long spin_limit) {
+    scan_lb_phase(op, status, epoch, spin_limit);
 }
 
 // ---------------------------------------------------------------------------
@@ -297,5 +306,7 @@ kp_status launch_matching(const LevelLaunch &L, cudaStream_t s, int32_t *launche
 kp_status launch_relabel(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
 kp_status launch_contract(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
 kp_status launch_csr(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
+kp_status launch_tail(DevState *st, const Work &w, int rating, int matcher, int first, int last, int32_t n_bound,
+                      int32_t epoch0, cudaStream_t s, int32_t *launches);
 
 }  // namespace kp

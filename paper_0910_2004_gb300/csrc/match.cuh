@@ -1,0 +1,415 @@
+// Matching of locally heaviest edges (Section 3.3) on one level, read from
+// the device level table.  Two schemes reach the same unique matching (the
+// Greedy matching of Section 3.2 under the strict edge order):
+//   proposals (Suitor scheme, Manne & Halappanavar 2014): every node proposes
+//     to its best neighbour whose standing offer it beats, displaced
+//     proposers propose again; one 128-bit CAS per proposal, no rounds;
+//   handshake rounds: every free node names its best free neighbour, mutual
+//     names are matched, repeated until no edge has two free ends; one
+//     cooperative launch, rounds separated by bounded grid barriers.
+#pragma once
+
+#include "engine.cuh"
+
+namespace kp {
+
+// ---------------------------------------------------------------------------
+// level begin: carve map_l and c of level l+1, reset the per-node state
+// ---------------------------------------------------------------------------
+template <int R, bool SUITOR>
+__device__ void phase_level_begin(DevState *st, int level, const Work &w) {
+    const DevLevel L = st->lv[level];
+    if (!(L.flags & LV_ACTIVE)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int32_t *map = (int32_t *)arena_carve(st, 4ull * (unsigned long long)L.n);
+        int32_t *cv = map ? (int32_t *)arena_carve(st, 4ull * (unsigned long long)L.n) : nullptr;
+        if (!map || !cv) {
+            st->overflow = level + 1;
+            stop_at(st, level, 0);
+        } else {
+            st->lv[level].map = map;
+            st->lv[level + 1].vwgt = cv;
+        }
+    }
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < L.n; v += stride) {
+        if (SUITOR) {
+            Offer o;
+            o.s = -1;
+            o.w = 0;
+            o.as = 0;
+            o.au = rating_attr<R>(L.vwgt, L.outw, (int32_t)v);
+            w.offer[v] = o;
+        } else {
+            w.match[v] = -1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// proposals
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ Offer ld_offer(const Offer *p) {
+    Offer o;
+    asm volatile("ld.global.cg.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(o.s), "=r"(o.w), "=r"(o.as), "=r"(o.au)
+                 : "l"(p)
+                 : "memory");
+    return o;
+}
+
+__device__ __forceinline__ bool cas_offer(Offer *addr, const Offer &expect, const Offer &desired) {
+    const uint64_t elo = ((uint64_t)(uint32_t)expect.w << 32) | (uint32_t)expect.s;
+    const uint64_t ehi = ((uint64_t)(uint32_t)expect.au << 32) | (uint32_t)expect.as;
+    const uint64_t dlo = ((uint64_t)(uint32_t)desired.w << 32) | (uint32_t)desired.s;
+    const uint64_t dhi = ((uint64_t)(uint32_t)desired.au << 32) | (uint32_t)desired.as;
+    uint64_t olo, ohi;
+    asm volatile(
+        "{\n\t.reg .b128 e, d, o;\n\t"
+        "mov.b128 e, {%2, %3};\n\t"
+        "mov.b128 d, {%4, %5};\n\t"
+        "atom.global.cas.b128 o, [%6], e, d;\n\t"
+        "mov.b128 {%0, %1}, o;\n\t}"
+        : "=l"(olo), "=l"(ohi)
+        : "l"(elo), "l"(ehi), "l"(dlo), "l"(dhi), "l"(addr)
+        : "memory");
+    return olo == elo && ohi == ehi;
+}
+
+// Lanes per proposing node from the level's mean degree, and the row length
+// above which a node is left to the wide (one warp per node) pass.
+__device__ __forceinline__ int suitor_group(int32_t n, int32_t nnz) {
+    const int64_t a = n > 0 ? (int64_t)nnz : 0;
+    if (a <= 12ll * n) return 1;
+    if (a <= 40ll * n) return 4;
+    if (a <= 160ll * n) return 8;
+    return 32;
+}
+
+// G lanes per proposing node.  Start nodes are [0, n) (FROM_LIST = false)
+// or the parked list (FROM_LIST = true).  Every warp owns one contiguous range
+// of start nodes; its 32/G groups each follow one proposal chain (a node,
+// then whoever it displaced) and take the next start node of the range as
+// soon as their chain ends, so lanes stay busy until the range is used up.
+// With HEAVY > 0 a node whose row is longer than HEAVY entries is parked
+// instead of being scanned by so few lanes; the FROM_LIST pass (G = 32)
+// finishes those.  The order of proposals does not change the matching.
+template <int R, int G, int HEAVY, bool FROM_LIST>
+__device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Counters *ctr, int32_t *err) {
+    constexpr int NG = 32 / G;
+    const unsigned gmask = group_mask<G>();
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (G - 1);
+    const int leader = lane & ~(G - 1);
+    const unsigned below_leader = (1u << leader) - 1u;
+    const int32_t *__restrict__ xadj = L.xadj;
+    const int32_t *__restrict__ adjncy = L.adjncy;
+    const int32_t *__restrict__ ewgt = L.ewgt;
+    int32_t *parked = w.list0;
+    int32_t *parked_size = &ctr->list_size[0];
+    const int64_t count = FROM_LIST ? (int64_t)ld_relaxed_i32(parked_size) : (int64_t)L.n;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t chunk = (count + nwarps - 1) / nwarps;
+    int64_t pos = warp_id * chunk;
+    const int64_t stop = min(count, pos + chunk);
+    long long iters = 0;
+    unsigned long long fails = 0;
+    int32_t cur = -1;
+    bool aborted = false;
+    for (;;) {
+        // the whole warp leaves together (full-warp votes follow)
+        if (__any_sync(0xffffffffu, aborted)) break;
+        // give every idle group the next start node of the warp's range
+        const unsigned need = __ballot_sync(0xffffffffu, cur < 0 && gl == 0);
+        if (need && pos < stop) {
+            const int64_t avail = min((int64_t)NG, stop - pos);
+            const int rank = __popc(need & below_leader);
+            if (cur < 0 && rank < avail) cur = FROM_LIST ? parked[pos + rank] : (int32_t)(pos + rank);
+            pos += min((int64_t)__popc(need), avail);
+        }
+        if (__ballot_sync(0xffffffffu, cur >= 0) == 0) break;
+        if (cur < 0) continue;
+        if (++iters > w.spin_limit) {   // a bound, not a wait: report instead of looping on
+            if (gl == 0) atomicOr(err, ERR_TIMEOUT);
+            cur = -1;
+            aborted = true;
+            continue;
+        }
+        const int32_t beg = __ldg(xadj + cur), end = __ldg(xadj + cur + 1);
+        if (HEAVY > 0 && end - beg > HEAVY) {   // park it for the wide pass
+            if (gl == 0) parked[atomicAdd(parked_size, 1)] = cur;
+            cur = -1;
+            continue;
+        }
+        const int32_t acur = rating_attr<R>(L.vwgt, L.outw, cur);
+        Cand best;
+        best.u = -1;
+        best.num = best.den = best.h = 0;
+        int32_t bw = 0;
+        Offer bsnap = {-1, 0, 0, 0};
+#pragma unroll 4
+        for (int32_t e = beg + gl; e < end; e += G) {
+            const int32_t v = __ldg(adjncy + e);
+            const int32_t wt = __ldg(ewgt + e);
+            const Offer st = ld_offer(w.offer + v);
+            Cand c;
+            c.u = v;
+            rating_ab<R>(wt, acur, st.au, c.num, c.den);
+            c.h = edge_hash(w.seed, cur, v);
+            bool eligible = st.s < 0;
+            if (!eligible) {
+                // compare at v: the offer of cur against the standing offer of st.s
+                Cand a, b;
+                a.u = cur;
+                a.num = c.num;
+                a.den = c.den;
+                a.h = c.h;
+                b.u = st.s;
+                rating_ab<R>(st.w, st.as, st.au, b.num, b.den);
+                b.h = edge_hash(w.seed, st.s, v);
+                eligible = better(a, b, v);
+            }
+            if (eligible && better(c, best, cur)) {
+                best = c;
+                bw = wt;
+                bsnap = st;
+            }
+        }
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) {
+            Cand o;
+            o.num = __shfl_xor_sync(gmask, best.num, off);
+            o.den = __shfl_xor_sync(gmask, best.den, off);
+            o.h = __shfl_xor_sync(gmask, best.h, off);
+            o.u = __shfl_xor_sync(gmask, best.u, off);
+            const int32_t ow = __shfl_xor_sync(gmask, bw, off);
+            Offer os;
+            os.s = __shfl_xor_sync(gmask, bsnap.s, off);
+            os.w = __shfl_xor_sync(gmask, bsnap.w, off);
+            os.as = __shfl_xor_sync(gmask, bsnap.as, off);
+            os.au = __shfl_xor_sync(gmask, bsnap.au, off);
+            if (better(o, best, cur)) {
+                best = o;
+                bw = ow;
+                bsnap = os;
+            }
+        }
+        int32_t next = -1;
+        if (best.u >= 0 && gl == 0) {
+            Offer mine;
+            mine.s = cur;
+            mine.w = bw;
+            mine.as = acur;
+            mine.au = bsnap.au;
+            // success: the displaced suitor (if any) proposes next;
+            // failure: the record changed under us, so cur searches again
+            if (cas_offer(w.offer + best.u, bsnap, mine)) {
+                next = bsnap.s;
+            } else {
+                next = cur;
+                fails++;
+            }
+        }
+        cur = __shfl_sync(gmask, next, leader);
+    }
+    if (gl == 0) {
+        atomicAdd(&ctr->searches, (unsigned long long)iters);
+        if (fails) atomicAdd(&ctr->failed_cas, fails);
+    }
+}
+
+template <int R, bool FROM_LIST>
+__device__ void phase_suitor(DevState *st, int level, const Work &w) {
+    const DevLevel L = st->lv[level];
+    if (!(L.flags & LV_ACTIVE)) return;
+    Counters *ctr = &st->ctr[level];
+    if (FROM_LIST) {
+        suitor_body<R, 32, 0, true>(L, w, ctr, &st->err);
+    } else {
+        switch (suitor_group(L.n, L.nnz)) {
+        case 1: suitor_body<R, 1, 32, false>(L, w, ctr, &st->err); break;
+        case 4: suitor_body<R, 4, 128, false>(L, w, ctr, &st->err); break;
+        case 8: suitor_body<R, 8, 512, false>(L, w, ctr, &st->err); break;
+        default: suitor_body<R, 32, 0, false>(L, w, ctr, &st->err); break;
+        }
+    }
+    // a proposal chain that ran out ends the coarsening after this level (the
+    // offers stay consistent, so the level's own contraction is safe)
+    if (threadIdx.x == 0 && ld_relaxed_i32(&st->err) != 0) st->stop = 1;
+}
+
+// ---------------------------------------------------------------------------
+// handshake rounds
+// ---------------------------------------------------------------------------
+// Rates node v: its best free neighbour under the strict order, or marks v
+// single when it has no free neighbour.  With recheck, v is only re-rated if
+// its previous candidate has been matched meanwhile (the set of free
+// neighbours only shrinks, so a still-free candidate stays the best).
+template <int R, int G>
+__device__ __forceinline__ void rate_node(const DevLevel &L, const Work &w, Counters *ctr, int32_t v, bool recheck) {
+    const unsigned gmask = group_mask<G>();
+    const int gl = threadIdx.x & (G - 1);
+    const int leader = (threadIdx.x & 31) & ~(G - 1);
+    int need = 0;
+    if (gl == 0) {
+        if (w.match[v] == -1) {
+            if (!recheck) {
+                need = 1;
+            } else {
+                const int32_t c = w.cand[v];
+                need = (c < 0 || w.match[c] != -1) ? 1 : 0;
+            }
+        }
+    }
+    need = __shfl_sync(gmask, need, leader);
+    if (!need) return;
+    if (gl == 0) atomicAdd(&ctr->searches, 1ull);
+    const int32_t beg = __ldg(L.xadj + v), end = __ldg(L.xadj + v + 1);
+    const int32_t av = rating_attr<R>(L.vwgt, L.outw, v);
+    Cand best;
+    best.u = -1;
+    best.num = best.den = best.h = 0;
+    for (int32_t e = beg + gl; e < end; e += G) {
+        const int32_t u = __ldg(L.adjncy + e);
+        if (w.match[u] != -1) continue;
+        Cand c;
+        c.u = u;
+        rating_ab<R>(__ldg(L.ewgt + e), av, rating_attr<R>(L.vwgt, L.outw, u), c.num, c.den);
+        c.h = edge_hash(w.seed, v, u);
+        if (better(c, best, v)) best = c;
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        Cand o;
+        o.num = __shfl_xor_sync(gmask, best.num, off);
+        o.den = __shfl_xor_sync(gmask, best.den, off);
+        o.h = __shfl_xor_sync(gmask, best.h, off);
+        o.u = __shfl_xor_sync(gmask, best.u, off);
+        if (better(o, best, v)) best = o;
+    }
+    if (gl == 0) {
+        if (best.u < 0) {
+            w.match[v] = v;   // no free neighbour: stays single (nobody reads it this phase)
+            w.cand[v] = -1;
+        } else {
+            w.cand[v] = best.u;
+        }
+    }
+}
+
+template <int R, int G>
+__device__ void rate_phase(const DevLevel &L, const Work &w, Counters *ctr, const int32_t *lst, int64_t cnt,
+                           bool recheck) {
+    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+    for (int64_t i = gid; i < cnt; i += ngroups) rate_node<R, G>(L, w, ctr, lst ? lst[i] : (int32_t)i, recheck);
+}
+
+template <int R>
+__device__ void rate_phase_any(int G, const DevLevel &L, const Work &w, Counters *ctr, const int32_t *lst,
+                               int64_t cnt, bool recheck) {
+    switch (G) {
+    case 1: rate_phase<R, 1>(L, w, ctr, lst, cnt, recheck); break;
+    case 4: rate_phase<R, 4>(L, w, ctr, lst, cnt, recheck); break;
+    case 8: rate_phase<R, 8>(L, w, ctr, lst, cnt, recheck); break;
+    case 16: rate_phase<R, 16>(L, w, ctr, lst, cnt, recheck); break;
+    default: rate_phase<R, 32>(L, w, ctr, lst, cnt, recheck); break;
+    }
+}
+
+// Handshake: v is matched when its candidate names v too; otherwise it goes
+// to the next round's list.  Warp-uniform loop; appends are warp-aggregated.
+__device__ __forceinline__ void hand_phase(const Work &w, const int32_t *lst, int64_t cnt, int32_t *next,
+                                           int32_t *next_size) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < cnt; base += nthreads) {
+        const int64_t i = base + lane;
+        bool keep = false;
+        int32_t v = -1;
+        if (i < cnt) {
+            v = lst ? lst[i] : (int32_t)i;
+            if (w.match[v] == -1) {
+                const int32_t c = w.cand[v];
+                if (c >= 0 && w.cand[c] == v) w.match[v] = c;
+                else keep = true;
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (m) {
+            int32_t pos = 0;
+            if (lane == 0) pos = atomicAdd(next_size, __popc(m));
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (keep) next[pos + __popc(m & lanemask_lt())] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ int handshake_group(int32_t n, int32_t nnz) {
+    const int64_t a = n > 0 ? (int64_t)nnz : 0;
+    if (a <= 3ll * n) return 1;
+    if (a <= 6ll * n) return 8;
+    if (a <= 14ll * n) return 16;
+    return 32;
+}
+
+// Returns false when a grid barrier gave up (the caller must leave too).
+template <int R>
+__device__ bool phase_handshake(DevState *st, int level, const Work &w) {
+    const DevLevel L = st->lv[level];
+    if (!(L.flags & LV_ACTIVE)) return true;
+    Counters *ctr = &st->ctr[level];
+    const int G = handshake_group(L.n, L.nnz);
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr->rounds = 1;
+    // a barrier that gives up ends the coarsening; nodes still free then count
+    // as single in the relabel, so the level's own contraction stays safe
+    auto give_up = [&]() {
+        if (threadIdx.x == 0) {
+            atomicOr(&st->err, ERR_TIMEOUT);
+            st->stop = 1;
+        }
+        return false;
+    };
+    rate_phase_any<R>(G, L, w, ctr, nullptr, L.n, false);
+    if (!grid_sync(&ctr->bar, &ctr->err, w.spin_limit)) return give_up();
+    hand_phase(w, nullptr, L.n, w.list0, &ctr->list_size[0]);
+    if (!grid_sync(&ctr->bar, &ctr->err, w.spin_limit)) return give_up();
+    int cur = 0;
+    for (;;) {
+        const int32_t cnt = ld_relaxed_i32(&ctr->list_size[cur]);
+        if (cnt == 0) break;
+        const int32_t *lst = cur ? w.list1 : w.list0;
+        int32_t *nxt = cur ? w.list0 : w.list1;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctr->list_size[cur ^ 1] = 0;
+            ctr->rounds += 1;
+        }
+        rate_phase_any<R>(G, L, w, ctr, lst, cnt, true);
+        if (!grid_sync(&ctr->bar, &ctr->err, w.spin_limit)) return give_up();
+        hand_phase(w, lst, cnt, nxt, &ctr->list_size[cur ^ 1]);
+        if (!grid_sync(&ctr->bar, &ctr->err, w.spin_limit)) return give_up();
+        cur ^= 1;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// standalone kernels (one launch per phase)
+// ---------------------------------------------------------------------------
+template <int R, bool SUITOR>
+__global__ void k_level_begin(DevState *st, int level, Work w) {
+    phase_level_begin<R, SUITOR>(st, level, w);
+}
+
+template <int R, bool FROM_LIST>
+__global__ void __launch_bounds__(MATCH_BLOCK) k_suitor(DevState *st, int level, Work w) {
+    phase_suitor<R, FROM_LIST>(st, level, w);
+}
+
+template <int R>
+__global__ void __launch_bounds__(MATCH_BLOCK) k_match(DevState *st, int level, Work w) {
+    phase_handshake<R>(st, level, w);
+}
+
+}  // namespace kp
