@@ -19,6 +19,9 @@ LIB = os.path.join(OUT, "libkp.so")
 SOURCES = ["capi.cu", "coarsen.cu", "match.cu", "contract.cu", "tail.cu", "evaluate.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("kp_internal.cuh", "engine.cuh", "match.cuh", "contract.cuh")] + [os.path.join(INCLUDE, "kp.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The persistent tail kernel reads data written earlier in the same launch by
+# other blocks: its unit serves every global load from L2 (coherent).
+PER_FILE = {"tail.cu": ["-Xptxas", "-dlcm=cg", "-DKP_COHERENT_LOADS"]}
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
 
@@ -45,7 +48,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         o = os.path.join(OUT, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + HEADERS):
-            jobs.append([nvcc] + FLAGS + list(extra_flags) + ["-c", s, "-o", o])
+            jobs.append([nvcc] + FLAGS + PER_FILE.get(src, []) + list(extra_flags) + ["-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

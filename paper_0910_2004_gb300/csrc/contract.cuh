@@ -711,9 +711,9 @@ struct DegScanOp {
 static __device__ void phase_compact(DevState *st, int level, const Work &w) {
     if (!(st->lv[level].flags & LV_ACTIVE)) return;
     const int32_t cn = st->ctr[level].cn;
-    const int32_t *__restrict__ cxadj = st->lv[level + 1].xadj;
-    int32_t *__restrict__ cadj = st->lv[level + 1].adjncy;
-    int32_t *__restrict__ cw = st->lv[level + 1].ewgt;
+    const int32_t *KP_RESTRICT cxadj = st->lv[level + 1].xadj;
+    int32_t *KP_RESTRICT cadj = st->lv[level + 1].adjncy;
+    int32_t *KP_RESTRICT cw = st->lv[level + 1].ewgt;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int gl = threadIdx.x & 7;

@@ -11,6 +11,18 @@
 
 #include "kp_internal.cuh"
 
+// Read-only loads.  A persistent launch (the tail kernel) reads data that
+// other blocks wrote earlier in the same launch, so its translation unit
+// defines KP_COHERENT_LOADS: no read-only cache path, no __restrict__
+// aliasing promises, and (with -dlcm=cg) every global load served from L2.
+#ifdef KP_COHERENT_LOADS
+#define KP_LDG(p) (*(p))
+#define KP_RESTRICT
+#else
+#define KP_LDG(p) __ldg(p)
+#define KP_RESTRICT __restrict__
+#endif
+
 namespace kp {
 
 constexpr int32_t SENT = 0x7fffffff;   // sorts after every node id

@@ -102,9 +102,9 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
     const int gl = lane & (G - 1);
     const int leader = lane & ~(G - 1);
     const unsigned below_leader = (1u << leader) - 1u;
-    const int32_t *__restrict__ xadj = L.xadj;
-    const int32_t *__restrict__ adjncy = L.adjncy;
-    const int32_t *__restrict__ ewgt = L.ewgt;
+    const int32_t *KP_RESTRICT xadj = L.xadj;
+    const int32_t *KP_RESTRICT adjncy = L.adjncy;
+    const int32_t *KP_RESTRICT ewgt = L.ewgt;
     int32_t *parked = w.list0;
     int32_t *parked_size = &ctr->list_size[0];
     const int64_t count = FROM_LIST ? (int64_t)ld_relaxed_i32(parked_size) : (int64_t)L.n;
@@ -136,7 +136,7 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
             aborted = true;
             continue;
         }
-        const int32_t beg = __ldg(xadj + cur), end = __ldg(xadj + cur + 1);
+        const int32_t beg = KP_LDG(xadj + cur), end = KP_LDG(xadj + cur + 1);
         if (HEAVY > 0 && end - beg > HEAVY) {   // park it for the wide pass
             if (gl == 0) parked[atomicAdd(parked_size, 1)] = cur;
             cur = -1;
@@ -150,8 +150,8 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
         Offer bsnap = {-1, 0, 0, 0};
 #pragma unroll 4
         for (int32_t e = beg + gl; e < end; e += G) {
-            const int32_t v = __ldg(adjncy + e);
-            const int32_t wt = __ldg(ewgt + e);
+            const int32_t v = KP_LDG(adjncy + e);
+            const int32_t wt = KP_LDG(ewgt + e);
             const Offer st = ld_offer(w.offer + v);
             Cand c;
             c.u = v;
@@ -265,17 +265,17 @@ __device__ __forceinline__ void rate_node(const DevLevel &L, const Work &w, Coun
     need = __shfl_sync(gmask, need, leader);
     if (!need) return;
     if (gl == 0) atomicAdd(&ctr->searches, 1ull);
-    const int32_t beg = __ldg(L.xadj + v), end = __ldg(L.xadj + v + 1);
+    const int32_t beg = KP_LDG(L.xadj + v), end = KP_LDG(L.xadj + v + 1);
     const int32_t av = rating_attr<R>(L.vwgt, L.outw, v);
     Cand best;
     best.u = -1;
     best.num = best.den = best.h = 0;
     for (int32_t e = beg + gl; e < end; e += G) {
-        const int32_t u = __ldg(L.adjncy + e);
+        const int32_t u = KP_LDG(L.adjncy + e);
         if (w.match[u] != -1) continue;
         Cand c;
         c.u = u;
-        rating_ab<R>(__ldg(L.ewgt + e), av, rating_attr<R>(L.vwgt, L.outw, u), c.num, c.den);
+        rating_ab<R>(KP_LDG(L.ewgt + e), av, rating_attr<R>(L.vwgt, L.outw, u), c.num, c.den);
         c.h = edge_hash(w.seed, v, u);
         if (better(c, best, v)) best = c;
     }

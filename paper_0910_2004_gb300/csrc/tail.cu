@@ -7,6 +7,9 @@
 // arena full, or a bounded wait that gave up).
 #include <algorithm>
 
+#ifndef KP_COHERENT_LOADS
+#error "tail.cu must be compiled with -DKP_COHERENT_LOADS and -Xptxas -dlcm=cg"
+#endif
 #include "contract.cuh"
 #include "match.cuh"
 
