@@ -115,7 +115,10 @@ typedef enum {
  *                        found; both give the same unique matching
  *   arena_bytes          initial size of the device arena that holds the
  *                        coarse levels (0: sized from the input); the
- *                        arena grows automatically when a level does not fit */
+ *                        arena grows automatically when a level does not fit
+ *   tail_nodes           levels with at most this many nodes are contracted
+ *                        together in one persistent launch (0: 262144;
+ *                        -1: never); results do not depend on it */
 typedef struct {
     int32_t rating;
     uint64_t seed;
@@ -127,11 +130,12 @@ typedef struct {
     int32_t profile;
     int32_t matcher;
     int64_t arena_bytes;
+    int32_t tail_nodes;
 } kp_options;
 
 /* Fills *o with the defaults: EXPANSION_STAR2, seed 1, stop_size 40,
  * max_levels 64, min_shrink_permille 50, spin_limit 1<<22, validate 1,
- * profile 0, matcher SUITOR, arena_bytes 0. */
+ * profile 0, matcher SUITOR, arena_bytes 0, tail_nodes 0. */
 void kp_options_default(kp_options *o);
 
 /* A hierarchy of graphs G_0 (the input) .. G_L (the coarsest) with the maps

@@ -47,7 +47,7 @@ class kp_options(ctypes.Structure):
     _fields_ = [("rating", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stop_size", ctypes.c_int32),
                 ("max_levels", ctypes.c_int32), ("min_shrink_permille", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("validate", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("matcher", ctypes.c_int32), ("arena_bytes", ctypes.c_int64)]
+                ("matcher", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("tail_nodes", ctypes.c_int32)]
 
 
 class kp_cut_gain_out(ctypes.Structure):
@@ -255,7 +255,7 @@ class DeviceGraph:
 
 def make_options(rating="expansion*2", seed=1, stop_size=40, max_levels=64, min_shrink_permille=50,
                  spin_limit=1 << 22, validate=True, profile=False, matcher="suitor",
-                 arena_bytes=0) -> kp_options:
+                 arena_bytes=0, tail_nodes=0) -> kp_options:
     o = kp_options_default()
     o.rating = RATINGS[rating] if isinstance(rating, str) else int(rating)
     o.seed = seed
@@ -267,6 +267,7 @@ def make_options(rating="expansion*2", seed=1, stop_size=40, max_levels=64, min_
     o.profile = 1 if profile else 0
     o.matcher = MATCHERS[matcher] if isinstance(matcher, str) else int(matcher)
     o.arena_bytes = arena_bytes
+    o.tail_nodes = tail_nodes
     return o
 
 

@@ -207,6 +207,7 @@ void kp_options_default(kp_options *o) {
     o->profile = 0;
     o->matcher = KP_MATCHER_SUITOR;
     o->arena_bytes = 0;
+    o->tail_nodes = 0;
 }
 
 kp_status kp_coarsen(const kp_graph *g, const kp_options *o, kp_stream s, kp_hierarchy **out) {

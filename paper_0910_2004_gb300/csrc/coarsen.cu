@@ -20,7 +20,8 @@ namespace kp {
 namespace {
 
 constexpr int LOOKAHEAD = 2;
-// Levels with at most this many nodes run in the persistent tail launch.
+// Levels with at most this many nodes run in the persistent tail launch
+// (default of kp_options.tail_nodes).
 constexpr int32_t TAIL_NODES = 1 << 18;
 
 int g_coop_supported = -1;
@@ -72,7 +73,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     if (g->n > 0 && (!g->xadj || !g->vwgt || (g->nnz > 0 && (!g->adjncy || !g->ewgt))))
         return set_error(KP_ERR_INVALID, "null graph array");
     if (o->max_levels < 0 || o->max_levels > MAX_LEVELS - 8 || o->min_shrink_permille < 0 ||
-        o->min_shrink_permille > 1000 || o->spin_limit <= 0 || o->arena_bytes < 0)
+        o->min_shrink_permille > 1000 || o->spin_limit <= 0 || o->arena_bytes < 0 || o->tail_nodes < -1)
         return set_error(KP_ERR_INVALID, "bad option value");
     if (o->matcher == KP_MATCHER_HANDSHAKE) {
         if (g_coop_supported < 0) {
@@ -206,6 +207,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         if (st != KP_OK) return fail(st);
     }
 
+    const int32_t tail_nodes = o->tail_nodes == 0 ? TAIL_NODES : o->tail_nodes;   // -1: never
     int32_t epoch = 0;
     int start = 0;
     std::vector<int32_t> level_launches(MAX_LEVELS, 0);
@@ -221,7 +223,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         int32_t n_bound = start == 0 ? n0 : hs->lv[start].n;
         int64_t nnz_bound = start == 0 ? nnz0 : std::max(hs->lv[start].nnz, 1);
         for (int level = start; level < o->max_levels; level++) {
-            if (n_bound <= TAIL_NODES) {   // the rest in one persistent launch
+            if (n_bound <= tail_nodes) {   // the rest in one persistent launch
                 timer.mark(KP_PHASE_TAIL, level);
                 const int32_t before = launches;
                 st = launch_tail(dst, w, rating, o->matcher, level, o->max_levels, n_bound, epoch, s, &launches);

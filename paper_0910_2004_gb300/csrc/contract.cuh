@@ -7,7 +7,7 @@
 //                coarse level from the arena
 //   small rows   one thread per coarse node (<= 16 gathered entries):
 //                register bitonic network, run merge
-//   overflow     one kernel, block roles: rows <= 32 one warp (shuffle
+//   overflow     one kernel, classes in turn: rows <= 32 one warp (shuffle
 //                bitonic), <= 128 one warp (shared memory), <= MID_MAX one
 //                block (shared memory), longer one block (radix through global)
 //   degree scan  coarse xadj; its last tile records nnz' and decides the stop
@@ -636,31 +636,36 @@ union OverflowSmem {
 static __device__ void phase_contract_overflow(DevState *st, int level, const Work &w, OverflowSmem &sm) {
     CView p;
     if (!load_view(st, level, w, p)) return;
-    const int nb = gridDim.x;
-    const int r1 = nb * 3 / 8, r2 = nb * 6 / 8, r3 = nb * 7 / 8;   // role boundaries
-    const int b = blockIdx.x;
+    // every block takes part in every class in turn, so no class can be left
+    // without blocks however small the grid is
     const int warp = threadIdx.x >> 5;
     constexpr int NW = CONTRACT_BLOCK / 32;
-    if (b < r2) {
-        const int cls = b < r1 ? 1 : 2;
-        const int rb = b < r1 ? b : b - r1, nrb = b < r1 ? r1 : r2 - r1;
-        const int32_t count = p.ctr->nclass[cls];
-        for (int64_t li = (int64_t)rb * NW + warp; li < count; li += (int64_t)nrb * NW) {
-            const int32_t x = p.lists[cls][li];
-            if (cls == 1) contract_warp32(p, x);
-            else contract_warp_smem(p, x, sm.warp.K[warp], sm.warp.V[warp], sm.warp.S[warp]);
-        }
-    } else if (b < r3) {
+    const int64_t gw = (int64_t)blockIdx.x * NW + warp, nw = (int64_t)gridDim.x * NW;
+    {
+        const int32_t count = p.ctr->nclass[1];
+        for (int64_t li = gw; li < count; li += nw) contract_warp32(p, p.lists[1][li]);
+    }
+    {
+        const int32_t count = p.ctr->nclass[2];
+        for (int64_t li = gw; li < count; li += nw)
+            contract_warp_smem(p, p.lists[2][li], sm.warp.K[warp], sm.warp.V[warp], sm.warp.S[warp]);
+    }
+    __syncthreads();
+    {
         const int32_t count = p.ctr->nclass[3];
-        for (int32_t li = b - r2; li < count; li += r3 - r2)
+        for (int32_t li = blockIdx.x; li < count; li += gridDim.x)
             contract_block_smem(p, p.lists[3][li], sm.mid.keys, sm.mid.vals, sm.mid.sums, sm.mid.s_red);
-    } else {
+    }
+    __syncthreads();
+    {
         const int32_t count = p.ctr->nclass[4];
-        if (count == 0) return;
-        int bits = 1;
-        while (bits < 31 && ((int64_t)1 << bits) < (int64_t)p.cn) bits++;
-        const int passes = (bits + 7) / 8;
-        for (int32_t li = b - r3; li < count; li += nb - r3) contract_block_radix(p, p.lists[4][li], passes, sm.big);
+        if (count > 0) {
+            int bits = 1;
+            while (bits < 31 && ((int64_t)1 << bits) < (int64_t)p.cn) bits++;
+            const int passes = (bits + 7) / 8;
+            for (int32_t li = blockIdx.x; li < count; li += gridDim.x)
+                contract_block_radix(p, p.lists[4][li], passes, sm.big);
+        }
     }
 }
 

@@ -155,9 +155,12 @@ def match_from_map(mp):
 # many small and ragged graphs, every rating
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("tail", [0, -1])
 @pytest.mark.parametrize("matcher", MATCHERS)
 @pytest.mark.parametrize("rating", RATINGS)
-def test_random_graphs(rating, matcher):
+def test_random_graphs(rating, matcher, tail):
+    """tail 0: small graphs run in the persistent tail launch; -1: per-phase
+    kernels only."""
     for t in range(24):
         rng = np.random.default_rng(t)
         n = int(rng.integers(2, 400))
@@ -166,9 +169,10 @@ def test_random_graphs(rating, matcher):
                                  allow_zero_c=(t % 5 == 0))
         seed = int(rng.integers(0, 2**63))
         stop = int(rng.choice([1, 10, 50]))
-        h, dg, levels, maps = run_gpu(g, rating=rating, seed=seed, stop_size=stop, matcher=matcher)
+        h, dg, levels, maps = run_gpu(g, rating=rating, seed=seed, stop_size=stop, matcher=matcher,
+                                      tail_nodes=tail)
         ref = O.coarsen(g, rating, seed, stop)
-        assert_same(levels, maps, ref, f"{rating} {matcher} t={t}")
+        assert_same(levels, maps, ref, f"{rating} {matcher} tail={tail} t={t}")
         h.free()
 
 
@@ -245,12 +249,15 @@ def test_tiny_and_degenerate():
             h.free()
 
 
+@pytest.mark.parametrize("tail", [0, -1, 2000])
 @pytest.mark.parametrize("matcher", MATCHERS)
-def test_arena_growth_resumes_exactly(matcher):
+def test_arena_growth_resumes_exactly(matcher, tail):
     """A tiny initial arena overflows at several levels; the engine grows it
-    and resumes at the level that did not fit, with the same results."""
+    and resumes at the level that did not fit, with the same results, in the
+    per-phase path, the persistent tail, and a switch between them."""
     for g, r in [(I.rgg2d(30000, 9, wmax=5), "expansion*2"), (I.grid3d(20, 20, 20), "innerOuter")]:
-        h, dg, levels, maps = run_gpu(g, rating=r, seed=3, stop_size=20, matcher=matcher, arena_bytes=4096)
+        h, dg, levels, maps = run_gpu(g, rating=r, seed=3, stop_size=20, matcher=matcher, arena_bytes=4096,
+                                      tail_nodes=tail)
         assert_same(levels, maps, O.coarsen(g, r, 3, 20), f"arena {g.name} {matcher}")
         h.free()
 
