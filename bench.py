@@ -199,6 +199,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--matcher", default="suitor", choices=["suitor", "handshake"])
+    ap.add_argument("--tail-nodes", type=int, default=0)
     args = ap.parse_args()
     wl = workloads()[args.workload]
     g = wl["make"]()
@@ -231,7 +232,7 @@ def main():
 
     def step(seed, validate=False, want_sizes=False):
         h = B.coarsen(dg, rating=rating, seed=1, stop_size=stop, validate=validate, profile=True,
-                      matcher=args.matcher)
+                      matcher=args.matcher, tail_nodes=args.tail_nodes)
         L = h.num_levels()
         top, _ = B.kp_hierarchy_level(h.handle, L - 1)
         cpart = torch.from_numpy(I.random_balanced_partition(top.n, k, seed)).to("cuda", non_blocking=False)

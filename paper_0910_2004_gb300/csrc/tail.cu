@@ -28,11 +28,15 @@ __global__ void __launch_bounds__(MATCH_BLOCK) k_tail(DevState *st, int first, i
         if (SUITOR) {
             phase_suitor<R, false>(st, level, w);
             if (!grid_sync(bar, err, lim)) return;
-            phase_suitor<R, true>(st, level, w);
+            // the wide pass only when some node was parked (uniform decision)
+            if (ld_relaxed_i32(&st->ctr[level].list_size[0]) > 0) {
+                phase_suitor<R, true>(st, level, w);
+                if (!grid_sync(bar, err, lim)) return;
+            }
         } else {
             if (!phase_handshake<R>(st, level, w)) return;
+            if (!grid_sync(bar, err, lim)) return;
         }
-        if (!grid_sync(bar, err, lim)) return;
         {
             RelabelOp<SUITOR> op;
             op.st = st;
@@ -69,8 +73,8 @@ kp_status launch_tail_rs(DevState *st, const Work &w, int first, int last, int32
         KP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tail<R, SUITOR>, MATCH_BLOCK, 0));
         occ = o > 0 ? o : 1;
     }
-    const int64_t want = ((int64_t)std::max<int32_t>(n_bound, 1) + 1023) / 1024;
-    const int grid = (int)std::max<int64_t>(4, std::min<int64_t>(want, (int64_t)occ * num_sms()));
+    const int64_t want = ((int64_t)std::max<int32_t>(n_bound, 1) + 2047) / 2048;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)occ * num_sms()));
     DevState *a0 = st;
     int a1 = first, a2 = last;
     Work a3 = w;
