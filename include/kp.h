@@ -210,6 +210,43 @@ kp_status kp_hierarchy_profile(const kp_hierarchy *h, int32_t l, kp_level_profil
 /* Releases the hierarchy (synchronises the stream it was built on). */
 void kp_hierarchy_free(kp_hierarchy *h);
 
+/* Batches of independent graphs.  The graphs are stored as one disjoint
+ * union (a symmetric CSR with no edge between two graphs); graph i owns the
+ * nodes [node_offsets[i], node_offsets[i+1]).  Every graph is coarsened
+ * exactly as kp_coarsen would coarsen it alone with seed seeds[i] (all of
+ * them with o->seed when seeds is NULL): tie-break hashes use graph-local
+ * ids, and the stop rule is applied to each graph on its own, so a graph's
+ * result does not depend on the rest of the batch.  A graph that stops
+ * leaves the union; the union's levels keep the graphs still being
+ * contracted, in order.  One call coarsens the whole batch (the levels of
+ * all graphs together, small levels in one persistent launch).
+ *   node_offsets  device int32[num_graphs+1], from 0 to g->n, non-decreasing;
+ *                 BORROWED like the graph
+ *   seeds         device uint64[num_graphs] or NULL
+ * The view of graph i at level l (l < its level count) is nodes
+ * [off_l[i], off_l[i+1]) of union level l (kp_hierarchy_level_offsets),
+ * with neighbour ids off_l[i] higher than its local ids; map_l sends them to
+ * union level l+1.
+ * Errors: as kp_coarsen, plus KP_ERR_INVALID for bad offsets or (with
+ * o->validate) an edge between two graphs. */
+kp_status kp_coarsen_batch(const kp_graph *g, int32_t num_graphs, const int32_t *node_offsets,
+                           const uint64_t *seeds, const kp_options *o, kp_stream s, kp_hierarchy **out);
+
+/* Batch sizes (host outputs, either may be NULL): the number of graphs (0
+ * for a single-graph hierarchy) and, per graph, its number of levels
+ * including the input (host array of num_graphs). */
+kp_status kp_hierarchy_batch(const kp_hierarchy *h, int32_t *num_graphs, int32_t *levels);
+
+/* Device int32[num_graphs+1]: first node of every graph on union level l. */
+kp_status kp_hierarchy_level_offsets(const kp_hierarchy *h, int32_t l, const int32_t **node_offsets);
+
+/* Uncontraction of a batch: every graph from its own coarsest level.  The
+ * coarse partition of graph i sits at coarse_part[coarse_offsets[i] + j] for
+ * its coarsest node j (device arrays; coarse_offsets has num_graphs+1
+ * entries).  fine_part: device int32[n_0].  Does not synchronise. */
+kp_status kp_project_batch(const kp_hierarchy *h, const int32_t *coarse_part, const int32_t *coarse_offsets,
+                           int32_t *fine_part, kp_stream s);
+
 /* Uncontraction (Section 2): the block of every input node is the block of
  * the coarsest node it was contracted into, p_l(v) = p_{l+1}(map_l(v)) from
  * the coarsest level down to level 0.

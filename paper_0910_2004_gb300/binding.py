@@ -28,6 +28,7 @@ PHASES = ["validate", "out", "match", "relabel", "contract", "csr", "tail"]
 
 EXPORTED = ["kp_options_default", "kp_coarsen", "kp_hierarchy_num_levels", "kp_hierarchy_level",
             "kp_hierarchy_stats", "kp_hierarchy_profile", "kp_hierarchy_free", "kp_project", "kp_cut_gain", "kp_cut_gain_noalloc", "kp_pipeline_host",
+            "kp_coarsen_batch", "kp_hierarchy_batch", "kp_hierarchy_level_offsets", "kp_project_batch",
             "kp_last_error", "kp_version"]
 
 
@@ -106,6 +107,15 @@ def load(path: str = LIB_PATH):
                                        kp_initial_partition_fn, vp, vp, vp, vp, vp,
                                        ctypes.POINTER(kp_cut_gain_out), ctypes.POINTER(i32), vp]
         L.kp_pipeline_host.restype = ctypes.c_int
+        L.kp_coarsen_batch.argtypes = [ctypes.POINTER(kp_graph), i32, vp, vp, ctypes.POINTER(kp_options), vp,
+                                       ctypes.POINTER(vp)]
+        L.kp_coarsen_batch.restype = ctypes.c_int
+        L.kp_hierarchy_batch.argtypes = [vp, ctypes.POINTER(i32), vp]
+        L.kp_hierarchy_batch.restype = ctypes.c_int
+        L.kp_hierarchy_level_offsets.argtypes = [vp, i32, ctypes.POINTER(vp)]
+        L.kp_hierarchy_level_offsets.restype = ctypes.c_int
+        L.kp_project_batch.argtypes = [vp, vp, vp, vp, vp]
+        L.kp_project_batch.restype = ctypes.c_int
         L.kp_last_error.argtypes = []
         L.kp_last_error.restype = ctypes.c_char_p
         L.kp_version.argtypes = []
@@ -193,6 +203,35 @@ def kp_pipeline_host(graph: kp_graph, options: kp_options, k: int, eps: float, i
                                    ctypes.c_void_p(block_w), ctypes.byref(out), ctypes.byref(nl),
                                    ctypes.c_void_p(stream)), "kp_pipeline_host")
     return nl.value
+
+
+def kp_coarsen_batch(graph: kp_graph, num_graphs: int, node_offsets: int, seeds: int, options: kp_options,
+                     stream: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().kp_coarsen_batch(ctypes.byref(graph), num_graphs, ctypes.c_void_p(node_offsets),
+                                   ctypes.c_void_p(seeds), ctypes.byref(options), ctypes.c_void_p(stream),
+                                   ctypes.byref(h)), "kp_coarsen_batch")
+    return h.value
+
+
+def kp_hierarchy_batch(h: int):
+    ng = ctypes.c_int32()
+    _check(load().kp_hierarchy_batch(ctypes.c_void_p(h), ctypes.byref(ng), None), "kp_hierarchy_batch")
+    levels = (ctypes.c_int32 * max(ng.value, 1))()
+    _check(load().kp_hierarchy_batch(ctypes.c_void_p(h), ctypes.byref(ng), levels), "kp_hierarchy_batch")
+    return ng.value, list(levels)[:ng.value]
+
+
+def kp_hierarchy_level_offsets(h: int, level: int) -> int:
+    p = ctypes.c_void_p()
+    _check(load().kp_hierarchy_level_offsets(ctypes.c_void_p(h), level, ctypes.byref(p)),
+           "kp_hierarchy_level_offsets")
+    return p.value
+
+
+def kp_project_batch(h: int, coarse_part: int, coarse_offsets: int, fine_part: int, stream: int):
+    _check(load().kp_project_batch(ctypes.c_void_p(h), ctypes.c_void_p(coarse_part), ctypes.c_void_p(coarse_offsets),
+                                   ctypes.c_void_p(fine_part), ctypes.c_void_p(stream)), "kp_project_batch")
 
 
 def kp_last_error() -> str:
@@ -319,6 +358,60 @@ class Hierarchy:
 def coarsen(graph: DeviceGraph, **opts) -> Hierarchy:
     h = kp_coarsen(graph.kp, make_options(**opts), current_stream())
     return Hierarchy(graph, h)
+
+
+class BatchHierarchy(Hierarchy):
+    """Hierarchy of a batch of independent graphs (kp_coarsen_batch)."""
+
+    def __init__(self, graph: DeviceGraph, handle: int, offsets, seeds):
+        super().__init__(graph, handle)
+        self.offsets = offsets   # keep the borrowed arrays alive
+        self.seeds = seeds
+
+    def graph_levels(self):
+        return kp_hierarchy_batch(self.handle)[1]
+
+    def level_offsets(self, l: int):
+        ng, _ = kp_hierarchy_batch(self.handle)
+        return device_view(kp_hierarchy_level_offsets(self.handle, l), ng + 1)
+
+    def graph_level(self, gi: int, l: int):
+        """Graph gi at level l as host arrays with graph-local ids."""
+        lv = self.level(l)
+        off = self.level_offsets(l).cpu().numpy()
+        a, b = int(off[gi]), int(off[gi + 1])
+        X = lv["xadj"][a:b + 1].cpu().numpy().astype(np.int64)
+        e0, e1 = int(X[0]), int(X[-1])
+        out = {"n": b - a, "xadj": (X - e0).astype(np.int32),
+               "adjncy": (lv["adjncy"][e0:e1].cpu().numpy() - a).astype(np.int32),
+               "ewgt": lv["ewgt"][e0:e1].cpu().numpy(), "vwgt": lv["vwgt"][a:b].cpu().numpy(), "map": None}
+        levels = self.graph_levels()[gi]
+        if l < levels - 1:
+            nxt = self.level_offsets(l + 1).cpu().numpy()
+            out["map"] = (lv["map"][a:b].cpu().numpy() - nxt[gi]).astype(np.int32)
+        return out
+
+    def project(self, coarse_part, coarse_offsets, fine_part=None):
+        torch = _torch()
+        if fine_part is None:
+            fine_part = torch.empty(self.graph.n, dtype=torch.int32, device="cuda")
+        kp_project_batch(self.handle, coarse_part.data_ptr(), coarse_offsets.data_ptr(), fine_part.data_ptr(),
+                         current_stream())
+        return fine_part
+
+
+def coarsen_batch(graph: DeviceGraph, offsets, seeds=None, **opts) -> BatchHierarchy:
+    """graph: the disjoint union (DeviceGraph); offsets: int32 node offsets
+    [num_graphs+1] (array or CUDA tensor); seeds: per-graph uint64 or None."""
+    torch = _torch()
+    off = offsets if torch.is_tensor(offsets) else torch.as_tensor(np.asarray(offsets, dtype=np.int32))
+    off = off.to("cuda").contiguous()
+    sd = None
+    if seeds is not None:
+        sd = torch.as_tensor(np.asarray(seeds, dtype=np.uint64).view(np.int64)).to("cuda").contiguous()
+    h = kp_coarsen_batch(graph.kp, off.numel() - 1, off.data_ptr(), sd.data_ptr() if sd is not None else 0,
+                         make_options(**opts), current_stream())
+    return BatchHierarchy(graph, h, off, sd)
 
 
 def cut_gain(graph, part, k: int, eps: float, block_w=None, gain=None, target=None):

@@ -166,8 +166,9 @@ kp_status validate_graph(const kp_graph *g, cudaStream_t s, int64_t) {
     return KP_OK;
 }
 
-kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, kp_hierarchy **out);
 kp_status project_impl(const kp_hierarchy *h, const int32_t *coarse_part, int32_t *fine_part, cudaStream_t s);
+kp_status project_batch_impl(const kp_hierarchy *h, const int32_t *coarse_part, const int32_t *coarse_offsets,
+                             int32_t *fine_part, cudaStream_t s);
 kp_status cut_gain_impl(const kp_graph *g, const int32_t *part, int32_t k, double eps, kp_cut_gain_out *out,
                         cudaStream_t s);
 kp_status cut_gain_noalloc_impl(const kp_graph *g, const int32_t *part, int32_t k, double eps,
@@ -218,6 +219,42 @@ kp_status kp_coarsen(const kp_graph *g, const kp_options *o, kp_stream s, kp_hie
     if (o && o->max_levels > 120) return set_error(KP_ERR_UNSUPPORTED, "max_levels above 120");
     g_last_error.clear();
     KP_GUARD(coarsen_impl(g, o ? o : &def, (cudaStream_t)s, out));
+}
+
+kp_status kp_coarsen_batch(const kp_graph *g, int32_t num_graphs, const int32_t *node_offsets,
+                           const uint64_t *seeds, const kp_options *o, kp_stream s, kp_hierarchy **out) {
+    if (!g || !out) return set_error(KP_ERR_INVALID, "null argument");
+    *out = nullptr;
+    kp_options def;
+    kp_options_default(&def);
+    if (o && o->max_levels > 120) return set_error(KP_ERR_UNSUPPORTED, "max_levels above 120");
+    g_last_error.clear();
+    BatchSpec b;
+    b.num_graphs = num_graphs;
+    b.node_offsets = node_offsets;
+    b.seeds = seeds;
+    KP_GUARD(coarsen_impl(g, o ? o : &def, (cudaStream_t)s, out, &b));
+}
+
+kp_status kp_hierarchy_batch(const kp_hierarchy *h, int32_t *num_graphs, int32_t *levels) {
+    if (!h) return set_error(KP_ERR_INVALID, "null argument");
+    if (num_graphs) *num_graphs = h->num_graphs;
+    if (levels)
+        for (int32_t i = 0; i < h->num_graphs; i++) levels[i] = h->glevels[(size_t)i];
+    return KP_OK;
+}
+
+kp_status kp_hierarchy_level_offsets(const kp_hierarchy *h, int32_t l, const int32_t **node_offsets) {
+    if (!h || !node_offsets) return set_error(KP_ERR_INVALID, "null argument");
+    if (h->num_graphs == 0) return set_error(KP_ERR_INVALID, "not a batch hierarchy");
+    if (l < 0 || l >= (int32_t)h->levels.size()) return set_error(KP_ERR_INVALID, "level out of range");
+    *node_offsets = h->levels[(size_t)l].goff;
+    return KP_OK;
+}
+
+kp_status kp_project_batch(const kp_hierarchy *h, const int32_t *coarse_part, const int32_t *coarse_offsets,
+                           int32_t *fine_part, kp_stream s) {
+    KP_GUARD(project_batch_impl(h, coarse_part, coarse_offsets, fine_part, (cudaStream_t)s));
 }
 
 kp_status kp_hierarchy_num_levels(const kp_hierarchy *h, int32_t *num_levels) {

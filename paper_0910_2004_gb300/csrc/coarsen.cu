@@ -64,7 +64,8 @@ unsigned long long align256(unsigned long long b) { return (b + 255ull) & ~255ul
 
 kp_status validate_graph(const kp_graph *g, cudaStream_t s, int64_t spin_limit);
 
-kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, kp_hierarchy **out) {
+kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, kp_hierarchy **out,
+                       const BatchSpec *batch) {
     const int rating = o->rating;
     if (rating < 0 || rating > 4) return set_error(KP_ERR_UNSUPPORTED, "unknown rating");
     if (o->matcher != KP_MATCHER_SUITOR && o->matcher != KP_MATCHER_HANDSHAKE)
@@ -84,6 +85,19 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         }
         if (!g_coop_supported) return set_error(KP_ERR_UNSUPPORTED, "device lacks cooperative launch");
     }
+    const int32_t G = batch ? batch->num_graphs : 0;
+    std::vector<int32_t> host_off;
+    if (batch) {   // the node ranges of the graphs must tile [0, n)
+        if (G < 1 || !batch->node_offsets) return set_error(KP_ERR_INVALID, "batch needs num_graphs >= 1 and offsets");
+        host_off.resize((size_t)G + 1);
+        KP_CUDA(cudaMemcpyAsync(host_off.data(), batch->node_offsets, sizeof(int32_t) * ((size_t)G + 1),
+                                cudaMemcpyDeviceToHost, s));
+        KP_CUDA(cudaStreamSynchronize(s));
+        if (host_off[0] != 0 || host_off[(size_t)G] != g->n) return set_error(KP_ERR_INVALID, "batch offsets must run from 0 to n");
+        for (int32_t i = 0; i < G; i++)
+            if (host_off[(size_t)i + 1] < host_off[(size_t)i])
+                return set_error(KP_ERR_INVALID, "batch offsets must not decrease");
+    }
     PhaseTimer timer(o->profile != 0, s);
     int32_t launches = 0;
     if (o->validate && g->n > 0) {
@@ -95,6 +109,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
 
     kp_hierarchy *h = new kp_hierarchy();
     h->stream = s;
+    h->num_graphs = G;
     KP_CUDA(cudaGetDevice(&h->device));
     kp_level l0;
     l0.n = g->n;
@@ -113,7 +128,38 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     const int32_t nnz0 = g->nnz;
     const bool suitor = o->matcher == KP_MATCHER_SUITOR;
     const bool inner_outer = rating == KP_RATING_INNER_OUTER;
-    const bool active0 = n0 > o->stop_size && o->max_levels > 0;
+    const bool active0 = batch ? true : (n0 > o->stop_size && o->max_levels > 0);
+    h->levels[0].goff = batch ? const_cast<int32_t *>(batch->node_offsets) : nullptr;
+    if (batch) {   // per-graph level counts (1 until a graph is contracted)
+        h->glevels.assign((size_t)G, 1);
+        kp_status st0 = dev_alloc_n(&h->glevels_dev, G, s);
+        if (st0 != KP_OK) return fail(st0);
+        h->allocations.push_back(h->glevels_dev);
+        st0 = dev_alloc_n(&h->gid0, n0, s);
+        if (st0 != KP_OK) return fail(st0);
+        h->allocations.push_back(h->gid0);
+        if (cudaMemcpyAsync(h->glevels_dev, h->glevels.data(), sizeof(int32_t) * (size_t)G, cudaMemcpyHostToDevice,
+                            s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "upload graph levels"));
+        if (n0 > 0) {
+            st0 = launch_graph_ids(n0, G, batch->node_offsets, h->gid0, s, &launches);
+            if (st0 != KP_OK) return fail(st0);
+        }
+        if (o->validate && n0 > 0) {   // every edge stays inside its graph
+            int32_t *flag = nullptr;
+            st0 = dev_alloc_n(&flag, 1, s);
+            if (st0 != KP_OK) return fail(st0);
+            int32_t hflag = 0;
+            cudaMemsetAsync(flag, 0, sizeof(int32_t), s);
+            st0 = launch_check_batch_edges(g, h->gid0, batch->node_offsets, flag, s);
+            if (st0 == KP_OK && (cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                                 cudaStreamSynchronize(s) != cudaSuccess))
+                st0 = cuda_error(cudaGetLastError(), "batch edge check");
+            dev_free(flag, s);
+            if (st0 != KP_OK) return fail(st0);
+            if (hflag) return fail(set_error(KP_ERR_INVALID, "a batch edge joins two different graphs"));
+        }
+    }
     if (n0 == 0 || !active0) {
         h->total.n = n0;
         h->total.nnz = nnz0;
@@ -156,6 +202,14 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
 #undef SC_GET
     w.seed = o->seed;
     w.spin_limit = o->spin_limit;
+    if (batch) {
+        w.batch = 1;
+        w.num_graphs = G;
+        w.seeds = batch->seeds;
+        w.glevels = h->glevels_dev;
+        kp_status st1 = sc.get(&w.gactive, G);
+        if (st1 != KP_OK) return fail(st1);
+    }
     if (cudaMemsetAsync(w.status, 0, sizeof(TileStatus) * (size_t)(scan_tiles(n0) + 1), s) != cudaSuccess)
         return fail(cuda_error(cudaGetLastError(), "clear scan status"));
 
@@ -187,6 +241,10 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     L0.adjncy = const_cast<int32_t *>(g->adjncy);
     L0.ewgt = const_cast<int32_t *>(g->ewgt);
     L0.vwgt = const_cast<int32_t *>(g->vwgt);
+    if (batch) {
+        L0.gid = h->gid0;
+        L0.goff = const_cast<int32_t *>(batch->node_offsets);
+    }
     hs->arena = arena;
     hs->arena_cap = arena_cap;
     hs->arena_used = 0;
@@ -222,15 +280,18 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     for (;;) {   // one pass per arena size
         int32_t n_bound = start == 0 ? n0 : hs->lv[start].n;
         int64_t nnz_bound = start == 0 ? nnz0 : std::max(hs->lv[start].nnz, 1);
-        for (int level = start; level < o->max_levels; level++) {
+        // a batch runs one more level: graphs stopping at the level cap are
+        // only recorded at the level after it
+        const int level_end = o->max_levels + (batch ? 1 : 0);
+        for (int level = start; level < level_end; level++) {
             if (n_bound <= tail_nodes) {   // the rest in one persistent launch
                 timer.mark(KP_PHASE_TAIL, level);
                 const int32_t before = launches;
-                st = launch_tail(dst, w, rating, o->matcher, level, o->max_levels, n_bound, epoch, s, &launches);
+                st = launch_tail(dst, w, rating, o->matcher, level, level_end, n_bound, epoch, s, &launches);
                 timer.mark(-1, level);
                 if (st != KP_OK) return bail(st);
                 level_launches[(size_t)level] += launches - before;
-                epoch += 2 * (o->max_levels - level) + 2;
+                epoch += 2 * (level_end - level) + 2;
                 break;
             }
             LevelLaunch LL;
@@ -324,6 +385,13 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     }
     for (int l = 0; l < last; l++) h->levels[(size_t)l].map = hs->lv[l].map;
     h->levels[(size_t)last].map = nullptr;
+    if (batch) {
+        for (int l = 1; l <= last; l++) h->levels[(size_t)l].goff = hs->lv[l].goff;
+        if (cudaMemcpyAsync(h->glevels.data(), h->glevels_dev, sizeof(int32_t) * (size_t)G, cudaMemcpyDeviceToHost,
+                            s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(cuda_error(cudaGetLastError(), "read graph levels"));
+    }
     h->per_level.resize((size_t)last);
     int32_t total_rounds = 0;
     int64_t total_matched = 0;

@@ -29,8 +29,8 @@ struct RelabelOp {
     Work w;
     // loaded by prepare()
     int32_t n;
-    const int32_t *xadj, *vwgt;
-    int32_t *map, *cvwgt;
+    const int32_t *xadj, *vwgt, *gid;
+    int32_t *map, *cvwgt, *gidn;
 
     __device__ bool prepare() {
         const DevLevel L = st->lv[level];
@@ -39,7 +39,9 @@ struct RelabelOp {
         xadj = L.xadj;
         vwgt = L.vwgt;
         map = L.map;
+        gid = L.gid;
         cvwgt = st->lv[level + 1].vwgt;
+        gidn = st->lv[level + 1].gid;
         return true;
     }
     __device__ int64_t count() const { return n; }
@@ -54,6 +56,10 @@ struct RelabelOp {
         return p < 0 ? (int32_t)v : p;   // still free after a barrier gave up: single
     }
     __device__ uint64_t load(int64_t v) const {
+        if (w.batch && !w.gactive[gid[v]]) {   // its graph has stopped: not carried on
+            map[v] = -1;
+            return 0;
+        }
         const int32_t p = partner(v);
         if (p < v) return 0;   // not the representative of its pair
         int32_t ub = xadj[v + 1] - xadj[v];
@@ -75,6 +81,7 @@ struct RelabelOp {
             cvwgt[x] = vwgt[v];
         }
         w.off[x] = (int32_t)(excl & 0xffffffffu);
+        if (w.batch) gidn[x] = gid[v];
     }
     // One thread: the coarse sizes are known, carve the coarse level.
     __device__ void total(uint64_t t) const {
@@ -84,7 +91,9 @@ struct RelabelOp {
         c->cn = cn;
         c->U = U;
         DevLevel *L = &st->lv[level];
-        if (cn == n) {   // nothing matched: the level is not kept
+        // one graph: nothing matched, the level is not kept; a batch: every
+        // graph has stopped (graphs without a match are found at the next level)
+        if (w.batch ? cn == 0 : cn == n) {
             atomicOr(&L->flags, LV_NOMATCH);
             stop_at(st, level, 0);
             return;
@@ -222,6 +231,20 @@ __device__ __forceinline__ void contract_thread(const CView &p, int32_t x, int32
 static __device__ void phase_contract_small(DevState *st, int level, const Work &w) {
     CView p;
     if (!load_view(st, level, w, p)) return;
+    if (w.batch) {   // first coarse node of every graph (the coarse graph ids are sorted)
+        const int32_t *gidn = st->lv[level + 1].gid;
+        int32_t *goffn = st->lv[level + 1].goff;
+        const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g <= w.num_graphs; g += gs) {
+            int32_t lo = 0, hi = p.cn;
+            while (lo < hi) {
+                const int32_t mid = lo + (hi - lo) / 2;
+                if (gidn[mid] < g) lo = mid + 1;
+                else hi = mid;
+            }
+            goffn[g] = lo;
+        }
+    }
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); x0 < p.cn; x0 += stride) {
@@ -698,10 +721,15 @@ struct DegScanOp {
         DevLevel *C = &st->lv[level + 1];
         C->nnz = (int32_t)t;
         const int64_t n = st->lv[level].n;
-        const bool small = cn <= st->stop_size;
-        const bool capped = level + 1 >= st->max_levels;
-        const bool stalled = (int64_t)cn * 1000 > n * (1000 - st->min_shrink_permille);
-        const bool next = !(small || capped || stalled || st->stop || st->err);
+        bool next;
+        if (w.batch) {   // graphs decide for themselves at the next level start
+            next = cn > 0 && level + 1 <= st->max_levels && !(st->stop || st->err);
+        } else {
+            const bool small = cn <= st->stop_size;
+            const bool capped = level + 1 >= st->max_levels;
+            const bool stalled = (int64_t)cn * 1000 > n * (1000 - st->min_shrink_permille);
+            next = !(small || capped || stalled || st->stop || st->err);
+        }
         C->flags = LV_BUILT | (next ? LV_ACTIVE : 0);
         if (!next) st->stop = 1;
         volatile LevelSnap *s = st->snap + level;

@@ -52,8 +52,10 @@ struct Counters {   // one per level, zeroed before the level runs
 struct DevLevel {
     int32_t n, nnz, U, flags;
     int32_t *xadj, *adjncy, *ewgt, *vwgt;
-    int32_t *map;    // to level l+1
+    int32_t *map;    // to level l+1 (-1: the node's graph has stopped)
     int32_t *outw;   // Out(v) (innerOuter only)
+    int32_t *gid;    // batches: graph of each node
+    int32_t *goff;   // batches: first node of each graph, [num_graphs+1]
 };
 
 // What the host needs to steer the loop, written by the device into mapped
@@ -118,7 +120,37 @@ struct Work {
     TileStatus *status;
     uint64_t seed;
     long long spin_limit;
+    // batches of independent graphs (batch = 0: one graph)
+    int32_t batch;
+    int32_t num_graphs;
+    const uint64_t *seeds;   // per graph, or null: `seed` for all
+    int32_t *gactive;        // per graph: contracted at the current level
+    int32_t *glevels;        // per graph: levels of its hierarchy (input included)
 };
+
+// Tie-break hash context of a node: the seed of its graph and the id offset
+// that makes ids graph-local, so a graph's result does not depend on where it
+// sits in a batch.
+struct HashCtx {
+    uint64_t seed;
+    int32_t base;
+};
+
+__device__ __forceinline__ HashCtx hash_ctx(const Work &w, const DevLevel &L, int32_t v) {
+    HashCtx h;
+    h.seed = w.seed;
+    h.base = 0;
+    if (w.batch) {
+        const int32_t g = L.gid[v];
+        if (w.seeds) h.seed = w.seeds[g];
+        h.base = L.goff[g];
+    }
+    return h;
+}
+
+__device__ __forceinline__ uint64_t edge_hash_in(const HashCtx &h, int32_t u, int32_t v) {
+    return edge_hash(h.seed, u - h.base, v - h.base);
+}
 
 // ---------------------------------------------------------------------------
 // ratings (Section 3.1) as exact fractions
@@ -312,6 +344,10 @@ struct LevelLaunch {
     int32_t epoch_relabel, epoch_degscan;
 };
 
+kp_status launch_graph_ids(int32_t n0, int32_t num_graphs, const int32_t *goff, int32_t *gid, cudaStream_t s,
+                           int32_t *launches);
+kp_status launch_check_batch_edges(const kp_graph *g, const int32_t *gid, const int32_t *goff, int32_t *flag,
+                                   cudaStream_t s);
 kp_status launch_out_weight(DevState *st, int32_t n0, const int32_t *xadj, const int32_t *ewgt, int32_t *outw,
                             cudaStream_t s, int32_t *launches);
 kp_status launch_matching(const LevelLaunch &L, cudaStream_t s, int32_t *launches);

@@ -392,6 +392,57 @@ kp_status cut_gain_impl(const kp_graph *g, const int32_t *part, int32_t k, doubl
     return st;
 }
 
+struct ProjectBatchParams {
+    int32_t n0;
+    const int32_t *gid0;
+    const int32_t *glevels;
+    const int32_t *coarse_part;
+    const int32_t *coarse_offsets;
+    int32_t *fine_part;
+    const int32_t *maps[PROJECT_MAX_LEVELS];
+    const int32_t *goffs[PROJECT_MAX_LEVELS];
+};
+
+// Batches: every graph from its own coarsest level, whose partition sits at
+// coarse_part[coarse_offsets[g] + local id].
+__global__ void k_project_batch(const __grid_constant__ ProjectBatchParams p) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < p.n0; v += stride) {
+        const int32_t g = p.gid0[v];
+        const int32_t L = p.glevels[g] - 1;
+        int32_t x = (int32_t)v;
+        for (int l = 0; l < L; l++) x = p.maps[l][x];
+        p.fine_part[v] = p.coarse_part[p.coarse_offsets[g] + (x - p.goffs[L][g])];
+    }
+}
+
+kp_status project_batch_impl(const kp_hierarchy *h, const int32_t *coarse_part, const int32_t *coarse_offsets,
+                             int32_t *fine_part, cudaStream_t s) {
+    if (!h) return set_error(KP_ERR_INVALID, "null argument");
+    if (h->num_graphs == 0) return set_error(KP_ERR_INVALID, "not a batch hierarchy");
+    const int32_t n0 = h->levels[0].n;
+    if (n0 == 0) return KP_OK;
+    if (!coarse_part || !coarse_offsets || !fine_part) return set_error(KP_ERR_INVALID, "null argument");
+    const int32_t L = (int32_t)h->levels.size();
+    if (L > PROJECT_MAX_LEVELS) return set_error(KP_ERR_UNSUPPORTED, "too many levels");
+    ProjectBatchParams p;
+    std::memset(&p, 0, sizeof p);
+    p.n0 = n0;
+    p.gid0 = h->gid0;
+    p.glevels = h->glevels_dev;
+    p.coarse_part = coarse_part;
+    p.coarse_offsets = coarse_offsets;
+    p.fine_part = fine_part;
+    for (int l = 0; l < L; l++) {
+        p.maps[l] = h->levels[(size_t)l].map;
+        p.goffs[l] = h->levels[(size_t)l].goff;
+    }
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n0 + 255) / 256, (int64_t)num_sms() * 16));
+    k_project_batch<<<grid, 256, 0, s>>>(p);
+    KP_CUDA(cudaGetLastError());
+    return KP_OK;
+}
+
 kp_status project_impl(const kp_hierarchy *h, const int32_t *coarse_part, int32_t *fine_part, cudaStream_t s) {
     if (!h || (h->levels[0].n > 0 && (!coarse_part || !fine_part))) return set_error(KP_ERR_INVALID, "null argument");
     const int32_t L = (int32_t)h->levels.size() - 1;
@@ -411,7 +462,6 @@ kp_status project_impl(const kp_hierarchy *h, const int32_t *coarse_part, int32_
     return KP_OK;
 }
 
-kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, kp_hierarchy **out);
 
 kp_status pipeline_host_impl(const kp_graph *hg, const kp_options *o, int32_t k, double eps,
                              kp_initial_partition_fn ip, void *user, int32_t *fine_part, int64_t *gain,

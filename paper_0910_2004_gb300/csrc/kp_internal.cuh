@@ -33,6 +33,16 @@ kp_status cuda_error(cudaError_t e, const char *what);
 
 int num_sms();
 
+// A batch of independent graphs stored as one disjoint union.
+struct BatchSpec {
+    int32_t num_graphs;
+    const int32_t *node_offsets;   // device [num_graphs+1]: graph i is [off[i], off[i+1])
+    const uint64_t *seeds;         // device [num_graphs] or null
+};
+
+kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, kp_hierarchy **out,
+                       const BatchSpec *batch = nullptr);
+
 // Stream-ordered device allocation from the device's default memory pool
 // (its release threshold is raised once so freed blocks are reused).
 kp_status dev_alloc(void **p, size_t bytes, cudaStream_t s);
@@ -270,6 +280,7 @@ struct kp_level {
     int32_t *ewgt = nullptr;
     int32_t *vwgt = nullptr;
     int32_t *map = nullptr;   // to the next level; nullptr on the coarsest
+    int32_t *goff = nullptr;  // batches: first node of each graph on this level
     bool owned = false;
 };
 
@@ -282,6 +293,11 @@ struct kp_hierarchy {
     int64_t total_matched = 0;
     kp_level_profile total = {};
     std::vector<kp_level_profile> per_level;
+    // batches of independent graphs
+    int32_t num_graphs = 0;             // 0: one graph
+    std::vector<int32_t> glevels;       // per graph: number of levels
+    int32_t *glevels_dev = nullptr;     // the same on the device
+    int32_t *gid0 = nullptr;            // graph of every input node (device)
 };
 
 namespace kp {

@@ -78,6 +78,57 @@ kp_status launch_matching(const LevelLaunch &L, cudaStream_t s, int32_t *launche
     }
 }
 
+// Graph of every input node of a batch: the last graph whose first node is
+// at or before it.
+__global__ void k_graph_ids(int32_t n0, int32_t num_graphs, const int32_t *__restrict__ goff,
+                            int32_t *__restrict__ gid) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n0; v += stride) {
+        int32_t lo = 0, hi = num_graphs - 1;
+        while (lo < hi) {
+            const int32_t mid = lo + (hi - lo + 1) / 2;
+            if (goff[mid] <= v) lo = mid;
+            else hi = mid - 1;
+        }
+        gid[v] = lo;
+    }
+}
+
+// Every edge of a batch stays inside its graph.
+__global__ void k_check_batch_edges(int32_t n, const int32_t *__restrict__ xadj, const int32_t *__restrict__ adjncy,
+                                    const int32_t *__restrict__ gid, const int32_t *__restrict__ goff,
+                                    int32_t *flag) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+        const int32_t g = gid[v];
+        const int32_t lo = goff[g], hi = goff[g + 1];
+        for (int32_t e = xadj[v]; e < xadj[v + 1]; e++) {
+            const int32_t u = adjncy[e];
+            if (u < lo || u >= hi) {
+                atomicOr(flag, 1);
+                break;
+            }
+        }
+    }
+}
+
+kp_status launch_graph_ids(int32_t n0, int32_t num_graphs, const int32_t *goff, int32_t *gid, cudaStream_t s,
+                           int32_t *launches) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n0 + 255) / 256, (int64_t)num_sms() * 8));
+    k_graph_ids<<<grid, 256, 0, s>>>(n0, num_graphs, goff, gid);
+    *launches += 1;
+    KP_CUDA(cudaGetLastError());
+    return KP_OK;
+}
+
+kp_status launch_check_batch_edges(const kp_graph *g, const int32_t *gid, const int32_t *goff, int32_t *flag,
+                                   cudaStream_t s) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->n + 255) / 256, (int64_t)num_sms() * 8));
+    k_check_batch_edges<<<grid, 256, 0, s>>>(g->n, g->xadj, g->adjncy, gid, goff, flag);
+    KP_CUDA(cudaGetLastError());
+    return KP_OK;
+}
+
 kp_status launch_out_weight(DevState *, int32_t n0, const int32_t *xadj, const int32_t *ewgt, int32_t *outw,
                             cudaStream_t s, int32_t *launches) {
     const int64_t threads = (int64_t)n0 * 8;

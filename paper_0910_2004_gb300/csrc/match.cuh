@@ -23,12 +23,43 @@ __device__ void phase_level_begin(DevState *st, int level, const Work &w) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         int32_t *map = (int32_t *)arena_carve(st, 4ull * (unsigned long long)L.n);
         int32_t *cv = map ? (int32_t *)arena_carve(st, 4ull * (unsigned long long)L.n) : nullptr;
-        if (!map || !cv) {
+        int32_t *gidn = cv, *goffn = cv;
+        if (cv && w.batch) {
+            gidn = (int32_t *)arena_carve(st, 4ull * (unsigned long long)L.n);
+            goffn = gidn ? (int32_t *)arena_carve(st, 4ull * ((unsigned long long)w.num_graphs + 1)) : nullptr;
+        }
+        if (!map || !cv || !gidn || !goffn) {
             st->overflow = level + 1;
             stop_at(st, level, 0);
         } else {
             st->lv[level].map = map;
             st->lv[level + 1].vwgt = cv;
+            if (w.batch) {
+                st->lv[level + 1].gid = gidn;
+                st->lv[level + 1].goff = goffn;
+            }
+        }
+    }
+    if (w.batch) {
+        // per graph: is it contracted at this level?  (the stop rule of a
+        // single graph, applied to each graph of the batch)
+        const int32_t *prev = level > 0 ? st->lv[level - 1].goff : nullptr;
+        const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < w.num_graphs; g += gstride) {
+            const int64_t nc = L.goff[g + 1] - L.goff[g];
+            const int64_t np = prev ? (int64_t)(prev[g + 1] - prev[g]) : -1;
+            int32_t act = 0;
+            if (nc == 0) {
+                act = 0;   // left the batch at an earlier level
+            } else if (level > 0 && nc == np) {
+                w.glevels[g] = level;   // nothing matched: that copy is not a level
+            } else if (nc <= st->stop_size || level >= st->max_levels ||
+                       (level > 0 && nc * 1000 > np * (1000 - st->min_shrink_permille))) {
+                w.glevels[g] = level + 1;
+            } else {
+                act = 1;
+            }
+            w.gactive[g] = act;
         }
     }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -143,6 +174,7 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
             continue;
         }
         const int32_t acur = rating_attr<R>(L.vwgt, L.outw, cur);
+        const HashCtx hc = hash_ctx(w, L, cur);
         Cand best;
         best.u = -1;
         best.num = best.den = best.h = 0;
@@ -156,7 +188,7 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
             Cand c;
             c.u = v;
             rating_ab<R>(wt, acur, st.au, c.num, c.den);
-            c.h = edge_hash(w.seed, cur, v);
+            c.h = edge_hash_in(hc, cur, v);
             bool eligible = st.s < 0;
             if (!eligible) {
                 // compare at v: the offer of cur against the standing offer of st.s
@@ -167,7 +199,7 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
                 a.h = c.h;
                 b.u = st.s;
                 rating_ab<R>(st.w, st.as, st.au, b.num, b.den);
-                b.h = edge_hash(w.seed, st.s, v);
+                b.h = edge_hash_in(hc, st.s, v);
                 eligible = better(a, b, v);
             }
             if (eligible && better(c, best, cur)) {
@@ -267,6 +299,7 @@ __device__ __forceinline__ void rate_node(const DevLevel &L, const Work &w, Coun
     if (gl == 0) atomicAdd(&ctr->searches, 1ull);
     const int32_t beg = KP_LDG(L.xadj + v), end = KP_LDG(L.xadj + v + 1);
     const int32_t av = rating_attr<R>(L.vwgt, L.outw, v);
+    const HashCtx hc = hash_ctx(w, L, v);
     Cand best;
     best.u = -1;
     best.num = best.den = best.h = 0;
@@ -276,7 +309,7 @@ __device__ __forceinline__ void rate_node(const DevLevel &L, const Work &w, Coun
         Cand c;
         c.u = u;
         rating_ab<R>(KP_LDG(L.ewgt + e), av, rating_attr<R>(L.vwgt, L.outw, u), c.num, c.den);
-        c.h = edge_hash(w.seed, v, u);
+        c.h = edge_hash_in(hc, v, u);
         if (better(c, best, v)) best = c;
     }
 #pragma unroll

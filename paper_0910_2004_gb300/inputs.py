@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "CSRGraph", "from_edges", "grid2d", "grid3d", "rgg2d", "rmat",
     "random_small_graph", "path_graph", "star_graph", "batch_rgg_sizes",
-    "random_balanced_partition", "random_partition",
+    "random_balanced_partition", "random_partition", "union_graph",
 ]
 
 
@@ -223,6 +223,28 @@ def batch_rgg_sizes(count: int, seed: int, nmin: int = 1024, nmax: int = 65536) 
     """Node counts log-uniform in [nmin, nmax] for a batch of independent RGGs."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.floor(np.exp(rng.uniform(math.log(nmin), math.log(nmax), size=count))).astype(np.int64)
+
+
+def union_graph(graphs) -> tuple:
+    """Disjoint union of graphs in order: graph i's node v becomes node
+    offsets[i] + v.  Returns (CSRGraph, offsets int32[len(graphs)+1])."""
+    ns = np.array([g.n for g in graphs], dtype=np.int64)
+    offsets = np.zeros(len(graphs) + 1, dtype=np.int64)
+    np.cumsum(ns, out=offsets[1:])
+    nnzs = np.array([g.nnz for g in graphs], dtype=np.int64)
+    eoff = np.zeros(len(graphs) + 1, dtype=np.int64)
+    np.cumsum(nnzs, out=eoff[1:])
+    xadj = np.zeros(int(offsets[-1]) + 1, dtype=np.int64)
+    adj = np.empty(int(eoff[-1]), dtype=np.int32)
+    ew = np.empty(int(eoff[-1]), dtype=np.int32)
+    vw = np.empty(int(offsets[-1]), dtype=np.int32)
+    for i, g in enumerate(graphs):
+        o, e = int(offsets[i]), int(eoff[i])
+        xadj[o:o + g.n + 1] = g.xadj.astype(np.int64) + e
+        adj[e:e + g.nnz] = g.adjncy + o
+        ew[e:e + g.nnz] = g.ewgt
+        vw[o:o + g.n] = g.vwgt
+    return CSRGraph(xadj.astype(np.int32), adj, ew, vw, f"union_{len(graphs)}"), offsets.astype(np.int32)
 
 
 def random_balanced_partition(n: int, k: int, seed: int) -> np.ndarray:
