@@ -48,6 +48,11 @@ def workloads():
             desc="2D random geometric graph, n=2^22 uniform points, radius for mean degree 6, unit int32 "
                  "weights, expansion*2 rating, full hierarchy to <= 20*64 nodes, cut/gain k=64 eps=0.03",
             make=lambda: I.rgg2d(1 << 22, 1), rating="expansion*2", k=64, eps=0.03),
+        "batch4096": dict(
+            desc="batched: 4,096 independent 2D random geometric graphs, n log-uniform in [1k, 64k], mean degree 6, "
+                 "integer edge weights uniform in [1,16], expansion*2, each graph coarsened to <= 20*2 nodes in one "
+                 "batch (union) call, per-graph seed = graph index, random balanced 2-way partitions projected back",
+            make=None, rating="expansion*2", k=2, eps=0.03, batch=4096),
         "grid64": dict(
             desc="2D 5-point grid 64x64, unit weights, expansion*2, coarsen to <= 20*2 nodes, cut/gain k=2 eps=0.03",
             make=lambda: I.grid2d(64, 64), rating="expansion*2", k=2, eps=0.03),
@@ -202,6 +207,8 @@ def main():
     ap.add_argument("--tail-nodes", type=int, default=0)
     args = ap.parse_args()
     wl = workloads()[args.workload]
+    if wl.get("batch"):
+        return run_batch(args, wl)
     g = wl["make"]()
     if args.impl == "reference":
         return run_reference(args, wl, g)
@@ -380,6 +387,223 @@ def main():
         line["cpu_baseline"] = {"value": g.m / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
                                 "sample": "one full step of the same workload (coarsen + project + cut/gain), "
                                           "single-threaded C/numpy oracle"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# batched workload: many independent graphs in one call
+# ---------------------------------------------------------------------------
+def batch_slices(xadj, adj, ew, vw, off, idx):
+    """Host CSRs of the graphs `idx` of a union (numpy)."""
+    import numpy as _np
+    x, a, w, v, o = [t.cpu().numpy() for t in (xadj, adj, ew, vw, off)]
+    out = []
+    for gi in idx:
+        s0, e0 = int(o[gi]), int(o[gi + 1])
+        X = (x[s0:e0 + 1].astype(_np.int64) - x[s0]).astype(_np.int32)
+        out.append(I.CSRGraph(X, (a[x[s0]:x[e0]] - s0).astype(_np.int32), w[x[s0]:x[e0]].copy(), v[s0:e0].copy(),
+                              f"batch_graph_{gi}"))
+    return out
+
+
+def run_batch(args, wl):
+    G = wl["batch"]
+    k, eps, rating = wl["k"], wl["eps"], wl["rating"]
+    stop = 20 * k
+    sizes = I.batch_rgg_sizes(G, seed=1, nmin=1024, nmax=65536)
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return 0
+        import oracle as O
+        xadj, adj, ew, vw, off = I.rgg2d_batch(sizes, 1, wmax=16, device="cpu")
+        sample = list(range(0, G, max(1, G // 64)))
+        graphs = batch_slices(xadj, adj, ew, vw, off, sample)
+        msum = sum(g.m for g in graphs)
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            for gi, g in zip(sample, graphs):
+                h = O.coarsen(g, rating, gi, stop)
+                p = O.project(h.maps, I.random_balanced_partition(h.levels[-1].n, k, gi))
+                O.cut_gain(g, p, k, eps)
+            times.append(time.perf_counter() - t0)
+        value = msum * args.steps / sum(times)
+        print(json.dumps({
+            "impl": "reference", "metric": "coarsened edges/s (full hierarchy)", "value": value, "unit": "edges/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * sum(times) / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "graphs": G},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(sample)} of the {G} graphs per step, single-threaded oracle"},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+        return 0
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0910_2004_gb300 import binding as B
+
+    xadj, adj, ew, vw, off = I.rgg2d_batch(sizes, 1, wmax=16, device="cuda")
+    n, nnz = int(vw.numel()), int(adj.numel())
+    m = nnz // 2
+    dg = B.DeviceGraph(xadj, adj, ew, vw)
+    seeds = np.arange(G, dtype=np.uint64)
+    gidx = torch.repeat_interleave(torch.arange(G, device="cuda", dtype=torch.int32),
+                                   (off[1:] - off[:-1]).long())
+    fine = torch.empty(n, dtype=torch.int32, device="cuda")
+    bw = torch.empty(k * G, dtype=torch.int64, device="cuda")
+    gain = torch.empty(n, dtype=torch.int64, device="cuda")
+    target = torch.empty(n, dtype=torch.int32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(seed, validate=False, want_profile=False):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = B.coarsen_batch(dg, off, seeds, rating=rating, stop_size=stop, validate=validate, profile=True,
+                            matcher=args.matcher, tail_nodes=args.tail_nodes)
+        e1.record(stream)
+        cs = h.coarsest_sizes()
+        part, poff = I.batch_partition(cs, k, seed)
+        part = part + k * np.repeat(np.arange(G, dtype=np.int32), cs)   # block ids of the union
+        cp = torch.from_numpy(part.astype(np.int32)).to("cuda")
+        co = torch.from_numpy(poff).to("cuda")
+        h.project(cp, co, fine)
+        res = B.cut_gain(dg, fine, k * G, eps, block_w=bw, gain=gain, target=target)
+        tot = h.profile()
+        levels = None
+        if want_profile:
+            levels = []
+            for l in range(h.num_levels() - 1):
+                lp = h.profile(l)
+                levels.append({"n": lp["n"], "nnz": lp["nnz"], "searches": lp["searches"],
+                               **{kk + "_ms": round(v, 4) for kk, v in lp["phase_ms"].items() if v}})
+        h.free()
+        return res, tot, (e0, e1), levels
+
+    for wi in range(max(args.warmup, 3)):
+        step(wi, validate=(wi == 0))
+    _, _, _, level_profile = step(0, want_profile=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, coarsen_ms, phase_tot, launches = [], [], {}, 0
+    for si in range(args.steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        res, tot, ev, _ = step(100 + si)
+        b.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(a.elapsed_time(b))
+        coarsen_ms.append(ev[0].elapsed_time(ev[1]))
+        for kk, v in tot["phase_ms"].items():
+            phase_tot[kk] = phase_tot.get(kk, 0.0) + v
+        launches += tot["launches"] + 4
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # the same graphs coarsened one call each (a sample), for comparison
+    sample = list(range(0, G, max(1, G // 128)))
+    graphs = batch_slices(xadj, adj, ew, vw, off, sample)
+    dgs = [B.DeviceGraph.from_csr(g) for g in graphs]
+    for d, gi in zip(dgs[:8], sample[:8]):
+        B.coarsen(d, rating=rating, seed=gi, stop_size=stop, validate=False, matcher=args.matcher).free()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for d, gi in zip(dgs, sample):
+        B.coarsen(d, rating=rating, seed=gi, stop_size=stop, validate=False, matcher=args.matcher).free()
+    b.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = a.elapsed_time(b)
+    loop_m = sum(g.m for g in graphs)
+
+    # end to end from pinned host buffers: copies in, the whole step, results out
+    host = [t.cpu().pin_memory() for t in (xadj, adj, ew, vw, off)]
+    dev = [torch.empty_like(t) for t in (xadj, adj, ew, vw, off)]
+    outs = (torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.int64).pin_memory())
+    dge = B.DeviceGraph(dev[0], dev[1], dev[2], dev[3])
+    e2e_ms = []
+    for si in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for hst, d in zip(host, dev):
+            d.copy_(hst, non_blocking=True)
+        h = B.coarsen_batch(dge, dev[4], seeds, rating=rating, stop_size=stop, validate=False,
+                            matcher=args.matcher, tail_nodes=args.tail_nodes)
+        cs = h.coarsest_sizes()
+        part, poff = I.batch_partition(cs, k, si)
+        part = part + k * np.repeat(np.arange(G, dtype=np.int32), cs)
+        h.project(torch.from_numpy(part.astype(np.int32)).to("cuda"), torch.from_numpy(poff).to("cuda"), fine)
+        B.cut_gain(dge, fine, k * G, eps, block_w=bw, gain=gain, target=target)
+        outs[0].copy_(fine, non_blocking=True)
+        outs[1].copy_(gain, non_blocking=True)
+        torch.cuda.synchronize()
+        h.free()
+        e2e_ms.append(1000 * (time.perf_counter() - t0))
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    steps = args.steps
+    peak, peak_kind = load_peaks()
+    line = {
+        "metric": "coarsened edges/s (full hierarchy)",
+        "value": world * m * steps / (total_ms / 1000.0), "unit": "edges/s", "n_gpus": world, "steps": steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": total_ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "graphs": G, "n": n, "m": m,
+                   "union_levels": len(level_profile) + 1, "l2": "inputs larger than L2; also flushed",
+                   "matcher": args.matcher, "parallelism": f"replicas x{world}"},
+        "coarsen_only": {"batch_edges_per_s": m * steps / (sum(coarsen_ms) / 1000.0),
+                         "per_graph_loop_edges_per_s": loop_m / (loop_ms / 1000.0),
+                         "per_graph_loop_sample_graphs": len(sample),
+                         "speedup": (m * steps / sum(coarsen_ms)) / (loop_m / loop_ms)},
+        "phase_ms_per_step": {kk: v / steps for kk, v in phase_tot.items()},
+        "level_profile": level_profile,
+        "clocks": clocks,
+        "e2e": {"value": world * m * len(e2e_ms) / (sum(e2e_ms) / 1000.0), "unit": "edges/s",
+                "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in host),
+                "d2h_bytes_per_step": 12 * n, "steps": len(e2e_ms),
+                "api": "kp_coarsen_batch + kp_project_batch + kp_cut_gain, inputs copied from pinned host memory"},
+        "gpu_launches": launches,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        osample = sample[:32]
+        og = graphs[:32]
+        t0 = time.perf_counter()
+        for gi, g in zip(osample, og):
+            h = O.coarsen(g, rating, gi, stop)
+            p = O.project(h.maps, I.random_balanced_partition(h.levels[-1].n, k, gi))
+            O.cut_gain(g, p, k, eps)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sum(g.m for g in og) / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{len(og)} of the {G} graphs (every {G // 128}th), single-threaded oracle"}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

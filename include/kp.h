@@ -237,6 +237,10 @@ kp_status kp_coarsen_batch(const kp_graph *g, int32_t num_graphs, const int32_t 
  * including the input (host array of num_graphs). */
 kp_status kp_hierarchy_batch(const kp_hierarchy *h, int32_t *num_graphs, int32_t *levels);
 
+/* Coarsest size of every graph of a batch (host int32[num_graphs]).
+ * Synchronises the stream. */
+kp_status kp_hierarchy_batch_coarsest(const kp_hierarchy *h, int32_t *sizes, kp_stream s);
+
 /* Device int32[num_graphs+1]: first node of every graph on union level l. */
 kp_status kp_hierarchy_level_offsets(const kp_hierarchy *h, int32_t l, const int32_t **node_offsets);
 

@@ -29,6 +29,7 @@ PHASES = ["validate", "out", "match", "relabel", "contract", "csr", "tail"]
 EXPORTED = ["kp_options_default", "kp_coarsen", "kp_hierarchy_num_levels", "kp_hierarchy_level",
             "kp_hierarchy_stats", "kp_hierarchy_profile", "kp_hierarchy_free", "kp_project", "kp_cut_gain", "kp_cut_gain_noalloc", "kp_pipeline_host",
             "kp_coarsen_batch", "kp_hierarchy_batch", "kp_hierarchy_level_offsets", "kp_project_batch",
+            "kp_hierarchy_batch_coarsest",
             "kp_last_error", "kp_version"]
 
 
@@ -114,6 +115,8 @@ def load(path: str = LIB_PATH):
         L.kp_hierarchy_batch.restype = ctypes.c_int
         L.kp_hierarchy_level_offsets.argtypes = [vp, i32, ctypes.POINTER(vp)]
         L.kp_hierarchy_level_offsets.restype = ctypes.c_int
+        L.kp_hierarchy_batch_coarsest.argtypes = [vp, vp, vp]
+        L.kp_hierarchy_batch_coarsest.restype = ctypes.c_int
         L.kp_project_batch.argtypes = [vp, vp, vp, vp, vp]
         L.kp_project_batch.restype = ctypes.c_int
         L.kp_last_error.argtypes = []
@@ -227,6 +230,13 @@ def kp_hierarchy_level_offsets(h: int, level: int) -> int:
     _check(load().kp_hierarchy_level_offsets(ctypes.c_void_p(h), level, ctypes.byref(p)),
            "kp_hierarchy_level_offsets")
     return p.value
+
+
+def kp_hierarchy_batch_coarsest(h: int, num_graphs: int, stream: int) -> np.ndarray:
+    out = np.empty(max(num_graphs, 1), dtype=np.int32)
+    _check(load().kp_hierarchy_batch_coarsest(ctypes.c_void_p(h), ctypes.c_void_p(out.ctypes.data),
+                                              ctypes.c_void_p(stream)), "kp_hierarchy_batch_coarsest")
+    return out[:num_graphs]
 
 
 def kp_project_batch(h: int, coarse_part: int, coarse_offsets: int, fine_part: int, stream: int):
@@ -370,6 +380,9 @@ class BatchHierarchy(Hierarchy):
 
     def graph_levels(self):
         return kp_hierarchy_batch(self.handle)[1]
+
+    def coarsest_sizes(self) -> np.ndarray:
+        return kp_hierarchy_batch_coarsest(self.handle, self.offsets.numel() - 1, current_stream())
 
     def level_offsets(self, l: int):
         ng, _ = kp_hierarchy_batch(self.handle)

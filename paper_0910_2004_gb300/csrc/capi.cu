@@ -169,6 +169,7 @@ kp_status validate_graph(const kp_graph *g, cudaStream_t s, int64_t) {
 kp_status project_impl(const kp_hierarchy *h, const int32_t *coarse_part, int32_t *fine_part, cudaStream_t s);
 kp_status project_batch_impl(const kp_hierarchy *h, const int32_t *coarse_part, const int32_t *coarse_offsets,
                              int32_t *fine_part, cudaStream_t s);
+kp_status batch_coarsest_impl(const kp_hierarchy *h, int32_t *sizes, cudaStream_t s);
 kp_status cut_gain_impl(const kp_graph *g, const int32_t *part, int32_t k, double eps, kp_cut_gain_out *out,
                         cudaStream_t s);
 kp_status cut_gain_noalloc_impl(const kp_graph *g, const int32_t *part, int32_t k, double eps,
@@ -242,6 +243,10 @@ kp_status kp_hierarchy_batch(const kp_hierarchy *h, int32_t *num_graphs, int32_t
     if (levels)
         for (int32_t i = 0; i < h->num_graphs; i++) levels[i] = h->glevels[(size_t)i];
     return KP_OK;
+}
+
+kp_status kp_hierarchy_batch_coarsest(const kp_hierarchy *h, int32_t *sizes, kp_stream s) {
+    KP_GUARD(batch_coarsest_impl(h, sizes, (cudaStream_t)s));
 }
 
 kp_status kp_hierarchy_level_offsets(const kp_hierarchy *h, int32_t l, const int32_t **node_offsets) {

@@ -416,6 +416,44 @@ __global__ void k_project_batch(const __grid_constant__ ProjectBatchParams p) {
     }
 }
 
+struct CoarsestParams {
+    int32_t num_graphs;
+    const int32_t *glevels;
+    int32_t *sizes;
+    const int32_t *goffs[PROJECT_MAX_LEVELS];
+};
+
+__global__ void k_batch_coarsest(const __grid_constant__ CoarsestParams p) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < p.num_graphs; g += stride) {
+        const int32_t L = p.glevels[g] - 1;
+        p.sizes[g] = p.goffs[L][g + 1] - p.goffs[L][g];
+    }
+}
+
+kp_status batch_coarsest_impl(const kp_hierarchy *h, int32_t *sizes, cudaStream_t s) {
+    if (!h || !sizes) return set_error(KP_ERR_INVALID, "null argument");
+    if (h->num_graphs == 0) return set_error(KP_ERR_INVALID, "not a batch hierarchy");
+    const int32_t L = (int32_t)h->levels.size();
+    if (L > PROJECT_MAX_LEVELS) return set_error(KP_ERR_UNSUPPORTED, "too many levels");
+    CoarsestParams p;
+    std::memset(&p, 0, sizeof p);
+    p.num_graphs = h->num_graphs;
+    p.glevels = h->glevels_dev;
+    for (int l = 0; l < L; l++) p.goffs[l] = h->levels[(size_t)l].goff;
+    int32_t *d = nullptr;
+    KP_TRY(dev_alloc_n(&d, h->num_graphs, s));
+    p.sizes = d;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)h->num_graphs + 255) / 256, 1024));
+    k_batch_coarsest<<<grid, 256, 0, s>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sizes, d, sizeof(int32_t) * (size_t)h->num_graphs, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(d, s);
+    if (e != cudaSuccess) return cuda_error(e, "batch coarsest sizes");
+    return KP_OK;
+}
+
 kp_status project_batch_impl(const kp_hierarchy *h, const int32_t *coarse_part, const int32_t *coarse_offsets,
                              int32_t *fine_part, cudaStream_t s) {
     if (!h) return set_error(KP_ERR_INVALID, "null argument");

@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "CSRGraph", "from_edges", "grid2d", "grid3d", "rgg2d", "rmat",
     "random_small_graph", "path_graph", "star_graph", "batch_rgg_sizes",
-    "random_balanced_partition", "random_partition", "union_graph",
+    "random_balanced_partition", "random_partition", "union_graph", "rgg2d_batch", "batch_partition",
 ]
 
 
@@ -245,6 +245,91 @@ def union_graph(graphs) -> tuple:
         ew[e:e + g.nnz] = g.ewgt
         vw[o:o + g.n] = g.vwgt
     return CSRGraph(xadj.astype(np.int32), adj, ew, vw, f"union_{len(graphs)}"), offsets.astype(np.int32)
+
+
+def rgg2d_batch(sizes, seed: int, mean_degree: float = 6.0, wmax: int = 16, device: str = "cuda"):
+    """Disjoint union of independent 2D random geometric graphs, built with
+    torch on `device` (fast at tens of millions of nodes).  Graph i has
+    sizes[i] points uniform in [0,1)^2 in generation order, an edge joins
+    points closer than sqrt(mean_degree / (pi n_i)), and integer edge weights
+    are uniform in [1, wmax].  Returns int32 tensors (xadj, adjncy, ewgt,
+    vwgt, offsets); graph i owns nodes [offsets[i], offsets[i+1])."""
+    import torch
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    sz = torch.as_tensor(np.asarray(sizes, dtype=np.int64), device=dev)
+    G = int(sz.numel())
+    P = int(sz.sum().item())
+    offsets = torch.zeros(G + 1, dtype=torch.int64, device=dev)
+    offsets[1:] = torch.cumsum(sz, 0)
+    gid = torch.repeat_interleave(torch.arange(G, device=dev), sz)
+    pts = torch.rand((P, 2), generator=gen, dtype=torch.float64, device=dev)
+    r = torch.sqrt(mean_degree / (math.pi * sz.double()))
+    cells = torch.clamp(torch.floor(1.0 / r).long(), min=1)
+    cell_base = torch.zeros(G, dtype=torch.int64, device=dev)
+    cell_base[1:] = torch.cumsum(cells * cells, 0)[:-1]
+    gp = cells[gid]
+    cx = torch.minimum((pts[:, 0] * gp).long(), gp - 1)
+    cy = torch.minimum((pts[:, 1] * gp).long(), gp - 1)
+    key = cell_base[gid] + cx + gp * cy
+    order = torch.argsort(key)
+    ncells = int((cell_base[-1] + cells[-1] * cells[-1]).item())
+    count = torch.bincount(key, minlength=ncells)
+    start = torch.cumsum(count, 0) - count
+    maxc = int(count.max().item()) if P else 0
+    r2 = (r * r)[gid]
+    pid = torch.arange(P, device=dev)
+    los, his = [], []
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            ncx, ncy = cx + dx, cy + dy
+            ok = (ncx >= 0) & (ncx < gp) & (ncy >= 0) & (ncy < gp)
+            src = pid[ok]
+            ncell = (cell_base[gid] + ncx + gp * ncy)[ok]
+            s0, c0 = start[ncell], count[ncell]
+            for j in range(maxc):
+                has = c0 > j
+                if not bool(has.any()):
+                    break
+                a = src[has]
+                b = order[s0[has] + j]
+                keep = a < b
+                a, b = a[keep], b[keep]
+                d = pts[a] - pts[b]
+                close = (d * d).sum(dim=1) < r2[a]
+                los.append(a[close])
+                his.append(b[close])
+    lo = torch.cat(los) if los else torch.zeros(0, dtype=torch.int64, device=dev)
+    hi = torch.cat(his) if his else torch.zeros(0, dtype=torch.int64, device=dev)
+    if wmax > 1:
+        w = torch.randint(1, wmax + 1, (lo.numel(),), generator=gen, device=dev)
+    else:
+        w = torch.ones(lo.numel(), dtype=torch.int64, device=dev)
+    src = torch.cat([lo, hi])
+    dst = torch.cat([hi, lo])
+    ww = torch.cat([w, w])
+    perm = torch.argsort(src * max(P, 1) + dst)
+    src, dst, ww = src[perm], dst[perm], ww[perm]
+    xadj = torch.zeros(P + 1, dtype=torch.int64, device=dev)
+    xadj[1:] = torch.cumsum(torch.bincount(src, minlength=P), 0)
+    return (xadj.int(), dst.int(), ww.int(), torch.ones(P, dtype=torch.int32, device=dev), offsets.int())
+
+
+def batch_partition(coarse_sizes, k: int, seed: int) -> tuple:
+    """Seeded random balanced k-way partitions of many small graphs at once:
+    within each graph a random order is dealt round-robin to blocks
+    0..k-1 (block ids local to the graph).  Returns (part int32[sum], offsets
+    int32[len+1])."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.asarray(coarse_sizes, dtype=np.int64)
+    off = np.zeros(len(sizes) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    g = np.repeat(np.arange(len(sizes)), sizes)
+    order = np.lexsort((rng.random(int(off[-1])), g))
+    rank = np.empty(int(off[-1]), dtype=np.int64)
+    rank[order] = np.arange(int(off[-1])) - off[g[order]]
+    return (rank % k).astype(np.int32), off.astype(np.int32)
 
 
 def random_balanced_partition(n: int, k: int, seed: int) -> np.ndarray:

@@ -90,6 +90,7 @@ def test_rgg_batch_log_uniform_sizes_and_projection():
     graphs = [I.rgg2d(int(n), 1000 + i, wmax=16) for i, n in enumerate(sizes)]
     seeds = np.arange(len(graphs), dtype=np.uint64)
     h, dg, refs, off = check_batch(graphs, seeds, "expansion*2", 40, "suitor", 0)
+    assert list(h.coarsest_sizes()) == [ref.levels[-1].n for ref in refs]
     parts, coarse_off = [], [0]
     for gi, ref in enumerate(refs):
         p = I.random_balanced_partition(ref.levels[-1].n, 2, seed=gi)
