@@ -56,6 +56,12 @@ def workloads():
         "grid64": dict(
             desc="2D 5-point grid 64x64, unit weights, expansion*2, coarsen to <= 20*2 nodes, cut/gain k=2 eps=0.03",
             make=lambda: I.grid2d(64, 64), rating="expansion*2", k=2, eps=0.03),
+        "served": dict(
+            desc="served: Poisson stream of coarsen+partition+project+cut/gain requests drawn uniformly from a pool "
+                 "of 2D/3D grids, 2D random geometric graphs and R-MAT graphs (a=0.57, b=0.19, c=0.19, edge factor "
+                 "16, duplicates merged into weights) with 2^12..2^22 nodes, k = 2^U{1..6}, stop at 20k nodes, "
+                 "eps=0.03; first saturated, then at 50% and 90% of the saturated request rate",
+            make=None, rating="expansion*2", k=None, eps=0.03, served=True),
         "grid256": dict(
             desc="3D 7-point grid 256^3, unit weights, innerOuter, full hierarchy to <= 20*256 nodes, "
                  "cut/gain k=256 eps=0.03",
@@ -205,10 +211,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--matcher", default="suitor", choices=["suitor", "handshake"])
     ap.add_argument("--tail-nodes", type=int, default=0)
+    ap.add_argument("--requests", type=int, default=None, help="served: requests per load phase")
+    ap.add_argument("--workers", type=int, default=4, help="served: server worker streams")
     args = ap.parse_args()
     wl = workloads()[args.workload]
     if wl.get("batch"):
         return run_batch(args, wl)
+    if wl.get("served"):
+        return run_served(args, wl)
     g = wl["make"]()
     if args.impl == "reference":
         return run_reference(args, wl, g)
@@ -604,6 +614,251 @@ def run_batch(args, wl):
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": sum(g.m for g in og) / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
                                 "sample": f"{len(og)} of the {G} graphs (every {G // 128}th), single-threaded oracle"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# served workload: a request stream through the library's request server
+# ---------------------------------------------------------------------------
+def served_requests(pool, count, seed):
+    """(pool index, k, eps, seed, stop size) of `count` requests: pool entry
+    uniform, k = 2^U{1..6}, stop at 20k nodes."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        pi = int(rng.integers(len(pool)))
+        k = int(2 ** int(rng.integers(1, 7)))
+        out.append((pi, k, 0.03, int(rng.integers(1, 1 << 62)), 20 * k))
+    return out
+
+
+def poisson_arrivals(count, rate, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.cumsum(rng.exponential(1.0 / rate, size=count))
+
+
+def serve_phase(sv, pool, reqs, arrivals):
+    """Submits reqs at the given arrival offsets (seconds; None: all at once)
+    while a second thread waits for and releases them in order.  Latency of a
+    request: from its scheduled arrival to its completion (server clock for
+    submit..done, plus the lag of the submit call behind the schedule)."""
+    import queue
+    import threading
+    q = queue.Queue()
+    results = [None] * len(reqs)
+
+    def reaper():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            i, rid, lag = item
+            res = sv.wait(rid)
+            sv.release(rid)
+            res["lag_s"] = lag
+            results[i] = res
+
+    th = threading.Thread(target=reaper)
+    th.start()
+    t0 = time.perf_counter()
+    for i, (pi, k, eps, seed, stop) in enumerate(reqs):
+        g = pool[pi][2]
+        if arrivals is not None:
+            dt = t0 + arrivals[i] - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+        lag = 0.0 if arrivals is None else max(0.0, time.perf_counter() - (t0 + arrivals[i]))
+        rid = sv.submit(g.xadj, g.adjncy, g.ewgt, g.vwgt, k, eps, seed, stop)
+        q.put((i, rid, lag))
+    q.put(None)
+    th.join()
+    lat = np.array([(r["t_done_us"] - r["t_submit_us"]) / 1000.0 + 1000.0 * r["lag_s"] for r in results])
+    span_s = (max(r["t_done_us"] for r in results) - min(r["t_submit_us"] for r in results)) / 1e6
+    m = sum(pool[pi][2].m for pi, *_ in reqs)
+    groups = {}
+    for r in results:
+        groups[r["group_id"]] = (r["launches"], r["group_size"])
+    assert all(r["status"] == 0 for r in results)
+    return {"requests": len(reqs), "edges": m, "span_s": span_s, "edges_per_s": m / span_s,
+            "requests_per_s": len(reqs) / span_s, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+            "groups": len(groups), "mean_group_size": len(reqs) / max(1, len(groups)),
+            "launches": sum(v[0] for v in groups.values())}
+
+
+def replay_fifo(arrivals, service):
+    """Latencies of a single FIFO server (the per-graph path, one request at
+    a time) for given arrival times and service times (seconds)."""
+    t, lat = 0.0, []
+    for a, s in zip(arrivals, service):
+        t = max(t, a) + s
+        lat.append(t - a)
+    return np.array(lat) * 1000.0
+
+
+def run_served(args, wl):
+    eps, rating = wl["eps"], wl["rating"]
+    R = args.requests if args.requests is not None else max(200, 8 * args.steps)
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return 0
+        import oracle as O
+        pool = I.served_mix(range(12, 17), seed=1, device="cpu")
+        reqs = served_requests(pool, 64, seed=3)
+        times, msum = [], 0
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            msum = 0
+            for pi, k, e, sd, stop in reqs[:16]:
+                g = pool[pi][2]
+                h = O.coarsen(g, rating, sd, stop)
+                O.cut_gain(g, O.project(h.maps, I.random_balanced_partition(h.levels[-1].n, k, 1)), k, e)
+                msum += g.m
+            times.append(time.perf_counter() - t0)
+        value = msum * args.steps / sum(times)
+        print(json.dumps({
+            "impl": "reference", "metric": "served edges/s", "value": value, "unit": "edges/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * sum(times) / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"]},
+            "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                             "sample": "16 requests of the mix restricted to 2^12..2^16 nodes per step, "
+                                       "one after another, single-threaded oracle"},
+            "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+            flush=True)
+        return 0
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0910_2004_gb300 import binding as B
+
+    pool = I.served_mix(range(12, 23), seed=1, device="cuda")
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * 0.6)
+    sat_reqs = served_requests(pool, R, seed=11)
+    load_reqs = {0.5: served_requests(pool, R, seed=12), 0.9: served_requests(pool, R, seed=13)}
+
+    sv = B.Server(workers=args.workers, max_batch=64, batch_max_nodes=1 << 16, hbm_budget_bytes=budget,
+                  rating=rating, validate=False, matcher=args.matcher, tail_nodes=args.tail_nodes)
+    # warm-up: every pool graph once (allocator pool, library state)
+    for _ in range(max(1, min(args.warmup, 2))):
+        serve_phase(sv, pool, [(pi, 2, eps, 1, 40) for pi in range(len(pool))], None)
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    sat = serve_phase(sv, pool, sat_reqs, None)
+    loads = {}
+    for load, reqs in load_reqs.items():
+        rate = load * sat["requests_per_s"]
+        arr = poisson_arrivals(R, rate, seed=int(load * 100))
+        loads[load] = serve_phase(sv, pool, reqs, arr)
+        loads[load]["offered_requests_per_s"] = rate
+        loads[load]["arrivals"] = arr
+    clocks = sampler.stop()
+    sv.close()
+
+    # the plain per-graph GPU path: kp_pipeline_host, one request after the
+    # other; its service times replayed through a FIFO queue at the same
+    # arrivals
+    def ip(nc, cw, kk):
+        return I.random_balanced_partition(nc, kk, 1)
+
+    service = {}
+    for pi in sorted({r[0] for rs in [sat_reqs] + list(load_reqs.values()) for r in rs}):
+        g = pool[pi][2]
+        B.pipeline_host(g.xadj, g.adjncy, g.ewgt, g.vwgt, 2, eps, ip, rating=rating, seed=1, stop_size=40,
+                        validate=False, matcher=args.matcher)
+    for rs in [sat_reqs] + list(load_reqs.values()):
+        for pi, k, e, sd, stop in rs:
+            if (pi, k) in service:
+                continue
+            g = pool[pi][2]
+            t0 = time.perf_counter()
+            B.pipeline_host(g.xadj, g.adjncy, g.ewgt, g.vwgt, k, e, ip, rating=rating, seed=sd, stop_size=stop,
+                            validate=False, matcher=args.matcher)
+            service[(pi, k)] = time.perf_counter() - t0
+    plain_sat_s = sum(service[(pi, k)] for pi, k, *_ in sat_reqs)
+    plain = {"edges_per_s": sat["edges"] / plain_sat_s, "requests_per_s": R / plain_sat_s}
+    for load, reqs in load_reqs.items():
+        lat = replay_fifo(loads[load]["arrivals"], [service[(pi, k)] for pi, k, *_ in reqs])
+        plain[f"load{int(load * 100)}"] = {"p50_ms": float(np.percentile(lat, 50)),
+                                           "p99_ms": float(np.percentile(lat, 99))}
+
+    # algorithmic bytes of the whole path per pool graph and k (level sizes
+    # from one coarsening each)
+    path_bytes = {}
+    for pi, (fam, sc, g) in enumerate(pool):
+        dg = B.DeviceGraph.from_csr(g)
+        for k in (2, 4, 8, 16, 32, 64):
+            h = B.coarsen(dg, rating=rating, seed=1, stop_size=20 * k, validate=False)
+            sizes = [(B.kp_hierarchy_level(h.handle, l)[0].n, B.kp_hierarchy_level(h.handle, l)[0].nnz)
+                     for l in range(h.num_levels())]
+            h.free()
+            path_bytes[(pi, k)] = (sum(algorithmic_bytes(sizes, rating).values()) + eval_bytes(g.n, g.nnz, k)
+                                   + 8 * g.n)
+        del dg
+    sat_bytes = sum(path_bytes[(pi, k)] for pi, k, *_ in sat_reqs)
+    peak, peak_kind = load_peaks()
+    achieved = sat_bytes / sat["span_s"] / 1e9
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    for v in loads.values():
+        v.pop("arrivals")
+    h2d = sum(4 * (pool[pi][2].n + 1) + 8 * pool[pi][2].nnz + 4 * pool[pi][2].n for pi, *_ in sat_reqs) / R
+    line = {
+        "metric": "served edges/s at 90% load (p50/p99 ms beside)",
+        "value": world * loads[0.9]["edges_per_s"], "unit": "edges/s", "n_gpus": world, "steps": R,
+        "warmup": max(1, min(args.warmup, 2)), "ms_per_step": 1000.0 * loads[0.9]["span_s"] / R,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "pool_graphs": len(pool),
+                   "requests_per_phase": R, "workers": args.workers, "max_batch": 64,
+                   "batch_max_nodes": 1 << 16, "hbm_budget_gb": budget / 1e9, "matcher": args.matcher,
+                   "l2": "inputs of the large requests exceed L2; no flush between requests (a stream)",
+                   "parallelism": f"replicas x{world}", "step": "one request"},
+        "served": {"saturated": sat, "load50": loads[0.5], "load90": loads[0.9]},
+        "p50_ms": loads[0.9]["p50_ms"], "p99_ms": loads[0.9]["p99_ms"],
+        "plain_per_graph_path": {**plain, "api": "kp_pipeline_host per request, serial; latencies by FIFO replay "
+                                                 "of measured service times at the same arrivals"},
+        "roofline": {"bound": "hbm", "kernel": "whole path, saturated server", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_step": sat_bytes / R},
+        "clocks": clocks,
+        "e2e": {"value": world * sat["edges_per_s"], "unit": "edges/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 32, "api": "kp_server_submit from host arrays .. kp_server_wait (saturated); "
+                "results stay on the device"},
+        "gpu_launches": sat["launches"] + sum(v["launches"] for v in loads.values()),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        small = [r for r in sat_reqs if pool[r[0]][1] <= 16][:24]
+        t0 = time.perf_counter()
+        for pi, k, e, sd, stop in small:
+            g = pool[pi][2]
+            h = O.coarsen(g, rating, sd, stop)
+            O.cut_gain(g, O.project(h.maps, I.random_balanced_partition(h.levels[-1].n, k, 1)), k, e)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": sum(pool[r[0]][2].m for r in small) / dt, "unit": "edges/s", "cores": 1,
+                                "kind": "oracle", "sample": f"{len(small)} requests of the saturated stream with "
+                                                            "<= 2^16 nodes, one after another, single-threaded oracle"}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

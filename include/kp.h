@@ -116,7 +116,8 @@ typedef enum {
  *   arena_bytes          initial size of the device arena that holds the
  *                        coarse levels (0: sized from the input); the
  *                        arena grows automatically when a level does not fit
- *   tail_nodes           levels with at most this many nodes are contracted
+ *   tail_nodes           levels with at most this many nodes and at most 16
+ *                        times as many directed edges are contracted
  *                        together in one persistent launch (0: 262144;
  *                        -1: never); results do not depend on it */
 typedef struct {
@@ -223,6 +224,8 @@ void kp_hierarchy_free(kp_hierarchy *h);
  *   node_offsets  device int32[num_graphs+1], from 0 to g->n, non-decreasing;
  *                 BORROWED like the graph
  *   seeds         device uint64[num_graphs] or NULL
+ *   stop_sizes    device int32[num_graphs] or NULL: graph i stops at
+ *                 stop_sizes[i] nodes instead of o->stop_size
  * The view of graph i at level l (l < its level count) is nodes
  * [off_l[i], off_l[i+1]) of union level l (kp_hierarchy_level_offsets),
  * with neighbour ids off_l[i] higher than its local ids; map_l sends them to
@@ -230,7 +233,8 @@ void kp_hierarchy_free(kp_hierarchy *h);
  * Errors: as kp_coarsen, plus KP_ERR_INVALID for bad offsets or (with
  * o->validate) an edge between two graphs. */
 kp_status kp_coarsen_batch(const kp_graph *g, int32_t num_graphs, const int32_t *node_offsets,
-                           const uint64_t *seeds, const kp_options *o, kp_stream s, kp_hierarchy **out);
+                           const uint64_t *seeds, const int32_t *stop_sizes, const kp_options *o, kp_stream s,
+                           kp_hierarchy **out);
 
 /* Batch sizes (host outputs, either may be NULL): the number of graphs (0
  * for a single-graph hierarchy) and, per graph, its number of levels
@@ -332,6 +336,96 @@ kp_status kp_pipeline_host(const kp_graph *g, const kp_options *o, int32_t k, do
                            kp_initial_partition_fn ip, void *user, int32_t *fine_part,
                            int64_t *gain, int32_t *target, int64_t *block_w,
                            kp_cut_gain_out *out, int32_t *num_levels, kp_stream s);
+
+/* ------------------------------------------------------------------------
+ * Request server (serving pattern; the paper has no counterpart).  Clients
+ * submit graphs on HOST memory over time; each request runs the whole path
+ * (coarsening as kp_coarsen, a seeded initial partition of the coarsest graph,
+ * projection as kp_project, evaluation as kp_cut_gain) and its results stay
+ * on the device until the client releases the request.
+ * Workers: `workers` host threads, each with its own non-blocking CUDA stream
+ * on the device current at kp_server_create, so groups run concurrently.
+ * Admission: first in, first out; the oldest waiting request starts once its
+ * estimated device footprint fits into hbm_budget_bytes minus the footprint
+ * of running and resident requests (a request runs alone if nothing else is
+ * charged, whatever its size).  Footprint while running: 140 n + 56 nnz + 2 MB
+ * bytes; while resident: 88 n + 40 nnz + 1 MB.
+ * Continuous batching: when a worker takes a request with at most
+ * batch_max_nodes nodes, it also takes further waiting requests with at most
+ * batch_max_nodes nodes that fit the budget, up to
+ * max_batch in all, and runs them as one kp_coarsen_batch call and one batched
+ * projection.  A request's results do not depend on the group it ran in.
+ * The initial partition of a coarsest graph with c nodes: a permutation of
+ * 0..c-1 by Fisher-Yates driven by splitmix64 from the request's seed, dealt
+ * round-robin to blocks 0..k-1.
+ * ------------------------------------------------------------------------ */
+typedef struct kp_server kp_server;
+
+typedef struct kp_server_config {
+    int32_t workers;           /* worker threads/streams, 1..64 */
+    int32_t max_batch;         /* most requests merged into one group, >= 1 */
+    int32_t batch_max_nodes;   /* requests above this size always run alone */
+    int32_t pad;
+    int64_t hbm_budget_bytes;  /* device bytes for running + resident requests */
+    kp_options options;        /* engine options; seed and stop_size are per request */
+} kp_server_config;
+
+typedef struct kp_request_params {
+    int32_t k;          /* blocks, >= 1 */
+    int32_t stop_size;  /* coarsening stops at this many nodes (kp_options.stop_size) */
+    double eps;         /* imbalance parameter of L_max */
+    uint64_t seed;      /* tie-break hash seed and initial-partition seed */
+} kp_request_params;
+
+typedef struct kp_request_result {
+    kp_status status;
+    int32_t num_levels;   /* levels of the request's hierarchy (input included) */
+    int32_t coarsest_n;
+    int32_t group_size;   /* requests in the group it ran in */
+    int32_t launches;     /* kernel launches of that group (all its requests) */
+    int32_t pad;
+    int64_t group_id;     /* groups are numbered from 1 in start order */
+    int64_t cut;          /* as kp_cut_gain_out */
+    int64_t total_c;
+    int64_t l_max;
+    int64_t imbalance;
+    double t_submit_us;   /* microseconds since kp_server_create: entry of submit */
+    double t_admit_us;    /* taken by a worker */
+    double t_done_us;     /* results on the device, scalars on the host */
+} kp_request_result;
+
+/* Starts the workers.  Errors: KP_ERR_INVALID (workers outside 1..64,
+ * max_batch < 1, budget <= 0), KP_ERR_CUDA. */
+kp_status kp_server_create(const kp_server_config *cfg, kp_server **out);
+
+/* Copies the host graph into the server and queues it; *id receives the
+ * request id.  The caller's arrays may be reused once this returns.
+ * Errors: KP_ERR_INVALID (null pointers, negative sizes, k < 1, eps outside
+ * [0,1000], server stopping), KP_ERR_OOM (host copy). */
+kp_status kp_server_submit(kp_server *sv, const kp_graph *g, const kp_request_params *p, uint64_t *id);
+
+/* *done = 1 once the request has finished (successfully or not); res (may
+ * be NULL) receives its result so far.  Errors: KP_ERR_INVALID (unknown id). */
+kp_status kp_server_poll(kp_server *sv, uint64_t id, int32_t *done, kp_request_result *res);
+
+/* Blocks until the request has finished; res (may be NULL) receives its
+ * result; returns the request's own status (with its message). */
+kp_status kp_server_wait(kp_server *sv, uint64_t id, kp_request_result *res);
+
+/* Copies a finished request's results to HOST buffers (each may be NULL):
+ * fine_part int32[n], gain int64[n], target int32[n], coarse_part
+ * int32[coarsest_n] (the initial partition).  Errors: KP_ERR_INVALID
+ * (unknown, unfinished or released request), the request's own error. */
+kp_status kp_server_fetch(kp_server *sv, uint64_t id, int32_t *fine_part, int64_t *gain, int32_t *target,
+                          int32_t *coarse_part);
+
+/* Drops a finished request; its device memory returns to the budget when
+ * every request of its group has been released.  Does not wait for the GPU.
+ * Errors: KP_ERR_INVALID (unknown or unfinished request). */
+kp_status kp_server_release(kp_server *sv, uint64_t id);
+
+/* Stops the workers after their running groups, frees every request. */
+void kp_server_destroy(kp_server *sv);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *kp_last_error(void);

@@ -30,6 +30,8 @@ EXPORTED = ["kp_options_default", "kp_coarsen", "kp_hierarchy_num_levels", "kp_h
             "kp_hierarchy_stats", "kp_hierarchy_profile", "kp_hierarchy_free", "kp_project", "kp_cut_gain", "kp_cut_gain_noalloc", "kp_pipeline_host",
             "kp_coarsen_batch", "kp_hierarchy_batch", "kp_hierarchy_level_offsets", "kp_project_batch",
             "kp_hierarchy_batch_coarsest",
+            "kp_server_create", "kp_server_submit", "kp_server_poll", "kp_server_wait", "kp_server_fetch",
+            "kp_server_release", "kp_server_destroy",
             "kp_last_error", "kp_version"]
 
 
@@ -62,6 +64,24 @@ class kp_level_profile(ctypes.Structure):
     _fields_ = [("phase_ms", ctypes.c_double * 7), ("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("searches", ctypes.c_int64), ("failed_cas", ctypes.c_int64), ("launches", ctypes.c_int32),
                 ("rounds", ctypes.c_int32)]
+
+
+class kp_server_config(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("batch_max_nodes", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64), ("options", kp_options)]
+
+
+class kp_request_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("stop_size", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class kp_request_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("num_levels", ctypes.c_int32), ("coarsest_n", ctypes.c_int32),
+                ("group_size", ctypes.c_int32), ("launches", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("group_id", ctypes.c_int64), ("cut", ctypes.c_int64), ("total_c", ctypes.c_int64),
+                ("l_max", ctypes.c_int64), ("imbalance", ctypes.c_int64), ("t_submit_us", ctypes.c_double),
+                ("t_admit_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
 
 
 kp_initial_partition_fn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
@@ -108,7 +128,7 @@ def load(path: str = LIB_PATH):
                                        kp_initial_partition_fn, vp, vp, vp, vp, vp,
                                        ctypes.POINTER(kp_cut_gain_out), ctypes.POINTER(i32), vp]
         L.kp_pipeline_host.restype = ctypes.c_int
-        L.kp_coarsen_batch.argtypes = [ctypes.POINTER(kp_graph), i32, vp, vp, ctypes.POINTER(kp_options), vp,
+        L.kp_coarsen_batch.argtypes = [ctypes.POINTER(kp_graph), i32, vp, vp, vp, ctypes.POINTER(kp_options), vp,
                                        ctypes.POINTER(vp)]
         L.kp_coarsen_batch.restype = ctypes.c_int
         L.kp_hierarchy_batch.argtypes = [vp, ctypes.POINTER(i32), vp]
@@ -119,6 +139,21 @@ def load(path: str = LIB_PATH):
         L.kp_hierarchy_batch_coarsest.restype = ctypes.c_int
         L.kp_project_batch.argtypes = [vp, vp, vp, vp, vp]
         L.kp_project_batch.restype = ctypes.c_int
+        L.kp_server_create.argtypes = [ctypes.POINTER(kp_server_config), ctypes.POINTER(vp)]
+        L.kp_server_create.restype = ctypes.c_int
+        L.kp_server_submit.argtypes = [vp, ctypes.POINTER(kp_graph), ctypes.POINTER(kp_request_params),
+                                       ctypes.POINTER(ctypes.c_uint64)]
+        L.kp_server_submit.restype = ctypes.c_int
+        L.kp_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(i32), ctypes.POINTER(kp_request_result)]
+        L.kp_server_poll.restype = ctypes.c_int
+        L.kp_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(kp_request_result)]
+        L.kp_server_wait.restype = ctypes.c_int
+        L.kp_server_fetch.argtypes = [vp, ctypes.c_uint64, vp, vp, vp, vp]
+        L.kp_server_fetch.restype = ctypes.c_int
+        L.kp_server_release.argtypes = [vp, ctypes.c_uint64]
+        L.kp_server_release.restype = ctypes.c_int
+        L.kp_server_destroy.argtypes = [vp]
+        L.kp_server_destroy.restype = None
         L.kp_last_error.argtypes = []
         L.kp_last_error.restype = ctypes.c_char_p
         L.kp_version.argtypes = []
@@ -208,12 +243,12 @@ def kp_pipeline_host(graph: kp_graph, options: kp_options, k: int, eps: float, i
     return nl.value
 
 
-def kp_coarsen_batch(graph: kp_graph, num_graphs: int, node_offsets: int, seeds: int, options: kp_options,
-                     stream: int) -> int:
+def kp_coarsen_batch(graph: kp_graph, num_graphs: int, node_offsets: int, seeds: int, stop_sizes: int,
+                     options: kp_options, stream: int) -> int:
     h = ctypes.c_void_p()
     _check(load().kp_coarsen_batch(ctypes.byref(graph), num_graphs, ctypes.c_void_p(node_offsets),
-                                   ctypes.c_void_p(seeds), ctypes.byref(options), ctypes.c_void_p(stream),
-                                   ctypes.byref(h)), "kp_coarsen_batch")
+                                   ctypes.c_void_p(seeds), ctypes.c_void_p(stop_sizes), ctypes.byref(options),
+                                   ctypes.c_void_p(stream), ctypes.byref(h)), "kp_coarsen_batch")
     return h.value
 
 
@@ -242,6 +277,44 @@ def kp_hierarchy_batch_coarsest(h: int, num_graphs: int, stream: int) -> np.ndar
 def kp_project_batch(h: int, coarse_part: int, coarse_offsets: int, fine_part: int, stream: int):
     _check(load().kp_project_batch(ctypes.c_void_p(h), ctypes.c_void_p(coarse_part), ctypes.c_void_p(coarse_offsets),
                                    ctypes.c_void_p(fine_part), ctypes.c_void_p(stream)), "kp_project_batch")
+
+
+def kp_server_create(config: kp_server_config) -> int:
+    sv = ctypes.c_void_p()
+    _check(load().kp_server_create(ctypes.byref(config), ctypes.byref(sv)), "kp_server_create")
+    return sv.value
+
+
+def kp_server_submit(sv: int, graph: kp_graph, params: kp_request_params) -> int:
+    rid = ctypes.c_uint64()
+    _check(load().kp_server_submit(sv, ctypes.byref(graph), ctypes.byref(params), ctypes.byref(rid)),
+           "kp_server_submit")
+    return rid.value
+
+
+def kp_server_poll(sv: int, rid: int):
+    done = ctypes.c_int32()
+    res = kp_request_result()
+    _check(load().kp_server_poll(sv, rid, ctypes.byref(done), ctypes.byref(res)), "kp_server_poll")
+    return bool(done.value), res
+
+
+def kp_server_wait(sv: int, rid: int) -> kp_request_result:
+    res = kp_request_result()
+    _check(load().kp_server_wait(sv, rid, ctypes.byref(res)), "kp_server_wait")
+    return res
+
+
+def kp_server_fetch(sv: int, rid: int, fine_part: int, gain: int, target: int, coarse_part: int):
+    _check(load().kp_server_fetch(sv, rid, fine_part, gain, target, coarse_part), "kp_server_fetch")
+
+
+def kp_server_release(sv: int, rid: int):
+    _check(load().kp_server_release(sv, rid), "kp_server_release")
+
+
+def kp_server_destroy(sv: int):
+    load().kp_server_destroy(sv)
 
 
 def kp_last_error() -> str:
@@ -413,18 +486,23 @@ class BatchHierarchy(Hierarchy):
         return fine_part
 
 
-def coarsen_batch(graph: DeviceGraph, offsets, seeds=None, **opts) -> BatchHierarchy:
+def coarsen_batch(graph: DeviceGraph, offsets, seeds=None, stop_sizes=None, **opts) -> BatchHierarchy:
     """graph: the disjoint union (DeviceGraph); offsets: int32 node offsets
-    [num_graphs+1] (array or CUDA tensor); seeds: per-graph uint64 or None."""
+    [num_graphs+1] (array or CUDA tensor); seeds: per-graph uint64 or None;
+    stop_sizes: per-graph int32 stop sizes or None (opts' stop_size for all)."""
     torch = _torch()
     off = offsets if torch.is_tensor(offsets) else torch.as_tensor(np.asarray(offsets, dtype=np.int32))
     off = off.to("cuda").contiguous()
     sd = None
     if seeds is not None:
         sd = torch.as_tensor(np.asarray(seeds, dtype=np.uint64).view(np.int64)).to("cuda").contiguous()
+    ss = None
+    if stop_sizes is not None:
+        ss = stop_sizes if torch.is_tensor(stop_sizes) else torch.as_tensor(np.asarray(stop_sizes, dtype=np.int32))
+        ss = ss.to("cuda").contiguous()
     h = kp_coarsen_batch(graph.kp, off.numel() - 1, off.data_ptr(), sd.data_ptr() if sd is not None else 0,
-                         make_options(**opts), current_stream())
-    return BatchHierarchy(graph, h, off, sd)
+                         ss.data_ptr() if ss is not None else 0, make_options(**opts), current_stream())
+    return BatchHierarchy(graph, h, off, (sd, ss))
 
 
 def cut_gain(graph, part, k: int, eps: float, block_w=None, gain=None, target=None):
@@ -475,3 +553,56 @@ def pipeline_host(xadj, adjncy, ewgt, vwgt, k: int, eps: float, initial_partitio
         raise err[0]
     return {"cut": out.cut, "total_c": out.total_c, "max_c": out.max_c, "L_max": out.l_max,
             "imbalance": out.imbalance, "num_levels": levels, **outputs}
+
+
+def _result_dict(res: kp_request_result) -> dict:
+    return {name: getattr(res, name) for name, _ in kp_request_result._fields_}
+
+
+class Server:
+    """Request server of the library (kp_server_*): submit host graphs, wait,
+    fetch the results, release.  Timestamps are microseconds since start."""
+
+    def __init__(self, workers=4, max_batch=64, batch_max_nodes=1 << 16, hbm_budget_bytes=64 << 30, **opts):
+        cfg = kp_server_config(workers, max_batch, batch_max_nodes, 0, hbm_budget_bytes, make_options(**opts))
+        self._sv = kp_server_create(cfg)
+
+    def submit(self, xadj, adjncy, ewgt, vwgt, k: int, eps: float, seed: int = 1, stop_size: int = 40) -> int:
+        arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in (xadj, adjncy, ewgt, vwgt)]
+        g = kp_graph(len(arrs[0]) - 1, len(arrs[1]), *[a.ctypes.data for a in arrs])
+        return kp_server_submit(self._sv, g, kp_request_params(k, stop_size, eps, seed))
+
+    def poll(self, rid: int):
+        done, res = kp_server_poll(self._sv, rid)
+        return done, _result_dict(res)
+
+    def wait(self, rid: int) -> dict:
+        return _result_dict(kp_server_wait(self._sv, rid))
+
+    def fetch(self, rid: int, n: int, coarsest_n: int) -> dict:
+        out = {"part": np.empty(max(n, 1), np.int32), "gain": np.empty(max(n, 1), np.int64),
+               "target": np.empty(max(n, 1), np.int32), "coarse_part": np.empty(max(coarsest_n, 1), np.int32)}
+        kp_server_fetch(self._sv, rid, out["part"].ctypes.data, out["gain"].ctypes.data,
+                        out["target"].ctypes.data, out["coarse_part"].ctypes.data)
+        return {"part": out["part"][:n], "gain": out["gain"][:n], "target": out["target"][:n],
+                "coarse_part": out["coarse_part"][:coarsest_n]}
+
+    def release(self, rid: int):
+        kp_server_release(self._sv, rid)
+
+    def close(self):
+        if self._sv:
+            kp_server_destroy(self._sv)
+            self._sv = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,6 +1,7 @@
 // C ABI entry points (include/kp.h), error state, allocation and the
 // device-side input check of Section 2's requirements (omega > 0, c >= 0,
 // undirected graph stored symmetrically, no self loops).
+#include <atomic>
 #include <cstdio>
 #include <mutex>
 #include <new>
@@ -27,20 +28,22 @@ kp_status cuda_error(cudaError_t e, const char *what) {
 }
 
 int num_sms() {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-    if (cached[dev] == 0) {
+    int c = cached[dev].load(std::memory_order_relaxed);
+    if (c == 0) {
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        cached[dev] = v > 0 ? v : 1;
+        c = v > 0 ? v : 1;
+        cached[dev].store(c, std::memory_order_relaxed);
     }
-    return cached[dev];
+    return c;
 }
 
 kp_status dev_alloc(void **p, size_t bytes, cudaStream_t s) {
     static std::mutex mu;
-    static bool configured[64] = {false};
+    static std::atomic<bool> configured[64];
     int dev = 0;
     KP_CUDA(cudaGetDevice(&dev));
     if (dev >= 0 && dev < 64 && !configured[dev]) {
@@ -223,7 +226,8 @@ kp_status kp_coarsen(const kp_graph *g, const kp_options *o, kp_stream s, kp_hie
 }
 
 kp_status kp_coarsen_batch(const kp_graph *g, int32_t num_graphs, const int32_t *node_offsets,
-                           const uint64_t *seeds, const kp_options *o, kp_stream s, kp_hierarchy **out) {
+                           const uint64_t *seeds, const int32_t *stop_sizes, const kp_options *o, kp_stream s,
+                           kp_hierarchy **out) {
     if (!g || !out) return set_error(KP_ERR_INVALID, "null argument");
     *out = nullptr;
     kp_options def;
@@ -234,6 +238,7 @@ kp_status kp_coarsen_batch(const kp_graph *g, int32_t num_graphs, const int32_t 
     b.num_graphs = num_graphs;
     b.node_offsets = node_offsets;
     b.seeds = seeds;
+    b.stop_sizes = stop_sizes;
     KP_GUARD(coarsen_impl(g, o ? o : &def, (cudaStream_t)s, out, &b));
 }
 

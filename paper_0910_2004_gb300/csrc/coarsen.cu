@@ -11,6 +11,7 @@
 // inactive and return at once.  If the arena runs out, the device stops at
 // the level that did not fit; the host adds a larger arena and resumes there.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 
 #include "engine.cuh"
@@ -24,7 +25,7 @@ constexpr int LOOKAHEAD = 2;
 // (default of kp_options.tail_nodes).
 constexpr int32_t TAIL_NODES = 1 << 18;
 
-int g_coop_supported = -1;
+std::atomic<int> g_coop_supported{-1};
 
 struct Scratch {
     cudaStream_t s = nullptr;
@@ -206,6 +207,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         w.batch = 1;
         w.num_graphs = G;
         w.seeds = batch->seeds;
+        w.stops = batch->stop_sizes;
         w.glevels = h->glevels_dev;
         kp_status st1 = sc.get(&w.gactive, G);
         if (st1 != KP_OK) return fail(st1);
@@ -284,7 +286,9 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         // only recorded at the level after it
         const int level_end = o->max_levels + (batch ? 1 : 0);
         for (int level = start; level < level_end; level++) {
-            if (n_bound <= tail_nodes) {   // the rest in one persistent launch
+            // the rest in one persistent launch once the level is small (dense
+            // small levels, as in power-law graphs, stay with the wide grids)
+            if (n_bound <= tail_nodes && nnz_bound <= 16ll * tail_nodes) {
                 timer.mark(KP_PHASE_TAIL, level);
                 const int32_t before = launches;
                 st = launch_tail(dst, w, rating, o->matcher, level, level_end, n_bound, epoch, s, &launches);

@@ -124,6 +124,7 @@ struct Work {
     int32_t batch;
     int32_t num_graphs;
     const uint64_t *seeds;   // per graph, or null: `seed` for all
+    const int32_t *stops;    // per graph stop sizes, or null: the state's for all
     int32_t *gactive;        // per graph: contracted at the current level
     int32_t *glevels;        // per graph: levels of its hierarchy (input included)
 };

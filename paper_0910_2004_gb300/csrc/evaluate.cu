@@ -48,6 +48,7 @@ constexpr int BW_SMEM = 2048;   // block weights kept in shared memory up to thi
 struct CutGainParams {
     int32_t n;
     int32_t k;
+    int32_t id_base;   // neighbour ids minus this are the graph's node ids (0 for a whole graph)
     const int32_t *__restrict__ xadj;
     const int32_t *__restrict__ adjncy;
     const int32_t *__restrict__ ewgt;
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p) {
         // entries held in registers when the row fits the group
         int32_t rb = -1, rw = 0;
         if (deg <= G && gl < deg) {
-            rb = p.part[p.adjncy[beg + gl]];
+            rb = p.part[p.adjncy[beg + gl] - p.id_base];
             rw = p.ewgt[beg + gl];
             if (rb < 0 || rb >= p.k) {
                 bad = 1;
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p) {
             }
         } else {
             for (int32_t e = beg + gl; e < end; e += G) {
-                const int32_t b = p.part[p.adjncy[e]];
+                const int32_t b = p.part[p.adjncy[e] - p.id_base];
                 const int32_t w = p.ewgt[e];
                 if (b < 0 || b >= p.k) {
                     bad = 1;
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p) {
                 else if (rb > cur && rb != pv) nextb = rb;
             } else {
                 for (int32_t e = beg + gl; e < end; e += G) {
-                    const int32_t b = p.part[p.adjncy[e]];
+                    const int32_t b = p.part[p.adjncy[e] - p.id_base];
                     if (b < 0 || b >= p.k) continue;
                     if (b == cur) conn += p.ewgt[e];
                     else if (b > cur && b != pv) nextb = min(nextb, b);
@@ -237,7 +238,7 @@ kp_status check_eval_args(const kp_graph *g, const int32_t *part, int32_t k, dou
 
 // Evaluation with the accumulators in caller-provided device memory `acc`.
 kp_status cut_gain_with(const kp_graph *g, const int32_t *part, int32_t k, double eps, kp_cut_gain_out *out,
-                        cudaStream_t s, EvalAcc *acc, EvalAcc *host_acc) {
+                        cudaStream_t s, EvalAcc *acc, EvalAcc *host_acc, int32_t id_base = 0) {
     KP_TRY(check_eval_args(g, part, k, eps, out));
     KP_CUDA(cudaMemsetAsync(acc, 0, sizeof(EvalAcc), s));
     KP_CUDA(cudaMemsetAsync(out->block_w, 0, sizeof(int64_t) * (size_t)k, s));
@@ -245,6 +246,7 @@ kp_status cut_gain_with(const kp_graph *g, const int32_t *part, int32_t k, doubl
         CutGainParams p;
         p.n = g->n;
         p.k = k;
+        p.id_base = id_base;
         p.xadj = g->xadj;
         p.adjncy = g->adjncy;
         p.ewgt = g->ewgt;
@@ -341,6 +343,7 @@ kp_status cut_gain_noalloc_impl(const kp_graph *g, const int32_t *part, int32_t 
         CutGainParams p;
         p.n = g->n;
         p.k = k;
+        p.id_base = 0;
         p.xadj = g->xadj;
         p.adjncy = g->adjncy;
         p.ewgt = g->ewgt;
@@ -374,6 +377,25 @@ kp_status cut_gain_noalloc_impl(const kp_graph *g, const int32_t *part, int32_t 
     out->l_max = l_max_of(out->total_c, out->max_c, k, eps);
     out->imbalance = std::max<int64_t>(0, (int64_t)host_acc.max_bw - out->l_max);
     return KP_OK;
+}
+
+// Cut/gain of one graph of a batch union: `view` is the graph's slice (its
+// xadj and vwgt start at the graph's first node, adjncy and ewgt are the
+// union's arrays), neighbour ids are id_base higher than the graph's ids.
+kp_status cut_gain_slice(const kp_graph *view, int32_t id_base, const int32_t *part, int32_t k, double eps,
+                         kp_cut_gain_out *out, cudaStream_t s) {
+    KP_TRY(check_eval_args(view, part, k, eps, out));
+    EvalAcc *acc = nullptr;
+    KP_TRY(dev_alloc_n(&acc, 1, s));
+    thread_local EvalAcc *host_acc = nullptr;
+    if (!host_acc && cudaMallocHost((void **)&host_acc, sizeof(EvalAcc)) != cudaSuccess) {
+        host_acc = nullptr;
+        dev_free(acc, s);
+        return set_error(KP_ERR_OOM, "pinned host accumulator");
+    }
+    const kp_status st = cut_gain_with(view, part, k, eps, out, s, acc, host_acc, id_base);
+    dev_free(acc, s);
+    return st;
 }
 
 kp_status cut_gain_impl(const kp_graph *g, const int32_t *part, int32_t k, double eps, kp_cut_gain_out *out,

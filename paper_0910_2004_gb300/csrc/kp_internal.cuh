@@ -38,6 +38,7 @@ struct BatchSpec {
     int32_t num_graphs;
     const int32_t *node_offsets;   // device [num_graphs+1]: graph i is [off[i], off[i+1])
     const uint64_t *seeds;         // device [num_graphs] or null
+    const int32_t *stop_sizes = nullptr;   // device [num_graphs] or null
 };
 
 kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, kp_hierarchy **out,

@@ -53,7 +53,7 @@ __device__ void phase_level_begin(DevState *st, int level, const Work &w) {
                 act = 0;   // left the batch at an earlier level
             } else if (level > 0 && nc == np) {
                 w.glevels[g] = level;   // nothing matched: that copy is not a level
-            } else if (nc <= st->stop_size || level >= st->max_levels ||
+            } else if (nc <= (w.stops ? (int64_t)w.stops[g] : (int64_t)st->stop_size) || level >= st->max_levels ||
                        (level > 0 && nc * 1000 > np * (1000 - st->min_shrink_permille))) {
                 w.glevels[g] = level + 1;
             } else {
@@ -117,15 +117,15 @@ __device__ __forceinline__ int suitor_group(int32_t n, int32_t nnz) {
     return 32;
 }
 
-// G lanes per proposing node.  Start nodes are [0, n) (FROM_LIST = false)
-// or the parked list (FROM_LIST = true).  Every warp owns one contiguous range
-// of start nodes; its 32/G groups each follow one proposal chain (a node,
-// then whoever it displaced) and take the next start node of the range as
-// soon as their chain ends, so lanes stay busy until the range is used up.
-// With HEAVY > 0 a node whose row is longer than HEAVY entries is parked
-// instead of being scanned by so few lanes; the FROM_LIST pass (G = 32)
-// finishes those.  The order of proposals does not change the matching.
-template <int R, int G, int HEAVY, bool FROM_LIST>
+// G lanes per proposing node, start nodes [0, n).  Every warp owns one
+// contiguous range of start nodes; its 32/G groups each follow one proposal
+// chain (a node, then whoever it displaced) and take the next start node of
+// the range as soon as their chain ends, so lanes stay busy until the range
+// is used up.  A node whose row is longer than HEAVY entries is parked
+// instead of being scanned by so few lanes; the wide pass (one block per
+// search) finishes those.  The order of proposals does not change the
+// matching.
+template <int R, int G, int HEAVY>
 __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Counters *ctr, int32_t *err) {
     constexpr int NG = 32 / G;
     const unsigned gmask = group_mask<G>();
@@ -138,7 +138,7 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
     const int32_t *KP_RESTRICT ewgt = L.ewgt;
     int32_t *parked = w.list0;
     int32_t *parked_size = &ctr->list_size[0];
-    const int64_t count = FROM_LIST ? (int64_t)ld_relaxed_i32(parked_size) : (int64_t)L.n;
+    const int64_t count = L.n;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t chunk = (count + nwarps - 1) / nwarps;
@@ -156,7 +156,7 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
         if (need && pos < stop) {
             const int64_t avail = min((int64_t)NG, stop - pos);
             const int rank = __popc(need & below_leader);
-            if (cur < 0 && rank < avail) cur = FROM_LIST ? parked[pos + rank] : (int32_t)(pos + rank);
+            if (cur < 0 && rank < avail) cur = (int32_t)(pos + rank);
             pos += min((int64_t)__popc(need), avail);
         }
         if (__ballot_sync(0xffffffffu, cur >= 0) == 0) break;
@@ -168,7 +168,7 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
             continue;
         }
         const int32_t beg = KP_LDG(xadj + cur), end = KP_LDG(xadj + cur + 1);
-        if (HEAVY > 0 && end - beg > HEAVY) {   // park it for the wide pass
+        if (end - beg > HEAVY) {   // park it for the wide pass
             if (gl == 0) parked[atomicAdd(parked_size, 1)] = cur;
             cur = -1;
             continue;
@@ -251,19 +251,153 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
     }
 }
 
+// The wide pass: one block per search.  Blocks take parked nodes from the
+// list in turn (a counter, so long and short rows spread over the blocks)
+// and follow each node's proposal chain; every search scans the row with all
+// threads of the block and reduces the best neighbour through shared memory.
+// Rows of hubs (power-law graphs) are thousands of times longer than the
+// mean, so this keeps a hub's search from holding one warp for its whole
+// row while the rest of the GPU idles.
+template <int R>
+__device__ __forceinline__ void suitor_wide(const DevLevel &L, const Work &w, Counters *ctr, int32_t *err) {
+    constexpr int NW = MATCH_BLOCK / 32;
+    __shared__ uint64_t s_num[NW], s_den[NW], s_h[NW];
+    __shared__ int32_t s_u[NW], s_bw[NW];
+    __shared__ Offer s_snap[NW];
+    __shared__ int32_t s_cur;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t *parked = w.list0;
+    const int32_t count = ld_relaxed_i32(&ctr->list_size[0]);
+    int32_t cur = -1;                 // thread 0's chain
+    long long iters = 0;
+    unsigned long long fails = 0;
+    bool aborted = false;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            if (cur < 0 && !aborted) {
+                const int32_t i = atomicAdd(&ctr->list_size[1], 1);
+                cur = i < count ? parked[i] : -1;
+            }
+            if (cur >= 0 && ++iters > w.spin_limit) {   // a bound, not a wait
+                atomicOr(err, ERR_TIMEOUT);
+                cur = -1;
+                aborted = true;
+            }
+            s_cur = cur;
+        }
+        __syncthreads();
+        const int32_t c = s_cur;
+        if (c < 0) break;
+        const int32_t beg = KP_LDG(L.xadj + c), end = KP_LDG(L.xadj + c + 1);
+        const int32_t ac = rating_attr<R>(L.vwgt, L.outw, c);
+        const HashCtx hc = hash_ctx(w, L, c);
+        Cand best;
+        best.u = -1;
+        best.num = best.den = best.h = 0;
+        int32_t bw = 0;
+        Offer bsnap = {-1, 0, 0, 0};
+#pragma unroll 4
+        for (int32_t e = beg + (int32_t)threadIdx.x; e < end; e += MATCH_BLOCK) {
+            const int32_t v = KP_LDG(L.adjncy + e);
+            const int32_t wt = KP_LDG(L.ewgt + e);
+            const Offer so = ld_offer(w.offer + v);
+            Cand cd;
+            cd.u = v;
+            rating_ab<R>(wt, ac, so.au, cd.num, cd.den);
+            cd.h = edge_hash_in(hc, c, v);
+            bool eligible = so.s < 0;
+            if (!eligible) {
+                Cand a = cd, b;
+                a.u = c;
+                b.u = so.s;
+                rating_ab<R>(so.w, so.as, so.au, b.num, b.den);
+                b.h = edge_hash_in(hc, so.s, v);
+                eligible = better(a, b, v);
+            }
+            if (eligible && better(cd, best, c)) {
+                best = cd;
+                bw = wt;
+                bsnap = so;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            Cand o;
+            o.num = __shfl_xor_sync(0xffffffffu, best.num, off);
+            o.den = __shfl_xor_sync(0xffffffffu, best.den, off);
+            o.h = __shfl_xor_sync(0xffffffffu, best.h, off);
+            o.u = __shfl_xor_sync(0xffffffffu, best.u, off);
+            const int32_t ow = __shfl_xor_sync(0xffffffffu, bw, off);
+            Offer os;
+            os.s = __shfl_xor_sync(0xffffffffu, bsnap.s, off);
+            os.w = __shfl_xor_sync(0xffffffffu, bsnap.w, off);
+            os.as = __shfl_xor_sync(0xffffffffu, bsnap.as, off);
+            os.au = __shfl_xor_sync(0xffffffffu, bsnap.au, off);
+            if (better(o, best, c)) {
+                best = o;
+                bw = ow;
+                bsnap = os;
+            }
+        }
+        if (lane == 0) {
+            s_num[warp] = best.num;
+            s_den[warp] = best.den;
+            s_h[warp] = best.h;
+            s_u[warp] = best.u;
+            s_bw[warp] = bw;
+            s_snap[warp] = bsnap;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int i = 1; i < NW; i++) {
+                Cand o;
+                o.num = s_num[i];
+                o.den = s_den[i];
+                o.h = s_h[i];
+                o.u = s_u[i];
+                if (better(o, best, c)) {
+                    best = o;
+                    bw = s_bw[i];
+                    bsnap = s_snap[i];
+                }
+            }
+            cur = -1;
+            if (best.u >= 0) {
+                Offer mine;
+                mine.s = c;
+                mine.w = bw;
+                mine.as = ac;
+                mine.au = bsnap.au;
+                if (cas_offer(w.offer + best.u, bsnap, mine)) {
+                    cur = bsnap.s;   // the displaced suitor searches next (or -1)
+                } else {
+                    cur = c;         // the record changed: search again
+                    fails++;
+                }
+            }
+        }
+        // thread 0 writes s_cur only after the barrier at the top of the next
+        // search, which every thread reaches after it is done with this one
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&ctr->searches, (unsigned long long)iters);
+        if (fails) atomicAdd(&ctr->failed_cas, fails);
+    }
+}
+
 template <int R, bool FROM_LIST>
 __device__ void phase_suitor(DevState *st, int level, const Work &w) {
     const DevLevel L = st->lv[level];
     if (!(L.flags & LV_ACTIVE)) return;
     Counters *ctr = &st->ctr[level];
     if (FROM_LIST) {
-        suitor_body<R, 32, 0, true>(L, w, ctr, &st->err);
+        suitor_wide<R>(L, w, ctr, &st->err);
     } else {
         switch (suitor_group(L.n, L.nnz)) {
-        case 1: suitor_body<R, 1, 32, false>(L, w, ctr, &st->err); break;
-        case 4: suitor_body<R, 4, 128, false>(L, w, ctr, &st->err); break;
-        case 8: suitor_body<R, 8, 512, false>(L, w, ctr, &st->err); break;
-        default: suitor_body<R, 32, 0, false>(L, w, ctr, &st->err); break;
+        case 1: suitor_body<R, 1, 32>(L, w, ctr, &st->err); break;
+        case 4: suitor_body<R, 4, 128>(L, w, ctr, &st->err); break;
+        case 8: suitor_body<R, 8, 512>(L, w, ctr, &st->err); break;
+        default: suitor_body<R, 32, 2048>(L, w, ctr, &st->err); break;
         }
     }
     // a proposal chain that ran out ends the coarsening after this level (the

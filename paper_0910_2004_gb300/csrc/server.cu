@@ -1,0 +1,491 @@
+// Request server for the serving pattern: coarsen + partition + project +
+// cut/gain requests arrive over time; each worker (a host thread with its own
+// non-blocking CUDA stream) takes the oldest waiting request once its
+// estimated device footprint fits the HBM budget, merges further small
+// waiting requests into the same batched call, and runs the whole path on
+// its stream, so the work of several groups overlaps on the device.  Results
+// stay resident on the device until the client releases them; released
+// memory lets waiting requests in.  A request's result does not depend on the
+// group it ran in: batched coarsening coarsens every graph exactly as alone.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "kp_internal.cuh"
+
+namespace kp {
+
+kp_status project_impl(const kp_hierarchy *h, const int32_t *coarse_part, int32_t *fine_part, cudaStream_t s);
+kp_status project_batch_impl(const kp_hierarchy *h, const int32_t *coarse_part, const int32_t *coarse_offsets,
+                             int32_t *fine_part, cudaStream_t s);
+kp_status batch_coarsest_impl(const kp_hierarchy *h, int32_t *sizes, cudaStream_t s);
+kp_status cut_gain_impl(const kp_graph *g, const int32_t *part, int32_t k, double eps, kp_cut_gain_out *out,
+                        cudaStream_t s);
+kp_status cut_gain_slice(const kp_graph *view, int32_t id_base, const int32_t *part, int32_t k, double eps,
+                         kp_cut_gain_out *out, cudaStream_t s);
+
+namespace {
+
+uint64_t mix64(uint64_t x) {
+    uint64_t z = x + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+// The initial partition the server applies to a coarsest graph (the stand-in
+// for initial partitioning): a seeded permutation (Fisher-Yates driven by
+// splitmix64) dealt round-robin to blocks 0..k-1.
+void server_initial_partition(int32_t n, int32_t k, uint64_t seed, int32_t *part) {
+    std::vector<int32_t> perm((size_t)n);
+    for (int32_t i = 0; i < n; i++) perm[(size_t)i] = i;
+    uint64_t state = seed;
+    for (int32_t i = n - 1; i > 0; i--) {
+        state += 0x9e3779b97f4a7c15ull;
+        const int32_t j = (int32_t)(mix64(state) % (uint64_t)(i + 1));
+        std::swap(perm[(size_t)i], perm[(size_t)j]);
+    }
+    for (int32_t i = 0; i < n; i++) part[perm[(size_t)i]] = i % k;
+}
+
+}  // namespace kp
+
+using namespace kp;
+
+struct ServerGroup;
+
+struct ServerRequest {
+    uint64_t id = 0;
+    std::vector<int32_t> xadj, adjncy, ewgt, vwgt;
+    int32_t n = 0, nnz = 0;
+    kp_request_params params{};
+    int64_t footprint = 0;  // while running
+    int64_t resident = 0;   // after the run, until release
+    kp_request_result res{};
+    std::string error;
+    std::vector<int32_t> coarse_part;
+    ServerGroup *grp = nullptr;
+    int32_t node_base = 0;   // first node in the group's graph
+    int32_t block_base = 0;  // first block weight slot in the group's buffer
+    bool done = false;
+    bool released = false;
+};
+
+struct ServerGroup {
+    std::vector<ServerRequest *> reqs;
+    kp_hierarchy *h = nullptr;
+    cudaStream_t s = nullptr;
+    std::vector<void *> dev;
+    int32_t *d_fine = nullptr, *d_target = nullptr;
+    int64_t *d_gain = nullptr, *d_bw = nullptr;
+    int64_t footprint = 0;  // charged against the budget now
+    int64_t resident = 0;
+    int32_t live = 0;
+    int64_t id = 0;
+    int32_t launches = 0;
+};
+
+struct kp_server {
+    kp_server_config cfg{};
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<ServerRequest *> queue;
+    std::map<uint64_t, ServerRequest *> reqs;
+    uint64_t next_id = 1;
+    int64_t next_group = 1;
+    int64_t used = 0;
+    bool stopping = false;
+    int device = 0;
+    std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;
+    std::chrono::steady_clock::time_point t0;
+    double now_us() const {
+        return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+// Device bytes of one request: what stays resident until release (the input
+// graph, the arena holding the coarse levels and maps, fine partition, gains,
+// targets) and the engine's level-0 scratch, freed when coarsening returns.
+int64_t resident_bytes(int64_t n, int64_t nnz) { return 8 * n + 8 * nnz + 64 * n + 32 * nnz + 16 * n + (1 << 20); }
+int64_t scratch_bytes(int64_t n, int64_t nnz) { return 52 * n + 16 * nnz + (1 << 20); }
+
+// Stream-ordered frees on the group's stream; the caller does not wait.
+void free_group(ServerGroup *g) {
+    if (g->h) {
+        for (void *p : g->h->allocations) dev_free(p, g->s);
+        delete g->h;
+        g->h = nullptr;
+    }
+    for (void *p : g->dev) dev_free(p, g->s);
+    g->dev.clear();
+}
+
+template <class T>
+kp_status galloc(ServerGroup *g, T **p, int64_t count) {
+    KP_TRY(dev_alloc_n(p, count, g->s));
+    g->dev.push_back(*p);
+    return KP_OK;
+}
+
+kp_status run_group(kp_server *S, ServerGroup *g) {
+    cudaStream_t s = g->s;
+    const size_t G = g->reqs.size();
+    kp_options o = S->cfg.options;
+    o.stop_size = g->reqs[0]->params.stop_size;   // a batch takes every graph's own
+    // the group's graph: one request, or the disjoint union of several
+    int64_t n = 0, nnz = 0, kt = 0;
+    std::vector<int32_t> off(G + 1, 0), eoff(G + 1, 0);
+    for (size_t i = 0; i < G; i++) {
+        ServerRequest *r = g->reqs[i];
+        r->node_base = (int32_t)n;
+        r->block_base = (int32_t)kt;
+        n += r->n;
+        nnz += r->nnz;
+        kt += r->params.k;
+        off[i + 1] = (int32_t)n;
+        eoff[i + 1] = (int32_t)nnz;
+    }
+    if (n >= (1ll << 31) || nnz >= (1ll << 31)) return set_error(KP_ERR_OVERFLOW, "group too large");
+    std::vector<int32_t> hx((size_t)n + 1), ha((size_t)nnz), hw((size_t)nnz), hc((size_t)n);
+    for (size_t i = 0; i < G; i++) {
+        ServerRequest *r = g->reqs[i];
+        for (int32_t v = 0; v <= r->n; v++) hx[(size_t)off[i] + v] = r->xadj[(size_t)v] + eoff[i];
+        for (int32_t e = 0; e < r->nnz; e++) {
+            ha[(size_t)eoff[i] + e] = r->adjncy[(size_t)e] + off[i];
+            hw[(size_t)eoff[i] + e] = r->ewgt[(size_t)e];
+        }
+        std::memcpy(hc.data() + off[i], r->vwgt.data(), sizeof(int32_t) * (size_t)r->n);
+    }
+    int32_t *dx, *da, *dw, *dc, *doff, *dstops;
+    uint64_t *dseeds;
+    KP_TRY(galloc(g, &dx, n + 1));
+    KP_TRY(galloc(g, &da, nnz));
+    KP_TRY(galloc(g, &dw, nnz));
+    KP_TRY(galloc(g, &dc, n));
+    KP_TRY(galloc(g, &doff, (int64_t)G + 1));
+    KP_TRY(galloc(g, &dseeds, (int64_t)G));
+    KP_TRY(galloc(g, &dstops, (int64_t)G));
+    KP_TRY(galloc(g, &g->d_fine, n));
+    KP_TRY(galloc(g, &g->d_target, n));
+    KP_TRY(galloc(g, &g->d_gain, n));
+    KP_TRY(galloc(g, &g->d_bw, kt));
+    std::vector<uint64_t> seeds(G);
+    std::vector<int32_t> stops(G);
+    for (size_t i = 0; i < G; i++) {
+        seeds[i] = g->reqs[i]->params.seed;
+        stops[i] = g->reqs[i]->params.stop_size;
+    }
+    KP_CUDA(cudaMemcpyAsync(dx, hx.data(), sizeof(int32_t) * hx.size(), cudaMemcpyHostToDevice, s));
+    if (nnz > 0) {
+        KP_CUDA(cudaMemcpyAsync(da, ha.data(), sizeof(int32_t) * ha.size(), cudaMemcpyHostToDevice, s));
+        KP_CUDA(cudaMemcpyAsync(dw, hw.data(), sizeof(int32_t) * hw.size(), cudaMemcpyHostToDevice, s));
+    }
+    if (n > 0) KP_CUDA(cudaMemcpyAsync(dc, hc.data(), sizeof(int32_t) * hc.size(), cudaMemcpyHostToDevice, s));
+    KP_CUDA(cudaMemcpyAsync(doff, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, s));
+    KP_CUDA(cudaMemcpyAsync(dseeds, seeds.data(), sizeof(uint64_t) * G, cudaMemcpyHostToDevice, s));
+    KP_CUDA(cudaMemcpyAsync(dstops, stops.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s));
+    kp_graph ug = {(int32_t)n, (int32_t)nnz, dx, da, dw, dc};
+
+    // coarsen, partition the coarsest graphs, project
+    std::vector<int32_t> csz(G), cpart, coff(G + 1, 0);
+    if (G == 1) {
+        o.seed = seeds[0];
+        KP_TRY(coarsen_impl(&ug, &o, s, &g->h));
+        csz[0] = g->h->levels.back().n;
+    } else {
+        BatchSpec b{(int32_t)G, doff, dseeds, dstops};
+        KP_TRY(coarsen_impl(&ug, &o, s, &g->h, &b));
+        KP_TRY(batch_coarsest_impl(g->h, csz.data(), s));
+    }
+    // coarsening, coarsest sizes (batch), projection
+    g->launches = g->h->total.launches + (G > 1 ? 1 : 0) + 1;
+    for (size_t i = 0; i < G; i++) coff[i + 1] = coff[i] + csz[i];
+    cpart.resize((size_t)std::max(coff[G], 1));
+    for (size_t i = 0; i < G; i++) {
+        ServerRequest *r = g->reqs[i];
+        server_initial_partition(csz[i], r->params.k, r->params.seed, cpart.data() + coff[i]);
+        r->coarse_part.assign(cpart.begin() + coff[i], cpart.begin() + coff[i + 1]);
+        r->res.coarsest_n = csz[i];
+        r->res.num_levels = G == 1 ? (int32_t)g->h->levels.size() : g->h->glevels[i];
+    }
+    int32_t *dcp, *dco;
+    KP_TRY(galloc(g, &dcp, std::max(coff[G], 1)));
+    KP_TRY(galloc(g, &dco, (int64_t)G + 1));
+    if (coff[G] > 0)
+        KP_CUDA(cudaMemcpyAsync(dcp, cpart.data(), sizeof(int32_t) * (size_t)coff[G], cudaMemcpyHostToDevice, s));
+    KP_CUDA(cudaMemcpyAsync(dco, coff.data(), sizeof(int32_t) * coff.size(), cudaMemcpyHostToDevice, s));
+    if (G == 1) KP_TRY(project_impl(g->h, dcp, g->d_fine, s));
+    else KP_TRY(project_batch_impl(g->h, dcp, dco, g->d_fine, s));
+
+    // evaluate every request on its own graph
+    for (size_t i = 0; i < G; i++) {
+        ServerRequest *r = g->reqs[i];
+        kp_graph view = {r->n, r->nnz, dx + off[i], da, dw, dc + off[i]};
+        kp_cut_gain_out out;
+        std::memset(&out, 0, sizeof out);
+        out.block_w = g->d_bw + r->block_base;
+        out.gain = g->d_gain + off[i];
+        out.target = g->d_target + off[i];
+        KP_TRY(cut_gain_slice(&view, off[i], g->d_fine + off[i], r->params.k, r->params.eps, &out, s));
+        r->res.cut = out.cut;
+        r->res.total_c = out.total_c;
+        r->res.l_max = out.l_max;
+        r->res.imbalance = out.imbalance;
+        r->res.group_size = (int32_t)G;
+        g->launches += 2;   // evaluation: gains + block maximum
+    }
+    KP_CUDA(cudaStreamSynchronize(s));
+    return KP_OK;
+}
+
+bool fits(const kp_server *S, const ServerRequest *r) {
+    return S->used == 0 || S->used + r->footprint <= S->cfg.hbm_budget_bytes;
+}
+
+void worker_main(kp_server *S, int wi) {
+    cudaSetDevice(S->device);
+    for (;;) {
+        ServerGroup *g = new ServerGroup();
+        g->s = S->streams[(size_t)wi];
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] { return S->stopping || (!S->queue.empty() && fits(S, S->queue.front())); });
+            if (S->stopping) {
+                delete g;
+                return;
+            }
+            ServerRequest *head = S->queue.front();
+            S->queue.pop_front();
+            g->reqs.push_back(head);
+            g->footprint = head->footprint;
+            g->resident = head->resident;
+            // merge further small waiting requests that fit
+            if (head->n <= S->cfg.batch_max_nodes) {
+                for (auto it = S->queue.begin(); it != S->queue.end() && (int)g->reqs.size() < S->cfg.max_batch;) {
+                    ServerRequest *r = *it;
+                    if (r->n <= S->cfg.batch_max_nodes &&
+                        S->used + g->footprint + r->footprint <= S->cfg.hbm_budget_bytes) {
+                        g->reqs.push_back(r);
+                        g->footprint += r->footprint;
+                        g->resident += r->resident;
+                        it = S->queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+            }
+            S->used += g->footprint;
+            const double t = S->now_us();
+            for (ServerRequest *r : g->reqs) {
+                r->res.t_admit_us = t;
+                r->grp = g;
+            }
+            g->live = (int32_t)g->reqs.size();
+            g->id = S->next_group++;
+        }
+        kp_status st;
+        try {
+            st = run_group(S, g);
+        } catch (const std::bad_alloc &) {
+            st = set_error(KP_ERR_OOM, "host allocation failed");
+        }
+        std::string msg = st == KP_OK ? "" : kp_last_error();
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            // the scratch is back in the pool: charge only what stays
+            S->used -= g->footprint - g->resident;
+            g->footprint = g->resident;
+            const double t = S->now_us();
+            for (ServerRequest *r : g->reqs) {
+                r->res.group_id = g->id;
+                r->res.launches = g->launches;
+                r->res.status = st;
+                r->error = msg;
+                r->res.t_done_us = t;
+                r->done = true;
+            }
+        }
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+}
+
+ServerRequest *find(kp_server *S, uint64_t id) {
+    auto it = S->reqs.find(id);
+    return it == S->reqs.end() ? nullptr : it->second;
+}
+
+}  // namespace
+
+extern "C" {
+
+kp_status kp_server_create(const kp_server_config *cfg, kp_server **out) {
+    if (!cfg || !out) return set_error(KP_ERR_INVALID, "null argument");
+    if (cfg->workers < 1 || cfg->workers > 64 || cfg->max_batch < 1 || cfg->hbm_budget_bytes <= 0)
+        return set_error(KP_ERR_INVALID, "bad server configuration");
+    kp_server *S = new kp_server();
+    S->cfg = *cfg;
+    S->t0 = std::chrono::steady_clock::now();
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
+        delete S;
+        return cuda_error(cudaGetLastError(), "cudaGetDevice");
+    }
+    for (int i = 0; i < cfg->workers; i++) {
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            for (cudaStream_t q : S->streams) cudaStreamDestroy(q);
+            delete S;
+            return cuda_error(cudaGetLastError(), "cudaStreamCreate");
+        }
+        S->streams.push_back(s);
+    }
+    try {
+        for (int i = 0; i < cfg->workers; i++) S->workers.emplace_back(worker_main, S, i);
+    } catch (...) {
+        kp_server_destroy(S);
+        return set_error(KP_ERR_INVALID, "cannot start worker threads");
+    }
+    *out = S;
+    return KP_OK;
+}
+
+kp_status kp_server_submit(kp_server *S, const kp_graph *g, const kp_request_params *p, uint64_t *id) {
+    if (!S || !g || !p || !id) return set_error(KP_ERR_INVALID, "null argument");
+    if (g->n < 0 || g->nnz < 0 || (g->n > 0 && (!g->xadj || !g->vwgt)) || (g->nnz > 0 && (!g->adjncy || !g->ewgt)))
+        return set_error(KP_ERR_INVALID, "bad graph");
+    if (p->k < 1 || !(p->eps >= 0.0) || p->eps > 1000.0) return set_error(KP_ERR_INVALID, "bad request parameters");
+    const double t_in = S->now_us();   // latency includes the host copy
+    ServerRequest *r = new ServerRequest();
+    try {
+        r->n = g->n;
+        r->nnz = g->nnz;
+        r->xadj.assign(g->xadj, g->xadj + g->n + 1);
+        r->adjncy.assign(g->adjncy, g->adjncy + g->nnz);
+        r->ewgt.assign(g->ewgt, g->ewgt + g->nnz);
+        r->vwgt.assign(g->vwgt, g->vwgt + g->n);
+    } catch (...) {
+        delete r;
+        return set_error(KP_ERR_OOM, "host copy of the request");
+    }
+    r->params = *p;
+    r->resident = resident_bytes(g->n, g->nnz);
+    r->footprint = r->resident + scratch_bytes(g->n, g->nnz);
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stopping) {
+            delete r;
+            return set_error(KP_ERR_INVALID, "server is stopping");
+        }
+        r->id = S->next_id++;
+        r->res.t_submit_us = t_in;
+        S->reqs[r->id] = r;
+        S->queue.push_back(r);
+        *id = r->id;
+    }
+    S->cv_work.notify_all();
+    return KP_OK;
+}
+
+kp_status kp_server_poll(kp_server *S, uint64_t id, int32_t *done, kp_request_result *res) {
+    if (!S || !done) return set_error(KP_ERR_INVALID, "null argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    ServerRequest *r = find(S, id);
+    if (!r) return set_error(KP_ERR_INVALID, "unknown request");
+    *done = r->done ? 1 : 0;
+    if (res) *res = r->res;
+    return KP_OK;
+}
+
+kp_status kp_server_wait(kp_server *S, uint64_t id, kp_request_result *res) {
+    if (!S) return set_error(KP_ERR_INVALID, "null argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    ServerRequest *r = find(S, id);
+    if (!r) return set_error(KP_ERR_INVALID, "unknown request");
+    S->cv_done.wait(lk, [&] { return r->done; });
+    if (res) *res = r->res;
+    if (r->res.status != KP_OK) return set_error(r->res.status, r->error);
+    return KP_OK;
+}
+
+kp_status kp_server_fetch(kp_server *S, uint64_t id, int32_t *fine_part, int64_t *gain, int32_t *target,
+                          int32_t *coarse_part) {
+    if (!S) return set_error(KP_ERR_INVALID, "null argument");
+    ServerRequest *r;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        r = find(S, id);
+        if (!r) return set_error(KP_ERR_INVALID, "unknown request");
+        if (!r->done || r->released) return set_error(KP_ERR_INVALID, "request not finished or released");
+        if (r->res.status != KP_OK) return set_error(r->res.status, r->error);
+    }
+    ServerGroup *g = r->grp;
+    const size_t n = (size_t)r->n;
+    if (fine_part && n) KP_CUDA(cudaMemcpy(fine_part, g->d_fine + r->node_base, 4 * n, cudaMemcpyDeviceToHost));
+    if (gain && n) KP_CUDA(cudaMemcpy(gain, g->d_gain + r->node_base, 8 * n, cudaMemcpyDeviceToHost));
+    if (target && n) KP_CUDA(cudaMemcpy(target, g->d_target + r->node_base, 4 * n, cudaMemcpyDeviceToHost));
+    if (coarse_part) std::memcpy(coarse_part, r->coarse_part.data(), 4 * r->coarse_part.size());
+    return KP_OK;
+}
+
+kp_status kp_server_release(kp_server *S, uint64_t id) {
+    if (!S) return set_error(KP_ERR_INVALID, "null argument");
+    ServerGroup *to_free = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        ServerRequest *r = find(S, id);
+        if (!r) return set_error(KP_ERR_INVALID, "unknown request");
+        if (!r->done) return set_error(KP_ERR_INVALID, "request not finished");
+        if (!r->released) {
+            r->released = true;
+            ServerGroup *g = r->grp;
+            if (g && --g->live == 0) {
+                S->used -= g->footprint;
+                to_free = g;
+            }
+        }
+        S->reqs.erase(id);
+        delete r;
+    }
+    if (to_free) {
+        free_group(to_free);
+        delete to_free;
+    }
+    S->cv_work.notify_all();
+    return KP_OK;
+}
+
+void kp_server_destroy(kp_server *S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stopping = true;
+    }
+    S->cv_work.notify_all();
+    for (auto &t : S->workers) t.join();
+    std::vector<ServerGroup *> groups;
+    for (auto &kv : S->reqs) {
+        ServerRequest *r = kv.second;
+        if (r->grp && std::find(groups.begin(), groups.end(), r->grp) == groups.end()) groups.push_back(r->grp);
+        delete r;
+    }
+    for (ServerGroup *g : groups) {
+        free_group(g);
+        delete g;
+    }
+    for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
+    delete S;
+}
+
+}  // extern "C"

@@ -67,12 +67,12 @@ namespace {
 template <int R, bool SUITOR>
 kp_status launch_tail_rs(DevState *st, const Work &w, int first, int last, int32_t n_bound, int32_t epoch0,
                          cudaStream_t s) {
-    static int occ = -1;
-    if (occ < 0) {
+    static const int occ = [] {
         int o = 0;
-        KP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tail<R, SUITOR>, MATCH_BLOCK, 0));
-        occ = o > 0 ? o : 1;
-    }
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_tail<R, SUITOR>, MATCH_BLOCK, 0) != cudaSuccess)
+            o = 1;
+        return o > 0 ? o : 1;
+    }();
     const int64_t want = ((int64_t)std::max<int32_t>(n_bound, 1) + 2047) / 2048;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)occ * num_sms()));
     DevState *a0 = st;

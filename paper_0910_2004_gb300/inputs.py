@@ -29,6 +29,7 @@ __all__ = [
     "CSRGraph", "from_edges", "grid2d", "grid3d", "rgg2d", "rmat",
     "random_small_graph", "path_graph", "star_graph", "batch_rgg_sizes",
     "random_balanced_partition", "random_partition", "union_graph", "rgg2d_batch", "batch_partition",
+    "rmat_torch", "rgg2d_torch", "served_mix",
 ]
 
 
@@ -347,3 +348,70 @@ def random_partition(n: int, k: int, seed: int) -> np.ndarray:
     """Uniformly random block per node (not balanced)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.integers(0, k, size=n).astype(np.int32)
+
+
+def _csr_from_edges_torch(n: int, lo, hi, w, name: str) -> CSRGraph:
+    """Symmetric host CSR (int32, rows sorted) from undirected edges lo < hi
+    held as torch tensors."""
+    import torch
+    src = torch.cat([lo, hi])
+    dst = torch.cat([hi, lo])
+    ww = torch.cat([w, w])
+    perm = torch.argsort(src * max(n, 1) + dst)
+    src, dst, ww = src[perm], dst[perm], ww[perm]
+    xadj = torch.zeros(n + 1, dtype=torch.int64, device=src.device)
+    xadj[1:] = torch.cumsum(torch.bincount(src, minlength=n), 0)
+    return CSRGraph(xadj.int().cpu().numpy(), dst.int().cpu().numpy(), ww.int().cpu().numpy(),
+                    np.ones(n, dtype=np.int32), name)
+
+
+def rmat_torch(scale: int, seed: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+               device: str = "cuda") -> CSRGraph:
+    """R-MAT graph as rmat() builds it (edge_factor * 2^scale quadrant-
+    recursive samples, symmetrised, self loops dropped, duplicates merged
+    into integer weights), drawn with torch on `device` for large scales;
+    returned as host arrays.  Same distribution as rmat(), other draws."""
+    import torch
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    n = 1 << scale
+    M = edge_factor * n
+    u = torch.zeros(M, dtype=torch.int64, device=dev)
+    v = torch.zeros(M, dtype=torch.int64, device=dev)
+    for bit in range(scale):
+        r = torch.rand(M, generator=gen, device=dev)
+        ubit = r >= a + b
+        vbit = ((r >= a) & (r < a + b)) | (r >= a + b + c)
+        u |= ubit.long() << bit
+        v |= vbit.long() << bit
+    keep = u != v
+    u, v = u[keep], v[keep]
+    key, cnt = torch.unique(torch.minimum(u, v) * n + torch.maximum(u, v), return_counts=True)
+    return _csr_from_edges_torch(n, key // n, key % n, cnt, f"rmat_s{scale}_seed{seed}")
+
+
+def rgg2d_torch(n: int, seed: int, mean_degree: float = 6.0, device: str = "cuda") -> CSRGraph:
+    """2D random geometric graph with unit weights (as rgg2d), built with
+    torch on `device`; returned as host arrays."""
+    xadj, adj, ew, vw, _ = rgg2d_batch([n], seed, mean_degree=mean_degree, wmax=1, device=device)
+    return CSRGraph(xadj.cpu().numpy(), adj.cpu().numpy(), ew.cpu().numpy(), vw.cpu().numpy(),
+                    f"rgg2d_n{n}_s{seed}")
+
+
+def served_mix(scales=range(12, 23), seed: int = 1, device: str = "cuda"):
+    """The request pool of the serving workload: for every scale s, a 2D
+    5-point grid and a 3D 7-point grid with about 2^s nodes, a 2D random
+    geometric graph with 2^s nodes (mean degree 6) and an R-MAT graph of
+    scale s (a=0.57, b=0.19, c=0.19, edge factor 16, duplicates merged into
+    integer weights); unit node weights.  Returns a list of (family, scale,
+    CSRGraph)."""
+    pool = []
+    for s in scales:
+        side2 = int(round(2 ** (s / 2)))
+        side3 = int(round(2 ** (s / 3)))
+        pool.append(("grid2d", s, grid2d(side2, (1 << s) // side2)))
+        pool.append(("grid3d", s, grid3d(side3, side3, max(1, (1 << s) // (side3 * side3)))))
+        pool.append(("rgg2d", s, rgg2d_torch(1 << s, seed * 1000 + s, device=device)))
+        pool.append(("rmat", s, rmat_torch(s, seed * 1000 + s, device=device)))
+    return pool

@@ -41,16 +41,16 @@ def mixed_graphs(seed):
     return [gs[i] for i in order]
 
 
-def check_batch(graphs, seeds, rating, stop, matcher, tail, max_levels=64):
+def check_batch(graphs, seeds, rating, stop, matcher, tail, max_levels=64, stops=None):
     import torch
     U, off = I.union_graph(graphs)
     dg = B().DeviceGraph.from_csr(U)
-    h = B().coarsen_batch(dg, off, seeds, rating=rating, stop_size=stop, matcher=matcher, tail_nodes=tail,
-                          max_levels=max_levels)
+    h = B().coarsen_batch(dg, off, seeds, stop_sizes=stops, rating=rating, stop_size=stop, matcher=matcher,
+                          tail_nodes=tail, max_levels=max_levels)
     levels = h.graph_levels()
     refs = []
     for gi, g in enumerate(graphs):
-        ref = O.coarsen(g, rating, int(seeds[gi]), stop, max_levels=max_levels)
+        ref = O.coarsen(g, rating, int(seeds[gi]), stop if stops is None else int(stops[gi]), max_levels=max_levels)
         refs.append(ref)
         assert levels[gi] == len(ref.levels), (gi, g.name, levels[gi], [l.n for l in ref.levels])
         for l, rl in enumerate(ref.levels):
@@ -78,6 +78,15 @@ def test_placement_does_not_matter_and_level_cap():
     rev = list(reversed(graphs))
     check_batch(rev, seeds[::-1].copy(), "expansion*2", 2, "suitor", 0)
     check_batch(graphs, seeds, "weight", 2, "suitor", 0, max_levels=2)
+
+
+@pytest.mark.parametrize("matcher", ["suitor", "handshake"])
+def test_per_graph_stop_sizes(matcher):
+    graphs = mixed_graphs(11)
+    seeds = np.arange(len(graphs), dtype=np.uint64) * 31 + 2
+    stops = np.random.default_rng(4).choice([1, 2, 6, 40, 1000], size=len(graphs)).astype(np.int32)
+    check_batch(graphs, seeds, "expansion*2", 6, matcher, 0, stops=stops)
+    check_batch(graphs, seeds, "innerOuter", 6, matcher, -1, stops=stops)
 
 
 def test_rgg_batch_log_uniform_sizes_and_projection():

@@ -71,9 +71,9 @@ def check_eval(dg, g, part, k, eps):
     return got
 
 
-def full_path(g, rating, seed, stop, k, eps=0.03, part_seed=1, matcher="suitor"):
+def full_path(g, rating, seed, stop, k, eps=0.03, part_seed=1, matcher="suitor", tail=0):
     import torch
-    h, dg, levels, maps = run_gpu(g, rating=rating, seed=seed, stop_size=stop, matcher=matcher)
+    h, dg, levels, maps = run_gpu(g, rating=rating, seed=seed, stop_size=stop, matcher=matcher, tail_nodes=tail)
     ref = O.coarsen(g, rating, seed, stop)
     assert_same(levels, maps, ref, g.name)
     cpart = I.random_balanced_partition(ref.levels[-1].n, k, seed=part_seed)
@@ -212,6 +212,19 @@ def test_star_hub_rows():
     for r in ["expansion*2", "innerOuter", "weight"]:
         for m in MATCHERS:
             full_path(g, r, 11, 4, 3, matcher=m)
+
+
+@pytest.mark.parametrize("tail", [0, -1])
+@pytest.mark.parametrize("matcher", MATCHERS)
+def test_power_law_hub_rows(matcher, tail):
+    """R-MAT graphs: hub rows thousands of times longer than the mean take
+    the block-per-search pass, at every mean degree (lanes per node 4 and
+    32); with tail=-1 every level runs in separate launches."""
+    for g, r in [(I.rmat(14, 8), "expansion*2"), (I.rmat(13, 6, edge_factor=256), "expansion*2"),
+                 (I.rmat(13, 9, edge_factor=256), "innerOuter")]:
+        d = np.diff(g.xadj)
+        assert d.max() > 2048
+        full_path(g, r, 5, 40, 4, matcher=matcher, tail=tail)
 
 
 @pytest.mark.parametrize("matcher", MATCHERS)
