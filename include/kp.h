@@ -116,7 +116,7 @@ typedef enum {
  *   arena_bytes          initial size of the device arena that holds the
  *                        coarse levels (0: sized from the input); the
  *                        arena grows automatically when a level does not fit
- *   tail_nodes           levels with at most this many nodes and at most 16
+ *   tail_nodes           levels with at most this many nodes and at most 8
  *                        times as many directed edges are contracted
  *                        together in one persistent launch (0: 262144;
  *                        -1: never); results do not depend on it */

@@ -288,7 +288,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         for (int level = start; level < level_end; level++) {
             // the rest in one persistent launch once the level is small (dense
             // small levels, as in power-law graphs, stay with the wide grids)
-            if (n_bound <= tail_nodes && nnz_bound <= 16ll * tail_nodes) {
+            if (n_bound <= tail_nodes && nnz_bound <= 8ll * tail_nodes) {
                 timer.mark(KP_PHASE_TAIL, level);
                 const int32_t before = launches;
                 st = launch_tail(dst, w, rating, o->matcher, level, level_end, n_bound, epoch, s, &launches);

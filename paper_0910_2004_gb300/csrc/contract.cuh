@@ -497,106 +497,123 @@ static __device__ void contract_block_smem(const CView &p, int32_t x, int32_t *k
     __syncthreads();
 }
 
-// Rows longer than MID_MAX gathered entries: one block.
-// 1. gather (map(u), omega) without the contracted edge into tmp at off[x]
+// Rows longer than MID_MAX gathered entries: one block, RADIX_ITEMS entries
+// per thread and chunk.
+// 1. gather (map(u), omega) without the contracted edge into the slot at
+//    off[x] (tmp or big, chosen so that the last pass ends in big), counting
+//    the digits of every radix pass on the way
 // 2. stable LSD radix sort by coarse neighbour, 8 bits per pass, ping-pong
-//    between tmp and big at the same offsets (an extra copy makes the number
-//    of moves odd, so the sorted row ends in big); each chunk of one element
-//    per thread is ranked with warp match masks and per-warp digit counts
-// 3. merge equal neighbours from big back into tmp (run sums by atomics)
+//    between tmp and big; a chunk is ranked warp by warp (match masks, item
+//    by item in index order) and the warps' digit counts are scanned
+// 3. merge equal neighbours from big into tmp (run heads by ballots, run
+//    sums by atomics)
+constexpr int RADIX_ITEMS = 8;
+constexpr int RADIX_CHUNK = CONTRACT_BLOCK * RADIX_ITEMS;
+
 struct BigSmem {
+    int32_t hist[4][256];
     int32_t base[256];
     int32_t chunk_tot[256];
     int32_t wcnt[CONTRACT_BLOCK / 32][256];
+    int32_t wsum[CONTRACT_BLOCK / 32];
     int32_t s_red[CONTRACT_BLOCK / 32];
     int32_t s_carry;
 };
 
 static __device__ void contract_block_radix(const CView &p, int32_t x, int passes, BigSmem &sm) {
+    static_assert(CONTRACT_BLOCK == 256, "one thread per digit");
     constexpr int NW = CONTRACT_BLOCK / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
     int32_t xa, da, xb, db;
     members(p, x, xa, da, xb, db);
     const int32_t L = da + db;
     const int32_t o = p.off[x];
+    int32_t *src_k = (passes & 1) ? p.tmp_adj + o : p.big_adj + o;
+    int32_t *src_v = (passes & 1) ? p.tmp_w + o : p.big_w + o;
+    int32_t *dst_k = (passes & 1) ? p.big_adj + o : p.tmp_adj + o;
+    int32_t *dst_v = (passes & 1) ? p.big_w + o : p.tmp_w + o;
+    for (int i = threadIdx.x; i < 4 * 256; i += CONTRACT_BLOCK) (&sm.hist[0][0])[i] = 0;
     if (threadIdx.x == 0) sm.s_carry = 0;
     __syncthreads();
-    for (int32_t c0 = 0; c0 < L; c0 += CONTRACT_BLOCK) {
-        const int32_t i = c0 + threadIdx.x;
-        int32_t t = x, wv = 0;
-        if (i < L) {
-            const int32_t e = i < da ? xa + i : xb + (i - da);
-            t = p.map[p.adjncy[e]];
-            wv = p.ewgt[e];
-        }
-        const bool keep = i < L && t != x;
-        uint64_t tot;
-        const int32_t pos = (int32_t)block_exclusive_scan<CONTRACT_BLOCK>(keep ? 1 : 0, &tot);
-        const int32_t carry = sm.s_carry;
-        if (keep) {
-            p.tmp_adj[o + carry + pos] = t;
-            p.tmp_w[o + carry + pos] = wv;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) sm.s_carry = carry + (int32_t)tot;
-        __syncthreads();
-    }
-    const int32_t M = sm.s_carry;   // == off[x+1] - off[x]
-    int32_t *src_k = p.tmp_adj + o, *src_v = p.tmp_w + o;
-    int32_t *dst_k = p.big_adj + o, *dst_v = p.big_w + o;
-    const int moves = (passes & 1) ? passes : passes + 1;
-    for (int pass = 0; pass < moves; pass++) {
-        if (pass >= passes) {
-            for (int32_t i = threadIdx.x; i < M; i += blockDim.x) {
-                dst_k[i] = src_k[i];
-                dst_v[i] = src_v[i];
+    // 1. gather (the order of the kept entries does not matter: they are
+    //    sorted next and equal keys are summed)
+    for (int32_t c0 = 0; c0 < L; c0 += RADIX_CHUNK) {
+#pragma unroll
+        for (int j = 0; j < RADIX_ITEMS; j++) {
+            const int32_t i = c0 + (warp * RADIX_ITEMS + j) * 32 + lane;
+            int32_t t = x, wv = 0;
+            if (i < L) {
+                const int32_t e = i < da ? xa + i : xb + (i - da);
+                t = p.map[p.adjncy[e]];
+                wv = p.ewgt[e];
             }
-        } else {
-            const int shift = 8 * pass;
-            for (int i = threadIdx.x; i < 256; i += blockDim.x) sm.base[i] = 0;
+            const bool keep = i < L && t != x;
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            int32_t at = 0;
+            if (lane == 0 && m) at = atomicAdd(&sm.s_carry, __popc(m));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            if (keep) {
+                const int32_t r = at + __popc(m & lt);
+                src_k[r] = t;
+                src_v[r] = wv;
+                for (int ps = 0; ps < passes; ps++) atomicAdd(&sm.hist[ps][(t >> (8 * ps)) & 255], 1);
+            }
+        }
+    }
+    __syncthreads();
+    const int32_t M = sm.s_carry;   // == off[x+1] - off[x]
+    // 2. radix passes
+    for (int pass = 0; pass < passes; pass++) {
+        const int shift = 8 * pass;
+        {
+            uint64_t tot;
+            sm.base[threadIdx.x] =
+                (int32_t)block_exclusive_scan<CONTRACT_BLOCK>((uint64_t)sm.hist[pass][threadIdx.x], &tot);
+        }
+        for (int32_t c0 = 0; c0 < M; c0 += RADIX_CHUNK) {
+#pragma unroll
+            for (int j = 0; j < 256 / 32; j++) sm.wcnt[warp][j * 32 + lane] = 0;
+            __syncwarp();
+            int32_t kk[RADIX_ITEMS], vv[RADIX_ITEMS], rk[RADIX_ITEMS];
+#pragma unroll
+            for (int j = 0; j < RADIX_ITEMS; j++) {
+                const int32_t i = c0 + (warp * RADIX_ITEMS + j) * 32 + lane;
+                const bool valid = i < M;
+                kk[j] = valid ? src_k[i] : 0;
+                vv[j] = valid ? src_v[i] : 0;
+                const int d = valid ? ((kk[j] >> shift) & 255) : 256 + lane;   // invalid lanes: unique
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                const int wr = __popc(peers & lt);
+                rk[j] = valid ? sm.wcnt[warp][d] + wr : 0;
+                __syncwarp();
+                if (valid && wr == 0) sm.wcnt[warp][d] += __popc(peers);
+                __syncwarp();
+            }
             __syncthreads();
-            for (int32_t i = threadIdx.x; i < M; i += blockDim.x) atomicAdd(&sm.base[(src_k[i] >> shift) & 255], 1);
-            __syncthreads();
-            if (threadIdx.x == 0) {
+            {
                 int32_t run = 0;
-                for (int d = 0; d < 256; d++) {
-                    const int32_t c = sm.base[d];
-                    sm.base[d] = run;
+#pragma unroll
+                for (int w2 = 0; w2 < NW; w2++) {
+                    const int32_t c = sm.wcnt[w2][threadIdx.x];
+                    sm.wcnt[w2][threadIdx.x] = run;
                     run += c;
                 }
+                sm.chunk_tot[threadIdx.x] = run;
             }
             __syncthreads();
-            for (int32_t c0 = 0; c0 < M; c0 += CONTRACT_BLOCK) {
-                for (int i = threadIdx.x; i < NW * 256; i += blockDim.x) (&sm.wcnt[0][0])[i] = 0;
-                __syncthreads();
-                const int32_t i = c0 + threadIdx.x;
-                const bool valid = i < M;
-                const int32_t k = valid ? src_k[i] : 0;
-                const int32_t v = valid ? src_v[i] : 0;
-                const int d = valid ? ((k >> shift) & 255) : 256 + lane;   // invalid lanes: unique
-                const unsigned peers = __match_any_sync(0xffffffffu, d);
-                const int wr = __popc(peers & lanemask_lt());
-                if (valid && wr == 0) sm.wcnt[warp][d] = __popc(peers);
-                __syncthreads();
-                if (threadIdx.x < 256) {
-                    int32_t run = 0;
-                    for (int w2 = 0; w2 < NW; w2++) {
-                        const int32_t c = sm.wcnt[w2][threadIdx.x];
-                        sm.wcnt[w2][threadIdx.x] = run;
-                        run += c;
-                    }
-                    sm.chunk_tot[threadIdx.x] = run;
+#pragma unroll
+            for (int j = 0; j < RADIX_ITEMS; j++) {
+                const int32_t i = c0 + (warp * RADIX_ITEMS + j) * 32 + lane;
+                if (i < M) {
+                    const int d = (kk[j] >> shift) & 255;
+                    const int32_t r = sm.base[d] + sm.wcnt[warp][d] + rk[j];
+                    dst_k[r] = kk[j];
+                    dst_v[r] = vv[j];
                 }
-                __syncthreads();
-                if (valid) {
-                    const int32_t r = sm.base[d] + sm.wcnt[warp][d] + wr;
-                    dst_k[r] = k;
-                    dst_v[r] = v;
-                }
-                __syncthreads();
-                if (threadIdx.x < 256) sm.base[threadIdx.x] += sm.chunk_tot[threadIdx.x];
-                __syncthreads();
             }
+            __syncthreads();
+            sm.base[threadIdx.x] += sm.chunk_tot[threadIdx.x];
         }
         __syncthreads();
         int32_t *tk = src_k, *tv = src_v;
@@ -605,27 +622,47 @@ static __device__ void contract_block_radix(const CView &p, int32_t x, int passe
         dst_k = tk;
         dst_v = tv;
     }
-    // src == big now; merge into tmp
-    for (int32_t i = threadIdx.x; i < M; i += blockDim.x) p.tmp_w[o + i] = 0;
+    // src == big now; 3. merge into tmp
+    for (int32_t i = threadIdx.x; i < M; i += CONTRACT_BLOCK) p.tmp_w[o + i] = 0;
     if (threadIdx.x == 0) sm.s_carry = 0;
     __syncthreads();
     int32_t wsum = 0;
-    for (int32_t c0 = 0; c0 < M; c0 += CONTRACT_BLOCK) {
-        const int32_t i = c0 + threadIdx.x;
-        const bool valid = i < M;
-        const int32_t k = valid ? src_k[i] : SENT;
-        const bool head = valid && (i == 0 || src_k[i - 1] != k);
-        uint64_t tot;
-        const int32_t pos = (int32_t)block_exclusive_scan<CONTRACT_BLOCK>(head ? 1 : 0, &tot);
-        const int32_t carry = sm.s_carry;
-        if (valid) {
-            const int32_t r = carry + pos + (head ? 1 : 0) - 1;
-            if (head) p.tmp_adj[o + r] = k;
-            atomicAdd(&p.tmp_w[o + r], src_v[i]);
-            wsum += src_v[i];
+    for (int32_t c0 = 0; c0 < M; c0 += RADIX_CHUNK) {
+        int32_t hk[RADIX_ITEMS];
+        unsigned hm[RADIX_ITEMS];
+        int32_t wrun = 0;
+#pragma unroll
+        for (int j = 0; j < RADIX_ITEMS; j++) {
+            const int32_t i = c0 + (warp * RADIX_ITEMS + j) * 32 + lane;
+            const bool valid = i < M;
+            hk[j] = valid ? src_k[i] : SENT;
+            const bool head = valid && (i == 0 || src_k[i - 1] != hk[j]);
+            hm[j] = __ballot_sync(0xffffffffu, head);
+            wrun += __popc(hm[j]);
+        }
+        if (lane == 0) sm.wsum[warp] = wrun;
+        __syncthreads();
+        int32_t before = sm.s_carry;
+        for (int w2 = 0; w2 < warp; w2++) before += sm.wsum[w2];
+#pragma unroll
+        for (int j = 0; j < RADIX_ITEMS; j++) {
+            const int32_t i = c0 + (warp * RADIX_ITEMS + j) * 32 + lane;
+            // run index: heads up to and including this entry, minus one
+            const int32_t r = before + __popc(hm[j] & (lt | (1u << lane))) - 1;
+            before += __popc(hm[j]);
+            if (i < M) {
+                const int32_t v = src_v[i];
+                if ((hm[j] >> lane) & 1u) p.tmp_adj[o + r] = hk[j];
+                atomicAdd(&p.tmp_w[o + r], v);
+                wsum += v;
+            }
         }
         __syncthreads();
-        if (threadIdx.x == 0) sm.s_carry = carry + (int32_t)tot;
+        if (threadIdx.x == 0) {
+            int32_t t = sm.s_carry;
+            for (int w2 = 0; w2 < NW; w2++) t += sm.wsum[w2];
+            sm.s_carry = t;
+        }
         __syncthreads();
     }
     for (int off2 = 16; off2 > 0; off2 >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, off2);
@@ -740,10 +777,14 @@ struct DegScanOp {
     }
 };
 
-// Moves every merged coarse row from its upper-bound slot to the CSR.
+// Moves every merged coarse row from its upper-bound slot to the CSR: rows
+// of at most 128 gathered entries with 8 lanes each, the longer ones (the
+// class lists of the contraction) with a warp each (up to MID_MAX) or a
+// block each, so a hub's row is not left to 8 lanes.
 static __device__ void phase_compact(DevState *st, int level, const Work &w) {
     if (!(st->lv[level].flags & LV_ACTIVE)) return;
-    const int32_t cn = st->ctr[level].cn;
+    const Counters *ctr = &st->ctr[level];
+    const int32_t cn = ctr->cn;
     const int32_t *KP_RESTRICT cxadj = st->lv[level + 1].xadj;
     int32_t *KP_RESTRICT cadj = st->lv[level + 1].adjncy;
     int32_t *KP_RESTRICT cw = st->lv[level + 1].ewgt;
@@ -751,8 +792,30 @@ static __device__ void phase_compact(DevState *st, int level, const Work &w) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int gl = threadIdx.x & 7;
     for (int64_t g = t >> 3; g < cn; g += stride >> 3) {
-        const int32_t o = w.off[g], d = w.degp[g], s = cxadj[g];
+        const int32_t o = w.off[g];
+        // gathered entries = the slot plus the pair's own two, as classified
+        if (w.off[g + 1] - o + (w.second[g] >= 0 ? 2 : 0) > 128) continue;
+        const int32_t d = w.degp[g], s = cxadj[g];
         for (int32_t i = gl; i < d; i += 8) {
+            cadj[s + i] = w.tmp_adj[o + i];
+            cw[s + i] = w.tmp_w[o + i];
+        }
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = stride >> 5;
+    const int32_t n3 = ctr->nclass[3], n4 = ctr->nclass[4];
+    for (int64_t li = t >> 5; li < n3; li += nw) {
+        const int32_t g = w.lists[3][li];
+        const int32_t o = w.off[g], d = w.degp[g], s = cxadj[g];
+        for (int32_t i = lane; i < d; i += 32) {
+            cadj[s + i] = w.tmp_adj[o + i];
+            cw[s + i] = w.tmp_w[o + i];
+        }
+    }
+    for (int64_t li = blockIdx.x; li < n4; li += gridDim.x) {
+        const int32_t g = w.lists[4][li];
+        const int32_t o = w.off[g], d = w.degp[g], s = cxadj[g];
+        for (int32_t i = threadIdx.x; i < d; i += blockDim.x) {
             cadj[s + i] = w.tmp_adj[o + i];
             cw[s + i] = w.tmp_w[o + i];
         }
