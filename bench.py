@@ -640,7 +640,7 @@ def poisson_arrivals(count, rate, seed):
     return np.cumsum(rng.exponential(1.0 / rate, size=count))
 
 
-def serve_phase(sv, pool, reqs, arrivals):
+def serve_phase(sv, pool, reqs, arrivals, borrow=False):
     """Submits reqs at the given arrival offsets (seconds; None: all at once)
     while a second thread waits for and releases them in order.  Latency of a
     request: from its scheduled arrival to its completion (server clock for
@@ -671,7 +671,7 @@ def serve_phase(sv, pool, reqs, arrivals):
             if dt > 0:
                 time.sleep(dt)
         lag = 0.0 if arrivals is None else max(0.0, time.perf_counter() - (t0 + arrivals[i]))
-        rid = sv.submit(g.xadj, g.adjncy, g.ewgt, g.vwgt, k, eps, seed, stop)
+        rid = sv.submit(g.xadj, g.adjncy, g.ewgt, g.vwgt, k, eps, seed, stop, borrow=borrow)
         q.put((i, rid, lag))
     q.put(None)
     th.join()
@@ -755,7 +755,7 @@ def run_served(args, wl):
     load_reqs = {0.5: served_requests(pool, R, seed=12), 0.9: served_requests(pool, R, seed=13)}
 
     sv = B.Server(workers=args.workers, max_batch=64, batch_max_nodes=1 << 16, hbm_budget_bytes=budget,
-                  rating=rating, validate=False, matcher=args.matcher, tail_nodes=args.tail_nodes)
+                  small_workers=1, rating=rating, validate=False, matcher=args.matcher, tail_nodes=args.tail_nodes)
     # warm-up: every pool graph once (allocator pool, library state)
     for _ in range(max(1, min(args.warmup, 2))):
         serve_phase(sv, pool, [(pi, 2, eps, 1, 40) for pi in range(len(pool))], None)
@@ -830,7 +830,8 @@ def run_served(args, wl):
         "warmup": max(1, min(args.warmup, 2)), "ms_per_step": 1000.0 * loads[0.9]["span_s"] / R,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "pool_graphs": len(pool),
-                   "requests_per_phase": R, "workers": args.workers, "max_batch": 64,
+                   "requests_per_phase": R, "workers": args.workers, "small_workers": 1, "max_batch": 64,
+                   "host_arrays": "copied by the server at submit (pageable numpy arrays)",
                    "batch_max_nodes": 1 << 16, "hbm_budget_gb": budget / 1e9, "matcher": args.matcher,
                    "l2": "inputs of the large requests exceed L2; no flush between requests (a stream)",
                    "parallelism": f"replicas x{world}", "step": "one request"},

@@ -119,7 +119,17 @@ typedef enum {
  *   tail_nodes           levels with at most this many nodes and at most 8
  *                        times as many directed edges are contracted
  *                        together in one persistent launch (0: 262144;
- *                        -1: never); results do not depend on it */
+ *                        -1: never; 2^31-1: the whole hierarchy)
+ * Tuning knobs (0: the built-in choice; results never depend on them, only
+ * the time does -- kp_autotune picks them by measurement):
+ *   suitor_lanes         lanes per proposing node in the Suitor pass: 1, 4,
+ *                        8 or 32 (0: from the level's mean degree)
+ *   tail_block_nodes     nodes per block of the persistent tail launch,
+ *                        256..16384 (0: 2048)
+ *   sort_shared_max      coarse rows of up to this many gathered entries are
+ *                        sorted by one block in shared memory, longer ones by
+ *                        the radix path, 128..2048 (0: 2048)
+ *   radix_bits           bits per pass of the radix path, 4..8 (0: 8) */
 typedef struct {
     int32_t rating;
     uint64_t seed;
@@ -132,11 +142,16 @@ typedef struct {
     int32_t matcher;
     int64_t arena_bytes;
     int32_t tail_nodes;
+    int32_t suitor_lanes;
+    int32_t tail_block_nodes;
+    int32_t sort_shared_max;
+    int32_t radix_bits;
 } kp_options;
 
 /* Fills *o with the defaults: EXPANSION_STAR2, seed 1, stop_size 40,
  * max_levels 64, min_shrink_permille 50, spin_limit 1<<22, validate 1,
- * profile 0, matcher SUITOR, arena_bytes 0, tail_nodes 0. */
+ * profile 0, matcher SUITOR, arena_bytes 0, tail_nodes 0, and 0 for every
+ * tuning knob. */
 void kp_options_default(kp_options *o);
 
 /* A hierarchy of graphs G_0 (the input) .. G_L (the coarsest) with the maps
@@ -348,7 +363,10 @@ kp_status kp_pipeline_host(const kp_graph *g, const kp_options *o, int32_t k, do
  * Admission: first in, first out; the oldest waiting request starts once its
  * estimated device footprint fits into hbm_budget_bytes minus the footprint
  * of running and resident requests (a request runs alone if nothing else is
- * charged, whatever its size).  Footprint while running: 140 n + 56 nnz + 2 MB
+ * charged, whatever its size).  Workers kept for small requests take the
+ * oldest waiting request of at most batch_max_nodes nodes instead, so small
+ * requests do not queue behind large ones.  Footprint while running:
+ * 140 n + 56 nnz + 2 MB
  * bytes; while resident: 88 n + 40 nnz + 1 MB.
  * Continuous batching: when a worker takes a request with at most
  * batch_max_nodes nodes, it also takes further waiting requests with at most
@@ -365,16 +383,24 @@ typedef struct kp_server_config {
     int32_t workers;           /* worker threads/streams, 1..64 */
     int32_t max_batch;         /* most requests merged into one group, >= 1 */
     int32_t batch_max_nodes;   /* requests above this size always run alone */
-    int32_t pad;
+    int32_t small_workers;     /* of the workers, how many take only requests of
+                                  at most batch_max_nodes nodes (0..workers-1) */
     int64_t hbm_budget_bytes;  /* device bytes for running + resident requests */
     kp_options options;        /* engine options; seed and stop_size are per request */
 } kp_server_config;
+
+/* kp_request_params.flags: the server reads the caller's arrays when the
+ * request runs instead of copying them at submit; they must stay valid and
+ * unchanged until the request has finished. */
+#define KP_REQUEST_BORROW 1
 
 typedef struct kp_request_params {
     int32_t k;          /* blocks, >= 1 */
     int32_t stop_size;  /* coarsening stops at this many nodes (kp_options.stop_size) */
     double eps;         /* imbalance parameter of L_max */
     uint64_t seed;      /* tie-break hash seed and initial-partition seed */
+    int32_t flags;      /* 0 or KP_REQUEST_BORROW */
+    int32_t pad;
 } kp_request_params;
 
 typedef struct kp_request_result {
@@ -395,11 +421,13 @@ typedef struct kp_request_result {
 } kp_request_result;
 
 /* Starts the workers.  Errors: KP_ERR_INVALID (workers outside 1..64,
- * max_batch < 1, budget <= 0), KP_ERR_CUDA. */
+ * max_batch < 1, budget <= 0, small_workers outside 0..workers-1),
+ * KP_ERR_CUDA. */
 kp_status kp_server_create(const kp_server_config *cfg, kp_server **out);
 
-/* Copies the host graph into the server and queues it; *id receives the
- * request id.  The caller's arrays may be reused once this returns.
+/* Copies the host graph into the server (unless p->flags has
+ * KP_REQUEST_BORROW) and queues it; *id receives the request id.  Without
+ * KP_REQUEST_BORROW the caller's arrays may be reused once this returns.
  * Errors: KP_ERR_INVALID (null pointers, negative sizes, k < 1, eps outside
  * [0,1000], server stopping), KP_ERR_OOM (host copy). */
 kp_status kp_server_submit(kp_server *sv, const kp_graph *g, const kp_request_params *p, uint64_t *id);
@@ -426,6 +454,64 @@ kp_status kp_server_release(kp_server *sv, uint64_t id);
 
 /* Stops the workers after their running groups, frees every request. */
 void kp_server_destroy(kp_server *sv);
+
+/* ------------------------------------------------------------------------
+ * Captured plans (the paper has no counterpart).  kp_plan_create records the
+ * coarsening of one graph (num_graphs = 0) or of a batch (num_graphs > 0,
+ * arguments as kp_coarsen_batch) into a CUDA graph: the state upload, the
+ * batch's graph ids, Out (innerOuter) and ONE persistent cooperative launch
+ * that builds the whole hierarchy level after level (tail_nodes is taken as
+ * 2^31-1).  kp_plan_run replays it on any stream and returns the hierarchy.
+ * The input arrays, offsets, seeds and stop sizes are BORROWED for the
+ * plan's life and read at every run: their contents may change between runs
+ * (the sizes n, nnz and num_graphs may not).  Results equal kp_coarsen[_batch]
+ * with the same options.
+ * kp_plan_create first coarsens once in the plan's mode (this checks the
+ * options, offsets and, with o->validate, the input), then allocates the
+ * plan's scratch and arena and records the graph; it synchronises s.
+ * Errors: those of kp_coarsen[_batch]; KP_ERR_INVALID for n = 0;
+ * KP_ERR_CUDA when the device cannot record the launch sequence.
+ * ------------------------------------------------------------------------ */
+typedef struct kp_plan kp_plan;
+
+kp_status kp_plan_create(const kp_graph *g, int32_t num_graphs, const int32_t *node_offsets, const uint64_t *seeds,
+                         const int32_t *stop_sizes, const kp_options *o, kp_stream s, kp_plan **out);
+
+/* Replays the plan on stream s and synchronises it.  *out is a hierarchy
+ * whose coarse levels live in the plan's arena: it is valid until the next
+ * kp_plan_run or kp_plan_destroy of this plan; release it with
+ * kp_hierarchy_free (which then frees only the handle).  If the arena turns
+ * out too small, a larger one is taken and the run repeated.  Errors:
+ * KP_ERR_TIMEOUT (a bounded wait gave up), KP_ERR_OOM, KP_ERR_CUDA. */
+kp_status kp_plan_run(kp_plan *p, kp_stream s, kp_hierarchy **out);
+
+/* Waits for the plan's work and frees it (hierarchies from it become
+ * invalid). */
+void kp_plan_destroy(kp_plan *p);
+
+/* ------------------------------------------------------------------------
+ * Autotuning (the paper has no counterpart).  The tuning knobs of
+ * kp_options never change a result, only the time; kp_autotune measures.
+ * Coordinate descent from *o over tail_nodes, suitor_lanes (Suitor only),
+ * tail_block_nodes, sort_shared_max and radix_bits, in that order: every
+ * candidate coarsens the caller's graph (num_graphs = 0) or batch
+ * (num_graphs > 0, arguments as kp_coarsen_batch) once untimed and `reps`
+ * times timed by CUDA events on the stream; a knob keeps the value with the
+ * least minimum time.  *best receives *o with the chosen knobs.  trials
+ * (may be NULL when max_trials is 0) receives up to max_trials candidates
+ * with their times in measuring order, *num_trials (may be NULL) how many
+ * were measured.  Synchronises the stream many times; allocates like
+ * kp_coarsen.  Errors: KP_ERR_INVALID (null pointers, reps outside 1..100,
+ * negative num_graphs or max_trials), and those of kp_coarsen[_batch].
+ * ------------------------------------------------------------------------ */
+typedef struct kp_tune_trial {
+    kp_options options;
+    double ms;
+} kp_tune_trial;
+
+kp_status kp_autotune(const kp_graph *g, int32_t num_graphs, const int32_t *node_offsets, const uint64_t *seeds,
+                      const int32_t *stop_sizes, const kp_options *o, int32_t reps, kp_options *best,
+                      kp_tune_trial *trials, int32_t max_trials, int32_t *num_trials, kp_stream s);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *kp_last_error(void);

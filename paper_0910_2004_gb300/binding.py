@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libkp.so")
 
 KP_CUT_GAIN_NOALLOC_MAX_K = 16384
+KP_REQUEST_BORROW = 1
 
 KP_OK, KP_ERR_INVALID, KP_ERR_OVERFLOW, KP_ERR_OOM, KP_ERR_CUDA, KP_ERR_TIMEOUT, KP_ERR_UNSUPPORTED = range(7)
 STATUS_NAMES = ["KP_OK", "KP_ERR_INVALID", "KP_ERR_OVERFLOW", "KP_ERR_OOM", "KP_ERR_CUDA",
@@ -31,7 +32,8 @@ EXPORTED = ["kp_options_default", "kp_coarsen", "kp_hierarchy_num_levels", "kp_h
             "kp_coarsen_batch", "kp_hierarchy_batch", "kp_hierarchy_level_offsets", "kp_project_batch",
             "kp_hierarchy_batch_coarsest",
             "kp_server_create", "kp_server_submit", "kp_server_poll", "kp_server_wait", "kp_server_fetch",
-            "kp_server_release", "kp_server_destroy",
+            "kp_server_release", "kp_server_destroy", "kp_autotune", "kp_plan_create", "kp_plan_run",
+            "kp_plan_destroy",
             "kp_last_error", "kp_version"]
 
 
@@ -51,7 +53,11 @@ class kp_options(ctypes.Structure):
     _fields_ = [("rating", ctypes.c_int32), ("seed", ctypes.c_uint64), ("stop_size", ctypes.c_int32),
                 ("max_levels", ctypes.c_int32), ("min_shrink_permille", ctypes.c_int32),
                 ("spin_limit", ctypes.c_int64), ("validate", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("matcher", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("tail_nodes", ctypes.c_int32)]
+                ("matcher", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("tail_nodes", ctypes.c_int32),
+                ("suitor_lanes", ctypes.c_int32), ("tail_block_nodes", ctypes.c_int32),
+                ("sort_shared_max", ctypes.c_int32), ("radix_bits", ctypes.c_int32)]
+
+TUNING_KNOBS = ("suitor_lanes", "tail_block_nodes", "sort_shared_max", "radix_bits", "tail_nodes", "matcher")
 
 
 class kp_cut_gain_out(ctypes.Structure):
@@ -66,14 +72,18 @@ class kp_level_profile(ctypes.Structure):
                 ("rounds", ctypes.c_int32)]
 
 
+class kp_tune_trial(ctypes.Structure):
+    _fields_ = [("options", kp_options), ("ms", ctypes.c_double)]
+
+
 class kp_server_config(ctypes.Structure):
     _fields_ = [("workers", ctypes.c_int32), ("max_batch", ctypes.c_int32), ("batch_max_nodes", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64), ("options", kp_options)]
+                ("small_workers", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64), ("options", kp_options)]
 
 
 class kp_request_params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("stop_size", ctypes.c_int32), ("eps", ctypes.c_double),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("flags", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class kp_request_result(ctypes.Structure):
@@ -154,6 +164,17 @@ def load(path: str = LIB_PATH):
         L.kp_server_release.restype = ctypes.c_int
         L.kp_server_destroy.argtypes = [vp]
         L.kp_server_destroy.restype = None
+        L.kp_autotune.argtypes = [ctypes.POINTER(kp_graph), i32, vp, vp, vp, ctypes.POINTER(kp_options), i32,
+                                  ctypes.POINTER(kp_options), ctypes.POINTER(kp_tune_trial), i32,
+                                  ctypes.POINTER(i32), vp]
+        L.kp_autotune.restype = ctypes.c_int
+        L.kp_plan_create.argtypes = [ctypes.POINTER(kp_graph), i32, vp, vp, vp, ctypes.POINTER(kp_options), vp,
+                                     ctypes.POINTER(vp)]
+        L.kp_plan_create.restype = ctypes.c_int
+        L.kp_plan_run.argtypes = [vp, vp, ctypes.POINTER(vp)]
+        L.kp_plan_run.restype = ctypes.c_int
+        L.kp_plan_destroy.argtypes = [vp]
+        L.kp_plan_destroy.restype = None
         L.kp_last_error.argtypes = []
         L.kp_last_error.restype = ctypes.c_char_p
         L.kp_version.argtypes = []
@@ -317,6 +338,36 @@ def kp_server_destroy(sv: int):
     load().kp_server_destroy(sv)
 
 
+def kp_autotune(graph: kp_graph, num_graphs: int, node_offsets: int, seeds: int, stop_sizes: int,
+                options: kp_options, reps: int, max_trials: int, stream: int):
+    best = kp_options()
+    trials = (kp_tune_trial * max(max_trials, 1))()
+    nt = ctypes.c_int32()
+    _check(load().kp_autotune(ctypes.byref(graph), num_graphs, ctypes.c_void_p(node_offsets), ctypes.c_void_p(seeds),
+                              ctypes.c_void_p(stop_sizes), ctypes.byref(options), reps, ctypes.byref(best), trials,
+                              max_trials, ctypes.byref(nt), ctypes.c_void_p(stream)), "kp_autotune")
+    return best, [trials[i] for i in range(min(nt.value, max_trials))]
+
+
+def kp_plan_create(graph: kp_graph, num_graphs: int, node_offsets: int, seeds: int, stop_sizes: int,
+                   options: kp_options, stream: int) -> int:
+    p = ctypes.c_void_p()
+    _check(load().kp_plan_create(ctypes.byref(graph), num_graphs, ctypes.c_void_p(node_offsets),
+                                 ctypes.c_void_p(seeds), ctypes.c_void_p(stop_sizes), ctypes.byref(options),
+                                 ctypes.c_void_p(stream), ctypes.byref(p)), "kp_plan_create")
+    return p.value
+
+
+def kp_plan_run(plan: int, stream: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().kp_plan_run(ctypes.c_void_p(plan), ctypes.c_void_p(stream), ctypes.byref(h)), "kp_plan_run")
+    return h.value
+
+
+def kp_plan_destroy(plan: int):
+    load().kp_plan_destroy(ctypes.c_void_p(plan))
+
+
 def kp_last_error() -> str:
     return load().kp_last_error().decode(errors="replace")
 
@@ -377,7 +428,8 @@ class DeviceGraph:
 
 def make_options(rating="expansion*2", seed=1, stop_size=40, max_levels=64, min_shrink_permille=50,
                  spin_limit=1 << 22, validate=True, profile=False, matcher="suitor",
-                 arena_bytes=0, tail_nodes=0) -> kp_options:
+                 arena_bytes=0, tail_nodes=0, suitor_lanes=0, tail_block_nodes=0, sort_shared_max=0,
+                 radix_bits=0) -> kp_options:
     o = kp_options_default()
     o.rating = RATINGS[rating] if isinstance(rating, str) else int(rating)
     o.seed = seed
@@ -390,6 +442,10 @@ def make_options(rating="expansion*2", seed=1, stop_size=40, max_levels=64, min_
     o.matcher = MATCHERS[matcher] if isinstance(matcher, str) else int(matcher)
     o.arena_bytes = arena_bytes
     o.tail_nodes = tail_nodes
+    o.suitor_lanes = suitor_lanes
+    o.tail_block_nodes = tail_block_nodes
+    o.sort_shared_max = sort_shared_max
+    o.radix_bits = radix_bits
     return o
 
 
@@ -563,14 +619,24 @@ class Server:
     """Request server of the library (kp_server_*): submit host graphs, wait,
     fetch the results, release.  Timestamps are microseconds since start."""
 
-    def __init__(self, workers=4, max_batch=64, batch_max_nodes=1 << 16, hbm_budget_bytes=64 << 30, **opts):
-        cfg = kp_server_config(workers, max_batch, batch_max_nodes, 0, hbm_budget_bytes, make_options(**opts))
+    def __init__(self, workers=4, max_batch=64, batch_max_nodes=1 << 16, hbm_budget_bytes=64 << 30,
+                 small_workers=0, **opts):
+        cfg = kp_server_config(workers, max_batch, batch_max_nodes, small_workers, hbm_budget_bytes,
+                               make_options(**opts))
         self._sv = kp_server_create(cfg)
+        self._borrowed = {}
 
-    def submit(self, xadj, adjncy, ewgt, vwgt, k: int, eps: float, seed: int = 1, stop_size: int = 40) -> int:
+    def submit(self, xadj, adjncy, ewgt, vwgt, k: int, eps: float, seed: int = 1, stop_size: int = 40,
+               borrow: bool = False) -> int:
+        """borrow=True: the server reads the arrays when the request runs (no
+        copy at submit); they are kept referenced until release."""
         arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in (xadj, adjncy, ewgt, vwgt)]
         g = kp_graph(len(arrs[0]) - 1, len(arrs[1]), *[a.ctypes.data for a in arrs])
-        return kp_server_submit(self._sv, g, kp_request_params(k, stop_size, eps, seed))
+        rid = kp_server_submit(self._sv, g, kp_request_params(k, stop_size, eps, seed,
+                                                              KP_REQUEST_BORROW if borrow else 0, 0))
+        if borrow:
+            self._borrowed[rid] = arrs
+        return rid
 
     def poll(self, rid: int):
         done, res = kp_server_poll(self._sv, rid)
@@ -589,6 +655,7 @@ class Server:
 
     def release(self, rid: int):
         kp_server_release(self._sv, rid)
+        self._borrowed.pop(rid, None)
 
     def close(self):
         if self._sv:
@@ -606,3 +673,101 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def _knobs(o: kp_options) -> dict:
+    return {k: int(getattr(o, k)) for k in TUNING_KNOBS}
+
+
+def shape_key(graph, num_graphs: int = 0, rating="expansion*2", matcher="suitor") -> str:
+    """Shape class of a tuning problem: powers of two of the node count and
+    of the mean degree, the batch size class, rating and matcher."""
+    import math
+    n, nnz = max(graph.kp.n, 1), graph.kp.nnz
+    return (f"n2^{round(math.log2(n))}|deg2^{round(math.log2(max(nnz / n, 1.0)))}|"
+            f"graphs2^{round(math.log2(num_graphs)) if num_graphs > 0 else 'single'}|{rating}|{matcher}")
+
+
+def autotune(graph: DeviceGraph, offsets=None, seeds=None, stop_sizes=None, reps: int = 2, cache: str | None = None,
+             max_trials: int = 64, **opts):
+    """Tuning knobs for this graph (or batch when offsets is given) by
+    kp_autotune, cached in the JSON file `cache` under the GPU's name and the
+    shape class.  Returns (knobs dict, trials [(knobs, ms)], from_cache)."""
+    import json
+    torch = _torch()
+    key = f"{torch.cuda.get_device_name()}|" + shape_key(graph, 0 if offsets is None else len(offsets) - 1,
+                                                            opts.get("rating", "expansion*2"),
+                                                            opts.get("matcher", "suitor"))
+    table = {}
+    if cache and os.path.exists(cache):
+        with open(cache) as f:
+            table = json.load(f)
+        if key in table:
+            return table[key]["knobs"], [], True
+    off = sd = ss = None
+    if offsets is not None:
+        off = offsets if torch.is_tensor(offsets) else torch.as_tensor(np.asarray(offsets, dtype=np.int32))
+        off = off.to("cuda").contiguous()
+        if seeds is not None:
+            sd = torch.as_tensor(np.asarray(seeds, dtype=np.uint64).view(np.int64)).to("cuda").contiguous()
+        if stop_sizes is not None:
+            ss = torch.as_tensor(np.asarray(stop_sizes, dtype=np.int32)).to("cuda").contiguous()
+    best, trials = kp_autotune(graph.kp, 0 if off is None else off.numel() - 1, 0 if off is None else off.data_ptr(),
+                               0 if sd is None else sd.data_ptr(), 0 if ss is None else ss.data_ptr(),
+                               make_options(**opts), reps, max_trials, current_stream())
+    knobs = _knobs(best)
+    if cache:
+        table[key] = {"knobs": knobs, "best_ms": min(t.ms for t in trials) if trials else None}
+        d = os.path.dirname(os.path.abspath(cache))
+        os.makedirs(d, exist_ok=True)
+        tmp = cache + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(table, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache)
+    return knobs, [(_knobs(t.options), t.ms) for t in trials], False
+
+
+class Plan:
+    """A coarsening recorded once into a CUDA graph (kp_plan_*): one graph,
+    or a batch when offsets is given.  run() replays it and returns a
+    Hierarchy (BatchHierarchy for a batch) valid until the next run."""
+
+    def __init__(self, graph: DeviceGraph, offsets=None, seeds=None, stop_sizes=None, **opts):
+        torch = _torch()
+        self.graph = graph
+        self.off = self.sd = self.ss = None
+        if offsets is not None:
+            off = offsets if torch.is_tensor(offsets) else torch.as_tensor(np.asarray(offsets, dtype=np.int32))
+            self.off = off.to("cuda").contiguous()
+            if seeds is not None:
+                self.sd = torch.as_tensor(np.asarray(seeds, dtype=np.uint64).view(np.int64)).to("cuda").contiguous()
+            if stop_sizes is not None:
+                self.ss = torch.as_tensor(np.asarray(stop_sizes, dtype=np.int32)).to("cuda").contiguous()
+        G = 0 if self.off is None else self.off.numel() - 1
+        self.handle = kp_plan_create(graph.kp, G, 0 if self.off is None else self.off.data_ptr(),
+                                     0 if self.sd is None else self.sd.data_ptr(),
+                                     0 if self.ss is None else self.ss.data_ptr(), make_options(**opts),
+                                     current_stream())
+        self._last = None
+
+    def run(self):
+        if self._last is not None:
+            self._last.free()
+        h = kp_plan_run(self.handle, current_stream())
+        self._last = (BatchHierarchy(self.graph, h, self.off, (self.sd, self.ss)) if self.off is not None
+                      else Hierarchy(self.graph, h))
+        return self._last
+
+    def close(self):
+        if self._last is not None:
+            self._last.free()
+            self._last = None
+        if self.handle:
+            kp_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -213,6 +213,10 @@ void kp_options_default(kp_options *o) {
     o->matcher = KP_MATCHER_SUITOR;
     o->arena_bytes = 0;
     o->tail_nodes = 0;
+    o->suitor_lanes = 0;
+    o->tail_block_nodes = 0;
+    o->sort_shared_max = 0;
+    o->radix_bits = 0;
 }
 
 kp_status kp_coarsen(const kp_graph *g, const kp_options *o, kp_stream s, kp_hierarchy **out) {

@@ -63,6 +63,139 @@ unsigned long long align256(unsigned long long b) { return (b + 255ull) & ~255ul
 
 }  // namespace
 
+// Device scratch of the level loop, sized for level 0 (every later level is
+// smaller), and the device state.
+kp_status alloc_work(Scratch &sc, Work &w, int32_t n0, int32_t nnz0, const kp_options *o, const BatchSpec *batch,
+                     int32_t *glevels_dev, DevState **dst) {
+    std::memset(&w, 0, sizeof w);
+    if (o->matcher == KP_MATCHER_SUITOR) {
+        KP_TRY(sc.get(&w.offer, n0));
+    } else {
+        KP_TRY(sc.get(&w.match, n0));
+        KP_TRY(sc.get(&w.cand, n0));
+        KP_TRY(sc.get(&w.list1, n0));
+    }
+    KP_TRY(sc.get(&w.list0, n0));
+    KP_TRY(sc.get(&w.first, n0));
+    KP_TRY(sc.get(&w.second, n0));
+    KP_TRY(sc.get(&w.off, (int64_t)n0 + 1));
+    KP_TRY(sc.get(&w.degp, n0));
+    KP_TRY(sc.get(&w.tmp_adj, nnz0));
+    KP_TRY(sc.get(&w.tmp_w, nnz0));
+    KP_TRY(sc.get(&w.big_adj, nnz0));
+    KP_TRY(sc.get(&w.big_w, nnz0));
+    for (int c = 1; c <= 4; c++) KP_TRY(sc.get(&w.lists[c], n0));
+    KP_TRY(sc.get(&w.status, scan_tiles(n0) + 1));
+    KP_TRY(sc.get(dst, 1));
+    w.seed = o->seed;
+    w.spin_limit = o->spin_limit;
+    if (batch) {
+        w.batch = 1;
+        w.num_graphs = batch->num_graphs;
+        w.seeds = batch->seeds;
+        w.stops = batch->stop_sizes;
+        w.glevels = glevels_dev;
+        KP_TRY(sc.get(&w.gactive, batch->num_graphs));
+    }
+    return KP_OK;
+}
+
+unsigned long long initial_arena(const kp_options *o, int32_t n0, int32_t nnz0) {
+    unsigned long long cap =
+        o->arena_bytes > 0
+            ? align256((unsigned long long)o->arena_bytes)
+            : align256(4ull * (16ull * (unsigned long long)n0 + 8ull * (unsigned long long)nnz0) + (1ull << 20));
+    if (o->rating == KP_RATING_INNER_OUTER)   // Out of the input lives at the arena's start
+        cap = std::max<unsigned long long>(cap, align256(4ull * (unsigned long long)n0) + 4096);
+    return cap;
+}
+
+// Host image of the device state before level 0: the input as level 0, the
+// arena, the options the kernels read.
+void init_state(DevState *hs, const kp_graph *g, const kp_options *o, const BatchSpec *batch, int32_t *gid0,
+                char *arena, unsigned long long arena_cap, LevelSnap *snap_dev) {
+    const bool inner_outer = o->rating == KP_RATING_INNER_OUTER;
+    std::memset(hs, 0, sizeof(DevState));
+    DevLevel &L0 = hs->lv[0];
+    L0.n = g->n;
+    L0.nnz = g->nnz;
+    L0.U = g->nnz;
+    // one graph is contracted at all only above the stop size; the graphs of
+    // a batch decide for themselves at the level start
+    const bool active0 = batch ? true : (g->n > o->stop_size && o->max_levels > 0);
+    L0.flags = LV_BUILT | (active0 ? LV_ACTIVE : 0);
+    L0.xadj = const_cast<int32_t *>(g->xadj);
+    L0.adjncy = const_cast<int32_t *>(g->adjncy);
+    L0.ewgt = const_cast<int32_t *>(g->ewgt);
+    L0.vwgt = const_cast<int32_t *>(g->vwgt);
+    if (batch) {
+        L0.gid = gid0;
+        L0.goff = const_cast<int32_t *>(batch->node_offsets);
+    }
+    hs->arena = arena;
+    hs->arena_cap = arena_cap;
+    hs->arena_used = 0;
+    if (inner_outer) {
+        L0.outw = (int32_t *)arena;
+        hs->arena_used = align256(4ull * (unsigned long long)g->n);
+    }
+    hs->stop_size = o->stop_size;
+    hs->max_levels = o->max_levels;
+    hs->min_shrink_permille = o->min_shrink_permille;
+    hs->inner_outer = inner_outer ? 1 : 0;
+    hs->suitor_lanes = o->suitor_lanes;
+    hs->sort_shared_max = o->sort_shared_max ? o->sort_shared_max : MID_MAX;
+    hs->radix_bits = o->radix_bits ? o->radix_bits : 8;
+    hs->snap = snap_dev;
+}
+
+// The coarse levels, maps, batch offsets and per-level counters from the
+// device state read back after the loop (h holds level 0 already).
+kp_status assemble_hierarchy(kp_hierarchy *h, const DevState *hs, bool suitor, int32_t G,
+                             const int32_t *level_launches, cudaStream_t s) {
+    int last = 0;
+    while (last + 1 < MAX_LEVELS && (hs->lv[last + 1].flags & LV_BUILT)) last++;
+    for (int l = 1; l <= last; l++) {
+        const DevLevel &D = hs->lv[l];
+        kp_level kl;
+        kl.n = D.n;
+        kl.nnz = D.nnz;
+        kl.xadj = D.xadj;
+        kl.adjncy = D.adjncy;
+        kl.ewgt = D.ewgt;
+        kl.vwgt = D.vwgt;
+        kl.owned = true;
+        h->levels.push_back(kl);
+    }
+    for (int l = 0; l < last; l++) h->levels[(size_t)l].map = hs->lv[l].map;
+    h->levels[(size_t)last].map = nullptr;
+    if (G > 0) {
+        for (int l = 1; l <= last; l++) h->levels[(size_t)l].goff = hs->lv[l].goff;
+        h->glevels.resize((size_t)G);
+        KP_CUDA(cudaMemcpyAsync(h->glevels.data(), h->glevels_dev, sizeof(int32_t) * (size_t)G,
+                                cudaMemcpyDeviceToHost, s));
+        KP_CUDA(cudaStreamSynchronize(s));
+    }
+    h->per_level.assign((size_t)last, kp_level_profile{});
+    int32_t total_rounds = 0;
+    int64_t total_matched = 0;
+    for (int l = 0; l < last; l++) {
+        kp_level_profile &P = h->per_level[(size_t)l];
+        const Counters &C = hs->ctr[l];
+        P.n = hs->lv[l].n;
+        P.nnz = hs->lv[l].nnz;
+        P.rounds = suitor ? 1 : C.rounds;
+        P.searches = (int64_t)C.searches;
+        P.failed_cas = (int64_t)C.failed_cas;
+        P.launches = level_launches ? level_launches[l] : 0;
+        total_rounds += P.rounds;
+        total_matched += (int64_t)hs->lv[l].n - hs->lv[l + 1].n;
+    }
+    h->total_rounds = total_rounds;
+    h->total_matched = total_matched;
+    return KP_OK;
+}
+
 kp_status validate_graph(const kp_graph *g, cudaStream_t s, int64_t spin_limit);
 
 kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, kp_hierarchy **out,
@@ -77,6 +210,12 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     if (o->max_levels < 0 || o->max_levels > MAX_LEVELS - 8 || o->min_shrink_permille < 0 ||
         o->min_shrink_permille > 1000 || o->spin_limit <= 0 || o->arena_bytes < 0 || o->tail_nodes < -1)
         return set_error(KP_ERR_INVALID, "bad option value");
+    if (!(o->suitor_lanes == 0 || o->suitor_lanes == 1 || o->suitor_lanes == 4 || o->suitor_lanes == 8 ||
+          o->suitor_lanes == 32) ||
+        (o->tail_block_nodes != 0 && (o->tail_block_nodes < 256 || o->tail_block_nodes > 16384)) ||
+        (o->sort_shared_max != 0 && (o->sort_shared_max < 128 || o->sort_shared_max > MID_MAX)) ||
+        (o->radix_bits != 0 && (o->radix_bits < 4 || o->radix_bits > 8)))
+        return set_error(KP_ERR_INVALID, "bad tuning knob");
     if (o->matcher == KP_MATCHER_HANDSHAKE) {
         if (g_coop_supported < 0) {
             int dev = 0, v = 0;
@@ -175,43 +314,9 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     Scratch sc;
     sc.s = s;
     Work w;
-    std::memset(&w, 0, sizeof w);
-    kp_status st;
-#define SC_GET(ptr, cnt)               \
-    st = sc.get(&(ptr), (cnt));        \
-    if (st != KP_OK) return fail(st);
-    if (suitor) {
-        SC_GET(w.offer, n0);
-    } else {
-        SC_GET(w.match, n0);
-        SC_GET(w.cand, n0);
-        SC_GET(w.list1, n0);
-    }
-    SC_GET(w.list0, n0);
-    SC_GET(w.first, n0);
-    SC_GET(w.second, n0);
-    SC_GET(w.off, (int64_t)n0 + 1);
-    SC_GET(w.degp, n0);
-    SC_GET(w.tmp_adj, nnz0);
-    SC_GET(w.tmp_w, nnz0);
-    SC_GET(w.big_adj, nnz0);
-    SC_GET(w.big_w, nnz0);
-    for (int c = 1; c <= 4; c++) SC_GET(w.lists[c], n0);
-    SC_GET(w.status, scan_tiles(n0) + 1);
     DevState *dst = nullptr;
-    SC_GET(dst, 1);
-#undef SC_GET
-    w.seed = o->seed;
-    w.spin_limit = o->spin_limit;
-    if (batch) {
-        w.batch = 1;
-        w.num_graphs = G;
-        w.seeds = batch->seeds;
-        w.stops = batch->stop_sizes;
-        w.glevels = h->glevels_dev;
-        kp_status st1 = sc.get(&w.gactive, G);
-        if (st1 != KP_OK) return fail(st1);
-    }
+    kp_status st = alloc_work(sc, w, n0, nnz0, o, batch, h->glevels_dev, &dst);
+    if (st != KP_OK) return fail(st);
     if (cudaMemsetAsync(w.status, 0, sizeof(TileStatus) * (size_t)(scan_tiles(n0) + 1), s) != cudaSuccess)
         return fail(cuda_error(cudaGetLastError(), "clear scan status"));
 
@@ -221,44 +326,14 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     LevelSnap *snap = mirror.snap;
 
     // the arena for all coarse levels (grown on overflow)
-    unsigned long long arena_cap =
-        o->arena_bytes > 0
-            ? align256((unsigned long long)o->arena_bytes)
-            : align256(4ull * (16ull * (unsigned long long)n0 + 8ull * (unsigned long long)nnz0) + (1ull << 20));
-    if (inner_outer)   // Out of the input lives at the arena's start
-        arena_cap = std::max<unsigned long long>(arena_cap, align256(4ull * (unsigned long long)n0) + 4096);
+    unsigned long long arena_cap = initial_arena(o, n0, nnz0);
     char *arena = nullptr;
     st = dev_alloc((void **)&arena, arena_cap, s);
     if (st != KP_OK) return fail(st);
     h->allocations.push_back(arena);
-
-    std::memset(hs, 0, sizeof(DevState));
     std::memset(snap, 0, sizeof(LevelSnap) * MAX_LEVELS);
+    init_state(hs, g, o, batch, h->gid0, arena, arena_cap, mirror.snap_dev);
     DevLevel &L0 = hs->lv[0];
-    L0.n = n0;
-    L0.nnz = nnz0;
-    L0.U = nnz0;
-    L0.flags = LV_BUILT | LV_ACTIVE;
-    L0.xadj = const_cast<int32_t *>(g->xadj);
-    L0.adjncy = const_cast<int32_t *>(g->adjncy);
-    L0.ewgt = const_cast<int32_t *>(g->ewgt);
-    L0.vwgt = const_cast<int32_t *>(g->vwgt);
-    if (batch) {
-        L0.gid = h->gid0;
-        L0.goff = const_cast<int32_t *>(batch->node_offsets);
-    }
-    hs->arena = arena;
-    hs->arena_cap = arena_cap;
-    hs->arena_used = 0;
-    if (inner_outer) {
-        L0.outw = (int32_t *)arena;
-        hs->arena_used = align256(4ull * (unsigned long long)n0);
-    }
-    hs->stop_size = o->stop_size;
-    hs->max_levels = o->max_levels;
-    hs->min_shrink_permille = o->min_shrink_permille;
-    hs->inner_outer = inner_outer ? 1 : 0;
-    hs->snap = mirror.snap_dev;
     if (cudaMemcpyAsync(dst, hs, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess)
         return fail(cuda_error(cudaGetLastError(), "upload state"));
     if (inner_outer) {
@@ -291,7 +366,8 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
             if (n_bound <= tail_nodes && nnz_bound <= 8ll * tail_nodes) {
                 timer.mark(KP_PHASE_TAIL, level);
                 const int32_t before = launches;
-                st = launch_tail(dst, w, rating, o->matcher, level, level_end, n_bound, epoch, s, &launches);
+                st = launch_tail(dst, w, rating, o->matcher, level, level_end, n_bound,
+                                 o->tail_block_nodes ? o->tail_block_nodes : 2048, epoch, s, &launches);
                 timer.mark(-1, level);
                 if (st != KP_OK) return bail(st);
                 level_launches[(size_t)level] += launches - before;
@@ -372,50 +448,11 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     }
     for (auto &ev : ring) cudaEventDestroy(ev);
 
-    // assemble the hierarchy from the table
-    int last = 0;
-    while (last + 1 < MAX_LEVELS && (hs->lv[last + 1].flags & LV_BUILT)) last++;
-    for (int l = 1; l <= last; l++) {
-        const DevLevel &D = hs->lv[l];
-        kp_level kl;
-        kl.n = D.n;
-        kl.nnz = D.nnz;
-        kl.xadj = D.xadj;
-        kl.adjncy = D.adjncy;
-        kl.ewgt = D.ewgt;
-        kl.vwgt = D.vwgt;
-        kl.owned = true;
-        h->levels.push_back(kl);
-    }
-    for (int l = 0; l < last; l++) h->levels[(size_t)l].map = hs->lv[l].map;
-    h->levels[(size_t)last].map = nullptr;
-    if (batch) {
-        for (int l = 1; l <= last; l++) h->levels[(size_t)l].goff = hs->lv[l].goff;
-        if (cudaMemcpyAsync(h->glevels.data(), h->glevels_dev, sizeof(int32_t) * (size_t)G, cudaMemcpyDeviceToHost,
-                            s) != cudaSuccess ||
-            cudaStreamSynchronize(s) != cudaSuccess)
-            return fail(cuda_error(cudaGetLastError(), "read graph levels"));
-    }
-    h->per_level.resize((size_t)last);
-    int32_t total_rounds = 0;
-    int64_t total_matched = 0;
-    for (int l = 0; l < last; l++) {
-        kp_level_profile &P = h->per_level[(size_t)l];
-        const Counters &C = hs->ctr[l];
-        P.n = hs->lv[l].n;
-        P.nnz = hs->lv[l].nnz;
-        P.rounds = suitor ? 1 : C.rounds;
-        P.searches = (int64_t)C.searches;
-        P.failed_cas = (int64_t)C.failed_cas;
-        P.launches = level_launches[(size_t)l];
-        total_rounds += P.rounds;
-        total_matched += (int64_t)hs->lv[l].n - hs->lv[l + 1].n;
-    }
-    h->total_rounds = total_rounds;
-    h->total_matched = total_matched;
+    st = assemble_hierarchy(h, hs, suitor, G, level_launches.data(), s);
+    if (st != KP_OK) return fail(st);
     timer.accumulate(&h->total, h->per_level);
     h->total.launches = launches;
-    h->total.rounds = total_rounds;
+    h->total.rounds = h->total_rounds;
     h->total.n = n0;
     h->total.nnz = nnz0;
     for (const auto &lp : h->per_level) {
@@ -427,3 +464,238 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
 }
 
 }  // namespace kp
+
+// ---------------------------------------------------------------------------
+// captured plans: the whole hierarchy in one persistent launch, recorded
+// once into a CUDA graph and replayed
+// ---------------------------------------------------------------------------
+struct kp_plan {
+    kp_graph g{};
+    kp_options o{};
+    kp::BatchSpec b{};
+    bool batch = false;
+    int32_t G = 0;
+    int device = 0;
+    cudaStream_t s0 = nullptr;   // allocations are stream-ordered on it
+    cudaStream_t cap = nullptr;  // capture stream (the default stream cannot capture)
+    kp::Scratch sc;
+    kp::Work w{};
+    kp::DevState *dst = nullptr;
+    int32_t *glevels_dev = nullptr, *gid0 = nullptr;
+    char *arena = nullptr;
+    unsigned long long arena_cap = 0;
+    kp::DevState *hs_init = nullptr, *hs_read = nullptr;   // pinned
+    kp::LevelSnap *snap = nullptr, *snap_dev = nullptr;    // mapped
+    int32_t *glevels_init = nullptr;                       // pinned ones
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int32_t launches = 0;
+    int32_t block_nodes = 2048;
+    ~kp_plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        kp::dev_free(arena, s0);
+        kp::dev_free(glevels_dev, s0);
+        kp::dev_free(gid0, s0);
+        if (hs_init) cudaFreeHost(hs_init);
+        if (hs_read) cudaFreeHost(hs_read);
+        if (snap) cudaFreeHost(snap);
+        if (glevels_init) cudaFreeHost(glevels_init);
+        if (cap) cudaStreamDestroy(cap);
+    }
+};
+
+namespace kp {
+
+kp_status plan_capture(kp_plan *p) {
+    cudaStream_t s = p->cap;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->exec = nullptr;
+    p->graph = nullptr;
+    p->launches = 0;
+    KP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    kp_status st = KP_OK;
+    const int32_t n0 = p->g.n;
+    if (cudaMemsetAsync(p->w.status, 0, sizeof(TileStatus) * (size_t)(scan_tiles(n0) + 1), s) != cudaSuccess ||
+        cudaMemcpyAsync(p->dst, p->hs_init, sizeof(DevState), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = cuda_error(cudaGetLastError(), "capture: state");
+    if (st == KP_OK && p->batch) {
+        if (cudaMemcpyAsync(p->glevels_dev, p->glevels_init, sizeof(int32_t) * (size_t)p->G, cudaMemcpyHostToDevice,
+                            s) != cudaSuccess)
+            st = cuda_error(cudaGetLastError(), "capture: graph levels");
+        if (st == KP_OK) st = launch_graph_ids(n0, p->G, p->b.node_offsets, p->gid0, s, &p->launches);
+    }
+    if (st == KP_OK && p->o.rating == KP_RATING_INNER_OUTER)
+        st = launch_out_weight(p->dst, n0, p->g.xadj, p->g.ewgt, p->hs_init->lv[0].outw, s, &p->launches);
+    if (st == KP_OK) {
+        const int level_end = p->o.max_levels + (p->batch ? 1 : 0);
+        st = launch_tail(p->dst, p->w, p->o.rating, p->o.matcher, 0, level_end, n0, p->block_nodes, 0, s,
+                         &p->launches);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (st != KP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (ce != cudaSuccess) return cuda_error(ce, "end capture");
+    p->graph = graph;
+    KP_CUDA(cudaGraphInstantiate(&p->exec, graph, 0));
+    return KP_OK;
+}
+
+kp_status plan_create_impl(const kp_graph *g, int32_t num_graphs, const int32_t *node_offsets, const uint64_t *seeds,
+                           const int32_t *stop_sizes, const kp_options *o, cudaStream_t s, kp_plan **out) {
+    if (g->n <= 0) return set_error(KP_ERR_INVALID, "a plan needs a non-empty graph");
+    if (num_graphs < 0) return set_error(KP_ERR_INVALID, "negative num_graphs");
+    BatchSpec b;
+    b.num_graphs = num_graphs;
+    b.node_offsets = node_offsets;
+    b.seeds = seeds;
+    b.stop_sizes = stop_sizes;
+    // checks the options, the batch offsets and (with o->validate) the input
+    // once, by an ordinary coarsening in the plan's mode
+    kp_options first = *o;
+    first.tail_nodes = 0x7fffffff;
+    first.profile = 0;
+    kp_hierarchy *h0 = nullptr;
+    KP_TRY(coarsen_impl(g, &first, s, &h0, num_graphs > 0 ? &b : nullptr));
+    kp_hierarchy_free(h0);
+
+    kp_plan *p = new kp_plan();
+    p->g = *g;
+    p->o = first;
+    p->o.validate = 0;
+    p->b = b;
+    p->batch = num_graphs > 0;
+    p->G = num_graphs;
+    p->s0 = s;
+    p->sc.s = s;
+    p->block_nodes = o->tail_block_nodes ? o->tail_block_nodes : 2048;
+    auto fail = [&](kp_status st) {
+        delete p;
+        return st;
+    };
+    if (cudaGetDevice(&p->device) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "device"));
+    if (cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(cuda_error(cudaGetLastError(), "capture stream"));
+    if (p->batch) {
+        kp_status st = dev_alloc_n(&p->glevels_dev, num_graphs, s);
+        if (st == KP_OK) st = dev_alloc_n(&p->gid0, g->n, s);
+        if (st != KP_OK) return fail(st);
+        if (cudaMallocHost((void **)&p->glevels_init, sizeof(int32_t) * (size_t)num_graphs) != cudaSuccess)
+            return fail(set_error(KP_ERR_OOM, "pinned graph levels"));
+        for (int32_t i = 0; i < num_graphs; i++) p->glevels_init[i] = 1;
+    }
+    kp_status st = alloc_work(p->sc, p->w, g->n, g->nnz, &p->o, p->batch ? &p->b : nullptr, p->glevels_dev, &p->dst);
+    if (st != KP_OK) return fail(st);
+    if (cudaMallocHost((void **)&p->hs_init, sizeof(DevState)) != cudaSuccess ||
+        cudaMallocHost((void **)&p->hs_read, sizeof(DevState)) != cudaSuccess ||
+        cudaHostAlloc((void **)&p->snap, sizeof(LevelSnap) * MAX_LEVELS, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&p->snap_dev, p->snap, 0) != cudaSuccess)
+        return fail(set_error(KP_ERR_OOM, "pinned plan state"));
+    p->arena_cap = initial_arena(&p->o, g->n, g->nnz);
+    st = dev_alloc((void **)&p->arena, p->arena_cap, s);
+    if (st != KP_OK) return fail(st);
+    init_state(p->hs_init, g, &p->o, p->batch ? &p->b : nullptr, p->gid0, p->arena, p->arena_cap, p->snap_dev);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "sync"));
+    st = plan_capture(p);
+    if (st != KP_OK) return fail(st);
+    *out = p;
+    return KP_OK;
+}
+
+kp_status plan_run_impl(kp_plan *p, cudaStream_t s, kp_hierarchy **out) {
+    for (int attempt = 0;; attempt++) {
+        std::memset(p->snap, 0, sizeof(LevelSnap) * MAX_LEVELS);
+        KP_CUDA(cudaGraphLaunch(p->exec, s));
+        KP_CUDA(cudaMemcpyAsync(p->hs_read, p->dst, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+        KP_CUDA(cudaStreamSynchronize(s));
+        if (p->hs_read->err & ERR_TIMEOUT) return set_error(KP_ERR_TIMEOUT, "a bounded wait gave up");
+        if (!p->hs_read->overflow) break;
+        if (attempt >= 8) return set_error(KP_ERR_OOM, "the plan's arena kept overflowing");
+        // the arena was too small: a larger one, the captured state upload
+        // reads the new image, and the run starts over
+        const unsigned long long cap =
+            align256(std::max<unsigned long long>(p->arena_cap * 2, 2 * p->hs_read->arena_used + 4096));
+        char *arena = nullptr;
+        KP_TRY(dev_alloc((void **)&arena, cap, s));
+        dev_free(p->arena, s);
+        p->arena = arena;
+        p->arena_cap = cap;
+        init_state(p->hs_init, &p->g, &p->o, p->batch ? &p->b : nullptr, p->gid0, p->arena, p->arena_cap,
+                   p->snap_dev);
+        if (p->o.rating == KP_RATING_INNER_OUTER) {   // Out lives at the arena start: record again
+            KP_CUDA(cudaStreamSynchronize(s));
+            KP_TRY(plan_capture(p));
+        }
+    }
+    kp_hierarchy *h = new kp_hierarchy();
+    h->stream = s;
+    h->device = p->device;
+    h->num_graphs = p->G;
+    h->glevels_dev = p->glevels_dev;
+    h->gid0 = p->gid0;
+    kp_level l0;
+    l0.n = p->g.n;
+    l0.nnz = p->g.nnz;
+    l0.xadj = const_cast<int32_t *>(p->g.xadj);
+    l0.adjncy = const_cast<int32_t *>(p->g.adjncy);
+    l0.ewgt = const_cast<int32_t *>(p->g.ewgt);
+    l0.vwgt = const_cast<int32_t *>(p->g.vwgt);
+    l0.owned = false;
+    l0.goff = p->batch ? const_cast<int32_t *>(p->b.node_offsets) : nullptr;
+    h->levels.push_back(l0);
+    const kp_status st = assemble_hierarchy(h, p->hs_read, p->o.matcher == KP_MATCHER_SUITOR, p->G, nullptr, s);
+    if (st != KP_OK) {
+        delete h;
+        return st;
+    }
+    h->total.launches = p->launches;
+    h->total.rounds = h->total_rounds;
+    h->total.n = p->g.n;
+    h->total.nnz = p->g.nnz;
+    for (const auto &lp : h->per_level) {
+        h->total.searches += lp.searches;
+        h->total.failed_cas += lp.failed_cas;
+    }
+    *out = h;
+    return KP_OK;
+}
+
+}  // namespace kp
+
+extern "C" {
+
+kp_status kp_plan_create(const kp_graph *g, int32_t num_graphs, const int32_t *node_offsets, const uint64_t *seeds,
+                         const int32_t *stop_sizes, const kp_options *o, kp_stream s, kp_plan **out) {
+    if (!g || !out) return kp::set_error(KP_ERR_INVALID, "null argument");
+    *out = nullptr;
+    kp_options def;
+    kp_options_default(&def);
+    try {
+        return kp::plan_create_impl(g, num_graphs, node_offsets, seeds, stop_sizes, o ? o : &def, (cudaStream_t)s,
+                                    out);
+    } catch (const std::bad_alloc &) {
+        return kp::set_error(KP_ERR_OOM, "host allocation failed");
+    }
+}
+
+kp_status kp_plan_run(kp_plan *p, kp_stream s, kp_hierarchy **out) {
+    if (!p || !out) return kp::set_error(KP_ERR_INVALID, "null argument");
+    *out = nullptr;
+    try {
+        return kp::plan_run_impl(p, (cudaStream_t)s, out);
+    } catch (const std::bad_alloc &) {
+        return kp::set_error(KP_ERR_OOM, "host allocation failed");
+    }
+}
+
+void kp_plan_destroy(kp_plan *p) {
+    if (!p) return;
+    cudaStreamSynchronize(p->s0);
+    delete p;
+}
+
+}  // extern "C"

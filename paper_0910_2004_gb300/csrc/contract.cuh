@@ -130,6 +130,8 @@ struct CView {
     int32_t *tmp_adj, *tmp_w, *big_adj, *big_w, *degp, *outw;
     int32_t *const *lists;
     Counters *ctr;
+    int32_t sort_shared_max;   // longest row sorted in shared memory (<= MID_MAX)
+    int32_t radix_bits;        // bits per pass of the radix path
 };
 
 __device__ __forceinline__ bool load_view(DevState *st, int level, const Work &w, CView &v) {
@@ -137,6 +139,8 @@ __device__ __forceinline__ bool load_view(DevState *st, int level, const Work &w
     if (!(L.flags & LV_ACTIVE)) return false;
     v.ctr = &st->ctr[level];
     v.cn = v.ctr->cn;
+    v.sort_shared_max = st->sort_shared_max;
+    v.radix_bits = st->radix_bits;
     v.xadj = L.xadj;
     v.adjncy = L.adjncy;
     v.ewgt = L.ewgt;
@@ -254,7 +258,7 @@ static __device__ void phase_contract_small(DevState *st, int level, const Work 
         if (x < p.cn) {
             members(p, (int32_t)x, xa, da, xb, db);
             const int32_t L = da + db;
-            cls = L <= TNET ? 0 : L <= 32 ? 1 : L <= 128 ? 2 : L <= MID_MAX ? 3 : 4;
+            cls = L <= TNET ? 0 : L <= 32 ? 1 : L <= 128 ? 2 : L <= p.sort_shared_max ? 3 : 4;
         }
 #pragma unroll
         for (int c = 1; c <= 4; c++) {
@@ -502,7 +506,7 @@ static __device__ void contract_block_smem(const CView &p, int32_t x, int32_t *k
 // 1. gather (map(u), omega) without the contracted edge into the slot at
 //    off[x] (tmp or big, chosen so that the last pass ends in big), counting
 //    the digits of every radix pass on the way
-// 2. stable LSD radix sort by coarse neighbour, 8 bits per pass, ping-pong
+// 2. stable LSD radix sort by coarse neighbour, radix_bits (4..8) bits per pass, ping-pong
 //    between tmp and big; a chunk is ranked warp by warp (match masks, item
 //    by item in index order) and the warps' digit counts are scanned
 // 3. merge equal neighbours from big into tmp (run heads by ballots, run
@@ -511,7 +515,7 @@ constexpr int RADIX_ITEMS = 8;
 constexpr int RADIX_CHUNK = CONTRACT_BLOCK * RADIX_ITEMS;
 
 struct BigSmem {
-    int32_t hist[4][256];
+    int32_t hist[8][256];
     int32_t base[256];
     int32_t chunk_tot[256];
     int32_t wcnt[CONTRACT_BLOCK / 32][256];
@@ -533,7 +537,9 @@ static __device__ void contract_block_radix(const CView &p, int32_t x, int passe
     int32_t *src_v = (passes & 1) ? p.tmp_w + o : p.big_w + o;
     int32_t *dst_k = (passes & 1) ? p.big_adj + o : p.tmp_adj + o;
     int32_t *dst_v = (passes & 1) ? p.big_w + o : p.tmp_w + o;
-    for (int i = threadIdx.x; i < 4 * 256; i += CONTRACT_BLOCK) (&sm.hist[0][0])[i] = 0;
+    const int rb = p.radix_bits;
+    const int32_t dmask = (1 << rb) - 1;
+    for (int i = threadIdx.x; i < 8 * 256; i += CONTRACT_BLOCK) (&sm.hist[0][0])[i] = 0;
     if (threadIdx.x == 0) sm.s_carry = 0;
     __syncthreads();
     // 1. gather (the order of the kept entries does not matter: they are
@@ -557,7 +563,7 @@ static __device__ void contract_block_radix(const CView &p, int32_t x, int passe
                 const int32_t r = at + __popc(m & lt);
                 src_k[r] = t;
                 src_v[r] = wv;
-                for (int ps = 0; ps < passes; ps++) atomicAdd(&sm.hist[ps][(t >> (8 * ps)) & 255], 1);
+                for (int ps = 0; ps < passes; ps++) atomicAdd(&sm.hist[ps][(t >> (rb * ps)) & dmask], 1);
             }
         }
     }
@@ -565,7 +571,7 @@ static __device__ void contract_block_radix(const CView &p, int32_t x, int passe
     const int32_t M = sm.s_carry;   // == off[x+1] - off[x]
     // 2. radix passes
     for (int pass = 0; pass < passes; pass++) {
-        const int shift = 8 * pass;
+        const int shift = rb * pass;
         {
             uint64_t tot;
             sm.base[threadIdx.x] =
@@ -582,7 +588,7 @@ static __device__ void contract_block_radix(const CView &p, int32_t x, int passe
                 const bool valid = i < M;
                 kk[j] = valid ? src_k[i] : 0;
                 vv[j] = valid ? src_v[i] : 0;
-                const int d = valid ? ((kk[j] >> shift) & 255) : 256 + lane;   // invalid lanes: unique
+                const int d = valid ? ((kk[j] >> shift) & dmask) : 256 + lane;   // invalid lanes: unique
                 const unsigned peers = __match_any_sync(0xffffffffu, d);
                 const int wr = __popc(peers & lt);
                 rk[j] = valid ? sm.wcnt[warp][d] + wr : 0;
@@ -606,7 +612,7 @@ static __device__ void contract_block_radix(const CView &p, int32_t x, int passe
             for (int j = 0; j < RADIX_ITEMS; j++) {
                 const int32_t i = c0 + (warp * RADIX_ITEMS + j) * 32 + lane;
                 if (i < M) {
-                    const int d = (kk[j] >> shift) & 255;
+                    const int d = (kk[j] >> shift) & dmask;
                     const int32_t r = sm.base[d] + sm.wcnt[warp][d] + rk[j];
                     dst_k[r] = kk[j];
                     dst_v[r] = vv[j];
@@ -722,7 +728,7 @@ static __device__ void phase_contract_overflow(DevState *st, int level, const Wo
         if (count > 0) {
             int bits = 1;
             while (bits < 31 && ((int64_t)1 << bits) < (int64_t)p.cn) bits++;
-            const int passes = (bits + 7) / 8;
+            const int passes = (bits + p.radix_bits - 1) / p.radix_bits;
             for (int32_t li = blockIdx.x; li < count; li += gridDim.x)
                 contract_block_radix(p, p.lists[4][li], passes, sm.big);
         }

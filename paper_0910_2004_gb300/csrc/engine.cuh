@@ -76,7 +76,9 @@ struct DevState {
     int32_t stop;       // coarsening has ended
     int32_t overflow;   // 1 + the level whose arrays did not fit the arena
     int32_t err;        // ERR_TIMEOUT from a bounded wait
-    int32_t pad;
+    int32_t suitor_lanes;      // 0: from the mean degree
+    int32_t sort_shared_max;   // longest row sorted in shared memory
+    int32_t radix_bits;        // bits per radix pass (4..8)
     LevelSnap *snap;    // host-mapped, one per level
     GridBarrier tail_bar;
 };
@@ -356,6 +358,6 @@ kp_status launch_relabel(const LevelLaunch &L, cudaStream_t s, int32_t *launches
 kp_status launch_contract(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
 kp_status launch_csr(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
 kp_status launch_tail(DevState *st, const Work &w, int rating, int matcher, int first, int last, int32_t n_bound,
-                      int32_t epoch0, cudaStream_t s, int32_t *launches);
+                      int32_t block_nodes, int32_t epoch0, cudaStream_t s, int32_t *launches);
 
 }  // namespace kp

@@ -393,7 +393,7 @@ __device__ void phase_suitor(DevState *st, int level, const Work &w) {
     if (FROM_LIST) {
         suitor_wide<R>(L, w, ctr, &st->err);
     } else {
-        switch (suitor_group(L.n, L.nnz)) {
+        switch (st->suitor_lanes ? st->suitor_lanes : suitor_group(L.n, L.nnz)) {
         case 1: suitor_body<R, 1, 32>(L, w, ctr, &st->err); break;
         case 4: suitor_body<R, 4, 128>(L, w, ctr, &st->err); break;
         case 8: suitor_body<R, 8, 512>(L, w, ctr, &st->err); break;

@@ -65,7 +65,8 @@ struct ServerGroup;
 
 struct ServerRequest {
     uint64_t id = 0;
-    std::vector<int32_t> xadj, adjncy, ewgt, vwgt;
+    std::vector<int32_t> own;   // the server's copy (empty when borrowed)
+    const int32_t *xadj = nullptr, *adjncy = nullptr, *ewgt = nullptr, *vwgt = nullptr;
     int32_t n = 0, nnz = 0;
     kp_request_params params{};
     int64_t footprint = 0;  // while running
@@ -158,15 +159,25 @@ kp_status run_group(kp_server *S, ServerGroup *g) {
         eoff[i + 1] = (int32_t)nnz;
     }
     if (n >= (1ll << 31) || nnz >= (1ll << 31)) return set_error(KP_ERR_OVERFLOW, "group too large");
-    std::vector<int32_t> hx((size_t)n + 1), ha((size_t)nnz), hw((size_t)nnz), hc((size_t)n);
-    for (size_t i = 0; i < G; i++) {
-        ServerRequest *r = g->reqs[i];
-        for (int32_t v = 0; v <= r->n; v++) hx[(size_t)off[i] + v] = r->xadj[(size_t)v] + eoff[i];
-        for (int32_t e = 0; e < r->nnz; e++) {
-            ha[(size_t)eoff[i] + e] = r->adjncy[(size_t)e] + off[i];
-            hw[(size_t)eoff[i] + e] = r->ewgt[(size_t)e];
+    // host arrays of the group's graph: a single request's own, or the union
+    std::vector<int32_t> hx, ha, hw, hc;
+    const int32_t *px = g->reqs[0]->xadj, *pa = g->reqs[0]->adjncy, *pw = g->reqs[0]->ewgt, *pc = g->reqs[0]->vwgt;
+    if (G > 1) {
+        hx.resize((size_t)n + 1);
+        ha.resize((size_t)nnz);
+        hw.resize((size_t)nnz);
+        hc.resize((size_t)n);
+        for (size_t i = 0; i < G; i++) {
+            ServerRequest *r = g->reqs[i];
+            for (int32_t v = 0; v <= r->n; v++) hx[(size_t)off[i] + v] = r->xadj[(size_t)v] + eoff[i];
+            for (int32_t e = 0; e < r->nnz; e++) ha[(size_t)eoff[i] + e] = r->adjncy[(size_t)e] + off[i];
+            std::memcpy(hw.data() + eoff[i], r->ewgt, sizeof(int32_t) * (size_t)r->nnz);
+            std::memcpy(hc.data() + off[i], r->vwgt, sizeof(int32_t) * (size_t)r->n);
         }
-        std::memcpy(hc.data() + off[i], r->vwgt.data(), sizeof(int32_t) * (size_t)r->n);
+        px = hx.data();
+        pa = ha.data();
+        pw = hw.data();
+        pc = hc.data();
     }
     int32_t *dx, *da, *dw, *dc, *doff, *dstops;
     uint64_t *dseeds;
@@ -187,12 +198,12 @@ kp_status run_group(kp_server *S, ServerGroup *g) {
         seeds[i] = g->reqs[i]->params.seed;
         stops[i] = g->reqs[i]->params.stop_size;
     }
-    KP_CUDA(cudaMemcpyAsync(dx, hx.data(), sizeof(int32_t) * hx.size(), cudaMemcpyHostToDevice, s));
+    KP_CUDA(cudaMemcpyAsync(dx, px, sizeof(int32_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s));
     if (nnz > 0) {
-        KP_CUDA(cudaMemcpyAsync(da, ha.data(), sizeof(int32_t) * ha.size(), cudaMemcpyHostToDevice, s));
-        KP_CUDA(cudaMemcpyAsync(dw, hw.data(), sizeof(int32_t) * hw.size(), cudaMemcpyHostToDevice, s));
+        KP_CUDA(cudaMemcpyAsync(da, pa, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
+        KP_CUDA(cudaMemcpyAsync(dw, pw, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
     }
-    if (n > 0) KP_CUDA(cudaMemcpyAsync(dc, hc.data(), sizeof(int32_t) * hc.size(), cudaMemcpyHostToDevice, s));
+    if (n > 0) KP_CUDA(cudaMemcpyAsync(dc, pc, sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice, s));
     KP_CUDA(cudaMemcpyAsync(doff, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, s));
     KP_CUDA(cudaMemcpyAsync(dseeds, seeds.data(), sizeof(uint64_t) * G, cudaMemcpyHostToDevice, s));
     KP_CUDA(cudaMemcpyAsync(dstops, stops.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s));
@@ -254,20 +265,32 @@ bool fits(const kp_server *S, const ServerRequest *r) {
     return S->used == 0 || S->used + r->footprint <= S->cfg.hbm_budget_bytes;
 }
 
+// The request a worker takes next: the oldest one, or for a worker kept for
+// small requests the oldest small one; end() when it does not fit yet.
+std::deque<ServerRequest *>::iterator next_request(kp_server *S, bool small_only) {
+    auto it = S->queue.begin();
+    if (small_only)
+        while (it != S->queue.end() && (*it)->n > S->cfg.batch_max_nodes) ++it;
+    if (it != S->queue.end() && !fits(S, *it)) it = S->queue.end();
+    return it;
+}
+
 void worker_main(kp_server *S, int wi) {
     cudaSetDevice(S->device);
+    const bool small_only = wi < S->cfg.small_workers;
     for (;;) {
         ServerGroup *g = new ServerGroup();
         g->s = S->streams[(size_t)wi];
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_work.wait(lk, [&] { return S->stopping || (!S->queue.empty() && fits(S, S->queue.front())); });
+            S->cv_work.wait(lk, [&] { return S->stopping || next_request(S, small_only) != S->queue.end(); });
             if (S->stopping) {
                 delete g;
                 return;
             }
-            ServerRequest *head = S->queue.front();
-            S->queue.pop_front();
+            auto hit = next_request(S, small_only);
+            ServerRequest *head = *hit;
+            S->queue.erase(hit);
             g->reqs.push_back(head);
             g->footprint = head->footprint;
             g->resident = head->resident;
@@ -333,7 +356,8 @@ extern "C" {
 
 kp_status kp_server_create(const kp_server_config *cfg, kp_server **out) {
     if (!cfg || !out) return set_error(KP_ERR_INVALID, "null argument");
-    if (cfg->workers < 1 || cfg->workers > 64 || cfg->max_batch < 1 || cfg->hbm_budget_bytes <= 0)
+    if (cfg->workers < 1 || cfg->workers > 64 || cfg->max_batch < 1 || cfg->hbm_budget_bytes <= 0 ||
+        cfg->small_workers < 0 || cfg->small_workers >= cfg->workers)
         return set_error(KP_ERR_INVALID, "bad server configuration");
     kp_server *S = new kp_server();
     S->cfg = *cfg;
@@ -365,19 +389,34 @@ kp_status kp_server_submit(kp_server *S, const kp_graph *g, const kp_request_par
     if (!S || !g || !p || !id) return set_error(KP_ERR_INVALID, "null argument");
     if (g->n < 0 || g->nnz < 0 || (g->n > 0 && (!g->xadj || !g->vwgt)) || (g->nnz > 0 && (!g->adjncy || !g->ewgt)))
         return set_error(KP_ERR_INVALID, "bad graph");
-    if (p->k < 1 || !(p->eps >= 0.0) || p->eps > 1000.0) return set_error(KP_ERR_INVALID, "bad request parameters");
+    if (p->k < 1 || !(p->eps >= 0.0) || p->eps > 1000.0 || (p->flags & ~KP_REQUEST_BORROW))
+        return set_error(KP_ERR_INVALID, "bad request parameters");
     const double t_in = S->now_us();   // latency includes the host copy
     ServerRequest *r = new ServerRequest();
-    try {
-        r->n = g->n;
-        r->nnz = g->nnz;
-        r->xadj.assign(g->xadj, g->xadj + g->n + 1);
-        r->adjncy.assign(g->adjncy, g->adjncy + g->nnz);
-        r->ewgt.assign(g->ewgt, g->ewgt + g->nnz);
-        r->vwgt.assign(g->vwgt, g->vwgt + g->n);
-    } catch (...) {
-        delete r;
-        return set_error(KP_ERR_OOM, "host copy of the request");
+    r->n = g->n;
+    r->nnz = g->nnz;
+    if (p->flags & KP_REQUEST_BORROW) {
+        r->xadj = g->xadj;
+        r->adjncy = g->adjncy;
+        r->ewgt = g->ewgt;
+        r->vwgt = g->vwgt;
+    } else {
+        const size_t n1 = (size_t)g->n + 1, m = (size_t)g->nnz, n = (size_t)g->n;
+        try {
+            r->own.resize(n1 + 2 * m + n);
+        } catch (...) {
+            delete r;
+            return set_error(KP_ERR_OOM, "host copy of the request");
+        }
+        int32_t *b = r->own.data();
+        std::memcpy(b, g->xadj, 4 * n1);
+        if (m) std::memcpy(b + n1, g->adjncy, 4 * m);
+        if (m) std::memcpy(b + n1 + m, g->ewgt, 4 * m);
+        if (n) std::memcpy(b + n1 + 2 * m, g->vwgt, 4 * n);
+        r->xadj = b;
+        r->adjncy = b + n1;
+        r->ewgt = b + n1 + m;
+        r->vwgt = b + n1 + 2 * m;
     }
     r->params = *p;
     r->resident = resident_bytes(g->n, g->nnz);

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(MATCH_BLOCK) k_tail(DevState *st, int first, i
 namespace {
 
 template <int R, bool SUITOR>
-kp_status launch_tail_rs(DevState *st, const Work &w, int first, int last, int32_t n_bound, int32_t epoch0,
+kp_status launch_tail_rs(DevState *st, const Work &w, int first, int last, int32_t n_bound, int32_t block_nodes, int32_t epoch0,
                          cudaStream_t s) {
     static const int occ = [] {
         int o = 0;
@@ -73,7 +73,7 @@ kp_status launch_tail_rs(DevState *st, const Work &w, int first, int last, int32
             o = 1;
         return o > 0 ? o : 1;
     }();
-    const int64_t want = ((int64_t)std::max<int32_t>(n_bound, 1) + 2047) / 2048;
+    const int64_t want = ((int64_t)std::max<int32_t>(n_bound, 1) + block_nodes - 1) / block_nodes;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)occ * num_sms()));
     DevState *a0 = st;
     int a1 = first, a2 = last;
@@ -86,29 +86,29 @@ kp_status launch_tail_rs(DevState *st, const Work &w, int first, int last, int32
 
 template <int R>
 kp_status launch_tail_r(DevState *st, const Work &w, int matcher, int first, int last, int32_t n_bound,
-                        int32_t epoch0, cudaStream_t s) {
-    if (matcher == KP_MATCHER_SUITOR) return launch_tail_rs<R, true>(st, w, first, last, n_bound, epoch0, s);
-    return launch_tail_rs<R, false>(st, w, first, last, n_bound, epoch0, s);
+                        int32_t block_nodes, int32_t epoch0, cudaStream_t s) {
+    if (matcher == KP_MATCHER_SUITOR) return launch_tail_rs<R, true>(st, w, first, last, n_bound, block_nodes, epoch0, s);
+    return launch_tail_rs<R, false>(st, w, first, last, n_bound, block_nodes, epoch0, s);
 }
 
 }  // namespace
 
 kp_status launch_tail(DevState *st, const Work &w, int rating, int matcher, int first, int last, int32_t n_bound,
-                      int32_t epoch0, cudaStream_t s, int32_t *launches) {
+                      int32_t block_nodes, int32_t epoch0, cudaStream_t s, int32_t *launches) {
     kp_status r;
     switch (rating) {
     case KP_RATING_EXPANSION_STAR2:
-        r = launch_tail_r<KP_RATING_EXPANSION_STAR2>(st, w, matcher, first, last, n_bound, epoch0, s);
+        r = launch_tail_r<KP_RATING_EXPANSION_STAR2>(st, w, matcher, first, last, n_bound, block_nodes, epoch0, s);
         break;
     case KP_RATING_INNER_OUTER:
-        r = launch_tail_r<KP_RATING_INNER_OUTER>(st, w, matcher, first, last, n_bound, epoch0, s);
+        r = launch_tail_r<KP_RATING_INNER_OUTER>(st, w, matcher, first, last, n_bound, block_nodes, epoch0, s);
         break;
-    case KP_RATING_WEIGHT: r = launch_tail_r<KP_RATING_WEIGHT>(st, w, matcher, first, last, n_bound, epoch0, s); break;
+    case KP_RATING_WEIGHT: r = launch_tail_r<KP_RATING_WEIGHT>(st, w, matcher, first, last, n_bound, block_nodes, epoch0, s); break;
     case KP_RATING_EXPANSION:
-        r = launch_tail_r<KP_RATING_EXPANSION>(st, w, matcher, first, last, n_bound, epoch0, s);
+        r = launch_tail_r<KP_RATING_EXPANSION>(st, w, matcher, first, last, n_bound, block_nodes, epoch0, s);
         break;
     case KP_RATING_EXPANSION_STAR:
-        r = launch_tail_r<KP_RATING_EXPANSION_STAR>(st, w, matcher, first, last, n_bound, epoch0, s);
+        r = launch_tail_r<KP_RATING_EXPANSION_STAR>(st, w, matcher, first, last, n_bound, block_nodes, epoch0, s);
         break;
     default: return set_error(KP_ERR_UNSUPPORTED, "unknown rating");
     }

@@ -73,9 +73,10 @@ def request_pool(seed):
     return reqs
 
 
-def submit_all(sv, reqs):
-    return [sv.submit(r["g"].xadj, r["g"].adjncy, r["g"].ewgt, r["g"].vwgt, r["k"], r["eps"], r["seed"], r["stop"])
-            for r in reqs]
+def submit_all(sv, reqs, borrow_every=0):
+    return [sv.submit(r["g"].xadj, r["g"].adjncy, r["g"].ewgt, r["g"].vwgt, r["k"], r["eps"], r["seed"], r["stop"],
+                      borrow=bool(borrow_every) and i % borrow_every == 0)
+            for i, r in enumerate(reqs)]
 
 
 def collect(sv, ids, reqs):
@@ -115,8 +116,8 @@ def test_requests_equal_oracle_alone_and_in_the_mix(matcher):
     with B().Server(workers=1, max_batch=1, matcher=matcher) as alone:
         a = collect(alone, submit_all(alone, reqs), reqs)
     assert all(x["group_size"] == 1 for x in a)
-    with B().Server(workers=3, max_batch=16, batch_max_nodes=4096, matcher=matcher) as mix:
-        m = collect(mix, submit_all(mix, reqs), reqs)
+    with B().Server(workers=3, max_batch=16, batch_max_nodes=4096, small_workers=1, matcher=matcher) as mix:
+        m = collect(mix, submit_all(mix, reqs, borrow_every=2), reqs)
     assert max(x["group_size"] for x in m) > 1     # some requests did run merged
     for r, x, y in zip(reqs, a, m):
         for key in ("num_levels", "coarsest_n", "cut", "total_c", "l_max", "imbalance"):
@@ -176,4 +177,7 @@ def test_fifo_order_and_errors():
             sv.release(i)
     with pytest.raises(B().KpError) as e:
         B().Server(workers=0)
+    assert e.value.status == B().KP_ERR_INVALID
+    with pytest.raises(B().KpError) as e:
+        B().Server(workers=2, small_workers=2)        # nobody left for large requests
     assert e.value.status == B().KP_ERR_INVALID
