@@ -459,16 +459,19 @@ void kp_server_destroy(kp_server *sv);
  * Captured plans (the paper has no counterpart).  kp_plan_create records the
  * coarsening of one graph (num_graphs = 0) or of a batch (num_graphs > 0,
  * arguments as kp_coarsen_batch) into a CUDA graph: the state upload, the
- * batch's graph ids, Out (innerOuter) and ONE persistent cooperative launch
- * that builds the whole hierarchy level after level (tail_nodes is taken as
- * 2^31-1).  kp_plan_run replays it on any stream and returns the hierarchy.
+ * batch's graph ids, Out (innerOuter), the per-phase launches of the levels
+ * that a first, checking coarsening found above the tail threshold
+ * (o->tail_nodes; their grids sized by that run) and one persistent
+ * cooperative launch for every later level.  With tail_nodes = 2^31-1 the
+ * whole hierarchy is that one persistent launch.  kp_plan_run replays the
+ * graph on any stream and returns the hierarchy.
  * The input arrays, offsets, seeds and stop sizes are BORROWED for the
  * plan's life and read at every run: their contents may change between runs
  * (the sizes n, nnz and num_graphs may not).  Results equal kp_coarsen[_batch]
  * with the same options.
- * kp_plan_create first coarsens once in the plan's mode (this checks the
- * options, offsets and, with o->validate, the input), then allocates the
- * plan's scratch and arena and records the graph; it synchronises s.
+ * kp_plan_create first coarsens once (this checks the options, offsets and,
+ * with o->validate, the input), then allocates the plan's scratch and arena
+ * and records the graph; it synchronises s.
  * Errors: those of kp_coarsen[_batch]; KP_ERR_INVALID for n = 0;
  * KP_ERR_CUDA when the device cannot record the launch sequence.
  * ------------------------------------------------------------------------ */

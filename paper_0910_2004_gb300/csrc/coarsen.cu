@@ -491,6 +491,7 @@ struct kp_plan {
     cudaGraphExec_t exec = nullptr;
     int32_t launches = 0;
     int32_t block_nodes = 2048;
+    std::vector<std::pair<int32_t, int32_t>> sizes;   // (n, nnz) per level of the checking run
     ~kp_plan() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -528,11 +529,39 @@ kp_status plan_capture(kp_plan *p) {
     }
     if (st == KP_OK && p->o.rating == KP_RATING_INNER_OUTER)
         st = launch_out_weight(p->dst, n0, p->g.xadj, p->g.ewgt, p->hs_init->lv[0].outw, s, &p->launches);
-    if (st == KP_OK) {
-        const int level_end = p->o.max_levels + (p->batch ? 1 : 0);
-        st = launch_tail(p->dst, p->w, p->o.rating, p->o.matcher, 0, level_end, n0, p->block_nodes, 0, s,
-                         &p->launches);
+    // the levels the checking run found above the tail threshold as separate
+    // launches (grids sized by that run's sizes; every kernel covers any
+    // size), the rest in one persistent launch
+    const int level_end = p->o.max_levels + (p->batch ? 1 : 0);
+    const int64_t tail_nodes = p->o.tail_nodes == 0 ? TAIL_NODES : p->o.tail_nodes;
+    int K = 0;
+    if (tail_nodes >= 0)
+        while (K + 1 < (int)p->sizes.size() && K < level_end &&
+               !(p->sizes[(size_t)K].first <= tail_nodes && p->sizes[(size_t)K].second <= 8 * tail_nodes))
+            K++;
+    else
+        K = std::min<int>((int)p->sizes.size() - 1, level_end);
+    int32_t epoch = 0;
+    for (int level = 0; level < K && st == KP_OK; level++) {
+        LevelLaunch LL;
+        LL.st = p->dst;
+        LL.w = p->w;
+        LL.level = level;
+        LL.rating = p->o.rating;
+        LL.matcher = p->o.matcher;
+        LL.n_bound = p->sizes[(size_t)level].first;
+        LL.nnz_bound = std::max(p->sizes[(size_t)level].second, 1);
+        LL.epoch_relabel = ++epoch;
+        LL.epoch_degscan = ++epoch;
+        st = launch_matching(LL, s, &p->launches);
+        if (st == KP_OK) st = launch_relabel(LL, s, &p->launches);
+        if (st == KP_OK) st = launch_contract(LL, s, &p->launches);
+        if (st == KP_OK) st = launch_csr(LL, s, &p->launches);
     }
+    if (st == KP_OK && K < level_end)
+        st = launch_tail(p->dst, p->w, p->o.rating, p->o.matcher, K, level_end,
+                         std::max(1, p->sizes[(size_t)std::min<int>(K, (int)p->sizes.size() - 1)].first),
+                         p->block_nodes, epoch, s, &p->launches);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(s, &graph);
     if (st != KP_OK) {
@@ -555,12 +584,13 @@ kp_status plan_create_impl(const kp_graph *g, int32_t num_graphs, const int32_t 
     b.seeds = seeds;
     b.stop_sizes = stop_sizes;
     // checks the options, the batch offsets and (with o->validate) the input
-    // once, by an ordinary coarsening in the plan's mode
+    // once, by an ordinary coarsening; its level sizes size the recorded grids
     kp_options first = *o;
-    first.tail_nodes = 0x7fffffff;
     first.profile = 0;
     kp_hierarchy *h0 = nullptr;
     KP_TRY(coarsen_impl(g, &first, s, &h0, num_graphs > 0 ? &b : nullptr));
+    std::vector<std::pair<int32_t, int32_t>> sizes;
+    for (const kp_level &l : h0->levels) sizes.emplace_back(l.n, l.nnz);
     kp_hierarchy_free(h0);
 
     kp_plan *p = new kp_plan();
@@ -573,6 +603,7 @@ kp_status plan_create_impl(const kp_graph *g, int32_t num_graphs, const int32_t 
     p->s0 = s;
     p->sc.s = s;
     p->block_nodes = o->tail_block_nodes ? o->tail_block_nodes : 2048;
+    p->sizes = sizes;
     auto fail = [&](kp_status st) {
         delete p;
         return st;

@@ -501,7 +501,7 @@ static __device__ void contract_block_smem(const CView &p, int32_t x, int32_t *k
     __syncthreads();
 }
 
-// Rows longer than MID_MAX gathered entries: one block, RADIX_ITEMS entries
+// Rows longer than the shared-memory limit: one block, RADIX_ITEMS entries
 // per thread and chunk.
 // 1. gather (map(u), omega) without the contracted edge into the slot at
 //    off[x] (tmp or big, chosen so that the last pass ends in big), counting
@@ -511,8 +511,6 @@ static __device__ void contract_block_smem(const CView &p, int32_t x, int32_t *k
 //    by item in index order) and the warps' digit counts are scanned
 // 3. merge equal neighbours from big into tmp (run heads by ballots, run
 //    sums by atomics)
-constexpr int RADIX_ITEMS = 8;
-constexpr int RADIX_CHUNK = CONTRACT_BLOCK * RADIX_ITEMS;
 
 struct BigSmem {
     int32_t hist[8][256];
@@ -524,7 +522,9 @@ struct BigSmem {
     int32_t s_carry;
 };
 
+template <int RADIX_ITEMS>
 static __device__ void contract_block_radix(const CView &p, int32_t x, int passes, BigSmem &sm) {
+    constexpr int RADIX_CHUNK = CONTRACT_BLOCK * RADIX_ITEMS;
     static_assert(CONTRACT_BLOCK == 256, "one thread per digit");
     constexpr int NW = CONTRACT_BLOCK / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -699,6 +699,10 @@ union OverflowSmem {
     BigSmem big;
 };
 
+// MID: the classes of up to sort_shared_max entries (warps, blocks in shared
+// memory); BIG: the radix class.  The separate launches keep the radix
+// path's registers out of the many-warp classes.
+template <bool MID, bool BIG, int RADIX_ITEMS>
 static __device__ void phase_contract_overflow(DevState *st, int level, const Work &w, OverflowSmem &sm) {
     CView p;
     if (!load_view(st, level, w, p)) return;
@@ -707,30 +711,32 @@ static __device__ void phase_contract_overflow(DevState *st, int level, const Wo
     const int warp = threadIdx.x >> 5;
     constexpr int NW = CONTRACT_BLOCK / 32;
     const int64_t gw = (int64_t)blockIdx.x * NW + warp, nw = (int64_t)gridDim.x * NW;
-    {
-        const int32_t count = p.ctr->nclass[1];
-        for (int64_t li = gw; li < count; li += nw) contract_warp32(p, p.lists[1][li]);
+    if (MID) {
+        {
+            const int32_t count = p.ctr->nclass[1];
+            for (int64_t li = gw; li < count; li += nw) contract_warp32(p, p.lists[1][li]);
+        }
+        {
+            const int32_t count = p.ctr->nclass[2];
+            for (int64_t li = gw; li < count; li += nw)
+                contract_warp_smem(p, p.lists[2][li], sm.warp.K[warp], sm.warp.V[warp], sm.warp.S[warp]);
+        }
+        __syncthreads();
+        {
+            const int32_t count = p.ctr->nclass[3];
+            for (int32_t li = blockIdx.x; li < count; li += gridDim.x)
+                contract_block_smem(p, p.lists[3][li], sm.mid.keys, sm.mid.vals, sm.mid.sums, sm.mid.s_red);
+        }
+        __syncthreads();
     }
-    {
-        const int32_t count = p.ctr->nclass[2];
-        for (int64_t li = gw; li < count; li += nw)
-            contract_warp_smem(p, p.lists[2][li], sm.warp.K[warp], sm.warp.V[warp], sm.warp.S[warp]);
-    }
-    __syncthreads();
-    {
-        const int32_t count = p.ctr->nclass[3];
-        for (int32_t li = blockIdx.x; li < count; li += gridDim.x)
-            contract_block_smem(p, p.lists[3][li], sm.mid.keys, sm.mid.vals, sm.mid.sums, sm.mid.s_red);
-    }
-    __syncthreads();
-    {
+    if (BIG) {
         const int32_t count = p.ctr->nclass[4];
         if (count > 0) {
             int bits = 1;
             while (bits < 31 && ((int64_t)1 << bits) < (int64_t)p.cn) bits++;
             const int passes = (bits + p.radix_bits - 1) / p.radix_bits;
             for (int32_t li = blockIdx.x; li < count; li += gridDim.x)
-                contract_block_radix(p, p.lists[4][li], passes, sm.big);
+                contract_block_radix<RADIX_ITEMS>(p, p.lists[4][li], passes, sm.big);
         }
     }
 }

@@ -35,9 +35,10 @@ def check_graph(h, gi, g, ref):
             assert np.array_equal(got["map"], ref.maps[l]), (gi, l, "map")
 
 
+@pytest.mark.parametrize("tail", [0, 0x7fffffff, -1, 2000])
 @pytest.mark.parametrize("matcher", ["suitor", "handshake"])
 @pytest.mark.parametrize("rating", ["expansion*2", "innerOuter"])
-def test_batch_plan_replays_equal_oracle(rating, matcher):
+def test_batch_plan_replays_equal_oracle(rating, matcher, tail):
     import torch
     graphs = [I.rgg2d(int(n), 70 + i, wmax=16) for i, n in enumerate(I.batch_rgg_sizes(20, 3, 1024, 6000))]
     graphs += [I.rmat(10, 3), I.grid2d(17, 5), I.star_graph(200),
@@ -47,7 +48,7 @@ def test_batch_plan_replays_equal_oracle(rating, matcher):
     stops = np.where(np.arange(len(graphs)) % 3 == 0, 8, 40).astype(np.int32)
     dg = B().DeviceGraph.from_csr(U)
     refs = [O.coarsen(g, rating, int(seeds[i]), int(stops[i])) for i, g in enumerate(graphs)]
-    with B().Plan(dg, off, seeds, stops, rating=rating, matcher=matcher) as plan:
+    with B().Plan(dg, off, seeds, stops, rating=rating, matcher=matcher, tail_nodes=tail) as plan:
         for rep in range(3):
             h = plan.run()
             for gi, g in enumerate(graphs):
