@@ -6,18 +6,16 @@
 
 namespace kp {
 
+// 4 resident blocks per SM (64 registers) measured best for the small rows
 __global__ void __launch_bounds__(CONTRACT_BLOCK, 4) k_contract_small(DevState *st, int level, Work w) {
     phase_contract_small(st, level, w);
 }
 
-__global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_radix(DevState *st, int level, Work w) {
-    __shared__ OverflowSmem sm;
-    phase_contract_overflow<false, true, 8>(st, level, w, sm);
-}
-
 __global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_overflow(DevState *st, int level, Work w) {
     __shared__ OverflowSmem sm;
-    phase_contract_overflow<true, false, 8>(st, level, w, sm);
+    // 2 radix entries per thread and chunk keep the kernel at 48 registers,
+    // so the many-warp classes run at full occupancy and the classes overlap
+    phase_contract_overflow<true, true, 2>(st, level, w, sm);
 }
 
 __global__ void k_compact(DevState *st, int level, Work w) { phase_compact(st, level, w); }
@@ -51,8 +49,7 @@ kp_status launch_contract(const LevelLaunch &L, cudaStream_t s, int32_t *launche
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)1 << 30));
     k_contract_small<<<grid, CONTRACT_BLOCK, 0, s>>>(L.st, L.level, L.w);
     k_contract_overflow<<<num_sms() * 8, CONTRACT_BLOCK, 0, s>>>(L.st, L.level, L.w);
-    k_contract_radix<<<num_sms() * 2, CONTRACT_BLOCK, 0, s>>>(L.st, L.level, L.w);
-    *launches += 3;
+    *launches += 2;
     KP_CUDA(cudaGetLastError());
     return KP_OK;
 }

@@ -700,8 +700,7 @@ union OverflowSmem {
 };
 
 // MID: the classes of up to sort_shared_max entries (warps, blocks in shared
-// memory); BIG: the radix class.  The separate launches keep the radix
-// path's registers out of the many-warp classes.
+// memory); BIG: the radix class, RADIX_ITEMS entries per thread and chunk.
 template <bool MID, bool BIG, int RADIX_ITEMS>
 static __device__ void phase_contract_overflow(DevState *st, int level, const Work &w, OverflowSmem &sm) {
     CView p;

@@ -570,7 +570,10 @@ __global__ void k_level_begin(DevState *st, int level, Work w) {
 }
 
 template <int R, bool FROM_LIST>
-__global__ void __launch_bounds__(MATCH_BLOCK) k_suitor(DevState *st, int level, Work w) {
+#ifndef KP_SUITOR_MIN_BLOCKS
+#define KP_SUITOR_MIN_BLOCKS 3   // resident blocks per SM the register budget must allow
+#endif
+__global__ void __launch_bounds__(MATCH_BLOCK, KP_SUITOR_MIN_BLOCKS) k_suitor(DevState *st, int level, Work w) {
     phase_suitor<R, FROM_LIST>(st, level, w);
 }
 

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(MATCH_BLOCK) k_tail(DevState *st, int first, i
         if (!grid_sync(bar, err, lim)) return;
         phase_contract_small(st, level, w);
         if (!grid_sync(bar, err, lim)) return;
-        phase_contract_overflow<true, true, 4>(st, level, w, sm);
+        phase_contract_overflow<true, true, 2>(st, level, w, sm);
         if (!grid_sync(bar, err, lim)) return;
         {
             DegScanOp op;
