@@ -506,10 +506,9 @@ def run_batch(args, wl):
         h = plan.run()
         e1.record(stream)
         cs = h.coarsest_sizes()
-        part, poff = I.batch_partition(cs, k, seed)
-        part = part + k * np.repeat(np.arange(G, dtype=np.int32), cs)   # block ids of the union
-        cp = torch.from_numpy(part.astype(np.int32)).to("cuda")
-        co = torch.from_numpy(poff).to("cuda")
+        cp, co = I.batch_partition_torch(cs, k, seed)
+        cp += k * torch.repeat_interleave(torch.arange(G, device="cuda", dtype=torch.int32),
+                                          torch.as_tensor(cs, device="cuda").long())   # block ids of the union
         h.project(cp, co, fine)
         res = B.cut_gain(dg, fine, k * G, eps, block_w=bw, gain=gain, target=target)
         tot = h.profile()
@@ -610,9 +609,10 @@ def run_batch(args, wl):
             d.copy_(hst, non_blocking=True)
         h = plan_e.run()
         cs = h.coarsest_sizes()
-        part, poff = I.batch_partition(cs, k, si)
-        part = part + k * np.repeat(np.arange(G, dtype=np.int32), cs)
-        h.project(torch.from_numpy(part.astype(np.int32)).to("cuda"), torch.from_numpy(poff).to("cuda"), fine)
+        cp, co = I.batch_partition_torch(cs, k, si)
+        cp += k * torch.repeat_interleave(torch.arange(G, device="cuda", dtype=torch.int32),
+                                          torch.as_tensor(cs, device="cuda").long())
+        h.project(cp, co, fine)
         B.cut_gain(dge, fine, k * G, eps, block_w=bw, gain=gain, target=target)
         outs[0].copy_(fine, non_blocking=True)
         outs[1].copy_(gain, non_blocking=True)

@@ -39,7 +39,8 @@ struct EvalAcc {
     long long max_c;
     long long max_bw;
     int32_t err;
-    int32_t pad[3];
+    int32_t long_count;   // rows left to the group kernel by the thread kernel
+    int32_t pad[2];
 };
 
 constexpr int EVAL_BLOCK = 256;
@@ -63,9 +64,11 @@ struct CutGainParams {
 // One G-lane group per node.  The adjacent blocks of v are visited in
 // increasing id order (each step finds the smallest block id above the last
 // one and sums the weight towards it), so the first block reaching the
-// largest connection is the smallest such id.
-template <int G>
-__global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p) {
+// largest connection is the smallest such id.  FROM_LIST: only the rows of
+// `rows` (count in acc->long_count), without the node weights (the thread
+// kernel has added those for every node).
+template <int G, bool FROM_LIST = false>
+__global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p, const int32_t *rows = nullptr) {
     __shared__ unsigned long long s_bw[BW_SMEM];
     __shared__ unsigned long long s_red[EVAL_BLOCK / 32];
     __shared__ long long s_max[EVAL_BLOCK / 32];
@@ -81,7 +84,9 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p) {
     unsigned long long ext_acc = 0, c_acc = 0;
     long long cmax = 0;
     int32_t bad = 0;
-    for (int64_t v = gid; v < p.n; v += ngroups) {
+    const int64_t count = FROM_LIST ? (int64_t)*(volatile int32_t *)&p.acc->long_count : (int64_t)p.n;
+    for (int64_t i = gid; i < count; i += ngroups) {
+        const int64_t v = FROM_LIST ? (int64_t)rows[i] : i;
         const int32_t pv = p.part[v];
         const bool pv_ok = pv >= 0 && pv < p.k;
         const int32_t beg = p.xadj[v], end = p.xadj[v + 1];
@@ -152,10 +157,12 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p) {
             }
         }
         if (gl == 0) {
-            const int32_t c = p.vwgt[v];
             p.gain[v] = (best >= 0 ? best_conn : 0) - inw;
             p.target[v] = best;
             ext_acc += (unsigned long long)(tot - inw);
+        }
+        if (gl == 0 && !FROM_LIST) {
+            const int32_t c = p.vwgt[v];
             c_acc += (unsigned long long)(long long)c;
             cmax = max(cmax, (long long)c);
             if (!pv_ok) {
@@ -204,6 +211,143 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p) {
             if (s_bw[i]) atomicAdd(&p.block_w[i], s_bw[i]);
 }
 
+// One thread per node for rows of at most EVAL_TROW entries (the row is read
+// into registers with independent loads; the connection to every adjacent
+// block is summed over the row, the largest wins, ties to the smaller block
+// id, as in the group kernel); longer rows are listed for the group kernel.
+// Node weights, their sum and maximum and the block weights are added here
+// for every node; with k above BW_SMEM the block weights of a warp's nodes
+// are combined per block before the global atomic.
+constexpr int EVAL_TROW = 16;
+
+template <bool SMEM_BW>
+__global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain_rows(CutGainParams p, int32_t *long_rows) {
+    __shared__ unsigned long long s_bw[SMEM_BW ? BW_SMEM : 1];
+    __shared__ unsigned long long s_red[EVAL_BLOCK / 32];
+    __shared__ long long s_max[EVAL_BLOCK / 32];
+    if (SMEM_BW)
+        for (int i = threadIdx.x; i < p.k; i += blockDim.x) s_bw[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    unsigned long long ext_acc = 0, c_acc = 0;
+    long long cmax = 0;
+    int32_t bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); v0 < p.n; v0 += stride) {
+        const int64_t v = v0 + lane;
+        const bool live = v < p.n;
+        int32_t pv = -1, c = 0, beg = 0, d = 0;
+        if (live) {
+            pv = p.part[v];
+            c = p.vwgt[v];
+            beg = p.xadj[v];
+            d = p.xadj[v + 1] - beg;
+        }
+        const bool pv_ok = pv >= 0 && pv < p.k;
+        if (live) {
+            c_acc += (unsigned long long)(long long)c;
+            cmax = max(cmax, (long long)c);
+            if (!pv_ok) bad = 1;
+        }
+        if (SMEM_BW) {
+            if (live && pv_ok) atomicAdd(&s_bw[pv], (unsigned long long)(long long)c);
+        } else {
+            const int key = (live && pv_ok) ? pv : -1 - lane;   // unique for lanes without a block
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            long long sum = 0;
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                const long long cj = __shfl_sync(0xffffffffu, (long long)c, j);
+                if ((peers >> j) & 1u) sum += cj;
+            }
+            if (live && pv_ok && (peers & ((1u << lane) - 1u)) == 0)
+                atomicAdd(&p.block_w[pv], (unsigned long long)sum);
+        }
+        if (!live) continue;
+        if (d > EVAL_TROW) {
+            long_rows[atomicAdd(&p.acc->long_count, 1)] = (int32_t)v;
+            continue;
+        }
+        int32_t b[EVAL_TROW], w[EVAL_TROW];
+#pragma unroll
+        for (int i = 0; i < EVAL_TROW; i++)
+            if (i < d) b[i] = p.adjncy[beg + i];
+#pragma unroll
+        for (int i = 0; i < EVAL_TROW; i++)
+            if (i < d) w[i] = p.ewgt[beg + i];
+#pragma unroll
+        for (int i = 0; i < EVAL_TROW; i++)
+            if (i < d) {
+                const int32_t bb = p.part[b[i] - p.id_base];
+                if (bb < 0 || bb >= p.k) {
+                    bad = 1;
+                    b[i] = -1;
+                } else {
+                    b[i] = bb;
+                }
+            }
+        long long inw = 0, tot = 0;
+#pragma unroll
+        for (int i = 0; i < EVAL_TROW; i++)
+            if (i < d && b[i] >= 0) {
+                tot += w[i];
+                if (b[i] == pv) inw += w[i];
+            }
+        int32_t best = -1;
+        long long best_conn = 0;
+#pragma unroll
+        for (int i = 0; i < EVAL_TROW; i++) {
+            if (i < d && b[i] >= 0 && b[i] != pv) {
+                long long conn = 0;
+#pragma unroll
+                for (int j = 0; j < EVAL_TROW; j++)
+                    if (j < d && b[j] == b[i]) conn += w[j];
+                if (conn > best_conn || (conn == best_conn && best >= 0 && b[i] < best)) {
+                    best_conn = conn;
+                    best = b[i];
+                }
+            }
+        }
+        p.gain[v] = (best >= 0 ? best_conn : 0) - inw;
+        p.target[v] = best;
+        ext_acc += (unsigned long long)(tot - inw);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ext_acc += __shfl_xor_sync(0xffffffffu, ext_acc, o);
+        c_acc += __shfl_xor_sync(0xffffffffu, c_acc, o);
+        cmax = max(cmax, __shfl_xor_sync(0xffffffffu, cmax, o));
+    }
+    const int warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_red[warp] = ext_acc;
+        s_max[warp] = cmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long e = 0;
+        long long m = 0;
+        for (int w2 = 0; w2 < EVAL_BLOCK / 32; w2++) {
+            e += s_red[w2];
+            m = max(m, s_max[w2]);
+        }
+        atomicAdd(&p.acc->ext_sum, e);
+        atomicMax(&p.acc->max_c, m);
+    }
+    __syncthreads();
+    if (lane == 0) s_red[warp] = c_acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w2 = 0; w2 < EVAL_BLOCK / 32; w2++) t += s_red[w2];
+        atomicAdd(&p.acc->total_c, t);
+    }
+    if (bad) atomicOr(&p.acc->err, ERR_BAD_PART);
+    if (SMEM_BW)
+        for (int i = threadIdx.x; i < p.k; i += blockDim.x)
+            if (s_bw[i]) atomicAdd(&p.block_w[i], s_bw[i]);
+}
+
 __global__ void k_max_block(int32_t k, const long long *block_w, EvalAcc *acc) {
     long long m = 0;
     for (int i = threadIdx.x; i < k; i += blockDim.x) m = max(m, block_w[i]);
@@ -238,7 +382,8 @@ kp_status check_eval_args(const kp_graph *g, const int32_t *part, int32_t k, dou
 
 // Evaluation with the accumulators in caller-provided device memory `acc`.
 kp_status cut_gain_with(const kp_graph *g, const int32_t *part, int32_t k, double eps, kp_cut_gain_out *out,
-                        cudaStream_t s, EvalAcc *acc, EvalAcc *host_acc, int32_t id_base = 0) {
+                        cudaStream_t s, EvalAcc *acc, EvalAcc *host_acc, int32_t id_base = 0,
+                        int32_t *long_rows = nullptr) {
     KP_TRY(check_eval_args(g, part, k, eps, out));
     KP_CUDA(cudaMemsetAsync(acc, 0, sizeof(EvalAcc), s));
     KP_CUDA(cudaMemsetAsync(out->block_w, 0, sizeof(int64_t) * (size_t)k, s));
@@ -262,10 +407,22 @@ kp_status cut_gain_with(const kp_graph *g, const int32_t *part, int32_t k, doubl
             const int64_t want = ((int64_t)g->n * G + EVAL_BLOCK - 1) / EVAL_BLOCK;
             return (int)std::max<int64_t>(1, std::min<int64_t>(want, grid_cap));
         };
-        if (avg <= 5.0) k_cut_gain<4><<<grid_for(4), EVAL_BLOCK, 0, s>>>(p);
-        else if (avg <= 10.0) k_cut_gain<8><<<grid_for(8), EVAL_BLOCK, 0, s>>>(p);
-        else if (avg <= 20.0) k_cut_gain<16><<<grid_for(16), EVAL_BLOCK, 0, s>>>(p);
-        else k_cut_gain<32><<<grid_for(32), EVAL_BLOCK, 0, s>>>(p);
+        if (long_rows && avg <= 12.0) {
+            // rows of up to 16 entries one thread each, the longer ones listed
+            // for one warp each
+            if (k <= BW_SMEM) k_cut_gain_rows<true><<<grid_for(1), EVAL_BLOCK, 0, s>>>(p, long_rows);
+            else k_cut_gain_rows<false><<<grid_for(1), EVAL_BLOCK, 0, s>>>(p, long_rows);
+            KP_CUDA(cudaGetLastError());
+            k_cut_gain<32, true><<<grid_cap, EVAL_BLOCK, 0, s>>>(p, long_rows);
+        } else if (avg <= 5.0) {
+            k_cut_gain<4><<<grid_for(4), EVAL_BLOCK, 0, s>>>(p);
+        } else if (avg <= 10.0) {
+            k_cut_gain<8><<<grid_for(8), EVAL_BLOCK, 0, s>>>(p);
+        } else if (avg <= 20.0) {
+            k_cut_gain<16><<<grid_for(16), EVAL_BLOCK, 0, s>>>(p);
+        } else {
+            k_cut_gain<32><<<grid_for(32), EVAL_BLOCK, 0, s>>>(p);
+        }
         KP_CUDA(cudaGetLastError());
         k_max_block<<<1, 1024, 0, s>>>(k, reinterpret_cast<const long long *>(out->block_w), acc);
         KP_CUDA(cudaGetLastError());
@@ -393,7 +550,10 @@ kp_status cut_gain_slice(const kp_graph *view, int32_t id_base, const int32_t *p
         dev_free(acc, s);
         return set_error(KP_ERR_OOM, "pinned host accumulator");
     }
-    const kp_status st = cut_gain_with(view, part, k, eps, out, s, acc, host_acc, id_base);
+    int32_t *rows = nullptr;
+    kp_status st = dev_alloc_n(&rows, view->n, s);
+    if (st == KP_OK) st = cut_gain_with(view, part, k, eps, out, s, acc, host_acc, id_base, rows);
+    dev_free(rows, s);
     dev_free(acc, s);
     return st;
 }
@@ -409,7 +569,10 @@ kp_status cut_gain_impl(const kp_graph *g, const int32_t *part, int32_t k, doubl
         dev_free(acc, s);
         return set_error(KP_ERR_OOM, "pinned host accumulator");
     }
-    const kp_status st = cut_gain_with(g, part, k, eps, out, s, acc, host_acc);
+    int32_t *rows = nullptr;
+    kp_status st = dev_alloc_n(&rows, g->n, s);
+    if (st == KP_OK) st = cut_gain_with(g, part, k, eps, out, s, acc, host_acc, 0, rows);
+    dev_free(rows, s);
     dev_free(acc, s);
     return st;
 }

@@ -29,7 +29,7 @@ __all__ = [
     "CSRGraph", "from_edges", "grid2d", "grid3d", "rgg2d", "rmat",
     "random_small_graph", "path_graph", "star_graph", "batch_rgg_sizes",
     "random_balanced_partition", "random_partition", "union_graph", "rgg2d_batch", "batch_partition",
-    "rmat_torch", "rgg2d_torch", "served_mix",
+    "rmat_torch", "rgg2d_torch", "served_mix", "batch_partition_torch",
 ]
 
 
@@ -415,3 +415,26 @@ def served_mix(scales=range(12, 23), seed: int = 1, device: str = "cuda"):
         pool.append(("rgg2d", s, rgg2d_torch(1 << s, seed * 1000 + s, device=device)))
         pool.append(("rmat", s, rmat_torch(s, seed * 1000 + s, device=device)))
     return pool
+
+
+def batch_partition_torch(coarse_sizes, k: int, seed: int, device: str = "cuda"):
+    """batch_partition's distribution drawn with torch on `device` (other
+    draws): within each graph a seeded random order dealt round-robin to
+    blocks 0..k-1.  Returns (part int32 tensor of graph-local block ids,
+    offsets int32 tensor [len+1])."""
+    import torch
+    dev = torch.device(device)
+    sizes = torch.as_tensor(np.asarray(coarse_sizes, dtype=np.int64), device=dev)
+    G = int(sizes.numel())
+    N = int(sizes.sum().item()) if G else 0
+    off = torch.zeros(G + 1, dtype=torch.int64, device=dev)
+    if G:
+        off[1:] = torch.cumsum(sizes, 0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    gid = torch.repeat_interleave(torch.arange(G, device=dev), sizes)
+    r = torch.randint(0, 1 << 31, (N,), generator=gen, device=dev, dtype=torch.int64)
+    order = torch.argsort((gid << 31) | r)
+    rank = torch.empty(N, dtype=torch.int64, device=dev)
+    rank[order] = torch.arange(N, device=dev) - off[gid[order]]
+    return (rank % k).to(torch.int32), off.to(torch.int32)

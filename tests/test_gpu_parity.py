@@ -291,7 +291,10 @@ def test_stop_rules():
 # ---------------------------------------------------------------------------
 
 def test_cut_gain_many_k():
-    for g in [I.grid2d(40, 30), I.rmat(11, 2), I.rgg2d(5000, 3, wmax=9)]:
+    # mean degree <= 12 takes the thread-per-row kernel (rows above 16
+    # entries listed for the warp kernel): grids, RGGs, a star, a sparse R-MAT
+    for g in [I.grid2d(40, 30), I.rmat(11, 2), I.rgg2d(5000, 3, wmax=9), I.star_graph(3000),
+              I.rmat(12, 5, edge_factor=4), I.rgg2d(4000, 4, mean_degree=11, wmax=3)]:
         dg = B().DeviceGraph.from_csr(g)
         for k in [1, 2, 3, 64, 256, 3000]:
             check_eval(dg, g, I.random_partition(g.n, k, seed=k), k, 0.03)
