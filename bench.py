@@ -211,6 +211,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--matcher", default="suitor", choices=["suitor", "handshake"])
     ap.add_argument("--tail-nodes", type=int, default=0)
+    ap.add_argument("--no-tune", action="store_true", help="built-in knobs instead of the autotuner's")
     ap.add_argument("--requests", type=int, default=None, help="served: requests per load phase")
     ap.add_argument("--workers", type=int, default=4, help="served: server worker streams")
     args = ap.parse_args()
@@ -246,10 +247,19 @@ def main():
     target = torch.empty(g.n, dtype=torch.int32, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
+    # the tuning knobs, measured on this graph (cached per GPU and shape class)
+    knobs = {"matcher": args.matcher, "tail_nodes": args.tail_nodes}
+    tuning = {"knobs": "built-in (--no-tune)"}
+    if not args.no_tune:
+        cache = os.path.join(os.path.expanduser("~"), ".cache", "paper_0910_2004_gb300", "tune.json")
+        t_tune = time.perf_counter()
+        knobs, trials, from_cache = B.autotune(dg, reps=2, cache=cache, rating=rating, stop_size=stop,
+                                               matcher=args.matcher)
+        tuning = {"knobs": knobs, "trials": len(trials), "from_cache": from_cache,
+                  "seconds": time.perf_counter() - t_tune}
 
     def step(seed, validate=False, want_sizes=False):
-        h = B.coarsen(dg, rating=rating, seed=1, stop_size=stop, validate=validate, profile=True,
-                      matcher=args.matcher, tail_nodes=args.tail_nodes)
+        h = B.coarsen(dg, rating=rating, seed=1, stop_size=stop, validate=validate, profile=True, **knobs)
         L = h.num_levels()
         top, _ = B.kp_hierarchy_level(h.handle, L - 1)
         cpart = torch.from_numpy(I.random_balanced_partition(top.n, k, seed)).to("cuda", non_blocking=False)
@@ -331,7 +341,7 @@ def main():
             return I.random_balanced_partition(nc, kk, 7)
 
         arrs = [pin[x].numpy() for x in ("xadj", "adjncy", "ewgt", "vwgt")]
-        B.pipeline_host(*arrs, k, eps, ip, outputs=outs, rating=rating, seed=1, stop_size=stop)
+        B.pipeline_host(*arrs, k, eps, ip, outputs=outs, rating=rating, seed=1, stop_size=stop, **knobs)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -340,8 +350,7 @@ def main():
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            B.pipeline_host(*arrs, k, eps, ip, outputs=outs, rating=rating, seed=1, stop_size=stop,
-                            matcher=args.matcher)
+            B.pipeline_host(*arrs, k, eps, ip, outputs=outs, rating=rating, seed=1, stop_size=stop, **knobs)
             e2e_ms.append(1000 * (time.perf_counter() - t0))
         e2e_total = sum(e2e_ms)
         if dist:
@@ -392,6 +401,7 @@ def main():
         "path_roofline": {"bytes_per_step": path_bytes, "achieved_gbs": path_bytes / (total_ms / steps / 1000) / 1e9,
                           "frac": path_bytes / (total_ms / steps / 1000) / 1e9 / peak},
         "phase_ms_per_step": {**phase_ms, "project": proj_ms / steps, "cut_gain": eval_ms / steps},
+        "tuning": tuning,
         "level_profile": level_profile,
         "clocks": clocks,
         "e2e": e2e_line,

@@ -270,41 +270,54 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain_rows(CutGainParams p, i
         }
         int32_t b[EVAL_TROW], w[EVAL_TROW];
 #pragma unroll
-        for (int i = 0; i < EVAL_TROW; i++)
-            if (i < d) b[i] = p.adjncy[beg + i];
-#pragma unroll
-        for (int i = 0; i < EVAL_TROW; i++)
-            if (i < d) w[i] = p.ewgt[beg + i];
-#pragma unroll
-        for (int i = 0; i < EVAL_TROW; i++)
-            if (i < d) {
-                const int32_t bb = p.part[b[i] - p.id_base];
-                if (bb < 0 || bb >= p.k) {
-                    bad = 1;
-                    b[i] = -1;
-                } else {
-                    b[i] = bb;
-                }
-            }
-        long long inw = 0, tot = 0;
-#pragma unroll
-        for (int i = 0; i < EVAL_TROW; i++)
-            if (i < d && b[i] >= 0) {
-                tot += w[i];
-                if (b[i] == pv) inw += w[i];
-            }
-        int32_t best = -1;
-        long long best_conn = 0;
+        for (int i = 0; i < EVAL_TROW; i++) {
+            if (i >= d) break;
+            b[i] = p.adjncy[beg + i];
+        }
 #pragma unroll
         for (int i = 0; i < EVAL_TROW; i++) {
-            if (i < d && b[i] >= 0 && b[i] != pv) {
-                long long conn = 0;
+            if (i >= d) break;
+            w[i] = p.ewgt[beg + i];
+        }
 #pragma unroll
-                for (int j = 0; j < EVAL_TROW; j++)
-                    if (j < d && b[j] == b[i]) conn += w[j];
-                if (conn > best_conn || (conn == best_conn && best >= 0 && b[i] < best)) {
-                    best_conn = conn;
-                    best = b[i];
+        for (int i = 0; i < EVAL_TROW; i++) {
+            if (i >= d) break;
+            const int32_t bb = p.part[b[i] - p.id_base];
+            if (bb < 0 || bb >= p.k) {
+                bad = 1;
+                b[i] = -1;
+            } else {
+                b[i] = bb;
+            }
+        }
+        long long inw = 0, tot = 0;
+        bool boundary = false;
+#pragma unroll
+        for (int i = 0; i < EVAL_TROW; i++) {
+            if (i >= d) break;
+            if (b[i] >= 0) {
+                tot += w[i];
+                if (b[i] == pv) inw += w[i];
+                else boundary = true;
+            }
+        }
+        int32_t best = -1;
+        long long best_conn = 0;
+        if (boundary) {   // interior nodes (every neighbour in pv) skip the search
+#pragma unroll
+            for (int i = 0; i < EVAL_TROW; i++) {
+                if (i >= d) break;
+                if (b[i] >= 0 && b[i] != pv) {
+                    long long conn = 0;
+#pragma unroll
+                    for (int j = 0; j < EVAL_TROW; j++) {
+                        if (j >= d) break;
+                        if (b[j] == b[i]) conn += w[j];
+                    }
+                    if (conn > best_conn || (conn == best_conn && best >= 0 && b[i] < best)) {
+                        best_conn = conn;
+                        best = b[i];
+                    }
                 }
             }
         }

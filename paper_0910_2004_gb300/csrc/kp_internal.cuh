@@ -308,15 +308,20 @@ namespace kp {
 class PhaseTimer {
   public:
     PhaseTimer(bool on, cudaStream_t s) : on_(on), s_(s) {}
-    ~PhaseTimer() {
-        for (auto &m : marks_) cudaEventDestroy(m.ev);
+    ~PhaseTimer() {   // the events go back to this thread's pool
+        for (auto &m : marks_) pool().push_back(m.ev);
     }
     // Starts `phase_starting` (-1: only ends the running interval) of level
     // `level` (-1: outside the level loop).
     void mark(int phase_starting, int level = -1) {
         if (!on_) return;
         cudaEvent_t e;
-        if (cudaEventCreate(&e) != cudaSuccess) return;
+        if (!pool().empty()) {
+            e = pool().back();
+            pool().pop_back();
+        } else if (cudaEventCreate(&e) != cudaSuccess) {
+            return;
+        }
         cudaEventRecord(e, s_);
         marks_.push_back({e, phase_starting, level});
     }
@@ -334,6 +339,13 @@ class PhaseTimer {
     }
 
   private:
+    // Events are created once per thread and reused (creating one per mark
+    // costs host time inside the enqueue loop).  They belong to the device
+    // that was current when they were made; the pool is per thread.
+    static std::vector<cudaEvent_t> &pool() {
+        thread_local std::vector<cudaEvent_t> p;
+        return p;
+    }
     struct Mark {
         cudaEvent_t ev;
         int phase;
