@@ -129,7 +129,11 @@ typedef enum {
  *   sort_shared_max      coarse rows of up to this many gathered entries are
  *                        sorted by one block in shared memory, longer ones by
  *                        the radix path, 128..2048 (0: 2048)
- *   radix_bits           bits per pass of the radix path, 4..8 (0: 8) */
+ *   radix_bits           bits per pass of the radix path, 4..8 (0: 8)
+ *   cluster_nodes        tail levels with at most this many nodes run in one
+ *                        thread-block cluster (16 CTAs, or 8) whose phases
+ *                        are separated by the hardware cluster barrier
+ *                        (0: 8192; -1: never) */
 typedef struct {
     int32_t rating;
     uint64_t seed;
@@ -146,6 +150,7 @@ typedef struct {
     int32_t tail_block_nodes;
     int32_t sort_shared_max;
     int32_t radix_bits;
+    int32_t cluster_nodes;
 } kp_options;
 
 /* Fills *o with the defaults: EXPANSION_STAR2, seed 1, stop_size 40,
@@ -496,7 +501,8 @@ void kp_plan_destroy(kp_plan *p);
  * Autotuning (the paper has no counterpart).  The tuning knobs of
  * kp_options never change a result, only the time; kp_autotune measures.
  * Coordinate descent from *o over tail_nodes, suitor_lanes (Suitor only),
- * tail_block_nodes, sort_shared_max and radix_bits, in that order: every
+ * tail_block_nodes, sort_shared_max, radix_bits and cluster_nodes, in that
+ * order: every
  * candidate coarsens the caller's graph (num_graphs = 0) or batch
  * (num_graphs > 0, arguments as kp_coarsen_batch) once untimed and `reps`
  * times timed by CUDA events on the stream; a knob keeps the value with the

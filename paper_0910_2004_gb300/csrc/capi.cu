@@ -217,6 +217,7 @@ void kp_options_default(kp_options *o) {
     o->tail_block_nodes = 0;
     o->sort_shared_max = 0;
     o->radix_bits = 0;
+    o->cluster_nodes = 0;
 }
 
 kp_status kp_coarsen(const kp_graph *g, const kp_options *o, kp_stream s, kp_hierarchy **out) {

@@ -100,6 +100,10 @@ kp_status alloc_work(Scratch &sc, Work &w, int32_t n0, int32_t nnz0, const kp_op
     return KP_OK;
 }
 
+// Levels with at most this many nodes run in one thread-block cluster
+// (-1: never).
+int32_t cluster_nodes_of(const kp_options *o) { return o->cluster_nodes == 0 ? 8192 : o->cluster_nodes; }
+
 unsigned long long initial_arena(const kp_options *o, int32_t n0, int32_t nnz0) {
     unsigned long long cap =
         o->arena_bytes > 0
@@ -146,6 +150,7 @@ void init_state(DevState *hs, const kp_graph *g, const kp_options *o, const Batc
     hs->suitor_lanes = o->suitor_lanes;
     hs->sort_shared_max = o->sort_shared_max ? o->sort_shared_max : MID_MAX;
     hs->radix_bits = o->radix_bits ? o->radix_bits : 8;
+    hs->tail_resume = -1;
     hs->snap = snap_dev;
 }
 
@@ -214,7 +219,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
           o->suitor_lanes == 32) ||
         (o->tail_block_nodes != 0 && (o->tail_block_nodes < 256 || o->tail_block_nodes > 16384)) ||
         (o->sort_shared_max != 0 && (o->sort_shared_max < 128 || o->sort_shared_max > MID_MAX)) ||
-        (o->radix_bits != 0 && (o->radix_bits < 4 || o->radix_bits > 8)))
+        (o->radix_bits != 0 && (o->radix_bits < 4 || o->radix_bits > 8)) || o->cluster_nodes < -1)
         return set_error(KP_ERR_INVALID, "bad tuning knob");
     if (o->matcher == KP_MATCHER_HANDSHAKE) {
         if (g_coop_supported < 0) {
@@ -366,8 +371,14 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
             if (n_bound <= tail_nodes && nnz_bound <= 8ll * tail_nodes) {
                 timer.mark(KP_PHASE_TAIL, level);
                 const int32_t before = launches;
-                st = launch_tail(dst, w, rating, o->matcher, level, level_end, n_bound,
-                                 o->tail_block_nodes ? o->tail_block_nodes : 2048, epoch, s, &launches);
+                TailLaunch t;
+                t.first = level;
+                t.last = level_end;
+                t.n_bound = n_bound;
+                t.block_nodes = o->tail_block_nodes ? o->tail_block_nodes : 2048;
+                t.cluster_nodes = cluster_nodes_of(o);
+                t.epoch0 = epoch;
+                st = launch_tail(dst, w, rating, o->matcher, t, s, &launches);
                 timer.mark(-1, level);
                 if (st != KP_OK) return bail(st);
                 level_launches[(size_t)level] += launches - before;
@@ -436,6 +447,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         hs->arena_used = 0;
         hs->overflow = 0;
         hs->stop = 0;
+        hs->tail_resume = -1;
         hs->lv[lo].flags = LV_BUILT | LV_ACTIVE;
         std::memset(&hs->ctr[lo], 0, sizeof(Counters));
         for (int l = lo; l < MAX_LEVELS; l++) {
@@ -559,9 +571,16 @@ kp_status plan_capture(kp_plan *p) {
         if (st == KP_OK) st = launch_csr(LL, s, &p->launches);
     }
     if (st == KP_OK && K < level_end)
-        st = launch_tail(p->dst, p->w, p->o.rating, p->o.matcher, K, level_end,
-                         std::max(1, p->sizes[(size_t)std::min<int>(K, (int)p->sizes.size() - 1)].first),
-                         p->block_nodes, epoch, s, &p->launches);
+    {
+        TailLaunch t;
+        t.first = K;
+        t.last = level_end;
+        t.n_bound = std::max(1, p->sizes[(size_t)std::min<int>(K, (int)p->sizes.size() - 1)].first);
+        t.block_nodes = p->block_nodes;
+        t.cluster_nodes = cluster_nodes_of(&p->o);
+        t.epoch0 = epoch;
+        st = launch_tail(p->dst, p->w, p->o.rating, p->o.matcher, t, s, &p->launches);
+    }
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(s, &graph);
     if (st != KP_OK) {

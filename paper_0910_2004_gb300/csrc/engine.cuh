@@ -79,6 +79,8 @@ struct DevState {
     int32_t suitor_lanes;      // 0: from the mean degree
     int32_t sort_shared_max;   // longest row sorted in shared memory
     int32_t radix_bits;        // bits per radix pass (4..8)
+    int32_t tail_resume;       // first level left to the cluster tail (-1: none)
+    int32_t pad2;
     LevelSnap *snap;    // host-mapped, one per level
     GridBarrier tail_bar;
 };
@@ -357,7 +359,18 @@ kp_status launch_matching(const LevelLaunch &L, cudaStream_t s, int32_t *launche
 kp_status launch_relabel(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
 kp_status launch_contract(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
 kp_status launch_csr(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
-kp_status launch_tail(DevState *st, const Work &w, int rating, int matcher, int first, int last, int32_t n_bound,
-                      int32_t block_nodes, int32_t epoch0, cudaStream_t s, int32_t *launches);
+// The persistent tail from level `first`: levels above cluster_nodes in one
+// cooperative grid (block_nodes nodes per block), the later ones in one
+// thread-block cluster with hardware barriers (cluster_nodes < 0: no
+// cluster part; the grid part hands over through DevState::tail_resume).
+struct TailLaunch {
+    int first, last;
+    int32_t n_bound;
+    int32_t block_nodes;
+    int32_t cluster_nodes;
+    int32_t epoch0;
+};
+kp_status launch_tail(DevState *st, const Work &w, int rating, int matcher, const TailLaunch &t, cudaStream_t s,
+                      int32_t *launches);
 
 }  // namespace kp

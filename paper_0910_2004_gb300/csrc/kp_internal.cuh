@@ -117,11 +117,41 @@ __device__ __forceinline__ int ld_relaxed_i32(const int32_t *p) {
 // All blocks of the grid meet here.  Returns false (and every block returns
 // false soon after) when a wait exceeded spin_limit iterations or another
 // block already flagged an error; the error flag then holds ERR_TIMEOUT.
+__device__ __forceinline__ unsigned cluster_ctas() {
+    unsigned r;
+    asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// A word every block of a one-cluster grid reads with the same value: read
+// between two cluster barriers (no block writes it in between).
+__device__ __forceinline__ int32_t cluster_uniform_read(const int32_t *p) {
+    cluster_barrier();
+    const int32_t v = ld_relaxed_i32(p);
+    cluster_barrier();
+    return v;
+}
+
 __device__ __forceinline__ bool grid_sync(GridBarrier *bar, int32_t *err, long long spin_limit) {
     __shared__ int s_ok;
     if (gridDim.x == 1) {   // one block: a block barrier is a grid barrier
         __syncthreads();
         return ld_relaxed_i32(err) == 0;
+    }
+    if (cluster_ctas() == gridDim.x) {
+        // the grid is one thread-block cluster: the hardware cluster barrier
+        // (release/acquire at cluster scope; every CTA of a cluster is
+        // resident together).  The error flag is read between two barriers,
+        // where no block runs a phase, so every block takes the same
+        // decision and none leaves while the others wait.
+        cluster_barrier();
+        const bool ok = ld_relaxed_i32(err) == 0;
+        cluster_barrier();
+        return ok;
     }
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -1,6 +1,6 @@
 // Autotuner of the coarsening's tuning knobs (lanes per proposing node, the
-// tail launch's threshold and block size, the shared-memory sort limit and
-// the radix width).  None of them changes a result, only the time, so the
+// tail launch's threshold and block size, the shared-memory sort limit, the
+// radix width and the cluster tail's threshold).  None of them changes a result, only the time, so the
 // tuner may pick them by measurement: coordinate descent from the caller's
 // options, every candidate timed on the caller's own graph (or batch) with
 // CUDA events on the caller's stream, the minimum over `reps` runs after one
@@ -89,6 +89,7 @@ extern "C" kp_status kp_autotune(const kp_graph *g, int32_t num_graphs, const in
     knobs.push_back({&kp_options::tail_block_nodes, {512, 1024, 2048, 4096, 8192}});
     knobs.push_back({&kp_options::sort_shared_max, {512, 1024, 2048}});
     knobs.push_back({&kp_options::radix_bits, {6, 7, 8}});
+    knobs.push_back({&kp_options::cluster_nodes, {-1, 8192, 32768, 131072}});
     for (const Knob &k : knobs) {
         if (st != KP_OK) break;
         const int32_t start = cur.*(k.field);

@@ -54,6 +54,7 @@ HUBS = [(lambda: I.rmat(13, 21, edge_factor=64), "expansion*2"), (lambda: I.rmat
     ("sort_shared_max", [128, 512, 1024]),
     ("tail_block_nodes", [256, 16384]),
     ("tail_nodes", [0x7fffffff, 1 << 12]),
+    ("cluster_nodes", [-1, 64, 5000, 1 << 20]),
 ])
 def test_every_knob_value_gives_the_oracle_hierarchy(knob, values):
     for make, rating in HUBS:
