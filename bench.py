@@ -707,7 +707,7 @@ def poisson_arrivals(count, rate, seed):
     return np.cumsum(rng.exponential(1.0 / rate, size=count))
 
 
-def serve_phase(sv, pool, reqs, arrivals, borrow=False):
+def serve_phase(sv, pool, reqs, arrivals, borrow=True):
     """Submits reqs at the given arrival offsets (seconds; None: all at once)
     while a second thread waits for and releases them in order.  Latency of a
     request: from its scheduled arrival to its completion (server clock for
@@ -898,7 +898,8 @@ def run_served(args, wl):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "pool_graphs": len(pool),
                    "requests_per_phase": R, "workers": args.workers, "small_workers": 1, "max_batch": 64,
-                   "host_arrays": "copied by the server at submit (pageable numpy arrays)",
+                   "host_arrays": "pageable numpy arrays of the pool, borrowed by the server (KP_REQUEST_BORROW: "
+                                  "read by the worker's host-to-device copy, no copy at submit)",
                    "batch_max_nodes": 1 << 16, "hbm_budget_gb": budget / 1e9, "matcher": args.matcher,
                    "l2": "inputs of the large requests exceed L2; no flush between requests (a stream)",
                    "parallelism": f"replicas x{world}", "step": "one request"},
