@@ -11,11 +11,15 @@ __global__ void __launch_bounds__(CONTRACT_BLOCK, 4) k_contract_small(DevState *
     phase_contract_small(st, level, w);
 }
 
+__global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_rows32(DevState *st, int level, Work w) {
+    phase_contract_rows32(st, level, w);
+}
+
 __global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_overflow(DevState *st, int level, Work w) {
     __shared__ OverflowSmem sm;
     // 2 radix entries per thread and chunk keep the kernel at 48 registers,
     // so the many-warp classes run at full occupancy and the classes overlap
-    phase_contract_overflow<true, true, 2>(st, level, w, sm);
+    phase_contract_overflow<true, true, 2, false>(st, level, w, sm);
 }
 
 __global__ void k_compact(DevState *st, int level, Work w) { phase_compact(st, level, w); }
@@ -48,8 +52,11 @@ kp_status launch_contract(const LevelLaunch &L, cudaStream_t s, int32_t *launche
     const int64_t want = ((int64_t)std::max<int32_t>(1, L.n_bound) + CONTRACT_BLOCK - 1) / CONTRACT_BLOCK;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)1 << 30));
     k_contract_small<<<grid, CONTRACT_BLOCK, 0, s>>>(L.st, L.level, L.w);
+    // rows of 17..32 entries: one thread each when there are many of them
+    // (decided on the device from the class count), else a warp each
+    k_contract_rows32<<<num_sms() * 8, CONTRACT_BLOCK, 0, s>>>(L.st, L.level, L.w);
     k_contract_overflow<<<num_sms() * 8, CONTRACT_BLOCK, 0, s>>>(L.st, L.level, L.w);
-    *launches += 2;
+    *launches += 3;
     KP_CUDA(cudaGetLastError());
     return KP_OK;
 }

@@ -172,6 +172,7 @@ __device__ __forceinline__ void members(const CView &p, int32_t x, int32_t &xa, 
 // (sentinels last), merged run by run.
 constexpr int TNET = 16;
 
+template <int TNET>
 __device__ __forceinline__ void contract_thread(const CView &p, int32_t x, int32_t xa, int32_t da, int32_t xb,
                                                 int32_t db) {
     constexpr uint64_t SENT64 = (uint64_t)SENT << 32;
@@ -272,7 +273,7 @@ static __device__ void phase_contract_small(DevState *st, int level, const Work 
                 if (mine) p.lists[c][pos + __popc(m & lanemask_lt())] = (int32_t)x;
             }
         }
-        if (cls == 0) contract_thread(p, (int32_t)x, xa, da, xb, db);
+        if (cls == 0) contract_thread<TNET>(p, (int32_t)x, xa, da, xb, db);
     }
 }
 
@@ -699,9 +700,32 @@ union OverflowSmem {
     BigSmem big;
 };
 
+// Rows of 17..32 gathered entries (class 1), one thread each with a
+// 32-entry register network: for the separate launches (a warp per such row
+// leaves half the warp idle; the register network needs its own kernel so
+// that the other classes keep their occupancy).  It takes the class when it
+// has at least ROWS32_MIN rows; fewer go to the overflow kernel's warps.
+constexpr int32_t ROWS32_MIN = 2048;
+
+static __device__ void phase_contract_rows32(DevState *st, int level, const Work &w) {
+    CView p;
+    if (!load_view(st, level, w, p)) return;
+    const int32_t count = p.ctr->nclass[1];
+    if (count < ROWS32_MIN) return;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < count; li += stride) {
+        const int32_t x = p.lists[1][li];
+        int32_t xa, da, xb, db;
+        members(p, x, xa, da, xb, db);
+        contract_thread<32>(p, x, xa, da, xb, db);
+    }
+}
+
 // MID: the classes of up to sort_shared_max entries (warps, blocks in shared
-// memory); BIG: the radix class, RADIX_ITEMS entries per thread and chunk.
-template <bool MID, bool BIG, int RADIX_ITEMS>
+// memory; class 1 with WARP32 always, without it only when the rows32
+// kernel leaves it); BIG: the radix class, RADIX_ITEMS entries per thread
+// and chunk.
+template <bool MID, bool BIG, int RADIX_ITEMS, bool WARP32 = true>
 static __device__ void phase_contract_overflow(DevState *st, int level, const Work &w, OverflowSmem &sm) {
     CView p;
     if (!load_view(st, level, w, p)) return;
@@ -713,7 +737,8 @@ static __device__ void phase_contract_overflow(DevState *st, int level, const Wo
     if (MID) {
         {
             const int32_t count = p.ctr->nclass[1];
-            for (int64_t li = gw; li < count; li += nw) contract_warp32(p, p.lists[1][li]);
+            if (WARP32 || count < ROWS32_MIN)
+                for (int64_t li = gw; li < count; li += nw) contract_warp32(p, p.lists[1][li]);
         }
         {
             const int32_t count = p.ctr->nclass[2];
