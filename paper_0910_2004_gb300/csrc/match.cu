@@ -6,19 +6,22 @@
 
 namespace kp {
 
-// Out(v) = sum of the weights of v's edges (Section 3.1), input level.
+// Out(v) = sum of the weights of v's edges (Section 3.1), input level: 8
+// lanes per node over a grid of resident blocks (grid-stride over nodes).
 __global__ void k_out_weight(int32_t n, const int32_t *__restrict__ xadj, const int32_t *__restrict__ ewgt,
                              int32_t *__restrict__ outw) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t v = t >> 3;
     const int gl = threadIdx.x & 7;
-    if (v >= n) return;
     const unsigned gmask = group_mask<8>();
-    int64_t s = 0;
-    for (int32_t e = xadj[v] + gl; e < xadj[v + 1]; e += 8) s += ewgt[e];
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) >> 3;
+    // the loop bound is the same for the 8 lanes of a group (shuffles below)
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; v < n; v += groups) {
+        int64_t s = 0;
+        const int32_t beg = xadj[v], end = xadj[v + 1];
+        for (int32_t e = beg + gl; e < end; e += 8) s += ewgt[e];
 #pragma unroll
-    for (int off = 4; off > 0; off >>= 1) s += __shfl_xor_sync(gmask, s, off);
-    if (gl == 0) outw[v] = (int32_t)s;
+        for (int off = 4; off > 0; off >>= 1) s += __shfl_xor_sync(gmask, s, off);
+        if (gl == 0) outw[v] = (int32_t)s;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -131,7 +134,8 @@ kp_status launch_check_batch_edges(const kp_graph *g, const int32_t *gid, const 
 kp_status launch_out_weight(DevState *, int32_t n0, const int32_t *xadj, const int32_t *ewgt, int32_t *outw,
                             cudaStream_t s, int32_t *launches) {
     const int64_t threads = (int64_t)n0 * 8;
-    k_out_weight<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(n0, xadj, ewgt, outw);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, (int64_t)num_sms() * 16));
+    k_out_weight<<<grid, 256, 0, s>>>(n0, xadj, ewgt, outw);
     *launches += 1;
     KP_CUDA(cudaGetLastError());
     return KP_OK;
