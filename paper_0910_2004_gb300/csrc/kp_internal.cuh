@@ -136,12 +136,6 @@ __device__ __forceinline__ int32_t cluster_uniform_read(const int32_t *p) {
     return v;
 }
 
-#ifndef KP_BARRIER_FENCES
-#define KP_BARRIER_FENCES 0
-#endif
-#ifndef KP_BARRIER_SLEEP_NS
-#define KP_BARRIER_SLEEP_NS 64
-#endif
 __device__ __forceinline__ bool grid_sync(GridBarrier *bar, int32_t *err, long long spin_limit) {
     __shared__ int s_ok;
     if (gridDim.x == 1) {   // one block: a block barrier is a grid barrier
@@ -163,10 +157,6 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *bar, int32_t *err, long l
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned int gen = ld_acquire_u32(&bar->generation);
-#if KP_BARRIER_FENCES
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&bar->count, 1u);
-#else
         // arrive: acquire-release at gpu scope.  Releasing covers the writes
         // of the whole block (ordered before by the block barrier above); the
         // last arriver has acquired every earlier arrival through the
@@ -174,12 +164,8 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *bar, int32_t *err, long l
         // new generation, which the waiters acquire.
         unsigned int arrived;
         asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(&bar->count) : "memory");
-#endif
         if (arrived == gridDim.x - 1) {
             atomicExch(&bar->count, 0u);
-#if KP_BARRIER_FENCES
-            __threadfence();
-#endif
             st_release_u32(&bar->generation, gen + 1);
         } else {
             long long it = 0;
@@ -190,12 +176,9 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *bar, int32_t *err, long l
                     ok = 0;
                     break;
                 }
-                __nanosleep(KP_BARRIER_SLEEP_NS);
+                __nanosleep(64);
             }
         }
-#if KP_BARRIER_FENCES
-        __threadfence();
-#endif
         if (ok && ld_relaxed_i32(err) != 0) ok = 0;
         s_ok = ok;
     }
