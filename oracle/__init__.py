@@ -9,6 +9,8 @@ oracle.c (compiled here with gcc), the level loop, the stop rule, projection
 and the balance bound are plain Python/numpy below.
 
 Each function names the passage it follows.  All arithmetic is integer.
+The refinement-side helpers at the end (quotient graph, bounded boundary
+search, Section 5) are plain Python/numpy.
 """
 from __future__ import annotations
 
@@ -25,7 +27,7 @@ __all__ = [
     "RATINGS", "Level", "Hierarchy", "build", "lib", "validate", "out_weight",
     "frac_cmp", "splitmix64", "edge_hash", "edge_order", "greedy_matching",
     "handshake_matching", "check_greedy_matching", "contract", "coarsen",
-    "project", "l_max", "cut_gain",
+    "project", "l_max", "cut_gain", "quotient_graph", "boundary_band",
 ]
 
 RATINGS = {"expansion*2": 0, "innerOuter": 1, "weight": 2, "expansion": 3, "expansion*": 4}
@@ -274,3 +276,69 @@ def cut_gain(g, part, k: int, eps: float) -> dict:
     imb = max(0, int(bw[:k].max()) - lm) if k else 0
     return {"cut": int(cut.value), "block_w": bw[:k], "L_max": lm, "imbalance": imb,
             "gain": gain, "target": target}
+
+
+def quotient_graph(g, part, k: int):
+    """Quotient graph Q (Section 5): one node per block, an edge {a, b}
+    whenever an edge of G joins blocks a and b, weighted by the total edge
+    weight between them.  Returned as a symmetric CSR over the k blocks with
+    ascending neighbour blocks: (xadj int32[k+1], adjncy int32[], ewgt
+    int64[])."""
+    g = _as_level(g)
+    part = np.asarray(part, dtype=np.int64)
+    acc = {}
+    for u in range(g.n):
+        pu = int(part[u])
+        for e in range(int(g.xadj[u]), int(g.xadj[u + 1])):
+            pv = int(part[int(g.adjncy[e])])
+            if pv != pu:
+                acc[(pu, pv)] = acc.get((pu, pv), 0) + int(g.ewgt[e])
+    xadj = np.zeros(k + 1, dtype=np.int32)
+    adj, w = [], []
+    for a in range(k):
+        row = sorted((b, c) for (aa, b), c in acc.items() if aa == a)
+        for b, c in row:
+            adj.append(b)
+            w.append(c)
+        xadj[a + 1] = len(adj)
+    return xadj, np.asarray(adj, dtype=np.int32), np.asarray(w, dtype=np.int64)
+
+
+def boundary_band(g, part, depth: int, pair=None) -> np.ndarray:
+    """Bounded breadth-first search from the block boundaries (Section 5):
+    dist[v] = length of a shortest path from v to a boundary node of its own
+    block through nodes of that block, if at most `depth`, else -1.  A
+    boundary node has a neighbour in another block.  With pair = (a, b) only
+    blocks a and b take part: the boundary is the a-b boundary and nodes of
+    other blocks get -2."""
+    g = _as_level(g)
+    part = np.asarray(part, dtype=np.int64)
+    n = g.n
+    dist = np.full(n, -1, dtype=np.int32)
+    inside = np.ones(n, dtype=bool)
+    if pair is not None:
+        a, b = pair
+        inside = (part == a) | (part == b)
+        dist[~inside] = -2
+    frontier = []
+    for v in range(n):
+        if not inside[v]:
+            continue
+        pv = int(part[v])
+        for e in range(int(g.xadj[v]), int(g.xadj[v + 1])):
+            pu = int(part[int(g.adjncy[e])])
+            other = (pu != pv) if pair is None else (pu == (pair[1] if pv == pair[0] else pair[0]))
+            if other and pu != pv:
+                dist[v] = 0
+                frontier.append(v)
+                break
+    for d in range(1, depth + 1):
+        nxt = []
+        for u in frontier:
+            for e in range(int(g.xadj[u]), int(g.xadj[u + 1])):
+                v = int(g.adjncy[e])
+                if dist[v] == -1 and part[v] == part[u]:
+                    dist[v] = d
+                    nxt.append(v)
+        frontier = nxt
+    return dist

@@ -451,3 +451,84 @@ def test_generators_shapes():
     assert O.validate(g) == 0 and g.ewgt.max() > 1
     p = I.random_balanced_partition(1000, 7, 3)
     assert np.bincount(p, minlength=7).max() - np.bincount(p, minlength=7).min() <= 1
+
+
+# ---------------------------------------------------------------------------
+# Section 5: quotient graph and bounded boundary search
+# ---------------------------------------------------------------------------
+
+def test_quotient_graph_of_grid_strips_closed_form():
+    """A 12x9 grid cut into vertical strips of widths 3, 4, 5: the quotient
+    graph is the path 0-1-2 and each edge weighs the strip height (9 unit
+    edges cross each strip border)."""
+    g = I.grid2d(12, 9)
+    xs = np.arange(g.n) % 12
+    part = np.where(xs < 3, 0, np.where(xs < 7, 1, 2)).astype(np.int32)
+    xadj, adj, w = O.quotient_graph(g, part, 3)
+    assert list(xadj) == [0, 1, 3, 4]
+    assert list(adj) == [1, 0, 2, 1]
+    assert list(w) == [9, 9, 9, 9]
+
+
+def test_quotient_graph_weights_sum_to_twice_the_cut():
+    for seed in range(20):
+        rng = np.random.default_rng(seed)
+        g = I.random_small_graph(int(rng.integers(2, 60)), 0.15, seed=seed, wmax=9)
+        k = int(rng.integers(1, 7))
+        part = I.random_partition(g.n, k, seed=seed)
+        xadj, adj, w = O.quotient_graph(g, part, k)
+        assert int(w.sum()) == 2 * O.cut_gain(g, part, k, 0.0)["cut"]
+        # symmetric, sorted rows, no self loops
+        for a in range(k):
+            row = list(adj[xadj[a]:xadj[a + 1]])
+            assert row == sorted(row) and a not in row
+            for b, c in zip(row, w[xadj[a]:xadj[a + 1]]):
+                j = list(adj[xadj[b]:xadj[b + 1]]).index(a)
+                assert w[xadj[b] + j] == c
+
+
+def test_boundary_band_closed_forms():
+    # a path split in the middle: distance to the split point
+    g = I.path_graph(11)
+    part = (np.arange(11) >= 5).astype(np.int32)
+    d = O.boundary_band(g, part, 100)
+    assert list(d) == [4, 3, 2, 1, 0, 0, 1, 2, 3, 4, 5]
+    assert list(O.boundary_band(g, part, 2)) == [-1, -1, 2, 1, 0, 0, 1, 2, -1, -1, -1]
+    # grid strips: the distance to the nearest strip border in x
+    g = I.grid2d(12, 5)
+    xs = np.arange(g.n) % 12
+    part = np.where(xs < 3, 0, np.where(xs < 7, 1, 2)).astype(np.int32)
+    want = np.where(xs < 3, 2 - xs, np.where(xs < 7, np.minimum(xs - 3, 6 - xs), xs - 7))
+    assert np.array_equal(O.boundary_band(g, part, 100), want)
+    # the pair (0, 1): block 2 is out, block 1's border with block 2 is not a source
+    d = O.boundary_band(g, part, 100, pair=(0, 1))
+    want = np.where(xs < 3, 2 - xs, np.where(xs < 7, xs - 3, -2))
+    assert np.array_equal(d, want)
+
+
+def test_boundary_band_brute_force():
+    """Each node's distance by its own breadth-first search inside its block
+    to the nearest node with a neighbour in another block."""
+    from collections import deque
+    for seed in range(25):
+        rng = np.random.default_rng(100 + seed)
+        g = I.random_small_graph(int(rng.integers(2, 50)), float(rng.uniform(0.03, 0.2)), seed=seed)
+        k = int(rng.integers(1, 5))
+        part = I.random_partition(g.n, k, seed=seed)
+        depth = int(rng.integers(0, 6))
+        got = O.boundary_band(g, part, depth)
+        nbrs = [g.adjncy[g.xadj[v]:g.xadj[v + 1]] for v in range(g.n)]
+        boundary = [any(part[u] != part[v] for u in nbrs[v]) for v in range(g.n)]
+        for v in range(g.n):
+            seen, q, found = {v: 0}, deque([v]), -1
+            while q:
+                x = q.popleft()
+                if boundary[x]:
+                    found = seen[x]
+                    break
+                for y in nbrs[x]:
+                    if part[y] == part[v] and y not in seen:
+                        seen[y] = seen[x] + 1
+                        q.append(y)
+            want = found if 0 <= found <= depth else -1
+            assert got[v] == want, (seed, v)
