@@ -336,6 +336,33 @@ kp_status kp_cut_gain(const kp_graph *g, const int32_t *part, int32_t k, double 
 kp_status kp_cut_gain_noalloc(const kp_graph *g, const int32_t *part, int32_t k, double eps,
                               kp_cut_gain_out *out, kp_stream s);
 
+/* Quotient graph (Section 5): one node per block, an edge {a,b} whenever an
+ * edge of G joins blocks a and b, weighted by the total edge weight between
+ * them (the a-b cut).  Written as a symmetric CSR over the k blocks with
+ * ascending neighbour blocks:
+ *   q_xadj    device int32[k+1] (always written)
+ *   q_adjncy  device int32[capacity], q_ewgt device int64[capacity]
+ *   *q_nnz    host: the number of directed quotient entries
+ * Synchronises the stream.  Errors: KP_ERR_INVALID (k < 1, null arrays, a
+ * block id outside [0,k)), KP_ERR_OVERFLOW (*q_nnz > capacity: the entries are
+ * not written; retry with larger buffers), KP_ERR_UNSUPPORTED (k > 4096: the
+ * accumulator is a dense k x k matrix), KP_ERR_OOM, KP_ERR_CUDA. */
+kp_status kp_quotient_graph(const kp_graph *g, const int32_t *part, int32_t k, int32_t *q_xadj, int32_t *q_adjncy,
+                            int64_t *q_ewgt, int64_t capacity, int64_t *q_nnz, kp_stream s);
+
+/* Bounded breadth-first search from the block boundaries (Section 5: local
+ * search is limited to the band it finds; the strategies use depths 1, 5
+ * and 20).  dist[v] (device int32[n]) = the length of a shortest path from v
+ * to a boundary node of its own block through nodes of that block, when at
+ * most `depth`, else -1.  A boundary node has a neighbour in another block.
+ * With pair_a, pair_b >= 0 (two different blocks) only those two blocks take
+ * part: the boundary is the a-b boundary and nodes of other blocks get -2;
+ * (-1, -1) means every block.  Synchronises the stream.  Errors:
+ * KP_ERR_INVALID (k < 1, depth < 0, a bad pair, null arrays, a block id
+ * outside [0,k)), KP_ERR_OOM, KP_ERR_CUDA. */
+kp_status kp_boundary_band(const kp_graph *g, const int32_t *part, int32_t k, int32_t depth, int32_t pair_a,
+                           int32_t pair_b, int32_t *dist, kp_stream s);
+
 /* Initial partitioning callback for kp_pipeline_host (Section 4 partitions
  * the coarsest graph on one PE).  Receives the coarsest graph's size and its
  * node weights (host) and writes a block id in [0,k) for every coarsest node

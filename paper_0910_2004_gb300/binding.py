@@ -33,7 +33,7 @@ EXPORTED = ["kp_options_default", "kp_coarsen", "kp_hierarchy_num_levels", "kp_h
             "kp_hierarchy_batch_coarsest",
             "kp_server_create", "kp_server_submit", "kp_server_poll", "kp_server_wait", "kp_server_fetch",
             "kp_server_release", "kp_server_destroy", "kp_autotune", "kp_plan_create", "kp_plan_run",
-            "kp_plan_destroy",
+            "kp_plan_destroy", "kp_quotient_graph", "kp_boundary_band",
             "kp_last_error", "kp_version"]
 
 
@@ -177,6 +177,10 @@ def load(path: str = LIB_PATH):
         L.kp_plan_run.restype = ctypes.c_int
         L.kp_plan_destroy.argtypes = [vp]
         L.kp_plan_destroy.restype = None
+        L.kp_quotient_graph.argtypes = [ctypes.POINTER(kp_graph), vp, i32, vp, vp, vp, i64, ctypes.POINTER(i64), vp]
+        L.kp_quotient_graph.restype = ctypes.c_int
+        L.kp_boundary_band.argtypes = [ctypes.POINTER(kp_graph), vp, i32, i32, i32, i32, vp, vp]
+        L.kp_boundary_band.restype = ctypes.c_int
         L.kp_last_error.argtypes = []
         L.kp_last_error.restype = ctypes.c_char_p
         L.kp_version.argtypes = []
@@ -368,6 +372,24 @@ def kp_plan_run(plan: int, stream: int) -> int:
 
 def kp_plan_destroy(plan: int):
     load().kp_plan_destroy(ctypes.c_void_p(plan))
+
+
+def kp_quotient_graph(graph: kp_graph, part: int, k: int, q_xadj: int, q_adjncy: int, q_ewgt: int, capacity: int,
+                      stream: int) -> int:
+    nnz = ctypes.c_int64()
+    st = load().kp_quotient_graph(ctypes.byref(graph), ctypes.c_void_p(part), k, ctypes.c_void_p(q_xadj),
+                                  ctypes.c_void_p(q_adjncy), ctypes.c_void_p(q_ewgt), capacity, ctypes.byref(nnz),
+                                  ctypes.c_void_p(stream))
+    if st == KP_ERR_OVERFLOW:
+        return -nnz.value - 1   # too small: -(needed) - 1
+    _check(st, "kp_quotient_graph")
+    return nnz.value
+
+
+def kp_boundary_band(graph: kp_graph, part: int, k: int, depth: int, pair_a: int, pair_b: int, dist: int,
+                     stream: int):
+    _check(load().kp_boundary_band(ctypes.byref(graph), ctypes.c_void_p(part), k, depth, pair_a, pair_b,
+                                   ctypes.c_void_p(dist), ctypes.c_void_p(stream)), "kp_boundary_band")
 
 
 def kp_last_error() -> str:
@@ -774,3 +796,33 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def quotient_graph(graph, part, k: int):
+    """Quotient graph of a partition (kp_quotient_graph): (q_xadj, q_adjncy,
+    q_ewgt) CUDA tensors; buffers grow once if the first guess is small."""
+    torch = _torch()
+    kg = graph.kp if isinstance(graph, DeviceGraph) else graph
+    q_xadj = torch.empty(k + 1, dtype=torch.int32, device="cuda")
+    cap = max(16, min(k * (k - 1), 8 * k))
+    for _ in range(2):
+        q_adj = torch.empty(cap, dtype=torch.int32, device="cuda")
+        q_w = torch.empty(cap, dtype=torch.int64, device="cuda")
+        got = kp_quotient_graph(kg, part.data_ptr() if kg.n > 0 else 0, k, q_xadj.data_ptr(), q_adj.data_ptr(),
+                                q_w.data_ptr(), cap, current_stream())
+        if got >= 0:
+            return q_xadj, q_adj[:got], q_w[:got]
+        cap = -got - 1
+    raise RuntimeError("quotient graph did not fit twice")
+
+
+def boundary_band(graph, part, k: int, depth: int, pair=None, dist=None):
+    """Bounded breadth-first search from the block boundaries
+    (kp_boundary_band); returns dist (int32 CUDA tensor)."""
+    torch = _torch()
+    kg = graph.kp if isinstance(graph, DeviceGraph) else graph
+    if dist is None:
+        dist = torch.empty(max(kg.n, 1), dtype=torch.int32, device="cuda")
+    a, b = pair if pair is not None else (-1, -1)
+    kp_boundary_band(kg, part.data_ptr() if kg.n > 0 else 0, k, depth, a, b, dist.data_ptr(), current_stream())
+    return dist[:kg.n]
