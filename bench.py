@@ -331,6 +331,29 @@ def main():
     if dist:
         dist.barrier()
 
+    # the refinement-side helpers (Section 5) on the last projected partition:
+    # quotient graph and the bounded boundary search at the strong setting's
+    # depth 20 (not part of the step; reported beside it)
+    refine = {}
+    for name, fn, nbytes in [
+            ("quotient_graph", lambda: B.quotient_graph(dg, fine, k), 8 * g.n + 12 * g.nnz + 16 * k * k),
+            ("boundary_band_depth20", lambda: B.boundary_band(dg, fine, k, 20), 12 * g.n + 8 * g.nnz)]:
+        fn()
+        times = []
+        for _ in range(5):
+            flush.zero_()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a0.record(stream)
+            fn()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            times.append(a0.elapsed_time(a1))
+        ms = statistics.median(times)
+        refine[name] = {"ms": ms, "algorithmic_bytes": nbytes,
+                        "achieved_gbs": nbytes / (ms / 1000.0) / 1e9}
+
     # end to end through the host-buffer entry point
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(3, min(args.steps, 20))
     e2e_line = None
@@ -389,6 +412,8 @@ def main():
     dom_bytes, dom_ms = cands[dom]
     achieved = dom_bytes / (dom_ms / 1000.0) / 1e9 if dom_ms > 0 else 0.0
     path_bytes = sum(ab.values()) + eval_bytes(g.n, g.nnz, k) + 8 * g.n
+    for v in refine.values():
+        v["frac_of_measured_hbm"] = v["achieved_gbs"] / peak
     line = {
         "metric": "coarsened edges/s (full hierarchy)",
         "value": value, "unit": "edges/s", "n_gpus": world, "steps": steps, "warmup": max(args.warmup, 3),
@@ -408,6 +433,7 @@ def main():
         "level_profile": level_profile,
         "clocks": clocks,
         "e2e": e2e_line,
+        "refinement_helpers": refine,
         "gpu_launches": launches_tot,
     }
     if world == 1 and not args.no_cpu_baseline:

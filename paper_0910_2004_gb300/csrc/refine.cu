@@ -15,23 +15,23 @@ constexpr int32_t QUOTIENT_MAX_K = 4096;   // dense k x k accumulator
 // quotient graph
 // ---------------------------------------------------------------------------
 // Every directed cut entry adds its weight to cell (p(u), p(v)) of a dense
-// k x k matrix; a warp per node row, with warp-combined atomics for runs of
-// equal cells.  Block ids outside [0,k) set the error flag.
-__global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_acc(int32_t n, const int32_t *__restrict__ xadj,
-                                                               const int32_t *__restrict__ adjncy,
-                                                               const int32_t *__restrict__ ewgt,
-                                                               const int32_t *__restrict__ part, int32_t k,
-                                                               unsigned long long *cells, int32_t *err) {
+// k x k matrix.  Rows of at most QROW entries: one thread each, the weight
+// towards each other block summed in registers, one atomic per (row, block);
+// longer rows: the whole warp, 32 entries at a time, warp-combined atomics.
+// With k*k <= QSMEM_CELLS the cells are kept per block in shared memory and
+// added to the matrix at the end.  Block ids outside [0,k) set the error flag.
+constexpr int QROW = 16;
+constexpr int QSMEM_CELLS = 4096;
+
+__device__ __forceinline__ void quotient_row_warp(int32_t u, int32_t pu, int32_t beg, int32_t end,
+                                                  const int32_t *__restrict__ adjncy,
+                                                  const int32_t *__restrict__ ewgt,
+                                                  const int32_t *__restrict__ part, int32_t k,
+                                                  unsigned long long *cells, int32_t *err) {
     const int lane = threadIdx.x & 31;
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
-        const int32_t pu = part[u];
-        if (pu < 0 || pu >= k) {
-            if (lane == 0) atomicOr(err, 1);
-            continue;
-        }
-        const int32_t beg = xadj[u], end = xadj[u + 1];
-        for (int32_t e0 = beg; e0 < end; e0 += 32) {
+    (void)u;
+    {
+        for (int32_t e0 = beg; e0 < end; e0 += 32) {   // the same bounds for the whole warp
             const int32_t e = e0 + lane;
             int32_t pv = -1;
             int32_t w = 0;
@@ -55,6 +55,96 @@ __global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_acc(int32_t n, const 
             if (cut && (peers & ((1u << lane) - 1u)) == 0)
                 atomicAdd(&cells[(int64_t)pu * k + pv], (unsigned long long)sum);
         }
+    }
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_acc(int32_t n, const int32_t *__restrict__ xadj,
+                                                               const int32_t *__restrict__ adjncy,
+                                                               const int32_t *__restrict__ ewgt,
+                                                               const int32_t *__restrict__ part, int32_t k,
+                                                               unsigned long long *gcells, int32_t *err) {
+    __shared__ unsigned long long s_cells[SMEM ? QSMEM_CELLS : 1];
+    const int64_t kk = (int64_t)k * k;
+    if (SMEM) {
+        for (int64_t i = threadIdx.x; i < kk; i += blockDim.x) s_cells[i] = 0;
+        __syncthreads();
+    }
+    unsigned long long *cells = SMEM ? s_cells : gcells;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); v0 < n; v0 += stride) {
+        const int64_t u = v0 + lane;
+        int32_t pu = -1, beg = 0, d = 0;
+        if (u < n) {
+            pu = part[u];
+            beg = xadj[u];
+            d = xadj[u + 1] - beg;
+            if (pu < 0 || pu >= k) {
+                atomicOr(err, 1);
+                pu = -1;
+            }
+        }
+        if (pu >= 0 && d <= QROW) {
+            int32_t b[QROW], w[QROW];
+#pragma unroll
+            for (int i = 0; i < QROW; i++) {
+                if (i >= d) break;
+                b[i] = adjncy[beg + i];
+            }
+#pragma unroll
+            for (int i = 0; i < QROW; i++) {
+                if (i >= d) break;
+                w[i] = ewgt[beg + i];
+            }
+            bool any_cut = false;
+#pragma unroll
+            for (int i = 0; i < QROW; i++) {
+                if (i >= d) break;
+                const int32_t pb = part[b[i]];
+                if (pb < 0 || pb >= k) {
+                    atomicOr(err, 1);
+                    b[i] = pu;   // skipped below
+                } else {
+                    b[i] = pb;
+                    any_cut |= pb != pu;
+                }
+            }
+            if (any_cut) {
+#pragma unroll
+                for (int i = 0; i < QROW; i++) {
+                    if (i >= d) break;
+                    if (b[i] == pu) continue;
+                    bool first = true;
+                    long long sum = 0;
+#pragma unroll
+                    for (int j = 0; j < QROW; j++) {
+                        if (j >= d) break;
+                        if (b[j] == b[i]) {
+                            if (j < i) first = false;
+                            sum += w[j];
+                        }
+                    }
+                    if (first) atomicAdd(&cells[(int64_t)pu * k + b[i]], (unsigned long long)sum);
+                }
+            }
+        }
+        // the long rows of this warp's 32 nodes, one after the other
+        unsigned longm = __ballot_sync(0xffffffffu, pu >= 0 && d > QROW);
+        while (longm) {
+            const int j = __ffs(longm) - 1;
+            longm &= longm - 1;
+            const int32_t uj = __shfl_sync(0xffffffffu, (int32_t)u, j);
+            const int32_t pj = __shfl_sync(0xffffffffu, pu, j);
+            const int32_t bj = __shfl_sync(0xffffffffu, beg, j);
+            const int32_t dj = __shfl_sync(0xffffffffu, d, j);
+            quotient_row_warp(uj, pj, bj, bj + dj, adjncy, ewgt, part, k, cells, err);
+        }
+    }
+    if (SMEM) {
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < kk; i += blockDim.x)
+            if (s_cells[i]) atomicAdd(&gcells[i], s_cells[i]);
     }
 }
 
@@ -244,9 +334,14 @@ kp_status quotient_graph_impl(const kp_graph *g, const int32_t *part, int32_t k,
         cudaMemsetAsync(err, 0, sizeof(int32_t), s) != cudaSuccess ||
         cudaMemsetAsync(q_xadj, 0, sizeof(int32_t), s) != cudaSuccess)
         return done(cuda_error(cudaGetLastError(), "clear"));
-    if (g->n > 0)
-        k_quotient_acc<<<grid_for((int64_t)g->n * 32), REFINE_BLOCK, 0, s>>>(g->n, g->xadj, g->adjncy, g->ewgt, part,
-                                                                              k, cells, err);
+    if (g->n > 0) {
+        if ((int64_t)k * k <= QSMEM_CELLS)
+            k_quotient_acc<true><<<grid_for(g->n), REFINE_BLOCK, 0, s>>>(g->n, g->xadj, g->adjncy, g->ewgt, part, k,
+                                                                         cells, err);
+        else
+            k_quotient_acc<false><<<grid_for(g->n), REFINE_BLOCK, 0, s>>>(g->n, g->xadj, g->adjncy, g->ewgt, part, k,
+                                                                          cells, err);
+    }
     k_quotient_count<<<grid_for((int64_t)k * 32), REFINE_BLOCK, 0, s>>>(k, cells, q_xadj);
     k_quotient_scan<<<1, 1024, 0, s>>>(k, q_xadj, nnz_dev);
     k_quotient_write<<<grid_for((int64_t)k * 32), REFINE_BLOCK, 0, s>>>(k, cells, q_xadj, capacity, q_adjncy,
