@@ -268,6 +268,27 @@ kp_status kp_hierarchy_batch_coarsest(const kp_hierarchy *h, int32_t *sizes, kp_
 /* Device int32[num_graphs+1]: first node of every graph on union level l. */
 kp_status kp_hierarchy_level_offsets(const kp_hierarchy *h, int32_t l, const int32_t **node_offsets);
 
+/* Writes the whole hierarchy (every level's CSR and node weights, every map,
+ * a batch's per-level offsets, per-graph level counts and graph ids) to a
+ * file, little-endian: u64 magic "KPHIER01", i32 version 1, i32 levels,
+ * i32 num_graphs, i32 0; per level i32 n, i32 nnz, xadj[n+1], adjncy[nnz],
+ * ewgt[nnz], vwgt[n], map[n] (not on the coarsest), goff[G+1] (batches);
+ * then glevels[G] and gid0[n_0] (batches); all int32.  Synchronises the
+ * hierarchy's stream.  Errors: KP_ERR_INVALID (null arguments, the file
+ * cannot be written), KP_ERR_CUDA. */
+kp_status kp_hierarchy_save(const kp_hierarchy *h, const char *path);
+
+/* Reads a file written by kp_hierarchy_save into device memory on the
+ * current device: every level, including the input level, is owned by the
+ * returned hierarchy (release with kp_hierarchy_free); projection works as
+ * on the original.  The whole file is read and checked on the host first
+ * (CSR offsets and neighbour ids in range, maps into the next level, batch
+ * offsets and graph ids consistent) so that no kernel indexes with a bad
+ * value.  Synchronises s.  Errors: KP_ERR_INVALID (cannot open, not a
+ * hierarchy file, truncated, inconsistent contents, trailing bytes),
+ * KP_ERR_UNSUPPORTED (another version), KP_ERR_OOM, KP_ERR_CUDA. */
+kp_status kp_hierarchy_load(const char *path, kp_stream s, kp_hierarchy **out);
+
 /* Uncontraction of a batch: every graph from its own coarsest level.  The
  * coarse partition of graph i sits at coarse_part[coarse_offsets[i] + j] for
  * its coarsest node j (device arrays; coarse_offsets has num_graphs+1

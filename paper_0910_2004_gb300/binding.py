@@ -33,7 +33,7 @@ EXPORTED = ["kp_options_default", "kp_coarsen", "kp_hierarchy_num_levels", "kp_h
             "kp_hierarchy_batch_coarsest",
             "kp_server_create", "kp_server_submit", "kp_server_poll", "kp_server_wait", "kp_server_fetch",
             "kp_server_release", "kp_server_destroy", "kp_autotune", "kp_plan_create", "kp_plan_run",
-            "kp_plan_destroy", "kp_quotient_graph", "kp_boundary_band",
+            "kp_plan_destroy", "kp_quotient_graph", "kp_boundary_band", "kp_hierarchy_save", "kp_hierarchy_load",
             "kp_last_error", "kp_version"]
 
 
@@ -181,6 +181,10 @@ def load(path: str = LIB_PATH):
         L.kp_quotient_graph.restype = ctypes.c_int
         L.kp_boundary_band.argtypes = [ctypes.POINTER(kp_graph), vp, i32, i32, i32, i32, vp, vp]
         L.kp_boundary_band.restype = ctypes.c_int
+        L.kp_hierarchy_save.argtypes = [vp, ctypes.c_char_p]
+        L.kp_hierarchy_save.restype = ctypes.c_int
+        L.kp_hierarchy_load.argtypes = [ctypes.c_char_p, vp, ctypes.POINTER(vp)]
+        L.kp_hierarchy_load.restype = ctypes.c_int
         L.kp_last_error.argtypes = []
         L.kp_last_error.restype = ctypes.c_char_p
         L.kp_version.argtypes = []
@@ -392,6 +396,17 @@ def kp_boundary_band(graph: kp_graph, part: int, k: int, depth: int, pair_a: int
                                    ctypes.c_void_p(dist), ctypes.c_void_p(stream)), "kp_boundary_band")
 
 
+def kp_hierarchy_save(h: int, path: str):
+    _check(load().kp_hierarchy_save(ctypes.c_void_p(h), os.fsencode(path)), "kp_hierarchy_save")
+
+
+def kp_hierarchy_load(path: str, stream: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().kp_hierarchy_load(os.fsencode(path), ctypes.c_void_p(stream), ctypes.byref(h)),
+           "kp_hierarchy_load")
+    return h.value
+
+
 def kp_last_error() -> str:
     return load().kp_last_error().decode(errors="replace")
 
@@ -485,6 +500,13 @@ class Hierarchy:
     def num_levels(self) -> int:
         return kp_hierarchy_num_levels(self.handle)
 
+    def n0(self) -> int:
+        return self.graph.n if self.graph is not None else kp_hierarchy_level(self.handle, 0)[0].n
+
+    def save(self, path: str):
+        """kp_hierarchy_save: every level, map and batch offset to a file."""
+        kp_hierarchy_save(self.handle, path)
+
     def level(self, l: int):
         g, mp = kp_hierarchy_level(self.handle, l)
         out = {"n": g.n, "nnz": g.nnz, "xadj": device_view(g.xadj, g.n + 1),
@@ -501,7 +523,7 @@ class Hierarchy:
 
     def project(self, coarse_part, fine_part=None):
         torch = _torch()
-        n0 = self.graph.n
+        n0 = self.n0()
         if fine_part is None:
             fine_part = torch.empty(n0, dtype=torch.int32, device="cuda")
         kp_project(self.handle, coarse_part.data_ptr(), fine_part.data_ptr(), current_stream())
@@ -561,7 +583,7 @@ class BatchHierarchy(Hierarchy):
     def project(self, coarse_part, coarse_offsets, fine_part=None):
         torch = _torch()
         if fine_part is None:
-            fine_part = torch.empty(self.graph.n, dtype=torch.int32, device="cuda")
+            fine_part = torch.empty(self.n0(), dtype=torch.int32, device="cuda")
         kp_project_batch(self.handle, coarse_part.data_ptr(), coarse_offsets.data_ptr(), fine_part.data_ptr(),
                          current_stream())
         return fine_part
@@ -826,3 +848,14 @@ def boundary_band(graph, part, k: int, depth: int, pair=None, dist=None):
     a, b = pair if pair is not None else (-1, -1)
     kp_boundary_band(kg, part.data_ptr() if kg.n > 0 else 0, k, depth, a, b, dist.data_ptr(), current_stream())
     return dist[:kg.n]
+
+
+def load_hierarchy(path: str):
+    """kp_hierarchy_load: a saved hierarchy back on the device (it owns every
+    level).  Returns a Hierarchy, or a BatchHierarchy for a batch."""
+    h = kp_hierarchy_load(path, current_stream())
+    G, _ = kp_hierarchy_batch(h)
+    if G == 0:
+        return Hierarchy(None, h)
+    off = device_view(kp_hierarchy_level_offsets(h, 0), G + 1).clone()
+    return BatchHierarchy(None, h, off, None)

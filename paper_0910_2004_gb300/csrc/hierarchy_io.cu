@@ -1,0 +1,201 @@
+// Saving a hierarchy to a file and loading it back onto the device, so a
+// coarsened graph (every level, every map, a batch's offsets) can be kept
+// and refined later without coarsening again.  The file is little-endian:
+//
+//   u64 magic "KPHIER01", i32 version (1), i32 levels L, i32 num_graphs G,
+//   i32 reserved; then for l = 0..L-1: i32 n, i32 nnz, int32 xadj[n+1],
+//   adjncy[nnz], ewgt[nnz], vwgt[n], and for l < L-1 map[n]; for a batch
+//   (G > 0) also goff[G+1] per level, then glevels[G] and gid0[n_0].
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "kp_internal.cuh"
+
+using namespace kp;
+
+namespace {
+
+constexpr uint64_t KP_HIER_MAGIC = 0x313052454948504bull;   // "KPHIER01"
+constexpr int32_t KP_HIER_VERSION = 1;
+
+struct File {
+    FILE *f = nullptr;
+    ~File() {
+        if (f) fclose(f);
+    }
+};
+
+kp_status put(FILE *f, const void *p, size_t bytes) {
+    if (bytes && fwrite(p, 1, bytes, f) != bytes) return set_error(KP_ERR_INVALID, "write failed");
+    return KP_OK;
+}
+
+kp_status get(FILE *f, void *p, size_t bytes) {
+    if (bytes && fread(p, 1, bytes, f) != bytes) return set_error(KP_ERR_INVALID, "truncated hierarchy file");
+    return KP_OK;
+}
+
+// A device array to the file through a host buffer.
+kp_status put_dev(FILE *f, const int32_t *d, int64_t count, std::vector<int32_t> &buf) {
+    if (count <= 0) return KP_OK;
+    buf.resize((size_t)count);
+    KP_CUDA(cudaMemcpy(buf.data(), d, sizeof(int32_t) * (size_t)count, cudaMemcpyDeviceToHost));
+    return put(f, buf.data(), sizeof(int32_t) * (size_t)count);
+}
+
+}  // namespace
+
+extern "C" kp_status kp_hierarchy_save(const kp_hierarchy *h, const char *path) {
+    if (!h || !path) return set_error(KP_ERR_INVALID, "null argument");
+    if (h->stream && cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return cuda_error(cudaGetLastError(), "sync");
+    File file;
+    file.f = fopen(path, "wb");
+    if (!file.f) return set_error(KP_ERR_INVALID, std::string("cannot open for writing: ") + path);
+    FILE *f = file.f;
+    const int32_t L = (int32_t)h->levels.size(), G = h->num_graphs;
+    const uint64_t magic = KP_HIER_MAGIC;
+    const int32_t head[4] = {KP_HIER_VERSION, L, G, 0};
+    KP_TRY(put(f, &magic, 8));
+    KP_TRY(put(f, head, sizeof head));
+    std::vector<int32_t> buf;
+    for (int32_t l = 0; l < L; l++) {
+        const kp_level &lv = h->levels[(size_t)l];
+        const int32_t sz[2] = {lv.n, lv.nnz};
+        KP_TRY(put(f, sz, sizeof sz));
+        KP_TRY(put_dev(f, lv.xadj, (int64_t)lv.n + 1, buf));
+        KP_TRY(put_dev(f, lv.adjncy, lv.nnz, buf));
+        KP_TRY(put_dev(f, lv.ewgt, lv.nnz, buf));
+        KP_TRY(put_dev(f, lv.vwgt, lv.n, buf));
+        if (l < L - 1) KP_TRY(put_dev(f, lv.map, lv.n, buf));
+        if (G > 0) KP_TRY(put_dev(f, lv.goff, (int64_t)G + 1, buf));
+    }
+    if (G > 0) {
+        KP_TRY(put(f, h->glevels.data(), sizeof(int32_t) * (size_t)G));
+        KP_TRY(put_dev(f, h->gid0, L > 0 ? h->levels[0].n : 0, buf));
+    }
+    if (fflush(f) != 0) return set_error(KP_ERR_INVALID, "write failed");
+    return KP_OK;
+}
+
+extern "C" kp_status kp_hierarchy_load(const char *path, kp_stream stream, kp_hierarchy **out) {
+    if (!path || !out) return set_error(KP_ERR_INVALID, "null argument");
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    File file;
+    file.f = fopen(path, "rb");
+    if (!file.f) return set_error(KP_ERR_INVALID, std::string("cannot open: ") + path);
+    FILE *f = file.f;
+    uint64_t magic = 0;
+    int32_t head[4] = {0, 0, 0, 0};
+    KP_TRY(get(f, &magic, 8));
+    KP_TRY(get(f, head, sizeof head));
+    if (magic != KP_HIER_MAGIC) return set_error(KP_ERR_INVALID, "not a hierarchy file");
+    if (head[0] != KP_HIER_VERSION) return set_error(KP_ERR_UNSUPPORTED, "hierarchy file version");
+    const int32_t L = head[1], G = head[2];
+    if (L < 1 || L > 128 || G < 0) return set_error(KP_ERR_INVALID, "bad hierarchy header");   // at most 128 levels
+
+    // everything is read and checked on the host before anything reaches the
+    // device: the kernels index with these arrays
+    struct HostLevel {
+        int32_t n = 0, nnz = 0;
+        std::vector<int32_t> xadj, adjncy, ewgt, vwgt, map, goff;
+    };
+    std::vector<HostLevel> lv((size_t)L);
+    auto rd = [&](std::vector<int32_t> &v, int64_t count) -> kp_status {
+        if (count < 0 || count > (1ll << 31)) return set_error(KP_ERR_INVALID, "bad array size in hierarchy file");
+        v.resize((size_t)count);
+        return get(f, v.data(), sizeof(int32_t) * (size_t)count);
+    };
+    for (int32_t l = 0; l < L; l++) {
+        HostLevel &H = lv[(size_t)l];
+        int32_t sz[2];
+        KP_TRY(get(f, sz, sizeof sz));
+        H.n = sz[0];
+        H.nnz = sz[1];
+        if (H.n < 0 || H.nnz < 0 || (l > 0 && H.n > lv[(size_t)l - 1].n))
+            return set_error(KP_ERR_INVALID, "bad level sizes in hierarchy file");
+        KP_TRY(rd(H.xadj, (int64_t)H.n + 1));
+        KP_TRY(rd(H.adjncy, H.nnz));
+        KP_TRY(rd(H.ewgt, H.nnz));
+        KP_TRY(rd(H.vwgt, H.n));
+        if (l < L - 1) KP_TRY(rd(H.map, H.n));
+        if (G > 0) KP_TRY(rd(H.goff, (int64_t)G + 1));
+    }
+    std::vector<int32_t> glevels, gid0;
+    if (G > 0) {
+        KP_TRY(rd(glevels, G));
+        KP_TRY(rd(gid0, lv[0].n));
+    }
+    char extra;
+    if (fread(&extra, 1, 1, f) != 0) return set_error(KP_ERR_INVALID, "trailing bytes in hierarchy file");
+    for (int32_t l = 0; l < L; l++) {
+        const HostLevel &H = lv[(size_t)l];
+        bool ok = H.xadj[0] == 0 && H.xadj[(size_t)H.n] == H.nnz;
+        for (int32_t v = 0; ok && v < H.n; v++) ok = H.xadj[(size_t)v] <= H.xadj[(size_t)v + 1];
+        for (int32_t e = 0; ok && e < H.nnz; e++) ok = H.adjncy[(size_t)e] >= 0 && H.adjncy[(size_t)e] < H.n;
+        if (l < L - 1) {
+            const int32_t n2 = lv[(size_t)l + 1].n;
+            for (int32_t v = 0; ok && v < H.n; v++) ok = H.map[(size_t)v] >= -1 && H.map[(size_t)v] < n2;
+        }
+        if (G > 0) {
+            ok = ok && H.goff[0] == 0 && H.goff[(size_t)G] == H.n;
+            for (int32_t g = 0; ok && g < G; g++) ok = H.goff[(size_t)g] <= H.goff[(size_t)g + 1];
+        }
+        if (!ok) return set_error(KP_ERR_INVALID, "inconsistent level in hierarchy file");
+    }
+    for (int32_t v : glevels)
+        if (v < 1 || v > L) return set_error(KP_ERR_INVALID, "bad graph level count in hierarchy file");
+    for (int32_t g : gid0)
+        if (g < 0 || g >= G) return set_error(KP_ERR_INVALID, "bad graph id in hierarchy file");
+
+    kp_hierarchy *h = new kp_hierarchy();
+    h->stream = s;
+    h->num_graphs = G;
+    auto fail = [&](kp_status st) {
+        kp_hierarchy_free(h);
+        return st;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "device"));
+    auto up = [&](int32_t **dst, const std::vector<int32_t> &src) -> kp_status {
+        KP_TRY(dev_alloc_n(dst, (int64_t)src.size(), s));
+        h->allocations.push_back(*dst);
+        if (!src.empty())
+            KP_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(int32_t) * src.size(), cudaMemcpyHostToDevice, s));
+        return KP_OK;
+    };
+    for (int32_t l = 0; l < L; l++) {
+        const HostLevel &H = lv[(size_t)l];
+        kp_level k;
+        k.n = H.n;
+        k.nnz = H.nnz;
+        k.owned = true;
+        kp_status st = up(&k.xadj, H.xadj);
+        if (st == KP_OK) st = up(&k.adjncy, H.adjncy);
+        if (st == KP_OK) st = up(&k.ewgt, H.ewgt);
+        if (st == KP_OK) st = up(&k.vwgt, H.vwgt);
+        if (st == KP_OK && l < L - 1) st = up(&k.map, H.map);
+        if (st == KP_OK && G > 0) st = up(&k.goff, H.goff);
+        if (st != KP_OK) return fail(st);
+        h->levels.push_back(k);
+    }
+    if (G > 0) {
+        h->glevels = glevels;
+        kp_status st = up(&h->glevels_dev, glevels);
+        if (st == KP_OK) st = up(&h->gid0, gid0);
+        if (st != KP_OK) return fail(st);
+    }
+    h->per_level.assign((size_t)(L - 1), kp_level_profile{});
+    for (int32_t l = 0; l + 1 < L; l++) {
+        h->per_level[(size_t)l].n = h->levels[(size_t)l].n;
+        h->per_level[(size_t)l].nnz = h->levels[(size_t)l].nnz;
+        h->total_matched += (int64_t)h->levels[(size_t)l].n - h->levels[(size_t)l + 1].n;
+    }
+    h->total.n = h->levels[0].n;
+    h->total.nnz = h->levels[0].nnz;
+    // the host vectors are the copies' sources: wait before they go
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "sync"));
+    *out = h;
+    return KP_OK;
+}

@@ -124,3 +124,34 @@ def test_batch_rejects_bad_input():
     with pytest.raises(B().KpError) as e:
         B().coarsen_batch(dg, np.array([0, 10, 25], dtype=np.int32))     # edges cross graphs
     assert e.value.status == B().KP_ERR_INVALID
+
+
+def test_saved_and_loaded_batch_hierarchy_is_identical(tmp_path):
+    import torch
+    graphs = mixed_graphs(21)
+    seeds = np.arange(len(graphs), dtype=np.uint64) + 3
+    h, dg, refs, off = check_batch(graphs, seeds, "innerOuter", 6, "suitor", 0)
+    path = str(tmp_path / "batch.kph")
+    h.save(path)
+    h2 = B().load_hierarchy(path)
+    assert h2.graph_levels() == h.graph_levels()
+    assert list(h2.coarsest_sizes()) == list(h.coarsest_sizes())
+    for gi, ref in enumerate(refs):
+        for l, rl in enumerate(ref.levels):
+            got = h2.graph_level(gi, l)
+            for key in ("xadj", "adjncy", "ewgt", "vwgt"):
+                assert np.array_equal(got[key], getattr(rl, key)), (gi, l, key)
+    cs = h.coarsest_sizes()
+    cp, co = I.batch_partition(cs, 3, 5)
+    a = h.project(torch.as_tensor(cp).cuda(), torch.as_tensor(co).cuda()).cpu().numpy()
+    b = h2.project(torch.as_tensor(cp).cuda(), torch.as_tensor(co).cuda()).cpu().numpy()
+    assert np.array_equal(a, b)
+    h2.free()
+    # a damaged file is refused
+    data = open(path, "rb").read()
+    for bad in (data[:len(data) // 2], b"XXXXXXXX" + data[8:], data + b"\0"):
+        p2 = str(tmp_path / "bad.kph")
+        open(p2, "wb").write(bad)
+        with pytest.raises(B().KpError) as e:
+            B().load_hierarchy(p2)
+        assert e.value.status == B().KP_ERR_INVALID

@@ -390,3 +390,34 @@ def test_deterministic_across_runs_and_streams():
         assert np.array_equal(a, b)
     h1.free()
     h2.free()
+
+
+def test_saved_and_loaded_hierarchy_is_identical(tmp_path):
+    import torch
+    g = I.rgg2d(20000, 9, wmax=16)
+    h, dg, levels, maps = run_gpu(g, rating="expansion*2", seed=4, stop_size=40)
+    path = str(tmp_path / "h.kph")
+    h.save(path)
+    h2 = B().load_hierarchy(path)
+    assert h2.num_levels() == h.num_levels()
+    for l in range(h.num_levels()):
+        a, b = h.level(l), h2.level(l)
+        for key in ("xadj", "adjncy", "ewgt", "vwgt"):
+            assert np.array_equal(a[key].cpu().numpy(), b[key].cpu().numpy()), (l, key)
+        if a["map"] is not None:
+            assert np.array_equal(a["map"].cpu().numpy(), b["map"].cpu().numpy()), (l, "map")
+    top = levels[-1].n
+    cp = torch.as_tensor(I.random_balanced_partition(top, 4, seed=1)).cuda()
+    assert np.array_equal(h.project(cp).cpu().numpy(), h2.project(cp).cpu().numpy())
+    h2.free()
+    h.free()
+    # a map entry pointing past the next level is refused before any upload
+    data = bytearray(open(path, "rb").read())
+    n0, nnz0 = g.n, g.nnz
+    map0 = 24 + 8 + 4 * (n0 + 1) + 8 * nnz0 + 4 * n0
+    data[map0:map0 + 4] = np.int32(levels[1].n).tobytes()
+    bad = str(tmp_path / "bad.kph")
+    open(bad, "wb").write(bytes(data))
+    with pytest.raises(B().KpError) as e:
+        B().load_hierarchy(bad)
+    assert e.value.status == B().KP_ERR_INVALID
