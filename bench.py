@@ -235,7 +235,8 @@ def main():
     ap.add_argument("--tail-nodes", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="built-in knobs instead of the autotuner's")
     ap.add_argument("--requests", type=int, default=None, help="served: requests per load phase")
-    ap.add_argument("--workers", type=int, default=4, help="served: server worker streams")
+    ap.add_argument("--workers", type=int, default=4, help="served: server workers")
+    ap.add_argument("--small-workers", type=int, default=1, help="served: workers kept for small requests")
     args = ap.parse_args()
     wl = workloads()[args.workload]
     if wl.get("batch"):
@@ -860,7 +861,8 @@ def run_served(args, wl):
     load_reqs = {0.5: served_requests(pool, R, seed=12), 0.9: served_requests(pool, R, seed=13)}
 
     sv = B.Server(workers=args.workers, max_batch=64, batch_max_nodes=1 << 16, hbm_budget_bytes=budget,
-                  small_workers=1, rating=rating, validate=False, matcher=args.matcher, tail_nodes=args.tail_nodes)
+                  small_workers=args.small_workers, rating=rating, validate=False, matcher=args.matcher,
+                  tail_nodes=args.tail_nodes)
     # warm-up: every pool graph once (allocator pool, library state)
     for _ in range(max(1, min(args.warmup, 2))):
         serve_phase(sv, pool, [(pi, 2, eps, 1, 40) for pi in range(len(pool))], None)
@@ -941,7 +943,8 @@ def run_served(args, wl):
         "warmup": max(1, min(args.warmup, 2)), "ms_per_step": 1000.0 * loads[0.9]["span_s"] / R,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "pool_graphs": len(pool),
-                   "requests_per_phase": R, "workers": args.workers, "small_workers": 1, "max_batch": 64,
+                   "requests_per_phase": R, "workers": args.workers, "small_workers": args.small_workers,
+                   "max_batch": 64,
                    "host_arrays": "pageable numpy arrays of the pool, borrowed by the server (KP_REQUEST_BORROW: "
                                   "read by the worker's host-to-device copy, no copy at submit)",
                    "batch_max_nodes": 1 << 16, "hbm_budget_gb": budget / 1e9, "matcher": args.matcher,

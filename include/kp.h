@@ -411,8 +411,10 @@ kp_status kp_pipeline_host(const kp_graph *g, const kp_options *o, int32_t k, do
  * (coarsening as kp_coarsen, a seeded initial partition of the coarsest graph,
  * projection as kp_project, evaluation as kp_cut_gain) and its results stay
  * on the device until the client releases the request.
- * Workers: `workers` host threads, each with its own non-blocking CUDA stream
- * on the device current at kp_server_create, so groups run concurrently.
+ * Workers: `workers` host threads, each with two non-blocking CUDA streams on
+ * the device current at kp_server_create (high priority for groups of small
+ * requests, low priority for large ones), so groups run concurrently and the
+ * small ones are scheduled first.
  * Admission: first in, first out; the oldest waiting request starts once its
  * estimated device footprint fits into hbm_budget_bytes minus the footprint
  * of running and resident requests (a request runs alone if nothing else is

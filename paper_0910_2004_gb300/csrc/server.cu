@@ -1,6 +1,7 @@
 // Request server for the serving pattern: coarsen + partition + project +
-// cut/gain requests arrive over time; each worker (a host thread with its own
-// non-blocking CUDA stream) takes the oldest waiting request once its
+// cut/gain requests arrive over time; each worker (a host thread with two
+// non-blocking CUDA streams: a high-priority one for groups of small requests,
+// a low-priority one for large requests) takes the oldest waiting request once its
 // estimated device footprint fits the HBM budget, merges further small
 // waiting requests into the same batched call, and runs the whole path on
 // its stream, so the work of several groups overlaps on the device.  Results
@@ -280,7 +281,6 @@ void worker_main(kp_server *S, int wi) {
     const bool small_only = wi < S->cfg.small_workers;
     for (;;) {
         ServerGroup *g = new ServerGroup();
-        g->s = S->streams[(size_t)wi];
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv_work.wait(lk, [&] { return S->stopping || next_request(S, small_only) != S->queue.end(); });
@@ -310,6 +310,9 @@ void worker_main(kp_server *S, int wi) {
                 }
             }
             S->used += g->footprint;
+            // small groups on the worker's high-priority stream, so their
+            // blocks are scheduled ahead of a large request's on the device
+            g->s = S->streams[2 * (size_t)wi + (head->n <= S->cfg.batch_max_nodes ? 0 : 1)];
             const double t = S->now_us();
             for (ServerRequest *r : g->reqs) {
                 r->res.t_admit_us = t;
@@ -366,9 +369,14 @@ kp_status kp_server_create(const kp_server_config *cfg, kp_server **out) {
         delete S;
         return cuda_error(cudaGetLastError(), "cudaGetDevice");
     }
-    for (int i = 0; i < cfg->workers; i++) {
+    int prio_low = 0, prio_high = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        cudaGetLastError();
+        prio_low = prio_high = 0;
+    }
+    for (int i = 0; i < 2 * cfg->workers; i++) {   // per worker: high priority (small), low priority (large)
         cudaStream_t s;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+        if (cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, (i & 1) ? prio_low : prio_high) != cudaSuccess) {
             for (cudaStream_t q : S->streams) cudaStreamDestroy(q);
             delete S;
             return cuda_error(cudaGetLastError(), "cudaStreamCreate");
