@@ -502,6 +502,11 @@ kp_status kp_server_wait(kp_server *sv, uint64_t id, kp_request_result *res);
 kp_status kp_server_fetch(kp_server *sv, uint64_t id, int32_t *fine_part, int64_t *gain, int32_t *target,
                           int32_t *coarse_part);
 
+/* Withdraws a request that is still waiting (not yet taken by a worker): it
+ * leaves the queue and its id is forgotten.  Errors: KP_ERR_INVALID (unknown
+ * id, or the request has started: wait for it and release it instead). */
+kp_status kp_server_cancel(kp_server *sv, uint64_t id);
+
 /* Drops a finished request; its device memory returns to the budget when
  * every request of its group has been released.  Does not wait for the GPU.
  * Errors: KP_ERR_INVALID (unknown or unfinished request). */
@@ -571,6 +576,16 @@ typedef struct kp_tune_trial {
 kp_status kp_autotune(const kp_graph *g, int32_t num_graphs, const int32_t *node_offsets, const uint64_t *seeds,
                       const int32_t *stop_sizes, const kp_options *o, int32_t reps, kp_options *best,
                       kp_tune_trial *trials, int32_t max_trials, int32_t *num_trials, kp_stream s);
+
+/* Test hooks (failure injection on the host; no GPU fault is ever made).
+ * kp_test_fail_allocation(after): the library's device allocation that
+ * follows `after` more successful ones fails with KP_ERR_OOM as if the device
+ * were full, then the hook switches itself off (after < 0: off).  Every entry
+ * point must then return KP_ERR_OOM with nothing leaked.
+ * kp_test_device_bytes_in_use(): bytes currently allocated from the current
+ * device's default memory pool (the library's allocations), -1 on error. */
+void kp_test_fail_allocation(int64_t after);
+int64_t kp_test_device_bytes_in_use(void);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *kp_last_error(void);

@@ -32,7 +32,8 @@ EXPORTED = ["kp_options_default", "kp_coarsen", "kp_hierarchy_num_levels", "kp_h
             "kp_coarsen_batch", "kp_hierarchy_batch", "kp_hierarchy_level_offsets", "kp_project_batch",
             "kp_hierarchy_batch_coarsest",
             "kp_server_create", "kp_server_submit", "kp_server_poll", "kp_server_wait", "kp_server_fetch",
-            "kp_server_release", "kp_server_destroy", "kp_autotune", "kp_plan_create", "kp_plan_run",
+            "kp_server_release", "kp_server_cancel", "kp_server_destroy", "kp_autotune",
+            "kp_test_fail_allocation", "kp_test_device_bytes_in_use", "kp_plan_create", "kp_plan_run",
             "kp_plan_destroy", "kp_quotient_graph", "kp_boundary_band", "kp_hierarchy_save", "kp_hierarchy_load",
             "kp_last_error", "kp_version"]
 
@@ -164,6 +165,12 @@ def load(path: str = LIB_PATH):
         L.kp_server_fetch.restype = ctypes.c_int
         L.kp_server_release.argtypes = [vp, ctypes.c_uint64]
         L.kp_server_release.restype = ctypes.c_int
+        L.kp_server_cancel.argtypes = [vp, ctypes.c_uint64]
+        L.kp_server_cancel.restype = ctypes.c_int
+        L.kp_test_fail_allocation.argtypes = [i64]
+        L.kp_test_fail_allocation.restype = None
+        L.kp_test_device_bytes_in_use.argtypes = []
+        L.kp_test_device_bytes_in_use.restype = i64
         L.kp_server_destroy.argtypes = [vp]
         L.kp_server_destroy.restype = None
         L.kp_autotune.argtypes = [ctypes.POINTER(kp_graph), i32, vp, vp, vp, ctypes.POINTER(kp_options), i32,
@@ -342,6 +349,18 @@ def kp_server_fetch(sv: int, rid: int, fine_part: int, gain: int, target: int, c
 
 def kp_server_release(sv: int, rid: int):
     _check(load().kp_server_release(sv, rid), "kp_server_release")
+
+
+def kp_server_cancel(sv: int, rid: int):
+    _check(load().kp_server_cancel(sv, rid), "kp_server_cancel")
+
+
+def kp_test_fail_allocation(after: int):
+    load().kp_test_fail_allocation(after)
+
+
+def kp_test_device_bytes_in_use() -> int:
+    return load().kp_test_device_bytes_in_use()
 
 
 def kp_server_destroy(sv: int):
@@ -702,6 +721,10 @@ class Server:
 
     def release(self, rid: int):
         kp_server_release(self._sv, rid)
+        self._borrowed.pop(rid, None)
+
+    def cancel(self, rid: int):
+        kp_server_cancel(self._sv, rid)
         self._borrowed.pop(rid, None)
 
     def close(self):

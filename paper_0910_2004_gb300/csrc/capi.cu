@@ -41,6 +41,22 @@ int num_sms() {
     return c;
 }
 
+// Test hook: the allocation after `g_fail_after` more successful ones fails
+// with KP_ERR_OOM (-1: never), then the hook switches itself off.
+static std::mutex g_inject_mu;
+static int64_t g_fail_after = -1;
+
+static bool injected_failure() {
+    std::lock_guard<std::mutex> lock(g_inject_mu);
+    if (g_fail_after < 0) return false;
+    if (g_fail_after == 0) {
+        g_fail_after = -1;
+        return true;
+    }
+    g_fail_after--;
+    return false;
+}
+
 kp_status dev_alloc(void **p, size_t bytes, cudaStream_t s) {
     static std::mutex mu;
     static std::atomic<bool> configured[64];
@@ -56,6 +72,10 @@ kp_status dev_alloc(void **p, size_t bytes, cudaStream_t s) {
             }
             configured[dev] = true;
         }
+    }
+    if (injected_failure()) {
+        *p = nullptr;
+        return set_error(KP_ERR_OOM, "injected allocation failure");
     }
     const cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) {
@@ -347,3 +367,18 @@ const char *kp_last_error(void) { return g_last_error.c_str(); }
 const char *kp_version(void) { return "kp-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+extern "C" void kp_test_fail_allocation(int64_t after) {
+    std::lock_guard<std::mutex> lock(kp::g_inject_mu);
+    kp::g_fail_after = after < 0 ? -1 : after;
+}
+
+extern "C" int64_t kp_test_device_bytes_in_use(void) {
+    int dev = 0;
+    cudaMemPool_t pool;
+    uint64_t used = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess)
+        return -1;
+    return (int64_t)used;
+}

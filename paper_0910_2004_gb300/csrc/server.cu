@@ -486,6 +486,21 @@ kp_status kp_server_fetch(kp_server *S, uint64_t id, int32_t *fine_part, int64_t
     return KP_OK;
 }
 
+kp_status kp_server_cancel(kp_server *S, uint64_t id) {
+    if (!S) return set_error(KP_ERR_INVALID, "null argument");
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto q = std::find_if(S->queue.begin(), S->queue.end(), [&](ServerRequest *r) { return r->id == id; });
+        if (q == S->queue.end()) return set_error(KP_ERR_INVALID, "unknown or already started request");
+        ServerRequest *r = *q;
+        S->queue.erase(q);
+        S->reqs.erase(id);
+        delete r;
+    }
+    S->cv_work.notify_all();   // the next request may fit now that this one is gone
+    return KP_OK;
+}
+
 kp_status kp_server_release(kp_server *S, uint64_t id) {
     if (!S) return set_error(KP_ERR_INVALID, "null argument");
     ServerGroup *to_free = nullptr;
