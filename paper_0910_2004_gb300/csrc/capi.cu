@@ -241,6 +241,7 @@ void kp_options_default(kp_options *o) {
 }
 
 kp_status kp_coarsen(const kp_graph *g, const kp_options *o, kp_stream s, kp_hierarchy **out) {
+    kp::TraceRange trace("kp_coarsen");
     if (!g || !out) return set_error(KP_ERR_INVALID, "null argument");
     *out = nullptr;
     kp_options def;
@@ -253,6 +254,7 @@ kp_status kp_coarsen(const kp_graph *g, const kp_options *o, kp_stream s, kp_hie
 kp_status kp_coarsen_batch(const kp_graph *g, int32_t num_graphs, const int32_t *node_offsets,
                            const uint64_t *seeds, const int32_t *stop_sizes, const kp_options *o, kp_stream s,
                            kp_hierarchy **out) {
+    kp::TraceRange trace("kp_coarsen_batch");
     if (!g || !out) return set_error(KP_ERR_INVALID, "null argument");
     *out = nullptr;
     kp_options def;
@@ -289,6 +291,7 @@ kp_status kp_hierarchy_level_offsets(const kp_hierarchy *h, int32_t l, const int
 
 kp_status kp_project_batch(const kp_hierarchy *h, const int32_t *coarse_part, const int32_t *coarse_offsets,
                            int32_t *fine_part, kp_stream s) {
+    kp::TraceRange trace("kp_project_batch");
     KP_GUARD(project_batch_impl(h, coarse_part, coarse_offsets, fine_part, (cudaStream_t)s));
 }
 
@@ -338,11 +341,13 @@ void kp_hierarchy_free(kp_hierarchy *h) {
 }
 
 kp_status kp_project(const kp_hierarchy *h, const int32_t *coarse_part, int32_t *fine_part, kp_stream s) {
+    kp::TraceRange trace("kp_project");
     KP_GUARD(project_impl(h, coarse_part, fine_part, (cudaStream_t)s));
 }
 
 kp_status kp_cut_gain(const kp_graph *g, const int32_t *part, int32_t k, double eps, kp_cut_gain_out *out,
                       kp_stream s) {
+    kp::TraceRange trace("kp_cut_gain");
     KP_GUARD(cut_gain_impl(g, part, k, eps, out, (cudaStream_t)s));
 }
 
@@ -355,6 +360,7 @@ kp_status kp_pipeline_host(const kp_graph *g, const kp_options *o, int32_t k, do
                            kp_initial_partition_fn ip, void *user, int32_t *fine_part, int64_t *gain,
                            int32_t *target, int64_t *block_w, kp_cut_gain_out *out, int32_t *num_levels,
                            kp_stream s) {
+    kp::TraceRange trace("kp_pipeline_host");
     kp_options def;
     kp_options_default(&def);
     if (o && o->max_levels > 120) return set_error(KP_ERR_UNSUPPORTED, "max_levels above 120");

@@ -11,6 +11,7 @@
 // inactive and return at once.  If the arena runs out, the device stops at
 // the level that did not fit; the host adds a larger arena and resumes there.
 #include <algorithm>
+#include <cstdio>
 #include <atomic>
 #include <cstring>
 
@@ -366,6 +367,9 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         // only recorded at the level after it
         const int level_end = o->max_levels + (batch ? 1 : 0);
         for (int level = start; level < level_end; level++) {
+            char trace_name[32];
+            snprintf(trace_name, sizeof trace_name, "level %d", level);
+            TraceRange trace(trace_name);
             // the rest in one persistent launch once the level is small (dense
             // small levels, as in power-law graphs, stay with the wide grids)
             if (n_bound <= tail_nodes && nnz_bound <= 8ll * tail_nodes) {
@@ -657,6 +661,7 @@ kp_status plan_create_impl(const kp_graph *g, int32_t num_graphs, const int32_t 
 }
 
 kp_status plan_run_impl(kp_plan *p, cudaStream_t s, kp_hierarchy **out) {
+    TraceRange trace("kp_plan_run");
     for (int attempt = 0;; attempt++) {
         std::memset(p->snap, 0, sizeof(LevelSnap) * MAX_LEVELS);
         KP_CUDA(cudaGraphLaunch(p->exec, s));

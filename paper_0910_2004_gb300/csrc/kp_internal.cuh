@@ -4,12 +4,26 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
 #include <vector>
 
 #include "kp.h"
+
+namespace kp {
+
+// A named range on the host timeline for tracing tools (NVTX; free when no
+// tool is attached): entry points, levels, server groups.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+
+}  // namespace kp
 
 namespace kp {
 

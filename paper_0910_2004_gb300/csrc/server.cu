@@ -142,6 +142,7 @@ kp_status galloc(ServerGroup *g, T **p, int64_t count) {
 }
 
 kp_status run_group(kp_server *S, ServerGroup *g) {
+    TraceRange trace(g->reqs.size() > 1 ? "server batch group" : "server request");
     cudaStream_t s = g->s;
     const size_t G = g->reqs.size();
     kp_options o = S->cfg.options;

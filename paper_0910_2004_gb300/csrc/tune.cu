@@ -43,6 +43,7 @@ extern "C" kp_status kp_autotune(const kp_graph *g, int32_t num_graphs, const in
     if (reps < 1 || reps > 100 || max_trials < 0 || (max_trials > 0 && !trials))
         return set_error(KP_ERR_INVALID, "bad tuner arguments");
     cudaStream_t s = (cudaStream_t)stream;
+    TraceRange trace("kp_autotune");
     BatchSpec b;
     b.num_graphs = num_graphs;
     b.node_offsets = node_offsets;
