@@ -252,10 +252,14 @@ __global__ void __launch_bounds__(REFINE_BLOCK) k_band_init(int32_t n, const int
     }
 }
 
-// One breadth-first step: every frontier node claims its unvisited
-// neighbours of the same block (the first claim wins; the distance is the
-// same whoever claims) and appends them to the next frontier.
-__global__ void __launch_bounds__(REFINE_BLOCK) k_band_step(const int32_t *__restrict__ xadj,
+// One breadth-first step.  Push (small frontier): every frontier node claims
+// its unvisited neighbours of the same block (the first claim wins; the
+// distance is the same whoever claims).  Pull (frontier above n/16): every
+// unvisited node looks for a same-block neighbour at distance depth-1 and
+// takes depth itself, no atomics on dist.  The choice is made on the device
+// from the frontier size, the same for every block.  New nodes are appended
+// to the next frontier either way.
+__global__ void __launch_bounds__(REFINE_BLOCK) k_band_step(int32_t n, const int32_t *__restrict__ xadj,
                                                             const int32_t *__restrict__ adjncy,
                                                             const int32_t *__restrict__ part, int32_t *dist,
                                                             const int32_t *frontier, const int32_t *count,
@@ -263,6 +267,34 @@ __global__ void __launch_bounds__(REFINE_BLOCK) k_band_step(const int32_t *__res
     const int lane = threadIdx.x & 31;
     const int64_t cnt = *count;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (cnt * 16 > n) {
+        for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); v0 < n; v0 += stride) {
+            const int64_t v = v0 + lane;
+            bool found = false;
+            if (v < n && dist[v] == -1) {
+                const int32_t pv = part[v];
+                for (int32_t e = xadj[v]; e < xadj[v + 1]; e++) {
+                    const int32_t u = adjncy[e];
+                    if (dist[u] == depth - 1 && part[u] == pv) {
+                        found = true;
+                        break;
+                    }
+                }
+            }
+            // this step writes only the value `depth` and the test above looks
+            // for depth-1 (set by the previous step), so what other threads
+            // write meanwhile cannot change any decision
+            const unsigned m = __ballot_sync(0xffffffffu, found);
+            int32_t base = 0;
+            if (lane == 0 && m) base = atomicAdd(next_count, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (found) {
+                dist[v] = depth;
+                next[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
+            }
+        }
+        return;
+    }
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < cnt; i0 += stride) {
         const int64_t i = i0 + lane;
         int32_t u = -1, beg = 0, end = 0, pu = -1;
@@ -388,7 +420,7 @@ kp_status boundary_band_impl(const kp_graph *g, const int32_t *part, int32_t k, 
     // each step reads the frontier size on the device: no host round trip
     for (int32_t d = 1; d <= depth; d++) {
         int32_t *cur = (d & 1) ? fa : fb, *nxt = (d & 1) ? fb : fa;
-        k_band_step<<<grid_for(n), REFINE_BLOCK, 0, s>>>(g->xadj, g->adjncy, part, dist, cur, counts + d - 1, nxt,
+        k_band_step<<<grid_for(n), REFINE_BLOCK, 0, s>>>(n, g->xadj, g->adjncy, part, dist, cur, counts + d - 1, nxt,
                                                         counts + d, d);
     }
     if (cudaGetLastError() != cudaSuccess) return done(cuda_error(cudaGetLastError(), "band kernels"));
