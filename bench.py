@@ -35,6 +35,11 @@ sys.path.insert(0, ROOT)
 from paper_0910_2004_gb300 import inputs as I  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+
+# DRAM bytes (read + write) of one launch of a workload's dominant kernel,
+# from one ncu capture of this build (profiles/k_tail_rgg20.md); a kernel
+# without an entry reports traffic null.
+NCU_TRAFFIC = {("rgg20", "tail"): 3_721_984 + 339_456}
 HBM_PEAK_FALLBACK = 6800.0
 
 
@@ -437,7 +442,8 @@ def main():
                    "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}",
                    "matcher": args.matcher, "input_check": "once before timing (kp_options.validate=0 in timed steps)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": NCU_TRAFFIC.get((args.workload, dom)),
                      "algorithmic_bytes_per_step": dom_bytes, "kernel_ms_per_step": dom_ms},
         "path_roofline": {"bytes_per_step": path_bytes, "achieved_gbs": path_bytes / (total_ms / steps / 1000) / 1e9,
                           "frac": path_bytes / (total_ms / steps / 1000) / 1e9 / peak},
