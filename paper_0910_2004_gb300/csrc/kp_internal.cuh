@@ -260,62 +260,7 @@ __device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t *t
     return warp_prefix + x - v;
 }
 
-template <class Op>
-__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_up(Op op, int64_t count, uint64_t *partials) {
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
-    uint64_t s = 0;
-#pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; j++)
-        if (base + j < count) s += op.load(base + j);
-    uint64_t total;
-    block_exclusive_scan<SCAN_BLOCK>(s, &total);
-    if (threadIdx.x == 0) partials[blockIdx.x] = total;
-}
-
-template <class Op>
-__global__ void __launch_bounds__(1024) k_scan_mid(Op op, int64_t tiles, uint64_t *partials) {
-    uint64_t carry = 0;
-    for (int64_t base = 0; base < tiles; base += 1024) {
-        const int64_t i = base + threadIdx.x;
-        const uint64_t v = i < tiles ? partials[i] : 0;
-        uint64_t total;
-        const uint64_t ex = block_exclusive_scan<1024>(v, &total);
-        if (i < tiles) partials[i] = carry + ex;
-        carry += total;
-    }
-    if (threadIdx.x == 0) op.total(carry);
-}
-
-template <class Op>
-__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_down(Op op, int64_t count, const uint64_t *partials) {
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
-    uint64_t v[SCAN_ITEMS];
-    uint64_t s = 0;
-#pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; j++) {
-        v[j] = base + j < count ? op.load(base + j) : 0;
-        s += v[j];
-    }
-    uint64_t total;
-    uint64_t p = partials[blockIdx.x] + block_exclusive_scan<SCAN_BLOCK>(s, &total);
-#pragma unroll
-    for (int j = 0; j < SCAN_ITEMS; j++) {
-        if (base + j < count) op.store(base + j, p, v[j]);
-        p += v[j];
-    }
-}
-
 inline int64_t scan_tiles(int64_t count) { return (count + SCAN_TILE - 1) / SCAN_TILE; }
-
-// partials must hold scan_tiles(count) entries.
-template <class Op>
-cudaError_t device_scan(const Op &op, int64_t count, uint64_t *partials, cudaStream_t s) {
-    const int64_t tiles = scan_tiles(count);
-    if (tiles > 0) k_scan_up<Op><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(op, count, partials);
-    k_scan_mid<Op><<<1, 1024, 0, s>>>(op, tiles, partials);
-    if (tiles > 0) k_scan_down<Op><<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(op, count, partials);
-    return cudaGetLastError();
-}
 
 }  // namespace kp
 
