@@ -74,9 +74,9 @@ kp_status alloc_work(Scratch &sc, Work &w, int32_t n0, int32_t nnz0, const kp_op
     } else {
         KP_TRY(sc.get(&w.match, n0));
         KP_TRY(sc.get(&w.cand, n0));
-        KP_TRY(sc.get(&w.list1, n0));
     }
     KP_TRY(sc.get(&w.list0, n0));
+    KP_TRY(sc.get(&w.list1, n0));
     KP_TRY(sc.get(&w.first, n0));
     KP_TRY(sc.get(&w.second, n0));
     KP_TRY(sc.get(&w.off, (int64_t)n0 + 1));
@@ -351,6 +351,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     const int32_t tail_nodes = o->tail_nodes == 0 ? TAIL_NODES : o->tail_nodes;   // -1: never
     int32_t epoch = 0;
     int start = 0;
+    int32_t spares = 0;   // spare arena chunks supplied
     std::vector<int32_t> level_launches(MAX_LEVELS, 0);
     cudaEvent_t ring[LOOKAHEAD + 1];
     for (auto &e : ring)
@@ -429,6 +430,30 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
                 if (sn->done && sn->cn > 0) {   // a tighter bound for the grids
                     n_bound = sn->cn;
                     nnz_bound = std::max<int64_t>(sn->nnz, 1);
+                }
+                // a spare arena chunk before the levels already enqueued and
+                // the next ones could run out (graphs that shrink slowly, as
+                // power-law ones do): no restart, no round trip.  A level
+                // after `seen` carves at most 24 bytes per coarse node of
+                // `seen` and 8 per coarse entry (maps, weights, CSR).
+                if (sn->done && sn->arena_gen == spares) {
+                    const unsigned long long per_level = 24ull * (unsigned long long)sn->cn +
+                                                         8ull * (unsigned long long)sn->nnz +
+                                                         4ull * (unsigned long long)(G + 1) + 8192ull;
+                    if (sn->room < (LOOKAHEAD + 2) * per_level) {
+                        const unsigned long long cap =
+                            align256(std::max<unsigned long long>(arena_cap, 4ull * (LOOKAHEAD + 2) * per_level));
+                        char *chunk = nullptr;
+                        st = dev_alloc((void **)&chunk, cap, s);
+                        if (st != KP_OK) return bail(st);
+                        h->allocations.push_back(chunk);
+                        hs->arena_next = chunk;
+                        hs->arena_next_cap = cap;
+                        if (cudaMemcpyAsync(&dst->arena_next, &hs->arena_next, sizeof(char *) + sizeof(unsigned long long),
+                                            cudaMemcpyHostToDevice, s) != cudaSuccess)
+                            return bail(cuda_error(cudaGetLastError(), "spare arena"));
+                        spares++;
+                    }
                 }
             }
         }

@@ -808,6 +808,8 @@ struct DegScanOp {
         volatile LevelSnap *s = st->snap + level;
         s->cn = cn;
         s->nnz = (int32_t)t;
+        s->room = st->arena_cap - st->arena_used;
+        s->arena_gen = st->arena_gen;
         s->stop = next ? 0 : 1;
         s->done = 1;
     }

@@ -37,7 +37,7 @@ enum : int32_t { LV_ACTIVE = 1, LV_BUILT = 2, LV_NOMATCH = 4 };
 struct Counters {   // one per level, zeroed before the level runs
     GridBarrier bar;
     int32_t err;
-    int32_t list_size[2];
+    int32_t list_size[4];  // proposals: [0],[1] middle pass list and counter, [2],[3] wide pass
     int32_t rounds;
     int32_t cn;            // coarse node count
     int32_t U;             // sum of coarse row upper bounds
@@ -65,6 +65,9 @@ struct LevelSnap {
     int32_t cn;
     int32_t nnz;
     int32_t done;
+    unsigned long long room;   // arena bytes left after the level
+    int32_t arena_gen;         // spare chunks taken so far
+    int32_t pad;
 };
 
 struct DevState {
@@ -72,6 +75,10 @@ struct DevState {
     Counters ctr[MAX_LEVELS];
     char *arena;
     unsigned long long arena_cap, arena_used;
+    // a spare chunk the host supplies ahead of need (stream-ordered copy of
+    // these two words); the arena continues there when a carve does not fit
+    char *arena_next;
+    unsigned long long arena_next_cap;
     int32_t stop_size, max_levels, min_shrink_permille, inner_outer;
     int32_t stop;       // coarsening has ended
     int32_t overflow;   // 1 + the level whose arrays did not fit the arena
@@ -80,7 +87,7 @@ struct DevState {
     int32_t sort_shared_max;   // longest row sorted in shared memory
     int32_t radix_bits;        // bits per radix pass (4..8)
     int32_t tail_resume;       // first level left to the cluster tail (-1: none)
-    int32_t pad2;
+    int32_t arena_gen;         // spare chunks taken so far
     LevelSnap *snap;    // host-mapped, one per level
     GridBarrier tail_bar;
 };
@@ -231,8 +238,18 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned l
 // Carves `bytes` (256-byte aligned) from the arena; nullptr when full.
 __device__ __forceinline__ char *arena_carve(DevState *st, unsigned long long bytes) {
     const unsigned long long b = (bytes + 255ull) & ~255ull;
-    const unsigned long long at = st->arena_used;
-    if (at + b > st->arena_cap) return nullptr;
+    unsigned long long at = st->arena_used;
+    if (at + b > st->arena_cap) {
+        // continue in the spare chunk, if the host has supplied one; arrays
+        // carved before stay where they are
+        if (!st->arena_next || b > st->arena_next_cap) return nullptr;
+        st->arena = st->arena_next;
+        st->arena_cap = st->arena_next_cap;
+        st->arena_next = nullptr;
+        st->arena_next_cap = 0;
+        st->arena_gen++;
+        at = 0;
+    }
     st->arena_used = at + b;
     return st->arena + at;
 }

@@ -108,7 +108,7 @@ __device__ __forceinline__ bool cas_offer(Offer *addr, const Offer &expect, cons
 }
 
 // Lanes per proposing node from the level's mean degree, and the row length
-// above which a node is left to the wide (one warp per node) pass.
+// above which a node is left to the later passes.
 __device__ __forceinline__ int suitor_group(int32_t n, int32_t nnz) {
     const int64_t a = n > 0 ? (int64_t)nnz : 0;
     if (a <= 12ll * n) return 1;
@@ -117,14 +117,113 @@ __device__ __forceinline__ int suitor_group(int32_t n, int32_t nnz) {
     return 32;
 }
 
-// G lanes per proposing node, start nodes [0, n).  Every warp owns one
-// contiguous range of start nodes; its 32/G groups each follow one proposal
-// chain (a node, then whoever it displaced) and take the next start node of
-// the range as soon as their chain ends, so lanes stay busy until the range
-// is used up.  A node whose row is longer than HEAVY entries is parked
-// instead of being scanned by so few lanes; the wide pass (one block per
-// search) finishes those.  The order of proposals does not change the
-// matching.
+// Rows up to this length that the first pass parks are searched by one warp
+// each (the middle pass); longer rows by one block each (the wide pass).
+constexpr int32_t SUITOR_WARP_ROW = 1024;
+
+// A node's best proposal so far: the edge, its weight, and the record of the
+// other end as it was read (the compare-and-swap expects that record).
+struct Proposal {
+    Cand c;
+    int32_t w;
+    Offer snap;
+};
+
+// One thread's share of a search: the entries e0, e0 + STRIDE, ... < end of
+// cur's row.  An edge {cur,v} is eligible when v holds no offer or when cur's
+// offer beats v's standing one at v; the best eligible edge is kept.
+template <int R, int STRIDE>
+__device__ __forceinline__ void scan_row(const DevLevel &L, const Work &w, const HashCtx &hc, int32_t cur,
+                                         int32_t acur, int32_t e0, int32_t end, Proposal &best) {
+    const int32_t *KP_RESTRICT adjncy = L.adjncy;
+    const int32_t *KP_RESTRICT ewgt = L.ewgt;
+    best.c.u = -1;
+    best.c.num = best.c.den = best.c.h = 0;
+    best.w = 0;
+    best.snap = {-1, 0, 0, 0};
+#pragma unroll 4
+    for (int32_t e = e0; e < end; e += STRIDE) {
+        const int32_t v = KP_LDG(adjncy + e);
+        const int32_t wt = KP_LDG(ewgt + e);
+        const Offer st = ld_offer(w.offer + v);
+        Cand c;
+        c.u = v;
+        rating_ab<R>(wt, acur, st.au, c.num, c.den);
+        c.h = edge_hash_in(hc, cur, v);
+        bool eligible = st.s < 0;
+        if (!eligible) {
+            // compare at v: the offer of cur against the standing offer of st.s
+            Cand a, b;
+            a.u = cur;
+            a.num = c.num;
+            a.den = c.den;
+            a.h = c.h;
+            b.u = st.s;
+            rating_ab<R>(st.w, st.as, st.au, b.num, b.den);
+            b.h = edge_hash_in(hc, st.s, v);
+            eligible = better(a, b, v);
+        }
+        if (eligible && better(c, best.c, cur)) {
+            best.c = c;
+            best.w = wt;
+            best.snap = st;
+        }
+    }
+}
+
+// The best proposal over the G lanes of a group (all of them end with it).
+template <int G>
+__device__ __forceinline__ void reduce_proposal(unsigned gmask, int32_t cur, Proposal &best) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        Proposal o;
+        o.c.num = __shfl_xor_sync(gmask, best.c.num, off);
+        o.c.den = __shfl_xor_sync(gmask, best.c.den, off);
+        o.c.h = __shfl_xor_sync(gmask, best.c.h, off);
+        o.c.u = __shfl_xor_sync(gmask, best.c.u, off);
+        o.w = __shfl_xor_sync(gmask, best.w, off);
+        o.snap.s = __shfl_xor_sync(gmask, best.snap.s, off);
+        o.snap.w = __shfl_xor_sync(gmask, best.snap.w, off);
+        o.snap.as = __shfl_xor_sync(gmask, best.snap.as, off);
+        o.snap.au = __shfl_xor_sync(gmask, best.snap.au, off);
+        if (better(o.c, best.c, cur)) best = o;
+    }
+}
+
+// Makes cur's proposal and returns the node that searches next: the suitor
+// it displaced (-1 if none, or if cur found nothing to propose to), or cur
+// itself when the record changed under it.
+__device__ __forceinline__ int32_t propose(const Work &w, int32_t cur, int32_t acur, const Proposal &b,
+                                           unsigned long long &fails) {
+    if (b.c.u < 0) return -1;
+    Offer mine;
+    mine.s = cur;
+    mine.w = b.w;
+    mine.as = acur;
+    mine.au = b.snap.au;
+    if (cas_offer(w.offer + b.c.u, b.snap, mine)) return b.snap.s;
+    fails++;
+    return cur;
+}
+
+// Parks node v for a later pass: rows up to SUITOR_WARP_ROW for the middle
+// pass (list0) unless the calling pass already searches rows that long,
+// longer rows for the wide pass (list1).
+template <int HEAVY>
+__device__ __forceinline__ void park(const Work &w, Counters *ctr, int32_t v, int32_t len) {
+    if (HEAVY < SUITOR_WARP_ROW && len <= SUITOR_WARP_ROW)
+        w.list0[atomicAdd(&ctr->list_size[0], 1)] = v;
+    else
+        w.list1[atomicAdd(&ctr->list_size[2], 1)] = v;
+}
+
+// First pass: G lanes per proposing node, start nodes [0, n).  Every warp
+// owns one contiguous range of start nodes; its 32/G groups each follow one
+// proposal chain (a node, then whoever it displaced) and take the next start
+// node of the range as soon as their chain ends, so lanes stay busy until the
+// range is used up.  A node whose row is longer than HEAVY entries is parked
+// instead of being scanned by so few lanes.  The order of proposals does not
+// change the matching.
 template <int R, int G, int HEAVY>
 __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Counters *ctr, int32_t *err) {
     constexpr int NG = 32 / G;
@@ -134,10 +233,6 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
     const int leader = lane & ~(G - 1);
     const unsigned below_leader = (1u << leader) - 1u;
     const int32_t *KP_RESTRICT xadj = L.xadj;
-    const int32_t *KP_RESTRICT adjncy = L.adjncy;
-    const int32_t *KP_RESTRICT ewgt = L.ewgt;
-    int32_t *parked = w.list0;
-    int32_t *parked_size = &ctr->list_size[0];
     const int64_t count = L.n;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -168,81 +263,18 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
             continue;
         }
         const int32_t beg = KP_LDG(xadj + cur), end = KP_LDG(xadj + cur + 1);
-        if (end - beg > HEAVY) {   // park it for the wide pass
-            if (gl == 0) parked[atomicAdd(parked_size, 1)] = cur;
+        if (end - beg > HEAVY) {
+            if (gl == 0) park<HEAVY>(w, ctr, cur, end - beg);
             cur = -1;
             continue;
         }
         const int32_t acur = rating_attr<R>(L.vwgt, L.outw, cur);
         const HashCtx hc = hash_ctx(w, L, cur);
-        Cand best;
-        best.u = -1;
-        best.num = best.den = best.h = 0;
-        int32_t bw = 0;
-        Offer bsnap = {-1, 0, 0, 0};
-#pragma unroll 4
-        for (int32_t e = beg + gl; e < end; e += G) {
-            const int32_t v = KP_LDG(adjncy + e);
-            const int32_t wt = KP_LDG(ewgt + e);
-            const Offer st = ld_offer(w.offer + v);
-            Cand c;
-            c.u = v;
-            rating_ab<R>(wt, acur, st.au, c.num, c.den);
-            c.h = edge_hash_in(hc, cur, v);
-            bool eligible = st.s < 0;
-            if (!eligible) {
-                // compare at v: the offer of cur against the standing offer of st.s
-                Cand a, b;
-                a.u = cur;
-                a.num = c.num;
-                a.den = c.den;
-                a.h = c.h;
-                b.u = st.s;
-                rating_ab<R>(st.w, st.as, st.au, b.num, b.den);
-                b.h = edge_hash_in(hc, st.s, v);
-                eligible = better(a, b, v);
-            }
-            if (eligible && better(c, best, cur)) {
-                best = c;
-                bw = wt;
-                bsnap = st;
-            }
-        }
-#pragma unroll
-        for (int off = G / 2; off > 0; off >>= 1) {
-            Cand o;
-            o.num = __shfl_xor_sync(gmask, best.num, off);
-            o.den = __shfl_xor_sync(gmask, best.den, off);
-            o.h = __shfl_xor_sync(gmask, best.h, off);
-            o.u = __shfl_xor_sync(gmask, best.u, off);
-            const int32_t ow = __shfl_xor_sync(gmask, bw, off);
-            Offer os;
-            os.s = __shfl_xor_sync(gmask, bsnap.s, off);
-            os.w = __shfl_xor_sync(gmask, bsnap.w, off);
-            os.as = __shfl_xor_sync(gmask, bsnap.as, off);
-            os.au = __shfl_xor_sync(gmask, bsnap.au, off);
-            if (better(o, best, cur)) {
-                best = o;
-                bw = ow;
-                bsnap = os;
-            }
-        }
+        Proposal best;
+        scan_row<R, G>(L, w, hc, cur, acur, beg + gl, end, best);
+        reduce_proposal<G>(gmask, cur, best);
         int32_t next = -1;
-        if (best.u >= 0 && gl == 0) {
-            Offer mine;
-            mine.s = cur;
-            mine.w = bw;
-            mine.as = acur;
-            mine.au = bsnap.au;
-            // success: the displaced suitor (if any) proposes next;
-            // failure: the record changed under us, so cur searches again
-            if (cas_offer(w.offer + best.u, bsnap, mine)) {
-                next = bsnap.s;
-            } else {
-                next = cur;
-                fails++;
-            }
-        }
+        if (gl == 0) next = propose(w, cur, acur, best, fails);
         cur = __shfl_sync(gmask, next, leader);
     }
     if (gl == 0) {
@@ -251,9 +283,55 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
     }
 }
 
-// The wide pass: one block per search.  Blocks take parked nodes from the
-// list in turn (a counter, so long and short rows spread over the blocks)
-// and follow each node's proposal chain; every search scans the row with all
+// The middle pass: one warp per search.  Warps take nodes parked in list0
+// in turn (a counter, so rows of different lengths spread over the warps)
+// and follow each node's chain; a displaced node whose row is longer than
+// SUITOR_WARP_ROW is parked for the wide pass.  Power-law graphs put most of
+// their entries in rows of a few dozen to a thousand entries: a warp each
+// keeps eight times as many of those searches in flight as a block each.
+template <int R>
+__device__ __forceinline__ void suitor_warp(const DevLevel &L, const Work &w, Counters *ctr, int32_t *err) {
+    const int lane = threadIdx.x & 31;
+    const int32_t count = ld_relaxed_i32(&ctr->list_size[0]);
+    long long iters = 0;
+    unsigned long long fails = 0;
+    int32_t cur = -1;
+    for (;;) {
+        if (cur < 0) {
+            int32_t i = 0;
+            if (lane == 0) i = atomicAdd(&ctr->list_size[1], 1);
+            i = __shfl_sync(0xffffffffu, i, 0);
+            if (i >= count) break;
+            cur = w.list0[i];
+        }
+        if (++iters > w.spin_limit) {   // a bound, not a wait
+            if (lane == 0) atomicOr(err, ERR_TIMEOUT);
+            break;
+        }
+        const int32_t beg = KP_LDG(L.xadj + cur), end = KP_LDG(L.xadj + cur + 1);
+        if (end - beg > SUITOR_WARP_ROW) {
+            if (lane == 0) park<SUITOR_WARP_ROW>(w, ctr, cur, end - beg);
+            cur = -1;
+            continue;
+        }
+        const int32_t acur = rating_attr<R>(L.vwgt, L.outw, cur);
+        const HashCtx hc = hash_ctx(w, L, cur);
+        Proposal best;
+        scan_row<R, 32>(L, w, hc, cur, acur, beg + lane, end, best);
+        reduce_proposal<32>(0xffffffffu, cur, best);
+        int32_t next = -1;
+        if (lane == 0) next = propose(w, cur, acur, best, fails);
+        cur = __shfl_sync(0xffffffffu, next, 0);
+    }
+    if (lane == 0) {
+        atomicAdd(&ctr->searches, (unsigned long long)iters);
+        if (fails) atomicAdd(&ctr->failed_cas, fails);
+    }
+}
+
+// The wide pass: one block per search.  Blocks take nodes parked in list1
+// in turn (a counter, so long and short rows spread over the blocks) and
+// follow each node's proposal chain; every search scans the row with all
 // threads of the block and reduces the best neighbour through shared memory.
 // Rows of hubs (power-law graphs) are thousands of times longer than the
 // mean, so this keeps a hub's search from holding one warp for its whole
@@ -261,13 +339,10 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
 template <int R>
 __device__ __forceinline__ void suitor_wide(const DevLevel &L, const Work &w, Counters *ctr, int32_t *err) {
     constexpr int NW = MATCH_BLOCK / 32;
-    __shared__ uint64_t s_num[NW], s_den[NW], s_h[NW];
-    __shared__ int32_t s_u[NW], s_bw[NW];
-    __shared__ Offer s_snap[NW];
+    __shared__ Proposal s_best[NW];
     __shared__ int32_t s_cur;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int32_t *parked = w.list0;
-    const int32_t count = ld_relaxed_i32(&ctr->list_size[0]);
+    const int32_t count = ld_relaxed_i32(&ctr->list_size[2]);
     int32_t cur = -1;                 // thread 0's chain
     long long iters = 0;
     unsigned long long fails = 0;
@@ -275,8 +350,8 @@ __device__ __forceinline__ void suitor_wide(const DevLevel &L, const Work &w, Co
     for (;;) {
         if (threadIdx.x == 0) {
             if (cur < 0 && !aborted) {
-                const int32_t i = atomicAdd(&ctr->list_size[1], 1);
-                cur = i < count ? parked[i] : -1;
+                const int32_t i = atomicAdd(&ctr->list_size[3], 1);
+                cur = i < count ? w.list1[i] : -1;
             }
             if (cur >= 0 && ++iters > w.spin_limit) {   // a bound, not a wait
                 atomicOr(err, ERR_TIMEOUT);
@@ -291,90 +366,15 @@ __device__ __forceinline__ void suitor_wide(const DevLevel &L, const Work &w, Co
         const int32_t beg = KP_LDG(L.xadj + c), end = KP_LDG(L.xadj + c + 1);
         const int32_t ac = rating_attr<R>(L.vwgt, L.outw, c);
         const HashCtx hc = hash_ctx(w, L, c);
-        Cand best;
-        best.u = -1;
-        best.num = best.den = best.h = 0;
-        int32_t bw = 0;
-        Offer bsnap = {-1, 0, 0, 0};
-#pragma unroll 4
-        for (int32_t e = beg + (int32_t)threadIdx.x; e < end; e += MATCH_BLOCK) {
-            const int32_t v = KP_LDG(L.adjncy + e);
-            const int32_t wt = KP_LDG(L.ewgt + e);
-            const Offer so = ld_offer(w.offer + v);
-            Cand cd;
-            cd.u = v;
-            rating_ab<R>(wt, ac, so.au, cd.num, cd.den);
-            cd.h = edge_hash_in(hc, c, v);
-            bool eligible = so.s < 0;
-            if (!eligible) {
-                Cand a = cd, b;
-                a.u = c;
-                b.u = so.s;
-                rating_ab<R>(so.w, so.as, so.au, b.num, b.den);
-                b.h = edge_hash_in(hc, so.s, v);
-                eligible = better(a, b, v);
-            }
-            if (eligible && better(cd, best, c)) {
-                best = cd;
-                bw = wt;
-                bsnap = so;
-            }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            Cand o;
-            o.num = __shfl_xor_sync(0xffffffffu, best.num, off);
-            o.den = __shfl_xor_sync(0xffffffffu, best.den, off);
-            o.h = __shfl_xor_sync(0xffffffffu, best.h, off);
-            o.u = __shfl_xor_sync(0xffffffffu, best.u, off);
-            const int32_t ow = __shfl_xor_sync(0xffffffffu, bw, off);
-            Offer os;
-            os.s = __shfl_xor_sync(0xffffffffu, bsnap.s, off);
-            os.w = __shfl_xor_sync(0xffffffffu, bsnap.w, off);
-            os.as = __shfl_xor_sync(0xffffffffu, bsnap.as, off);
-            os.au = __shfl_xor_sync(0xffffffffu, bsnap.au, off);
-            if (better(o, best, c)) {
-                best = o;
-                bw = ow;
-                bsnap = os;
-            }
-        }
-        if (lane == 0) {
-            s_num[warp] = best.num;
-            s_den[warp] = best.den;
-            s_h[warp] = best.h;
-            s_u[warp] = best.u;
-            s_bw[warp] = bw;
-            s_snap[warp] = bsnap;
-        }
+        Proposal best;
+        scan_row<R, MATCH_BLOCK>(L, w, hc, c, ac, beg + (int32_t)threadIdx.x, end, best);
+        reduce_proposal<32>(0xffffffffu, c, best);
+        if (lane == 0) s_best[warp] = best;
         __syncthreads();
         if (threadIdx.x == 0) {
-            for (int i = 1; i < NW; i++) {
-                Cand o;
-                o.num = s_num[i];
-                o.den = s_den[i];
-                o.h = s_h[i];
-                o.u = s_u[i];
-                if (better(o, best, c)) {
-                    best = o;
-                    bw = s_bw[i];
-                    bsnap = s_snap[i];
-                }
-            }
-            cur = -1;
-            if (best.u >= 0) {
-                Offer mine;
-                mine.s = c;
-                mine.w = bw;
-                mine.as = ac;
-                mine.au = bsnap.au;
-                if (cas_offer(w.offer + best.u, bsnap, mine)) {
-                    cur = bsnap.s;   // the displaced suitor searches next (or -1)
-                } else {
-                    cur = c;         // the record changed: search again
-                    fails++;
-                }
-            }
+            for (int i = 1; i < NW; i++)
+                if (better(s_best[i].c, best.c, c)) best = s_best[i];
+            cur = propose(w, c, ac, best, fails);
         }
         // thread 0 writes s_cur only after the barrier at the top of the next
         // search, which every thread reaches after it is done with this one
@@ -385,13 +385,18 @@ __device__ __forceinline__ void suitor_wide(const DevLevel &L, const Work &w, Co
     }
 }
 
-template <int R, bool FROM_LIST>
+// Passes of the proposal scheme on one level.
+enum : int { SUITOR_FIRST = 0, SUITOR_WARP = 1, SUITOR_WIDE = 2 };
+
+template <int R, int PASS>
 __device__ void phase_suitor(DevState *st, int level, const Work &w) {
     const DevLevel L = st->lv[level];
     if (!(L.flags & LV_ACTIVE)) return;
     Counters *ctr = &st->ctr[level];
-    if (FROM_LIST) {
+    if (PASS == SUITOR_WIDE) {
         suitor_wide<R>(L, w, ctr, &st->err);
+    } else if (PASS == SUITOR_WARP) {
+        suitor_warp<R>(L, w, ctr, &st->err);
     } else {
         switch (st->suitor_lanes ? st->suitor_lanes : suitor_group(L.n, L.nnz)) {
         case 1: suitor_body<R, 1, 32>(L, w, ctr, &st->err); break;
@@ -569,12 +574,12 @@ __global__ void k_level_begin(DevState *st, int level, Work w) {
     phase_level_begin<R, SUITOR>(st, level, w);
 }
 
-template <int R, bool FROM_LIST>
+template <int R, int PASS>
 #ifndef KP_SUITOR_MIN_BLOCKS
 #define KP_SUITOR_MIN_BLOCKS 3   // resident blocks per SM the register budget must allow
 #endif
 __global__ void __launch_bounds__(MATCH_BLOCK, KP_SUITOR_MIN_BLOCKS) k_suitor(DevState *st, int level, Work w) {
-    phase_suitor<R, FROM_LIST>(st, level, w);
+    phase_suitor<R, PASS>(st, level, w);
 }
 
 template <int R>

@@ -49,11 +49,17 @@ __global__ void __launch_bounds__(MATCH_BLOCK) k_tail(DevState *st, int first, i
         phase_level_begin<R, SUITOR>(st, level, w);
         if (!grid_sync(bar, err, lim)) return;
         if (SUITOR) {
-            phase_suitor<R, false>(st, level, w);
+            phase_suitor<R, SUITOR_FIRST>(st, level, w);
             if (!grid_sync(bar, err, lim)) return;
-            // the wide pass only when some node was parked (uniform decision)
+            // the later passes only when some node was parked for them
+            // (uniform decisions: the passes after a barrier do not write
+            // the size they read)
             if (ld_relaxed_i32(&st->ctr[level].list_size[0]) > 0) {
-                phase_suitor<R, true>(st, level, w);
+                phase_suitor<R, SUITOR_WARP>(st, level, w);
+                if (!grid_sync(bar, err, lim)) return;
+            }
+            if (ld_relaxed_i32(&st->ctr[level].list_size[2]) > 0) {
+                phase_suitor<R, SUITOR_WIDE>(st, level, w);
                 if (!grid_sync(bar, err, lim)) return;
             }
         } else {

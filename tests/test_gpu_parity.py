@@ -275,6 +275,20 @@ def test_arena_growth_resumes_exactly(matcher, tail):
         h.free()
 
 
+@pytest.mark.parametrize("tail", [0, -1])
+def test_power_law_levels_continue_in_spare_arena(tail):
+    """R-MAT graphs shrink by a few percent a level, so the initial arena runs
+    low after a few levels; the engine continues in spare chunks supplied
+    ahead of need (and restarts only if one comes too late), with the same
+    results.  The hubs also take all three proposal passes."""
+    for sc, seed in [(13, 3), (15, 4)]:
+        g = I.rmat(sc, seed)
+        for m in MATCHERS:
+            h, dg, levels, maps = run_gpu(g, seed=5, stop_size=40, matcher=m, tail_nodes=tail)
+            assert_same(levels, maps, O.coarsen(g, "expansion*2", 5, 40), f"{g.name} {m} tail={tail}")
+            h.free()
+
+
 def test_stop_rules():
     g = I.grid2d(64, 64)
     for kw in [dict(max_levels=2), dict(max_levels=0), dict(min_shrink_permille=600),
