@@ -71,6 +71,11 @@ kp_status alloc_work(Scratch &sc, Work &w, int32_t n0, int32_t nnz0, const kp_op
     std::memset(&w, 0, sizeof w);
     if (o->matcher == KP_MATCHER_SUITOR) {
         KP_TRY(sc.get(&w.offer, n0));
+        // list1 holds rows longer than the middle pass's limit only
+        w.cache_slots = (int32_t)std::min<int64_t>((int64_t)n0, (int64_t)nnz0 / SUITOR_WARP_ROW + 2);
+        KP_TRY(sc.get(&w.wslot, n0));
+        KP_TRY(sc.get(&w.cache, (int64_t)w.cache_slots * SUITOR_CACHE_K));
+        KP_TRY(sc.get(&w.cache_hdr, w.cache_slots));
     } else {
         KP_TRY(sc.get(&w.match, n0));
         KP_TRY(sc.get(&w.cand, n0));
@@ -86,6 +91,7 @@ kp_status alloc_work(Scratch &sc, Work &w, int32_t n0, int32_t nnz0, const kp_op
     KP_TRY(sc.get(&w.big_adj, nnz0));
     KP_TRY(sc.get(&w.big_w, nnz0));
     for (int c = 1; c <= 4; c++) KP_TRY(sc.get(&w.lists[c], n0));
+    KP_TRY(sc.get(&w.lists[5], (int64_t)nnz0 / HUGE_ROW + 2));   // each such row holds more than HUGE_ROW entries
     KP_TRY(sc.get(&w.status, scan_tiles(n0) + 1));
     KP_TRY(sc.get(dst, 1));
     w.seed = o->seed;
@@ -352,6 +358,8 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     int32_t epoch = 0;
     int start = 0;
     int32_t spares = 0;   // spare arena chunks supplied
+    int deg_level = -1;   // level whose largest degree is known (deg_max), -1: none yet
+    int64_t deg_max = 0;
     std::vector<int32_t> level_launches(MAX_LEVELS, 0);
     cudaEvent_t ring[LOOKAHEAD + 1];
     for (auto &e : ring)
@@ -398,6 +406,10 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
             LL.matcher = o->matcher;
             LL.n_bound = n_bound;
             LL.nnz_bound = nnz_bound;
+            // a coarse degree is at most twice the largest of the level
+            // before, and a gathered row holds the degrees of two nodes
+            LL.huge = deg_level < 0 || level - deg_level > 20 ||
+                      2 * (deg_max << (level - deg_level)) > (int64_t)HUGE_ROW;
             LL.epoch_relabel = ++epoch;
             LL.epoch_degscan = ++epoch;
             const int32_t before = launches;
@@ -430,12 +442,16 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
                 if (sn->done && sn->cn > 0) {   // a tighter bound for the grids
                     n_bound = sn->cn;
                     nnz_bound = std::max<int64_t>(sn->nnz, 1);
+                    deg_level = seen + 1;   // its largest degree (below 1024 when not recorded)
+                    deg_max = std::max<int64_t>(sn->maxdeg, 1023);
                 }
                 // a spare arena chunk before the levels already enqueued and
                 // the next ones could run out (graphs that shrink slowly, as
                 // power-law ones do): no restart, no round trip.  A level
-                // after `seen` carves at most 24 bytes per coarse node of
-                // `seen` and 8 per coarse entry (maps, weights, CSR).
+                // after `seen` reserves at most 24 bytes per coarse node of
+                // `seen` and 8 per coarse entry (maps, weights, CSR); the
+                // device moves to the spare when a level's reservation does
+                // not fit the rest of the current chunk.
                 if (sn->done && sn->arena_gen == spares) {
                     const unsigned long long per_level = 24ull * (unsigned long long)sn->cn +
                                                          8ull * (unsigned long long)sn->nnz +
@@ -592,6 +608,7 @@ kp_status plan_capture(kp_plan *p) {
         LL.matcher = p->o.matcher;
         LL.n_bound = p->sizes[(size_t)level].first;
         LL.nnz_bound = std::max(p->sizes[(size_t)level].second, 1);
+        LL.huge = true;   // a replay may meet other degrees than the checking run
         LL.epoch_relabel = ++epoch;
         LL.epoch_degscan = ++epoch;
         st = launch_matching(LL, s, &p->launches);

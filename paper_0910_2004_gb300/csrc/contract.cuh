@@ -233,7 +233,10 @@ __device__ __forceinline__ void contract_thread(const CView &p, int32_t x, int32
     if (p.outw) p.outw[x] = total;
 }
 
-static __device__ void phase_contract_small(DevState *st, int level, const Work &w) {
+// Contracts the rows of at most TNET gathered entries and sorts the others
+// into class lists by length; rows of more than huge_row entries (0: none)
+// form class 5, which the caller hands to the cluster kernel.
+static __device__ void phase_contract_small(DevState *st, int level, const Work &w, int32_t huge_row) {
     CView p;
     if (!load_view(st, level, w, p)) return;
     if (w.batch) {   // first coarse node of every graph (the coarse graph ids are sorted)
@@ -260,9 +263,10 @@ static __device__ void phase_contract_small(DevState *st, int level, const Work 
             members(p, (int32_t)x, xa, da, xb, db);
             const int32_t L = da + db;
             cls = L <= TNET ? 0 : L <= 32 ? 1 : L <= 128 ? 2 : L <= p.sort_shared_max ? 3 : 4;
+            if (cls == 4 && huge_row > 0 && L > huge_row) cls = 5;
         }
 #pragma unroll
-        for (int c = 1; c <= 4; c++) {
+        for (int c = 1; c <= 5; c++) {
             const bool mine = cls == c;
             const unsigned m = __ballot_sync(0xffffffffu, mine);
             if (m) {
@@ -497,6 +501,7 @@ static __device__ void contract_block_smem(const CView &p, int32_t x, int32_t *k
         int32_t t = 0;
         for (int wi = 0; wi < CONTRACT_BLOCK / 32; wi++) t += s_red[wi];
         p.degp[x] = (int32_t)tot;
+        if (tot >= 1024) atomicMax(&p.ctr->maxdeg, (int32_t)tot);
         if (p.outw) p.outw[x] = t;
     }
     __syncthreads();
@@ -679,6 +684,7 @@ static __device__ void contract_block_radix(const CView &p, int32_t x, int passe
         int32_t t = 0;
         for (int w2 = 0; w2 < NW; w2++) t += sm.s_red[w2];
         p.degp[x] = sm.s_carry;
+        if (sm.s_carry >= 1024) atomicMax(&p.ctr->maxdeg, sm.s_carry);
         if (p.outw) p.outw[x] = t;
     }
     __syncthreads();
@@ -808,6 +814,7 @@ struct DegScanOp {
         volatile LevelSnap *s = st->snap + level;
         s->cn = cn;
         s->nnz = (int32_t)t;
+        s->maxdeg = st->ctr[level].maxdeg;   // the contraction kernels ended before this scan
         s->room = st->arena_cap - st->arena_used;
         s->arena_gen = st->arena_gen;
         s->stop = next ? 0 : 1;
@@ -854,6 +861,16 @@ static __device__ void phase_compact(DevState *st, int level, const Work &w) {
         const int32_t g = w.lists[4][li];
         const int32_t o = w.off[g], d = w.degp[g], s = cxadj[g];
         for (int32_t i = threadIdx.x; i < d; i += blockDim.x) {
+            cadj[s + i] = w.tmp_adj[o + i];
+            cw[s + i] = w.tmp_w[o + i];
+        }
+    }
+    // the few huge rows: each one over the whole grid
+    const int32_t n5 = ctr->nclass[5];
+    for (int32_t li = 0; li < n5; li++) {
+        const int32_t g = w.lists[5][li];
+        const int32_t o = w.off[g], d = w.degp[g], s = cxadj[g];
+        for (int64_t i = t; i < d; i += stride) {
             cadj[s + i] = w.tmp_adj[o + i];
             cw[s + i] = w.tmp_w[o + i];
         }

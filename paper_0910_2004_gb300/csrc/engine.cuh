@@ -30,6 +30,15 @@ constexpr int MID_MAX = 2048;          // longest row handled in shared memory
 constexpr int MATCH_BLOCK = 256;
 constexpr int CONTRACT_BLOCK = 256;
 constexpr int MAX_LEVELS = 128;        // level table size (kp_options.max_levels <= 120)
+// proposals: rows up to SUITOR_WARP_ROW that the first pass parks are
+// searched by one warp each, longer ones by one block each; rows longer than
+// SUITOR_CACHE_ROW keep up to SUITOR_CACHE_K candidates between searches
+constexpr int32_t SUITOR_WARP_ROW = 1024;
+constexpr int32_t SUITOR_CACHE_ROW = 4096;
+constexpr int SUITOR_CACHE_K = 8;
+// contraction: rows of more gathered entries than this are sorted by a
+// thread-block cluster each (levels launched one kernel per phase)
+constexpr int32_t HUGE_ROW = 32768;
 
 // level flags
 enum : int32_t { LV_ACTIVE = 1, LV_BUILT = 2, LV_NOMATCH = 4 };
@@ -41,10 +50,10 @@ struct Counters {   // one per level, zeroed before the level runs
     int32_t rounds;
     int32_t cn;            // coarse node count
     int32_t U;             // sum of coarse row upper bounds
-    int32_t nclass[5];     // overflow lists: [1] <=32, [2] <=128, [3] <=MID_MAX, [4] longer
+    int32_t nclass[6];     // overflow lists: [1] <=32, [2] <=128, [3] <=MID_MAX, [4] longer, [5] > huge_row
     int32_t nnz_out;       // coarse entry count
     int32_t tile_counter[2];
-    int32_t pad;
+    int32_t maxdeg;        // largest coarse degree if it is at least 1024, else 0
     unsigned long long searches;     // rating passes over a row
     unsigned long long failed_cas;   // lost proposal races
 };
@@ -67,7 +76,7 @@ struct LevelSnap {
     int32_t done;
     unsigned long long room;   // arena bytes left after the level
     int32_t arena_gen;         // spare chunks taken so far
-    int32_t pad;
+    int32_t maxdeg;            // Counters::maxdeg of the level
 };
 
 struct DevState {
@@ -127,7 +136,13 @@ struct Work {
     int32_t *match, *cand, *list0, *list1;
     int32_t *first, *second, *off, *degp;
     int32_t *tmp_adj, *tmp_w, *big_adj, *big_w;
-    int32_t *lists[5];
+    int32_t *lists[6];
+    // proposals: candidate caches of the rows searched by the wide pass,
+    // one slot per entry of list1 (wslot: node -> slot, checked on use)
+    int32_t *wslot;
+    int2 *cache;       // SUITOR_CACHE_K candidates {node, edge weight} per slot
+    int2 *cache_hdr;   // per slot {candidates kept, next to try}
+    int32_t cache_slots;
     TileStatus *status;
     uint64_t seed;
     long long spin_limit;
@@ -235,21 +250,25 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned l
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Before a level carves anything (one thread): when the rest of the arena
+// may be too small for the level's arrays (`need` bytes at most), continue
+// in the spare chunk the host supplied, if there is one and it is large
+// enough.  Arrays carved before stay where they are.
+__device__ __forceinline__ void arena_reserve(DevState *st, unsigned long long need) {
+    if (st->arena_used + need <= st->arena_cap || !st->arena_next || need > st->arena_next_cap) return;
+    st->arena = st->arena_next;
+    st->arena_cap = st->arena_next_cap;
+    st->arena_used = 0;
+    st->arena_next = nullptr;
+    st->arena_next_cap = 0;
+    st->arena_gen++;
+}
+
 // Carves `bytes` (256-byte aligned) from the arena; nullptr when full.
 __device__ __forceinline__ char *arena_carve(DevState *st, unsigned long long bytes) {
     const unsigned long long b = (bytes + 255ull) & ~255ull;
-    unsigned long long at = st->arena_used;
-    if (at + b > st->arena_cap) {
-        // continue in the spare chunk, if the host has supplied one; arrays
-        // carved before stay where they are
-        if (!st->arena_next || b > st->arena_next_cap) return nullptr;
-        st->arena = st->arena_next;
-        st->arena_cap = st->arena_next_cap;
-        st->arena_next = nullptr;
-        st->arena_next_cap = 0;
-        st->arena_gen++;
-        at = 0;
-    }
+    const unsigned long long at = st->arena_used;
+    if (at + b > st->arena_cap) return nullptr;
     st->arena_used = at + b;
     return st->arena + at;
 }
@@ -363,6 +382,7 @@ struct LevelLaunch {
     int matcher;
     int32_t n_bound;     // upper bound of the level's node count (grid sizes)
     int64_t nnz_bound;   // upper bound of its entry count
+    bool huge;           // rows of more than HUGE_ROW gathered entries are possible
     int32_t epoch_relabel, epoch_degscan;
 };
 

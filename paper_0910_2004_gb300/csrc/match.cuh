@@ -21,6 +21,10 @@ __device__ void phase_level_begin(DevState *st, int level, const Work &w) {
     const DevLevel L = st->lv[level];
     if (!(L.flags & LV_ACTIVE)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // what the level carves at most: map, c', batch ids and offsets,
+        // coarse xadj, entries (at most nnz), Out, each 256-byte aligned
+        arena_reserve(st, 24ull * (unsigned long long)L.n + 8ull * (unsigned long long)L.nnz +
+                              4ull * ((unsigned long long)w.num_graphs + 1) + 8ull * 256ull);
         int32_t *map = (int32_t *)arena_carve(st, 4ull * (unsigned long long)L.n);
         int32_t *cv = map ? (int32_t *)arena_carve(st, 4ull * (unsigned long long)L.n) : nullptr;
         int32_t *gidn = cv, *goffn = cv;
@@ -117,10 +121,6 @@ __device__ __forceinline__ int suitor_group(int32_t n, int32_t nnz) {
     return 32;
 }
 
-// Rows up to this length that the first pass parks are searched by one warp
-// each (the middle pass); longer rows by one block each (the wide pass).
-constexpr int32_t SUITOR_WARP_ROW = 1024;
-
 // A node's best proposal so far: the edge, its weight, and the record of the
 // other end as it was read (the compare-and-swap expects that record).
 struct Proposal {
@@ -129,9 +129,30 @@ struct Proposal {
     Offer snap;
 };
 
+// Whether cur may propose to v now (v's record as read: so): v holds no
+// offer, or cur's offer beats the standing one at v.  cd gets the edge as
+// seen from cur.
+template <int R>
+__device__ __forceinline__ bool eligible_at(const HashCtx &hc, int32_t cur, int32_t acur, int32_t v, int32_t wt,
+                                            const Offer &so, Cand &cd) {
+    cd.u = v;
+    rating_ab<R>(wt, acur, so.au, cd.num, cd.den);
+    cd.h = edge_hash_in(hc, cur, v);
+    if (so.s < 0) return true;
+    // compare at v: the offer of cur against the standing offer of so.s
+    Cand a, b;
+    a.u = cur;
+    a.num = cd.num;
+    a.den = cd.den;
+    a.h = cd.h;
+    b.u = so.s;
+    rating_ab<R>(so.w, so.as, so.au, b.num, b.den);
+    b.h = edge_hash_in(hc, so.s, v);
+    return better(a, b, v);
+}
+
 // One thread's share of a search: the entries e0, e0 + STRIDE, ... < end of
-// cur's row.  An edge {cur,v} is eligible when v holds no offer or when cur's
-// offer beats v's standing one at v; the best eligible edge is kept.
+// cur's row; the best eligible edge is kept.
 template <int R, int STRIDE>
 __device__ __forceinline__ void scan_row(const DevLevel &L, const Work &w, const HashCtx &hc, int32_t cur,
                                          int32_t acur, int32_t e0, int32_t end, Proposal &best) {
@@ -147,26 +168,52 @@ __device__ __forceinline__ void scan_row(const DevLevel &L, const Work &w, const
         const int32_t wt = KP_LDG(ewgt + e);
         const Offer st = ld_offer(w.offer + v);
         Cand c;
-        c.u = v;
-        rating_ab<R>(wt, acur, st.au, c.num, c.den);
-        c.h = edge_hash_in(hc, cur, v);
-        bool eligible = st.s < 0;
-        if (!eligible) {
-            // compare at v: the offer of cur against the standing offer of st.s
-            Cand a, b;
-            a.u = cur;
-            a.num = c.num;
-            a.den = c.den;
-            a.h = c.h;
-            b.u = st.s;
-            rating_ab<R>(st.w, st.as, st.au, b.num, b.den);
-            b.h = edge_hash_in(hc, st.s, v);
-            eligible = better(a, b, v);
-        }
-        if (eligible && better(c, best.c, cur)) {
+        if (eligible_at<R>(hc, cur, acur, v, wt, st, c) && better(c, best.c, cur)) {
             best.c = c;
             best.w = wt;
             best.snap = st;
+        }
+    }
+}
+
+// A candidate without the record it was read with.
+struct Cached {
+    Cand c;
+    int32_t w;
+};
+
+// scan_row that also keeps the second best eligible edge of the thread's
+// share and counts the eligible edges it saw (up to 3).
+template <int R, int STRIDE>
+__device__ __forceinline__ void scan_row_top2(const DevLevel &L, const Work &w, const HashCtx &hc, int32_t cur,
+                                              int32_t acur, int32_t e0, int32_t end, Proposal &best, Cached &second,
+                                              int32_t &seen) {
+    const int32_t *KP_RESTRICT adjncy = L.adjncy;
+    const int32_t *KP_RESTRICT ewgt = L.ewgt;
+    best.c.u = -1;
+    best.c.num = best.c.den = best.c.h = 0;
+    best.w = 0;
+    best.snap = {-1, 0, 0, 0};
+    second.c = best.c;
+    second.w = 0;
+    seen = 0;
+#pragma unroll 4
+    for (int32_t e = e0; e < end; e += STRIDE) {
+        const int32_t v = KP_LDG(adjncy + e);
+        const int32_t wt = KP_LDG(ewgt + e);
+        const Offer st = ld_offer(w.offer + v);
+        Cand c;
+        if (!eligible_at<R>(hc, cur, acur, v, wt, st, c)) continue;
+        seen = min(seen + 1, 3);
+        if (better(c, best.c, cur)) {
+            second.c = best.c;
+            second.w = best.w;
+            best.c = c;
+            best.w = wt;
+            best.snap = st;
+        } else if (better(c, second.c, cur)) {
+            second.c = c;
+            second.w = wt;
         }
     }
 }
@@ -206,15 +253,12 @@ __device__ __forceinline__ int32_t propose(const Work &w, int32_t cur, int32_t a
     return cur;
 }
 
-// Parks node v for a later pass: rows up to SUITOR_WARP_ROW for the middle
-// pass (list0) unless the calling pass already searches rows that long,
-// longer rows for the wide pass (list1).
-template <int HEAVY>
-__device__ __forceinline__ void park(const Work &w, Counters *ctr, int32_t v, int32_t len) {
-    if (HEAVY < SUITOR_WARP_ROW && len <= SUITOR_WARP_ROW)
-        w.list0[atomicAdd(&ctr->list_size[0], 1)] = v;
-    else
-        w.list1[atomicAdd(&ctr->list_size[2], 1)] = v;
+// Parks node v for the wide pass (list1), with an empty candidate cache.
+__device__ __forceinline__ void park_wide(const Work &w, Counters *ctr, int32_t v) {
+    const int32_t slot = atomicAdd(&ctr->list_size[2], 1);
+    w.list1[slot] = v;
+    w.wslot[v] = slot;
+    if (slot < w.cache_slots) w.cache_hdr[slot] = make_int2(0, 0);
 }
 
 // First pass: G lanes per proposing node, start nodes [0, n).  Every warp
@@ -222,8 +266,9 @@ __device__ __forceinline__ void park(const Work &w, Counters *ctr, int32_t v, in
 // proposal chain (a node, then whoever it displaced) and take the next start
 // node of the range as soon as their chain ends, so lanes stay busy until the
 // range is used up.  A node whose row is longer than HEAVY entries is parked
-// instead of being scanned by so few lanes.  The order of proposals does not
-// change the matching.
+// for the middle pass (list0) instead of being scanned by so few lanes; that
+// pass hands the rows too long for a warp on to the wide pass.  The order of
+// proposals does not change the matching.
 template <int R, int G, int HEAVY>
 __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Counters *ctr, int32_t *err) {
     constexpr int NG = 32 / G;
@@ -264,7 +309,7 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
         }
         const int32_t beg = KP_LDG(xadj + cur), end = KP_LDG(xadj + cur + 1);
         if (end - beg > HEAVY) {
-            if (gl == 0) park<HEAVY>(w, ctr, cur, end - beg);
+            if (gl == 0) w.list0[atomicAdd(&ctr->list_size[0], 1)] = cur;
             cur = -1;
             continue;
         }
@@ -285,7 +330,7 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
 
 // The middle pass: one warp per search.  Warps take nodes parked in list0
 // in turn (a counter, so rows of different lengths spread over the warps)
-// and follow each node's chain; a displaced node whose row is longer than
+// and follow each node's chain; a node whose row is longer than
 // SUITOR_WARP_ROW is parked for the wide pass.  Power-law graphs put most of
 // their entries in rows of a few dozen to a thousand entries: a warp each
 // keeps eight times as many of those searches in flight as a block each.
@@ -293,6 +338,7 @@ template <int R>
 __device__ __forceinline__ void suitor_warp(const DevLevel &L, const Work &w, Counters *ctr, int32_t *err) {
     const int lane = threadIdx.x & 31;
     const int32_t count = ld_relaxed_i32(&ctr->list_size[0]);
+    if (count == 0) return;   // nothing parked: no counter traffic
     long long iters = 0;
     unsigned long long fails = 0;
     int32_t cur = -1;
@@ -310,7 +356,7 @@ __device__ __forceinline__ void suitor_warp(const DevLevel &L, const Work &w, Co
         }
         const int32_t beg = KP_LDG(L.xadj + cur), end = KP_LDG(L.xadj + cur + 1);
         if (end - beg > SUITOR_WARP_ROW) {
-            if (lane == 0) park<SUITOR_WARP_ROW>(w, ctr, cur, end - beg);
+            if (lane == 0) park_wide(w, ctr, cur);
             cur = -1;
             continue;
         }
@@ -329,74 +375,228 @@ __device__ __forceinline__ void suitor_warp(const DevLevel &L, const Work &w, Co
     }
 }
 
+// The candidate cache of a long row (wide pass).  Offers only improve, so an
+// edge {c,v} that was not eligible when c's row was scanned never becomes
+// eligible again.  A scan of c's row therefore keeps the best eligible
+// candidates it saw, in c's order and as an exact prefix of that order, and
+// c's later searches (after it is displaced) take the first of them that is
+// still eligible: the same proposal a full scan would make.  Only when all
+// are used up is the row scanned again.  A hub displaced many times then
+// scans its row a few times instead of once per displacement.
+
+// c's cache slot, -1 if it has none (slots left from earlier levels fail
+// the check against list1).
+__device__ __forceinline__ int32_t cache_slot(const Work &w, int32_t count, int32_t c) {
+    const int32_t slot = __ldcg(w.wslot + c);
+    if (slot < 0 || slot >= count || slot >= w.cache_slots) return -1;
+    return __ldcg(w.list1 + slot) == c ? slot : -1;
+}
+
+// One proposal of c from its cache (one thread).  Returns the node that
+// searches next (the displaced suitor, -1 if none, or c after a lost race),
+// or -2 when the cache is used up and c's row has to be scanned again.
+template <int R>
+__device__ __forceinline__ int32_t propose_cached(const DevLevel &L, const Work &w, int32_t slot, int32_t c,
+                                                  unsigned long long &fails) {
+    __threadfence();   // the cache as c's previous search left it (another block)
+    int2 hd = __ldcg(w.cache_hdr + slot);
+    const int32_t ac = rating_attr<R>(L.vwgt, L.outw, c);
+    const HashCtx hc = hash_ctx(w, L, c);
+    for (; hd.y < hd.x; hd.y++) {
+        const int2 cand = __ldcg(w.cache + (int64_t)slot * SUITOR_CACHE_K + hd.y);
+        const Offer so = ld_offer(w.offer + cand.x);
+        Cand cd;
+        if (!eligible_at<R>(hc, c, ac, cand.x, cand.y, so, cd)) continue;
+        __stcg(w.cache_hdr + slot, hd);
+        __threadfence();   // the cache position is visible before the proposal is
+        Offer mine;
+        mine.s = c;
+        mine.w = cand.y;
+        mine.as = ac;
+        mine.au = so.au;
+        if (cas_offer(w.offer + cand.x, so, mine)) return so.s;
+        fails++;
+        return c;
+    }
+    __stcg(w.cache_hdr + slot, hd);
+    return -2;
+}
+
 // The wide pass: one block per search.  Blocks take nodes parked in list1
 // in turn (a counter, so long and short rows spread over the blocks) and
 // follow each node's proposal chain; every search scans the row with all
 // threads of the block and reduces the best neighbour through shared memory.
 // Rows of hubs (power-law graphs) are thousands of times longer than the
 // mean, so this keeps a hub's search from holding one warp for its whole
-// row while the rest of the GPU idles.
-template <int R>
+// row while the rest of the GPU idles.  Rows longer than SUITOR_CACHE_ROW
+// fill and use their candidate cache.  TAIL: the persistent tail's form,
+// whose levels are small: it takes every node the first pass parked (list0,
+// no middle pass) and keeps no cache, which keeps the tail's registers.
+template <int R, bool TAIL>
 __device__ __forceinline__ void suitor_wide(const DevLevel &L, const Work &w, Counters *ctr, int32_t *err) {
     constexpr int NW = MATCH_BLOCK / 32;
     __shared__ Proposal s_best[NW];
-    __shared__ int32_t s_cur;
+    __shared__ int32_t s_tid[NW], s_last[NW];
+    __shared__ int32_t s_cur, s_slot, s_win, s_stop;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int32_t count = ld_relaxed_i32(&ctr->list_size[2]);
+    constexpr bool CACHE = !TAIL;
+    const int32_t *parked = TAIL ? w.list0 : w.list1;
+    int32_t *next_parked = TAIL ? &ctr->list_size[1] : &ctr->list_size[3];
+    const int32_t count = ld_relaxed_i32(&ctr->list_size[TAIL ? 0 : 2]);
+    if (count == 0) return;   // nothing parked (the same for every thread)
     int32_t cur = -1;                 // thread 0's chain
-    long long iters = 0;
+    long long iters = 0, scans = 0;
     unsigned long long fails = 0;
     bool aborted = false;
     for (;;) {
         if (threadIdx.x == 0) {
-            if (cur < 0 && !aborted) {
-                const int32_t i = atomicAdd(&ctr->list_size[3], 1);
-                cur = i < count ? w.list1[i] : -1;
-            }
-            if (cur >= 0 && ++iters > w.spin_limit) {   // a bound, not a wait
-                atomicOr(err, ERR_TIMEOUT);
-                cur = -1;
-                aborted = true;
+            // the next search: from the cache while it lasts, else a scan
+            int32_t slot = -1;
+            for (;;) {
+                if (cur < 0 && !aborted) {
+                    const int32_t i = atomicAdd(next_parked, 1);
+                    cur = i < count ? parked[i] : -1;
+                }
+                if (cur < 0) break;
+                if (++iters > w.spin_limit) {   // a bound, not a wait
+                    atomicOr(err, ERR_TIMEOUT);
+                    cur = -1;
+                    aborted = true;
+                    break;
+                }
+                if (!CACHE || KP_LDG(L.xadj + cur + 1) - KP_LDG(L.xadj + cur) <= SUITOR_CACHE_ROW) break;
+                slot = cache_slot(w, count, cur);
+                if (slot < 0) break;
+                const int32_t next = propose_cached<R>(L, w, slot, cur, fails);
+                if (next == -2) break;   // scan the row and refill the cache
+                cur = next;
+                slot = -1;
             }
             s_cur = cur;
+            s_slot = slot;
         }
         __syncthreads();
         const int32_t c = s_cur;
         if (c < 0) break;
+        const int32_t slot = s_slot;
         const int32_t beg = KP_LDG(L.xadj + c), end = KP_LDG(L.xadj + c + 1);
         const int32_t ac = rating_attr<R>(L.vwgt, L.outw, c);
         const HashCtx hc = hash_ctx(w, L, c);
-        Proposal best;
-        scan_row<R, MATCH_BLOCK>(L, w, hc, c, ac, beg + (int32_t)threadIdx.x, end, best);
-        reduce_proposal<32>(0xffffffffu, c, best);
-        if (lane == 0) s_best[warp] = best;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int i = 1; i < NW; i++)
-                if (better(s_best[i].c, best.c, c)) best = s_best[i];
-            cur = propose(w, c, ac, best, fails);
+        scans++;
+        if (CACHE && slot >= 0) {
+            // every thread keeps its two best; SUITOR_CACHE_K rounds of a
+            // block-wide argmax over the threads' next candidates fill the
+            // cache, which ends after a thread's second candidate if that
+            // thread saw more eligible edges than it kept
+            Proposal best;
+            Cached second;
+            int32_t seen;
+            scan_row_top2<R, MATCH_BLOCK>(L, w, hc, c, ac, beg + (int32_t)threadIdx.x, end, best, second, seen);
+            const int32_t kept = min(seen, 2);
+            int32_t idx = 0, filled = 0;
+            for (int k = 0; k < SUITOR_CACHE_K; k++) {
+                Cached h;
+                int32_t last = 0, tid = (int32_t)threadIdx.x;
+                if (idx < kept) {
+                    h.c = idx == 0 ? best.c : second.c;
+                    h.w = idx == 0 ? best.w : second.w;
+                    last = (idx == 1 && seen > 2) ? 1 : 0;
+                } else {
+                    h.c.u = -1;
+                    h.c.num = h.c.den = h.c.h = 0;
+                    h.w = 0;
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    Cached o;
+                    o.c.num = __shfl_xor_sync(0xffffffffu, h.c.num, off);
+                    o.c.den = __shfl_xor_sync(0xffffffffu, h.c.den, off);
+                    o.c.h = __shfl_xor_sync(0xffffffffu, h.c.h, off);
+                    o.c.u = __shfl_xor_sync(0xffffffffu, h.c.u, off);
+                    o.w = __shfl_xor_sync(0xffffffffu, h.w, off);
+                    const int32_t ot = __shfl_xor_sync(0xffffffffu, tid, off);
+                    const int32_t ol = __shfl_xor_sync(0xffffffffu, last, off);
+                    if (better(o.c, h.c, c)) {
+                        h = o;
+                        tid = ot;
+                        last = ol;
+                    }
+                }
+                if (lane == 0) {
+                    s_best[warp].c = h.c;
+                    s_best[warp].w = h.w;
+                    s_tid[warp] = tid;
+                    s_last[warp] = last;
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    for (int i = 1; i < NW; i++)
+                        if (better(s_best[i].c, h.c, c)) {
+                            h.c = s_best[i].c;
+                            h.w = s_best[i].w;
+                            tid = s_tid[i];
+                            last = s_last[i];
+                        }
+                    if (h.c.u >= 0) {
+                        __stcg(w.cache + (int64_t)slot * SUITOR_CACHE_K + k, make_int2(h.c.u, h.w));
+                        filled = k + 1;
+                    }
+                    s_win = h.c.u >= 0 ? tid : -1;
+                    s_stop = (h.c.u < 0 || last) ? 1 : 0;
+                }
+                __syncthreads();
+                if ((int32_t)threadIdx.x == s_win) idx++;
+                if (s_stop) break;
+            }
+            if (threadIdx.x == 0) {
+                __stcg(w.cache_hdr + slot, make_int2(filled, 0));
+                cur = filled > 0 ? c : -1;   // c proposes from its cache next (or stays single)
+            }
+            // s_stop, s_win and s_best are written again only after the
+            // barrier at the top of the next search
+        } else {
+            Proposal best;
+            scan_row<R, MATCH_BLOCK>(L, w, hc, c, ac, beg + (int32_t)threadIdx.x, end, best);
+            reduce_proposal<32>(0xffffffffu, c, best);
+            if (lane == 0) s_best[warp] = best;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int i = 1; i < NW; i++)
+                    if (better(s_best[i].c, best.c, c)) best = s_best[i];
+                cur = propose(w, c, ac, best, fails);
+            }
+            // thread 0 writes s_cur only after the barrier at the top of the
+            // next search, which every thread reaches after it is done with this one
         }
-        // thread 0 writes s_cur only after the barrier at the top of the next
-        // search, which every thread reaches after it is done with this one
     }
     if (threadIdx.x == 0) {
-        atomicAdd(&ctr->searches, (unsigned long long)iters);
+        atomicAdd(&ctr->searches, (unsigned long long)scans);
         if (fails) atomicAdd(&ctr->failed_cas, fails);
     }
 }
 
-// Passes of the proposal scheme on one level.
-enum : int { SUITOR_FIRST = 0, SUITOR_WARP = 1, SUITOR_WIDE = 2 };
+// Passes of the proposal scheme on one level: the first pass, the middle
+// and wide passes over the parked nodes (one cooperative launch, a grid
+// barrier between them), and the wide pass as the persistent tail runs it
+// right after the first.
+enum : int { SUITOR_FIRST = 0, SUITOR_PARKED = 1, SUITOR_WIDE_TAIL = 2 };
 
 template <int R, int PASS>
 __device__ void phase_suitor(DevState *st, int level, const Work &w) {
     const DevLevel L = st->lv[level];
     if (!(L.flags & LV_ACTIVE)) return;
     Counters *ctr = &st->ctr[level];
-    if (PASS == SUITOR_WIDE) {
-        suitor_wide<R>(L, w, ctr, &st->err);
-    } else if (PASS == SUITOR_WARP) {
-        suitor_warp<R>(L, w, ctr, &st->err);
+    if (PASS == SUITOR_WIDE_TAIL) {
+        suitor_wide<R, true>(L, w, ctr, &st->err);
+    } else if (PASS == SUITOR_PARKED) {
+        // the first pass ended with the previous launch: every block sees
+        // the same list sizes; with nothing parked this costs no barrier
+        bool ok = true;
+        if (ld_relaxed_i32(&ctr->list_size[0]) > 0) {
+            suitor_warp<R>(L, w, ctr, &st->err);
+            ok = grid_sync(&ctr->bar, &st->err, w.spin_limit);   // false: err is set, the level stops
+        }
+        if (ok) suitor_wide<R, false>(L, w, ctr, &st->err);
     } else {
         switch (st->suitor_lanes ? st->suitor_lanes : suitor_group(L.n, L.nnz)) {
         case 1: suitor_body<R, 1, 32>(L, w, ctr, &st->err); break;

@@ -121,7 +121,7 @@ namespace {
 // graph, the arena holding the coarse levels and maps, fine partition, gains,
 // targets) and the engine's level-0 scratch, freed when coarsening returns.
 int64_t resident_bytes(int64_t n, int64_t nnz) { return 8 * n + 8 * nnz + 64 * n + 32 * nnz + 16 * n + (1 << 20); }
-int64_t scratch_bytes(int64_t n, int64_t nnz) { return 56 * n + 16 * nnz + (1 << 20); }
+int64_t scratch_bytes(int64_t n, int64_t nnz) { return 60 * n + 17 * nnz + (1 << 20); }
 
 // Stream-ordered frees on the group's stream; the caller does not wait.
 void free_group(ServerGroup *g) {

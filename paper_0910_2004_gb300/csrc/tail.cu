@@ -22,8 +22,10 @@ namespace kp {
 // as one thread-block cluster, whose barrier is the hardware one.
 enum { TAIL_GRID = 0, TAIL_HANDOFF = 1, TAIL_CLUSTER_AFTER = 2, TAIL_CLUSTER = 3 };
 
+// three resident blocks per SM (at most 80 registers): the tail is latency
+// bound, and its grid is sized from the occupancy
 template <int R, bool SUITOR>
-__global__ void __launch_bounds__(MATCH_BLOCK) k_tail(DevState *st, int first, int last, Work w, int32_t epoch0,
+__global__ void __launch_bounds__(MATCH_BLOCK, 3) k_tail(DevState *st, int first, int last, Work w, int32_t epoch0,
                                                       int32_t handoff, int mode) {
     __shared__ OverflowSmem sm;
     GridBarrier *bar = &st->tail_bar;
@@ -51,15 +53,10 @@ __global__ void __launch_bounds__(MATCH_BLOCK) k_tail(DevState *st, int first, i
         if (SUITOR) {
             phase_suitor<R, SUITOR_FIRST>(st, level, w);
             if (!grid_sync(bar, err, lim)) return;
-            // the later passes only when some node was parked for them
-            // (uniform decisions: the passes after a barrier do not write
-            // the size they read)
+            // the wide pass only when some node was parked (a uniform
+            // decision: that pass does not write the size it reads)
             if (ld_relaxed_i32(&st->ctr[level].list_size[0]) > 0) {
-                phase_suitor<R, SUITOR_WARP>(st, level, w);
-                if (!grid_sync(bar, err, lim)) return;
-            }
-            if (ld_relaxed_i32(&st->ctr[level].list_size[2]) > 0) {
-                phase_suitor<R, SUITOR_WIDE>(st, level, w);
+                phase_suitor<R, SUITOR_WIDE_TAIL>(st, level, w);
                 if (!grid_sync(bar, err, lim)) return;
             }
         } else {
@@ -76,7 +73,7 @@ __global__ void __launch_bounds__(MATCH_BLOCK) k_tail(DevState *st, int first, i
             scan_lb_phase(op, w.status, epoch0 + 2 * (level - first) + 1, lim);
         }
         if (!grid_sync(bar, err, lim)) return;
-        phase_contract_small(st, level, w);
+        phase_contract_small(st, level, w, 0);   // no cluster kernel here: long rows stay in class 4
         if (!grid_sync(bar, err, lim)) return;
         phase_contract_overflow<true, true, 2>(st, level, w, sm);
         if (!grid_sync(bar, err, lim)) return;

@@ -289,6 +289,52 @@ def test_power_law_levels_continue_in_spare_arena(tail):
             h.free()
 
 
+def hub_graph(hubs, leaves, seed):
+    """`hubs` nodes joined to every leaf plus a sparse random graph on the
+    leaves, random weights: the hubs compete for the same leaves, so each is
+    displaced many times."""
+    rng = np.random.default_rng(seed)
+    h = np.repeat(np.arange(hubs), leaves)
+    lf = hubs + np.tile(np.arange(leaves), hubs)
+    a = hubs + rng.integers(0, leaves, 3 * leaves)
+    b = hubs + rng.integers(0, leaves, 3 * leaves)
+    pairs = np.unique(np.stack([np.minimum(a, b), np.maximum(a, b)])[:, a != b], axis=1)
+    lo = np.concatenate([h, pairs[0]])
+    hi = np.concatenate([lf, pairs[1]])
+    w = rng.integers(1, 10, len(lo))
+    vw = rng.integers(1, 4, hubs + leaves)
+    return I.from_edges(hubs + leaves, lo, hi, w, vwgt=vw, name=f"hubs{hubs}x{leaves}")
+
+
+@pytest.mark.parametrize("rating", ["expansion*2", "innerOuter", "weight"])
+def test_hub_rows_from_candidate_cache(rating):
+    """Rows far longer than the cache threshold whose nodes are displaced
+    again and again: proposals from the cached candidates reach the same
+    matching as full scans (the oracle), in the per-level kernels."""
+    for hubs, leaves, seed in [(12, 6000, 1), (40, 5000, 2), (3, 20000, 3)]:
+        g = hub_graph(hubs, leaves, seed)
+        assert np.diff(g.xadj).max() > 4096
+        for stop in (20, 2000):
+            h, dg, levels, maps = run_gpu(g, rating=rating, seed=7, stop_size=stop, tail_nodes=-1)
+            assert_same(levels, maps, O.coarsen(g, rating, 7, stop), f"{g.name} {rating} stop={stop}")
+            h.free()
+
+
+@pytest.mark.parametrize("radix_bits", [0, 5, 8])
+def test_huge_rows_by_cluster(radix_bits):
+    """Gathered rows longer than 32768 entries are contracted by a thread-
+    block cluster each (every radix pass split over the cluster's CTAs): the
+    same sorted coarse rows as the oracle, for 1, 2 and more hubs, with the
+    passes of 5 and 8 bits (0: the default)."""
+    kw = dict(radix_bits=radix_bits) if radix_bits else {}
+    for hubs, leaves, seed in [(1, 70000, 4), (2, 40000, 5), (5, 34000, 6)]:
+        g = hub_graph(hubs, leaves, seed)
+        for rating in ("expansion*2", "innerOuter"):
+            h, dg, levels, maps = run_gpu(g, rating=rating, seed=3, stop_size=30, tail_nodes=-1, **kw)
+            assert_same(levels, maps, O.coarsen(g, rating, 3, 30), f"{g.name} {rating} bits={radix_bits}")
+            h.free()
+
+
 def test_stop_rules():
     g = I.grid2d(64, 64)
     for kw in [dict(max_levels=2), dict(max_levels=0), dict(min_shrink_permille=600),
