@@ -91,6 +91,7 @@ kp_status alloc_work(Scratch &sc, Work &w, int32_t n0, int32_t nnz0, const kp_op
     KP_TRY(sc.get(&w.big_adj, nnz0));
     KP_TRY(sc.get(&w.big_w, nnz0));
     for (int c = 1; c <= 4; c++) KP_TRY(sc.get(&w.lists[c], n0));
+    KP_TRY(sc.get(&w.lists[6], n0));
     KP_TRY(sc.get(&w.lists[5], (int64_t)nnz0 / HUGE_ROW + 2));   // each such row holds more than HUGE_ROW entries
     KP_TRY(sc.get(&w.status, scan_tiles(n0) + 1));
     KP_TRY(sc.get(dst, 1));

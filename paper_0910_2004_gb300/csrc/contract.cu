@@ -9,7 +9,7 @@ namespace kp {
 // 4 resident blocks per SM (64 registers) measured best for the small rows
 __global__ void __launch_bounds__(CONTRACT_BLOCK, 4) k_contract_small(DevState *st, int level, Work w,
                                                                        int32_t huge_row) {
-    phase_contract_small(st, level, w, huge_row);
+    phase_contract_small(st, level, w, huge_row, WARP_ROW);
 }
 
 __global__ void __launch_bounds__(CONTRACT_BLOCK) k_contract_rows32(DevState *st, int level, Work w) {

@@ -235,8 +235,10 @@ __device__ __forceinline__ void contract_thread(const CView &p, int32_t x, int32
 
 // Contracts the rows of at most TNET gathered entries and sorts the others
 // into class lists by length; rows of more than huge_row entries (0: none)
-// form class 5, which the caller hands to the cluster kernel.
-static __device__ void phase_contract_small(DevState *st, int level, const Work &w, int32_t huge_row) {
+// form class 5, which the caller hands to the cluster kernel, rows of 129 to
+// warp_row entries (0: none) class 6, for the warp register sort.
+static __device__ void phase_contract_small(DevState *st, int level, const Work &w, int32_t huge_row,
+                                            int32_t warp_row) {
     CView p;
     if (!load_view(st, level, w, p)) return;
     if (w.batch) {   // first coarse node of every graph (the coarse graph ids are sorted)
@@ -264,9 +266,10 @@ static __device__ void phase_contract_small(DevState *st, int level, const Work 
             const int32_t L = da + db;
             cls = L <= TNET ? 0 : L <= 32 ? 1 : L <= 128 ? 2 : L <= p.sort_shared_max ? 3 : 4;
             if (cls == 4 && huge_row > 0 && L > huge_row) cls = 5;
+            if (cls == 3 && L <= warp_row) cls = 6;
         }
 #pragma unroll
-        for (int c = 1; c <= 5; c++) {
+        for (int c = 1; c <= 6; c++) {
             const bool mine = cls == c;
             const unsigned m = __ballot_sync(0xffffffffu, mine);
             if (m) {
@@ -706,6 +709,130 @@ union OverflowSmem {
     BigSmem big;
 };
 
+// Rows of 129..WARP_ROW gathered entries (class 6, levels launched one
+// kernel per phase): one warp, WARP_ROW / 32 entries per lane packed as
+// (map(u) << 32 | omega) in registers, sorted by a bitonic network over the
+// warp (element q = lane * N + i; partners in other lanes by shuffles, no
+// block barrier), then run heads by a warp scan and run sums written by the
+// run's first lane (lanes that continue a run add theirs after a warp
+// barrier).
+constexpr int32_t WARP_ROW = 512;
+
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m) {
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__device__ __forceinline__ void contract_warp_reg(const CView &p, int32_t x) {
+    constexpr int N = WARP_ROW / 32;
+    constexpr uint64_t SENT64 = (uint64_t)SENT << 32;
+    const int lane = threadIdx.x & 31;
+    int32_t xa, da, xb, db;
+    members(p, x, xa, da, xb, db);
+    const int32_t L = da + db;
+    uint64_t r[N];
+    // any placement works before a sort: element i of a lane is entry
+    // i * 32 + lane, so the loads are coalesced
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const int32_t q = i * 32 + lane;
+        uint64_t v = SENT64;
+        if (q < L) {
+            const int32_t e = q < da ? xa + q : xb + (q - da);
+            const int32_t t = p.map[p.adjncy[e]];
+            if (t != x) v = ((uint64_t)(uint32_t)t << 32) | (uint32_t)p.ewgt[e];
+        }
+        r[i] = v;
+    }
+#pragma unroll
+    for (int k = 2; k <= WARP_ROW; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= N) {
+                // partner: the same i in lane ^ (j / N)
+                const bool lower = (lane & (j / N)) == 0;
+                const bool up = ((lane * N) & k) == 0;
+#pragma unroll
+                for (int i = 0; i < N; i++) {
+                    const uint64_t o = shfl_xor_u64(r[i], j / N);
+                    const uint64_t mn = r[i] < o ? r[i] : o, mx = r[i] < o ? o : r[i];
+                    r[i] = (lower == up) ? mn : mx;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < N; i++) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const bool up = ((lane * N + i) & k) == 0;
+                        const uint64_t a = r[i], b = r[l];
+                        const bool sw = up ? (a > b) : (a < b);
+                        r[i] = sw ? b : a;
+                        r[l] = sw ? a : b;
+                    }
+                }
+            }
+        }
+    }
+    // runs: element q = lane * N + i in ascending order, sentinels last
+    const int32_t prev_last = (int32_t)(__shfl_up_sync(0xffffffffu, r[N - 1], 1) >> 32);
+    int32_t heads = 0, total = 0;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const int32_t k = (int32_t)(r[i] >> 32);
+        const int32_t pk = i > 0 ? (int32_t)(r[i - 1] >> 32) : (lane > 0 ? prev_last : -1);
+        heads += (k != SENT && k != pk) ? 1 : 0;
+        total += k != SENT ? (int32_t)(uint32_t)r[i] : 0;
+    }
+    int32_t incl = heads;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    const int32_t runs = __shfl_sync(0xffffffffu, incl, 31);
+    const int32_t o = p.off[x];
+    int32_t run = incl - heads - 1;   // the run in progress where this lane starts
+    int32_t sum = 0;
+    bool mine = false;                // that run started in this lane
+    int32_t lead_run = -1, lead_sum = 0;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+        const int32_t k = (int32_t)(r[i] >> 32);
+        if (k == SENT) continue;
+        const int32_t pk = i > 0 ? (int32_t)(r[i - 1] >> 32) : (lane > 0 ? prev_last : -1);
+        const int32_t wv = (int32_t)(uint32_t)r[i];
+        if (k != pk) {
+            if (mine) {
+                p.tmp_w[o + run] = sum;
+            } else if (i > 0 || sum != 0) {
+                lead_run = run;
+                lead_sum = sum;
+            }
+            run++;
+            mine = true;
+            sum = wv;
+            p.tmp_adj[o + run] = k;
+        } else {
+            sum += wv;
+        }
+    }
+    if (mine) {
+        p.tmp_w[o + run] = sum;
+    } else if (run >= 0 && sum != 0) {
+        lead_run = run;
+        lead_sum = sum;
+    }
+    __syncwarp();   // the first lane of every run has stored its part
+    if (lead_run >= 0) atomicAdd(&p.tmp_w[o + lead_run], lead_sum);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) total += __shfl_xor_sync(0xffffffffu, total, off);
+    if (lane == 0) {
+        p.degp[x] = runs;
+        if (p.outw) p.outw[x] = total;
+    }
+}
+
 // Rows of 17..32 gathered entries (class 1), one thread each with a
 // 32-entry register network: for the separate launches (a warp per such row
 // leaves half the warp idle; the register network needs its own kernel so
@@ -717,14 +844,19 @@ static __device__ void phase_contract_rows32(DevState *st, int level, const Work
     CView p;
     if (!load_view(st, level, w, p)) return;
     const int32_t count = p.ctr->nclass[1];
-    if (count < ROWS32_MIN) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < count; li += stride) {
-        const int32_t x = p.lists[1][li];
-        int32_t xa, da, xb, db;
-        members(p, x, xa, da, xb, db);
-        contract_thread<32>(p, x, xa, da, xb, db);
+    if (count >= ROWS32_MIN) {
+        for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < count; li += stride) {
+            const int32_t x = p.lists[1][li];
+            int32_t xa, da, xb, db;
+            members(p, x, xa, da, xb, db);
+            contract_thread<32>(p, x, xa, da, xb, db);
+        }
     }
+    // class 6: a warp per row (the loop bound is the same for a warp's lanes)
+    const int32_t count6 = p.ctr->nclass[6];
+    for (int64_t li = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; li < count6; li += stride >> 5)
+        contract_warp_reg(p, p.lists[6][li]);
 }
 
 // MID: the classes of up to sort_shared_max entries (warps, blocks in shared
@@ -848,9 +980,9 @@ static __device__ void phase_compact(DevState *st, int level, const Work &w) {
     }
     const int lane = threadIdx.x & 31;
     const int64_t nw = stride >> 5;
-    const int32_t n3 = ctr->nclass[3], n4 = ctr->nclass[4];
-    for (int64_t li = t >> 5; li < n3; li += nw) {
-        const int32_t g = w.lists[3][li];
+    const int32_t n3 = ctr->nclass[3], n4 = ctr->nclass[4], n6 = ctr->nclass[6];
+    for (int64_t li = t >> 5; li < (int64_t)n3 + n6; li += nw) {
+        const int32_t g = li < n3 ? w.lists[3][li] : w.lists[6][li - n3];
         const int32_t o = w.off[g], d = w.degp[g], s = cxadj[g];
         for (int32_t i = lane; i < d; i += 32) {
             cadj[s + i] = w.tmp_adj[o + i];

@@ -50,7 +50,8 @@ struct Counters {   // one per level, zeroed before the level runs
     int32_t rounds;
     int32_t cn;            // coarse node count
     int32_t U;             // sum of coarse row upper bounds
-    int32_t nclass[6];     // overflow lists: [1] <=32, [2] <=128, [3] <=MID_MAX, [4] longer, [5] > huge_row
+    int32_t nclass[7];     // class lists: [1] <=32, [2] <=128, [3] <=MID_MAX, [4] longer, [5] > huge_row,
+                           // [6] 129..warp_row (taken out of [3] where a warp kernel runs)
     int32_t nnz_out;       // coarse entry count
     int32_t tile_counter[2];
     int32_t maxdeg;        // largest coarse degree if it is at least 1024, else 0
@@ -136,7 +137,7 @@ struct Work {
     int32_t *match, *cand, *list0, *list1;
     int32_t *first, *second, *off, *degp;
     int32_t *tmp_adj, *tmp_w, *big_adj, *big_w;
-    int32_t *lists[6];
+    int32_t *lists[7];
     // proposals: candidate caches of the rows searched by the wide pass,
     // one slot per entry of list1 (wslot: node -> slot, checked on use)
     int32_t *wslot;

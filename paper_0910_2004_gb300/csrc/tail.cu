@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(MATCH_BLOCK, 3) k_tail(DevState *st, int first
             scan_lb_phase(op, w.status, epoch0 + 2 * (level - first) + 1, lim);
         }
         if (!grid_sync(bar, err, lim)) return;
-        phase_contract_small(st, level, w, 0);   // no cluster kernel here: long rows stay in class 4
+        // no cluster or warp-sort kernel here: those rows stay in classes 4 and 3
+        phase_contract_small(st, level, w, 0, 0);
         if (!grid_sync(bar, err, lim)) return;
         phase_contract_overflow<true, true, 2>(st, level, w, sm);
         if (!grid_sync(bar, err, lim)) return;
