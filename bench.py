@@ -54,6 +54,12 @@ def workloads():
                  "weights, expansion*2 rating, full hierarchy to <= 20*64 nodes, cut/gain k=64 eps=0.03",
             make=lambda: I.rgg2d(1 << 22, 1), rating="expansion*2", k=64, eps=0.03,
             sample=("the same generator at n=2^20", lambda: I.rgg2d(1 << 20, 1))),
+        "rmat22": dict(
+            desc="R-MAT graph, scale 22 (a=0.57, b=0.19, c=0.19, edge factor 16, self loops dropped, duplicates "
+                 "merged into integer weights; the largest graph of the served mix), unit node weights, expansion*2, "
+                 "hierarchy to <= 20*64 nodes or until a level shrinks by less than 5%, cut/gain k=64 eps=0.03",
+            make=lambda: I.rmat_torch(22, 1022), rating="expansion*2", k=64, eps=0.03,
+            sample=("the same generator at scale 17", lambda: I.rmat(17, 1017))),
         "batch4096": dict(
             desc="batched: 4,096 independent 2D random geometric graphs, n log-uniform in [1k, 64k], mean degree 6, "
                  "integer edge weights uniform in [1,16], expansion*2, each graph coarsened to <= 20*2 nodes in one "

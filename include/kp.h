@@ -421,7 +421,7 @@ kp_status kp_pipeline_host(const kp_graph *g, const kp_options *o, int32_t k, do
  * charged, whatever its size).  Workers kept for small requests take the
  * oldest waiting request of at most batch_max_nodes nodes instead, so small
  * requests do not queue behind large ones.  Footprint while running:
- * 140 n + 56 nnz + 2 MB
+ * 148 n + 57 nnz + 2 MB
  * bytes; while resident: 88 n + 40 nnz + 1 MB.
  * Continuous batching: when a worker takes a request with at most
  * batch_max_nodes nodes, it also takes further waiting requests with at most

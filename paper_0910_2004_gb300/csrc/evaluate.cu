@@ -45,6 +45,7 @@ struct EvalAcc {
 
 constexpr int EVAL_BLOCK = 256;
 constexpr int BW_SMEM = 2048;   // block weights kept in shared memory up to this k
+constexpr int HIST_K = 256;     // warp groups sum a long row's connections in shared memory up to this k
 
 struct CutGainParams {
     int32_t n;
@@ -64,7 +65,11 @@ struct CutGainParams {
 // One G-lane group per node.  The adjacent blocks of v are visited in
 // increasing id order (each step finds the smallest block id above the last
 // one and sums the weight towards it), so the first block reaching the
-// largest connection is the smallest such id.  FROM_LIST: only the rows of
+// largest connection is the smallest such id.  A whole warp (G = 32) with
+// k <= HIST_K instead sums a row longer than the warp into a per-warp
+// shared-memory array of k connections in one pass and takes the largest
+// (smallest id on ties): one pass instead of one per adjacent block, which
+// matters for the hubs of power-law graphs.  FROM_LIST: only the rows of
 // `rows` (count in acc->long_count), without the node weights (the thread
 // kernel has added those for every node).
 template <int G, bool FROM_LIST = false>
@@ -72,6 +77,9 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p, const 
     __shared__ unsigned long long s_bw[BW_SMEM];
     __shared__ unsigned long long s_red[EVAL_BLOCK / 32];
     __shared__ long long s_max[EVAL_BLOCK / 32];
+    constexpr bool HIST = G == 32;
+    __shared__ unsigned long long s_conn[HIST ? EVAL_BLOCK / 32 : 1][HIST ? HIST_K : 1];
+    const bool use_hist = HIST && p.k <= HIST_K;
     const bool smem_bw = p.k <= BW_SMEM;
     if (smem_bw)
         for (int i = threadIdx.x; i < p.k; i += blockDim.x) s_bw[i] = 0;
@@ -101,17 +109,16 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p, const 
                 rb = -1;
             }
         }
-        // pass over the row: internal weight, total weight, smallest other block
         long long inw = 0, tot = 0;
-        int32_t nextb = 0x7fffffff;
-        if (deg <= G) {
-            if (rb >= 0) {
-                tot = rw;
-                if (rb == pv) inw = rw;
-                else nextb = rb;
-            }
-        } else {
-            for (int32_t e = beg + gl; e < end; e += G) {
+        int32_t best = -1;
+        long long best_conn = 0;
+        if (use_hist && deg > G) {
+            // one pass: connection to every block in this warp's bins
+            unsigned long long *conn = s_conn[HIST ? threadIdx.x >> 5 : 0];
+            for (int32_t b = lane; b < p.k; b += 32) conn[b] = 0;
+            __syncwarp();
+#pragma unroll 4
+            for (int32_t e = beg + lane; e < end; e += 32) {
                 const int32_t b = p.part[p.adjncy[e] - p.id_base];
                 const int32_t w = p.ewgt[e];
                 if (b < 0 || b >= p.k) {
@@ -120,40 +127,80 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p, const 
                 }
                 tot += w;
                 if (b == pv) inw += w;
-                else nextb = min(nextb, b);
+                else atomicAdd(&conn[b], (unsigned long long)(long long)w);
             }
-        }
+            __syncwarp();
+            for (int32_t b = lane; b < p.k; b += 32) {   // increasing ids: ties keep the smaller
+                const long long c = (long long)conn[b];
+                if (c > best_conn) {
+                    best_conn = c;
+                    best = b;
+                }
+            }
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            inw += __shfl_xor_sync(gmask, inw, o);
-            tot += __shfl_xor_sync(gmask, tot, o);
-            nextb = min(nextb, __shfl_xor_sync(gmask, nextb, o));
-        }
-        int32_t best = -1;
-        long long best_conn = 0;
-        while (nextb != 0x7fffffff) {
-            const int32_t cur = nextb;
-            long long conn = 0;
-            nextb = 0x7fffffff;
+            for (int o = 16; o > 0; o >>= 1) {
+                inw += __shfl_xor_sync(0xffffffffu, inw, o);
+                tot += __shfl_xor_sync(0xffffffffu, tot, o);
+                const long long oc = __shfl_xor_sync(0xffffffffu, best_conn, o);
+                const int32_t ob = __shfl_xor_sync(0xffffffffu, best, o);
+                if (oc > best_conn || (oc == best_conn && oc > 0 && ob < best)) {
+                    best_conn = oc;
+                    best = ob;
+                }
+            }
+            __syncwarp();   // every lane has read the bins before the next row clears them
+        } else {
+            // pass over the row: internal weight, total weight, smallest other block
+            int32_t nextb = 0x7fffffff;
             if (deg <= G) {
-                if (rb == cur) conn = rw;
-                else if (rb > cur && rb != pv) nextb = rb;
+                if (rb >= 0) {
+                    tot = rw;
+                    if (rb == pv) inw = rw;
+                    else nextb = rb;
+                }
             } else {
                 for (int32_t e = beg + gl; e < end; e += G) {
                     const int32_t b = p.part[p.adjncy[e] - p.id_base];
-                    if (b < 0 || b >= p.k) continue;
-                    if (b == cur) conn += p.ewgt[e];
-                    else if (b > cur && b != pv) nextb = min(nextb, b);
+                    const int32_t w = p.ewgt[e];
+                    if (b < 0 || b >= p.k) {
+                        bad = 1;
+                        continue;
+                    }
+                    tot += w;
+                    if (b == pv) inw += w;
+                    else nextb = min(nextb, b);
                 }
             }
 #pragma unroll
             for (int o = G / 2; o > 0; o >>= 1) {
-                conn += __shfl_xor_sync(gmask, conn, o);
+                inw += __shfl_xor_sync(gmask, inw, o);
+                tot += __shfl_xor_sync(gmask, tot, o);
                 nextb = min(nextb, __shfl_xor_sync(gmask, nextb, o));
             }
-            if (conn > best_conn) {
-                best_conn = conn;
-                best = cur;
+            while (nextb != 0x7fffffff) {
+                const int32_t cur = nextb;
+                long long conn = 0;
+                nextb = 0x7fffffff;
+                if (deg <= G) {
+                    if (rb == cur) conn = rw;
+                    else if (rb > cur && rb != pv) nextb = rb;
+                } else {
+                    for (int32_t e = beg + gl; e < end; e += G) {
+                        const int32_t b = p.part[p.adjncy[e] - p.id_base];
+                        if (b < 0 || b >= p.k) continue;
+                        if (b == cur) conn += p.ewgt[e];
+                        else if (b > cur && b != pv) nextb = min(nextb, b);
+                    }
+                }
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) {
+                    conn += __shfl_xor_sync(gmask, conn, o);
+                    nextb = min(nextb, __shfl_xor_sync(gmask, nextb, o));
+                }
+                if (conn > best_conn) {
+                    best_conn = conn;
+                    best = cur;
+                }
             }
         }
         if (gl == 0) {

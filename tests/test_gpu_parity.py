@@ -362,6 +362,18 @@ def test_cut_gain_many_k():
         check_eval(dg, g, np.zeros(g.n, np.int32), 1, 0.0)
 
 
+def test_cut_gain_hub_rows():
+    """Rows far longer than a warp: with k <= 256 a warp sums the row's
+    connections in shared memory in one pass, above that it visits the
+    adjacent blocks one by one; both give the oracle's gains and targets
+    (largest connection, smallest block id on ties)."""
+    for g in [I.rmat(13, 6), hub_graph(3, 20000, 3), hub_graph(40, 5000, 2)]:
+        dg = B().DeviceGraph.from_csr(g)
+        for k in [2, 64, 256, 257]:
+            check_eval(dg, g, I.random_partition(g.n, k, seed=k), k, 0.03)
+            check_eval(dg, g, I.random_balanced_partition(g.n, k, seed=k + 5), k, 0.1)
+
+
 def test_cut_gain_closed_form_grid():
     g = I.grid2d(64, 64)
     dg = B().DeviceGraph.from_csr(g)
