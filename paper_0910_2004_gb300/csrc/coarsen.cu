@@ -48,15 +48,19 @@ struct HostMirror {
     DevState *state = nullptr;
     LevelSnap *snap = nullptr;
     LevelSnap *snap_dev = nullptr;
+    int32_t *deg0 = nullptr, *deg0_dev = nullptr;   // the input's largest degree + 1 (0: not yet)
     HostMirror() {
         if (cudaMallocHost((void **)&state, sizeof(DevState)) != cudaSuccess) state = nullptr;
         if (cudaHostAlloc((void **)&snap, sizeof(LevelSnap) * MAX_LEVELS, cudaHostAllocMapped) != cudaSuccess)
             snap = nullptr;
         if (snap && cudaHostGetDevicePointer((void **)&snap_dev, snap, 0) != cudaSuccess) snap_dev = nullptr;
+        if (cudaHostAlloc((void **)&deg0, sizeof(int32_t), cudaHostAllocMapped) != cudaSuccess) deg0 = nullptr;
+        if (deg0 && cudaHostGetDevicePointer((void **)&deg0_dev, deg0, 0) != cudaSuccess) deg0_dev = nullptr;
     }
     ~HostMirror() {
         if (state) cudaFreeHost(state);
         if (snap) cudaFreeHost(snap);
+        if (deg0) cudaFreeHost(deg0);
     }
 };
 
@@ -334,7 +338,10 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         return fail(cuda_error(cudaGetLastError(), "clear scan status"));
 
     thread_local HostMirror mirror;
-    if (!mirror.state || !mirror.snap || !mirror.snap_dev) return fail(set_error(KP_ERR_OOM, "pinned host state"));
+    if (!mirror.state || !mirror.snap || !mirror.snap_dev || !mirror.deg0_dev)
+        return fail(set_error(KP_ERR_OOM, "pinned host state"));
+    *(volatile int32_t *)mirror.deg0 = 0;
+    w.deg0_host = mirror.deg0_dev;
     DevState *hs = mirror.state;
     LevelSnap *snap = mirror.snap;
 
@@ -408,7 +415,16 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
             LL.n_bound = n_bound;
             LL.nnz_bound = nnz_bound;
             // a coarse degree is at most twice the largest of the level
-            // before, and a gathered row holds the degrees of two nodes
+            // before, and a gathered row holds the degrees of two nodes; the
+            // input's largest degree arrives from level 0's start (read
+            // without waiting: until then the kernel is launched)
+            if (deg_level < 0) {
+                const int32_t d0 = *(volatile int32_t *)mirror.deg0;
+                if (d0 > 0) {
+                    deg_level = 0;
+                    deg_max = d0 - 1;
+                }
+            }
             LL.huge = deg_level < 0 || level - deg_level > 20 ||
                       2 * (deg_max << (level - deg_level)) > (int64_t)HUGE_ROW;
             LL.epoch_relabel = ++epoch;

@@ -410,7 +410,10 @@ kp_status launch_contract(const LevelLaunch &L, cudaStream_t s, int32_t *launche
     // rows of more than HUGE_ROW entries get their own class only when the
     // cluster kernel runs for this level (else they stay with the radix class)
     const HugeLaunch &hl = huge_launch();
-    const bool huge = L.huge && hl.cluster > 0;
+    // a level of at most HUGE_ROW entries has no such row; else at most
+    // nnz / HUGE_ROW of them, one cluster each
+    const int64_t most = L.nnz_bound / HUGE_ROW;
+    const bool huge = L.huge && hl.cluster > 0 && most > 0;
     k_contract_small<<<grid, CONTRACT_BLOCK, 0, s>>>(L.st, L.level, L.w, huge ? HUGE_ROW : 0);
     // rows of 17..32 entries: one thread each when there are many of them
     // (decided on the device from the class count), else a warp each
@@ -425,7 +428,7 @@ kp_status launch_contract(const LevelLaunch &L, cudaStream_t s, int32_t *launche
         attr[0].val.clusterDim.x = hl.cluster;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3(hl.cluster * hl.clusters);
+        cfg.gridDim = dim3(hl.cluster * (int)std::min<int64_t>(hl.clusters, most));
         cfg.blockDim = dim3(CONTRACT_BLOCK);
         cfg.stream = s;
         cfg.attrs = attr;

@@ -98,6 +98,8 @@ struct DevState {
     int32_t radix_bits;        // bits per radix pass (4..8)
     int32_t tail_resume;       // first level left to the cluster tail (-1: none)
     int32_t arena_gen;         // spare chunks taken so far
+    int32_t maxdeg0;           // the input's largest degree (level 0's start)
+    int32_t maxdeg0_warps;     // warps that have added theirs
     LevelSnap *snap;    // host-mapped, one per level
     GridBarrier tail_bar;
 };
@@ -144,6 +146,9 @@ struct Work {
     int2 *cache;       // SUITOR_CACHE_K candidates {node, edge weight} per slot
     int2 *cache_hdr;   // per slot {candidates kept, next to try}
     int32_t cache_slots;
+    // the input's largest degree + 1, written by level 0's start into mapped
+    // host memory (null: not wanted)
+    int32_t *deg0_host;
     TileStatus *status;
     uint64_t seed;
     long long spin_limit;

@@ -43,21 +43,18 @@ kp_status launch_matching_r(const LevelLaunch &L, cudaStream_t s, int32_t *launc
     const int grid1 = (int)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, (int64_t)sms * 8));
     if (L.matcher == KP_MATCHER_SUITOR) {
         static const int occ = occupancy_of(k_suitor<R, SUITOR_FIRST>, MATCH_BLOCK);
-        static const int occ_parked = occupancy_of(k_suitor<R, SUITOR_PARKED>, MATCH_BLOCK);
+        static const int occ_warp = occupancy_of(k_suitor<R, SUITOR_WARP>, MATCH_BLOCK);
+        static const int occ_wide = occupancy_of(k_suitor<R, SUITOR_WIDE>, MATCH_BLOCK);
         // at least 32 start nodes per warp, at most the blocks that fit at once
         const int64_t want = (nb + 32 * (MATCH_BLOCK / 32) - 1) / (32 * (MATCH_BLOCK / 32));
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want * 4, (int64_t)occ * sms));
         k_level_begin<R, true><<<grid1, 256, 0, s>>>(L.st, L.level, L.w);
         k_suitor<R, SUITOR_FIRST><<<grid, MATCH_BLOCK, 0, s>>>(L.st, L.level, L.w);
-        // the passes over parked nodes wait on each other at a grid barrier:
-        // a cooperative launch of the blocks that fit at once
-        DevState *st = L.st;
-        int level = L.level;
-        Work w = L.w;
-        void *args[] = {&st, &level, &w};
-        KP_CUDA(cudaLaunchCooperativeKernel((const void *)k_suitor<R, SUITOR_PARKED>, dim3(occ_parked * sms),
-                                            dim3(MATCH_BLOCK), args, 0, s));
-        *launches += 3;
+        // the passes over parked nodes (they return at once when nothing is
+        // parked); ordinary launches, so other streams' kernels run beside them
+        k_suitor<R, SUITOR_WARP><<<occ_warp * sms, MATCH_BLOCK, 0, s>>>(L.st, L.level, L.w);
+        k_suitor<R, SUITOR_WIDE><<<occ_wide * sms, MATCH_BLOCK, 0, s>>>(L.st, L.level, L.w);
+        *launches += 4;
     } else {
         static const int occ = occupancy_of(k_match<R>, MATCH_BLOCK);
         const int64_t want = (nb * 8 + MATCH_BLOCK - 1) / MATCH_BLOCK;

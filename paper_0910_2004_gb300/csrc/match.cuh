@@ -67,6 +67,21 @@ __device__ void phase_level_begin(DevState *st, int level, const Work &w) {
         }
     }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (level == 0 && w.deg0_host) {
+        // the input's largest degree for the host (which contraction kernels
+        // to launch); the last warp to add its part writes it
+        int32_t d = 0;
+        for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < L.n; v += stride)
+            d = max(d, L.xadj[v + 1] - L.xadj[v]);
+        d = __reduce_max_sync(0xffffffffu, d);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMax(&st->maxdeg0, d);
+            __threadfence();
+            const int32_t warps = (int32_t)((stride + 31) >> 5);
+            if (atomicAdd(&st->maxdeg0_warps, 1) == warps - 1)
+                *(volatile int32_t *)w.deg0_host = atomicMax(&st->maxdeg0, 0) + 1;
+        }
+    }
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < L.n; v += stride) {
         if (SUITOR) {
             Offer o;
@@ -575,11 +590,11 @@ __device__ __forceinline__ void suitor_wide(const DevLevel &L, const Work &w, Co
     }
 }
 
-// Passes of the proposal scheme on one level: the first pass, the middle
-// and wide passes over the parked nodes (one cooperative launch, a grid
-// barrier between them), and the wide pass as the persistent tail runs it
-// right after the first.
-enum : int { SUITOR_FIRST = 0, SUITOR_PARKED = 1, SUITOR_WIDE_TAIL = 2 };
+// Passes of the proposal scheme on one level: the first, middle and wide
+// passes (ordinary launches, so that the kernels of other streams keep
+// running beside them: a server runs several hierarchies at once), and the
+// wide pass as the persistent tail runs it right after the first.
+enum : int { SUITOR_FIRST = 0, SUITOR_WARP = 1, SUITOR_WIDE = 2, SUITOR_WIDE_TAIL = 3 };
 
 template <int R, int PASS>
 __device__ void phase_suitor(DevState *st, int level, const Work &w) {
@@ -588,15 +603,10 @@ __device__ void phase_suitor(DevState *st, int level, const Work &w) {
     Counters *ctr = &st->ctr[level];
     if (PASS == SUITOR_WIDE_TAIL) {
         suitor_wide<R, true>(L, w, ctr, &st->err);
-    } else if (PASS == SUITOR_PARKED) {
-        // the first pass ended with the previous launch: every block sees
-        // the same list sizes; with nothing parked this costs no barrier
-        bool ok = true;
-        if (ld_relaxed_i32(&ctr->list_size[0]) > 0) {
-            suitor_warp<R>(L, w, ctr, &st->err);
-            ok = grid_sync(&ctr->bar, &st->err, w.spin_limit);   // false: err is set, the level stops
-        }
-        if (ok) suitor_wide<R, false>(L, w, ctr, &st->err);
+    } else if (PASS == SUITOR_WARP) {
+        suitor_warp<R>(L, w, ctr, &st->err);
+    } else if (PASS == SUITOR_WIDE) {
+        suitor_wide<R, false>(L, w, ctr, &st->err);
     } else {
         switch (st->suitor_lanes ? st->suitor_lanes : suitor_group(L.n, L.nnz)) {
         case 1: suitor_body<R, 1, 32>(L, w, ctr, &st->err); break;
