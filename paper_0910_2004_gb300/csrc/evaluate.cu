@@ -46,6 +46,8 @@ struct EvalAcc {
 constexpr int EVAL_BLOCK = 256;
 constexpr int BW_SMEM = 2048;   // block weights kept in shared memory up to this k
 constexpr int HIST_K = 256;     // warp groups sum a long row's connections in shared memory up to this k
+constexpr int HUB_ROW = 4096;   // longer rows (k <= HIST_K) go to a block each (k_cut_gain_hubs)
+constexpr int HUB_BLOCK = 512;
 
 struct CutGainParams {
     int32_t n;
@@ -60,6 +62,11 @@ struct CutGainParams {
     int64_t *gain;
     int32_t *target;
     EvalAcc *acc;
+    // G = 32 kernels with k <= HIST_K: leave rows of more than HUB_ROW
+    // entries to k_cut_gain_hubs (the list kernel skips them in its list,
+    // the per-node kernel appends them to hub_list)
+    int32_t hub_defer = 0;
+    int32_t *hub_list = nullptr;
 };
 
 // One G-lane group per node.  The adjacent blocks of v are visited in
@@ -112,7 +119,11 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p, const 
         long long inw = 0, tot = 0;
         int32_t best = -1;
         long long best_conn = 0;
-        if (use_hist && deg > G) {
+        // a hub left to the block kernel (its node weight is still added below)
+        const bool defer = HIST && use_hist && p.hub_defer && deg > HUB_ROW;
+        if (defer) {
+            if (!FROM_LIST && gl == 0) p.hub_list[atomicAdd(&p.acc->long_count, 1)] = (int32_t)v;
+        } else if (use_hist && deg > G) {
             // one pass: connection to every block in this warp's bins
             unsigned long long *conn = s_conn[HIST ? threadIdx.x >> 5 : 0];
             for (int32_t b = lane; b < p.k; b += 32) conn[b] = 0;
@@ -203,7 +214,7 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p, const 
                 }
             }
         }
-        if (gl == 0) {
+        if (gl == 0 && !defer) {
             p.gain[v] = (best >= 0 ? best_conn : 0) - inw;
             p.target[v] = best;
             ext_acc += (unsigned long long)(tot - inw);
@@ -256,6 +267,90 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p, const 
     if (smem_bw)
         for (int i = threadIdx.x; i < p.k; i += blockDim.x)
             if (s_bw[i]) atomicAdd(&p.block_w[i], s_bw[i]);
+}
+
+// Rows of more than HUB_ROW entries (hubs of power-law graphs), one block
+// each, k <= HIST_K: all threads sum the row's connection to every block in
+// shared memory in one pass and the largest is taken (smallest block id on
+// ties).  The G = 32 kernels leave these rows to it (their node weights
+// stay there); the rows are those of `rows` [0, acc->long_count) with more
+// than HUB_ROW entries.
+__global__ void __launch_bounds__(HUB_BLOCK) k_cut_gain_hubs(CutGainParams p, const int32_t *rows) {
+    constexpr int NW = HUB_BLOCK / 32;
+    __shared__ unsigned long long conn[HIST_K];
+    __shared__ long long s_in[NW], s_tot[NW], s_bc[NW];
+    __shared__ int32_t s_bb[NW];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t count = *(volatile int32_t *)&p.acc->long_count;
+    unsigned long long ext = 0;
+    int32_t bad = 0;
+    for (int32_t li = blockIdx.x; li < count; li += gridDim.x) {
+        const int32_t v = rows[li];
+        const int32_t beg = p.xadj[v], end = p.xadj[v + 1];
+        if (end - beg <= HUB_ROW) continue;   // the same for the whole block
+        const int32_t pv = p.part[v];
+        for (int32_t b = threadIdx.x; b < p.k; b += HUB_BLOCK) conn[b] = 0;
+        __syncthreads();
+        long long inw = 0, tot = 0;
+#pragma unroll 4
+        for (int32_t e = beg + (int32_t)threadIdx.x; e < end; e += HUB_BLOCK) {
+            const int32_t b = p.part[p.adjncy[e] - p.id_base];
+            const int32_t w = p.ewgt[e];
+            if (b < 0 || b >= p.k) {
+                bad = 1;
+                continue;
+            }
+            tot += w;
+            if (b == pv) inw += w;
+            else atomicAdd(&conn[b], (unsigned long long)(long long)w);
+        }
+        __syncthreads();
+        long long bc = 0;
+        int32_t bb = -1;
+        for (int32_t b = threadIdx.x; b < p.k; b += HUB_BLOCK) {   // increasing ids: ties keep the smaller
+            const long long c = (long long)conn[b];
+            if (c > bc) {
+                bc = c;
+                bb = b;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            inw += __shfl_xor_sync(0xffffffffu, inw, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            const long long oc = __shfl_xor_sync(0xffffffffu, bc, o);
+            const int32_t ob = __shfl_xor_sync(0xffffffffu, bb, o);
+            if (oc > bc || (oc == bc && oc > 0 && ob < bb)) {
+                bc = oc;
+                bb = ob;
+            }
+        }
+        if (lane == 0) {
+            s_in[warp] = inw;
+            s_tot[warp] = tot;
+            s_bc[warp] = bc;
+            s_bb[warp] = bb;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long in_all = 0, tot_all = 0, c = 0;
+            int32_t t = -1;
+            for (int i = 0; i < NW; i++) {
+                in_all += s_in[i];
+                tot_all += s_tot[i];
+                if (s_bc[i] > c || (s_bc[i] == c && c > 0 && s_bb[i] < t)) {
+                    c = s_bc[i];
+                    t = s_bb[i];
+                }
+            }
+            p.gain[v] = (t >= 0 ? c : 0) - in_all;
+            p.target[v] = t;
+            ext += (unsigned long long)(tot_all - in_all);
+        }
+        __syncthreads();   // the bins and partial sums are read before the next row
+    }
+    if (threadIdx.x == 0 && ext) atomicAdd(&p.acc->ext_sum, ext);
+    if (bad) atomicOr(&p.acc->err, ERR_BAD_PART);
 }
 
 // One thread per node for rows of at most EVAL_TROW entries (the row is read
@@ -467,6 +562,11 @@ kp_status cut_gain_with(const kp_graph *g, const int32_t *part, int32_t k, doubl
             const int64_t want = ((int64_t)g->n * G + EVAL_BLOCK - 1) / EVAL_BLOCK;
             return (int)std::max<int64_t>(1, std::min<int64_t>(want, grid_cap));
         };
+        // hub rows by a block each when a row list is at hand (the G = 32
+        // kernels below leave them to k_cut_gain_hubs)
+        const bool hubs = long_rows && k <= HIST_K && (avg <= 12.0 || avg > 20.0);
+        p.hub_defer = hubs ? 1 : 0;
+        p.hub_list = long_rows;
         if (long_rows && avg <= 12.0) {
             // rows of up to 16 entries one thread each, the longer ones listed
             // for one warp each
@@ -484,6 +584,7 @@ kp_status cut_gain_with(const kp_graph *g, const int32_t *part, int32_t k, doubl
             k_cut_gain<32><<<grid_for(32), EVAL_BLOCK, 0, s>>>(p);
         }
         KP_CUDA(cudaGetLastError());
+        if (hubs) k_cut_gain_hubs<<<num_sms() * 2, HUB_BLOCK, 0, s>>>(p, long_rows);
         k_max_block<<<1, 1024, 0, s>>>(k, reinterpret_cast<const long long *>(out->block_w), acc);
         KP_CUDA(cudaGetLastError());
     }
