@@ -16,7 +16,10 @@ namespace kp {
 // ---------------------------------------------------------------------------
 // level begin: carve map_l and c of level l+1, reset the per-node state
 // ---------------------------------------------------------------------------
-template <int R, bool SUITOR>
+// DEG0: the separately launched form, which also reports the input's
+// largest degree at level 0 (the persistent tail launches nothing the
+// degree could decide).
+template <int R, bool SUITOR, bool DEG0 = false>
 __device__ void phase_level_begin(DevState *st, int level, const Work &w) {
     const DevLevel L = st->lv[level];
     if (!(L.flags & LV_ACTIVE)) return;
@@ -67,7 +70,7 @@ __device__ void phase_level_begin(DevState *st, int level, const Work &w) {
         }
     }
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    if (level == 0 && w.deg0_host) {
+    if (DEG0 && level == 0 && w.deg0_host) {
         // the input's largest degree for the host (which contraction kernels
         // to launch); the last warp to add its part writes it
         int32_t d = 0;
@@ -781,7 +784,7 @@ __device__ bool phase_handshake(DevState *st, int level, const Work &w) {
 // ---------------------------------------------------------------------------
 template <int R, bool SUITOR>
 __global__ void k_level_begin(DevState *st, int level, Work w) {
-    phase_level_begin<R, SUITOR>(st, level, w);
+    phase_level_begin<R, SUITOR, true>(st, level, w);
 }
 
 template <int R, int PASS>
