@@ -114,21 +114,28 @@ typedef enum {
  *   matcher              a kp_matcher: how the matching of each level is
  *                        found; both give the same unique matching
  *   arena_bytes          initial size of the device arena that holds the
- *                        coarse levels (0: sized from the input); the
- *                        arena grows automatically when a level does not fit
+ *                        coarse levels (0: sized from the input); further
+ *                        chunks are added ahead of need when the levels
+ *                        shrink slowly, and the arena grows (the level is
+ *                        redone) when a level still does not fit
  *   tail_nodes           levels with at most this many nodes and at most 8
  *                        times as many directed edges are contracted
  *                        together in one persistent launch (0: 262144;
  *                        -1: never; 2^31-1: the whole hierarchy)
  * Tuning knobs (0: the built-in choice; results never depend on them, only
  * the time does -- kp_autotune picks them by measurement):
- *   suitor_lanes         lanes per proposing node in the Suitor pass: 1, 4,
- *                        8 or 32 (0: from the level's mean degree)
+ *   suitor_lanes         lanes per proposing node in the first Suitor pass:
+ *                        1, 4, 8 or 32 (0: from the level's mean degree);
+ *                        longer rows go to a warp (up to 1024 entries) or
+ *                        a block each
  *   tail_block_nodes     nodes per block of the persistent tail launch,
  *                        256..16384 (0: 2048)
  *   sort_shared_max      coarse rows of up to this many gathered entries are
- *                        sorted by one block in shared memory, longer ones by
- *                        the radix path, 128..2048 (0: 2048)
+ *                        sorted by one block in shared memory (rows of 129
+ *                        to 512 by one warp in registers when the level is
+ *                        launched phase by phase), longer ones by the radix
+ *                        path (rows above 32768 entries by a thread-block
+ *                        cluster each), 128..2048 (0: 2048)
  *   radix_bits           bits per pass of the radix path, 4..8 (0: 8)
  *   cluster_nodes        tail levels with at most this many nodes run in one
  *                        thread-block cluster (16 CTAs, or 8) whose phases
