@@ -474,8 +474,10 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
                                                          8ull * (unsigned long long)sn->nnz +
                                                          4ull * (unsigned long long)(G + 1) + 8192ull;
                     if (sn->room < (LOOKAHEAD + 2) * per_level) {
+                        // room for a few more levels of this size (each one
+                        // reservation fits it, so no level restarts for it)
                         const unsigned long long cap =
-                            align256(std::max<unsigned long long>(arena_cap, 4ull * (LOOKAHEAD + 2) * per_level));
+                            align256(std::max<unsigned long long>(arena_cap, (LOOKAHEAD + 4) * per_level));
                         char *chunk = nullptr;
                         st = dev_alloc((void **)&chunk, cap, s);
                         if (st != KP_OK) return bail(st);
