@@ -8,7 +8,7 @@ partitioning), project it back to the input, and evaluate cut, block weights
 and gains.  The metric is coarsened input edges per second (m_0 undirected
 edges per step / step time), aggregated over all ranks.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rgg20]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload grid256]
   python bench.py --impl reference ...   (the CPU oracle, timed on the host)
 
 Multi-GPU (torchrun): every rank coarsens its own replica of the workload
@@ -36,10 +36,11 @@ from paper_0910_2004_gb300 import inputs as I  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 
-# DRAM bytes (read + write) of one launch of a workload's dominant kernel,
-# from one ncu capture of this build (profiles/k_tail_rgg20.md); a kernel
-# without an entry reports traffic null.
-NCU_TRAFFIC = {("rgg20", "tail"): 3_726_592 + 264_960}
+# DRAM bytes (read + write) per step of a workload's dominant phase, from ncu
+# captures of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum
+# summed over the phase's launches); a phase without an entry reports traffic
+# null.  The summaries under profiles/ give the commands and the scaling.
+NCU_TRAFFIC = {}
 HBM_PEAK_FALLBACK = 6800.0
 
 
@@ -78,6 +79,11 @@ def workloads():
             desc="3D 7-point grid 256^3, unit weights, innerOuter, full hierarchy to <= 20*256 nodes, "
                  "cut/gain k=256 eps=0.03",
             make=lambda: I.grid3d(256, 256, 256), rating="innerOuter", k=256, eps=0.03,
+            sample=("the same generator at 64^3", lambda: I.grid3d(64, 64, 64))),
+        "grid256h": dict(
+            desc="3D 7-point grid 256x256x128 (half of the 256^3 grid, for counter captures that must stay a few GB), "
+                 "unit weights, innerOuter, full hierarchy to <= 20*256 nodes, cut/gain k=256 eps=0.03",
+            make=lambda: I.grid3d(256, 256, 128), rating="innerOuter", k=256, eps=0.03,
             sample=("the same generator at 64^3", lambda: I.grid3d(64, 64, 64))),
     }
 
@@ -221,7 +227,8 @@ def run_reference(args, wl, g):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": wl["desc"], "n": g.n, "m": g.m},
+        "config": {"workload": args.workload, "desc": wl["desc"]},
+        "graph": {"n": g.n, "m": g.m, "of": what},
         "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
                          "sample": f"{what} per step ({args.steps} steps), single-threaded C/numpy oracle"},
         "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -239,7 +246,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rgg20", choices=sorted(workloads()))
+    ap.add_argument("--workload", default="grid256", choices=sorted(workloads()))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--matcher", default="suitor", choices=["suitor", "handshake"])
@@ -450,10 +457,11 @@ def main():
         "value": value, "unit": "edges/s", "n_gpus": world, "steps": steps, "warmup": max(args.warmup, 3),
         "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": wl["desc"], "n": g.n, "m": g.m, "levels": len(sizes),
-                   "coarsest_n": sizes[-1][0], "level_n": [s[0] for s in sizes],
-                   "l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}",
-                   "matcher": args.matcher, "input_check": "once before timing (kp_options.validate=0 in timed steps)"},
+        "config": {"workload": args.workload, "desc": wl["desc"]},
+        "graph": {"n": g.n, "m": g.m, "levels": len(sizes), "coarsest_n": sizes[-1][0],
+                  "level_n": [s[0] for s in sizes]},
+        "run": {"l2": "flushed (512 MB write) before every timed step", "parallelism": f"replicas x{world}",
+                "matcher": args.matcher, "input_check": "once before timing (kp_options.validate=0 in timed steps)"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": NCU_TRAFFIC.get((args.workload, dom)),
@@ -526,7 +534,8 @@ def run_batch(args, wl):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * sum(times) / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"], "graphs": G},
+            "config": {"workload": args.workload, "desc": wl["desc"]},
+            "graph": {"graphs": G},
             "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
                              "sample": f"{len(sample)} of the {G} graphs per step, single-threaded oracle"},
             "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
@@ -703,9 +712,10 @@ def run_batch(args, wl):
         "value": world * m * steps / (total_ms / 1000.0), "unit": "edges/s", "n_gpus": world, "steps": steps,
         "warmup": max(args.warmup, 3), "ms_per_step": total_ms / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": wl["desc"], "graphs": G, "n": n, "m": m,
-                   "union_levels": len(level_profile) + 1, "l2": "inputs larger than L2; also flushed",
-                   "matcher": args.matcher, "parallelism": f"replicas x{world}"},
+        "config": {"workload": args.workload, "desc": wl["desc"]},
+        "graph": {"graphs": G, "n": n, "m": m, "union_levels": len(level_profile) + 1},
+        "run": {"l2": "inputs larger than L2; also flushed", "matcher": args.matcher,
+                "parallelism": f"replicas x{world}"},
         "coarsen_only": {"recorded_plan_edges_per_s": m * steps / (sum(coarsen_ms) / 1000.0),
                          "recorded_plan_ms": coarsen_ms_avg,
                          "unrecorded_call_edges_per_s": m / (min(plain_ms) / 1000.0),
@@ -961,8 +971,8 @@ def run_served(args, wl):
         "value": loads[0.9]["edges_per_s"], "unit": "edges/s", "n_gpus": world, "steps": R,
         "warmup": max(1, min(args.warmup, 2)), "ms_per_step": 1000.0 * loads[0.9]["span_s"] / R,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": wl["desc"], "pool_graphs": len(pool),
-                   "requests_per_phase": R, "workers": args.workers, "small_workers": args.small_workers,
+        "config": {"workload": args.workload, "desc": wl["desc"]},
+        "run": {"pool_graphs": len(pool), "requests_per_phase": R, "workers": args.workers, "small_workers": args.small_workers,
                    "max_batch": 64,
                    "host_arrays": "pageable numpy arrays of the pool, borrowed by the server (KP_REQUEST_BORROW: "
                                   "read by the worker's host-to-device copy, no copy at submit)",

@@ -135,20 +135,42 @@ extern "C" kp_status kp_hierarchy_load(const char *path, kp_stream stream, kp_hi
         bool ok = H.xadj[0] == 0 && H.xadj[(size_t)H.n] == H.nnz;
         for (int32_t v = 0; ok && v < H.n; v++) ok = H.xadj[(size_t)v] <= H.xadj[(size_t)v + 1];
         for (int32_t e = 0; ok && e < H.nnz; e++) ok = H.adjncy[(size_t)e] >= 0 && H.adjncy[(size_t)e] < H.n;
-        if (l < L - 1) {
-            const int32_t n2 = lv[(size_t)l + 1].n;
-            for (int32_t v = 0; ok && v < H.n; v++) ok = H.map[(size_t)v] >= -1 && H.map[(size_t)v] < n2;
-        }
         if (G > 0) {
             ok = ok && H.goff[0] == 0 && H.goff[(size_t)G] == H.n;
             for (int32_t g = 0; ok && g < G; g++) ok = H.goff[(size_t)g] <= H.goff[(size_t)g + 1];
+        } else if (l < L - 1) {
+            // one graph: every node is carried to the next level
+            const int32_t n2 = lv[(size_t)l + 1].n;
+            for (int32_t v = 0; ok && v < H.n; v++) ok = H.map[(size_t)v] >= 0 && H.map[(size_t)v] < n2;
         }
         if (!ok) return set_error(KP_ERR_INVALID, "inconsistent level in hierarchy file");
     }
     for (int32_t v : glevels)
         if (v < 1 || v > L) return set_error(KP_ERR_INVALID, "bad graph level count in hierarchy file");
-    for (int32_t g : gid0)
-        if (g < 0 || g >= G) return set_error(KP_ERR_INVALID, "bad graph id in hierarchy file");
+    if (G > 0) {
+        // the projection follows a node's maps inside its own graph: the
+        // input node of graph g lies in g's range of level 0 and carries g's
+        // id; on every level before g's coarsest, g's nodes map into g's range
+        // of the next level.  On g's coarsest and later levels a map is never
+        // followed: -1 (not carried), or into g's range (the copy a level that
+        // matched nothing leaves behind)
+        for (int32_t g = 0; g < G; g++)
+            for (int32_t v = lv[0].goff[(size_t)g]; v < lv[0].goff[(size_t)g + 1]; v++)
+                if (gid0[(size_t)v] != g) return set_error(KP_ERR_INVALID, "bad graph id in hierarchy file");
+        for (int32_t l = 0; l + 1 < L; l++) {
+            const HostLevel &H = lv[(size_t)l], &N = lv[(size_t)l + 1];
+            for (int32_t g = 0; g < G; g++) {
+                const bool carried = l < glevels[(size_t)g] - 1;
+                const int32_t lo = N.goff[(size_t)g], hi = N.goff[(size_t)g + 1];
+                for (int32_t v = H.goff[(size_t)g]; v < H.goff[(size_t)g + 1]; v++) {
+                    const int32_t m = H.map[(size_t)v];
+                    const bool inside = m >= lo && m < hi;
+                    if (carried ? !inside : !(inside || m == -1))
+                        return set_error(KP_ERR_INVALID, "map leaves its graph in hierarchy file");
+                }
+            }
+        }
+    }
 
     kp_hierarchy *h = new kp_hierarchy();
     h->stream = s;

@@ -80,6 +80,11 @@ struct ServerRequest {
     int32_t block_base = 0;  // first block weight slot in the group's buffer
     bool done = false;
     bool released = false;
+    // calls inside wait or fetch that hold this request without the lock;
+    // a request whose id is already forgotten (cancelled, released) is
+    // deleted by the last of them
+    int32_t users = 0;
+    bool forgotten = false;
 };
 
 struct ServerGroup {
@@ -354,6 +359,15 @@ ServerRequest *find(kp_server *S, uint64_t id) {
     return it == S->reqs.end() ? nullptr : it->second;
 }
 
+// Ends a use of r begun under the lock (the lock is held again here).
+void drop_user(kp_server *S, ServerRequest *r) {
+    if (--r->users == 0 && r->forgotten) {
+        delete r;
+        return;
+    }
+    S->cv_done.notify_all();   // a release may be waiting for the readers
+}
+
 }  // namespace
 
 extern "C" {
@@ -461,9 +475,13 @@ kp_status kp_server_wait(kp_server *S, uint64_t id, kp_request_result *res) {
     std::unique_lock<std::mutex> lk(S->mu);
     ServerRequest *r = find(S, id);
     if (!r) return set_error(KP_ERR_INVALID, "unknown request");
+    r->users++;   // a cancel meanwhile finishes r instead of deleting it
     S->cv_done.wait(lk, [&] { return r->done; });
     if (res) *res = r->res;
-    if (r->res.status != KP_OK) return set_error(r->res.status, r->error);
+    const kp_status st = r->res.status;
+    const std::string msg = r->error;
+    drop_user(S, r);
+    if (st != KP_OK) return set_error(st, msg);
     return KP_OK;
 }
 
@@ -477,13 +495,21 @@ kp_status kp_server_fetch(kp_server *S, uint64_t id, int32_t *fine_part, int64_t
         if (!r) return set_error(KP_ERR_INVALID, "unknown request");
         if (!r->done || r->released) return set_error(KP_ERR_INVALID, "request not finished or released");
         if (r->res.status != KP_OK) return set_error(r->res.status, r->error);
+        r->users++;   // a release meanwhile waits until the copies are done
     }
     ServerGroup *g = r->grp;
     const size_t n = (size_t)r->n;
-    if (fine_part && n) KP_CUDA(cudaMemcpy(fine_part, g->d_fine + r->node_base, 4 * n, cudaMemcpyDeviceToHost));
-    if (gain && n) KP_CUDA(cudaMemcpy(gain, g->d_gain + r->node_base, 8 * n, cudaMemcpyDeviceToHost));
-    if (target && n) KP_CUDA(cudaMemcpy(target, g->d_target + r->node_base, 4 * n, cudaMemcpyDeviceToHost));
-    if (coarse_part) std::memcpy(coarse_part, r->coarse_part.data(), 4 * r->coarse_part.size());
+    cudaError_t e = cudaSuccess;
+    if (fine_part && n) e = cudaMemcpy(fine_part, g->d_fine + r->node_base, 4 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && gain && n) e = cudaMemcpy(gain, g->d_gain + r->node_base, 8 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && target && n)
+        e = cudaMemcpy(target, g->d_target + r->node_base, 4 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && coarse_part) std::memcpy(coarse_part, r->coarse_part.data(), 4 * r->coarse_part.size());
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        drop_user(S, r);
+    }
+    if (e != cudaSuccess) return cuda_error(e, "kp_server_fetch copy");
     return KP_OK;
 }
 
@@ -496,8 +522,15 @@ kp_status kp_server_cancel(kp_server *S, uint64_t id) {
         ServerRequest *r = *q;
         S->queue.erase(q);
         S->reqs.erase(id);
-        delete r;
+        // finished as cancelled: threads waiting on it return an error and
+        // the last of them deletes it
+        r->done = true;
+        r->res.status = KP_ERR_INVALID;
+        r->error = "request cancelled";
+        r->forgotten = true;
+        if (r->users == 0) delete r;
     }
+    S->cv_done.notify_all();
     S->cv_work.notify_all();   // the next request may fit now that this one is gone
     return KP_OK;
 }
@@ -506,20 +539,25 @@ kp_status kp_server_release(kp_server *S, uint64_t id) {
     if (!S) return set_error(KP_ERR_INVALID, "null argument");
     ServerGroup *to_free = nullptr;
     {
-        std::lock_guard<std::mutex> lk(S->mu);
+        std::unique_lock<std::mutex> lk(S->mu);
         ServerRequest *r = find(S, id);
         if (!r) return set_error(KP_ERR_INVALID, "unknown request");
         if (!r->done) return set_error(KP_ERR_INVALID, "request not finished");
-        if (!r->released) {
-            r->released = true;
-            ServerGroup *g = r->grp;
-            if (g && --g->live == 0) {
-                S->used -= g->footprint;
-                to_free = g;
-            }
+        if (r->released) return set_error(KP_ERR_INVALID, "request already being released");
+        // claimed: no fetch starts from here on; the fetches still copying
+        // from the group's buffers finish first (other users of r are
+        // waiters that have seen it done and leave at once)
+        r->released = true;
+        r->users++;
+        S->cv_done.wait(lk, [&] { return r->users == 1; });
+        ServerGroup *g = r->grp;
+        if (g && --g->live == 0) {
+            S->used -= g->footprint;
+            to_free = g;
         }
         S->reqs.erase(id);
-        delete r;
+        r->forgotten = true;
+        drop_user(S, r);   // deletes r
     }
     if (to_free) {
         free_group(to_free);

@@ -33,4 +33,5 @@ def test_reference_arm_json_line():
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
     # edges/s of the workload's own graph: 64x64 grid, 8,064 undirected edges
-    assert d["config"]["m"] == 8064 and d["unit"] == "edges/s"
+    assert d["graph"]["m"] == 8064 and d["unit"] == "edges/s"
+    assert d["config"] == {"workload": "grid64", "desc": d["config"]["desc"]}

@@ -126,3 +126,56 @@ def test_server_cancel_of_a_waiting_request():
         second = sv.wait(ids[1])
         assert second["status"] == 0 and first["status"] == 0
         sv.release(ids[1])
+
+
+def test_server_cancel_wakes_a_thread_waiting_on_the_request():
+    import threading
+    import time
+    g = I.grid2d(30, 30)
+    with B().Server(workers=1, max_batch=1, hbm_budget_bytes=1) as sv:
+        ids = [sv.submit(g.xadj, g.adjncy, g.ewgt, g.vwgt, 2, 0.03, s, 40) for s in range(2)]
+        sv.wait(ids[0])                         # resident: ids[1] waits for budget
+        box = {}
+
+        def waiter():
+            try:
+                box["res"] = sv.wait(ids[1])
+            except B().KpError as e:
+                box["err"] = e
+
+        t = threading.Thread(target=waiter)
+        t.start()
+        time.sleep(0.3)                         # the waiter blocks on the queued request
+        sv.cancel(ids[1])
+        t.join(timeout=60)
+        assert not t.is_alive(), "a wait on a cancelled request must return"
+        assert "err" in box and box["err"].status == B().KP_ERR_INVALID
+        sv.release(ids[0])
+
+
+def test_server_release_waits_for_a_fetch_in_progress():
+    import threading
+    g = I.grid2d(200, 200)
+    with B().Server(workers=1, max_batch=1) as sv:
+        for rep in range(3):
+            rid = sv.submit(g.xadj, g.adjncy, g.ewgt, g.vwgt, 4, 0.03, rep, 80)
+            res = sv.wait(rid)
+            first = sv.fetch(rid, g.n, res["coarsest_n"])
+            seen = []
+
+            def reader():
+                for _ in range(20):
+                    try:
+                        got = sv.fetch(rid, g.n, res["coarsest_n"])
+                    except B().KpError as e:
+                        seen.append(e.status)
+                        return
+                    seen.append(bool(np.array_equal(got["part"], first["part"])))
+
+            t = threading.Thread(target=reader)
+            t.start()
+            sv.release(rid)
+            t.join(timeout=60)
+            assert not t.is_alive()
+            # every fetch that ran saw the results intact, then the id was gone
+            assert all(x is True or x == B().KP_ERR_INVALID for x in seen), seen

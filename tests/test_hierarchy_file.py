@@ -1,0 +1,111 @@
+"""kp_hierarchy_load checks a file on the host before anything reaches the
+device: maps that would send the projection outside a level, or outside a
+graph of a batch, are refused with KP_ERR_INVALID.  CPU only: every file here
+is rejected before the first CUDA call; the valid ones pass the checks and then
+either load (with a GPU) or stop at the first CUDA call (without one)."""
+import ctypes
+import os
+import struct
+
+import numpy as np
+import pytest
+
+MAGIC = b"KPHIER01"
+
+
+def write(path, levels, maps, goffs=None, glevels=None, gid0=None):
+    """levels: [(xadj, adjncy, ewgt, vwgt)], maps: one per level but the last."""
+    G = 0 if goffs is None else len(goffs[0]) - 1
+    out = bytearray(MAGIC + struct.pack("<4i", 1, len(levels), G, 0))
+    for l, (xadj, adj, ew, vw) in enumerate(levels):
+        n, nnz = len(xadj) - 1, len(adj)
+        out += struct.pack("<2i", n, nnz)
+        for a in (xadj, adj, ew, vw):
+            out += np.asarray(a, dtype="<i4").tobytes()
+        if l < len(levels) - 1:
+            out += np.asarray(maps[l], dtype="<i4").tobytes()
+        if G:
+            out += np.asarray(goffs[l], dtype="<i4").tobytes()
+    if G:
+        out += np.asarray(glevels, dtype="<i4").tobytes() + np.asarray(gid0, dtype="<i4").tobytes()
+    open(path, "wb").write(bytes(out))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_0910_2004_gb300 import binding
+    return binding.load()
+
+
+def load_status(lib, path):
+    h = ctypes.c_void_p()
+    st = lib.kp_hierarchy_load(os.fsencode(str(path)), None, ctypes.byref(h))
+    if st == 0:
+        lib.kp_hierarchy_free(h)
+    return st
+
+
+# a path 0-1-2-3 contracted to the edge {0,1}: level 1 has 2 nodes
+PATH = ([0, 1, 3, 5, 6], [1, 0, 2, 1, 3, 2], [1] * 6, [1] * 4)
+EDGE = ([0, 1, 2], [1, 0], [1, 1], [2, 2])
+SINGLE_NODE = ([0, 0], [], [], [2])
+
+
+def union(*gs):
+    xadj, adj, ew, vw, base = [0], [], [], [], 0
+    for x, a, e, v in gs:
+        start = xadj[-1]
+        xadj += [start + int(d) for d in x[1:]]
+        adj += [u + base for u in a]
+        ew += list(e)
+        vw += list(v)
+        base += len(x) - 1
+    return xadj, adj, ew, vw
+
+
+def test_single_graph_maps_must_stay_in_the_next_level(lib, tmp_path):
+    from paper_0910_2004_gb300 import binding as B
+    good = tmp_path / "good.kph"
+    write(good, [PATH, EDGE], [[0, 0, 1, 1]])
+    assert load_status(lib, good) in (B.KP_OK, B.KP_ERR_CUDA)
+    for bad_map in ([0, 0, 1, 2], [0, 0, 1, -1], [-1, 0, 1, 1]):
+        p = tmp_path / "bad.kph"
+        write(p, [PATH, EDGE], [bad_map])
+        assert load_status(lib, p) == B.KP_ERR_INVALID, bad_map
+
+
+def test_batch_maps_stay_inside_their_graph(lib, tmp_path):
+    from paper_0910_2004_gb300 import binding as B
+    # graph 0: the path (two levels); graph 1: one edge contracted to a node
+    lv0 = union(PATH, EDGE)
+    lv1 = union(EDGE, SINGLE_NODE)
+    goffs = [[0, 4, 6], [0, 2, 3]]
+    good_map = [0, 0, 1, 1, 2, 2]
+    good = tmp_path / "good.kph"
+    write(good, [lv0, lv1], [good_map], goffs, [2, 2], [0, 0, 0, 0, 1, 1])
+    assert load_status(lib, good) in (B.KP_OK, B.KP_ERR_CUDA)
+    cases = {
+        "into the other graph": ([0, 0, 1, 1, 1, 2], [2, 2], [0, 0, 0, 0, 1, 1]),
+        "carried node not carried": ([0, 0, 1, -1, 2, 2], [2, 2], [0, 0, 0, 0, 1, 1]),
+        "graph id disagrees with the offsets": (good_map, [2, 2], [0, 0, 0, 1, 1, 1]),
+    }
+    for what, (m, gl, gid) in cases.items():
+        p = tmp_path / "bad.kph"
+        write(p, [lv0, lv1], [m], goffs, gl, gid)
+        assert load_status(lib, p) == B.KP_ERR_INVALID, what
+
+
+def test_batch_graph_that_stopped_maps_nowhere(lib, tmp_path):
+    from paper_0910_2004_gb300 import binding as B
+    # graph 1 stops at the input (one level): its nodes map to -1
+    lv0 = union(PATH, EDGE)
+    lv1 = EDGE
+    goffs = [[0, 4, 6], [0, 2, 2]]
+    good = tmp_path / "good.kph"
+    write(good, [lv0, lv1], [[0, 0, 1, 1, -1, -1]], goffs, [2, 1], [0, 0, 0, 0, 1, 1])
+    assert load_status(lib, good) in (B.KP_OK, B.KP_ERR_CUDA)
+    p = tmp_path / "bad.kph"
+    write(p, [lv0, lv1], [[0, 0, 1, 1, 0, -1]], goffs, [2, 1], [0, 0, 0, 0, 1, 1])
+    assert load_status(lib, p) == B.KP_ERR_INVALID
