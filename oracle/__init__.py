@@ -26,7 +26,7 @@ import numpy as np
 __all__ = [
     "RATINGS", "Level", "Hierarchy", "build", "lib", "validate", "out_weight",
     "frac_cmp", "splitmix64", "edge_hash", "edge_order", "greedy_matching",
-    "handshake_matching", "check_greedy_matching", "contract", "coarsen",
+    "handshake_matching", "gpa_matching", "check_greedy_matching", "contract", "coarsen",
     "project", "l_max", "cut_gain", "quotient_graph", "boundary_band",
 ]
 
@@ -77,6 +77,8 @@ def lib():
             L.or_handshake_matching.argtypes = [i32, _i32p, _i32p, _i32p, _i32p, c_int, u64, _i32p,
                                                 ctypes.POINTER(i32), _i32p]
             L.or_handshake_matching.restype = i64
+            L.or_gpa_matching.argtypes = [i32, _i32p, _i32p, _i32p, _i32p, c_int, u64, _i32p, _i32p]
+            L.or_gpa_matching.restype = i64
             L.or_check_greedy_matching.argtypes = [i32, _i32p, _i32p, _i32p, _i32p, c_int, u64, _i32p]
             L.or_check_greedy_matching.restype = i64
             L.or_contract.argtypes = [i32, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p,
@@ -179,6 +181,21 @@ def handshake_matching(g, rating: str, seed: int):
     return match, int(size), int(rounds.value), cand1
 
 
+def gpa_matching(g, rating: str, seed: int):
+    """Global Path Algorithm (Section 3.2): paths and even cycles collected
+    in the strict edge order, then an optimal matching of each by dynamic
+    programming over the ratings in double precision (see oracle.c).
+    Returns (match, |M|, nbr2) with nbr2[2v], nbr2[2v+1] the collected
+    neighbours of v (-1 where fewer)."""
+    g = _as_level(g)
+    match = np.empty(g.n, dtype=np.int32)
+    nbr2 = np.empty(max(2 * g.n, 1), dtype=np.int32)
+    size = lib().or_gpa_matching(g.n, g.xadj, g.adjncy, g.ewgt, g.vwgt, RATINGS[rating], seed, match, nbr2)
+    if size < 0:
+        raise MemoryError("oracle GPA matching")
+    return match, int(size), nbr2[:2 * g.n]
+
+
 def check_greedy_matching(g, rating: str, seed: int, match) -> int:
     """-1 iff `match` is the Greedy matching of g (see oracle.c)."""
     g = _as_level(g)
@@ -223,6 +240,8 @@ def coarsen(g, rating: str, seed: int, stop_size: int, max_levels: int = 64,
             break
         if matcher == "greedy":
             match, size = greedy_matching(cur, rating, seed)
+        elif matcher == "gpa":
+            match, size, _ = gpa_matching(cur, rating, seed)
         else:
             match, size, _, _ = handshake_matching(cur, rating, seed)
         if size == 0:

@@ -296,6 +296,183 @@ int64_t or_handshake_matching(int32_t n, const int32_t *xadj, const int32_t *adj
     return size;
 }
 
+/* The rating of edge {u,v} as a real number for the dynamic programme of
+ * the Global Path Algorithm: the fraction num/den of or_rating evaluated in
+ * IEEE double (num and den converted with rounding to nearest, then one
+ * correctly rounded division; a zero denominator gives +infinity). */
+static double or_rating_real(const or_edge *e)
+{
+    return (double)e->num / (double)e->den;
+}
+
+/* One maximum weight matching of a path x_0 - x_1 - ... - x_L with edge
+ * weights w[1..L] (w[i] joins x_{i-1} and x_i), by dynamic programming:
+ * best[i] = max(best[i-1], best[i-2] + w[i]), taking edge i only when that
+ * is strictly larger.  The matched pairs are written into match[]; returns
+ * best[L].  best[] and take[] are scratch of L+1 entries. */
+static double or_path_dp(int32_t L, const int32_t *x, const double *w, double *best, char *take,
+                         int32_t *match)
+{
+    best[0] = 0.0;
+    take[0] = 0;
+    for (int32_t i = 1; i <= L; i++) {
+        double with = (i >= 2 ? best[i - 2] : 0.0) + w[i];
+        take[i] = with > best[i - 1];
+        best[i] = take[i] ? with : best[i - 1];
+    }
+    for (int32_t i = L; i >= 1;) {
+        if (take[i]) {
+            match[x[i - 1]] = x[i];
+            match[x[i]] = x[i - 1];
+            i -= 2;
+        } else {
+            i -= 1;
+        }
+    }
+    return best[L];
+}
+
+/* Global Path Algorithm (Section 3.2, after Maue and Sanders).
+ * Phase 1 scans the edges from heaviest to lightest under the strict order
+ * and collects a set of paths and even cycles: an edge is taken when both
+ * ends have fewer than two collected edges, unless its ends are the two ends
+ * of one path with an even number of edges (taking it would close an odd
+ * cycle).  Joining the two ends of a path with an odd number of edges closes
+ * an even cycle; that edge, the last one of its cycle, is the cycle's
+ * closing edge.
+ * Phase 2 computes a maximum weight matching of every path and every cycle
+ * by dynamic programming over the ratings (or_rating_real):
+ *  - a path is walked from its end with the smaller id;
+ *  - a cycle with closing edge {a,b}, a < b, is walked from a along its
+ *    other edges to b, giving the path x_0 = a, ..., x_{k-1} = b; the cycle's
+ *    matching is the better of that path's matching and the closing edge
+ *    plus the matching of x_1 .. x_{k-2}, the closing edge only when strictly
+ *    better.
+ * match[v] = partner, or v when v stays unmatched; nbr2 (may be NULL)
+ * receives the two collected neighbours of every node (-1 where fewer).
+ * Returns |M|, or -1 on allocation failure. */
+int64_t or_gpa_matching(int32_t n, const int32_t *xadj, const int32_t *adjncy,
+                        const int32_t *ewgt, const int32_t *vwgt, int rating,
+                        uint64_t seed, int32_t *match, int32_t *nbr2)
+{
+    int64_t m = (int64_t)xadj[n] / 2;
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    or_edge *edges = (or_edge *)malloc(sizeof(or_edge) * (size_t)(m > 0 ? m : 1));
+    int64_t *out = NULL;
+    int32_t *nb = (int32_t *)malloc(sizeof(int32_t) * 2 * nn);      /* collected neighbours */
+    double *nw = (double *)malloc(sizeof(double) * 2 * nn);         /* their ratings */
+    int32_t *parent = (int32_t *)malloc(sizeof(int32_t) * nn);     /* union-find over paths */
+    int64_t *len = (int64_t *)malloc(sizeof(int64_t) * nn);        /* edges of a root's path */
+    int32_t *closing = (int32_t *)malloc(sizeof(int32_t) * nn);    /* a cycle's closing edge: other end */
+    int32_t *x = (int32_t *)malloc(sizeof(int32_t) * (nn + 1));
+    double *w = (double *)malloc(sizeof(double) * (nn + 1));
+    double *best = (double *)malloc(sizeof(double) * (nn + 1));
+    char *take = (char *)malloc(nn + 1);
+    char *seen = (char *)calloc(nn, 1);
+    int64_t result = -1;
+    if (!edges || !nb || !nw || !parent || !len || !closing || !x || !w || !best || !take || !seen) goto done;
+    if (rating == RATING_INNER_OUTER) {
+        out = (int64_t *)malloc(sizeof(int64_t) * nn);
+        if (!out) goto done;
+        or_out_weight(n, xadj, ewgt, out);
+    }
+    int64_t k = 0;
+    for (int32_t v = 0; v < n; v++)
+        for (int32_t e = xadj[v]; e < xadj[v + 1]; e++)
+            if (adjncy[e] > v)
+                or_make_edge(&edges[k++], rating, seed, v, adjncy[e], ewgt[e], vwgt, out);
+    qsort(edges, (size_t)k, sizeof(or_edge), or_cmp_desc);
+    for (int32_t v = 0; v < n; v++) {
+        nb[2 * v] = nb[2 * v + 1] = -1;
+        parent[v] = v;
+        len[v] = 0;
+        closing[v] = -1;
+        match[v] = v;
+    }
+    /* phase 1: paths and even cycles */
+    for (int64_t i = 0; i < k; i++) {
+        int32_t a = edges[i].lo, b = edges[i].hi;
+        if (nb[2 * a + 1] >= 0 || nb[2 * b + 1] >= 0) continue;   /* an end has two edges */
+        int32_t ra = a, rb = b;   /* the paths' roots (path halving on the way) */
+        while (parent[ra] != ra) { parent[ra] = parent[parent[ra]]; ra = parent[ra]; }
+        while (parent[rb] != rb) { parent[rb] = parent[parent[rb]]; rb = parent[rb]; }
+        if (ra == rb && len[ra] % 2 == 0) continue;               /* would close an odd cycle */
+        double r = or_rating_real(&edges[i]);
+        nb[2 * a + (nb[2 * a] >= 0)] = b;
+        nw[2 * a + (nb[2 * a + 1] == b)] = r;
+        nb[2 * b + (nb[2 * b] >= 0)] = a;
+        nw[2 * b + (nb[2 * b + 1] == a)] = r;
+        if (ra == rb) {
+            len[ra] += 1;
+            closing[a] = b;
+            closing[b] = a;
+        } else {
+            parent[rb] = ra;
+            len[ra] += len[rb] + 1;
+        }
+    }
+    /* phase 2a: paths, each from its end with the smaller id */
+    for (int32_t v = 0; v < n; v++) {
+        if (seen[v] || nb[2 * v] < 0 || nb[2 * v + 1] >= 0) continue;   /* not an unseen path end */
+        int32_t L = 0, prev = -1, cur = v;
+        x[0] = v;
+        seen[v] = 1;
+        for (;;) {
+            int32_t s = nb[2 * cur] == prev ? 1 : 0;
+            int32_t nxt = nb[2 * cur + s];
+            if (nxt < 0) break;
+            w[++L] = nw[2 * cur + s];
+            x[L] = nxt;
+            seen[nxt] = 1;
+            prev = cur;
+            cur = nxt;
+        }
+        or_path_dp(L, x, w, best, take, match);
+    }
+    /* phase 2b: cycles, each cut at its closing edge {a,b}, a < b */
+    for (int32_t a = 0; a < n; a++) {
+        int32_t b = closing[a];
+        if (b < a || seen[a]) continue;
+        int32_t K = 0, prev = b, cur = a;   /* leave a by its edge that is not {a,b} */
+        x[0] = a;
+        seen[a] = 1;
+        while (cur != b) {
+            int32_t s = nb[2 * cur] == prev ? 1 : 0;
+            int32_t nxt = nb[2 * cur + s];
+            w[++K] = nw[2 * cur + s];
+            x[K] = nxt;
+            seen[nxt] = 1;
+            prev = cur;
+            cur = nxt;
+        }
+        /* x_0 = a .. x_K = b along the path; the closing edge joins x_K, x_0 */
+        double wc = nw[2 * a + (nb[2 * a + 1] == b)];
+        int32_t *keep = (int32_t *)malloc(sizeof(int32_t) * (size_t)(K + 1));
+        if (!keep) goto done;
+        for (int32_t i = 0; i <= K; i++) keep[i] = match[x[i]];
+        double without = or_path_dp(K, x, w, best, take, match);
+        for (int32_t i = 0; i <= K; i++) match[x[i]] = keep[i];   /* undo, then try with {a,b} */
+        double with = wc + (K >= 3 ? or_path_dp(K - 2, x + 1, w + 1, best, take, match) : 0.0);
+        if (with > without) {
+            match[a] = b;
+            match[b] = a;
+        } else {
+            for (int32_t i = 0; i <= K; i++) match[x[i]] = keep[i];
+            or_path_dp(K, x, w, best, take, match);
+        }
+        free(keep);
+    }
+    if (nbr2)
+        for (int32_t v = 0; v < 2 * n; v++) nbr2[v] = nb[v];
+    result = 0;
+    for (int32_t v = 0; v < n; v++)
+        if (match[v] > v) result++;
+done:
+    free(edges); free(out); free(nb); free(nw); free(parent); free(len); free(closing);
+    free(x); free(w); free(best); free(take); free(seen);
+    return result;
+}
+
 /* Checks that match[] is the Greedy matching of the graph under the strict
  * order, using a characterisation that needs no sort: a matching M is the
  * Greedy matching iff every edge e not in M touches an edge of M that comes

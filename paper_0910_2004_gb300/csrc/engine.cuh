@@ -57,6 +57,7 @@ struct Counters {   // one per level, zeroed before the level runs
     int32_t maxdeg;        // largest coarse degree if it is at least 1024, else 0
     unsigned long long searches;     // rating passes over a row
     unsigned long long failed_cas;   // lost proposal races
+    unsigned long long start_next;   // proposals: next start node handed to a warp
 };
 
 struct DevLevel {

@@ -279,17 +279,22 @@ __device__ __forceinline__ void park_wide(const Work &w, Counters *ctr, int32_t 
     if (slot < w.cache_slots) w.cache_hdr[slot] = make_int2(0, 0);
 }
 
-// First pass: G lanes per proposing node, start nodes [0, n).  Every warp
-// owns one contiguous range of start nodes; its 32/G groups each follow one
-// proposal chain (a node, then whoever it displaced) and take the next start
-// node of the range as soon as their chain ends, so lanes stay busy until the
-// range is used up.  A node whose row is longer than HEAVY entries is parked
-// for the middle pass (list0) instead of being scanned by so few lanes; that
-// pass hands the rows too long for a warp on to the wide pass.  The order of
-// proposals does not change the matching.
+// First pass: G lanes per proposing node, start nodes [0, n).  Warps take
+// short runs of consecutive start nodes (4 per group) from one counter, so
+// the nodes in flight on the whole GPU at any time form a narrow window that
+// sweeps through the ids; on mesh-like graphs with local ids the offer
+// records and rating attributes the window reads stay in L2 from their first
+// read to their last instead of being fetched from DRAM once per reader.
+// Every group follows one proposal chain (a node, then whoever it displaced)
+// and takes the next start node of its warp's run as soon as its chain ends,
+// so lanes stay busy until the counter is used up.  A node whose row is
+// longer than HEAVY entries is parked for the middle pass (list0) instead of
+// being scanned by so few lanes; that pass hands the rows too long for a warp
+// on to the wide pass.  The order of proposals does not change the matching.
 template <int R, int G, int HEAVY>
 __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Counters *ctr, int32_t *err) {
     constexpr int NG = 32 / G;
+    constexpr int RUN = 4 * NG;   // start nodes per counter step
     const unsigned gmask = group_mask<G>();
     const int lane = threadIdx.x & 31;
     const int gl = lane & (G - 1);
@@ -297,11 +302,7 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
     const unsigned below_leader = (1u << leader) - 1u;
     const int32_t *KP_RESTRICT xadj = L.xadj;
     const int64_t count = L.n;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t chunk = (count + nwarps - 1) / nwarps;
-    int64_t pos = warp_id * chunk;
-    const int64_t stop = min(count, pos + chunk);
+    int64_t pos = 0, stop = 0;
     long long iters = 0;
     unsigned long long fails = 0;
     int32_t cur = -1;
@@ -309,8 +310,16 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
     for (;;) {
         // the whole warp leaves together (full-warp votes follow)
         if (__any_sync(0xffffffffu, aborted)) break;
-        // give every idle group the next start node of the warp's range
+        // give every idle group the next start node of the warp's run, taking
+        // a new run from the counter when this one is used up
         const unsigned need = __ballot_sync(0xffffffffu, cur < 0 && gl == 0);
+        if (need && pos >= stop) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&ctr->start_next, (unsigned long long)RUN);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            pos = (int64_t)min(base, (unsigned long long)count);
+            stop = min(count, pos + RUN);
+        }
         if (need && pos < stop) {
             const int64_t avail = min((int64_t)NG, stop - pos);
             const int rank = __popc(need & below_leader);
