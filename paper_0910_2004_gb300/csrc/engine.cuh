@@ -147,6 +147,17 @@ struct Work {
     int2 *cache;       // SUITOR_CACHE_K candidates {node, edge weight} per slot
     int2 *cache_hdr;   // per slot {candidates kept, next to try}
     int32_t cache_slots;
+    // Global Path Algorithm: the collected neighbours of every node (two
+    // slots, -1 empty), per directed entry whether the edge was refused for
+    // closing an odd cycle, the other end of a cycle's closing edge, the
+    // dynamic programme's take flags, and the pending cycle checks with their
+    // decisions
+    int32_t *gnb;
+    uint8_t *grej;
+    int32_t *gclose;
+    uint8_t *gtake;
+    int32_t *gpend;
+    int8_t *gdec;
     // the input's largest degree + 1, written by level 0's start into mapped
     // host memory (null: not wanted)
     int32_t *deg0_host;
