@@ -249,12 +249,13 @@ def main():
     ap.add_argument("--workload", default="grid256", choices=sorted(workloads()))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--matcher", default="suitor", choices=["suitor", "handshake"])
+    ap.add_argument("--matcher", default="suitor", choices=["suitor", "handshake", "gpa"])
     ap.add_argument("--tail-nodes", type=int, default=0)
     ap.add_argument("--no-tune", action="store_true", help="built-in knobs instead of the autotuner's")
     ap.add_argument("--requests", type=int, default=None, help="served: requests per load phase")
     ap.add_argument("--workers", type=int, default=4, help="served: server workers")
     ap.add_argument("--small-workers", type=int, default=1, help="served: workers kept for small requests")
+    ap.add_argument("--repeats", type=int, default=3, help="served: repeats of each loaded phase")
     args = ap.parse_args()
     wl = workloads()[args.workload]
     if wl.get("batch"):
@@ -392,6 +393,30 @@ def main():
         refine[name] = {"ms": ms, "algorithmic_bytes": nbytes,
                         "achieved_gbs": nbytes / (ms / 1000.0) / 1e9}
 
+    # the other matchers on the same graph (not part of the step; reported
+    # beside it): coarsening time, levels and matched pairs of the hierarchy
+    matchers = {}
+    for mname in ("suitor", "gpa"):
+        mopts = dict(knobs) if mname == args.matcher else {"matcher": mname}
+        mopts["matcher"] = mname
+        times, info = [], None
+        for rep in range(3):
+            flush.zero_()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a0.record(stream)
+            hm = B.coarsen(dg, rating=rating, seed=1, stop_size=stop, validate=False, **mopts)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            times.append(a0.elapsed_time(a1))
+            tot = hm.profile()
+            info = {"levels": hm.num_levels(), "matched_pairs": int(tot["n"] - B.kp_hierarchy_level(
+                hm.handle, hm.num_levels() - 1)[0].n), "rounds": tot["rounds"]}
+            hm.free()
+        ms = statistics.median(times)
+        matchers[mname] = {"coarsen_ms": ms, "edges_per_s": g.m / (ms / 1000.0), **info}
+
     # end to end through the host-buffer entry point
     e2e_steps = args.e2e_steps if args.e2e_steps is not None else max(3, min(args.steps, 20))
     e2e_line = None
@@ -474,6 +499,7 @@ def main():
         "clocks": clocks,
         "e2e": e2e_line,
         "refinement_helpers": refine,
+        "matchers": matchers,
         "gpu_launches": launches_tot,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -902,11 +928,22 @@ def run_served(args, wl):
     sat = serve_phase(sv, pool, sat_reqs, None)
     loads = {}
     for load, reqs in load_reqs.items():
+        # the loaded phases are repeated with other arrival draws; the line
+        # reports every repeat and their medians
         rate = load * sat["requests_per_s"]
-        arr = poisson_arrivals(R, rate, seed=int(load * 100))
-        loads[load] = serve_phase(sv, pool, reqs, arr)
-        loads[load]["offered_requests_per_s"] = rate
-        loads[load]["arrivals"] = arr
+        reps = []
+        for rep in range(max(1, args.repeats)):
+            arr = poisson_arrivals(R, rate, seed=int(load * 100) + 1000 * rep)
+            ph = serve_phase(sv, pool, reqs, arr)
+            ph["arrivals"] = arr
+            reps.append(ph)
+        med = dict(reps[len(reps) // 2])
+        for key in ("p50_ms", "p99_ms", "edges_per_s", "requests_per_s", "span_s", "mean_ms"):
+            med[key] = float(np.median([r[key] for r in reps]))
+        med["repeats"] = [{key: r[key] for key in ("p50_ms", "p99_ms", "edges_per_s", "span_s")} for r in reps]
+        med["offered_requests_per_s"] = rate
+        med["arrivals"] = reps[len(reps) // 2]["arrivals"]
+        loads[load] = med
     clocks = sampler.stop()
     sv.close()
     # every rank served the same request sequence: the job's time is the

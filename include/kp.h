@@ -80,9 +80,10 @@ typedef struct {
     const int32_t *vwgt;
 } kp_graph;
 
-/* Two ways to reach the matching of locally heaviest edges (Section 3.3).
- * Under the strict edge order both end in the same unique matching, the
- * Greedy matching of Section 3.2:
+/* How the matching of each level is found.  SUITOR and HANDSHAKE reach the
+ * matching of locally heaviest edges (Section 3.3); under the strict edge
+ * order both end in the same unique matching, the Greedy matching of
+ * Section 3.2:
  *   SUITOR     every node proposes to its best neighbour whose standing offer
  *              it beats (one 128-bit compare-and-swap per proposal); a
  *              displaced proposer proposes again (Manne & Halappanavar's
@@ -90,10 +91,22 @@ typedef struct {
  *   HANDSHAKE  rounds: every free node names its best free neighbour, mutual
  *              names are matched, repeated until no edge has two free ends;
  *              one cooperative launch per level, rounds separated by bounded
- *              grid barriers. */
+ *              grid barriers.
+ * GPA computes the Global Path Algorithm's matching (Section 3.2, the
+ * paper's default matcher): the edges are taken in the strict order into a
+ * collection of paths and even cycles (an edge joins when both ends have
+ * fewer than two collected edges and it does not close an odd cycle), then
+ * every path and cycle gets a maximum weight matching by dynamic programming
+ * over the ratings in IEEE double, walked from the path end with the smaller
+ * id, a cycle from the smaller end of its closing (lightest) edge, an edge
+ * taken only when strictly better.  The result equals the sequential
+ * algorithm's; one cooperative launch per level decides the edges that are
+ * the best undecided edge at both ends in rounds.  With GPA every level is
+ * launched on its own (tail_nodes and cluster_nodes are not used). */
 typedef enum {
     KP_MATCHER_SUITOR = 0,
-    KP_MATCHER_HANDSHAKE = 1
+    KP_MATCHER_HANDSHAKE = 1,
+    KP_MATCHER_GPA = 2
 } kp_matcher;
 
 /* Coarsening options.
@@ -112,7 +125,8 @@ typedef enum {
  *   profile              1: time every phase with CUDA events on the stream
  *                        (read with kp_hierarchy_profile)
  *   matcher              a kp_matcher: how the matching of each level is
- *                        found; both give the same unique matching
+ *                        found (SUITOR and HANDSHAKE give the same unique
+ *                        matching, GPA the Global Path Algorithm's)
  *   arena_bytes          initial size of the device arena that holds the
  *                        coarse levels (0: sized from the input); further
  *                        chunks are added ahead of need when the levels
@@ -429,7 +443,10 @@ kp_status kp_pipeline_host(const kp_graph *g, const kp_options *o, int32_t k, do
  * oldest waiting request of at most batch_max_nodes nodes instead, so small
  * requests do not queue behind large ones.  Footprint while running:
  * 148 n + 57 nnz + 2 MB
- * bytes; while resident: 88 n + 40 nnz + 1 MB.
+ * bytes; while resident: 88 n + 40 nnz + 1 MB.  A coarsening that needs more
+ * arena than that (graphs that shrink slowly take spare chunks) is charged
+ * for every chunk as it is taken, until release, so requests admitted later
+ * wait for that memory too.
  * Continuous batching: when a worker takes a request with at most
  * batch_max_nodes nodes, it also takes further waiting requests with at most
  * batch_max_nodes nodes that fit the budget, up to
@@ -480,6 +497,9 @@ typedef struct kp_request_result {
     double t_submit_us;   /* microseconds since kp_server_create: entry of submit */
     double t_admit_us;    /* taken by a worker */
     double t_done_us;     /* results on the device, scalars on the host */
+    int64_t arena_grown_bytes;   /* device bytes the group's coarsening took beyond the
+                                    footprint estimate (spare arena chunks); charged to the
+                                    budget from the moment they were taken until release */
 } kp_request_result;
 
 /* Starts the workers.  Errors: KP_ERR_INVALID (workers outside 1..64,

@@ -23,7 +23,7 @@ KP_OK, KP_ERR_INVALID, KP_ERR_OVERFLOW, KP_ERR_OOM, KP_ERR_CUDA, KP_ERR_TIMEOUT,
 STATUS_NAMES = ["KP_OK", "KP_ERR_INVALID", "KP_ERR_OVERFLOW", "KP_ERR_OOM", "KP_ERR_CUDA",
                 "KP_ERR_TIMEOUT", "KP_ERR_UNSUPPORTED"]
 RATINGS = {"expansion*2": 0, "innerOuter": 1, "weight": 2, "expansion": 3, "expansion*": 4}
-MATCHERS = {"suitor": 0, "handshake": 1}
+MATCHERS = {"suitor": 0, "handshake": 1, "gpa": 2}
 
 PHASES = ["validate", "out", "match", "relabel", "contract", "csr", "tail"]
 
@@ -94,7 +94,8 @@ class kp_request_result(ctypes.Structure):
                 ("group_size", ctypes.c_int32), ("launches", ctypes.c_int32), ("pad", ctypes.c_int32),
                 ("group_id", ctypes.c_int64), ("cut", ctypes.c_int64), ("total_c", ctypes.c_int64),
                 ("l_max", ctypes.c_int64), ("imbalance", ctypes.c_int64), ("t_submit_us", ctypes.c_double),
-                ("t_admit_us", ctypes.c_double), ("t_done_us", ctypes.c_double)]
+                ("t_admit_us", ctypes.c_double), ("t_done_us", ctypes.c_double),
+                ("arena_grown_bytes", ctypes.c_int64)]
 
 
 kp_initial_partition_fn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),

@@ -89,6 +89,11 @@ void dev_free(void *p, cudaStream_t s) {
     if (p) cudaFreeAsync(p, s);
 }
 
+ArenaObserver &arena_observer() {
+    thread_local ArenaObserver o;
+    return o;
+}
+
 // ---------------------------------------------------------------------------
 // input check
 // ---------------------------------------------------------------------------
@@ -99,67 +104,82 @@ struct CheckAcc {
     int32_t pad;
 };
 
-__global__ void k_validate(int32_t n, int32_t nnz, const int32_t *__restrict__ xadj,
-                           const int32_t *__restrict__ adjncy, const int32_t *__restrict__ ewgt,
-                           const int32_t *__restrict__ vwgt, CheckAcc *acc) {
-    constexpr int G = 8;
-    const unsigned gmask = group_mask<G>();
-    const int gl = threadIdx.x & (G - 1);
-    const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-    const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
+// Input check in two kernels.  Nodes: row bounds, c >= 0 and the sum of c.
+__global__ void k_validate_nodes(int32_t n, int32_t nnz, const int32_t *__restrict__ xadj,
+                                 const int32_t *__restrict__ vwgt, CheckAcc *acc) {
     int bad = 0;
-    unsigned long long csum = 0, wsum = 0;
+    unsigned long long csum = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0 && (xadj[0] != 0 || xadj[n] != nnz)) bad = 1;
-    for (int64_t v = gid; v < n; v += ngroups) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         const int32_t beg = xadj[v], end = xadj[v + 1];
-        if (beg < 0 || end < beg || end > nnz) {
-            bad = 1;
-            continue;
+        if (beg < 0 || end < beg || end > nnz) bad = 1;
+        const int32_t c = vwgt[v];
+        if (c < 0) bad = 1;
+        else csum += (unsigned long long)c;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) csum += __shfl_xor_sync(0xffffffffu, csum, o);
+    if ((threadIdx.x & 31) == 0 && csum) atomicAdd(&acc->csum, csum);
+    if (bad) atomicOr(&acc->err, ERR_GRAPH_INVALID);
+}
+
+// Entries, in chunks of VALIDATE_CHUNK consecutive ones per thread, so hub
+// rows spread over many threads: the row of the chunk's first entry by a
+// binary search over xadj, then for every entry: neighbour in range, no self
+// loop, omega > 0, the row ascending, and the reverse entry with the same
+// weight (a binary search in the neighbour's row).  Every index is checked
+// before it is used, whatever the input (the node kernel reports bad rows).
+constexpr int VALIDATE_CHUNK = 8;
+
+__global__ void k_validate_entries(int32_t n, int32_t nnz, const int32_t *__restrict__ xadj,
+                                   const int32_t *__restrict__ adjncy, const int32_t *__restrict__ ewgt,
+                                   CheckAcc *acc) {
+    int bad = 0;
+    unsigned long long wsum = 0;
+    const int64_t chunks = ((int64_t)nnz + VALIDATE_CHUNK - 1) / VALIDATE_CHUNK;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < chunks; c += stride) {
+        const int64_t e0 = c * VALIDATE_CHUNK, e1 = min((int64_t)nnz, e0 + VALIDATE_CHUNK);
+        int32_t lo = 0, hi = n - 1;   // the last row starting at or before e0
+        while (lo < hi) {
+            const int32_t mid = lo + (hi - lo + 1) / 2;
+            if ((int64_t)xadj[mid] <= e0) lo = mid;
+            else hi = mid - 1;
         }
-        if (gl == 0) {
-            const int32_t c = vwgt[v];
-            if (c < 0) bad = 1;
-            else csum += (unsigned long long)c;
-        }
-        for (int32_t e = beg + gl; e < end; e += G) {
+        int32_t v = lo;
+        for (int64_t e = e0; e < e1; e++) {
+            while (v + 1 < n && (int64_t)xadj[v + 1] <= e) v++;
             const int32_t u = adjncy[e];
             const int32_t w = ewgt[e];
             if (u < 0 || u >= n || u == v || w <= 0) {
                 bad = 1;
                 continue;
             }
-            if (e > beg && adjncy[e - 1] >= u) bad = 1;
-            // the reverse entry (u, v) with the same weight
-            int32_t lo = xadj[u], hi = xadj[u + 1] - 1;
-            if (lo < 0 || hi >= nnz) {
+            if (e > 0 && e > xadj[v] && adjncy[e - 1] >= u) bad = 1;
+            int32_t a = xadj[u], b = xadj[u + 1] - 1;
+            if (a < 0 || b >= nnz) {
                 bad = 1;
                 continue;
             }
             int found = -1;
-            while (lo <= hi) {
-                const int32_t mid = lo + (hi - lo) / 2;
+            while (a <= b) {
+                const int32_t mid = a + (b - a) / 2;
                 const int32_t t = adjncy[mid];
-                if (t == (int32_t)v) {
+                if (t == v) {
                     found = mid;
                     break;
                 }
-                if (t < (int32_t)v) lo = mid + 1;
-                else hi = mid - 1;
+                if (t < v) a = mid + 1;
+                else b = mid - 1;
             }
             if (found < 0 || ewgt[found] != w) bad = 1;
             if (u > v) wsum += (unsigned long long)w;
         }
     }
-    (void)gmask;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        csum += __shfl_xor_sync(0xffffffffu, csum, o);
-        wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        if (csum) atomicAdd(&acc->csum, csum);
-        if (wsum) atomicAdd(&acc->wsum, wsum);
-    }
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(0xffffffffu, wsum, o);
+    if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&acc->wsum, wsum);
     if (bad) atomicOr(&acc->err, ERR_GRAPH_INVALID);
 }
 
@@ -174,9 +194,12 @@ kp_status validate_graph(const kp_graph *g, cudaStream_t s, int64_t) {
     }
     cudaError_t e = cudaMemsetAsync(acc, 0, sizeof(CheckAcc), s);
     if (e == cudaSuccess) {
-        const int64_t want = ((int64_t)g->n * 8 + 255) / 256;
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * 16));
-        k_validate<<<grid, 256, 0, s>>>(g->n, g->nnz, g->xadj, g->adjncy, g->ewgt, g->vwgt, acc);
+        const int cap = num_sms() * 16;
+        const int grid_n = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)g->n + 255) / 256, cap));
+        const int64_t chunks = ((int64_t)g->nnz + VALIDATE_CHUNK - 1) / VALIDATE_CHUNK;
+        const int grid_e = (int)std::max<int64_t>(1, std::min<int64_t>((chunks + 255) / 256, cap));
+        k_validate_nodes<<<grid_n, 256, 0, s>>>(g->n, g->nnz, g->xadj, g->vwgt, acc);
+        if (g->nnz > 0) k_validate_entries<<<grid_e, 256, 0, s>>>(g->n, g->nnz, g->xadj, g->adjncy, g->ewgt, acc);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(host, acc, sizeof(CheckAcc), cudaMemcpyDeviceToHost, s);

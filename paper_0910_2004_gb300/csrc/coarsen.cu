@@ -84,6 +84,14 @@ kp_status alloc_work(Scratch &sc, Work &w, int32_t n0, int32_t nnz0, const kp_op
         KP_TRY(sc.get(&w.match, n0));
         KP_TRY(sc.get(&w.cand, n0));
     }
+    if (o->matcher == KP_MATCHER_GPA) {
+        KP_TRY(sc.get(&w.gnb, 2 * (int64_t)n0));
+        KP_TRY(sc.get(&w.grej, nnz0));
+        KP_TRY(sc.get(&w.gclose, n0));
+        KP_TRY(sc.get(&w.gtake, n0));
+        KP_TRY(sc.get(&w.gpend, n0));
+        KP_TRY(sc.get(&w.gdec, n0));
+    }
     KP_TRY(sc.get(&w.list0, n0));
     KP_TRY(sc.get(&w.list1, n0));
     KP_TRY(sc.get(&w.first, n0));
@@ -219,7 +227,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
                        const BatchSpec *batch) {
     const int rating = o->rating;
     if (rating < 0 || rating > 4) return set_error(KP_ERR_UNSUPPORTED, "unknown rating");
-    if (o->matcher != KP_MATCHER_SUITOR && o->matcher != KP_MATCHER_HANDSHAKE)
+    if (o->matcher != KP_MATCHER_SUITOR && o->matcher != KP_MATCHER_HANDSHAKE && o->matcher != KP_MATCHER_GPA)
         return set_error(KP_ERR_UNSUPPORTED, "unknown matcher");
     if (g->n < 0 || g->nnz < 0) return set_error(KP_ERR_INVALID, "negative graph size");
     if (g->n > 0 && (!g->xadj || !g->vwgt || (g->nnz > 0 && (!g->adjncy || !g->ewgt))))
@@ -233,7 +241,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         (o->sort_shared_max != 0 && (o->sort_shared_max < 128 || o->sort_shared_max > MID_MAX)) ||
         (o->radix_bits != 0 && (o->radix_bits < 4 || o->radix_bits > 8)) || o->cluster_nodes < -1)
         return set_error(KP_ERR_INVALID, "bad tuning knob");
-    if (o->matcher == KP_MATCHER_HANDSHAKE) {
+    if (o->matcher == KP_MATCHER_HANDSHAKE || o->matcher == KP_MATCHER_GPA) {
         if (g_coop_supported < 0) {
             int dev = 0, v = 0;
             KP_CUDA(cudaGetDevice(&dev));
@@ -362,7 +370,8 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         if (st != KP_OK) return fail(st);
     }
 
-    const int32_t tail_nodes = o->tail_nodes == 0 ? TAIL_NODES : o->tail_nodes;   // -1: never
+    // -1: never (the Global Path Algorithm runs every level on its own)
+    const int32_t tail_nodes = o->matcher == KP_MATCHER_GPA ? -1 : o->tail_nodes == 0 ? TAIL_NODES : o->tail_nodes;
     int32_t epoch = 0;
     int start = 0;
     int32_t spares = 0;   // spare arena chunks supplied
@@ -482,6 +491,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
                         st = dev_alloc((void **)&chunk, cap, s);
                         if (st != KP_OK) return bail(st);
                         h->allocations.push_back(chunk);
+                        report_arena_growth((int64_t)cap);
                         hs->arena_next = chunk;
                         hs->arena_next_cap = cap;
                         if (cudaMemcpyAsync(&dst->arena_next, &hs->arena_next, sizeof(char *) + sizeof(unsigned long long),
@@ -506,6 +516,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         st = dev_alloc((void **)&arena, arena_cap, s);
         if (st != KP_OK) return bail(st);
         h->allocations.push_back(arena);
+        report_arena_growth((int64_t)arena_cap);
         hs->arena = arena;
         hs->arena_cap = arena_cap;
         hs->arena_used = 0;
@@ -611,7 +622,9 @@ kp_status plan_capture(kp_plan *p) {
     const int level_end = p->o.max_levels + (p->batch ? 1 : 0);
     const int64_t tail_nodes = p->o.tail_nodes == 0 ? TAIL_NODES : p->o.tail_nodes;
     int K = 0;
-    if (tail_nodes >= 0)
+    if (p->o.matcher == KP_MATCHER_GPA)   // every level on its own (a replay may run deeper)
+        K = level_end;
+    else if (tail_nodes >= 0)
         while (K + 1 < (int)p->sizes.size() && K < level_end &&
                !(p->sizes[(size_t)K].first <= tail_nodes && p->sizes[(size_t)K].second <= 8 * tail_nodes))
             K++;
@@ -625,8 +638,9 @@ kp_status plan_capture(kp_plan *p) {
         LL.level = level;
         LL.rating = p->o.rating;
         LL.matcher = p->o.matcher;
-        LL.n_bound = p->sizes[(size_t)level].first;
-        LL.nnz_bound = std::max(p->sizes[(size_t)level].second, 1);
+        const size_t sl = std::min<size_t>((size_t)level, p->sizes.size() - 1);
+        LL.n_bound = std::max(p->sizes[sl].first, 1);
+        LL.nnz_bound = std::max(p->sizes[sl].second, 1);
         LL.huge = true;   // a replay may meet other degrees than the checking run
         LL.epoch_relabel = ++epoch;
         LL.epoch_degscan = ++epoch;

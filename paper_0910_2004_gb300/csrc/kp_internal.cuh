@@ -63,6 +63,20 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
 kp_status dev_alloc(void **p, size_t bytes, cudaStream_t s);
 void dev_free(void *p, cudaStream_t s);
 
+// Device bytes a coarsening takes beyond its first arena (spare chunks for
+// slowly shrinking graphs, a larger arena after an overflow) are reported to
+// this thread's observer, if one is set (the request server charges them to
+// its device budget while the allocation is in use).
+struct ArenaObserver {
+    void (*grew)(void *ctx, int64_t bytes) = nullptr;
+    void *ctx = nullptr;
+};
+ArenaObserver &arena_observer();
+inline void report_arena_growth(int64_t bytes) {
+    ArenaObserver &o = arena_observer();
+    if (o.grew) o.grew(o.ctx, bytes);
+}
+
 template <class T>
 kp_status dev_alloc_n(T **p, int64_t count, cudaStream_t s) {
     return dev_alloc(reinterpret_cast<void **>(p), sizeof(T) * (size_t)(count > 0 ? count : 1), s);

@@ -2,7 +2,7 @@
 // per-phase kernels defined in match.cuh, and Out(v) of the input level.
 #include <algorithm>
 
-#include "match.cuh"
+#include "gpa.cuh"
 
 namespace kp {
 
@@ -55,6 +55,17 @@ kp_status launch_matching_r(const LevelLaunch &L, cudaStream_t s, int32_t *launc
         k_suitor<R, SUITOR_WARP><<<occ_warp * sms, MATCH_BLOCK, 0, s>>>(L.st, L.level, L.w);
         k_suitor<R, SUITOR_WIDE><<<occ_wide * sms, MATCH_BLOCK, 0, s>>>(L.st, L.level, L.w);
         *launches += 4;
+    } else if (L.matcher == KP_MATCHER_GPA) {
+        static const int occ = occupancy_of(k_gpa<R>, MATCH_BLOCK);
+        const int64_t want = (nb * 8 + MATCH_BLOCK - 1) / MATCH_BLOCK;
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)occ * sms));
+        k_level_begin<R, false><<<grid1, 256, 0, s>>>(L.st, L.level, L.w);
+        DevState *st = L.st;
+        int level = L.level;
+        Work w = L.w;
+        void *args[] = {&st, &level, &w};
+        KP_CUDA(cudaLaunchCooperativeKernel((const void *)k_gpa<R>, dim3(grid), dim3(MATCH_BLOCK), args, 0, s));
+        *launches += 2;
     } else {
         static const int occ = occupancy_of(k_match<R>, MATCH_BLOCK);
         const int64_t want = (nb * 8 + MATCH_BLOCK - 1) / MATCH_BLOCK;

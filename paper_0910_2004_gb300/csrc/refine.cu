@@ -22,6 +22,8 @@ constexpr int32_t QUOTIENT_MAX_K = 4096;   // dense k x k accumulator
 // added to the matrix at the end.  Block ids outside [0,k) set the error flag.
 constexpr int QROW = 16;
 constexpr int QSMEM_CELLS = 4096;
+constexpr int32_t QHUB_ROW = 2048;   // longer rows: a block each (k_quotient_hubs)
+constexpr int QHUB_BLOCK = 512;
 
 __device__ __forceinline__ void quotient_row_warp(int32_t u, int32_t pu, int32_t beg, int32_t end,
                                                   const int32_t *__restrict__ adjncy,
@@ -58,12 +60,14 @@ __device__ __forceinline__ void quotient_row_warp(int32_t u, int32_t pu, int32_t
     }
 }
 
+// Rows longer than QHUB_ROW are listed (hubs, hub_count) for k_quotient_hubs.
 template <bool SMEM>
 __global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_acc(int32_t n, const int32_t *__restrict__ xadj,
                                                                const int32_t *__restrict__ adjncy,
                                                                const int32_t *__restrict__ ewgt,
                                                                const int32_t *__restrict__ part, int32_t k,
-                                                               unsigned long long *gcells, int32_t *err) {
+                                                               unsigned long long *gcells, int32_t *err,
+                                                               int32_t *hubs, int32_t *hub_count) {
     __shared__ unsigned long long s_cells[SMEM ? QSMEM_CELLS : 1];
     const int64_t kk = (int64_t)k * k;
     if (SMEM) {
@@ -138,6 +142,10 @@ __global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_acc(int32_t n, const 
             const int32_t pj = __shfl_sync(0xffffffffu, pu, j);
             const int32_t bj = __shfl_sync(0xffffffffu, beg, j);
             const int32_t dj = __shfl_sync(0xffffffffu, d, j);
+            if (dj > QHUB_ROW) {   // a hub: one block, one pass over shared-memory sums
+                if (lane == 0) hubs[atomicAdd(hub_count, 1)] = uj;
+                continue;
+            }
             quotient_row_warp(uj, pj, bj, bj + dj, adjncy, ewgt, part, k, cells, err);
         }
     }
@@ -145,6 +153,39 @@ __global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_acc(int32_t n, const 
         __syncthreads();
         for (int64_t i = threadIdx.x; i < kk; i += blockDim.x)
             if (s_cells[i]) atomicAdd(&gcells[i], s_cells[i]);
+    }
+}
+
+// The listed hub rows, one block each: the weight towards every block is
+// summed in shared memory in one pass over the row (k 64-bit sums), then
+// each nonzero sum is added to its cell of the dense matrix.
+__global__ void __launch_bounds__(QHUB_BLOCK) k_quotient_hubs(const int32_t *__restrict__ xadj,
+                                                              const int32_t *__restrict__ adjncy,
+                                                              const int32_t *__restrict__ ewgt,
+                                                              const int32_t *__restrict__ part, int32_t k,
+                                                              const int32_t *__restrict__ hubs,
+                                                              const int32_t *hub_count, unsigned long long *gcells,
+                                                              int32_t *err) {
+    extern __shared__ unsigned long long s_bins[];
+    const int32_t count = *hub_count;
+    for (int32_t i = blockIdx.x; i < count; i += gridDim.x) {
+        const int32_t u = hubs[i];
+        const int32_t pu = part[u];   // checked by the row kernel
+        for (int32_t b = threadIdx.x; b < k; b += blockDim.x) s_bins[b] = 0;
+        __syncthreads();
+        const int32_t beg = xadj[u], end = xadj[u + 1];
+        for (int32_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+            const int32_t pv = part[adjncy[e]];
+            if (pv < 0 || pv >= k) {
+                atomicOr(err, 1);
+                continue;
+            }
+            if (pv != pu) atomicAdd(&s_bins[pv], (unsigned long long)ewgt[e]);
+        }
+        __syncthreads();
+        for (int32_t b = threadIdx.x; b < k; b += blockDim.x)
+            if (s_bins[b]) atomicAdd(&gcells[(int64_t)pu * k + b], s_bins[b]);
+        __syncthreads();
     }
 }
 
@@ -350,29 +391,35 @@ kp_status quotient_graph_impl(const kp_graph *g, const int32_t *part, int32_t k,
         return set_error(KP_ERR_INVALID, "null output");
     if (k > QUOTIENT_MAX_K) return set_error(KP_ERR_UNSUPPORTED, "quotient graph: k above 4096");
     unsigned long long *cells = nullptr;
-    int32_t *err = nullptr;
+    int32_t *err = nullptr;   // [0] block id error, [1] hub rows listed
+    int32_t *hubs = nullptr;
     long long *nnz_dev = nullptr;
     KP_TRY(dev_alloc_n(&cells, (int64_t)k * k, s));
-    kp_status st = dev_alloc_n(&err, 1, s);
+    kp_status st = dev_alloc_n(&err, 2, s);
     if (st == KP_OK) st = dev_alloc_n(&nnz_dev, 1, s);
+    if (st == KP_OK) st = dev_alloc_n(&hubs, (int64_t)g->nnz / QHUB_ROW + 1, s);
     auto done = [&](kp_status r) {
         dev_free(cells, s);
         dev_free(err, s);
         dev_free(nnz_dev, s);
+        dev_free(hubs, s);
         return r;
     };
     if (st != KP_OK) return done(st);
     if (cudaMemsetAsync(cells, 0, sizeof(unsigned long long) * (size_t)k * k, s) != cudaSuccess ||
-        cudaMemsetAsync(err, 0, sizeof(int32_t), s) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, 2 * sizeof(int32_t), s) != cudaSuccess ||
         cudaMemsetAsync(q_xadj, 0, sizeof(int32_t), s) != cudaSuccess)
         return done(cuda_error(cudaGetLastError(), "clear"));
     if (g->n > 0) {
         if ((int64_t)k * k <= QSMEM_CELLS)
             k_quotient_acc<true><<<grid_for(g->n), REFINE_BLOCK, 0, s>>>(g->n, g->xadj, g->adjncy, g->ewgt, part, k,
-                                                                         cells, err);
+                                                                         cells, err, hubs, err + 1);
         else
             k_quotient_acc<false><<<grid_for(g->n), REFINE_BLOCK, 0, s>>>(g->n, g->xadj, g->adjncy, g->ewgt, part, k,
-                                                                          cells, err);
+                                                                          cells, err, hubs, err + 1);
+        if (g->nnz > QHUB_ROW)
+            k_quotient_hubs<<<num_sms() * 2, QHUB_BLOCK, sizeof(unsigned long long) * (size_t)k, s>>>(
+                g->xadj, g->adjncy, g->ewgt, part, k, hubs, err + 1, cells, err);
     }
     k_quotient_count<<<grid_for((int64_t)k * 32), REFINE_BLOCK, 0, s>>>(k, cells, q_xadj);
     k_quotient_scan<<<1, 1024, 0, s>>>(k, q_xadj, nnz_dev);

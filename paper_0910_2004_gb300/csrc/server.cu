@@ -96,6 +96,7 @@ struct ServerGroup {
     int64_t *d_gain = nullptr, *d_bw = nullptr;
     int64_t footprint = 0;  // charged against the budget now
     int64_t resident = 0;
+    int64_t grown = 0;      // arena chunks taken beyond the estimate
     int32_t live = 0;
     int64_t id = 0;
     int32_t launches = 0;
@@ -268,6 +269,20 @@ kp_status run_group(kp_server *S, ServerGroup *g) {
     return KP_OK;
 }
 
+struct GrowthCharge {
+    kp_server *S;
+    ServerGroup *g;
+};
+
+void charge_growth(void *ctx, int64_t bytes) {
+    GrowthCharge *c = static_cast<GrowthCharge *>(ctx);
+    std::lock_guard<std::mutex> lk(c->S->mu);
+    c->S->used += bytes;
+    c->g->footprint += bytes;
+    c->g->resident += bytes;
+    c->g->grown += bytes;
+}
+
 bool fits(const kp_server *S, const ServerRequest *r) {
     return S->used == 0 || S->used + r->footprint <= S->cfg.hbm_budget_bytes;
 }
@@ -328,11 +343,17 @@ void worker_main(kp_server *S, int wi) {
             g->id = S->next_group++;
         }
         kp_status st;
+        // arena chunks the coarsening adds beyond the estimate stay with the
+        // group's hierarchy until release: they are charged to the budget
+        // as they are taken, so later admissions wait for them
+        GrowthCharge charge{S, g};
+        arena_observer() = ArenaObserver{&charge_growth, &charge};
         try {
             st = run_group(S, g);
         } catch (const std::bad_alloc &) {
             st = set_error(KP_ERR_OOM, "host allocation failed");
         }
+        arena_observer() = ArenaObserver{};
         std::string msg = st == KP_OK ? "" : kp_last_error();
         {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -341,6 +362,7 @@ void worker_main(kp_server *S, int wi) {
             g->footprint = g->resident;
             const double t = S->now_us();
             for (ServerRequest *r : g->reqs) {
+                r->res.arena_grown_bytes = g->grown;
                 r->res.group_id = g->id;
                 r->res.launches = g->launches;
                 r->res.status = st;

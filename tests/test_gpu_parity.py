@@ -493,3 +493,47 @@ def test_saved_and_loaded_hierarchy_is_identical(tmp_path):
     with pytest.raises(B().KpError) as e:
         B().load_hierarchy(bad)
     assert e.value.status == B().KP_ERR_INVALID
+
+
+def test_input_check_on_power_law_rows():
+    """The entry-parallel input check: valid R-MAT graphs (hub rows of
+    thousands of entries) pass; each kind of malformed row is refused, in a
+    hub row as well as in a short one."""
+    g = I.rmat(14, 8)
+    d = np.diff(g.xadj)
+    hub = int(np.argmax(d))
+    short = int(np.nonzero((d[:-1] == 3) & (d[1:] > 0))[0][0])
+    assert d[hub] > 2048
+    h = B().coarsen(B().DeviceGraph.from_csr(g), stop_size=40)
+    h.free()
+
+    def refused(xadj, adj, ew, vw):
+        dg = B().DeviceGraph(np.ascontiguousarray(xadj, np.int32), np.ascontiguousarray(adj, np.int32),
+                             np.ascontiguousarray(ew, np.int32), np.ascontiguousarray(vw, np.int32))
+        with pytest.raises(B().KpError) as e:
+            B().coarsen(dg, stop_size=40)
+        assert e.value.status == B().KP_ERR_INVALID
+
+    for row in (hub, short):
+        a, b = int(g.xadj[row]), int(g.xadj[row + 1])
+        adj = g.adjncy.copy()
+        adj[a], adj[a + 1] = adj[a + 1], adj[a]           # row not ascending
+        refused(g.xadj, adj, g.ewgt, g.vwgt)
+        adj = g.adjncy.copy()
+        adj[b - 1] = row                                   # self loop
+        refused(g.xadj, adj, g.ewgt, g.vwgt)
+        ew = g.ewgt.copy()
+        ew[a + 1] += 1                                     # reverse entry has another weight
+        refused(g.xadj, g.adjncy, ew, g.vwgt)
+        ew = g.ewgt.copy()
+        ew[a] = 0                                          # omega must be positive
+        refused(g.xadj, g.adjncy, ew, g.vwgt)
+        adj = g.adjncy.copy()
+        adj[b - 1] = g.n + 5                               # neighbour out of range
+        refused(g.xadj, adj, g.ewgt, g.vwgt)
+    vw = g.vwgt.copy()
+    vw[hub] = -1                                           # c must be >= 0
+    refused(g.xadj, g.adjncy, g.ewgt, vw)
+    xadj = g.xadj.copy()
+    xadj[short + 1], xadj[short + 2] = xadj[short + 2], xadj[short + 1]   # decreasing offsets (in range)
+    refused(xadj, g.adjncy, g.ewgt, g.vwgt)

@@ -181,3 +181,31 @@ def test_fifo_order_and_errors():
     with pytest.raises(B().KpError) as e:
         B().Server(workers=2, small_workers=2)        # nobody left for large requests
     assert e.value.status == B().KP_ERR_INVALID
+
+
+def test_spare_arena_chunks_are_charged_until_release():
+    """An R-MAT request shrinks slowly and takes spare arena chunks beyond its
+    footprint estimate; they are charged to the budget as they are taken, so
+    a request that fits the estimate but not the chunks waits for release."""
+    a = I.rmat(15, 4)
+    small = I.grid2d(20, 20)
+    # every level launched on its own: the host supplies spare chunks ahead of need
+    with B().Server(workers=1, max_batch=1, tail_nodes=-1) as sv:
+        ra = sv.wait(sv.submit(a.xadj, a.adjncy, a.ewgt, a.vwgt, 4, 0.03, 5, 40))
+    grown = ra["arena_grown_bytes"]
+    assert grown > 0
+    resident_a = 88 * a.n + 40 * a.nnz + (1 << 20)
+    running_small = 148 * small.n + 57 * small.nnz + (2 << 20)
+    budget = resident_a + running_small + grown // 2   # enough without the chunks, too little with them
+    with B().Server(workers=2, max_batch=1, hbm_budget_bytes=budget, tail_nodes=-1) as sv:
+        ia = sv.submit(a.xadj, a.adjncy, a.ewgt, a.vwgt, 4, 0.03, 5, 40)
+        ra2 = sv.wait(ia)
+        assert ra2["arena_grown_bytes"] == grown
+        ib = sv.submit(small.xadj, small.adjncy, small.ewgt, small.vwgt, 2, 0.03, 1, 40)
+        time.sleep(0.3)
+        done, _ = sv.poll(ib)
+        assert not done, "admitted although the spare chunks exhaust the budget"
+        sv.release(ia)
+        rb = sv.wait(ib)
+        assert rb["status"] == 0 and rb["t_admit_us"] >= ra2["t_done_us"]
+        sv.release(ib)
