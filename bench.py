@@ -40,7 +40,7 @@ L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 # captures of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum
 # summed over the phase's launches); a phase without an entry reports traffic
 # null.  The summaries under profiles/ give the commands and the scaling.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {("grid256", "match"): 4_260_000_000}
 HBM_PEAK_FALLBACK = 6800.0
 
 
@@ -248,6 +248,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="grid256", choices=sorted(workloads()))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-matchers", action="store_true",
+                    help="skip the side comparison of the matchers (kept out of launch-list captures)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--matcher", default="suitor", choices=["suitor", "handshake", "gpa"])
     ap.add_argument("--tail-nodes", type=int, default=0)
@@ -396,7 +398,7 @@ def main():
     # the other matchers on the same graph (not part of the step; reported
     # beside it): coarsening time, levels and matched pairs of the hierarchy
     matchers = {}
-    for mname in ("suitor", "gpa"):
+    for mname in (() if args.no_matchers else ("suitor", "gpa")):
         mopts = dict(knobs) if mname == args.matcher else {"matcher": mname}
         mopts["matcher"] = mname
         times, info = [], None

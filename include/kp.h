@@ -154,7 +154,11 @@ typedef enum {
  *   cluster_nodes        tail levels with at most this many nodes run in one
  *                        thread-block cluster (16 CTAs, or 8) whose phases
  *                        are separated by the hardware cluster barrier
- *                        (0: 8192; -1: never) */
+ *                        (0: 8192; -1: never)
+ *   suitor_blocks        resident 256-thread blocks per SM the first Suitor
+ *                        pass is compiled for: 3 (up to 80 registers per
+ *                        thread) or 4 (up to 64, more proposal chains in
+ *                        flight) (0: 3) */
 typedef struct {
     int32_t rating;
     uint64_t seed;
@@ -172,6 +176,7 @@ typedef struct {
     int32_t sort_shared_max;
     int32_t radix_bits;
     int32_t cluster_nodes;
+    int32_t suitor_blocks;
 } kp_options;
 
 /* Fills *o with the defaults: EXPANSION_STAR2, seed 1, stop_size 40,
@@ -582,9 +587,9 @@ void kp_plan_destroy(kp_plan *p);
 /* ------------------------------------------------------------------------
  * Autotuning (the paper has no counterpart).  The tuning knobs of
  * kp_options never change a result, only the time; kp_autotune measures.
- * Coordinate descent from *o over tail_nodes, suitor_lanes (Suitor only),
- * tail_block_nodes, sort_shared_max, radix_bits and cluster_nodes, in that
- * order: every
+ * Coordinate descent from *o over tail_nodes, suitor_lanes and suitor_blocks
+ * (Suitor only), tail_block_nodes, sort_shared_max, radix_bits and
+ * cluster_nodes, in that order: every
  * candidate coarsens the caller's graph (num_graphs = 0) or batch
  * (num_graphs > 0, arguments as kp_coarsen_batch) once untimed and `reps`
  * times timed by CUDA events on the stream; a knob keeps the value with the

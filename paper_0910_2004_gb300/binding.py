@@ -57,10 +57,10 @@ class kp_options(ctypes.Structure):
                 ("matcher", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("tail_nodes", ctypes.c_int32),
                 ("suitor_lanes", ctypes.c_int32), ("tail_block_nodes", ctypes.c_int32),
                 ("sort_shared_max", ctypes.c_int32), ("radix_bits", ctypes.c_int32),
-                ("cluster_nodes", ctypes.c_int32)]
+                ("cluster_nodes", ctypes.c_int32), ("suitor_blocks", ctypes.c_int32)]
 
 TUNING_KNOBS = ("suitor_lanes", "tail_block_nodes", "sort_shared_max", "radix_bits", "cluster_nodes", "tail_nodes",
-                "matcher")
+                "suitor_blocks", "matcher")
 
 
 class kp_cut_gain_out(ctypes.Structure):
@@ -488,7 +488,7 @@ class DeviceGraph:
 def make_options(rating="expansion*2", seed=1, stop_size=40, max_levels=64, min_shrink_permille=50,
                  spin_limit=1 << 22, validate=True, profile=False, matcher="suitor",
                  arena_bytes=0, tail_nodes=0, suitor_lanes=0, tail_block_nodes=0, sort_shared_max=0,
-                 radix_bits=0, cluster_nodes=0) -> kp_options:
+                 radix_bits=0, cluster_nodes=0, suitor_blocks=0) -> kp_options:
     o = kp_options_default()
     o.rating = RATINGS[rating] if isinstance(rating, str) else int(rating)
     o.seed = seed
@@ -506,6 +506,7 @@ def make_options(rating="expansion*2", seed=1, stop_size=40, max_levels=64, min_
     o.sort_shared_max = sort_shared_max
     o.radix_bits = radix_bits
     o.cluster_nodes = cluster_nodes
+    o.suitor_blocks = suitor_blocks
     return o
 
 

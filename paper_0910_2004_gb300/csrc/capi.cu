@@ -257,6 +257,7 @@ void kp_options_default(kp_options *o) {
     o->arena_bytes = 0;
     o->tail_nodes = 0;
     o->suitor_lanes = 0;
+    o->suitor_blocks = 0;
     o->tail_block_nodes = 0;
     o->sort_shared_max = 0;
     o->radix_bits = 0;

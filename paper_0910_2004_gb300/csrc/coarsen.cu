@@ -239,7 +239,8 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
           o->suitor_lanes == 32) ||
         (o->tail_block_nodes != 0 && (o->tail_block_nodes < 256 || o->tail_block_nodes > 16384)) ||
         (o->sort_shared_max != 0 && (o->sort_shared_max < 128 || o->sort_shared_max > MID_MAX)) ||
-        (o->radix_bits != 0 && (o->radix_bits < 4 || o->radix_bits > 8)) || o->cluster_nodes < -1)
+        (o->radix_bits != 0 && (o->radix_bits < 4 || o->radix_bits > 8)) || o->cluster_nodes < -1 ||
+        !(o->suitor_blocks == 0 || o->suitor_blocks == 3 || o->suitor_blocks == 4))
         return set_error(KP_ERR_INVALID, "bad tuning knob");
     if (o->matcher == KP_MATCHER_HANDSHAKE || o->matcher == KP_MATCHER_GPA) {
         if (g_coop_supported < 0) {
@@ -366,7 +367,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         return fail(cuda_error(cudaGetLastError(), "upload state"));
     if (inner_outer) {
         timer.mark(KP_PHASE_OUT);
-        st = launch_out_weight(dst, n0, g->xadj, g->ewgt, L0.outw, s, &launches);
+        st = launch_out_weight(dst, n0, nnz0, g->xadj, g->ewgt, L0.outw, s, &launches);
         if (st != KP_OK) return fail(st);
     }
 
@@ -421,6 +422,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
             LL.level = level;
             LL.rating = rating;
             LL.matcher = o->matcher;
+            LL.suitor_blocks = o->suitor_blocks;
             LL.n_bound = n_bound;
             LL.nnz_bound = nnz_bound;
             // a coarse degree is at most twice the largest of the level
@@ -615,7 +617,7 @@ kp_status plan_capture(kp_plan *p) {
         if (st == KP_OK) st = launch_graph_ids(n0, p->G, p->b.node_offsets, p->gid0, s, &p->launches);
     }
     if (st == KP_OK && p->o.rating == KP_RATING_INNER_OUTER)
-        st = launch_out_weight(p->dst, n0, p->g.xadj, p->g.ewgt, p->hs_init->lv[0].outw, s, &p->launches);
+        st = launch_out_weight(p->dst, n0, p->g.nnz, p->g.xadj, p->g.ewgt, p->hs_init->lv[0].outw, s, &p->launches);
     // the levels the checking run found above the tail threshold as separate
     // launches (grids sized by that run's sizes; every kernel covers any
     // size), the rest in one persistent launch
@@ -638,6 +640,7 @@ kp_status plan_capture(kp_plan *p) {
         LL.level = level;
         LL.rating = p->o.rating;
         LL.matcher = p->o.matcher;
+        LL.suitor_blocks = p->o.suitor_blocks;
         const size_t sl = std::min<size_t>((size_t)level, p->sizes.size() - 1);
         LL.n_bound = std::max(p->sizes[sl].first, 1);
         LL.nnz_bound = std::max(p->sizes[sl].second, 1);

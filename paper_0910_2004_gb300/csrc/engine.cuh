@@ -398,6 +398,7 @@ struct LevelLaunch {
     int level;
     int rating;
     int matcher;
+    int suitor_blocks;   // 3 or 4 (0: 3): the first proposal pass's register budget
     int32_t n_bound;     // upper bound of the level's node count (grid sizes)
     int64_t nnz_bound;   // upper bound of its entry count
     bool huge;           // rows of more than HUGE_ROW gathered entries are possible
@@ -408,8 +409,8 @@ kp_status launch_graph_ids(int32_t n0, int32_t num_graphs, const int32_t *goff, 
                            int32_t *launches);
 kp_status launch_check_batch_edges(const kp_graph *g, const int32_t *gid, const int32_t *goff, int32_t *flag,
                                    cudaStream_t s);
-kp_status launch_out_weight(DevState *st, int32_t n0, const int32_t *xadj, const int32_t *ewgt, int32_t *outw,
-                            cudaStream_t s, int32_t *launches);
+kp_status launch_out_weight(DevState *st, int32_t n0, int64_t nnz0, const int32_t *xadj, const int32_t *ewgt,
+                            int32_t *outw, cudaStream_t s, int32_t *launches);
 kp_status launch_matching(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
 kp_status launch_relabel(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
 kp_status launch_contract(const LevelLaunch &L, cudaStream_t s, int32_t *launches);

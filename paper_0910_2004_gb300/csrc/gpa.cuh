@@ -102,14 +102,21 @@ __device__ __forceinline__ int32_t gpa_next(const Work &w, int32_t x, int32_t pr
 // Best undecided edge of u: to a neighbour that is not collected with u,
 // has fewer than two collected edges, and whose edge was not refused for
 // closing an odd cycle.  G lanes per node; cand[u] = the neighbour or -1.
+// With recheck, u keeps its candidate while that edge is still undecided
+// (the undecided edges of u only ever become fewer, so it stays the best);
+// a refused edge has set cand to -2.
 template <int R, int G>
-__device__ __forceinline__ void gpa_rate_node(const DevLevel &L, const Work &w, int32_t u) {
+__device__ __forceinline__ void gpa_rate_node(const DevLevel &L, const Work &w, int32_t u, bool recheck) {
     const unsigned gmask = group_mask<G>();
     const int gl = threadIdx.x & (G - 1);
     const int2 mine = gpa_nb(w, u);
     if (mine.y >= 0) {   // two collected edges: every other edge is refused
         if (gl == 0) w.cand[u] = -1;
         return;
+    }
+    if (recheck) {
+        const int32_t c = __ldcg(w.cand + u);
+        if (c >= 0 && c != mine.x && __ldcg(w.gnb + 2 * (int64_t)c + 1) < 0) return;
     }
     const int32_t beg = KP_LDG(L.xadj + u), end = KP_LDG(L.xadj + u + 1);
     const int32_t au = rating_attr<R>(L.vwgt, L.outw, u);
@@ -144,7 +151,8 @@ template <int R, int G>
 __device__ void gpa_rate_phase(const DevLevel &L, const Work &w, const int32_t *lst, int64_t cnt) {
     const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
     const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
-    for (int64_t i = gid; i < cnt; i += ngroups) gpa_rate_node<R, G>(L, w, lst ? __ldcg(lst + i) : (int32_t)i);
+    for (int64_t i = gid; i < cnt; i += ngroups)
+        gpa_rate_node<R, G>(L, w, lst ? __ldcg(lst + i) : (int32_t)i, lst != nullptr);
 }
 
 // Mutual best edges: taken at once when an end has no collected edge, else
@@ -367,6 +375,8 @@ __device__ bool phase_gpa(DevState *st, int level, const Work &w) {
                 const int32_t e1 = gpa_entry(L, u, v), e2 = gpa_entry(L, v, u);
                 if (e1 >= 0) w.grej[e1] = 1;
                 if (e2 >= 0) w.grej[e2] = 1;
+                w.cand[u] = -2;   // both ends look for their next best edge
+                w.cand[v] = -2;
                 continue;
             }
             w.gnb[2 * (int64_t)u + 1] = v;   // both ends had one collected edge

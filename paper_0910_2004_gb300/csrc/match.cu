@@ -6,20 +6,23 @@
 
 namespace kp {
 
-// Out(v) = sum of the weights of v's edges (Section 3.1), input level: 8
-// lanes per node over a grid of resident blocks (grid-stride over nodes).
+// Out(v) = sum of the weights of v's edges (Section 3.1), input level: G
+// lanes per node (G = 1 for sparse graphs: a thread sums its short row with
+// independent loads, so many rows are in flight), grid-stride over nodes.
+template <int G>
 __global__ void k_out_weight(int32_t n, const int32_t *__restrict__ xadj, const int32_t *__restrict__ ewgt,
                              int32_t *__restrict__ outw) {
-    const int gl = threadIdx.x & 7;
-    const unsigned gmask = group_mask<8>();
-    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) >> 3;
-    // the loop bound is the same for the 8 lanes of a group (shuffles below)
-    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; v < n; v += groups) {
+    const int gl = threadIdx.x & (G - 1);
+    const unsigned gmask = group_mask<G>();
+    const int64_t groups = ((int64_t)gridDim.x * blockDim.x) / G;
+    // the loop bound is the same for the G lanes of a group (shuffles below)
+    for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
         int64_t s = 0;
         const int32_t beg = xadj[v], end = xadj[v + 1];
-        for (int32_t e = beg + gl; e < end; e += 8) s += ewgt[e];
+#pragma unroll 4
+        for (int32_t e = beg + gl; e < end; e += G) s += ewgt[e];
 #pragma unroll
-        for (int off = 4; off > 0; off >>= 1) s += __shfl_xor_sync(gmask, s, off);
+        for (int off = G / 2; off > 0; off >>= 1) s += __shfl_xor_sync(gmask, s, off);
         if (gl == 0) outw[v] = (int32_t)s;
     }
 }
@@ -42,14 +45,17 @@ kp_status launch_matching_r(const LevelLaunch &L, cudaStream_t s, int32_t *launc
     const int64_t nb = std::max<int64_t>(1, L.n_bound);
     const int grid1 = (int)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, (int64_t)sms * 8));
     if (L.matcher == KP_MATCHER_SUITOR) {
-        static const int occ = occupancy_of(k_suitor<R, SUITOR_FIRST>, MATCH_BLOCK);
+        static const int occ3 = occupancy_of(k_suitor<R, SUITOR_FIRST, 3>, MATCH_BLOCK);
+        static const int occ4 = occupancy_of(k_suitor<R, SUITOR_FIRST, 4>, MATCH_BLOCK);
         static const int occ_warp = occupancy_of(k_suitor<R, SUITOR_WARP>, MATCH_BLOCK);
         static const int occ_wide = occupancy_of(k_suitor<R, SUITOR_WIDE>, MATCH_BLOCK);
+        const bool four = L.suitor_blocks == 4;
         // at least 32 start nodes per warp, at most the blocks that fit at once
         const int64_t want = (nb + 32 * (MATCH_BLOCK / 32) - 1) / (32 * (MATCH_BLOCK / 32));
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want * 4, (int64_t)occ * sms));
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want * 4, (int64_t)(four ? occ4 : occ3) * sms));
         k_level_begin<R, true><<<grid1, 256, 0, s>>>(L.st, L.level, L.w);
-        k_suitor<R, SUITOR_FIRST><<<grid, MATCH_BLOCK, 0, s>>>(L.st, L.level, L.w);
+        if (four) k_suitor<R, SUITOR_FIRST, 4><<<grid, MATCH_BLOCK, 0, s>>>(L.st, L.level, L.w);
+        else k_suitor<R, SUITOR_FIRST, 3><<<grid, MATCH_BLOCK, 0, s>>>(L.st, L.level, L.w);
         // the passes over parked nodes (they return at once when nothing is
         // parked); ordinary launches, so other streams' kernels run beside them
         k_suitor<R, SUITOR_WARP><<<occ_warp * sms, MATCH_BLOCK, 0, s>>>(L.st, L.level, L.w);
@@ -146,11 +152,13 @@ kp_status launch_check_batch_edges(const kp_graph *g, const int32_t *gid, const 
     return KP_OK;
 }
 
-kp_status launch_out_weight(DevState *, int32_t n0, const int32_t *xadj, const int32_t *ewgt, int32_t *outw,
-                            cudaStream_t s, int32_t *launches) {
-    const int64_t threads = (int64_t)n0 * 8;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, (int64_t)num_sms() * 16));
-    k_out_weight<<<grid, 256, 0, s>>>(n0, xadj, ewgt, outw);
+kp_status launch_out_weight(DevState *, int32_t n0, int64_t nnz0, const int32_t *xadj, const int32_t *ewgt,
+                            int32_t *outw, cudaStream_t s, int32_t *launches) {
+    const bool sparse = nnz0 <= 16ll * n0;
+    const int64_t threads = (int64_t)n0 * (sparse ? 1 : 8);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((threads + 255) / 256, (int64_t)num_sms() * 32));
+    if (sparse) k_out_weight<1><<<grid, 256, 0, s>>>(n0, xadj, ewgt, outw);
+    else k_out_weight<8><<<grid, 256, 0, s>>>(n0, xadj, ewgt, outw);
     *launches += 1;
     KP_CUDA(cudaGetLastError());
     return KP_OK;

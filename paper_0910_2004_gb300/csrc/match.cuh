@@ -102,12 +102,17 @@ __device__ void phase_level_begin(DevState *st, int level, const Work &w) {
 // ---------------------------------------------------------------------------
 // proposals
 // ---------------------------------------------------------------------------
+// An offer record as it is now, read through L2 (other threads change it by
+// 128-bit CAS).  An ordinary load, so a row's gathers can be in flight
+// together; a stale record only makes the CAS that expects it fail.  The
+// CAS is a compiler barrier, so a record is read afresh after every proposal.
 __device__ __forceinline__ Offer ld_offer(const Offer *p) {
+    const int4 t = __ldcg(reinterpret_cast<const int4 *>(p));
     Offer o;
-    asm volatile("ld.global.cg.v4.s32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(o.s), "=r"(o.w), "=r"(o.as), "=r"(o.au)
-                 : "l"(p)
-                 : "memory");
+    o.s = t.x;
+    o.w = t.y;
+    o.as = t.z;
+    o.au = t.w;
     return o;
 }
 
@@ -796,11 +801,10 @@ __global__ void k_level_begin(DevState *st, int level, Work w) {
     phase_level_begin<R, SUITOR, true>(st, level, w);
 }
 
-template <int R, int PASS>
-#ifndef KP_SUITOR_MIN_BLOCKS
-#define KP_SUITOR_MIN_BLOCKS 3   // resident blocks per SM the register budget must allow
-#endif
-__global__ void __launch_bounds__(MATCH_BLOCK, KP_SUITOR_MIN_BLOCKS) k_suitor(DevState *st, int level, Work w) {
+// MINB: resident blocks per SM the register budget must allow (the
+// suitor_blocks knob chooses 3 or 4 for the first pass; the parked passes use 3).
+template <int R, int PASS, int MINB = 3>
+__global__ void __launch_bounds__(MATCH_BLOCK, MINB) k_suitor(DevState *st, int level, Work w) {
     phase_suitor<R, PASS>(st, level, w);
 }
 

@@ -60,14 +60,19 @@ __device__ __forceinline__ void quotient_row_warp(int32_t u, int32_t pu, int32_t
     }
 }
 
-// Rows longer than QHUB_ROW are listed (hubs, hub_count) for k_quotient_hubs.
+// Rows longer than QHUB_ROW are listed (hubs, hub_count) for k_quotient_hubs,
+// the other rows longer than QROW (mids, mid_count) for k_quotient_mid, whose
+// warps take them one at a time: a warp here would walk the long rows of its
+// 32 nodes one after the other, and the warps holding several long rows of a
+// power-law graph would set the kernel's time.
 template <bool SMEM>
 __global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_acc(int32_t n, const int32_t *__restrict__ xadj,
                                                                const int32_t *__restrict__ adjncy,
                                                                const int32_t *__restrict__ ewgt,
                                                                const int32_t *__restrict__ part, int32_t k,
                                                                unsigned long long *gcells, int32_t *err,
-                                                               int32_t *hubs, int32_t *hub_count) {
+                                                               int32_t *hubs, int32_t *hub_count, int32_t *mids,
+                                                               int32_t *mid_count) {
     __shared__ unsigned long long s_cells[SMEM ? QSMEM_CELLS : 1];
     const int64_t kk = (int64_t)k * k;
     if (SMEM) {
@@ -133,20 +138,22 @@ __global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_acc(int32_t n, const 
                 }
             }
         }
-        // the long rows of this warp's 32 nodes, one after the other
-        unsigned longm = __ballot_sync(0xffffffffu, pu >= 0 && d > QROW);
-        while (longm) {
-            const int j = __ffs(longm) - 1;
-            longm &= longm - 1;
-            const int32_t uj = __shfl_sync(0xffffffffu, (int32_t)u, j);
-            const int32_t pj = __shfl_sync(0xffffffffu, pu, j);
-            const int32_t bj = __shfl_sync(0xffffffffu, beg, j);
-            const int32_t dj = __shfl_sync(0xffffffffu, d, j);
-            if (dj > QHUB_ROW) {   // a hub: one block, one pass over shared-memory sums
-                if (lane == 0) hubs[atomicAdd(hub_count, 1)] = uj;
-                continue;
-            }
-            quotient_row_warp(uj, pj, bj, bj + dj, adjncy, ewgt, part, k, cells, err);
+        // the long rows of this warp's 32 nodes go to their lists
+        // (warp-aggregated appends)
+        const bool hub = pu >= 0 && d > QHUB_ROW, mid = pu >= 0 && d > QROW && !hub;
+        unsigned m = __ballot_sync(0xffffffffu, hub);
+        if (m) {
+            int32_t base = 0;
+            if (lane == 0) base = atomicAdd(hub_count, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (hub) hubs[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)u;
+        }
+        m = __ballot_sync(0xffffffffu, mid);
+        if (m) {
+            int32_t base = 0;
+            if (lane == 0) base = atomicAdd(mid_count, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (mid) mids[base + __popc(m & ((1u << lane) - 1u))] = (int32_t)u;
         }
     }
     if (SMEM) {
@@ -186,6 +193,41 @@ __global__ void __launch_bounds__(QHUB_BLOCK) k_quotient_hubs(const int32_t *__r
         for (int32_t b = threadIdx.x; b < k; b += blockDim.x)
             if (s_bins[b]) atomicAdd(&gcells[(int64_t)pu * k + b], s_bins[b]);
         __syncthreads();
+    }
+}
+
+// The listed long rows (QROW < d <= QHUB_ROW), one warp per row taken from a
+// counter (cells per block in shared memory when k*k <= QSMEM_CELLS).
+template <bool SMEM>
+__global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_mid(const int32_t *__restrict__ xadj,
+                                                               const int32_t *__restrict__ adjncy,
+                                                               const int32_t *__restrict__ ewgt,
+                                                               const int32_t *__restrict__ part, int32_t k,
+                                                               const int32_t *__restrict__ mids,
+                                                               const int32_t *mid_count, int32_t *next,
+                                                               unsigned long long *gcells, int32_t *err) {
+    __shared__ unsigned long long s_cells[SMEM ? QSMEM_CELLS : 1];
+    const int64_t kk = (int64_t)k * k;
+    if (SMEM) {
+        for (int64_t i = threadIdx.x; i < kk; i += blockDim.x) s_cells[i] = 0;
+        __syncthreads();
+    }
+    unsigned long long *cells = SMEM ? s_cells : gcells;
+    const int lane = threadIdx.x & 31;
+    const int32_t count = *mid_count;
+    for (;;) {
+        int32_t i = 0;
+        if (lane == 0) i = atomicAdd(next, 1);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= count) break;
+        const int32_t u = mids[i];
+        const int32_t beg = xadj[u], end = xadj[u + 1];
+        quotient_row_warp(u, part[u], beg, end, adjncy, ewgt, part, k, cells, err);
+    }
+    if (SMEM) {
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < kk; i += blockDim.x)
+            if (s_cells[i]) atomicAdd(&gcells[i], s_cells[i]);
     }
 }
 
@@ -391,32 +433,43 @@ kp_status quotient_graph_impl(const kp_graph *g, const int32_t *part, int32_t k,
         return set_error(KP_ERR_INVALID, "null output");
     if (k > QUOTIENT_MAX_K) return set_error(KP_ERR_UNSUPPORTED, "quotient graph: k above 4096");
     unsigned long long *cells = nullptr;
-    int32_t *err = nullptr;   // [0] block id error, [1] hub rows listed
-    int32_t *hubs = nullptr;
+    int32_t *err = nullptr;   // [0] block id error, [1] hub rows, [2] long rows, [3] long rows taken
+    int32_t *hubs = nullptr, *mids = nullptr;
     long long *nnz_dev = nullptr;
+    const bool smem = (int64_t)k * k <= QSMEM_CELLS;
     KP_TRY(dev_alloc_n(&cells, (int64_t)k * k, s));
-    kp_status st = dev_alloc_n(&err, 2, s);
+    kp_status st = dev_alloc_n(&err, 4, s);
     if (st == KP_OK) st = dev_alloc_n(&nnz_dev, 1, s);
     if (st == KP_OK) st = dev_alloc_n(&hubs, (int64_t)g->nnz / QHUB_ROW + 1, s);
+    if (st == KP_OK) st = dev_alloc_n(&mids, (int64_t)g->nnz / (QROW + 1) + 1, s);
     auto done = [&](kp_status r) {
         dev_free(cells, s);
         dev_free(err, s);
         dev_free(nnz_dev, s);
         dev_free(hubs, s);
+        dev_free(mids, s);
         return r;
     };
     if (st != KP_OK) return done(st);
     if (cudaMemsetAsync(cells, 0, sizeof(unsigned long long) * (size_t)k * k, s) != cudaSuccess ||
-        cudaMemsetAsync(err, 0, 2 * sizeof(int32_t), s) != cudaSuccess ||
+        cudaMemsetAsync(err, 0, 4 * sizeof(int32_t), s) != cudaSuccess ||
         cudaMemsetAsync(q_xadj, 0, sizeof(int32_t), s) != cudaSuccess)
         return done(cuda_error(cudaGetLastError(), "clear"));
     if (g->n > 0) {
-        if ((int64_t)k * k <= QSMEM_CELLS)
+        if (smem)
             k_quotient_acc<true><<<grid_for(g->n), REFINE_BLOCK, 0, s>>>(g->n, g->xadj, g->adjncy, g->ewgt, part, k,
-                                                                         cells, err, hubs, err + 1);
+                                                                         cells, err, hubs, err + 1, mids, err + 2);
         else
             k_quotient_acc<false><<<grid_for(g->n), REFINE_BLOCK, 0, s>>>(g->n, g->xadj, g->adjncy, g->ewgt, part, k,
-                                                                          cells, err, hubs, err + 1);
+                                                                          cells, err, hubs, err + 1, mids, err + 2);
+        if (g->nnz > QROW) {
+            if (smem)
+                k_quotient_mid<true><<<num_sms() * 4, REFINE_BLOCK, 0, s>>>(g->xadj, g->adjncy, g->ewgt, part, k, mids,
+                                                                            err + 2, err + 3, cells, err);
+            else
+                k_quotient_mid<false><<<num_sms() * 8, REFINE_BLOCK, 0, s>>>(g->xadj, g->adjncy, g->ewgt, part, k, mids,
+                                                                             err + 2, err + 3, cells, err);
+        }
         if (g->nnz > QHUB_ROW)
             k_quotient_hubs<<<num_sms() * 2, QHUB_BLOCK, sizeof(unsigned long long) * (size_t)k, s>>>(
                 g->xadj, g->adjncy, g->ewgt, part, k, hubs, err + 1, cells, err);
