@@ -46,8 +46,9 @@ struct EvalAcc {
 constexpr int EVAL_BLOCK = 256;
 constexpr int BW_SMEM = 2048;   // block weights kept in shared memory up to this k
 constexpr int HIST_K = 256;     // warp groups sum a long row's connections in shared memory up to this k
-constexpr int HUB_ROW = 4096;   // longer rows (k <= HIST_K) go to a block each (k_cut_gain_hubs)
+constexpr int HUB_ROW = 4096;   // longer rows (k <= HUB_K) go to a block each (k_cut_gain_hubs)
 constexpr int HUB_BLOCK = 512;
+constexpr int HUB_K = 4096;     // the hub kernel's k connection sums in shared memory (32 KB)
 
 struct CutGainParams {
     int32_t n;
@@ -62,10 +63,14 @@ struct CutGainParams {
     int64_t *gain;
     int32_t *target;
     EvalAcc *acc;
-    // G = 32 kernels with k <= HIST_K: leave rows of more than HUB_ROW
+    // G = 32 kernels with k <= HUB_K: leave rows of more than hub_min
     // entries to k_cut_gain_hubs (the list kernel skips them in its list,
-    // the per-node kernel appends them to hub_list)
+    // the per-node kernel appends them to hub_list).  hub_min is HUB_ROW
+    // when a warp can sum a row in its shared-memory bins (k <= HIST_K),
+    // else 32: above that a warp would pass over the row once per adjacent
+    // block
     int32_t hub_defer = 0;
+    int32_t hub_min = HUB_ROW;
     int32_t *hub_list = nullptr;
 };
 
@@ -120,7 +125,7 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p, const 
         int32_t best = -1;
         long long best_conn = 0;
         // a hub left to the block kernel (its node weight is still added below)
-        const bool defer = HIST && use_hist && p.hub_defer && deg > HUB_ROW;
+        const bool defer = HIST && p.hub_defer && deg > p.hub_min;
         if (defer) {
             if (!FROM_LIST && gl == 0) p.hub_list[atomicAdd(&p.acc->long_count, 1)] = (int32_t)v;
         } else if (use_hist && deg > G) {
@@ -269,15 +274,15 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p, const 
             if (s_bw[i]) atomicAdd(&p.block_w[i], s_bw[i]);
 }
 
-// Rows of more than HUB_ROW entries (hubs of power-law graphs), one block
-// each, k <= HIST_K: all threads sum the row's connection to every block in
-// shared memory in one pass and the largest is taken (smallest block id on
-// ties).  The G = 32 kernels leave these rows to it (their node weights
-// stay there); the rows are those of `rows` [0, acc->long_count) with more
-// than HUB_ROW entries.
+// Rows of more than p.hub_min entries (hubs of power-law graphs; with
+// k > HIST_K every row longer than a warp), one block each, k <= HUB_K: all
+// threads sum the row's connection to every block in shared memory in one
+// pass and the largest is taken (smallest block id on ties).  The G = 32
+// kernels leave these rows to it (their node weights stay there); the rows
+// are those of `rows` [0, acc->long_count) with more than p.hub_min entries.
 __global__ void __launch_bounds__(HUB_BLOCK) k_cut_gain_hubs(CutGainParams p, const int32_t *rows) {
     constexpr int NW = HUB_BLOCK / 32;
-    __shared__ unsigned long long conn[HIST_K];
+    extern __shared__ unsigned long long conn[];   // p.k sums (launched with 8k bytes)
     __shared__ long long s_in[NW], s_tot[NW], s_bc[NW];
     __shared__ int32_t s_bb[NW];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(HUB_BLOCK) k_cut_gain_hubs(CutGainParams p, co
     for (int32_t li = blockIdx.x; li < count; li += gridDim.x) {
         const int32_t v = rows[li];
         const int32_t beg = p.xadj[v], end = p.xadj[v + 1];
-        if (end - beg <= HUB_ROW) continue;   // the same for the whole block
+        if (end - beg <= p.hub_min) continue;   // the same for the whole block
         const int32_t pv = p.part[v];
         for (int32_t b = threadIdx.x; b < p.k; b += HUB_BLOCK) conn[b] = 0;
         __syncthreads();
@@ -564,10 +569,11 @@ kp_status cut_gain_with(const kp_graph *g, const int32_t *part, int32_t k, doubl
         };
         // hub rows by a block each when a row list is at hand (the G = 32
         // kernels below leave them to k_cut_gain_hubs)
-        const bool hubs = long_rows && k <= HIST_K && (avg <= 12.0 || avg > 20.0);
+        const bool hubs = long_rows && k <= HUB_K && (avg <= 12.0 || avg > 20.0);
         p.hub_defer = hubs ? 1 : 0;
+        p.hub_min = k <= HIST_K ? HUB_ROW : 32;
         p.hub_list = long_rows;
-        if (long_rows && avg <= 12.0) {
+        if (long_rows && (avg <= 12.0 || avg > 20.0)) {
             // rows of up to 16 entries one thread each, the longer ones listed
             // for one warp each
             if (k <= BW_SMEM) k_cut_gain_rows<true><<<grid_for(1), EVAL_BLOCK, 0, s>>>(p, long_rows);
@@ -584,7 +590,8 @@ kp_status cut_gain_with(const kp_graph *g, const int32_t *part, int32_t k, doubl
             k_cut_gain<32><<<grid_for(32), EVAL_BLOCK, 0, s>>>(p);
         }
         KP_CUDA(cudaGetLastError());
-        if (hubs) k_cut_gain_hubs<<<num_sms() * 2, HUB_BLOCK, 0, s>>>(p, long_rows);
+        if (hubs)
+            k_cut_gain_hubs<<<num_sms() * 2, HUB_BLOCK, sizeof(unsigned long long) * (size_t)k, s>>>(p, long_rows);
         k_max_block<<<1, 1024, 0, s>>>(k, reinterpret_cast<const long long *>(out->block_w), acc);
         KP_CUDA(cudaGetLastError());
     }

@@ -1,6 +1,6 @@
 // Internal declarations shared by the library's translation units.
 // Device helpers: exact rating comparison, tie-break hash, a bounded grid
-// barrier for persistent kernels, and a three-phase device-wide scan.
+// barrier for persistent kernels, and the block-wide scan of the scans.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -235,12 +235,8 @@ __device__ __forceinline__ unsigned group_mask() {
 }
 
 // ---------------------------------------------------------------------------
-// three-phase device-wide exclusive scan over 64-bit values produced and
-// consumed by an operator:
-//   uint64_t Op::load(int64_t i)                          value of item i
-//   void     Op::store(int64_t i, uint64_t excl, uint64_t v)  prefix of item i
-//   void     Op::total(uint64_t t)                        sum of all items
-// Items are processed in order, so store() sees the exact prefix.
+// tiles of the device-wide scans (engine.cuh: single pass, decoupled
+// look-back) and the block-wide exclusive scan they use
 // ---------------------------------------------------------------------------
 constexpr int SCAN_BLOCK = 256;
 constexpr int SCAN_ITEMS = 8;

@@ -365,11 +365,13 @@ def test_cut_gain_many_k():
 def test_cut_gain_hub_rows():
     """Rows far longer than a warp: with k <= 256 a warp sums the row's
     connections in shared memory in one pass, above that it visits the
-    adjacent blocks one by one; both give the oracle's gains and targets
-    (largest connection, smallest block id on ties)."""
+    adjacent blocks one by one; rows above 4096 entries take a block each
+    with shared-memory sums up to k = 4096; all give the oracle's gains and
+    targets (largest connection, smallest block id on ties).  R-MAT's mean
+    degree is above 20: the thread-per-row kernel lists its long rows."""
     for g in [I.rmat(13, 6), hub_graph(3, 20000, 3), hub_graph(40, 5000, 2)]:
         dg = B().DeviceGraph.from_csr(g)
-        for k in [2, 64, 256, 257]:
+        for k in [2, 64, 256, 257, 1000, 4096, 4097]:
             check_eval(dg, g, I.random_partition(g.n, k, seed=k), k, 0.03)
             check_eval(dg, g, I.random_balanced_partition(g.n, k, seed=k + 5), k, 0.1)
 
