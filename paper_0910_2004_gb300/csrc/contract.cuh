@@ -859,6 +859,18 @@ static __device__ void phase_contract_rows32(DevState *st, int level, const Work
         contract_warp_reg(p, p.lists[6][li]);
 }
 
+// The next row of a block-per-row class, taken from a counter by the whole
+// block: the rows of power-law graphs differ in length by orders of
+// magnitude, so a fixed round-robin share would leave some blocks with
+// several long rows while the others wait.
+__device__ __forceinline__ int32_t next_row(int32_t *counter) {
+    __shared__ int32_t s_row;
+    __syncthreads();   // the previous row is finished and s_row read by every thread
+    if (threadIdx.x == 0) s_row = atomicAdd(counter, 1);
+    __syncthreads();
+    return s_row;
+}
+
 // MID: the classes of up to sort_shared_max entries (warps, blocks in shared
 // memory; class 1 with WARP32 always, without it only when the rows32
 // kernel leaves it); BIG: the radix class, RADIX_ITEMS entries per thread
@@ -886,7 +898,7 @@ static __device__ void phase_contract_overflow(DevState *st, int level, const Wo
         __syncthreads();
         {
             const int32_t count = p.ctr->nclass[3];
-            for (int32_t li = blockIdx.x; li < count; li += gridDim.x)
+            for (int32_t li = next_row(&p.ctr->class_next[0]); li < count; li = next_row(&p.ctr->class_next[0]))
                 contract_block_smem(p, p.lists[3][li], sm.mid.keys, sm.mid.vals, sm.mid.sums, sm.mid.s_red);
         }
         __syncthreads();
@@ -897,7 +909,7 @@ static __device__ void phase_contract_overflow(DevState *st, int level, const Wo
             int bits = 1;
             while (bits < 31 && ((int64_t)1 << bits) < (int64_t)p.cn) bits++;
             const int passes = (bits + p.radix_bits - 1) / p.radix_bits;
-            for (int32_t li = blockIdx.x; li < count; li += gridDim.x)
+            for (int32_t li = next_row(&p.ctr->class_next[1]); li < count; li = next_row(&p.ctr->class_next[1]))
                 contract_block_radix<RADIX_ITEMS>(p, p.lists[4][li], passes, sm.big);
         }
     }

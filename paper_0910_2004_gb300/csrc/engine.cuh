@@ -58,6 +58,7 @@ struct Counters {   // one per level, zeroed before the level runs
     unsigned long long searches;     // rating passes over a row
     unsigned long long failed_cas;   // lost proposal races
     unsigned long long start_next;   // proposals: next start node handed to a warp
+    int32_t class_next[2];           // contraction: next row of classes 3 and 4 handed to a block
 };
 
 struct DevLevel {
