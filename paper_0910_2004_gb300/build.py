@@ -20,8 +20,9 @@ SOURCES = ["capi.cu", "coarsen.cu", "match.cu", "contract.cu", "tail.cu", "evalu
 HEADERS = [os.path.join(CSRC, h) for h in ("kp_internal.cuh", "engine.cuh", "match.cuh", "gpa.cuh", "contract.cuh")] + [os.path.join(INCLUDE, "kp.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The persistent tail kernel reads data written earlier in the same launch by
-# other blocks: its unit serves every global load from L2 (coherent).
-PER_FILE = {"tail.cu": ["-Xptxas", "-dlcm=cg", "-DKP_COHERENT_LOADS"]}
+# other blocks: its unit serves every global load from L2 (coherent); it also
+# keeps the 128-bit rating compare only (see cmp_frac).
+PER_FILE = {"tail.cu": ["-Xptxas", "-dlcm=cg", "-DKP_COHERENT_LOADS", "-DKP_FRAC_WIDE_ONLY"]}
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
 

@@ -96,8 +96,18 @@ enum : int32_t {
 // ---------------------------------------------------------------------------
 // a/b against c/d by the 128-bit cross products a*d and c*b.  Numerators are
 // > 0 and denominators >= 0, so a zero denominator (rating +infinity) wins
-// against any finite rating and ties with another infinity.
+// against any finite rating and ties with another infinity.  When all four
+// fit in 32 bits (small weights: the common case), the products fit in 64
+// bits and are formed by single widening multiplies (not in the persistent
+// tail's unit, KP_FRAC_WIDE_ONLY: at its register cap the extra branch
+// measured slower there).
 __device__ __forceinline__ int cmp_frac(uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+#ifndef KP_FRAC_WIDE_ONLY
+    if (((a | b | c | d) >> 32) == 0) {
+        const uint64_t l = (uint64_t)(uint32_t)a * (uint32_t)d, r = (uint64_t)(uint32_t)c * (uint32_t)b;
+        return (l > r) - (l < r);
+    }
+#endif
     const uint64_t lh = __umul64hi(a, d), ll = a * d;
     const uint64_t rh = __umul64hi(c, b), rl = c * b;
     if (lh != rh) return lh > rh ? 1 : -1;

@@ -162,16 +162,17 @@ __device__ __forceinline__ bool eligible_at(const HashCtx &hc, int32_t cur, int3
     rating_ab<R>(wt, acur, so.au, cd.num, cd.den);
     cd.h = edge_hash_in(hc, cur, v);
     if (so.s < 0) return true;
-    // compare at v: the offer of cur against the standing offer of so.s
-    Cand a, b;
-    a.u = cur;
-    a.num = cd.num;
-    a.den = cd.den;
-    a.h = cd.h;
-    b.u = so.s;
-    rating_ab<R>(so.w, so.as, so.au, b.num, b.den);
-    b.h = edge_hash_in(hc, so.s, v);
-    return better(a, b, v);
+    // compare at v: the offer of cur against the standing offer of so.s (the
+    // standing edge's hash only when the ratings are equal)
+    uint64_t bnum, bden;
+    rating_ab<R>(so.w, so.as, so.au, bnum, bden);
+    const int c = cmp_frac(cd.num, cd.den, bnum, bden);
+    if (c != 0) return c > 0;
+    const uint64_t bh = edge_hash_in(hc, so.s, v);
+    if (cd.h != bh) return cd.h > bh;
+    const int32_t alo = min(v, cur), ahi = max(v, cur), blo = min(v, so.s), bhi = max(v, so.s);
+    if (alo != blo) return alo < blo;
+    return ahi < bhi;
 }
 
 // One thread's share of a search: the entries e0, e0 + STRIDE, ... < end of
