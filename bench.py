@@ -40,7 +40,7 @@ L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 # captures of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum
 # summed over the phase's launches); a phase without an entry reports traffic
 # null.  The summaries under profiles/ give the commands and the scaling.
-NCU_TRAFFIC = {("grid256", "match"): 4_260_000_000}
+NCU_TRAFFIC = {("grid256", "match"): 4_235_000_000}
 HBM_PEAK_FALLBACK = 6800.0
 
 
