@@ -18,7 +18,11 @@
  *    with the same weight, there are no self loops, omega > 0 and c >= 0.
  *    nnz = 2|E| directed entries.  Section 2 requires omega > 0, c >= 0.
  *  - Integer ranges: sum of c < 2^31, sum of omega over undirected edges
- *    < 2^31, nnz < 2^31.  Then every coarse weight fits in int32.
+ *    < 2^31.  Then every coarse weight fits in int32.  Entry offsets and
+ *    counts (xadj, nnz) have the type kp_eoff below: int32 in the default
+ *    build (nnz < 2^31), int64 in the wide build, where nnz is bounded only
+ *    by the weight range (omega >= 1, so nnz = 2|E| < 2^32) and by device
+ *    memory (Section 5.2's static adjacency array with 64-bit offsets).
  *  - Pointers are DEVICE pointers unless a parameter says "host".
  *    Every call is ordered on the stream passed in (NULL = legacy default
  *    stream); calls that return host scalars synchronise that stream.
@@ -36,6 +40,19 @@
 
 #ifdef __cplusplus
 extern "C" {
+#endif
+
+/* Entry offsets and entry counts.  The library is built twice from the same
+ * sources: libkp (kp_eoff = int32_t) and libkp64 (KP_WIDE_OFFSETS defined,
+ * kp_eoff = int64_t).  A caller compiles against this header with the macro
+ * of the library it links (the struct layouts that hold a kp_eoff differ);
+ * kp_offset_bits() returns the linked library's width. */
+#ifdef KP_WIDE_OFFSETS
+typedef int64_t kp_eoff;
+#define KP_OFFSET_BITS 64
+#else
+typedef int32_t kp_eoff;
+#define KP_OFFSET_BITS 32
 #endif
 
 /* A CUDA stream (cudaStream_t / CUstream); NULL is the legacy default stream. */
@@ -73,8 +90,8 @@ typedef enum {
  *   vwgt[n] c. */
 typedef struct {
     int32_t n;
-    int32_t nnz;
-    const int32_t *xadj;
+    kp_eoff nnz;
+    const kp_eoff *xadj;
     const int32_t *adjncy;
     const int32_t *ewgt;
     const int32_t *vwgt;
@@ -624,6 +641,11 @@ const char *kp_last_error(void);
 
 /* Library version string. */
 const char *kp_version(void);
+
+/* Width in bits of kp_eoff in the linked library: 32 (libkp) or 64
+ * (libkp64).  A caller whose KP_OFFSET_BITS differs must not pass it a
+ * kp_graph. */
+int32_t kp_offset_bits(void);
 
 #ifdef __cplusplus
 }

@@ -60,9 +60,9 @@ def lib():
         if _lib is None:
             L = ctypes.CDLL(build())
             i32, i64, u64, c_int = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int
-            L.or_validate.argtypes = [i32, i64, _i32p, _i32p, _i32p, _i32p]
+            L.or_validate.argtypes = [i32, i64, i64, _i64p, _i32p, _i32p, _i32p]
             L.or_validate.restype = c_int
-            L.or_out_weight.argtypes = [i32, _i32p, _i32p, _i64p]
+            L.or_out_weight.argtypes = [i32, _i64p, _i32p, _i64p]
             L.or_out_weight.restype = None
             L.or_frac_cmp.argtypes = [u64, u64, u64, u64]
             L.or_frac_cmp.restype = c_int
@@ -72,21 +72,27 @@ def lib():
             L.or_edge_hash.restype = u64
             L.or_edge_order.argtypes = [c_int, u64, _i32p, _i64p, i32, i32, i32, i32, i32, i32]
             L.or_edge_order.restype = c_int
-            L.or_greedy_matching.argtypes = [i32, _i32p, _i32p, _i32p, _i32p, c_int, u64, _i32p]
+            L.or_greedy_matching.argtypes = [i32, _i64p, _i32p, _i32p, _i32p, c_int, u64, _i32p]
             L.or_greedy_matching.restype = i64
-            L.or_handshake_matching.argtypes = [i32, _i32p, _i32p, _i32p, _i32p, c_int, u64, _i32p,
+            L.or_handshake_matching.argtypes = [i32, _i64p, _i32p, _i32p, _i32p, c_int, u64, _i32p,
                                                 ctypes.POINTER(i32), _i32p]
             L.or_handshake_matching.restype = i64
-            L.or_gpa_matching.argtypes = [i32, _i32p, _i32p, _i32p, _i32p, c_int, u64, _i32p, _i32p]
+            L.or_gpa_matching.argtypes = [i32, _i64p, _i32p, _i32p, _i32p, c_int, u64, _i32p, _i32p]
             L.or_gpa_matching.restype = i64
-            L.or_check_greedy_matching.argtypes = [i32, _i32p, _i32p, _i32p, _i32p, c_int, u64, _i32p]
+            L.or_check_greedy_matching.argtypes = [i32, _i64p, _i32p, _i32p, _i32p, c_int, u64, _i32p]
             L.or_check_greedy_matching.restype = i64
-            L.or_contract.argtypes = [i32, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p,
-                                      ctypes.POINTER(i64), _i32p, _i32p, _i32p, _i32p]
+            L.or_check_greedy_matching_at.argtypes = [i32, _i64p, _i32p, _i32p, _i32p, c_int, u64, _i32p,
+                                                      i64, _i32p]
+            L.or_check_greedy_matching_at.restype = i64
+            L.or_coarse_row.argtypes = [_i64p, _i32p, _i32p, _i32p, _i32p, i32, i32, i32,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(i64)]
+            L.or_coarse_row.restype = i32
+            L.or_contract.argtypes = [i32, _i64p, _i32p, _i32p, _i32p, _i32p, _i32p,
+                                      ctypes.POINTER(i64), _i64p, _i32p, _i32p, _i32p]
             L.or_contract.restype = i32
             L.or_project_level.argtypes = [i32, _i32p, _i32p, _i32p]
             L.or_project_level.restype = None
-            L.or_cut_gain.argtypes = [i32, _i32p, _i32p, _i32p, _i32p, _i32p, i32,
+            L.or_cut_gain.argtypes = [i32, _i64p, _i32p, _i32p, _i32p, _i32p, i32,
                                       ctypes.POINTER(i64), _i64p, _i64p, _i32p]
             L.or_cut_gain.restype = c_int
             _lib = L
@@ -95,7 +101,8 @@ def lib():
 
 @dataclass
 class Level:
-    """One graph of the hierarchy as a symmetric sorted CSR (Section 5.2)."""
+    """One graph of the hierarchy as a symmetric sorted CSR (Section 5.2);
+    row offsets int64 (graphs of 2^31 entries or more fit)."""
     xadj: np.ndarray
     adjncy: np.ndarray
     ewgt: np.ndarray
@@ -119,15 +126,16 @@ class Hierarchy:
 
 def _as_level(g) -> Level:
     c = np.ascontiguousarray
-    return Level(c(g.xadj, dtype=np.int32), c(g.adjncy, dtype=np.int32),
+    return Level(c(g.xadj, dtype=np.int64), c(g.adjncy, dtype=np.int32),
                  c(g.ewgt, dtype=np.int32), c(g.vwgt, dtype=np.int32))
 
 
-def validate(g) -> int:
+def validate(g, nnz_limit: int = 1 << 31) -> int:
     """0 = valid, 1 = invalid (malformed/asymmetric/unsorted CSR, self loop,
-    omega <= 0, c < 0: Section 2), 2 = outside the integer ranges."""
+    omega <= 0, c < 0: Section 2), 2 = outside the integer ranges (nnz must
+    stay below nnz_limit: 2^31 with 32-bit offsets, 2^32 with 64-bit ones)."""
     g = _as_level(g)
-    return lib().or_validate(g.n, g.nnz, g.xadj, g.adjncy, g.ewgt, g.vwgt)
+    return lib().or_validate(g.n, g.nnz, nnz_limit, g.xadj, g.adjncy, g.ewgt, g.vwgt)
 
 
 def out_weight(g) -> np.ndarray:
@@ -204,13 +212,44 @@ def check_greedy_matching(g, rating: str, seed: int, match) -> int:
                                               RATINGS[rating], seed, m))
 
 
+def check_greedy_matching_at(g, rating: str, seed: int, match, nodes) -> int:
+    """check_greedy_matching restricted to the listed nodes (large graphs):
+    -1 iff every listed node passes."""
+    g = _as_level(g)
+    m = np.ascontiguousarray(match, dtype=np.int32)
+    nd = np.ascontiguousarray(nodes, dtype=np.int32)
+    return int(lib().or_check_greedy_matching_at(g.n, g.xadj, g.adjncy, g.ewgt, g.vwgt, RATINGS[rating], seed, m,
+                                                 nd.shape[0], nd))
+
+
+def coarse_rows(g, mp, rows):
+    """Rows of the coarse nodes x with members a, b (b = -1: one member)
+    under the map mp (Section 2), for rows = [(x, a, b), ...]: a list of
+    (neighbours, weights, c)."""
+    g = _as_level(g)
+    mp = np.ascontiguousarray(mp, dtype=np.int32)
+    res = []
+    for x, a, b in rows:
+        a, b = int(a), int(b)
+        cap = int(g.xadj[a + 1] - g.xadj[a]) + (int(g.xadj[b + 1] - g.xadj[b]) if b >= 0 else 0)
+        adj = np.empty(max(cap, 1), dtype=np.int32)
+        w = np.empty(max(cap, 1), dtype=np.int32)
+        c = ctypes.c_int64(0)
+        k = lib().or_coarse_row(g.xadj, g.adjncy, g.ewgt, g.vwgt, mp, int(x), a, b, adj.ctypes.data,
+                                w.ctypes.data, ctypes.byref(c))
+        if k < 0:
+            raise MemoryError("oracle coarse row")
+        res.append((adj[:k], w[:k], int(c.value)))
+    return res
+
+
 def contract(g, match):
     """Contract all matched edges (Section 2).  Returns (coarse Level, map)."""
     g = _as_level(g)
     match = np.ascontiguousarray(match, dtype=np.int32)
     n = g.n
     mp = np.empty(n, dtype=np.int32)
-    cxadj = np.empty(n + 1, dtype=np.int32)
+    cxadj = np.empty(n + 1, dtype=np.int64)
     cadj = np.empty(max(g.nnz, 1), dtype=np.int32)
     cew = np.empty(max(g.nnz, 1), dtype=np.int32)
     cvw = np.empty(max(n, 1), dtype=np.int32)
@@ -220,7 +259,8 @@ def contract(g, match):
     if cn < 0:
         raise MemoryError("oracle contraction")
     k = int(cnnz.value)
-    return Level(cxadj[:cn + 1].copy(), cadj[:k].copy(), cew[:k].copy(), cvw[:cn].copy()), mp
+    # views of the first cn / k elements (no second copy of large levels)
+    return Level(cxadj[:cn + 1], cadj[:k], cew[:k], cvw[:cn]), mp
 
 
 def coarsen(g, rating: str, seed: int, stop_size: int, max_levels: int = 64,

@@ -46,28 +46,29 @@
 
 /* Returns OR_OK, OR_INVALID (malformed CSR, asymmetric, unsorted row,
  * self loop, omega <= 0, c < 0) or OR_OVERFLOW (sum c >= 2^31, sum of
- * undirected edge weights >= 2^31, nnz >= 2^31). */
-int or_validate(int32_t n, int64_t nnz, const int32_t *xadj, const int32_t *adjncy,
+ * undirected edge weights >= 2^31, nnz >= nnz_limit: the offset width's
+ * range, 2^31 for 32-bit offsets). */
+int or_validate(int32_t n, int64_t nnz, int64_t nnz_limit, const int64_t *xadj, const int32_t *adjncy,
                 const int32_t *ewgt, const int32_t *vwgt)
 {
     if (n < 0 || nnz < 0) return OR_INVALID;
-    if (nnz >= ((int64_t)1 << 31)) return OR_OVERFLOW;
-    if (xadj[0] != 0 || (int64_t)xadj[n] != nnz) return OR_INVALID;
+    if (nnz >= nnz_limit) return OR_OVERFLOW;
+    if (xadj[0] != 0 || xadj[n] != nnz) return OR_INVALID;
     for (int32_t v = 0; v < n; v++)
         if (xadj[v + 1] < xadj[v]) return OR_INVALID;
     int64_t csum = 0, wsum = 0;
     for (int32_t v = 0; v < n; v++) {
         if (vwgt[v] < 0) return OR_INVALID;
         csum += vwgt[v];
-        for (int32_t e = xadj[v]; e < xadj[v + 1]; e++) {
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) {
             int32_t u = adjncy[e];
             if (u < 0 || u >= n || u == v) return OR_INVALID;
             if (ewgt[e] <= 0) return OR_INVALID;
             if (e > xadj[v] && adjncy[e - 1] >= u) return OR_INVALID;
             /* the reverse entry (u, v) must exist with the same weight */
-            int32_t lo = xadj[u], hi = xadj[u + 1] - 1, found = -1;
+            int64_t lo = xadj[u], hi = xadj[u + 1] - 1, found = -1;
             while (lo <= hi) {
-                int32_t mid = lo + (hi - lo) / 2;
+                int64_t mid = lo + (hi - lo) / 2;
                 if (adjncy[mid] == v) { found = mid; break; }
                 if (adjncy[mid] < v) lo = mid + 1; else hi = mid - 1;
             }
@@ -84,11 +85,11 @@ int or_validate(int32_t n, int64_t nnz, const int32_t *xadj, const int32_t *adjn
 /* ------------------------------------------------------------------------ */
 
 /* Out(v) = sum of omega({v,x}) over the neighbours x of v (Section 3.1). */
-void or_out_weight(int32_t n, const int32_t *xadj, const int32_t *ewgt, int64_t *out)
+void or_out_weight(int32_t n, const int64_t *xadj, const int32_t *ewgt, int64_t *out)
 {
     for (int32_t v = 0; v < n; v++) {
         int64_t s = 0;
-        for (int32_t e = xadj[v]; e < xadj[v + 1]; e++) s += ewgt[e];
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) s += ewgt[e];
         out[v] = s;
     }
 }
@@ -202,11 +203,11 @@ static int or_cmp_desc(const void *pa, const void *pb)
 /* Greedy matching (Section 3.2): scan the edges from heaviest to lightest
  * under the strict order and take an edge when both ends are still free.
  * match[v] = partner, or v when v stays unmatched.  Returns |M|, or -1.   */
-int64_t or_greedy_matching(int32_t n, const int32_t *xadj, const int32_t *adjncy,
+int64_t or_greedy_matching(int32_t n, const int64_t *xadj, const int32_t *adjncy,
                            const int32_t *ewgt, const int32_t *vwgt, int rating,
                            uint64_t seed, int32_t *match)
 {
-    int64_t m = (int64_t)xadj[n] / 2;
+    int64_t m = xadj[n] / 2;
     or_edge *edges = (or_edge *)malloc(sizeof(or_edge) * (size_t)(m > 0 ? m : 1));
     int64_t *out = NULL;
     if (!edges) return -1;
@@ -217,7 +218,7 @@ int64_t or_greedy_matching(int32_t n, const int32_t *xadj, const int32_t *adjncy
     }
     int64_t k = 0;
     for (int32_t v = 0; v < n; v++)
-        for (int32_t e = xadj[v]; e < xadj[v + 1]; e++)
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++)
             if (adjncy[e] > v)
                 or_make_edge(&edges[k++], rating, seed, v, adjncy[e], ewgt[e], vwgt, out);
     qsort(edges, (size_t)k, sizeof(or_edge), or_cmp_desc);
@@ -242,7 +243,7 @@ int64_t or_greedy_matching(int32_t n, const int32_t *xadj, const int32_t *adjncy
  * edge has two free ends.  cand1 (optional) receives the first round's picks
  * (-1 for a node with no neighbour).  Returns |M|, or -1 on allocation
  * failure; *rounds receives the number of rounds that matched something. */
-int64_t or_handshake_matching(int32_t n, const int32_t *xadj, const int32_t *adjncy,
+int64_t or_handshake_matching(int32_t n, const int64_t *xadj, const int32_t *adjncy,
                               const int32_t *ewgt, const int32_t *vwgt, int rating,
                               uint64_t seed, int32_t *match, int32_t *rounds, int32_t *cand1)
 {
@@ -263,7 +264,7 @@ int64_t or_handshake_matching(int32_t n, const int32_t *xadj, const int32_t *adj
             cand[v] = -1;
             if (match[v] != -1) continue;
             or_edge best, cur;
-            for (int32_t e = xadj[v]; e < xadj[v + 1]; e++) {
+            for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) {
                 int32_t u = adjncy[e];
                 if (match[u] != -1) continue;
                 or_make_edge(&cur, rating, seed, v, u, ewgt[e], vwgt, out);
@@ -351,11 +352,11 @@ static double or_path_dp(int32_t L, const int32_t *x, const double *w, double *b
  * match[v] = partner, or v when v stays unmatched; nbr2 (may be NULL)
  * receives the two collected neighbours of every node (-1 where fewer).
  * Returns |M|, or -1 on allocation failure. */
-int64_t or_gpa_matching(int32_t n, const int32_t *xadj, const int32_t *adjncy,
+int64_t or_gpa_matching(int32_t n, const int64_t *xadj, const int32_t *adjncy,
                         const int32_t *ewgt, const int32_t *vwgt, int rating,
                         uint64_t seed, int32_t *match, int32_t *nbr2)
 {
-    int64_t m = (int64_t)xadj[n] / 2;
+    int64_t m = xadj[n] / 2;
     size_t nn = (size_t)(n > 0 ? n : 1);
     or_edge *edges = (or_edge *)malloc(sizeof(or_edge) * (size_t)(m > 0 ? m : 1));
     int64_t *out = NULL;
@@ -378,7 +379,7 @@ int64_t or_gpa_matching(int32_t n, const int32_t *xadj, const int32_t *adjncy,
     }
     int64_t k = 0;
     for (int32_t v = 0; v < n; v++)
-        for (int32_t e = xadj[v]; e < xadj[v + 1]; e++)
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++)
             if (adjncy[e] > v)
                 or_make_edge(&edges[k++], rating, seed, v, adjncy[e], ewgt[e], vwgt, out);
     qsort(edges, (size_t)k, sizeof(or_edge), or_cmp_desc);
@@ -480,7 +481,7 @@ done:
  * with no such neighbour would have been taken by Greedy.)
  * Returns -1 if match[] passes, else the smallest node at which a check fails
  * (asymmetric match, matched non-edge, or an undominated non-matching edge). */
-int64_t or_check_greedy_matching(int32_t n, const int32_t *xadj, const int32_t *adjncy,
+int64_t or_check_greedy_matching(int32_t n, const int64_t *xadj, const int32_t *adjncy,
                                  const int32_t *ewgt, const int32_t *vwgt, int rating,
                                  uint64_t seed, const int32_t *match)
 {
@@ -499,13 +500,13 @@ int64_t or_check_greedy_matching(int32_t n, const int32_t *xadj, const int32_t *
         if (p < 0 || p >= n || match[p] != v) { bad = v; break; }
         if (p == v) continue;
         int32_t w = -1;
-        for (int32_t e = xadj[v]; e < xadj[v + 1]; e++)
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++)
             if (adjncy[e] == p) w = ewgt[e];
         if (w < 0) { bad = v; break; }
         or_make_edge(&medge[v], rating, seed, v, p, w, vwgt, out);
     }
     for (int32_t v = 0; v < n && bad < 0; v++) {
-        for (int32_t e = xadj[v]; e < xadj[v + 1]; e++) {
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) {
             int32_t u = adjncy[e];
             if (match[v] == u) continue;
             or_edge cur;
@@ -517,6 +518,62 @@ int64_t or_check_greedy_matching(int32_t n, const int32_t *xadj, const int32_t *
         }
     }
     free(medge);
+    free(out);
+    return bad;
+}
+
+/* The same characterisation checked only at the listed nodes (graphs too
+ * large for a whole pass): v's match is symmetric and an edge, and every edge
+ * of v outside M is dominated by the matched edge of v or of its other end.
+ * The matched edge of a node is looked up when needed (no n-sized table);
+ * Out (innerOuter) is computed for the whole graph.  Returns -1 if every
+ * listed node passes, else the first listed node that fails. */
+static int or_matched_edge(const int64_t *xadj, const int32_t *adjncy, const int32_t *ewgt,
+                           const int32_t *vwgt, const int64_t *out, int rating, uint64_t seed,
+                           int32_t n, const int32_t *match, int32_t v, or_edge *me)
+{
+    int32_t p = match[v];
+    if (p < 0 || p >= n || match[p] != v) return -1;
+    if (p == v) return 0;
+    int32_t w = -1;
+    for (int64_t e = xadj[v]; e < xadj[v + 1]; e++)
+        if (adjncy[e] == p) w = ewgt[e];
+    if (w < 0) return -1;
+    or_make_edge(me, rating, seed, v, p, w, vwgt, out);
+    return 1;
+}
+
+int64_t or_check_greedy_matching_at(int32_t n, const int64_t *xadj, const int32_t *adjncy,
+                                    const int32_t *ewgt, const int32_t *vwgt, int rating,
+                                    uint64_t seed, const int32_t *match, int64_t count,
+                                    const int32_t *nodes)
+{
+    int64_t *out = NULL;
+    if (rating == RATING_INNER_OUTER) {
+        out = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+        if (!out) return -2;
+        or_out_weight(n, xadj, ewgt, out);
+    }
+    int64_t bad = -1;
+    for (int64_t i = 0; i < count && bad < 0; i++) {
+        int32_t v = nodes[i];
+        if (v < 0 || v >= n) { bad = v; break; }
+        or_edge mv;
+        int hv = or_matched_edge(xadj, adjncy, ewgt, vwgt, out, rating, seed, n, match, v, &mv);
+        if (hv < 0) { bad = v; break; }
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) {
+            int32_t u = adjncy[e];
+            if (match[v] == u) continue;
+            or_edge cur, mu;
+            or_make_edge(&cur, rating, seed, v, u, ewgt[e], vwgt, out);
+            int hu = or_matched_edge(xadj, adjncy, ewgt, vwgt, out, rating, seed, n, match, u, &mu);
+            if (hu < 0) { bad = v; break; }
+            int dominated = 0;
+            if (hv > 0 && or_edge_better(&mv, &cur) > 0) dominated = 1;
+            if (hu > 0 && or_edge_better(&mu, &cur) > 0) dominated = 1;
+            if (!dominated) { bad = v; break; }
+        }
+    }
     free(out);
     return bad;
 }
@@ -541,9 +598,9 @@ static int or_cmp_target(const void *pa, const void *pb)
  * Outputs (caller-allocated, sizes <= the fine ones): map[n], cxadj[cn+1],
  * cadjncy/cewgt[cnnz], cvwgt[cn].  Returns cn, or -1 on allocation failure;
  * *cnnz receives the coarse entry count. */
-int32_t or_contract(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *ewgt,
+int32_t or_contract(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *ewgt,
                     const int32_t *vwgt, const int32_t *match, int32_t *map, int64_t *cnnz,
-                    int32_t *cxadj, int32_t *cadjncy, int32_t *cewgt, int32_t *cvwgt)
+                    int64_t *cxadj, int32_t *cadjncy, int32_t *cewgt, int32_t *cvwgt)
 {
     /* coarse ids: rank of the representative in fine-id order */
     int32_t cn = 0;
@@ -560,7 +617,7 @@ int32_t or_contract(int32_t n, const int32_t *xadj, const int32_t *adjncy, const
     int32_t *second = (int32_t *)malloc(sizeof(int32_t) * (size_t)(cn > 0 ? cn : 1));
     int32_t maxdeg = 0;
     for (int32_t v = 0; v < n; v++)
-        if (xadj[v + 1] - xadj[v] > maxdeg) maxdeg = xadj[v + 1] - xadj[v];
+        if (xadj[v + 1] - xadj[v] > maxdeg) maxdeg = (int32_t)(xadj[v + 1] - xadj[v]);
     or_entry *buf = (or_entry *)malloc(sizeof(or_entry) * (size_t)(2 * maxdeg + 1));
     if (!first || !second || !buf) { free(first); free(second); free(buf); return -1; }
     for (int32_t v = 0; v < n; v++) {
@@ -577,7 +634,7 @@ int32_t or_contract(int32_t n, const int32_t *xadj, const int32_t *adjncy, const
             int32_t v = mem[i];
             if (v < 0) continue;
             c += vwgt[v];
-            for (int32_t e = xadj[v]; e < xadj[v + 1]; e++) {
+            for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) {
                 int32_t t = map[adjncy[e]];
                 if (t == x) continue;            /* the contracted edge */
                 buf[len].t = t;
@@ -596,13 +653,56 @@ int32_t or_contract(int32_t n, const int32_t *xadj, const int32_t *adjncy, const
             pos++;
             i = j;
         }
-        cxadj[x + 1] = (int32_t)pos;
+        cxadj[x + 1] = pos;
     }
     *cnnz = pos;
     free(first);
     free(second);
     free(buf);
     return cn;
+}
+
+/* One coarse node x of the contraction, from its members a and b (b = -1:
+ * x has one member) and the map of every fine node: the images of the
+ * members' neighbours other than x itself, equal images merged with summed
+ * weights, in ascending order; *c = c(a) + c(b) (Section 2).  cadjncy and
+ * cewgt hold deg(a) + deg(b) entries.  Returns the row's length, or -1 on
+ * allocation failure. */
+int32_t or_coarse_row(const int64_t *xadj, const int32_t *adjncy, const int32_t *ewgt, const int32_t *vwgt,
+                      const int32_t *map, int32_t x, int32_t a, int32_t b, int32_t *cadjncy, int32_t *cewgt,
+                      int64_t *c)
+{
+    int32_t mem[2] = { a, b };
+    int64_t cap = (xadj[a + 1] - xadj[a]) + (b >= 0 ? xadj[b + 1] - xadj[b] : 0);
+    or_entry *buf = (or_entry *)malloc(sizeof(or_entry) * (size_t)(cap > 0 ? cap : 1));
+    if (!buf) return -1;
+    int32_t len = 0;
+    *c = 0;
+    for (int i = 0; i < 2; i++) {
+        int32_t v = mem[i];
+        if (v < 0) continue;
+        *c += vwgt[v];
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) {
+            int32_t t = map[adjncy[e]];
+            if (t == x) continue;
+            buf[len].t = t;
+            buf[len].w = ewgt[e];
+            len++;
+        }
+    }
+    qsort(buf, (size_t)len, sizeof(or_entry), or_cmp_target);
+    int32_t k = 0;
+    for (int32_t i = 0; i < len;) {
+        int32_t j = i;
+        int64_t w = 0;
+        while (j < len && buf[j].t == buf[i].t) { w += buf[j].w; j++; }
+        cadjncy[k] = buf[i].t;
+        cewgt[k] = (int32_t)w;
+        k++;
+        i = j;
+    }
+    free(buf);
+    return k;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -625,7 +725,7 @@ void or_project_level(int32_t n_fine, const int32_t *map, const int32_t *coarse_
  *              with the largest connection (smallest id on ties); a node with
  *              no neighbour in another block gets target -1 and gain -int(v).
  * Returns OR_OK, or OR_INVALID if a block id is outside [0,k). */
-int or_cut_gain(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int32_t *ewgt,
+int or_cut_gain(int32_t n, const int64_t *xadj, const int32_t *adjncy, const int32_t *ewgt,
                 const int32_t *vwgt, const int32_t *part, int32_t k, int64_t *cut,
                 int64_t *block_w, int64_t *gain, int32_t *target)
 {
@@ -636,23 +736,23 @@ int or_cut_gain(int32_t n, const int32_t *xadj, const int32_t *adjncy, const int
     for (int32_t v = 0; v < n; v++) block_w[part[v]] += vwgt[v];
     int64_t c = 0;
     for (int32_t v = 0; v < n; v++)
-        for (int32_t e = xadj[v]; e < xadj[v + 1]; e++)
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++)
             if (adjncy[e] > v && part[adjncy[e]] != part[v]) c += ewgt[e];
     *cut = c;
     int64_t *conn = (int64_t *)calloc((size_t)k, sizeof(int64_t));
     if (!conn) return OR_NOMEM;
     for (int32_t v = 0; v < n; v++) {
-        for (int32_t e = xadj[v]; e < xadj[v + 1]; e++) conn[part[adjncy[e]]] += ewgt[e];
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) conn[part[adjncy[e]]] += ewgt[e];
         int64_t internal = conn[part[v]];
         int32_t best = -1;
-        for (int32_t e = xadj[v]; e < xadj[v + 1]; e++) {
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) {
             int32_t b = part[adjncy[e]];
             if (b == part[v]) continue;
             if (best == -1 || conn[b] > conn[best] || (conn[b] == conn[best] && b < best)) best = b;
         }
         target[v] = best;
         gain[v] = (best == -1 ? 0 : conn[best]) - internal;
-        for (int32_t e = xadj[v]; e < xadj[v + 1]; e++) conn[part[adjncy[e]]] = 0;
+        for (int64_t e = xadj[v]; e < xadj[v + 1]; e++) conn[part[adjncy[e]]] = 0;
     }
     free(conn);
     return OR_OK;

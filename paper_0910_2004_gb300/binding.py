@@ -1,9 +1,12 @@
 """Thin ctypes binding of the C ABI in include/kp.h (argument marshalling only).
 
-Every computation runs in the CUDA library libkp.so.  The functions named
-kp_* mirror the C entry points one to one; the helpers below them only turn
-torch CUDA tensors into the plain pointers and sizes the ABI takes.  If the
-library has not been built, every call raises: there is no CPU fallback.
+Every computation runs in the CUDA library libkp.so, or libkp64.so when the
+environment sets KP_OFFSET_BITS=64 before this module is imported (64-bit
+entry offsets: graphs of 2^31 entries or more; kp_graph then holds an int64
+nnz and int64 row offsets, as KP_WIDE_OFFSETS makes it in C).  The functions
+named kp_* mirror the C entry points one to one; the helpers below them only
+turn torch CUDA tensors into the plain pointers and sizes the ABI takes.  If
+the library has not been built, every call raises: there is no CPU fallback.
 """
 from __future__ import annotations
 
@@ -14,7 +17,10 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libkp.so")
+OFFSET_BITS = 64 if os.environ.get("KP_OFFSET_BITS", "32") == "64" else 32
+LIB_PATH = os.path.join(HERE, "_build", "libkp64.so" if OFFSET_BITS == 64 else "libkp.so")
+XADJ_NP = np.int64 if OFFSET_BITS == 64 else np.int32   # row offsets (kp_eoff)
+XADJ_TYPESTR = "<i8" if OFFSET_BITS == 64 else "<i4"
 
 KP_CUT_GAIN_NOALLOC_MAX_K = 16384
 KP_REQUEST_BORROW = 1
@@ -35,7 +41,7 @@ EXPORTED = ["kp_options_default", "kp_coarsen", "kp_hierarchy_num_levels", "kp_h
             "kp_server_release", "kp_server_cancel", "kp_server_destroy", "kp_autotune",
             "kp_test_fail_allocation", "kp_test_device_bytes_in_use", "kp_plan_create", "kp_plan_run",
             "kp_plan_destroy", "kp_quotient_graph", "kp_boundary_band", "kp_hierarchy_save", "kp_hierarchy_load",
-            "kp_last_error", "kp_version"]
+            "kp_last_error", "kp_version", "kp_offset_bits"]
 
 
 class KpError(RuntimeError):
@@ -45,8 +51,11 @@ class KpError(RuntimeError):
         super().__init__(f"{where}: {name}: {msg}")
 
 
+_c_eoff = ctypes.c_int64 if OFFSET_BITS == 64 else ctypes.c_int32
+
+
 class kp_graph(ctypes.Structure):
-    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int32), ("xadj", ctypes.c_void_p),
+    _fields_ = [("n", ctypes.c_int32), ("nnz", _c_eoff), ("xadj", ctypes.c_void_p),
                 ("adjncy", ctypes.c_void_p), ("ewgt", ctypes.c_void_p), ("vwgt", ctypes.c_void_p)]
 
 
@@ -197,6 +206,10 @@ def load(path: str = LIB_PATH):
         L.kp_last_error.restype = ctypes.c_char_p
         L.kp_version.argtypes = []
         L.kp_version.restype = ctypes.c_char_p
+        L.kp_offset_bits.argtypes = []
+        L.kp_offset_bits.restype = ctypes.c_int32
+        if L.kp_offset_bits() != OFFSET_BITS:
+            raise RuntimeError(f"{path} has {L.kp_offset_bits()}-bit offsets, the binding {OFFSET_BITS}-bit")
         _lib = L
         return L
 
@@ -464,17 +477,23 @@ def device_view(ptr: int, n: int, dtype: str = "<i4"):
 
 
 class DeviceGraph:
-    """A CSR graph held in torch CUDA tensors (int32), with its kp_graph."""
+    """A CSR graph held in torch CUDA tensors (int32; the row offsets in the
+    library's offset width), with its kp_graph."""
 
     def __init__(self, xadj, adjncy, ewgt, vwgt):
         torch = _torch()
         dev = torch.device("cuda")
-        self.xadj = torch.as_tensor(np.asarray(xadj, dtype=np.int32)).to(dev) if not torch.is_tensor(xadj) else xadj
+        xt = torch.int64 if OFFSET_BITS == 64 else torch.int32
+        if torch.is_tensor(xadj):
+            self.xadj = xadj if xadj.dtype == xt else xadj.to(xt).contiguous()
+        else:
+            self.xadj = torch.as_tensor(np.asarray(xadj, dtype=XADJ_NP)).to(dev)
         self.adjncy = torch.as_tensor(np.asarray(adjncy, dtype=np.int32)).to(dev) if not torch.is_tensor(adjncy) else adjncy
         self.ewgt = torch.as_tensor(np.asarray(ewgt, dtype=np.int32)).to(dev) if not torch.is_tensor(ewgt) else ewgt
         self.vwgt = torch.as_tensor(np.asarray(vwgt, dtype=np.int32)).to(dev) if not torch.is_tensor(vwgt) else vwgt
-        for t in (self.xadj, self.adjncy, self.ewgt, self.vwgt):
+        for t in (self.adjncy, self.ewgt, self.vwgt):
             assert t.dtype == torch.int32 and t.is_cuda and t.is_contiguous()
+        assert self.xadj.dtype == xt and self.xadj.is_cuda and self.xadj.is_contiguous()
         self.n = int(self.xadj.numel() - 1)
         self.nnz = int(self.adjncy.numel())
         self.kp = kp_graph(self.n, self.nnz, self.xadj.data_ptr(), self.adjncy.data_ptr(),
@@ -530,7 +549,7 @@ class Hierarchy:
 
     def level(self, l: int):
         g, mp = kp_hierarchy_level(self.handle, l)
-        out = {"n": g.n, "nnz": g.nnz, "xadj": device_view(g.xadj, g.n + 1),
+        out = {"n": g.n, "nnz": g.nnz, "xadj": device_view(g.xadj, g.n + 1, XADJ_TYPESTR),
                "adjncy": device_view(g.adjncy, g.nnz), "ewgt": device_view(g.ewgt, g.nnz),
                "vwgt": device_view(g.vwgt, g.n), "map": device_view(mp, g.n) if mp else None}
         out["graph"] = g
@@ -592,7 +611,7 @@ class BatchHierarchy(Hierarchy):
         a, b = int(off[gi]), int(off[gi + 1])
         X = lv["xadj"][a:b + 1].cpu().numpy().astype(np.int64)
         e0, e1 = int(X[0]), int(X[-1])
-        out = {"n": b - a, "xadj": (X - e0).astype(np.int32),
+        out = {"n": b - a, "xadj": (X - e0).astype(XADJ_NP),
                "adjncy": (lv["adjncy"][e0:e1].cpu().numpy() - a).astype(np.int32),
                "ewgt": lv["ewgt"][e0:e1].cpu().numpy(), "vwgt": lv["vwgt"][a:b].cpu().numpy(), "map": None}
         levels = self.graph_levels()[gi]
@@ -650,7 +669,8 @@ def pipeline_host(xadj, adjncy, ewgt, vwgt, k: int, eps: float, initial_partitio
     np.ndarray[int32] of block ids."""
     n = len(xadj) - 1
     nnz = len(adjncy)
-    arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in (xadj, adjncy, ewgt, vwgt)]
+    arrs = [np.ascontiguousarray(xadj, dtype=XADJ_NP)] + [np.ascontiguousarray(a, dtype=np.int32)
+                                                          for a in (adjncy, ewgt, vwgt)]
     g = kp_graph(n, nnz, *[a.ctypes.data for a in arrs])
     if outputs is None:
         outputs = {"part": np.empty(n, np.int32), "gain": np.empty(n, np.int64),
@@ -698,7 +718,8 @@ class Server:
                borrow: bool = False) -> int:
         """borrow=True: the server reads the arrays when the request runs (no
         copy at submit); they are kept referenced until release."""
-        arrs = [np.ascontiguousarray(a, dtype=np.int32) for a in (xadj, adjncy, ewgt, vwgt)]
+        arrs = [np.ascontiguousarray(xadj, dtype=XADJ_NP)] + [np.ascontiguousarray(a, dtype=np.int32)
+                                                              for a in (adjncy, ewgt, vwgt)]
         g = kp_graph(len(arrs[0]) - 1, len(arrs[1]), *[a.ctypes.data for a in arrs])
         rid = kp_server_submit(self._sv, g, kp_request_params(k, stop_size, eps, seed,
                                                               KP_REQUEST_BORROW if borrow else 0, 0))

@@ -1,7 +1,10 @@
-"""Builds the CUDA library (libkp.so) in-tree for sm_103a with nvcc.
+"""Builds the CUDA libraries in-tree for sm_103a with nvcc.
 
-Each translation unit is compiled in parallel, then linked with the static
-CUDA runtime into paper_0910_2004_gb300/_build/libkp.so.
+The same sources are built twice: libkp.so with 32-bit entry offsets and
+libkp64.so with 64-bit ones (KP_WIDE_OFFSETS, for graphs of 2^31 entries or
+more).  Every translation unit of both is compiled in parallel, then each
+set is linked with the static CUDA runtime into
+paper_0910_2004_gb300/_build/.
 """
 from __future__ import annotations
 
@@ -16,6 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libkp.so")
+LIB64 = os.path.join(OUT, "libkp64.so")
 SOURCES = ["capi.cu", "coarsen.cu", "match.cu", "contract.cu", "tail.cu", "evaluate.cu", "server.cu", "tune.cu", "refine.cu", "hierarchy_io.cu"]
 HEADERS = [os.path.join(CSRC, h) for h in ("kp_internal.cuh", "engine.cuh", "match.cuh", "gpa.cuh", "contract.cuh")] + [os.path.join(INCLUDE, "kp.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,17 +43,21 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(), widths=(32, 64)) -> str:
+    """Builds the libraries of the given offset widths; returns libkp.so's
+    path (or libkp64.so's when only 64 is asked for)."""
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
-    objs = []
+    objs = {w: [] for w in widths}
     jobs = []
-    for src in SOURCES:
-        s = os.path.join(CSRC, src)
-        o = os.path.join(OUT, src.replace(".cu", ".o"))
-        objs.append(o)
-        if force or _stale(o, [s] + HEADERS):
-            jobs.append([nvcc] + FLAGS + PER_FILE.get(src, []) + list(extra_flags) + ["-c", s, "-o", o])
+    for w in widths:
+        for src in SOURCES:
+            s = os.path.join(CSRC, src)
+            o = os.path.join(OUT, src.replace(".cu", ".o" if w == 32 else ".w64.o"))
+            objs[w].append(o)
+            if force or _stale(o, [s] + HEADERS):
+                wide = ["-DKP_WIDE_OFFSETS"] if w == 64 else []
+                jobs.append([nvcc] + FLAGS + wide + PER_FILE.get(src, []) + list(extra_flags) + ["-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,13 +67,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             sys.stderr.write(r.stdout + r.stderr)
 
     if jobs:
-        with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        with ThreadPoolExecutor(max_workers=min(len(jobs), max(os.cpu_count() or 1, 1))) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"])
-        os.replace(tmp, LIB)
-    return LIB
+    for w in widths:
+        lib = LIB if w == 32 else LIB64
+        if force or jobs or _stale(lib, objs[w]):
+            tmp = lib + f".tmp{os.getpid()}"
+            run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs[w] + ["-lpthread"])
+            os.replace(tmp, lib)
+    return LIB if 32 in widths else LIB64
 
 
 if __name__ == "__main__":

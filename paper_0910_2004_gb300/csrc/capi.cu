@@ -105,14 +105,14 @@ struct CheckAcc {
 };
 
 // Input check in two kernels.  Nodes: row bounds, c >= 0 and the sum of c.
-__global__ void k_validate_nodes(int32_t n, int32_t nnz, const int32_t *__restrict__ xadj,
+__global__ void k_validate_nodes(int32_t n, eoff nnz, const eoff *__restrict__ xadj,
                                  const int32_t *__restrict__ vwgt, CheckAcc *acc) {
     int bad = 0;
     unsigned long long csum = 0;
     if (blockIdx.x == 0 && threadIdx.x == 0 && (xadj[0] != 0 || xadj[n] != nnz)) bad = 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
-        const int32_t beg = xadj[v], end = xadj[v + 1];
+        const eoff beg = xadj[v], end = xadj[v + 1];
         if (beg < 0 || end < beg || end > nnz) bad = 1;
         const int32_t c = vwgt[v];
         if (c < 0) bad = 1;
@@ -132,7 +132,7 @@ __global__ void k_validate_nodes(int32_t n, int32_t nnz, const int32_t *__restri
 // before it is used, whatever the input (the node kernel reports bad rows).
 constexpr int VALIDATE_CHUNK = 8;
 
-__global__ void k_validate_entries(int32_t n, int32_t nnz, const int32_t *__restrict__ xadj,
+__global__ void k_validate_entries(int32_t n, eoff nnz, const eoff *__restrict__ xadj,
                                    const int32_t *__restrict__ adjncy, const int32_t *__restrict__ ewgt,
                                    CheckAcc *acc) {
     int bad = 0;
@@ -157,14 +157,14 @@ __global__ void k_validate_entries(int32_t n, int32_t nnz, const int32_t *__rest
                 continue;
             }
             if (e > 0 && e > xadj[v] && adjncy[e - 1] >= u) bad = 1;
-            int32_t a = xadj[u], b = xadj[u + 1] - 1;
+            eoff a = xadj[u], b = xadj[u + 1] - 1;
             if (a < 0 || b >= nnz) {
                 bad = 1;
                 continue;
             }
-            int found = -1;
+            eoff found = -1;
             while (a <= b) {
-                const int32_t mid = a + (b - a) / 2;
+                const eoff mid = a + (b - a) / 2;
                 const int32_t t = adjncy[mid];
                 if (t == v) {
                     found = mid;
@@ -394,7 +394,11 @@ kp_status kp_pipeline_host(const kp_graph *g, const kp_options *o, int32_t k, do
 
 const char *kp_last_error(void) { return g_last_error.c_str(); }
 
-const char *kp_version(void) { return "kp-gb300 0.1 (sm_103a)"; }
+const char *kp_version(void) {
+    return KP_OFFSET_BITS == 64 ? "kp-gb300 0.1 (sm_103a, 64-bit offsets)" : "kp-gb300 0.1 (sm_103a)";
+}
+
+int32_t kp_offset_bits(void) { return KP_OFFSET_BITS; }
 
 }  // extern "C"
 

@@ -70,7 +70,7 @@ unsigned long long align256(unsigned long long b) { return (b + 255ull) & ~255ul
 
 // Device scratch of the level loop, sized for level 0 (every later level is
 // smaller), and the device state.
-kp_status alloc_work(Scratch &sc, Work &w, int32_t n0, int32_t nnz0, const kp_options *o, const BatchSpec *batch,
+kp_status alloc_work(Scratch &sc, Work &w, int32_t n0, eoff nnz0, const kp_options *o, const BatchSpec *batch,
                      int32_t *glevels_dev, DevState **dst) {
     std::memset(&w, 0, sizeof w);
     if (o->matcher == KP_MATCHER_SUITOR) {
@@ -124,11 +124,11 @@ kp_status alloc_work(Scratch &sc, Work &w, int32_t n0, int32_t nnz0, const kp_op
 // (-1: never).
 int32_t cluster_nodes_of(const kp_options *o) { return o->cluster_nodes == 0 ? 8192 : o->cluster_nodes; }
 
-unsigned long long initial_arena(const kp_options *o, int32_t n0, int32_t nnz0) {
+unsigned long long initial_arena(const kp_options *o, int32_t n0, eoff nnz0) {
     unsigned long long cap =
         o->arena_bytes > 0
             ? align256((unsigned long long)o->arena_bytes)
-            : align256(4ull * (16ull * (unsigned long long)n0 + 8ull * (unsigned long long)nnz0) + (1ull << 20));
+            : align256((60ull + sizeof(eoff)) * (unsigned long long)n0 + 32ull * (unsigned long long)nnz0 + (1ull << 20));
     if (o->rating == KP_RATING_INNER_OUTER)   // Out of the input lives at the arena's start
         cap = std::max<unsigned long long>(cap, align256(4ull * (unsigned long long)n0) + 4096);
     return cap;
@@ -148,7 +148,7 @@ void init_state(DevState *hs, const kp_graph *g, const kp_options *o, const Batc
     // a batch decide for themselves at the level start
     const bool active0 = batch ? true : (g->n > o->stop_size && o->max_levels > 0);
     L0.flags = LV_BUILT | (active0 ? LV_ACTIVE : 0);
-    L0.xadj = const_cast<int32_t *>(g->xadj);
+    L0.xadj = const_cast<eoff *>(g->xadj);
     L0.adjncy = const_cast<int32_t *>(g->adjncy);
     L0.ewgt = const_cast<int32_t *>(g->ewgt);
     L0.vwgt = const_cast<int32_t *>(g->vwgt);
@@ -223,15 +223,25 @@ kp_status assemble_hierarchy(kp_hierarchy *h, const DevState *hs, bool suitor, i
 
 kp_status validate_graph(const kp_graph *g, cudaStream_t s, int64_t spin_limit);
 
+// Sizes and arrays of an input graph, checked on the host whether or not
+// the graph itself is checked.  nnz = 2|E| and omega >= 1 with the sum of
+// omega below 2^31 bound nnz below 2^32, which the coarse row bounds of the
+// relabel scan rely on (their sum is kept in 32 bits).
+kp_status check_graph_sizes(const kp_graph *g) {
+    if (g->n < 0 || g->nnz < 0) return set_error(KP_ERR_INVALID, "negative graph size");
+    if ((int64_t)g->nnz >= NNZ_LIMIT) return set_error(KP_ERR_OVERFLOW, "nnz >= 2^32: the edge weights sum to 2^31 or more");
+    if (g->n > 0 && (!g->xadj || !g->vwgt || (g->nnz > 0 && (!g->adjncy || !g->ewgt))))
+        return set_error(KP_ERR_INVALID, "null graph array");
+    return KP_OK;
+}
+
 kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, kp_hierarchy **out,
                        const BatchSpec *batch) {
     const int rating = o->rating;
     if (rating < 0 || rating > 4) return set_error(KP_ERR_UNSUPPORTED, "unknown rating");
     if (o->matcher != KP_MATCHER_SUITOR && o->matcher != KP_MATCHER_HANDSHAKE && o->matcher != KP_MATCHER_GPA)
         return set_error(KP_ERR_UNSUPPORTED, "unknown matcher");
-    if (g->n < 0 || g->nnz < 0) return set_error(KP_ERR_INVALID, "negative graph size");
-    if (g->n > 0 && (!g->xadj || !g->vwgt || (g->nnz > 0 && (!g->adjncy || !g->ewgt))))
-        return set_error(KP_ERR_INVALID, "null graph array");
+    KP_TRY(check_graph_sizes(g));
     if (o->max_levels < 0 || o->max_levels > MAX_LEVELS - 8 || o->min_shrink_permille < 0 ||
         o->min_shrink_permille > 1000 || o->spin_limit <= 0 || o->arena_bytes < 0 || o->tail_nodes < -1)
         return set_error(KP_ERR_INVALID, "bad option value");
@@ -280,7 +290,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     kp_level l0;
     l0.n = g->n;
     l0.nnz = g->nnz;
-    l0.xadj = const_cast<int32_t *>(g->xadj);
+    l0.xadj = const_cast<eoff *>(g->xadj);
     l0.adjncy = const_cast<int32_t *>(g->adjncy);
     l0.ewgt = const_cast<int32_t *>(g->ewgt);
     l0.vwgt = const_cast<int32_t *>(g->vwgt);
@@ -291,7 +301,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
         return st;
     };
     const int32_t n0 = g->n;
-    const int32_t nnz0 = g->nnz;
+    const eoff nnz0 = g->nnz;
     const bool suitor = o->matcher == KP_MATCHER_SUITOR;
     const bool inner_outer = rating == KP_RATING_INNER_OUTER;
     const bool active0 = batch ? true : (n0 > o->stop_size && o->max_levels > 0);
@@ -389,7 +399,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     };
     for (;;) {   // one pass per arena size
         int32_t n_bound = start == 0 ? n0 : hs->lv[start].n;
-        int64_t nnz_bound = start == 0 ? nnz0 : std::max(hs->lv[start].nnz, 1);
+        int64_t nnz_bound = start == 0 ? (int64_t)nnz0 : std::max<int64_t>(hs->lv[start].nnz, 1);
         // a batch runs one more level: graphs stopping at the level cap are
         // only recorded at the level after it
         const int level_end = o->max_levels + (batch ? 1 : 0);
@@ -469,7 +479,7 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
                 if (sn->stop) break;
                 if (sn->done && sn->cn > 0) {   // a tighter bound for the grids
                     n_bound = sn->cn;
-                    nnz_bound = std::max<int64_t>(sn->nnz, 1);
+                    nnz_bound = std::max<int64_t>((int64_t)sn->nnz, 1);
                     deg_level = seen + 1;   // its largest degree (below 1024 when not recorded)
                     deg_max = std::max<int64_t>(sn->maxdeg, 1023);
                 }
@@ -580,7 +590,7 @@ struct kp_plan {
     cudaGraphExec_t exec = nullptr;
     int32_t launches = 0;
     int32_t block_nodes = 2048;
-    std::vector<std::pair<int32_t, int32_t>> sizes;   // (n, nnz) per level of the checking run
+    std::vector<std::pair<int32_t, int64_t>> sizes;   // (n, nnz) per level of the checking run
     ~kp_plan() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
@@ -643,7 +653,7 @@ kp_status plan_capture(kp_plan *p) {
         LL.suitor_blocks = p->o.suitor_blocks;
         const size_t sl = std::min<size_t>((size_t)level, p->sizes.size() - 1);
         LL.n_bound = std::max(p->sizes[sl].first, 1);
-        LL.nnz_bound = std::max(p->sizes[sl].second, 1);
+        LL.nnz_bound = std::max<int64_t>(p->sizes[sl].second, 1);
         LL.huge = true;   // a replay may meet other degrees than the checking run
         LL.epoch_relabel = ++epoch;
         LL.epoch_degscan = ++epoch;
@@ -690,8 +700,8 @@ kp_status plan_create_impl(const kp_graph *g, int32_t num_graphs, const int32_t 
     first.profile = 0;
     kp_hierarchy *h0 = nullptr;
     KP_TRY(coarsen_impl(g, &first, s, &h0, num_graphs > 0 ? &b : nullptr));
-    std::vector<std::pair<int32_t, int32_t>> sizes;
-    for (const kp_level &l : h0->levels) sizes.emplace_back(l.n, l.nnz);
+    std::vector<std::pair<int32_t, int64_t>> sizes;
+    for (const kp_level &l : h0->levels) sizes.emplace_back(l.n, (int64_t)l.nnz);
     kp_hierarchy_free(h0);
 
     kp_plan *p = new kp_plan();
@@ -773,7 +783,7 @@ kp_status plan_run_impl(kp_plan *p, cudaStream_t s, kp_hierarchy **out) {
     kp_level l0;
     l0.n = p->g.n;
     l0.nnz = p->g.nnz;
-    l0.xadj = const_cast<int32_t *>(p->g.xadj);
+    l0.xadj = const_cast<eoff *>(p->g.xadj);
     l0.adjncy = const_cast<int32_t *>(p->g.adjncy);
     l0.ewgt = const_cast<int32_t *>(p->g.ewgt);
     l0.vwgt = const_cast<int32_t *>(p->g.vwgt);

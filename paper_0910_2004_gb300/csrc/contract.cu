@@ -165,10 +165,11 @@ __device__ void contract_cluster_radix(const CView &p, int32_t x, int passes, Hu
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = CONTRACT_BLOCK / 32;
     const unsigned lt = lanemask_lt();
-    int32_t xa, da, xb, db;
+    eoff xa, xb;
+    int32_t da, db;
     members(p, x, xa, da, xb, db);
     const int32_t L = da + db;
-    const int32_t o = p.off[x];
+    const eoff o = p.off[x];
     int32_t *src_k = (passes & 1) ? p.tmp_adj + o : p.big_adj + o;
     int32_t *src_v = (passes & 1) ? p.tmp_w + o : p.big_w + o;
     int32_t *dst_k = (passes & 1) ? p.big_adj + o : p.tmp_adj + o;
@@ -207,7 +208,7 @@ __device__ void contract_cluster_radix(const CView &p, int32_t x, int passes, Hu
         const int32_t i = c0 + (int32_t)threadIdx.x;
         int32_t t = x, wv = 0;
         if (i < hi) {
-            const int32_t e = i < da ? xa + i : xb + (i - da);
+            const eoff e = i < da ? xa + i : xb + (i - da);
             t = p.map[p.adjncy[e]];
             wv = p.ewgt[e];
         }

@@ -29,7 +29,8 @@ struct RelabelOp {
     Work w;
     // loaded by prepare()
     int32_t n;
-    const int32_t *xadj, *vwgt, *gid;
+    const eoff *xadj;
+    const int32_t *vwgt, *gid;
     int32_t *map, *cvwgt, *gidn;
 
     __device__ bool prepare() {
@@ -62,7 +63,9 @@ struct RelabelOp {
         }
         const int32_t p = partner(v);
         if (p < v) return 0;   // not the representative of its pair
-        int32_t ub = xadj[v + 1] - xadj[v];
+        // row bounds are below 2^32 in both widths: U <= nnz < 2^32 (the
+        // weight range bounds |E| < 2^31), so the low half never carries
+        eoff ub = xadj[v + 1] - xadj[v];
         if (p != v) ub += xadj[p + 1] - xadj[p] - 2;   // the pair's own edge is dropped
         return (1ull << 32) | (uint32_t)ub;
     }
@@ -80,13 +83,13 @@ struct RelabelOp {
             w.second[x] = -1;
             cvwgt[x] = vwgt[v];
         }
-        w.off[x] = (int32_t)(excl & 0xffffffffu);
+        w.off[x] = (eoff)(excl & 0xffffffffu);
         if (w.batch) gidn[x] = gid[v];
     }
     // One thread: the coarse sizes are known, carve the coarse level.
     __device__ void total(uint64_t t) const {
         const int32_t cn = (int32_t)(t >> 32);
-        const int32_t U = (int32_t)(t & 0xffffffffu);
+        const eoff U = (eoff)(t & 0xffffffffu);
         Counters *c = &st->ctr[level];
         c->cn = cn;
         c->U = U;
@@ -98,7 +101,7 @@ struct RelabelOp {
             stop_at(st, level, 0);
             return;
         }
-        const unsigned long long need_x = 4ull * ((unsigned long long)cn + 1);
+        const unsigned long long need_x = sizeof(eoff) * ((unsigned long long)cn + 1);
         const unsigned long long need_e = 4ull * (unsigned long long)(U > 0 ? U : 1);
         char *px = arena_carve(st, need_x);
         char *pa = px ? arena_carve(st, need_e) : nullptr;
@@ -112,7 +115,7 @@ struct RelabelOp {
         DevLevel *C = &st->lv[level + 1];
         C->n = cn;
         C->U = U;
-        C->xadj = (int32_t *)px;
+        C->xadj = (eoff *)px;
         C->adjncy = (int32_t *)pa;
         C->ewgt = (int32_t *)pw;
         C->outw = st->inner_outer ? (int32_t *)po : nullptr;
@@ -125,8 +128,10 @@ struct RelabelOp {
 // ---------------------------------------------------------------------------
 struct CView {
     int32_t cn;
-    const int32_t *xadj, *adjncy, *ewgt, *map;
-    const int32_t *first, *second, *off;
+    const eoff *xadj;
+    const int32_t *adjncy, *ewgt, *map;
+    const int32_t *first, *second;
+    const eoff *off;
     int32_t *tmp_adj, *tmp_w, *big_adj, *big_w, *degp, *outw;
     int32_t *const *lists;
     Counters *ctr;
@@ -158,13 +163,12 @@ __device__ __forceinline__ bool load_view(DevState *st, int level, const Work &w
     return true;
 }
 
-__device__ __forceinline__ void members(const CView &p, int32_t x, int32_t &xa, int32_t &da, int32_t &xb,
-                                        int32_t &db) {
+__device__ __forceinline__ void members(const CView &p, int32_t x, eoff &xa, int32_t &da, eoff &xb, int32_t &db) {
     const int32_t a = p.first[x], b = p.second[x];
     xa = p.xadj[a];
-    da = p.xadj[a + 1] - xa;
+    da = (int32_t)(p.xadj[a + 1] - xa);
     xb = b >= 0 ? p.xadj[b] : 0;
-    db = b >= 0 ? p.xadj[b + 1] - xb : 0;
+    db = b >= 0 ? (int32_t)(p.xadj[b + 1] - xb) : 0;
 }
 
 // Rows with at most 16 gathered entries: one thread.  (map(u), omega) packed
@@ -173,15 +177,14 @@ __device__ __forceinline__ void members(const CView &p, int32_t x, int32_t &xa, 
 constexpr int TNET = 16;
 
 template <int TNET>
-__device__ __forceinline__ void contract_thread(const CView &p, int32_t x, int32_t xa, int32_t da, int32_t xb,
-                                                int32_t db) {
+__device__ __forceinline__ void contract_thread(const CView &p, int32_t x, eoff xa, int32_t da, eoff xb, int32_t db) {
     constexpr uint64_t SENT64 = (uint64_t)SENT << 32;
     uint64_t r[TNET];
 #pragma unroll
     for (int i = 0; i < TNET; i++) {
         uint64_t v = SENT64;
         if (i < da + db) {
-            const int32_t e = i < da ? xa + i : xb + (i - da);
+            const eoff e = i < da ? xa + i : xb + (i - da);
             const int32_t t = p.map[p.adjncy[e]];
             if (t != x) v = ((uint64_t)(uint32_t)t << 32) | (uint32_t)p.ewgt[e];
         }
@@ -203,7 +206,7 @@ __device__ __forceinline__ void contract_thread(const CView &p, int32_t x, int32
             }
         }
     }
-    const int32_t o = p.off[x];
+    const eoff o = p.off[x];
     int32_t cnt = 0, curk = -1, sum = 0, total = 0;
 #pragma unroll
     for (int i = 0; i < TNET; i++) {
@@ -260,7 +263,8 @@ static __device__ void phase_contract_small(DevState *st, int level, const Work 
     for (int64_t x0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); x0 < p.cn; x0 += stride) {
         const int64_t x = x0 + lane;
         int cls = -1;
-        int32_t da = 0, db = 0, xa = 0, xb = 0;
+        int32_t da = 0, db = 0;
+        eoff xa = 0, xb = 0;
         if (x < p.cn) {
             members(p, (int32_t)x, xa, da, xb, db);
             const int32_t L = da + db;
@@ -286,13 +290,14 @@ static __device__ void phase_contract_small(DevState *st, int level, const Work 
 
 // Rows of 17..32 gathered entries: one warp, bitonic sort over the lanes.
 __device__ __forceinline__ void contract_warp32(const CView &p, int32_t x) {
-    int32_t xa, da, xb, db;
+    eoff xa, xb;
+    int32_t da, db;
     members(p, x, xa, da, xb, db);
     const int gl = threadIdx.x & 31;
     const int32_t L = da + db;
     int32_t key = SENT, val = 0;
     if (gl < L) {
-        const int32_t e = gl < da ? xa + gl : xb + (gl - da);
+        const eoff e = gl < da ? xa + gl : xb + (gl - da);
         const int32_t t = p.map[p.adjncy[e]];
         if (t != x) {
             key = t;
@@ -335,7 +340,7 @@ __device__ __forceinline__ void contract_warp32(const CView &p, int32_t x) {
     const int32_t total = __shfl_sync(0xffffffffu, s, 31);
     if (tail) {
         const int32_t idx = __popc(tails & ((1u << gl) - 1u));
-        const int32_t o = p.off[x];
+        const eoff o = p.off[x];
         p.tmp_adj[o + idx] = key;
         p.tmp_w[o + idx] = run;
     }
@@ -352,14 +357,15 @@ constexpr int WSORT = 128;
 
 __device__ __forceinline__ void contract_warp_smem(const CView &p, int32_t x, int32_t *K, int32_t *V, int32_t *S) {
     const int lane = threadIdx.x & 31;
-    int32_t xa, da, xb, db;
+    eoff xa, xb;
+    int32_t da, db;
     members(p, x, xa, da, xb, db);
     const int32_t L = da + db;
     const int P = L <= 64 ? 64 : 128;
     for (int i = lane; i < P; i += 32) {
         int32_t key = SENT, val = 0;
         if (i < L) {
-            const int32_t e = i < da ? xa + i : xb + (i - da);
+            const eoff e = i < da ? xa + i : xb + (i - da);
             const int32_t t = p.map[p.adjncy[e]];
             if (t != x) {
                 key = t;
@@ -404,7 +410,7 @@ __device__ __forceinline__ void contract_warp_smem(const CView &p, int32_t x, in
     }
     const int nruns = __shfl_sync(0xffffffffu, incl, 31);
     int r = incl - heads - 1;
-    const int32_t o = p.off[x];
+    const eoff o = p.off[x];
     int32_t wsum = 0;
     for (int q = 0; q < per; q++) {
         const int i = base + q;
@@ -433,7 +439,8 @@ __device__ __forceinline__ void contract_warp_smem(const CView &p, int32_t x, in
 static __device__ void contract_block_smem(const CView &p, int32_t x, int32_t *keys, int32_t *vals, int32_t *sums,
                                     int32_t *s_red) {
     constexpr int IPT = MID_MAX / CONTRACT_BLOCK;
-    int32_t xa, da, xb, db;
+    eoff xa, xb;
+    int32_t da, db;
     members(p, x, xa, da, xb, db);
     const int32_t L = da + db;
     int32_t P = 64;
@@ -441,7 +448,7 @@ static __device__ void contract_block_smem(const CView &p, int32_t x, int32_t *k
     for (int32_t i = threadIdx.x; i < P; i += blockDim.x) {
         int32_t key = SENT, val = 0;
         if (i < L) {
-            const int32_t e = i < da ? xa + i : xb + (i - da);
+            const eoff e = i < da ? xa + i : xb + (i - da);
             const int32_t t = p.map[p.adjncy[e]];
             if (t != x) {
                 key = t;
@@ -483,7 +490,7 @@ static __device__ void contract_block_smem(const CView &p, int32_t x, int32_t *k
     }
     uint64_t tot;
     int32_t r = (int32_t)block_exclusive_scan<CONTRACT_BLOCK>((uint64_t)cnt, &tot) - 1;
-    const int32_t o = p.off[x];
+    const eoff o = p.off[x];
     int32_t wsum = 0;
 #pragma unroll
     for (int j = 0; j < IPT; j++) {
@@ -538,10 +545,11 @@ static __device__ void contract_block_radix(const CView &p, int32_t x, int passe
     constexpr int NW = CONTRACT_BLOCK / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
-    int32_t xa, da, xb, db;
+    eoff xa, xb;
+    int32_t da, db;
     members(p, x, xa, da, xb, db);
     const int32_t L = da + db;
-    const int32_t o = p.off[x];
+    const eoff o = p.off[x];
     int32_t *src_k = (passes & 1) ? p.tmp_adj + o : p.big_adj + o;
     int32_t *src_v = (passes & 1) ? p.tmp_w + o : p.big_w + o;
     int32_t *dst_k = (passes & 1) ? p.big_adj + o : p.tmp_adj + o;
@@ -559,7 +567,7 @@ static __device__ void contract_block_radix(const CView &p, int32_t x, int passe
             const int32_t i = c0 + (warp * RADIX_ITEMS + j) * 32 + lane;
             int32_t t = x, wv = 0;
             if (i < L) {
-                const int32_t e = i < da ? xa + i : xb + (i - da);
+                const eoff e = i < da ? xa + i : xb + (i - da);
                 t = p.map[p.adjncy[e]];
                 wv = p.ewgt[e];
             }
@@ -728,7 +736,8 @@ __device__ __forceinline__ void contract_warp_reg(const CView &p, int32_t x) {
     constexpr int N = WARP_ROW / 32;
     constexpr uint64_t SENT64 = (uint64_t)SENT << 32;
     const int lane = threadIdx.x & 31;
-    int32_t xa, da, xb, db;
+    eoff xa, xb;
+    int32_t da, db;
     members(p, x, xa, da, xb, db);
     const int32_t L = da + db;
     uint64_t r[N];
@@ -739,7 +748,7 @@ __device__ __forceinline__ void contract_warp_reg(const CView &p, int32_t x) {
         const int32_t q = i * 32 + lane;
         uint64_t v = SENT64;
         if (q < L) {
-            const int32_t e = q < da ? xa + q : xb + (q - da);
+            const eoff e = q < da ? xa + q : xb + (q - da);
             const int32_t t = p.map[p.adjncy[e]];
             if (t != x) v = ((uint64_t)(uint32_t)t << 32) | (uint32_t)p.ewgt[e];
         }
@@ -791,7 +800,7 @@ __device__ __forceinline__ void contract_warp_reg(const CView &p, int32_t x) {
         if (lane >= off) incl += y;
     }
     const int32_t runs = __shfl_sync(0xffffffffu, incl, 31);
-    const int32_t o = p.off[x];
+    const eoff o = p.off[x];
     int32_t run = incl - heads - 1;   // the run in progress where this lane starts
     int32_t sum = 0;
     bool mine = false;                // that run started in this lane
@@ -848,7 +857,8 @@ static __device__ void phase_contract_rows32(DevState *st, int level, const Work
     if (count >= ROWS32_MIN) {
         for (int64_t li = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; li < count; li += stride) {
             const int32_t x = p.lists[1][li];
-            int32_t xa, da, xb, db;
+            eoff xa, xb;
+            int32_t da, db;
             members(p, x, xa, da, xb, db);
             contract_thread<32>(p, x, xa, da, xb, db);
         }
@@ -923,7 +933,7 @@ struct DegScanOp {
     int level;
     Work w;
     int32_t cn;
-    int32_t *cxadj;
+    eoff *cxadj;
 
     __device__ bool prepare() {
         if (!(st->lv[level].flags & LV_ACTIVE)) return false;
@@ -935,14 +945,14 @@ struct DegScanOp {
     __device__ int32_t *tile_counter() const { return &st->ctr[level].tile_counter[1]; }
     __device__ void fail() const { stop_at(st, level, ERR_TIMEOUT); }
     __device__ uint64_t load(int64_t x) const { return (uint64_t)(uint32_t)w.degp[x]; }
-    __device__ void store(int64_t x, uint64_t excl, uint64_t) const { cxadj[x] = (int32_t)excl; }
+    __device__ void store(int64_t x, uint64_t excl, uint64_t) const { cxadj[x] = (eoff)excl; }
     // One thread: record nnz' and decide whether level+1 is contracted
     // (stop when small enough, after too little shrinkage, or at the level cap).
     __device__ void total(uint64_t t) const {
-        cxadj[cn] = (int32_t)t;
-        st->ctr[level].nnz_out = (int32_t)t;
+        cxadj[cn] = (eoff)t;
+        st->ctr[level].nnz_out = (eoff)t;
         DevLevel *C = &st->lv[level + 1];
-        C->nnz = (int32_t)t;
+        C->nnz = (eoff)t;
         const int64_t n = st->lv[level].n;
         bool next;
         if (w.batch) {   // graphs decide for themselves at the next level start
@@ -957,7 +967,7 @@ struct DegScanOp {
         if (!next) st->stop = 1;
         volatile LevelSnap *s = st->snap + level;
         s->cn = cn;
-        s->nnz = (int32_t)t;
+        s->nnz = (eoff)t;
         s->maxdeg = st->ctr[level].maxdeg;   // the contraction kernels ended before this scan
         s->room = st->arena_cap - st->arena_used;
         s->arena_gen = st->arena_gen;
@@ -974,17 +984,18 @@ static __device__ void phase_compact(DevState *st, int level, const Work &w) {
     if (!(st->lv[level].flags & LV_ACTIVE)) return;
     const Counters *ctr = &st->ctr[level];
     const int32_t cn = ctr->cn;
-    const int32_t *KP_RESTRICT cxadj = st->lv[level + 1].xadj;
+    const eoff *KP_RESTRICT cxadj = st->lv[level + 1].xadj;
     int32_t *KP_RESTRICT cadj = st->lv[level + 1].adjncy;
     int32_t *KP_RESTRICT cw = st->lv[level + 1].ewgt;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int gl = threadIdx.x & 7;
     for (int64_t g = t >> 3; g < cn; g += stride >> 3) {
-        const int32_t o = w.off[g];
+        const eoff o = w.off[g];
         // gathered entries = the slot plus the pair's own two, as classified
         if (w.off[g + 1] - o + (w.second[g] >= 0 ? 2 : 0) > 128) continue;
-        const int32_t d = w.degp[g], s = cxadj[g];
+        const int32_t d = w.degp[g];
+        const eoff s = cxadj[g];
         for (int32_t i = gl; i < d; i += 8) {
             cadj[s + i] = w.tmp_adj[o + i];
             cw[s + i] = w.tmp_w[o + i];
@@ -995,7 +1006,8 @@ static __device__ void phase_compact(DevState *st, int level, const Work &w) {
     const int32_t n3 = ctr->nclass[3], n4 = ctr->nclass[4], n6 = ctr->nclass[6];
     for (int64_t li = t >> 5; li < (int64_t)n3 + n6; li += nw) {
         const int32_t g = li < n3 ? w.lists[3][li] : w.lists[6][li - n3];
-        const int32_t o = w.off[g], d = w.degp[g], s = cxadj[g];
+        const eoff o = w.off[g], s = cxadj[g];
+        const int32_t d = w.degp[g];
         for (int32_t i = lane; i < d; i += 32) {
             cadj[s + i] = w.tmp_adj[o + i];
             cw[s + i] = w.tmp_w[o + i];
@@ -1003,7 +1015,8 @@ static __device__ void phase_compact(DevState *st, int level, const Work &w) {
     }
     for (int64_t li = blockIdx.x; li < n4; li += gridDim.x) {
         const int32_t g = w.lists[4][li];
-        const int32_t o = w.off[g], d = w.degp[g], s = cxadj[g];
+        const eoff o = w.off[g], s = cxadj[g];
+        const int32_t d = w.degp[g];
         for (int32_t i = threadIdx.x; i < d; i += blockDim.x) {
             cadj[s + i] = w.tmp_adj[o + i];
             cw[s + i] = w.tmp_w[o + i];
@@ -1013,7 +1026,8 @@ static __device__ void phase_compact(DevState *st, int level, const Work &w) {
     const int32_t n5 = ctr->nclass[5];
     for (int32_t li = 0; li < n5; li++) {
         const int32_t g = w.lists[5][li];
-        const int32_t o = w.off[g], d = w.degp[g], s = cxadj[g];
+        const eoff o = w.off[g], s = cxadj[g];
+        const int32_t d = w.degp[g];
         for (int64_t i = t; i < d; i += stride) {
             cadj[s + i] = w.tmp_adj[o + i];
             cw[s + i] = w.tmp_w[o + i];

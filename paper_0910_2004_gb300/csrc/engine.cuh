@@ -49,10 +49,10 @@ struct Counters {   // one per level, zeroed before the level runs
     int32_t list_size[4];  // proposals: [0],[1] middle pass list and counter, [2],[3] wide pass
     int32_t rounds;
     int32_t cn;            // coarse node count
-    int32_t U;             // sum of coarse row upper bounds
+    eoff U;                // sum of coarse row upper bounds
     int32_t nclass[7];     // class lists: [1] <=32, [2] <=128, [3] <=MID_MAX, [4] longer, [5] > huge_row,
                            // [6] 129..warp_row (taken out of [3] where a warp kernel runs)
-    int32_t nnz_out;       // coarse entry count
+    eoff nnz_out;          // coarse entry count
     int32_t tile_counter[2];
     int32_t maxdeg;        // largest coarse degree if it is at least 1024, else 0
     unsigned long long searches;     // rating passes over a row
@@ -62,8 +62,10 @@ struct Counters {   // one per level, zeroed before the level runs
 };
 
 struct DevLevel {
-    int32_t n, nnz, U, flags;
-    int32_t *xadj, *adjncy, *ewgt, *vwgt;
+    int32_t n, flags;
+    eoff nnz, U;
+    eoff *xadj;
+    int32_t *adjncy, *ewgt, *vwgt;
     int32_t *map;    // to level l+1 (-1: the node's graph has stopped)
     int32_t *outw;   // Out(v) (innerOuter only)
     int32_t *gid;    // batches: graph of each node
@@ -75,7 +77,7 @@ struct DevLevel {
 struct LevelSnap {
     int32_t stop;
     int32_t cn;
-    int32_t nnz;
+    eoff nnz;
     int32_t done;
     unsigned long long room;   // arena bytes left after the level
     int32_t arena_gen;         // spare chunks taken so far
@@ -139,7 +141,8 @@ struct TileStatus {
 struct Work {
     Offer *offer;
     int32_t *match, *cand, *list0, *list1;
-    int32_t *first, *second, *off, *degp;
+    int32_t *first, *second, *degp;
+    eoff *off;   // slot of every coarse row in tmp/big (upper bounds, scanned)
     int32_t *tmp_adj, *tmp_w, *big_adj, *big_w;
     int32_t *lists[7];
     // proposals: candidate caches of the rows searched by the wide pass,
@@ -410,7 +413,7 @@ kp_status launch_graph_ids(int32_t n0, int32_t num_graphs, const int32_t *goff, 
                            int32_t *launches);
 kp_status launch_check_batch_edges(const kp_graph *g, const int32_t *gid, const int32_t *goff, int32_t *flag,
                                    cudaStream_t s);
-kp_status launch_out_weight(DevState *st, int32_t n0, int64_t nnz0, const int32_t *xadj, const int32_t *ewgt,
+kp_status launch_out_weight(DevState *st, int32_t n0, int64_t nnz0, const eoff *xadj, const int32_t *ewgt,
                             int32_t *outw, cudaStream_t s, int32_t *launches);
 kp_status launch_matching(const LevelLaunch &L, cudaStream_t s, int32_t *launches);
 kp_status launch_relabel(const LevelLaunch &L, cudaStream_t s, int32_t *launches);

@@ -54,7 +54,7 @@ struct CutGainParams {
     int32_t n;
     int32_t k;
     int32_t id_base;   // neighbour ids minus this are the graph's node ids (0 for a whole graph)
-    const int32_t *__restrict__ xadj;
+    const eoff *__restrict__ xadj;
     const int32_t *__restrict__ adjncy;
     const int32_t *__restrict__ ewgt;
     const int32_t *__restrict__ vwgt;
@@ -109,8 +109,8 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p, const 
         const int64_t v = FROM_LIST ? (int64_t)rows[i] : i;
         const int32_t pv = p.part[v];
         const bool pv_ok = pv >= 0 && pv < p.k;
-        const int32_t beg = p.xadj[v], end = p.xadj[v + 1];
-        const int32_t deg = end - beg;
+        const eoff beg = p.xadj[v], end = p.xadj[v + 1];
+        const int32_t deg = (int32_t)(end - beg);
         // entries held in registers when the row fits the group
         int32_t rb = -1, rw = 0;
         if (deg <= G && gl < deg) {
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p, const 
             for (int32_t b = lane; b < p.k; b += 32) conn[b] = 0;
             __syncwarp();
 #pragma unroll 4
-            for (int32_t e = beg + lane; e < end; e += 32) {
+            for (eoff e = beg + lane; e < end; e += 32) {
                 const int32_t b = p.part[p.adjncy[e] - p.id_base];
                 const int32_t w = p.ewgt[e];
                 if (b < 0 || b >= p.k) {
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p, const 
                     else nextb = rb;
                 }
             } else {
-                for (int32_t e = beg + gl; e < end; e += G) {
+                for (eoff e = beg + gl; e < end; e += G) {
                     const int32_t b = p.part[p.adjncy[e] - p.id_base];
                     const int32_t w = p.ewgt[e];
                     if (b < 0 || b >= p.k) {
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain(CutGainParams p, const 
                     if (rb == cur) conn = rw;
                     else if (rb > cur && rb != pv) nextb = rb;
                 } else {
-                    for (int32_t e = beg + gl; e < end; e += G) {
+                    for (eoff e = beg + gl; e < end; e += G) {
                         const int32_t b = p.part[p.adjncy[e] - p.id_base];
                         if (b < 0 || b >= p.k) continue;
                         if (b == cur) conn += p.ewgt[e];
@@ -291,14 +291,14 @@ __global__ void __launch_bounds__(HUB_BLOCK) k_cut_gain_hubs(CutGainParams p, co
     int32_t bad = 0;
     for (int32_t li = blockIdx.x; li < count; li += gridDim.x) {
         const int32_t v = rows[li];
-        const int32_t beg = p.xadj[v], end = p.xadj[v + 1];
+        const eoff beg = p.xadj[v], end = p.xadj[v + 1];
         if (end - beg <= p.hub_min) continue;   // the same for the whole block
         const int32_t pv = p.part[v];
         for (int32_t b = threadIdx.x; b < p.k; b += HUB_BLOCK) conn[b] = 0;
         __syncthreads();
         long long inw = 0, tot = 0;
 #pragma unroll 4
-        for (int32_t e = beg + (int32_t)threadIdx.x; e < end; e += HUB_BLOCK) {
+        for (eoff e = beg + (eoff)threadIdx.x; e < end; e += HUB_BLOCK) {
             const int32_t b = p.part[p.adjncy[e] - p.id_base];
             const int32_t w = p.ewgt[e];
             if (b < 0 || b >= p.k) {
@@ -383,12 +383,13 @@ __global__ void __launch_bounds__(EVAL_BLOCK) k_cut_gain_rows(CutGainParams p, i
     for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); v0 < p.n; v0 += stride) {
         const int64_t v = v0 + lane;
         const bool live = v < p.n;
-        int32_t pv = -1, c = 0, beg = 0, d = 0;
+        int32_t pv = -1, c = 0, d = 0;
+        eoff beg = 0;
         if (live) {
             pv = p.part[v];
             c = p.vwgt[v];
             beg = p.xadj[v];
-            d = p.xadj[v + 1] - beg;
+            d = (int32_t)(p.xadj[v + 1] - beg);
         }
         const bool pv_ok = pv >= 0 && pv < p.k;
         if (live) {
@@ -861,8 +862,10 @@ kp_status pipeline_host_impl(const kp_graph *hg, const kp_options *o, int32_t k,
     if (!hg || !o || !ip || !out) return set_error(KP_ERR_INVALID, "null argument");
     if (hg->n < 0 || hg->nnz < 0) return set_error(KP_ERR_INVALID, "negative size");
     if (k < 1) return set_error(KP_ERR_INVALID, "k must be >= 1");
-    const int32_t n = hg->n, nnz = hg->nnz;
-    int32_t *d_xadj = nullptr, *d_adj = nullptr, *d_w = nullptr, *d_c = nullptr;
+    const int32_t n = hg->n;
+    const eoff nnz = hg->nnz;
+    eoff *d_xadj = nullptr;
+    int32_t *d_adj = nullptr, *d_w = nullptr, *d_c = nullptr;
     int32_t *d_cpart = nullptr, *d_fpart = nullptr, *d_target = nullptr;
     int64_t *d_gain = nullptr, *d_bw = nullptr;
     kp_hierarchy *h = nullptr;
@@ -891,7 +894,7 @@ kp_status pipeline_host_impl(const kp_graph *hg, const kp_options *o, int32_t k,
     PH(dev_alloc_n(&d_target, n, s));
     PH(dev_alloc_n(&d_gain, n, s));
     PH(dev_alloc_n(&d_bw, k, s));
-    PH_CUDA(cudaMemcpyAsync(d_xadj, hg->xadj, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice, s));
+    PH_CUDA(cudaMemcpyAsync(d_xadj, hg->xadj, sizeof(eoff) * ((size_t)n + 1), cudaMemcpyHostToDevice, s));
     if (nnz > 0) {
         PH_CUDA(cudaMemcpyAsync(d_adj, hg->adjncy, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
         PH_CUDA(cudaMemcpyAsync(d_w, hg->ewgt, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));

@@ -54,10 +54,10 @@ __device__ __forceinline__ bool gedge_before(const GEdge &a, const GEdge &b) {
 }
 
 // Entry of neighbour y in x's row (rows are sorted), -1 if absent.
-__device__ __forceinline__ int32_t gpa_entry(const DevLevel &L, int32_t x, int32_t y) {
-    int32_t lo = KP_LDG(L.xadj + x), hi = KP_LDG(L.xadj + x + 1) - 1;
+__device__ __forceinline__ eoff gpa_entry(const DevLevel &L, int32_t x, int32_t y) {
+    eoff lo = KP_LDG(L.xadj + x), hi = KP_LDG(L.xadj + x + 1) - 1;
     while (lo <= hi) {
-        const int32_t mid = lo + ((hi - lo) >> 1);
+        const eoff mid = lo + ((hi - lo) >> 1);
         const int32_t a = KP_LDG(L.adjncy + mid);
         if (a == y) return mid;
         if (a < y) lo = mid + 1;
@@ -68,7 +68,7 @@ __device__ __forceinline__ int32_t gpa_entry(const DevLevel &L, int32_t x, int32
 
 template <int R>
 __device__ __forceinline__ GEdge gpa_edge(const DevLevel &L, const Work &w, int32_t x, int32_t y) {
-    const int32_t e = gpa_entry(L, x, y);
+    const eoff e = gpa_entry(L, x, y);
     const int32_t wt = e >= 0 ? KP_LDG(L.ewgt + e) : 0;
     const HashCtx hc = hash_ctx(w, L, x);
     GEdge g;
@@ -82,7 +82,7 @@ __device__ __forceinline__ GEdge gpa_edge(const DevLevel &L, const Work &w, int3
 // The rating of {x,y} as a double for the dynamic programme.
 template <int R>
 __device__ __forceinline__ double gpa_weight(const DevLevel &L, int32_t x, int32_t y) {
-    const int32_t e = gpa_entry(L, x, y);
+    const eoff e = gpa_entry(L, x, y);
     const int32_t wt = e >= 0 ? KP_LDG(L.ewgt + e) : 0;
     uint64_t num, den;
     rating_ab<R>(wt, rating_attr<R>(L.vwgt, L.outw, x), rating_attr<R>(L.vwgt, L.outw, y), num, den);
@@ -118,13 +118,13 @@ __device__ __forceinline__ void gpa_rate_node(const DevLevel &L, const Work &w, 
         const int32_t c = __ldcg(w.cand + u);
         if (c >= 0 && c != mine.x && __ldcg(w.gnb + 2 * (int64_t)c + 1) < 0) return;
     }
-    const int32_t beg = KP_LDG(L.xadj + u), end = KP_LDG(L.xadj + u + 1);
+    const eoff beg = KP_LDG(L.xadj + u), end = KP_LDG(L.xadj + u + 1);
     const int32_t au = rating_attr<R>(L.vwgt, L.outw, u);
     const HashCtx hc = hash_ctx(w, L, u);
     Cand best;
     best.u = -1;
     best.num = best.den = best.h = 0;
-    for (int32_t e = beg + gl; e < end; e += G) {
+    for (eoff e = beg + gl; e < end; e += G) {
         const int32_t v = KP_LDG(L.adjncy + e);
         if (v == mine.x) continue;
         if (__ldcg(w.gnb + 2 * (int64_t)v + 1) >= 0) continue;
@@ -337,7 +337,7 @@ __device__ bool phase_gpa(DevState *st, int level, const Work &w) {
     for (int64_t v = tid; v < L.n; v += nthreads) {
         reinterpret_cast<int2 *>(w.gnb)[v] = make_int2(-1, -1);
         w.gclose[v] = -1;
-        w.match[v] = v;
+        w.match[v] = (int32_t)v;
     }
     for (int64_t e = tid; e < L.nnz; e += nthreads) w.grej[e] = 0;
     if (!grid_sync(&ctr->bar, &ctr->err, w.spin_limit)) return give_up();
@@ -372,7 +372,7 @@ __device__ bool phase_gpa(DevState *st, int level, const Work &w) {
             if (d == GPA_WAIT) continue;
             const int32_t u = __ldcg(w.gpend + i), v = __ldcg(w.cand + u);
             if (d == GPA_REFUSE) {
-                const int32_t e1 = gpa_entry(L, u, v), e2 = gpa_entry(L, v, u);
+                const eoff e1 = gpa_entry(L, u, v), e2 = gpa_entry(L, v, u);
                 if (e1 >= 0) w.grej[e1] = 1;
                 if (e2 >= 0) w.grej[e2] = 1;
                 w.cand[u] = -2;   // both ends look for their next best edge

@@ -2,12 +2,17 @@
 // coarsened graph (every level, every map, a batch's offsets) can be kept
 // and refined later without coarsening again.  The file is little-endian:
 //
-//   u64 magic "KPHIER01", i32 version (1), i32 levels L, i32 num_graphs G,
-//   i32 reserved; then for l = 0..L-1: i32 n, i32 nnz, int32 xadj[n+1],
+//   u64 magic "KPHIER01", i32 version, i32 levels L, i32 num_graphs G,
+//   i32 reserved; then for l = 0..L-1 the level's sizes and row offsets --
+//   version 1 (32-bit offsets): i32 n, i32 nnz, int32 xadj[n+1]; version 2
+//   (64-bit offsets): i32 n, i32 0, i64 nnz, int64 xadj[n+1] -- then
 //   adjncy[nnz], ewgt[nnz], vwgt[n], and for l < L-1 map[n]; for a batch
-//   (G > 0) also goff[G+1] per level, then glevels[G] and gid0[n_0].
+//   (G > 0) also goff[G+1] per level, then glevels[G] and gid0[n_0].  A
+//   library writes the version of its own offset width and reads both (a
+//   32-bit build refuses a level of 2^31 entries or more).
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "kp_internal.cuh"
@@ -17,7 +22,7 @@ using namespace kp;
 namespace {
 
 constexpr uint64_t KP_HIER_MAGIC = 0x313052454948504bull;   // "KPHIER01"
-constexpr int32_t KP_HIER_VERSION = 1;
+constexpr int32_t KP_HIER_VERSION = KP_OFFSET_BITS == 64 ? 2 : 1;
 
 struct File {
     FILE *f = nullptr;
@@ -37,11 +42,12 @@ kp_status get(FILE *f, void *p, size_t bytes) {
 }
 
 // A device array to the file through a host buffer.
-kp_status put_dev(FILE *f, const int32_t *d, int64_t count, std::vector<int32_t> &buf) {
+template <class T>
+kp_status put_dev(FILE *f, const T *d, int64_t count, std::vector<T> &buf) {
     if (count <= 0) return KP_OK;
     buf.resize((size_t)count);
-    KP_CUDA(cudaMemcpy(buf.data(), d, sizeof(int32_t) * (size_t)count, cudaMemcpyDeviceToHost));
-    return put(f, buf.data(), sizeof(int32_t) * (size_t)count);
+    KP_CUDA(cudaMemcpy(buf.data(), d, sizeof(T) * (size_t)count, cudaMemcpyDeviceToHost));
+    return put(f, buf.data(), sizeof(T) * (size_t)count);
 }
 
 }  // namespace
@@ -60,11 +66,19 @@ extern "C" kp_status kp_hierarchy_save(const kp_hierarchy *h, const char *path) 
     KP_TRY(put(f, &magic, 8));
     KP_TRY(put(f, head, sizeof head));
     std::vector<int32_t> buf;
+    std::vector<eoff> xbuf;
     for (int32_t l = 0; l < L; l++) {
         const kp_level &lv = h->levels[(size_t)l];
-        const int32_t sz[2] = {lv.n, lv.nnz};
-        KP_TRY(put(f, sz, sizeof sz));
-        KP_TRY(put_dev(f, lv.xadj, (int64_t)lv.n + 1, buf));
+        if (KP_HIER_VERSION == 1) {
+            const int32_t sz[2] = {lv.n, (int32_t)lv.nnz};
+            KP_TRY(put(f, sz, sizeof sz));
+        } else {
+            const int32_t sz[2] = {lv.n, 0};
+            const int64_t nnz = lv.nnz;
+            KP_TRY(put(f, sz, sizeof sz));
+            KP_TRY(put(f, &nnz, sizeof nnz));
+        }
+        KP_TRY(put_dev(f, lv.xadj, (int64_t)lv.n + 1, xbuf));
         KP_TRY(put_dev(f, lv.adjncy, lv.nnz, buf));
         KP_TRY(put_dev(f, lv.ewgt, lv.nnz, buf));
         KP_TRY(put_dev(f, lv.vwgt, lv.n, buf));
@@ -92,19 +106,22 @@ extern "C" kp_status kp_hierarchy_load(const char *path, kp_stream stream, kp_hi
     KP_TRY(get(f, &magic, 8));
     KP_TRY(get(f, head, sizeof head));
     if (magic != KP_HIER_MAGIC) return set_error(KP_ERR_INVALID, "not a hierarchy file");
-    if (head[0] != KP_HIER_VERSION) return set_error(KP_ERR_UNSUPPORTED, "hierarchy file version");
+    if (head[0] != 1 && head[0] != 2) return set_error(KP_ERR_UNSUPPORTED, "hierarchy file version");
+    const bool wide_file = head[0] == 2;
     const int32_t L = head[1], G = head[2];
     if (L < 1 || L > 128 || G < 0) return set_error(KP_ERR_INVALID, "bad hierarchy header");   // at most 128 levels
 
     // everything is read and checked on the host before anything reaches the
     // device: the kernels index with these arrays
     struct HostLevel {
-        int32_t n = 0, nnz = 0;
-        std::vector<int32_t> xadj, adjncy, ewgt, vwgt, map, goff;
+        int32_t n = 0;
+        int64_t nnz = 0;
+        std::vector<int64_t> xadj;   // the file's offsets, widened
+        std::vector<int32_t> adjncy, ewgt, vwgt, map, goff;
     };
     std::vector<HostLevel> lv((size_t)L);
     auto rd = [&](std::vector<int32_t> &v, int64_t count) -> kp_status {
-        if (count < 0 || count > (1ll << 31)) return set_error(KP_ERR_INVALID, "bad array size in hierarchy file");
+        if (count < 0 || count > (1ll << 32)) return set_error(KP_ERR_INVALID, "bad array size in hierarchy file");
         v.resize((size_t)count);
         return get(f, v.data(), sizeof(int32_t) * (size_t)count);
     };
@@ -114,9 +131,19 @@ extern "C" kp_status kp_hierarchy_load(const char *path, kp_stream stream, kp_hi
         KP_TRY(get(f, sz, sizeof sz));
         H.n = sz[0];
         H.nnz = sz[1];
+        if (wide_file) KP_TRY(get(f, &H.nnz, sizeof H.nnz));
         if (H.n < 0 || H.nnz < 0 || (l > 0 && H.n > lv[(size_t)l - 1].n))
             return set_error(KP_ERR_INVALID, "bad level sizes in hierarchy file");
-        KP_TRY(rd(H.xadj, (int64_t)H.n + 1));
+        if (H.nnz >= NNZ_LIMIT)
+            return set_error(KP_ERR_OVERFLOW, "a level of the hierarchy file has more entries than this build's offsets hold");
+        if (wide_file) {
+            H.xadj.resize((size_t)H.n + 1);
+            KP_TRY(get(f, H.xadj.data(), sizeof(int64_t) * H.xadj.size()));
+        } else {
+            std::vector<int32_t> x32;
+            KP_TRY(rd(x32, (int64_t)H.n + 1));
+            H.xadj.assign(x32.begin(), x32.end());
+        }
         KP_TRY(rd(H.adjncy, H.nnz));
         KP_TRY(rd(H.ewgt, H.nnz));
         KP_TRY(rd(H.vwgt, H.n));
@@ -134,7 +161,7 @@ extern "C" kp_status kp_hierarchy_load(const char *path, kp_stream stream, kp_hi
         const HostLevel &H = lv[(size_t)l];
         bool ok = H.xadj[0] == 0 && H.xadj[(size_t)H.n] == H.nnz;
         for (int32_t v = 0; ok && v < H.n; v++) ok = H.xadj[(size_t)v] <= H.xadj[(size_t)v + 1];
-        for (int32_t e = 0; ok && e < H.nnz; e++) ok = H.adjncy[(size_t)e] >= 0 && H.adjncy[(size_t)e] < H.n;
+        for (int64_t e = 0; ok && e < H.nnz; e++) ok = H.adjncy[(size_t)e] >= 0 && H.adjncy[(size_t)e] < H.n;
         if (G > 0) {
             ok = ok && H.goff[0] == 0 && H.goff[(size_t)G] == H.n;
             for (int32_t g = 0; ok && g < G; g++) ok = H.goff[(size_t)g] <= H.goff[(size_t)g + 1];
@@ -180,20 +207,24 @@ extern "C" kp_status kp_hierarchy_load(const char *path, kp_stream stream, kp_hi
         return st;
     };
     if (cudaGetDevice(&h->device) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "device"));
-    auto up = [&](int32_t **dst, const std::vector<int32_t> &src) -> kp_status {
+    auto up = [&](auto **dst, const auto &src) -> kp_status {
+        using T = typename std::remove_reference<decltype(src)>::type::value_type;
         KP_TRY(dev_alloc_n(dst, (int64_t)src.size(), s));
         h->allocations.push_back(*dst);
         if (!src.empty())
-            KP_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(int32_t) * src.size(), cudaMemcpyHostToDevice, s));
+            KP_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
         return KP_OK;
     };
+    // the offsets in this build's width (every value is below NNZ_LIMIT)
+    std::vector<std::vector<eoff>> xs((size_t)L);
+    for (int32_t l = 0; l < L; l++) xs[(size_t)l].assign(lv[(size_t)l].xadj.begin(), lv[(size_t)l].xadj.end());
     for (int32_t l = 0; l < L; l++) {
         const HostLevel &H = lv[(size_t)l];
         kp_level k;
         k.n = H.n;
-        k.nnz = H.nnz;
+        k.nnz = (eoff)H.nnz;
         k.owned = true;
-        kp_status st = up(&k.xadj, H.xadj);
+        kp_status st = up(&k.xadj, xs[(size_t)l]);
         if (st == KP_OK) st = up(&k.adjncy, H.adjncy);
         if (st == KP_OK) st = up(&k.ewgt, H.ewgt);
         if (st == KP_OK) st = up(&k.vwgt, H.vwgt);

@@ -27,6 +27,14 @@ struct TraceRange {
 
 namespace kp {
 
+// Entry offsets and counts (CSR row offsets, entry indices, nnz): int32 in
+// the default build, int64 in the wide build (KP_WIDE_OFFSETS).  Node ids,
+// degrees and weights stay int32 in both.
+using eoff = kp_eoff;
+// Inputs have nnz below this: the int32 range, or in the wide build 2^32
+// (nnz = 2|E|, omega >= 1 and the sum of omega below 2^31).
+constexpr int64_t NNZ_LIMIT = KP_OFFSET_BITS == 64 ? (1ll << 32) : (1ll << 31);
+
 // ---------------------------------------------------------------------------
 // error state (host)
 // ---------------------------------------------------------------------------
@@ -287,8 +295,8 @@ inline int64_t scan_tiles(int64_t count) { return (count + SCAN_TILE - 1) / SCAN
 // The hierarchy handle (opaque to C callers).
 struct kp_level {
     int32_t n = 0;
-    int32_t nnz = 0;
-    int32_t *xadj = nullptr;
+    kp_eoff nnz = 0;
+    kp_eoff *xadj = nullptr;
     int32_t *adjncy = nullptr;
     int32_t *ewgt = nullptr;
     int32_t *vwgt = nullptr;

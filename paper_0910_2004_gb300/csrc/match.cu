@@ -10,7 +10,7 @@ namespace kp {
 // lanes per node (G = 1 for sparse graphs: a thread sums its short row with
 // independent loads, so many rows are in flight), grid-stride over nodes.
 template <int G>
-__global__ void k_out_weight(int32_t n, const int32_t *__restrict__ xadj, const int32_t *__restrict__ ewgt,
+__global__ void k_out_weight(int32_t n, const eoff *__restrict__ xadj, const int32_t *__restrict__ ewgt,
                              int32_t *__restrict__ outw) {
     const int gl = threadIdx.x & (G - 1);
     const unsigned gmask = group_mask<G>();
@@ -18,9 +18,9 @@ __global__ void k_out_weight(int32_t n, const int32_t *__restrict__ xadj, const 
     // the loop bound is the same for the G lanes of a group (shuffles below)
     for (int64_t v = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; v < n; v += groups) {
         int64_t s = 0;
-        const int32_t beg = xadj[v], end = xadj[v + 1];
+        const eoff beg = xadj[v], end = xadj[v + 1];
 #pragma unroll 4
-        for (int32_t e = beg + gl; e < end; e += G) s += ewgt[e];
+        for (eoff e = beg + gl; e < end; e += G) s += ewgt[e];
 #pragma unroll
         for (int off = G / 2; off > 0; off >>= 1) s += __shfl_xor_sync(gmask, s, off);
         if (gl == 0) outw[v] = (int32_t)s;
@@ -118,14 +118,14 @@ __global__ void k_graph_ids(int32_t n0, int32_t num_graphs, const int32_t *__res
 }
 
 // Every edge of a batch stays inside its graph.
-__global__ void k_check_batch_edges(int32_t n, const int32_t *__restrict__ xadj, const int32_t *__restrict__ adjncy,
+__global__ void k_check_batch_edges(int32_t n, const eoff *__restrict__ xadj, const int32_t *__restrict__ adjncy,
                                     const int32_t *__restrict__ gid, const int32_t *__restrict__ goff,
                                     int32_t *flag) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
         const int32_t g = gid[v];
         const int32_t lo = goff[g], hi = goff[g + 1];
-        for (int32_t e = xadj[v]; e < xadj[v + 1]; e++) {
+        for (eoff e = xadj[v]; e < xadj[v + 1]; e++) {
             const int32_t u = adjncy[e];
             if (u < lo || u >= hi) {
                 atomicOr(flag, 1);
@@ -152,7 +152,7 @@ kp_status launch_check_batch_edges(const kp_graph *g, const int32_t *gid, const 
     return KP_OK;
 }
 
-kp_status launch_out_weight(DevState *, int32_t n0, int64_t nnz0, const int32_t *xadj, const int32_t *ewgt,
+kp_status launch_out_weight(DevState *, int32_t n0, int64_t nnz0, const eoff *xadj, const int32_t *ewgt,
                             int32_t *outw, cudaStream_t s, int32_t *launches) {
     const bool sparse = nnz0 <= 16ll * n0;
     const int64_t threads = (int64_t)n0 * (sparse ? 1 : 8);

@@ -26,7 +26,7 @@ __device__ void phase_level_begin(DevState *st, int level, const Work &w) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // what the level carves at most: map, c', batch ids and offsets,
         // coarse xadj, entries (at most nnz), Out, each 256-byte aligned
-        arena_reserve(st, 24ull * (unsigned long long)L.n + 8ull * (unsigned long long)L.nnz +
+        arena_reserve(st, (20ull + sizeof(eoff)) * (unsigned long long)L.n + 8ull * (unsigned long long)L.nnz +
                               4ull * ((unsigned long long)w.num_graphs + 1) + 8ull * 256ull);
         int32_t *map = (int32_t *)arena_carve(st, 4ull * (unsigned long long)L.n);
         int32_t *cv = map ? (int32_t *)arena_carve(st, 4ull * (unsigned long long)L.n) : nullptr;
@@ -75,7 +75,7 @@ __device__ void phase_level_begin(DevState *st, int level, const Work &w) {
         // to launch); the last warp to add its part writes it
         int32_t d = 0;
         for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < L.n; v += stride)
-            d = max(d, L.xadj[v + 1] - L.xadj[v]);
+            d = max(d, (int32_t)(L.xadj[v + 1] - L.xadj[v]));
         d = __reduce_max_sync(0xffffffffu, d);
         if ((threadIdx.x & 31) == 0) {
             atomicMax(&st->maxdeg0, d);
@@ -136,7 +136,7 @@ __device__ __forceinline__ bool cas_offer(Offer *addr, const Offer &expect, cons
 
 // Lanes per proposing node from the level's mean degree, and the row length
 // above which a node is left to the later passes.
-__device__ __forceinline__ int suitor_group(int32_t n, int32_t nnz) {
+__device__ __forceinline__ int suitor_group(int32_t n, eoff nnz) {
     const int64_t a = n > 0 ? (int64_t)nnz : 0;
     if (a <= 12ll * n) return 1;
     if (a <= 40ll * n) return 4;
@@ -179,7 +179,7 @@ __device__ __forceinline__ bool eligible_at(const HashCtx &hc, int32_t cur, int3
 // cur's row; the best eligible edge is kept.
 template <int R, int STRIDE>
 __device__ __forceinline__ void scan_row(const DevLevel &L, const Work &w, const HashCtx &hc, int32_t cur,
-                                         int32_t acur, int32_t e0, int32_t end, Proposal &best) {
+                                         int32_t acur, eoff e0, eoff end, Proposal &best) {
     const int32_t *KP_RESTRICT adjncy = L.adjncy;
     const int32_t *KP_RESTRICT ewgt = L.ewgt;
     best.c.u = -1;
@@ -187,7 +187,7 @@ __device__ __forceinline__ void scan_row(const DevLevel &L, const Work &w, const
     best.w = 0;
     best.snap = {-1, 0, 0, 0};
 #pragma unroll 4
-    for (int32_t e = e0; e < end; e += STRIDE) {
+    for (eoff e = e0; e < end; e += STRIDE) {
         const int32_t v = KP_LDG(adjncy + e);
         const int32_t wt = KP_LDG(ewgt + e);
         const Offer st = ld_offer(w.offer + v);
@@ -210,7 +210,7 @@ struct Cached {
 // share and counts the eligible edges it saw (up to 3).
 template <int R, int STRIDE>
 __device__ __forceinline__ void scan_row_top2(const DevLevel &L, const Work &w, const HashCtx &hc, int32_t cur,
-                                              int32_t acur, int32_t e0, int32_t end, Proposal &best, Cached &second,
+                                              int32_t acur, eoff e0, eoff end, Proposal &best, Cached &second,
                                               int32_t &seen) {
     const int32_t *KP_RESTRICT adjncy = L.adjncy;
     const int32_t *KP_RESTRICT ewgt = L.ewgt;
@@ -222,7 +222,7 @@ __device__ __forceinline__ void scan_row_top2(const DevLevel &L, const Work &w, 
     second.w = 0;
     seen = 0;
 #pragma unroll 4
-    for (int32_t e = e0; e < end; e += STRIDE) {
+    for (eoff e = e0; e < end; e += STRIDE) {
         const int32_t v = KP_LDG(adjncy + e);
         const int32_t wt = KP_LDG(ewgt + e);
         const Offer st = ld_offer(w.offer + v);
@@ -306,7 +306,7 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
     const int gl = lane & (G - 1);
     const int leader = lane & ~(G - 1);
     const unsigned below_leader = (1u << leader) - 1u;
-    const int32_t *KP_RESTRICT xadj = L.xadj;
+    const eoff *KP_RESTRICT xadj = L.xadj;
     const int64_t count = L.n;
     int64_t pos = 0, stop = 0;
     long long iters = 0;
@@ -340,7 +340,7 @@ __device__ __forceinline__ void suitor_body(const DevLevel &L, const Work &w, Co
             aborted = true;
             continue;
         }
-        const int32_t beg = KP_LDG(xadj + cur), end = KP_LDG(xadj + cur + 1);
+        const eoff beg = KP_LDG(xadj + cur), end = KP_LDG(xadj + cur + 1);
         if (end - beg > HEAVY) {
             if (gl == 0) w.list0[atomicAdd(&ctr->list_size[0], 1)] = cur;
             cur = -1;
@@ -387,7 +387,7 @@ __device__ __forceinline__ void suitor_warp(const DevLevel &L, const Work &w, Co
             if (lane == 0) atomicOr(err, ERR_TIMEOUT);
             break;
         }
-        const int32_t beg = KP_LDG(L.xadj + cur), end = KP_LDG(L.xadj + cur + 1);
+        const eoff beg = KP_LDG(L.xadj + cur), end = KP_LDG(L.xadj + cur + 1);
         if (end - beg > SUITOR_WARP_ROW) {
             if (lane == 0) park_wide(w, ctr, cur);
             cur = -1;
@@ -512,7 +512,7 @@ __device__ __forceinline__ void suitor_wide(const DevLevel &L, const Work &w, Co
         const int32_t c = s_cur;
         if (c < 0) break;
         const int32_t slot = s_slot;
-        const int32_t beg = KP_LDG(L.xadj + c), end = KP_LDG(L.xadj + c + 1);
+        const eoff beg = KP_LDG(L.xadj + c), end = KP_LDG(L.xadj + c + 1);
         const int32_t ac = rating_attr<R>(L.vwgt, L.outw, c);
         const HashCtx hc = hash_ctx(w, L, c);
         scans++;
@@ -524,7 +524,7 @@ __device__ __forceinline__ void suitor_wide(const DevLevel &L, const Work &w, Co
             Proposal best;
             Cached second;
             int32_t seen;
-            scan_row_top2<R, MATCH_BLOCK>(L, w, hc, c, ac, beg + (int32_t)threadIdx.x, end, best, second, seen);
+            scan_row_top2<R, MATCH_BLOCK>(L, w, hc, c, ac, beg + (eoff)threadIdx.x, end, best, second, seen);
             const int32_t kept = min(seen, 2);
             int32_t idx = 0, filled = 0;
             for (int k = 0; k < SUITOR_CACHE_K; k++) {
@@ -664,13 +664,13 @@ __device__ __forceinline__ void rate_node(const DevLevel &L, const Work &w, Coun
     need = __shfl_sync(gmask, need, leader);
     if (!need) return;
     if (gl == 0) atomicAdd(&ctr->searches, 1ull);
-    const int32_t beg = KP_LDG(L.xadj + v), end = KP_LDG(L.xadj + v + 1);
+    const eoff beg = KP_LDG(L.xadj + v), end = KP_LDG(L.xadj + v + 1);
     const int32_t av = rating_attr<R>(L.vwgt, L.outw, v);
     const HashCtx hc = hash_ctx(w, L, v);
     Cand best;
     best.u = -1;
     best.num = best.den = best.h = 0;
-    for (int32_t e = beg + gl; e < end; e += G) {
+    for (eoff e = beg + gl; e < end; e += G) {
         const int32_t u = KP_LDG(L.adjncy + e);
         if (w.match[u] != -1) continue;
         Cand c;
@@ -746,7 +746,7 @@ __device__ __forceinline__ void hand_phase(const Work &w, const int32_t *lst, in
     }
 }
 
-__device__ __forceinline__ int handshake_group(int32_t n, int32_t nnz) {
+__device__ __forceinline__ int handshake_group(int32_t n, eoff nnz) {
     const int64_t a = n > 0 ? (int64_t)nnz : 0;
     if (a <= 3ll * n) return 1;
     if (a <= 6ll * n) return 8;

@@ -25,7 +25,7 @@ constexpr int QSMEM_CELLS = 4096;
 constexpr int32_t QHUB_ROW = 2048;   // longer rows: a block each (k_quotient_hubs)
 constexpr int QHUB_BLOCK = 512;
 
-__device__ __forceinline__ void quotient_row_warp(int32_t u, int32_t pu, int32_t beg, int32_t end,
+__device__ __forceinline__ void quotient_row_warp(int32_t u, int32_t pu, eoff beg, eoff end,
                                                   const int32_t *__restrict__ adjncy,
                                                   const int32_t *__restrict__ ewgt,
                                                   const int32_t *__restrict__ part, int32_t k,
@@ -33,8 +33,8 @@ __device__ __forceinline__ void quotient_row_warp(int32_t u, int32_t pu, int32_t
     const int lane = threadIdx.x & 31;
     (void)u;
     {
-        for (int32_t e0 = beg; e0 < end; e0 += 32) {   // the same bounds for the whole warp
-            const int32_t e = e0 + lane;
+        for (eoff e0 = beg; e0 < end; e0 += 32) {   // the same bounds for the whole warp
+            const eoff e = e0 + lane;
             int32_t pv = -1;
             int32_t w = 0;
             if (e < end) {
@@ -66,7 +66,7 @@ __device__ __forceinline__ void quotient_row_warp(int32_t u, int32_t pu, int32_t
 // 32 nodes one after the other, and the warps holding several long rows of a
 // power-law graph would set the kernel's time.
 template <bool SMEM>
-__global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_acc(int32_t n, const int32_t *__restrict__ xadj,
+__global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_acc(int32_t n, const eoff *__restrict__ xadj,
                                                                const int32_t *__restrict__ adjncy,
                                                                const int32_t *__restrict__ ewgt,
                                                                const int32_t *__restrict__ part, int32_t k,
@@ -84,11 +84,12 @@ __global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_acc(int32_t n, const 
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); v0 < n; v0 += stride) {
         const int64_t u = v0 + lane;
-        int32_t pu = -1, beg = 0, d = 0;
+        int32_t pu = -1, d = 0;
+        eoff beg = 0;
         if (u < n) {
             pu = part[u];
             beg = xadj[u];
-            d = xadj[u + 1] - beg;
+            d = (int32_t)(xadj[u + 1] - beg);
             if (pu < 0 || pu >= k) {
                 atomicOr(err, 1);
                 pu = -1;
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_acc(int32_t n, const 
 // The listed hub rows, one block each: the weight towards every block is
 // summed in shared memory in one pass over the row (k 64-bit sums), then
 // each nonzero sum is added to its cell of the dense matrix.
-__global__ void __launch_bounds__(QHUB_BLOCK) k_quotient_hubs(const int32_t *__restrict__ xadj,
+__global__ void __launch_bounds__(QHUB_BLOCK) k_quotient_hubs(const eoff *__restrict__ xadj,
                                                               const int32_t *__restrict__ adjncy,
                                                               const int32_t *__restrict__ ewgt,
                                                               const int32_t *__restrict__ part, int32_t k,
@@ -180,8 +181,8 @@ __global__ void __launch_bounds__(QHUB_BLOCK) k_quotient_hubs(const int32_t *__r
         const int32_t pu = part[u];   // checked by the row kernel
         for (int32_t b = threadIdx.x; b < k; b += blockDim.x) s_bins[b] = 0;
         __syncthreads();
-        const int32_t beg = xadj[u], end = xadj[u + 1];
-        for (int32_t e = beg + threadIdx.x; e < end; e += blockDim.x) {
+        const eoff beg = xadj[u], end = xadj[u + 1];
+        for (eoff e = beg + threadIdx.x; e < end; e += blockDim.x) {
             const int32_t pv = part[adjncy[e]];
             if (pv < 0 || pv >= k) {
                 atomicOr(err, 1);
@@ -199,7 +200,7 @@ __global__ void __launch_bounds__(QHUB_BLOCK) k_quotient_hubs(const int32_t *__r
 // The listed long rows (QROW < d <= QHUB_ROW), one warp per row taken from a
 // counter (cells per block in shared memory when k*k <= QSMEM_CELLS).
 template <bool SMEM>
-__global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_mid(const int32_t *__restrict__ xadj,
+__global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_mid(const eoff *__restrict__ xadj,
                                                                const int32_t *__restrict__ adjncy,
                                                                const int32_t *__restrict__ ewgt,
                                                                const int32_t *__restrict__ part, int32_t k,
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(REFINE_BLOCK) k_quotient_mid(const int32_t *__
         i = __shfl_sync(0xffffffffu, i, 0);
         if (i >= count) break;
         const int32_t u = mids[i];
-        const int32_t beg = xadj[u], end = xadj[u + 1];
+        const eoff beg = xadj[u], end = xadj[u + 1];
         quotient_row_warp(u, part[u], beg, end, adjncy, ewgt, part, k, cells, err);
     }
     if (SMEM) {
@@ -294,7 +295,7 @@ __global__ void k_quotient_write(int32_t k, const unsigned long long *__restrict
 // a node of one pair block with a neighbour in the other), -1 for the other
 // nodes that take part, -2 for nodes outside the pair.  Boundary nodes form
 // the first frontier (warp-aggregated appends).
-__global__ void __launch_bounds__(REFINE_BLOCK) k_band_init(int32_t n, const int32_t *__restrict__ xadj,
+__global__ void __launch_bounds__(REFINE_BLOCK) k_band_init(int32_t n, const eoff *__restrict__ xadj,
                                                             const int32_t *__restrict__ adjncy,
                                                             const int32_t *__restrict__ part, int32_t k,
                                                             int32_t pa, int32_t pb, int32_t *dist,
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(REFINE_BLOCK) k_band_init(int32_t n, const int
                 dist[v] = -2;
             } else {
                 const int32_t want = pa < 0 ? -1 : (pv == pa ? pb : pa);   // -1: any other block
-                for (int32_t e = xadj[v]; e < xadj[v + 1]; e++) {
+                for (eoff e = xadj[v]; e < xadj[v + 1]; e++) {
                     const int32_t pu = part[adjncy[e]];
                     if (pu < 0 || pu >= k) {
                         atomicOr(err, 1);
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(REFINE_BLOCK) k_band_init(int32_t n, const int
 // takes depth itself, no atomics on dist.  The choice is made on the device
 // from the frontier size, the same for every block.  New nodes are appended
 // to the next frontier either way.
-__global__ void __launch_bounds__(REFINE_BLOCK) k_band_step(int32_t n, const int32_t *__restrict__ xadj,
+__global__ void __launch_bounds__(REFINE_BLOCK) k_band_step(int32_t n, const eoff *__restrict__ xadj,
                                                             const int32_t *__restrict__ adjncy,
                                                             const int32_t *__restrict__ part, int32_t *dist,
                                                             const int32_t *frontier, const int32_t *count,
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(REFINE_BLOCK) k_band_step(int32_t n, const int
             bool found = false;
             if (v < n && dist[v] == -1) {
                 const int32_t pv = part[v];
-                for (int32_t e = xadj[v]; e < xadj[v + 1]; e++) {
+                for (eoff e = xadj[v]; e < xadj[v + 1]; e++) {
                     const int32_t u = adjncy[e];
                     if (dist[u] == depth - 1 && part[u] == pv) {
                         found = true;
@@ -380,7 +381,8 @@ __global__ void __launch_bounds__(REFINE_BLOCK) k_band_step(int32_t n, const int
     }
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < cnt; i0 += stride) {
         const int64_t i = i0 + lane;
-        int32_t u = -1, beg = 0, end = 0, pu = -1;
+        int32_t u = -1, pu = -1;
+        eoff beg = 0, end = 0;
         if (i < cnt) {
             u = frontier[i];
             beg = xadj[u];

@@ -66,9 +66,12 @@ struct ServerGroup;
 
 struct ServerRequest {
     uint64_t id = 0;
-    std::vector<int32_t> own;   // the server's copy (empty when borrowed)
-    const int32_t *xadj = nullptr, *adjncy = nullptr, *ewgt = nullptr, *vwgt = nullptr;
-    int32_t n = 0, nnz = 0;
+    std::vector<eoff> own_x;    // the server's copy (empty when borrowed): offsets
+    std::vector<int32_t> own;   // and the other arrays
+    const eoff *xadj = nullptr;
+    const int32_t *adjncy = nullptr, *ewgt = nullptr, *vwgt = nullptr;
+    int32_t n = 0;
+    eoff nnz = 0;
     kp_request_params params{};
     int64_t footprint = 0;  // while running
     int64_t resident = 0;   // after the run, until release
@@ -126,7 +129,9 @@ namespace {
 // Device bytes of one request: what stays resident until release (the input
 // graph, the arena holding the coarse levels and maps, fine partition, gains,
 // targets) and the engine's level-0 scratch, freed when coarsening returns.
-int64_t resident_bytes(int64_t n, int64_t nnz) { return 8 * n + 8 * nnz + 64 * n + 32 * nnz + 16 * n + (1 << 20); }
+int64_t resident_bytes(int64_t n, int64_t nnz) {
+    return 8 * n + 8 * nnz + 64 * n + 32 * nnz + 16 * n + 2 * ((int64_t)sizeof(eoff) - 4) * n + (1 << 20);
+}
 int64_t scratch_bytes(int64_t n, int64_t nnz) { return 60 * n + 17 * nnz + (1 << 20); }
 
 // Stream-ordered frees on the group's stream; the caller does not wait.
@@ -155,7 +160,8 @@ kp_status run_group(kp_server *S, ServerGroup *g) {
     o.stop_size = g->reqs[0]->params.stop_size;   // a batch takes every graph's own
     // the group's graph: one request, or the disjoint union of several
     int64_t n = 0, nnz = 0, kt = 0;
-    std::vector<int32_t> off(G + 1, 0), eoff(G + 1, 0);
+    std::vector<int32_t> off(G + 1, 0);
+    std::vector<eoff> eo(G + 1, 0);
     for (size_t i = 0; i < G; i++) {
         ServerRequest *r = g->reqs[i];
         r->node_base = (int32_t)n;
@@ -164,12 +170,14 @@ kp_status run_group(kp_server *S, ServerGroup *g) {
         nnz += r->nnz;
         kt += r->params.k;
         off[i + 1] = (int32_t)n;
-        eoff[i + 1] = (int32_t)nnz;
+        eo[i + 1] = (eoff)nnz;
     }
-    if (n >= (1ll << 31) || nnz >= (1ll << 31)) return set_error(KP_ERR_OVERFLOW, "group too large");
+    if (n >= (1ll << 31) || nnz >= NNZ_LIMIT) return set_error(KP_ERR_OVERFLOW, "group too large");
     // host arrays of the group's graph: a single request's own, or the union
-    std::vector<int32_t> hx, ha, hw, hc;
-    const int32_t *px = g->reqs[0]->xadj, *pa = g->reqs[0]->adjncy, *pw = g->reqs[0]->ewgt, *pc = g->reqs[0]->vwgt;
+    std::vector<eoff> hx;
+    std::vector<int32_t> ha, hw, hc;
+    const eoff *px = g->reqs[0]->xadj;
+    const int32_t *pa = g->reqs[0]->adjncy, *pw = g->reqs[0]->ewgt, *pc = g->reqs[0]->vwgt;
     if (G > 1) {
         hx.resize((size_t)n + 1);
         ha.resize((size_t)nnz);
@@ -177,9 +185,9 @@ kp_status run_group(kp_server *S, ServerGroup *g) {
         hc.resize((size_t)n);
         for (size_t i = 0; i < G; i++) {
             ServerRequest *r = g->reqs[i];
-            for (int32_t v = 0; v <= r->n; v++) hx[(size_t)off[i] + v] = r->xadj[(size_t)v] + eoff[i];
-            for (int32_t e = 0; e < r->nnz; e++) ha[(size_t)eoff[i] + e] = r->adjncy[(size_t)e] + off[i];
-            std::memcpy(hw.data() + eoff[i], r->ewgt, sizeof(int32_t) * (size_t)r->nnz);
+            for (int32_t v = 0; v <= r->n; v++) hx[(size_t)off[i] + v] = r->xadj[(size_t)v] + eo[i];
+            for (eoff e = 0; e < r->nnz; e++) ha[(size_t)eo[i] + (size_t)e] = r->adjncy[(size_t)e] + off[i];
+            std::memcpy(hw.data() + eo[i], r->ewgt, sizeof(int32_t) * (size_t)r->nnz);
             std::memcpy(hc.data() + off[i], r->vwgt, sizeof(int32_t) * (size_t)r->n);
         }
         px = hx.data();
@@ -187,7 +195,8 @@ kp_status run_group(kp_server *S, ServerGroup *g) {
         pw = hw.data();
         pc = hc.data();
     }
-    int32_t *dx, *da, *dw, *dc, *doff, *dstops;
+    eoff *dx;
+    int32_t *da, *dw, *dc, *doff, *dstops;
     uint64_t *dseeds;
     KP_TRY(galloc(g, &dx, n + 1));
     KP_TRY(galloc(g, &da, nnz));
@@ -206,7 +215,7 @@ kp_status run_group(kp_server *S, ServerGroup *g) {
         seeds[i] = g->reqs[i]->params.seed;
         stops[i] = g->reqs[i]->params.stop_size;
     }
-    KP_CUDA(cudaMemcpyAsync(dx, px, sizeof(int32_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, s));
+    KP_CUDA(cudaMemcpyAsync(dx, px, sizeof(eoff) * (size_t)(n + 1), cudaMemcpyHostToDevice, s));
     if (nnz > 0) {
         KP_CUDA(cudaMemcpyAsync(da, pa, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
         KP_CUDA(cudaMemcpyAsync(dw, pw, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, s));
@@ -215,7 +224,7 @@ kp_status run_group(kp_server *S, ServerGroup *g) {
     KP_CUDA(cudaMemcpyAsync(doff, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice, s));
     KP_CUDA(cudaMemcpyAsync(dseeds, seeds.data(), sizeof(uint64_t) * G, cudaMemcpyHostToDevice, s));
     KP_CUDA(cudaMemcpyAsync(dstops, stops.data(), sizeof(int32_t) * G, cudaMemcpyHostToDevice, s));
-    kp_graph ug = {(int32_t)n, (int32_t)nnz, dx, da, dw, dc};
+    kp_graph ug = {(int32_t)n, (eoff)nnz, dx, da, dw, dc};
 
     // coarsen, partition the coarsest graphs, project
     std::vector<int32_t> csz(G), cpart, coff(G + 1, 0);
@@ -434,6 +443,7 @@ kp_status kp_server_submit(kp_server *S, const kp_graph *g, const kp_request_par
     if (!S || !g || !p || !id) return set_error(KP_ERR_INVALID, "null argument");
     if (g->n < 0 || g->nnz < 0 || (g->n > 0 && (!g->xadj || !g->vwgt)) || (g->nnz > 0 && (!g->adjncy || !g->ewgt)))
         return set_error(KP_ERR_INVALID, "bad graph");
+    if ((int64_t)g->nnz >= NNZ_LIMIT) return set_error(KP_ERR_OVERFLOW, "nnz >= 2^32: the edge weights sum to 2^31 or more");
     if (p->k < 1 || !(p->eps >= 0.0) || p->eps > 1000.0 || (p->flags & ~KP_REQUEST_BORROW))
         return set_error(KP_ERR_INVALID, "bad request parameters");
     const double t_in = S->now_us();   // latency includes the host copy
@@ -448,20 +458,21 @@ kp_status kp_server_submit(kp_server *S, const kp_graph *g, const kp_request_par
     } else {
         const size_t n1 = (size_t)g->n + 1, m = (size_t)g->nnz, n = (size_t)g->n;
         try {
-            r->own.resize(n1 + 2 * m + n);
+            r->own_x.resize(n1);
+            r->own.resize(2 * m + n);
         } catch (...) {
             delete r;
             return set_error(KP_ERR_OOM, "host copy of the request");
         }
+        std::memcpy(r->own_x.data(), g->xadj, sizeof(eoff) * n1);
         int32_t *b = r->own.data();
-        std::memcpy(b, g->xadj, 4 * n1);
-        if (m) std::memcpy(b + n1, g->adjncy, 4 * m);
-        if (m) std::memcpy(b + n1 + m, g->ewgt, 4 * m);
-        if (n) std::memcpy(b + n1 + 2 * m, g->vwgt, 4 * n);
-        r->xadj = b;
-        r->adjncy = b + n1;
-        r->ewgt = b + n1 + m;
-        r->vwgt = b + n1 + 2 * m;
+        if (m) std::memcpy(b, g->adjncy, 4 * m);
+        if (m) std::memcpy(b + m, g->ewgt, 4 * m);
+        if (n) std::memcpy(b + 2 * m, g->vwgt, 4 * n);
+        r->xadj = r->own_x.data();
+        r->adjncy = b;
+        r->ewgt = b + m;
+        r->vwgt = b + 2 * m;
     }
     r->params = *p;
     r->resident = resident_bytes(g->n, g->nnz);

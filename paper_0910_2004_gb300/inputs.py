@@ -29,7 +29,8 @@ __all__ = [
     "CSRGraph", "from_edges", "grid2d", "grid3d", "rgg2d", "rmat",
     "random_small_graph", "path_graph", "star_graph", "batch_rgg_sizes",
     "random_balanced_partition", "random_partition", "union_graph", "rgg2d_batch", "batch_partition",
-    "rmat_torch", "rgg2d_torch", "served_mix", "batch_partition_torch",
+    "rmat_torch", "rgg2d_torch", "served_mix", "batch_partition_torch", "circulant_strides", "circulant",
+    "circulant_torch",
 ]
 
 
@@ -438,3 +439,46 @@ def batch_partition_torch(coarse_sizes, k: int, seed: int, device: str = "cuda")
     rank = torch.empty(N, dtype=torch.int64, device=dev)
     rank[order] = torch.arange(N, device=dev) - off[gid[order]]
     return (rank % k).to(torch.int32), off.to(torch.int32)
+
+
+def circulant_strides(n: int, count: int, seed: int) -> np.ndarray:
+    """`count` distinct strides in [1, n/2) drawn with the seed (sorted)."""
+    rng = np.random.default_rng(seed)
+    hi = (n - 1) // 2   # s < n/2: v+s and v-s are different nodes
+    if count > hi:
+        raise ValueError("too many strides for n")
+    return np.sort(rng.choice(np.arange(1, hi + 1, dtype=np.int64), size=count, replace=False))
+
+
+def circulant(n: int, strides) -> CSRGraph:
+    """Circulant graph: node v is joined to v+s and v-s (mod n) for every
+    stride s; 2 * len(strides) neighbours per node, unit weights.  Pairs of a
+    matching share few neighbours, so contraction keeps most entries (the
+    sizes of a level barely fall while its nodes halve)."""
+    S = np.asarray(strides, dtype=np.int64)
+    D = np.concatenate([S, n - S])
+    v = np.arange(n, dtype=np.int64)[:, None]
+    adj = np.sort((v + D[None, :]) % n, axis=1).astype(np.int32).reshape(-1)
+    xadj = (np.arange(n + 1, dtype=np.int64) * D.size).astype(np.int32)
+    return CSRGraph(xadj, adj, np.ones(adj.size, np.int32), np.ones(n, np.int32), f"circulant_n{n}_k{S.size}")
+
+
+def circulant_torch(n: int, strides, device: str = "cuda", chunk: int = 1 << 23):
+    """circulant() built with torch on `device`, rows in chunks (large n:
+    more than 2^31 entries).  Returns device tensors (xadj int64, adjncy,
+    ewgt, vwgt int32)."""
+    import torch
+    dev = torch.device(device)
+    D = torch.as_tensor(np.concatenate([np.asarray(strides, np.int64), n - np.asarray(strides, np.int64)]),
+                        device=dev)
+    d = int(D.numel())
+    adj = torch.empty(n * d, dtype=torch.int32, device=dev)
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        v = torch.arange(a, b, dtype=torch.int64, device=dev)
+        nb, _ = torch.sort((v[:, None] + D[None, :]) % n, dim=1)
+        adj[a * d:b * d] = nb.to(torch.int32).reshape(-1)
+        del v, nb
+    xadj = torch.arange(n + 1, dtype=torch.int64, device=dev) * d
+    return (xadj, adj, torch.ones(n * d, dtype=torch.int32, device=dev),
+            torch.ones(n, dtype=torch.int32, device=dev))

@@ -13,14 +13,19 @@ import pytest
 MAGIC = b"KPHIER01"
 
 
-def write(path, levels, maps, goffs=None, glevels=None, gid0=None):
-    """levels: [(xadj, adjncy, ewgt, vwgt)], maps: one per level but the last."""
+def write(path, levels, maps, goffs=None, glevels=None, gid0=None, version=1):
+    """levels: [(xadj, adjncy, ewgt, vwgt)], maps: one per level but the last.
+    version 1: 32-bit row offsets; version 2: 64-bit (i32 n, i32 0, i64 nnz,
+    int64 xadj)."""
     G = 0 if goffs is None else len(goffs[0]) - 1
-    out = bytearray(MAGIC + struct.pack("<4i", 1, len(levels), G, 0))
+    out = bytearray(MAGIC + struct.pack("<4i", version, len(levels), G, 0))
     for l, (xadj, adj, ew, vw) in enumerate(levels):
         n, nnz = len(xadj) - 1, len(adj)
-        out += struct.pack("<2i", n, nnz)
-        for a in (xadj, adj, ew, vw):
+        if version == 1:
+            out += struct.pack("<2i", n, nnz) + np.asarray(xadj, dtype="<i4").tobytes()
+        else:
+            out += struct.pack("<2iq", n, 0, nnz) + np.asarray(xadj, dtype="<i8").tobytes()
+        for a in (adj, ew, vw):
             out += np.asarray(a, dtype="<i4").tobytes()
         if l < len(levels) - 1:
             out += np.asarray(maps[l], dtype="<i4").tobytes()
@@ -65,15 +70,32 @@ def union(*gs):
     return xadj, adj, ew, vw
 
 
-def test_single_graph_maps_must_stay_in_the_next_level(lib, tmp_path):
+@pytest.mark.parametrize("version", [1, 2])
+def test_single_graph_maps_must_stay_in_the_next_level(lib, tmp_path, version):
     from paper_0910_2004_gb300 import binding as B
     good = tmp_path / "good.kph"
-    write(good, [PATH, EDGE], [[0, 0, 1, 1]])
+    write(good, [PATH, EDGE], [[0, 0, 1, 1]], version=version)
     assert load_status(lib, good) in (B.KP_OK, B.KP_ERR_CUDA)
     for bad_map in ([0, 0, 1, 2], [0, 0, 1, -1], [-1, 0, 1, 1]):
         p = tmp_path / "bad.kph"
-        write(p, [PATH, EDGE], [bad_map])
+        write(p, [PATH, EDGE], [bad_map], version=version)
         assert load_status(lib, p) == B.KP_ERR_INVALID, bad_map
+    # row offsets that decrease, or end elsewhere than nnz
+    for bad_x in ([0, 1, 3, 2, 6], [0, 1, 3, 5, 5]):
+        p = tmp_path / "badx.kph"
+        write(p, [(bad_x,) + PATH[1:], EDGE], [[0, 0, 1, 1]], version=version)
+        assert load_status(lib, p) == B.KP_ERR_INVALID, bad_x
+
+
+def test_64_bit_offsets_beyond_the_32_bit_range_are_refused(lib, tmp_path):
+    """A version-2 level of 2^31 entries does not fit 32-bit offsets: the
+    32-bit library answers KP_ERR_OVERFLOW right after the level's sizes."""
+    from paper_0910_2004_gb300 import binding as B
+    p = tmp_path / "big.kph"
+    open(p, "wb").write(MAGIC + struct.pack("<4i", 2, 1, 0, 0) + struct.pack("<2iq", 5, 0, 1 << 31))
+    assert load_status(lib, p) == B.KP_ERR_OVERFLOW
+    open(p, "wb").write(MAGIC + struct.pack("<4i", 3, 1, 0, 0))
+    assert load_status(lib, p) == B.KP_ERR_UNSUPPORTED
 
 
 def test_batch_maps_stay_inside_their_graph(lib, tmp_path):

@@ -105,3 +105,18 @@ def test_single_graph_device_partition_is_balanced():
     part, off = I.batch_partition_torch([70001], 64, seed=3, device="cpu")
     counts = np.bincount(part.numpy(), minlength=64)
     assert counts.max() - counts.min() <= 1 and counts.sum() == 70001
+
+
+@pytest.mark.parametrize("n,count,seed", [(9, 4, 1), (101, 13, 2), (1000, 13, 3)])
+def test_circulant_structure_and_torch_equals_numpy(n, count, seed):
+    import oracle as O
+    S = I.circulant_strides(n, count, seed)
+    assert len(set(S.tolist())) == count and S.min() >= 1 and 2 * S.max() < n
+    g = I.circulant(n, S)
+    check_csr(g)
+    assert np.all(np.diff(g.xadj) == 2 * count)
+    assert O.validate(g) == 0
+    x, a, w, v = I.circulant_torch(n, S, device="cpu", chunk=7)
+    assert x.dtype == torch.int64
+    assert np.array_equal(x.numpy(), g.xadj) and np.array_equal(a.numpy(), g.adjncy)
+    assert np.array_equal(w.numpy(), g.ewgt) and np.array_equal(v.numpy(), g.vwgt)

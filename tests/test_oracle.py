@@ -214,6 +214,53 @@ def test_checker_rejects_wrong_matchings():
     assert O.check_greedy_matching(g, "expansion*2", 4, m2) >= 0
 
 
+@pytest.mark.parametrize("rating", ["expansion*2", "innerOuter", "weight"])
+def test_checker_at_listed_nodes_agrees_with_the_whole_pass(rating):
+    """The per-node form of the Greedy characterisation (for graphs too large
+    for a whole pass) passes exactly where the whole pass does: on every
+    Greedy matching, and it finds each planted defect."""
+    rng = np.random.default_rng(3)
+    for t, g in enumerate([I.grid2d(10, 10), I.random_small_graph(80, 0.08, 5, wmax=7, cmax=3),
+                           I.rmat(9, 4), I.circulant(101, I.circulant_strides(101, 5, 2))]):
+        nodes = np.arange(g.n, dtype=np.int32)
+        m, _ = O.greedy_matching(g, rating, t)
+        assert O.check_greedy_matching_at(g, rating, t, m, nodes) == -1
+        assert O.check_greedy_matching_at(g, rating, t, m, rng.permutation(nodes)[:7]) == -1
+        # unmatch one pair; match another seed's matching; break symmetry
+        bad1 = m.copy()
+        v = int(np.nonzero(bad1 != nodes)[0][0])
+        bad1[v], bad1[int(m[v])] = v, int(m[v])
+        bad2, _ = O.greedy_matching(g, rating, t + 100)
+        bad3 = m.copy()
+        bad3[v] = v
+        for bad in (bad1, bad2, bad3):
+            whole = O.check_greedy_matching(g, rating, t, bad)
+            if whole == -1:      # another seed may give the same matching
+                assert (bad == m).all()
+                continue
+            # found over all nodes (at `whole` or at a neighbour, which sees
+            # the broken matched edge of `whole`) and at `whole` alone
+            assert O.check_greedy_matching_at(g, rating, t, bad, nodes) != -1
+            assert O.check_greedy_matching_at(g, rating, t, bad, [whole]) == whole
+
+
+def test_coarse_row_equals_the_contraction():
+    """One coarse row from its members (for sampled checks of large graphs)
+    equals that row of the whole contraction, whose invariants are pinned in
+    test_contraction_invariants."""
+    for t, g in enumerate([I.grid2d(12, 9), I.random_small_graph(70, 0.1, 8, wmax=9, cmax=4), I.rmat(10, 3),
+                           I.star_graph(30), I.circulant(97, I.circulant_strides(97, 6, 4))]):
+        match, _ = O.greedy_matching(g, "expansion*2", t)
+        cg, mp = O.contract(g, match)
+        rows = [(int(mp[v]), v, int(match[v]) if int(match[v]) != v else -1)
+                for v in range(g.n) if int(match[v]) >= v]
+        assert len(rows) == cg.n
+        for (x, _, _), (adj, w, c) in zip(rows, O.coarse_rows(g, mp, rows)):
+            lo, hi = int(cg.xadj[x]), int(cg.xadj[x + 1])
+            assert np.array_equal(adj, cg.adjncy[lo:hi]) and np.array_equal(w, cg.ewgt[lo:hi]), (t, x)
+            assert c == int(cg.vwgt[x])
+
+
 def _brute_force_mwm(g, weights):
     edges = _edges(g)
     best = Fraction(0)
