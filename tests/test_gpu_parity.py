@@ -488,7 +488,10 @@ def test_saved_and_loaded_hierarchy_is_identical(tmp_path):
     # a map entry pointing past the next level is refused before any upload
     data = bytearray(open(path, "rb").read())
     n0, nnz0 = g.n, g.nnz
-    map0 = 24 + 8 + 4 * (n0 + 1) + 8 * nnz0 + 4 * n0
+    if B().OFFSET_BITS == 64:   # file version 2: i32 n, i32 0, i64 nnz, int64 xadj
+        map0 = 24 + 16 + 8 * (n0 + 1) + 8 * nnz0 + 4 * n0
+    else:                       # version 1: i32 n, i32 nnz, int32 xadj
+        map0 = 24 + 8 + 4 * (n0 + 1) + 8 * nnz0 + 4 * n0
     data[map0:map0 + 4] = np.int32(levels[1].n).tobytes()
     bad = str(tmp_path / "bad.kph")
     open(bad, "wb").write(bytes(data))
