@@ -305,7 +305,8 @@ __device__ __forceinline__ char *arena_carve(DevState *st, unsigned long long by
 //   void     Op::total(uint64_t t)         once, with the sum of all items
 //   void     Op::fail()                    a look-back wait ran out
 // Tiles are taken in order from a counter, so every tile's predecessors are
-// held by running blocks; each wait for a predecessor is bounded.
+// held by running blocks; each wait for a predecessor is bounded.  The look
+// back reads 32 predecessors at a time (one per lane of the first warp).
 // ---------------------------------------------------------------------------
 // Returns false when a look-back wait gave up (op.fail() has been called).
 template <class Op>
@@ -337,21 +338,32 @@ __device__ bool scan_lb_phase(Op &op, TileStatus *status, int32_t epoch, long lo
         }
         uint64_t total;
         const uint64_t excl = block_exclusive_scan<SCAN_BLOCK>(sum, &total);
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
+            // the first warp publishes the tile and looks back over its
+            // predecessors 32 at a time (lane i reads tile base - i); the
+            // nearest one with an inclusive prefix ends the walk, the
+            // aggregates of those after it are added
+            const int lane = threadIdx.x;
             unsigned long long prefix = 0;
             int ok = 1;
             TileStatus *me = status + tile;
             if (tile == 0) {
-                st_relaxed_u64(&me->incl, total);
-                st_release_i32(&me->flag, (epoch << 2) | 2);
+                if (lane == 0) {
+                    st_relaxed_u64(&me->incl, total);
+                    st_release_i32(&me->flag, (epoch << 2) | 2);
+                }
             } else {
-                st_relaxed_u64(&me->agg, total);
-                st_release_i32(&me->flag, (epoch << 2) | 1);
-                int64_t j = tile - 1;
+                if (lane == 0) {
+                    st_relaxed_u64(&me->agg, total);
+                    st_release_i32(&me->flag, (epoch << 2) | 1);
+                }
+                int64_t base = tile - 1;
                 long long it = 0;
-                while (j >= 0) {
-                    const int f = ld_acquire_i32(&status[j].flag);
-                    if ((f >> 2) != epoch || (f & 3) == 0) {
+                for (;;) {
+                    const int64_t j = base - lane;
+                    const int f = j >= 0 ? ld_acquire_i32(&status[j].flag) : ((epoch << 2) | 2);
+                    const bool ready = (f >> 2) == epoch && (f & 3) != 0;
+                    if (!__all_sync(0xffffffffu, ready)) {   // the same decision in every lane
                         if (++it > spin_limit) {
                             ok = 0;
                             break;
@@ -359,20 +371,29 @@ __device__ bool scan_lb_phase(Op &op, TileStatus *status, int32_t epoch, long lo
                         __nanosleep(32);
                         continue;
                     }
-                    if ((f & 3) == 2) {
-                        prefix += ld_relaxed_u64(&status[j].incl);
-                        break;
-                    }
-                    prefix += ld_relaxed_u64(&status[j].agg);
-                    j--;
+                    // tile 0 is inclusive, so a window that reaches it finds one
+                    const unsigned inc = __ballot_sync(0xffffffffu, j >= 0 && (f & 3) == 2);
+                    const int stop = inc ? __ffs(inc) - 1 : 32;
+                    unsigned long long v = 0;
+                    if (j >= 0 && lane < stop) v = ld_relaxed_u64(&status[j].agg);
+                    if (j >= 0 && lane == stop) v = ld_relaxed_u64(&status[j].incl);
+#pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+                    prefix += v;
+                    if (inc) break;
+                    base -= 32;
                 }
-                st_relaxed_u64(&me->incl, prefix + total);
-                st_release_i32(&me->flag, (epoch << 2) | 2);
+                if (lane == 0 && ok) {
+                    st_relaxed_u64(&me->incl, prefix + total);
+                    st_release_i32(&me->flag, (epoch << 2) | 2);
+                }
             }
-            s_prefix = prefix;
-            s_abort = !ok;
-            if (!ok) op.fail();
-            else if (tile == tiles - 1) op.total(prefix + total);
+            if (lane == 0) {
+                s_prefix = prefix;
+                s_abort = !ok;
+                if (!ok) op.fail();
+                else if (tile == tiles - 1) op.total(prefix + total);
+            }
         }
         __syncthreads();
         if (s_abort) return false;
