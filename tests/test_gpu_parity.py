@@ -178,6 +178,7 @@ def test_random_graphs(rating, matcher, tail):
 
 @pytest.mark.parametrize("make,rating", [
     (lambda: I.grid3d(23, 17, 9), "innerOuter"),
+    (lambda: I.grid3d(48, 40, 32), "innerOuter"),   # thousands of 17..32-entry coarse rows
     (lambda: I.grid2d(301, 77), "expansion*2"),
     (lambda: I.rgg2d(20000, 5, wmax=16), "expansion*2"),
     (lambda: I.rgg2d(30000, 6, mean_degree=14), "innerOuter"),
