@@ -33,9 +33,16 @@ __global__ void __launch_bounds__(MATCH_BLOCK, 3) k_tail(DevState *st, int first
     const long long lim = w.spin_limit;
     const bool in_cluster = mode >= TAIL_CLUSTER_AFTER;
     int start = first;
+    // a level's start (carving its map and coarse weights, clearing its
+    // offers) runs in the compaction phase of the level before, which reads
+    // none of what it writes: one barrier less per level.  The cluster part
+    // continues from a level the grid part has started, unless the grid
+    // part handed over at its own first level (it started none).
+    bool begun = false;
     if (mode == TAIL_CLUSTER_AFTER) {
         start = ld_relaxed_i32(&st->tail_resume);   // written by the previous launch
         if (start < first) return;   // the grid part finished the hierarchy
+        begun = start > first;
     }
     for (int level = start; level < last; level++) {
         // in a cluster every block must take the same decision: the level's
@@ -48,8 +55,11 @@ __global__ void __launch_bounds__(MATCH_BLOCK, 3) k_tail(DevState *st, int first
             if (blockIdx.x == 0 && threadIdx.x == 0) st->tail_resume = level;
             break;
         }
-        phase_level_begin<R, SUITOR>(st, level, w);
-        if (!grid_sync(bar, err, lim)) return;
+        if (!begun) {
+            phase_level_begin<R, SUITOR>(st, level, w);
+            if (!grid_sync(bar, err, lim)) return;
+        }
+        begun = false;
         if (SUITOR) {
             phase_suitor<R, SUITOR_FIRST>(st, level, w);
             if (!grid_sync(bar, err, lim)) return;
@@ -87,6 +97,12 @@ __global__ void __launch_bounds__(MATCH_BLOCK, 3) k_tail(DevState *st, int first
         }
         if (!grid_sync(bar, err, lim)) return;
         phase_compact(st, level, w);
+        if (level + 1 < last) {
+            // level+1's flags were decided by the degree scan (before the
+            // barrier above); the start returns at once if it is not active
+            phase_level_begin<R, SUITOR>(st, level + 1, w);
+            begun = true;
+        }
         if (!grid_sync(bar, err, lim)) return;
     }
 }
