@@ -218,8 +218,10 @@ typedef struct kp_hierarchy kp_hierarchy;
  *   o    options (host; NULL = defaults)
  *   out  receives the hierarchy (host pointer to a handle)
  * Blocks until the hierarchy is complete (level sizes are data-dependent).
- * Errors: KP_ERR_INVALID (malformed graph, with o->validate), KP_ERR_OVERFLOW,
- * KP_ERR_UNSUPPORTED (unknown rating or matcher), KP_ERR_OOM, KP_ERR_CUDA,
+ * Errors: KP_ERR_INVALID (malformed graph, with o->validate), KP_ERR_OVERFLOW
+ * (a weight sum out of range, with o->validate; nnz >= 2^32 in the wide
+ * build, always, before any device work), KP_ERR_UNSUPPORTED (unknown rating
+ * or matcher), KP_ERR_OOM, KP_ERR_CUDA,
  * KP_ERR_TIMEOUT (a grid-barrier wait, or a proposal chain longer than
  * spin_limit steps, gave up). */
 kp_status kp_coarsen(const kp_graph *g, const kp_options *o, kp_stream s, kp_hierarchy **out);
@@ -313,15 +315,19 @@ kp_status kp_hierarchy_level_offsets(const kp_hierarchy *h, int32_t l, const int
 
 /* Writes the whole hierarchy (every level's CSR and node weights, every map,
  * a batch's per-level offsets, per-graph level counts and graph ids) to a
- * file, little-endian: u64 magic "KPHIER01", i32 version 1, i32 levels,
- * i32 num_graphs, i32 0; per level i32 n, i32 nnz, xadj[n+1], adjncy[nnz],
+ * file, little-endian: u64 magic "KPHIER01", i32 version, i32 levels,
+ * i32 num_graphs, i32 0; per level its sizes and row offsets -- version 1
+ * (libkp, 32-bit offsets): i32 n, i32 nnz, int32 xadj[n+1]; version 2
+ * (libkp64): i32 n, i32 0, i64 nnz, int64 xadj[n+1] -- then adjncy[nnz],
  * ewgt[nnz], vwgt[n], map[n] (not on the coarsest), goff[G+1] (batches);
- * then glevels[G] and gid0[n_0] (batches); all int32.  Synchronises the
- * hierarchy's stream.  Errors: KP_ERR_INVALID (null arguments, the file
- * cannot be written), KP_ERR_CUDA. */
+ * then glevels[G] and gid0[n_0] (batches); everything else int32.
+ * Synchronises the hierarchy's stream.  Errors: KP_ERR_INVALID (null
+ * arguments, the file cannot be written), KP_ERR_CUDA. */
 kp_status kp_hierarchy_save(const kp_hierarchy *h, const char *path);
 
-/* Reads a file written by kp_hierarchy_save into device memory on the
+/* Reads a file written by kp_hierarchy_save (either version: offsets are
+ * converted to this library's width, and a level of 2^31 entries or more is
+ * refused by the 32-bit library with KP_ERR_OVERFLOW) into device memory on the
  * current device: every level, including the input level, is owned by the
  * returned hierarchy (release with kp_hierarchy_free); projection works as
  * on the original.  The whole file is read and checked on the host first
