@@ -156,7 +156,7 @@ typedef enum {
  * Tuning knobs (0: the built-in choice; results never depend on them, only
  * the time does -- kp_autotune picks them by measurement):
  *   suitor_lanes         lanes per proposing node in the first Suitor pass:
- *                        1, 4, 8 or 32 (0: from the level's mean degree);
+ *                        1, 2, 4, 8 or 32 (0: from the level's mean degree);
  *                        longer rows go to a warp (up to 1024 entries) or
  *                        a block each
  *   tail_block_nodes     nodes per block of the persistent tail launch,

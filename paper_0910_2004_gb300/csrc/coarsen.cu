@@ -245,8 +245,8 @@ kp_status coarsen_impl(const kp_graph *g, const kp_options *o, cudaStream_t s, k
     if (o->max_levels < 0 || o->max_levels > MAX_LEVELS - 8 || o->min_shrink_permille < 0 ||
         o->min_shrink_permille > 1000 || o->spin_limit <= 0 || o->arena_bytes < 0 || o->tail_nodes < -1)
         return set_error(KP_ERR_INVALID, "bad option value");
-    if (!(o->suitor_lanes == 0 || o->suitor_lanes == 1 || o->suitor_lanes == 4 || o->suitor_lanes == 8 ||
-          o->suitor_lanes == 32) ||
+    if (!(o->suitor_lanes == 0 || o->suitor_lanes == 1 || o->suitor_lanes == 2 || o->suitor_lanes == 4 ||
+          o->suitor_lanes == 8 || o->suitor_lanes == 32) ||
         (o->tail_block_nodes != 0 && (o->tail_block_nodes < 256 || o->tail_block_nodes > 16384)) ||
         (o->sort_shared_max != 0 && (o->sort_shared_max < 128 || o->sort_shared_max > MID_MAX)) ||
         (o->radix_bits != 0 && (o->radix_bits < 4 || o->radix_bits > 8)) || o->cluster_nodes < -1 ||

@@ -628,6 +628,7 @@ __device__ void phase_suitor(DevState *st, int level, const Work &w) {
     } else {
         switch (st->suitor_lanes ? st->suitor_lanes : suitor_group(L.n, L.nnz)) {
         case 1: suitor_body<R, 1, 32>(L, w, ctr, &st->err); break;
+        case 2: suitor_body<R, 2, 64>(L, w, ctr, &st->err); break;
         case 4: suitor_body<R, 4, 128>(L, w, ctr, &st->err); break;
         case 8: suitor_body<R, 8, 512>(L, w, ctr, &st->err); break;
         default: suitor_body<R, 32, 2048>(L, w, ctr, &st->err); break;

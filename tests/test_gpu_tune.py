@@ -49,7 +49,7 @@ HUBS = [(lambda: I.rmat(13, 21, edge_factor=64), "expansion*2"), (lambda: I.rmat
 
 
 @pytest.mark.parametrize("knob,values", [
-    ("suitor_lanes", [1, 4, 8, 32]),
+    ("suitor_lanes", [1, 2, 4, 8, 32]),
     ("suitor_blocks", [3, 4]),
     ("radix_bits", [4, 5, 6, 7]),
     ("sort_shared_max", [128, 512, 1024]),
@@ -72,7 +72,7 @@ def test_every_knob_value_gives_the_oracle_hierarchy(knob, values):
 
 def test_bad_knob_values_are_rejected():
     dg = B().DeviceGraph.from_csr(I.grid2d(8, 8))
-    for kw in [dict(suitor_lanes=2), dict(radix_bits=3), dict(radix_bits=9), dict(sort_shared_max=64),
+    for kw in [dict(suitor_lanes=3), dict(suitor_lanes=16), dict(radix_bits=3), dict(radix_bits=9), dict(sort_shared_max=64),
                dict(sort_shared_max=4096), dict(tail_block_nodes=100), dict(suitor_blocks=5)]:
         with pytest.raises(B().KpError) as e:
             B().coarsen(dg, **kw)
