@@ -87,7 +87,7 @@ extern "C" kp_status kp_autotune(const kp_graph *g, int32_t num_graphs, const in
     std::vector<Knob> knobs;
     knobs.push_back({&kp_options::tail_nodes, {-1, 1 << 14, 1 << 16, 1 << 18, 1 << 20, 0x7fffffff}});
     if (cur.matcher == KP_MATCHER_SUITOR) {
-        knobs.push_back({&kp_options::suitor_lanes, {1, 4, 8, 32}});
+        knobs.push_back({&kp_options::suitor_lanes, {1, 2, 4, 8, 32}});
         knobs.push_back({&kp_options::suitor_blocks, {3, 4}});
     }
     knobs.push_back({&kp_options::tail_block_nodes, {512, 1024, 2048, 4096, 8192}});
