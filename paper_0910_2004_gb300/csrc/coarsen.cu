@@ -91,6 +91,7 @@ kp_status alloc_work(Scratch &sc, Work &w, int32_t n0, eoff nnz0, const kp_optio
         KP_TRY(sc.get(&w.gtake, n0));
         KP_TRY(sc.get(&w.gpend, n0));
         KP_TRY(sc.get(&w.gdec, n0));
+        KP_TRY(sc.get(&w.ghub, (int64_t)nnz0 / 2048 + 1));   // rows longer than GPA_HUB_ROW = 2048
     }
     KP_TRY(sc.get(&w.list0, n0));
     KP_TRY(sc.get(&w.list1, n0));

@@ -162,6 +162,7 @@ struct Work {
     uint8_t *gtake;
     int32_t *gpend;
     int8_t *gdec;
+    int32_t *ghub;   // rows of more than GPA_HUB_ROW entries (at most nnz / GPA_HUB_ROW)
     // the input's largest degree + 1, written by level 0's start into mapped
     // host memory (null: not wanted)
     int32_t *deg0_host;

@@ -147,12 +147,83 @@ __device__ __forceinline__ void gpa_rate_node(const DevLevel &L, const Work &w, 
     if (gl == 0) w.cand[u] = best.u;
 }
 
+// Rows longer than this are rated by a whole block (listed once per level
+// in ghub): a hub's row is scanned again whenever its candidate is taken,
+// and G lanes would hold a round for the whole row.
+constexpr int32_t GPA_HUB_ROW = 2048;
+
+// gpa_rate_node for a hub, the block's threads over the row, the best
+// edge by a block reduction.  Every decision before the scan reads the same
+// words in every thread, so the block takes it together.
+template <int R>
+__device__ void gpa_rate_hub(const DevLevel &L, const Work &w, int32_t u, bool recheck) {
+    __shared__ Cand s_best[MATCH_BLOCK / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int2 mine = gpa_nb(w, u);
+    if (mine.y >= 0) {
+        if (threadIdx.x == 0) w.cand[u] = -1;
+        return;
+    }
+    if (recheck) {
+        const int32_t c = __ldcg(w.cand + u);
+        if (c >= 0 && c != mine.x && __ldcg(w.gnb + 2 * (int64_t)c + 1) < 0) return;
+    }
+    const eoff beg = KP_LDG(L.xadj + u), end = KP_LDG(L.xadj + u + 1);
+    const int32_t au = rating_attr<R>(L.vwgt, L.outw, u);
+    const HashCtx hc = hash_ctx(w, L, u);
+    Cand best;
+    best.u = -1;
+    best.num = best.den = best.h = 0;
+    for (eoff e = beg + (eoff)threadIdx.x; e < end; e += blockDim.x) {
+        const int32_t v = KP_LDG(L.adjncy + e);
+        if (v == mine.x) continue;
+        if (__ldcg(w.gnb + 2 * (int64_t)v + 1) >= 0) continue;
+        if (__ldcg(w.grej + e)) continue;
+        Cand c;
+        c.u = v;
+        rating_ab<R>(KP_LDG(L.ewgt + e), au, rating_attr<R>(L.vwgt, L.outw, v), c.num, c.den);
+        c.h = edge_hash_in(hc, u, v);
+        if (better(c, best, u)) best = c;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        Cand o;
+        o.num = __shfl_xor_sync(0xffffffffu, best.num, off);
+        o.den = __shfl_xor_sync(0xffffffffu, best.den, off);
+        o.h = __shfl_xor_sync(0xffffffffu, best.h, off);
+        o.u = __shfl_xor_sync(0xffffffffu, best.u, off);
+        if (better(o, best, u)) best = o;
+    }
+    if (lane == 0) s_best[warp] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Cand b = s_best[0];
+        for (int i = 1; i < MATCH_BLOCK / 32; i++)
+            if (better(s_best[i], b, u)) b = s_best[i];
+        w.cand[u] = b.u;
+    }
+    __syncthreads();   // s_best is read before the next hub
+}
+
+// Rates the round's nodes: G lanes per node, hubs (listed in ghub) a block
+// each.  A hub is in the round's list exactly when its candidate is not -1
+// (nodes leave the list when they find no undecided edge, and only then).
 template <int R, int G>
-__device__ void gpa_rate_phase(const DevLevel &L, const Work &w, const int32_t *lst, int64_t cnt) {
+__device__ void gpa_rate_phase(const DevLevel &L, const Work &w, const Counters *ctr, const int32_t *lst,
+                               int64_t cnt) {
     const int64_t gid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
     const int64_t ngroups = (int64_t)gridDim.x * blockDim.x / G;
-    for (int64_t i = gid; i < cnt; i += ngroups)
-        gpa_rate_node<R, G>(L, w, lst ? __ldcg(lst + i) : (int32_t)i, lst != nullptr);
+    for (int64_t i = gid; i < cnt; i += ngroups) {
+        const int32_t u = lst ? __ldcg(lst + i) : (int32_t)i;
+        if (KP_LDG(L.xadj + u + 1) - KP_LDG(L.xadj + u) > GPA_HUB_ROW) continue;   // the same in the group
+        gpa_rate_node<R, G>(L, w, u, lst != nullptr);
+    }
+    const int32_t nh = ld_relaxed_i32(&ctr->list_size[3]);
+    for (int32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+        const int32_t u = __ldcg(w.ghub + h);
+        if (lst && __ldcg(w.cand + u) == -1) continue;   // decided in an earlier round
+        gpa_rate_hub<R>(L, w, u, lst != nullptr);
+    }
 }
 
 // Mutual best edges: taken at once when an end has no collected edge, else
@@ -340,6 +411,9 @@ __device__ bool phase_gpa(DevState *st, int level, const Work &w) {
         w.match[v] = (int32_t)v;
     }
     for (int64_t e = tid; e < L.nnz; e += nthreads) w.grej[e] = 0;
+    // the hubs of this level (list_size[3] is zero when the level starts)
+    for (int64_t v = tid; v < L.n; v += nthreads)
+        if (L.xadj[v + 1] - L.xadj[v] > GPA_HUB_ROW) w.ghub[atomicAdd(&ctr->list_size[3], 1)] = (int32_t)v;
     if (!grid_sync(&ctr->bar, &ctr->err, w.spin_limit)) return give_up();
     const int32_t *lst = nullptr;   // round 1: every node
     int64_t cnt = L.n;
@@ -356,10 +430,10 @@ __device__ bool phase_gpa(DevState *st, int level, const Work &w) {
             ctr->rounds = (int32_t)round;
         }
         switch (G) {
-        case 1: gpa_rate_phase<R, 1>(L, w, lst, cnt); break;
-        case 8: gpa_rate_phase<R, 8>(L, w, lst, cnt); break;
-        case 16: gpa_rate_phase<R, 16>(L, w, lst, cnt); break;
-        default: gpa_rate_phase<R, 32>(L, w, lst, cnt); break;
+        case 1: gpa_rate_phase<R, 1>(L, w, ctr, lst, cnt); break;
+        case 8: gpa_rate_phase<R, 8>(L, w, ctr, lst, cnt); break;
+        case 16: gpa_rate_phase<R, 16>(L, w, ctr, lst, cnt); break;
+        default: gpa_rate_phase<R, 32>(L, w, ctr, lst, cnt); break;
         }
         if (!grid_sync(&ctr->bar, &ctr->err, w.spin_limit)) return give_up();
         gpa_pair_phase(w, lst, cnt, nxt, &ctr->list_size[cur ^ 1], &ctr->list_size[2]);

@@ -90,7 +90,8 @@ def test_structured_graphs(rating):
     cycle9 = I.from_edges(9, lo, (lo + 1) % 9, np.arange(1, 10), name="cycle9")
     lo = np.arange(12)
     cycle12 = I.from_edges(12, lo, (lo + 1) % 12, np.array([3, 1, 4, 1, 5, 9, 2, 6, 5, 3, 5, 8]), name="cycle12")
-    for g in [I.grid2d(64, 64), I.grid3d(20, 17, 9), I.rgg2d(1 << 16, 3, wmax=16), I.rmat(13, 5),
+    # R-MAT 2^15 and the star: rows above 2048 entries, rated by a block each
+    for g in [I.grid2d(64, 64), I.grid3d(20, 17, 9), I.rgg2d(1 << 16, 3, wmax=16), I.rmat(13, 5), I.rmat(15, 3),
               I.path_graph(3000), I.star_graph(3000), cycle9, cycle12]:
         gpa_path(g, rating, 7, 20, k=5)
 
