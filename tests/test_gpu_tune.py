@@ -70,6 +70,20 @@ def test_every_knob_value_gives_the_oracle_hierarchy(knob, values):
                 h.free()
 
 
+def test_radix_widths_on_mid_length_rows():
+    """With a low sort_shared_max the radix class (LSD passes through global
+    memory) also holds rows of 129..2048 entries: every radix width gives the
+    oracle's hierarchy."""
+    for make, rating in HUBS:
+        g = make()
+        ref = O.coarsen(g, rating, 3, 40)
+        dg = B().DeviceGraph.from_csr(g)
+        for rb in (4, 5, 7, 8):
+            h = B().coarsen(dg, rating=rating, seed=3, stop_size=40, tail_nodes=-1, sort_shared_max=128, radix_bits=rb)
+            same_as_oracle(gpu_levels(h), ref)
+            h.free()
+
+
 def test_bad_knob_values_are_rejected():
     dg = B().DeviceGraph.from_csr(I.grid2d(8, 8))
     for kw in [dict(suitor_lanes=3), dict(suitor_lanes=16), dict(radix_bits=3), dict(radix_bits=9), dict(sort_shared_max=64),
