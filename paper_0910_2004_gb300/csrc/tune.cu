@@ -91,7 +91,7 @@ extern "C" kp_status kp_autotune(const kp_graph *g, int32_t num_graphs, const in
         knobs.push_back({&kp_options::suitor_blocks, {3, 4}});
     }
     knobs.push_back({&kp_options::tail_block_nodes, {512, 1024, 2048, 4096, 8192}});
-    knobs.push_back({&kp_options::sort_shared_max, {512, 1024, 2048}});
+    knobs.push_back({&kp_options::sort_shared_max, {128, 256, 512, 1024, 2048}});
     knobs.push_back({&kp_options::radix_bits, {6, 7, 8}});
     knobs.push_back({&kp_options::cluster_nodes, {-1, 8192, 32768, 131072}});
     for (const Knob &k : knobs) {
