@@ -253,6 +253,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--matcher", default="suitor", choices=["suitor", "handshake", "gpa"])
     ap.add_argument("--tail-nodes", type=int, default=0)
+    ap.add_argument("--sort-shared-max", type=int, default=0, help="served: the server's sort_shared_max (0: built-in)")
     ap.add_argument("--no-tune", action="store_true", help="built-in knobs instead of the autotuner's")
     ap.add_argument("--requests", type=int, default=None, help="served: requests per load phase")
     ap.add_argument("--workers", type=int, default=4, help="served: server workers")
@@ -919,7 +920,7 @@ def run_served(args, wl):
 
     sv = B.Server(workers=args.workers, max_batch=64, batch_max_nodes=1 << 16, hbm_budget_bytes=budget,
                   small_workers=args.small_workers, rating=rating, validate=False, matcher=args.matcher,
-                  tail_nodes=args.tail_nodes)
+                  tail_nodes=args.tail_nodes, sort_shared_max=args.sort_shared_max)
     # warm-up: every pool graph once (allocator pool, library state)
     for _ in range(max(1, min(args.warmup, 2))):
         serve_phase(sv, pool, [(pi, 2, eps, 1, 40) for pi in range(len(pool))], None)

@@ -12,6 +12,7 @@
 //   32-bit build refuses a level of 2^31 entries or more).
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <type_traits>
 #include <vector>
 
@@ -52,7 +53,7 @@ kp_status put_dev(FILE *f, const T *d, int64_t count, std::vector<T> &buf) {
 
 }  // namespace
 
-extern "C" kp_status kp_hierarchy_save(const kp_hierarchy *h, const char *path) {
+static kp_status hierarchy_save_impl(const kp_hierarchy *h, const char *path) {
     if (!h || !path) return set_error(KP_ERR_INVALID, "null argument");
     if (h->stream && cudaStreamSynchronize(h->stream) != cudaSuccess)
         return cuda_error(cudaGetLastError(), "sync");
@@ -93,7 +94,69 @@ extern "C" kp_status kp_hierarchy_save(const kp_hierarchy *h, const char *path) 
     return KP_OK;
 }
 
-extern "C" kp_status kp_hierarchy_load(const char *path, kp_stream stream, kp_hierarchy **out) {
+// A level of a hierarchy file, read and checked on the host.
+struct HostLevel {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    std::vector<int64_t> xadj;   // the file's offsets, widened
+    std::vector<int32_t> adjncy, ewgt, vwgt, map, goff;
+};
+
+// Uploads the checked host arrays into h (which it frees on an error).
+static kp_status upload_hierarchy(kp_hierarchy *h, const std::vector<HostLevel> &lv, const std::vector<std::vector<eoff>> &xs,
+                                  const std::vector<int32_t> &glevels, const std::vector<int32_t> &gid0, int32_t L,
+                                  int32_t G, cudaStream_t s, kp_hierarchy **out) {
+    h->stream = s;
+    h->num_graphs = G;
+    auto fail = [&](kp_status st) {
+        kp_hierarchy_free(h);
+        return st;
+    };
+    if (cudaGetDevice(&h->device) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "device"));
+    auto up = [&](auto **dst, const auto &src) -> kp_status {
+        using T = typename std::remove_reference<decltype(src)>::type::value_type;
+        KP_TRY(dev_alloc_n(dst, (int64_t)src.size(), s));
+        h->allocations.push_back(*dst);
+        if (!src.empty())
+            KP_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
+        return KP_OK;
+    };
+    for (int32_t l = 0; l < L; l++) {
+        const HostLevel &H = lv[(size_t)l];
+        kp_level k;
+        k.n = H.n;
+        k.nnz = (eoff)H.nnz;
+        k.owned = true;
+        kp_status st = up(&k.xadj, xs[(size_t)l]);
+        if (st == KP_OK) st = up(&k.adjncy, H.adjncy);
+        if (st == KP_OK) st = up(&k.ewgt, H.ewgt);
+        if (st == KP_OK) st = up(&k.vwgt, H.vwgt);
+        if (st == KP_OK && l < L - 1) st = up(&k.map, H.map);
+        if (st == KP_OK && G > 0) st = up(&k.goff, H.goff);
+        if (st != KP_OK) return fail(st);
+        h->levels.push_back(k);
+    }
+    if (G > 0) {
+        h->glevels = glevels;
+        kp_status st = up(&h->glevels_dev, glevels);
+        if (st == KP_OK) st = up(&h->gid0, gid0);
+        if (st != KP_OK) return fail(st);
+    }
+    h->per_level.assign((size_t)(L - 1), kp_level_profile{});
+    for (int32_t l = 0; l + 1 < L; l++) {
+        h->per_level[(size_t)l].n = h->levels[(size_t)l].n;
+        h->per_level[(size_t)l].nnz = h->levels[(size_t)l].nnz;
+        h->total_matched += (int64_t)h->levels[(size_t)l].n - h->levels[(size_t)l + 1].n;
+    }
+    h->total.n = h->levels[0].n;
+    h->total.nnz = h->levels[0].nnz;
+    // the host vectors are the copies' sources: wait before they go
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "sync"));
+    *out = h;
+    return KP_OK;
+}
+
+static kp_status hierarchy_load_impl(const char *path, kp_stream stream, kp_hierarchy **out) {
     if (!path || !out) return set_error(KP_ERR_INVALID, "null argument");
     *out = nullptr;
     cudaStream_t s = (cudaStream_t)stream;
@@ -113,12 +176,6 @@ extern "C" kp_status kp_hierarchy_load(const char *path, kp_stream stream, kp_hi
 
     // everything is read and checked on the host before anything reaches the
     // device: the kernels index with these arrays
-    struct HostLevel {
-        int32_t n = 0;
-        int64_t nnz = 0;
-        std::vector<int64_t> xadj;   // the file's offsets, widened
-        std::vector<int32_t> adjncy, ewgt, vwgt, map, goff;
-    };
     std::vector<HostLevel> lv((size_t)L);
     auto rd = [&](std::vector<int32_t> &v, int64_t count) -> kp_status {
         if (count < 0 || count > (1ll << 32)) return set_error(KP_ERR_INVALID, "bad array size in hierarchy file");
@@ -199,56 +256,34 @@ extern "C" kp_status kp_hierarchy_load(const char *path, kp_stream stream, kp_hi
         }
     }
 
-    kp_hierarchy *h = new kp_hierarchy();
-    h->stream = s;
-    h->num_graphs = G;
-    auto fail = [&](kp_status st) {
-        kp_hierarchy_free(h);
-        return st;
-    };
-    if (cudaGetDevice(&h->device) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "device"));
-    auto up = [&](auto **dst, const auto &src) -> kp_status {
-        using T = typename std::remove_reference<decltype(src)>::type::value_type;
-        KP_TRY(dev_alloc_n(dst, (int64_t)src.size(), s));
-        h->allocations.push_back(*dst);
-        if (!src.empty())
-            KP_CUDA(cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
-        return KP_OK;
-    };
     // the offsets in this build's width (every value is below NNZ_LIMIT)
     std::vector<std::vector<eoff>> xs((size_t)L);
     for (int32_t l = 0; l < L; l++) xs[(size_t)l].assign(lv[(size_t)l].xadj.begin(), lv[(size_t)l].xadj.end());
-    for (int32_t l = 0; l < L; l++) {
-        const HostLevel &H = lv[(size_t)l];
-        kp_level k;
-        k.n = H.n;
-        k.nnz = (eoff)H.nnz;
-        k.owned = true;
-        kp_status st = up(&k.xadj, xs[(size_t)l]);
-        if (st == KP_OK) st = up(&k.adjncy, H.adjncy);
-        if (st == KP_OK) st = up(&k.ewgt, H.ewgt);
-        if (st == KP_OK) st = up(&k.vwgt, H.vwgt);
-        if (st == KP_OK && l < L - 1) st = up(&k.map, H.map);
-        if (st == KP_OK && G > 0) st = up(&k.goff, H.goff);
-        if (st != KP_OK) return fail(st);
-        h->levels.push_back(k);
+
+    kp_hierarchy *h = new kp_hierarchy();
+    try {
+        return upload_hierarchy(h, lv, xs, glevels, gid0, L, G, s, out);
+    } catch (...) {
+        kp_hierarchy_free(h);
+        throw;
     }
-    if (G > 0) {
-        h->glevels = glevels;
-        kp_status st = up(&h->glevels_dev, glevels);
-        if (st == KP_OK) st = up(&h->gid0, gid0);
-        if (st != KP_OK) return fail(st);
+}
+
+// The host buffers of a large file may not fit host memory: an allocation
+// failure is an error code, not an exception leaving the C ABI.
+extern "C" kp_status kp_hierarchy_save(const kp_hierarchy *h, const char *path) {
+    try {
+        return hierarchy_save_impl(h, path);
+    } catch (const std::bad_alloc &) {
+        return set_error(KP_ERR_OOM, "host buffer for the hierarchy file");
     }
-    h->per_level.assign((size_t)(L - 1), kp_level_profile{});
-    for (int32_t l = 0; l + 1 < L; l++) {
-        h->per_level[(size_t)l].n = h->levels[(size_t)l].n;
-        h->per_level[(size_t)l].nnz = h->levels[(size_t)l].nnz;
-        h->total_matched += (int64_t)h->levels[(size_t)l].n - h->levels[(size_t)l + 1].n;
+}
+
+extern "C" kp_status kp_hierarchy_load(const char *path, kp_stream stream, kp_hierarchy **out) {
+    try {
+        return hierarchy_load_impl(path, stream, out);
+    } catch (const std::bad_alloc &) {
+        if (out) *out = nullptr;
+        return set_error(KP_ERR_OOM, "host buffer for the hierarchy file");
     }
-    h->total.n = h->levels[0].n;
-    h->total.nnz = h->levels[0].nnz;
-    // the host vectors are the copies' sources: wait before they go
-    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(cuda_error(cudaGetLastError(), "sync"));
-    *out = h;
-    return KP_OK;
 }
