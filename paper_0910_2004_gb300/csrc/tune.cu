@@ -6,6 +6,7 @@
 // CUDA events on the caller's stream, the minimum over `reps` runs after one
 // untimed run.
 #include <cstring>
+#include <new>
 #include <limits>
 #include <vector>
 
@@ -35,10 +36,10 @@ kp_status time_once(const kp_graph *g, const kp_options *o, const BatchSpec *b, 
 
 }  // namespace
 
-extern "C" kp_status kp_autotune(const kp_graph *g, int32_t num_graphs, const int32_t *node_offsets,
-                                 const uint64_t *seeds, const int32_t *stop_sizes, const kp_options *o,
-                                 int32_t reps, kp_options *best, kp_tune_trial *trials, int32_t max_trials,
-                                 int32_t *num_trials, kp_stream stream) {
+static kp_status autotune_impl(const kp_graph *g, int32_t num_graphs, const int32_t *node_offsets,
+                               const uint64_t *seeds, const int32_t *stop_sizes, const kp_options *o, int32_t reps,
+                               kp_options *best, kp_tune_trial *trials, int32_t max_trials, int32_t *num_trials,
+                               kp_stream stream) {
     if (!g || !o || !best) return set_error(KP_ERR_INVALID, "null argument");
     if (reps < 1 || reps > 100 || max_trials < 0 || (max_trials > 0 && !trials))
         return set_error(KP_ERR_INVALID, "bad tuner arguments");
@@ -120,4 +121,16 @@ extern "C" kp_status kp_autotune(const kp_graph *g, int32_t num_graphs, const in
     cur.validate = o->validate;
     *best = cur;
     return KP_OK;
+}
+
+extern "C" kp_status kp_autotune(const kp_graph *g, int32_t num_graphs, const int32_t *node_offsets,
+                                 const uint64_t *seeds, const int32_t *stop_sizes, const kp_options *o,
+                                 int32_t reps, kp_options *best, kp_tune_trial *trials, int32_t max_trials,
+                                 int32_t *num_trials, kp_stream stream) {
+    try {
+        return autotune_impl(g, num_graphs, node_offsets, seeds, stop_sizes, o, reps, best, trials, max_trials,
+                             num_trials, stream);
+    } catch (const std::bad_alloc &) {
+        return set_error(KP_ERR_OOM, "host allocation failed");
+    }
 }
