@@ -799,31 +799,69 @@ def served_requests(pool, count, seed):
     return out
 
 
+def pin_pool(pool):
+    """The pool's arrays in page-locked host memory, as a client that stages
+    its requests in pinned buffers has them: the server's host-to-device
+    copies then run at the host link's rate instead of through the driver's
+    pageable path.  Returns the pool and the tensors that own the memory."""
+    import torch
+    keep, out = [], []
+    for fam, sc, g in pool:
+        arrs = []
+        for a in (g.xadj, g.adjncy, g.ewgt, g.vwgt):
+            t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            keep.append(t)
+            arrs.append(t.numpy())
+        out.append((fam, sc, I.CSRGraph(*arrs, g.name)))
+    return out, keep
+
+
 def poisson_arrivals(count, rate, seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.cumsum(rng.exponential(1.0 / rate, size=count))
 
 
-def serve_phase(sv, pool, reqs, arrivals, borrow=True):
+def serve_phase(sv, pool, reqs, arrivals, borrow=True, stall_s=300.0):
     """Submits reqs at the given arrival offsets (seconds; None: all at once)
-    while a second thread waits for and releases them in order.  Latency of a
+    while a second thread releases them as they finish (in any order, so no
+    finished result stays charged behind an unfinished one).  Latency of a
     request: from its scheduled arrival to its completion (server clock for
-    submit..done, plus the lag of the submit call behind the schedule)."""
+    submit..done, plus the lag of the submit call behind the schedule).  A
+    phase in which no request finishes for stall_s seconds is an error."""
     import queue
     import threading
     q = queue.Queue()
     results = [None] * len(reqs)
+    failure = []
 
     def reaper():
-        while True:
-            item = q.get()
-            if item is None:
+        pending, closed, last = {}, False, time.perf_counter()
+        while not (closed and not pending):
+            try:
+                while True:
+                    item = q.get_nowait()
+                    if item is None:
+                        closed = True
+                        break
+                    i, rid, lag = item
+                    pending[rid] = (i, lag)
+            except queue.Empty:
+                pass
+            done = [rid for rid in pending if sv.poll(rid)[0]]
+            for rid in done:
+                i, lag = pending.pop(rid)
+                res = sv.wait(rid)
+                sv.release(rid)
+                res["lag_s"] = lag
+                results[i] = res
+            now = time.perf_counter()
+            if done:
+                last = now
+            elif pending and now - last > stall_s:
+                failure.append(f"no request finished for {stall_s:.0f} s ({len(pending)} pending)")
                 return
-            i, rid, lag = item
-            res = sv.wait(rid)
-            sv.release(rid)
-            res["lag_s"] = lag
-            results[i] = res
+            if not done:
+                time.sleep(0.0002)
 
     th = threading.Thread(target=reaper)
     th.start()
@@ -839,6 +877,8 @@ def serve_phase(sv, pool, reqs, arrivals, borrow=True):
         q.put((i, rid, lag))
     q.put(None)
     th.join()
+    if failure:
+        raise RuntimeError("served phase stalled: " + failure[0])
     lat = np.array([(r["t_done_us"] - r["t_submit_us"]) / 1000.0 + 1000.0 * r["lag_s"] for r in results])
     span_s = (max(r["t_done_us"] for r in results) - min(r["t_submit_us"] for r in results)) / 1e6
     m = sum(pool[pi][2].m for pi, *_ in reqs)
@@ -910,7 +950,7 @@ def run_served(args, wl):
     __graft_entry__.build()
     from paper_0910_2004_gb300 import binding as B
 
-    pool = I.served_mix(range(12, 23), seed=1, device="cuda")
+    pool, pinned = pin_pool(I.served_mix(range(12, 23), seed=1, device="cuda"))
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info()
@@ -1014,7 +1054,7 @@ def run_served(args, wl):
         "config": {"workload": args.workload, "desc": wl["desc"]},
         "run": {"pool_graphs": len(pool), "requests_per_phase": R, "workers": args.workers, "small_workers": args.small_workers,
                    "max_batch": 64,
-                   "host_arrays": "pageable numpy arrays of the pool, borrowed by the server (KP_REQUEST_BORROW: "
+                   "host_arrays": "page-locked numpy arrays of the pool, borrowed by the server (KP_REQUEST_BORROW: "
                                   "read by the worker's host-to-device copy, no copy at submit)",
                    "batch_max_nodes": 1 << 16, "hbm_budget_gb": budget / 1e9, "matcher": args.matcher,
                    "l2": "inputs of the large requests exceed L2; no flush between requests (a stream)",

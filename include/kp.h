@@ -466,8 +466,11 @@ kp_status kp_pipeline_host(const kp_graph *g, const kp_options *o, int32_t k, do
  * small ones are scheduled first.
  * Admission: first in, first out; the oldest waiting request starts once its
  * estimated device footprint fits into hbm_budget_bytes minus the footprint
- * of running and resident requests (a request runs alone if nothing else is
- * charged, whatever its size).  Workers kept for small requests take the
+ * of running requests and of resident results of older requests (a request
+ * runs alone if nothing older is charged, whatever its size; results of
+ * younger requests that a small-request worker ran past it do not hold it
+ * back, so a client releasing in submission order cannot stall the queue).
+ * Workers kept for small requests take the
  * oldest waiting request of at most batch_max_nodes nodes instead, so small
  * requests do not queue behind large ones.  Footprint while running:
  * 148 n + 57 nnz + 2 MB

@@ -100,6 +100,8 @@ struct ServerGroup {
     int64_t footprint = 0;  // charged against the budget now
     int64_t resident = 0;
     int64_t grown = 0;      // arena chunks taken beyond the estimate
+    uint64_t min_id = 0;    // its oldest request
+    bool finished = false;  // run_group has returned (only its resident part is charged)
     int32_t live = 0;
     int64_t id = 0;
     int32_t launches = 0;
@@ -111,6 +113,7 @@ struct kp_server {
     std::condition_variable cv_work, cv_done;
     std::deque<ServerRequest *> queue;
     std::map<uint64_t, ServerRequest *> reqs;
+    std::vector<ServerGroup *> finished;   // groups whose results wait for release
     uint64_t next_id = 1;
     int64_t next_group = 1;
     int64_t used = 0;
@@ -292,8 +295,16 @@ void charge_growth(void *ctx, int64_t bytes) {
     c->g->grown += bytes;
 }
 
+// Whether r may start: what is charged, less the resident results of
+// requests younger than r (a worker for small requests may have run them
+// past r; a client that releases in submission order would release them
+// only after r, so counting them could keep r waiting for ever), leaves room
+// for r's footprint, or nothing older is charged at all.
 bool fits(const kp_server *S, const ServerRequest *r) {
-    return S->used == 0 || S->used + r->footprint <= S->cfg.hbm_budget_bytes;
+    int64_t used = S->used;
+    for (const ServerGroup *g : S->finished)
+        if (g->min_id > r->id) used -= g->footprint;
+    return used == 0 || used + r->footprint <= S->cfg.hbm_budget_bytes;
 }
 
 // The request a worker takes next: the oldest one, or for a worker kept for
@@ -350,6 +361,8 @@ void worker_main(kp_server *S, int wi) {
             }
             g->live = (int32_t)g->reqs.size();
             g->id = S->next_group++;
+            g->min_id = head->id;
+            for (ServerRequest *r : g->reqs) g->min_id = std::min(g->min_id, r->id);
         }
         kp_status st;
         // arena chunks the coarsening adds beyond the estimate stay with the
@@ -369,6 +382,8 @@ void worker_main(kp_server *S, int wi) {
             // the scratch is back in the pool: charge only what stays
             S->used -= g->footprint - g->resident;
             g->footprint = g->resident;
+            g->finished = true;
+            S->finished.push_back(g);
             const double t = S->now_us();
             for (ServerRequest *r : g->reqs) {
                 r->res.arena_grown_bytes = g->grown;
@@ -586,6 +601,7 @@ kp_status kp_server_release(kp_server *S, uint64_t id) {
         ServerGroup *g = r->grp;
         if (g && --g->live == 0) {
             S->used -= g->footprint;
+            S->finished.erase(std::remove(S->finished.begin(), S->finished.end(), g), S->finished.end());
             to_free = g;
         }
         S->reqs.erase(id);

@@ -157,6 +157,37 @@ def test_admission_waits_for_released_budget():
         sv.release(ids[2])
 
 
+def test_younger_results_do_not_hold_back_the_head():
+    """A large request H waits behind an older resident result X; a small
+    request Y (younger) runs past it on the small-request worker and stays
+    resident.  Once X is released, H starts although Y is still resident (a
+    client releasing in submission order waits for H before releasing Y)."""
+    big = I.grid2d(40, 40)     # 1600 nodes: above batch_max_nodes
+    small = I.grid2d(10, 10)
+    res_x = 88 * big.n + 40 * big.nnz + (1 << 20)
+    run_y = 148 * small.n + 57 * small.nnz + (2 << 20)
+    budget = res_x + run_y      # X resident + Y running fit; X + H and Y + H do not
+    with B().Server(workers=2, small_workers=1, max_batch=1, batch_max_nodes=1000, hbm_budget_bytes=budget,
+                    tail_nodes=-1) as sv:
+        ix = sv.submit(big.xadj, big.adjncy, big.ewgt, big.vwgt, 2, 0.03, 1, 40)
+        sv.wait(ix)
+        ih = sv.submit(big.xadj, big.adjncy, big.ewgt, big.vwgt, 2, 0.03, 2, 40)
+        iy = sv.submit(small.xadj, small.adjncy, small.ewgt, small.vwgt, 2, 0.03, 3, 40)
+        ry = sv.wait(iy)
+        assert ry["status"] == 0
+        done, _ = sv.poll(ih)
+        assert not done          # X is older and still charged
+        sv.release(ix)
+        deadline = time.time() + 30
+        while not sv.poll(ih)[0] and time.time() < deadline:
+            time.sleep(0.01)
+        assert sv.poll(ih)[0], "the head waited for a younger resident result"
+        rh = sv.wait(ih)
+        assert rh["status"] == 0 and rh["t_admit_us"] >= ry["t_done_us"]
+        sv.release(ih)
+        sv.release(iy)
+
+
 def test_fifo_order_and_errors():
     g = I.grid2d(20, 20)
     with B().Server(workers=1, max_batch=1) as sv:
