@@ -166,7 +166,7 @@ typedef enum {
  *                        to 512 by one warp in registers when the level is
  *                        launched phase by phase), longer ones by the radix
  *                        path (rows above 32768 entries by a thread-block
- *                        cluster each), 128..2048 (0: 2048)
+ *                        cluster each), 128..2048 (0: 256)
  *   radix_bits           bits per pass of the radix path, 4..8 (0: 8)
  *   cluster_nodes        tail levels with at most this many nodes run in one
  *                        thread-block cluster (16 CTAs, or 8) whose phases

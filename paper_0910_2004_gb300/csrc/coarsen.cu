@@ -169,7 +169,10 @@ void init_state(DevState *hs, const kp_graph *g, const kp_options *o, const Batc
     hs->min_shrink_permille = o->min_shrink_permille;
     hs->inner_outer = inner_outer ? 1 : 0;
     hs->suitor_lanes = o->suitor_lanes;
-    hs->sort_shared_max = o->sort_shared_max ? o->sort_shared_max : MID_MAX;
+    // built in: rows above 256 gathered entries take the radix passes, which
+    // measured faster there than the shared-memory and register networks
+    // (power-law graphs; grids have few such rows)
+    hs->sort_shared_max = o->sort_shared_max ? o->sort_shared_max : SORT_SHARED_DEFAULT;
     hs->radix_bits = o->radix_bits ? o->radix_bits : 8;
     hs->tail_resume = -1;
     hs->snap = snap_dev;

@@ -27,6 +27,7 @@ namespace kp {
 
 constexpr int32_t SENT = 0x7fffffff;   // sorts after every node id
 constexpr int MID_MAX = 2048;          // longest row handled in shared memory
+constexpr int SORT_SHARED_DEFAULT = 256;   // kp_options.sort_shared_max = 0
 constexpr int MATCH_BLOCK = 256;
 constexpr int CONTRACT_BLOCK = 256;
 constexpr int MAX_LEVELS = 128;        // level table size (kp_options.max_levels <= 120)
