@@ -65,7 +65,7 @@ typedef enum {
     KP_ERR_OOM = 3,         /* a device or host allocation failed */
     KP_ERR_CUDA = 4,        /* a CUDA runtime call failed */
     KP_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
-    KP_ERR_UNSUPPORTED = 6  /* a parameter value this build does not handle */
+    KP_ERR_UNSUPPORTED = 6  /* a parameter value this library does not handle */
 } kp_status;
 
 /* Edge ratings of Section 3.1, each kept as an exact fraction num/den:

@@ -192,7 +192,7 @@ static kp_status hierarchy_load_impl(const char *path, kp_stream stream, kp_hier
         if (H.n < 0 || H.nnz < 0 || (l > 0 && H.n > lv[(size_t)l - 1].n))
             return set_error(KP_ERR_INVALID, "bad level sizes in hierarchy file");
         if (H.nnz >= NNZ_LIMIT)
-            return set_error(KP_ERR_OVERFLOW, "a level of the hierarchy file has more entries than this build's offsets hold");
+            return set_error(KP_ERR_OVERFLOW, "a level of the hierarchy file has more entries than this library's offsets hold");
         if (wide_file) {
             H.xadj.resize((size_t)H.n + 1);
             KP_TRY(get(f, H.xadj.data(), sizeof(int64_t) * H.xadj.size()));
@@ -256,7 +256,7 @@ static kp_status hierarchy_load_impl(const char *path, kp_stream stream, kp_hier
         }
     }
 
-    // the offsets in this build's width (every value is below NNZ_LIMIT)
+    // the offsets in this library's width (every value is below NNZ_LIMIT)
     std::vector<std::vector<eoff>> xs((size_t)L);
     for (int32_t l = 0; l < L; l++) xs[(size_t)l].assign(lv[(size_t)l].xadj.begin(), lv[(size_t)l].xadj.end());
 
