@@ -15,6 +15,7 @@
 #include <deque>
 #include <map>
 #include <mutex>
+#include <new>
 #include <string>
 #include <thread>
 #include <vector>
@@ -423,7 +424,16 @@ kp_status kp_server_create(const kp_server_config *cfg, kp_server **out) {
     if (cfg->workers < 1 || cfg->workers > 64 || cfg->max_batch < 1 || cfg->hbm_budget_bytes <= 0 ||
         cfg->small_workers < 0 || cfg->small_workers >= cfg->workers)
         return set_error(KP_ERR_INVALID, "bad server configuration");
-    kp_server *S = new kp_server();
+    // host allocations fail with KP_ERR_OOM: no exception leaves the C ABI
+    kp_server *S = nullptr;
+    try {
+        S = new kp_server();
+        S->streams.reserve(2 * (size_t)cfg->workers);
+        S->workers.reserve((size_t)cfg->workers);
+    } catch (const std::bad_alloc &) {
+        delete S;
+        return set_error(KP_ERR_OOM, "host allocation failed");
+    }
     S->cfg = *cfg;
     S->t0 = std::chrono::steady_clock::now();
     if (cudaGetDevice(&S->device) != cudaSuccess) {
@@ -462,7 +472,8 @@ kp_status kp_server_submit(kp_server *S, const kp_graph *g, const kp_request_par
     if (p->k < 1 || !(p->eps >= 0.0) || p->eps > 1000.0 || (p->flags & ~KP_REQUEST_BORROW))
         return set_error(KP_ERR_INVALID, "bad request parameters");
     const double t_in = S->now_us();   // latency includes the host copy
-    ServerRequest *r = new ServerRequest();
+    ServerRequest *r = new (std::nothrow) ServerRequest();
+    if (!r) return set_error(KP_ERR_OOM, "host allocation failed");
     r->n = g->n;
     r->nnz = g->nnz;
     if (p->flags & KP_REQUEST_BORROW) {
@@ -500,8 +511,19 @@ kp_status kp_server_submit(kp_server *S, const kp_graph *g, const kp_request_par
         }
         r->id = S->next_id++;
         r->res.t_submit_us = t_in;
-        S->reqs[r->id] = r;
-        S->queue.push_back(r);
+        try {
+            S->reqs[r->id] = r;
+        } catch (const std::bad_alloc &) {
+            delete r;
+            return set_error(KP_ERR_OOM, "host allocation failed");
+        }
+        try {
+            S->queue.push_back(r);
+        } catch (const std::bad_alloc &) {
+            S->reqs.erase(r->id);
+            delete r;
+            return set_error(KP_ERR_OOM, "host allocation failed");
+        }
         *id = r->id;
     }
     S->cv_work.notify_all();
