@@ -164,6 +164,20 @@ static kp_status hierarchy_load_impl(const char *path, kp_stream stream, kp_hier
     file.f = fopen(path, "rb");
     if (!file.f) return set_error(KP_ERR_INVALID, std::string("cannot open: ") + path);
     FILE *f = file.f;
+    // the file's size bounds every array before a buffer is sized for it, so
+    // a damaged header cannot make the loader take more host memory than the
+    // file holds (a stream that cannot seek is read without the bound)
+    long fsize = -1;
+    if (fseek(f, 0, SEEK_END) == 0) fsize = ftell(f);
+    if (fseek(f, 0, SEEK_SET) != 0) {
+        clearerr(f);
+        fsize = -1;
+    }
+    auto room = [&](int64_t bytes) {
+        if (fsize < 0) return true;
+        const long pos = ftell(f);
+        return pos >= 0 && pos <= fsize && bytes <= (int64_t)(fsize - pos);
+    };
     uint64_t magic = 0;
     int32_t head[4] = {0, 0, 0, 0};
     KP_TRY(get(f, &magic, 8));
@@ -179,6 +193,7 @@ static kp_status hierarchy_load_impl(const char *path, kp_stream stream, kp_hier
     std::vector<HostLevel> lv((size_t)L);
     auto rd = [&](std::vector<int32_t> &v, int64_t count) -> kp_status {
         if (count < 0 || count > (1ll << 32)) return set_error(KP_ERR_INVALID, "bad array size in hierarchy file");
+        if (!room((int64_t)sizeof(int32_t) * count)) return set_error(KP_ERR_INVALID, "truncated hierarchy file");
         v.resize((size_t)count);
         return get(f, v.data(), sizeof(int32_t) * (size_t)count);
     };
@@ -194,6 +209,8 @@ static kp_status hierarchy_load_impl(const char *path, kp_stream stream, kp_hier
         if (H.nnz >= NNZ_LIMIT)
             return set_error(KP_ERR_OVERFLOW, "a level of the hierarchy file has more entries than this library's offsets hold");
         if (wide_file) {
+            if (!room((int64_t)sizeof(int64_t) * ((int64_t)H.n + 1)))
+                return set_error(KP_ERR_INVALID, "truncated hierarchy file");
             H.xadj.resize((size_t)H.n + 1);
             KP_TRY(get(f, H.xadj.data(), sizeof(int64_t) * H.xadj.size()));
         } else {

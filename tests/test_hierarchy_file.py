@@ -98,6 +98,40 @@ def test_64_bit_offsets_beyond_the_32_bit_range_are_refused(lib, tmp_path):
     assert load_status(lib, p) == B.KP_ERR_UNSUPPORTED
 
 
+_CAPPED_LOAD = """
+import ctypes, os, resource, sys
+resource.setrlimit(resource.RLIMIT_AS, (3 << 30, 3 << 30))
+lib = ctypes.CDLL(sys.argv[1])
+lib.kp_last_error.restype = ctypes.c_char_p
+h = ctypes.c_void_p()
+st = lib.kp_hierarchy_load(os.fsencode(sys.argv[2]), None, ctypes.byref(h))
+print(st, lib.kp_last_error().decode())
+"""
+
+
+@pytest.mark.parametrize("version", [1, 2])
+@pytest.mark.parametrize("libname", ["libkp.so", "libkp64.so"])
+def test_sizes_beyond_the_file_are_refused_before_any_buffer(lib, tmp_path, version, libname):
+    """A header that claims 2^31-2 nodes in a file of a few bytes: the loader
+    compares each array with what is left of the file before it sizes a
+    buffer, so the answer is KP_ERR_INVALID (truncated), not an allocation of
+    8-16 GB.  Run in a child whose address space is capped at 3 GB, where
+    allocating first fails with KP_ERR_OOM instead."""
+    import subprocess
+    import sys
+    from paper_0910_2004_gb300 import binding as B
+    path = os.path.join(os.path.dirname(B.LIB_PATH), libname)
+    n = (1 << 31) - 2
+    p = tmp_path / "claims_too_much.kph"
+    sizes = struct.pack("<2i", n, 0) if version == 1 else struct.pack("<2iq", n, 0, 0)
+    open(p, "wb").write(MAGIC + struct.pack("<4i", version, 1, 0, 0) + sizes + bytes(64))
+    r = subprocess.run([sys.executable, "-c", _CAPPED_LOAD, path, str(p)], capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0, r.stderr
+    st, msg = r.stdout.strip().split(" ", 1)
+    assert int(st) == B.KP_ERR_INVALID and "truncated" in msg, r.stdout
+
+
 def test_batch_maps_stay_inside_their_graph(lib, tmp_path):
     from paper_0910_2004_gb300 import binding as B
     # graph 0: the path (two levels); graph 1: one edge contracted to a node
