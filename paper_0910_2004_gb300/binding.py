@@ -54,6 +54,26 @@ class KpError(RuntimeError):
 _c_eoff = ctypes.c_int64 if OFFSET_BITS == 64 else ctypes.c_int32
 
 
+def check_offset_width(nnz: int, where: str):
+    """The 32-bit library's kp_graph holds nnz and the row offsets in int32:
+    a graph of 2^31 entries or more is refused here, before ctypes or numpy
+    would wrap the values into a smaller, consistent-looking graph."""
+    if OFFSET_BITS == 32 and nnz >= 1 << 31:
+        raise KpError(KP_ERR_OVERFLOW, where,
+                      f"{nnz} entries: 2^31 or more need the 64-bit offsets library (KP_OFFSET_BITS=64)")
+
+
+def host_offsets(xadj, where: str) -> np.ndarray:
+    """Row offsets as a contiguous host array of the library's width; a value
+    the width does not hold raises instead of wrapping."""
+    a = np.asarray(xadj)
+    if a.dtype != XADJ_NP and a.size:
+        info = np.iinfo(XADJ_NP)
+        if int(a.max()) > info.max or int(a.min()) < info.min:
+            raise KpError(KP_ERR_OVERFLOW, where, f"row offsets beyond {OFFSET_BITS} bits")
+    return np.ascontiguousarray(a, dtype=XADJ_NP)
+
+
 class kp_graph(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("nnz", _c_eoff), ("xadj", ctypes.c_void_p),
                 ("adjncy", ctypes.c_void_p), ("ewgt", ctypes.c_void_p), ("vwgt", ctypes.c_void_p)]
@@ -485,9 +505,11 @@ class DeviceGraph:
         dev = torch.device("cuda")
         xt = torch.int64 if OFFSET_BITS == 64 else torch.int32
         if torch.is_tensor(xadj):
+            if xadj.dtype != xt and xadj.element_size() > 4 and xadj.numel() and int(xadj.max()) >= 1 << 31:
+                raise KpError(KP_ERR_OVERFLOW, "DeviceGraph", f"row offsets beyond {OFFSET_BITS} bits")
             self.xadj = xadj if xadj.dtype == xt else xadj.to(xt).contiguous()
         else:
-            self.xadj = torch.as_tensor(np.asarray(xadj, dtype=XADJ_NP)).to(dev)
+            self.xadj = torch.as_tensor(host_offsets(xadj, "DeviceGraph")).to(dev)
         self.adjncy = torch.as_tensor(np.asarray(adjncy, dtype=np.int32)).to(dev) if not torch.is_tensor(adjncy) else adjncy
         self.ewgt = torch.as_tensor(np.asarray(ewgt, dtype=np.int32)).to(dev) if not torch.is_tensor(ewgt) else ewgt
         self.vwgt = torch.as_tensor(np.asarray(vwgt, dtype=np.int32)).to(dev) if not torch.is_tensor(vwgt) else vwgt
@@ -496,6 +518,7 @@ class DeviceGraph:
         assert self.xadj.dtype == xt and self.xadj.is_cuda and self.xadj.is_contiguous()
         self.n = int(self.xadj.numel() - 1)
         self.nnz = int(self.adjncy.numel())
+        check_offset_width(self.nnz, "DeviceGraph")
         self.kp = kp_graph(self.n, self.nnz, self.xadj.data_ptr(), self.adjncy.data_ptr(),
                            self.ewgt.data_ptr(), self.vwgt.data_ptr())
 
@@ -669,8 +692,9 @@ def pipeline_host(xadj, adjncy, ewgt, vwgt, k: int, eps: float, initial_partitio
     np.ndarray[int32] of block ids."""
     n = len(xadj) - 1
     nnz = len(adjncy)
-    arrs = [np.ascontiguousarray(xadj, dtype=XADJ_NP)] + [np.ascontiguousarray(a, dtype=np.int32)
-                                                          for a in (adjncy, ewgt, vwgt)]
+    check_offset_width(nnz, "kp_pipeline_host")
+    arrs = [host_offsets(xadj, "kp_pipeline_host")] + [np.ascontiguousarray(a, dtype=np.int32)
+                                                         for a in (adjncy, ewgt, vwgt)]
     g = kp_graph(n, nnz, *[a.ctypes.data for a in arrs])
     if outputs is None:
         outputs = {"part": np.empty(n, np.int32), "gain": np.empty(n, np.int64),
@@ -718,8 +742,9 @@ class Server:
                borrow: bool = False) -> int:
         """borrow=True: the server reads the arrays when the request runs (no
         copy at submit); they are kept referenced until release."""
-        arrs = [np.ascontiguousarray(xadj, dtype=XADJ_NP)] + [np.ascontiguousarray(a, dtype=np.int32)
-                                                              for a in (adjncy, ewgt, vwgt)]
+        arrs = [host_offsets(xadj, "kp_server_submit")] + [np.ascontiguousarray(a, dtype=np.int32)
+                                                             for a in (adjncy, ewgt, vwgt)]
+        check_offset_width(len(arrs[1]), "kp_server_submit")
         g = kp_graph(len(arrs[0]) - 1, len(arrs[1]), *[a.ctypes.data for a in arrs])
         rid = kp_server_submit(self._sv, g, kp_request_params(k, stop_size, eps, seed,
                                                               KP_REQUEST_BORROW if borrow else 0, 0))

@@ -57,6 +57,11 @@ class CSRGraph:
     def arrays(self):
         return self.xadj, self.adjncy, self.ewgt, self.vwgt
 
+    def __post_init__(self):
+        # a row offset that wrapped in a narrowing cast shows here
+        if self.xadj.shape[0] and int(self.xadj[-1]) != self.adjncy.shape[0]:
+            raise ValueError(f"{self.name}: xadj[n] = {int(self.xadj[-1])} but {self.adjncy.shape[0]} entries")
+
 
 def from_edges(n: int, lo: np.ndarray, hi: np.ndarray, w: np.ndarray | None = None,
                vwgt: np.ndarray | None = None, name: str = "") -> CSRGraph:
@@ -457,6 +462,8 @@ def circulant(n: int, strides) -> CSRGraph:
     sizes of a level barely fall while its nodes halve)."""
     S = np.asarray(strides, dtype=np.int64)
     D = np.concatenate([S, n - S])
+    if n * D.size >= 1 << 31:
+        raise ValueError("2^31 entries or more: circulant_torch builds those (int64 offsets)")
     v = np.arange(n, dtype=np.int64)[:, None]
     adj = np.sort((v + D[None, :]) % n, axis=1).astype(np.int32).reshape(-1)
     xadj = (np.arange(n + 1, dtype=np.int64) * D.size).astype(np.int32)

@@ -69,3 +69,31 @@ def test_product_path_has_no_oracle_import():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
+
+
+def test_binding_refuses_sizes_beyond_the_32_bit_offsets(lib):
+    """The 32-bit library holds nnz and the row offsets in int32: the binding
+    refuses larger values before numpy or ctypes would wrap them (a graph of
+    2^32 + 5 entries would otherwise reach the library as a consistent graph of
+    5)."""
+    import numpy as np
+    from paper_0910_2004_gb300 import binding as B
+    assert B.OFFSET_BITS == 32
+    B.check_offset_width((1 << 31) - 1, "t")
+    with pytest.raises(B.KpError) as e:
+        B.check_offset_width(1 << 31, "t")
+    assert e.value.status == B.KP_ERR_OVERFLOW
+    x = B.host_offsets(np.array([0, 3, 5], np.int64), "t")
+    assert x.dtype == np.int32 and x.flags.c_contiguous and list(x) == [0, 3, 5]
+    for bad in ([0, 1 << 31], np.array([0, 1 << 32], np.int64), [0, -(1 << 31) - 1]):
+        with pytest.raises(B.KpError) as e:
+            B.host_offsets(bad, "t")
+        assert e.value.status == B.KP_ERR_OVERFLOW
+    never = lambda *a: pytest.fail("the initial partitioner must not run")
+    with pytest.raises(B.KpError) as e:                  # offsets beyond int32, few entries
+        B.pipeline_host([0, 1 << 31], [0], [1], [1], 2, 0.03, never)
+    assert e.value.status == B.KP_ERR_OVERFLOW
+    huge = np.broadcast_to(np.int32(0), ((1 << 32) + 5,))  # 2^32 + 5 entries, no memory behind them
+    with pytest.raises(B.KpError) as e:
+        B.pipeline_host([0, 0], huge, huge, [1], 2, 0.03, never)
+    assert e.value.status == B.KP_ERR_OVERFLOW

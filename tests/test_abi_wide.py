@@ -37,6 +37,10 @@ def test_wide_library_loads_and_exports_every_symbol():
         assert "64-bit offsets" in B.kp_version()
         # int32 n, padding, int64 nnz, four pointers
         assert ctypes.sizeof(B.kp_graph) == 48 and B.kp_graph.nnz.offset == 8
+        # offsets of 2^31 and more pass the binding in this width
+        B.check_offset_width(1 << 31, "t")
+        x = B.host_offsets([0, 1 << 31, (1 << 32) - 1], "t")
+        assert x.dtype.itemsize == 8 and int(x[-1]) == (1 << 32) - 1
         print("ok")
     """)
     assert out.strip().endswith("ok")

@@ -120,3 +120,14 @@ def test_circulant_structure_and_torch_equals_numpy(n, count, seed):
     assert x.dtype == torch.int64
     assert np.array_equal(x.numpy(), g.xadj) and np.array_equal(a.numpy(), g.adjncy)
     assert np.array_equal(w.numpy(), g.ewgt) and np.array_equal(v.numpy(), g.vwgt)
+
+
+def test_csr_container_refuses_wrapped_offsets():
+    """xadj[n] must equal the number of entries: an offset that wrapped in a
+    narrowing cast is caught where a generator builds the graph."""
+    x = np.array([0, 1, 2], np.int32)
+    I.CSRGraph(x, np.array([1, 0], np.int32), np.ones(2, np.int32), np.ones(2, np.int32))
+    with pytest.raises(ValueError):
+        I.CSRGraph(x, np.array([1, 0, 0], np.int32), np.ones(3, np.int32), np.ones(2, np.int32))
+    with pytest.raises(ValueError):   # 2^26 nodes x 64 neighbours = 2^32 entries: the torch builder's size
+        I.circulant(1 << 26, I.circulant_strides(1 << 26, 32, seed=1))
