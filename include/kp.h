@@ -375,8 +375,9 @@ typedef struct {
  *   part  device int32[n], values in [0,k)
  *   out   host struct; its device buffers are filled, its scalars set
  * Synchronises the stream (the scalars are returned on the host).
- * Errors: KP_ERR_INVALID (k < 1, eps < 0, eps > 1000, or a block id outside
- * [0,k)), KP_ERR_OOM, KP_ERR_CUDA. */
+ * Errors: KP_ERR_INVALID (k < 1, eps < 0, eps > 1000, a negative size, a
+ * null array, or a block id outside [0,k)), KP_ERR_OVERFLOW (nnz >= 2^32 in
+ * the 64-bit library), KP_ERR_OOM, KP_ERR_CUDA. */
 kp_status kp_cut_gain(const kp_graph *g, const int32_t *part, int32_t k, double eps,
                       kp_cut_gain_out *out, kp_stream s);
 

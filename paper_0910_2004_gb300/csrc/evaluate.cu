@@ -532,8 +532,10 @@ kp_status check_eval_args(const kp_graph *g, const int32_t *part, int32_t k, dou
     if (!g || !out) return set_error(KP_ERR_INVALID, "null argument");
     if (k < 1) return set_error(KP_ERR_INVALID, "k must be >= 1");
     if (!(eps >= 0.0) || eps > 1000.0) return set_error(KP_ERR_INVALID, "eps must be in [0, 1000]");
-    if (g->n < 0) return set_error(KP_ERR_INVALID, "negative n");
-    if (g->n > 0 && (!part || !g->xadj || !g->vwgt || !out->gain || !out->target))
+    if (g->n < 0 || g->nnz < 0) return set_error(KP_ERR_INVALID, "negative graph size");
+    if ((int64_t)g->nnz >= NNZ_LIMIT) return set_error(KP_ERR_OVERFLOW, "nnz >= 2^32: the edge weights sum to 2^31 or more");
+    if (g->n > 0 && (!part || !g->xadj || !g->vwgt || !out->gain || !out->target ||
+                     (g->nnz > 0 && (!g->adjncy || !g->ewgt))))
         return set_error(KP_ERR_INVALID, "null array");
     if (!out->block_w) return set_error(KP_ERR_INVALID, "null block_w");
     return KP_OK;

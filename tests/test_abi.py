@@ -97,3 +97,21 @@ def test_binding_refuses_sizes_beyond_the_32_bit_offsets(lib):
     with pytest.raises(B.KpError) as e:
         B.pipeline_host([0, 0], huge, huge, [1], 2, 0.03, never)
     assert e.value.status == B.KP_ERR_OVERFLOW
+
+
+def test_cut_gain_refuses_bad_sizes_and_null_arrays_on_the_host(lib):
+    """kp_cut_gain and kp_cut_gain_noalloc check the graph's sizes and arrays
+    before any CUDA call, as kp_coarsen does (the pointers here are never
+    read)."""
+    from paper_0910_2004_gb300 import binding as B
+    out = B.kp_cut_gain_out()
+    out.gain, out.target, out.block_w = 16, 16, 16
+    for fn in (lib.kp_cut_gain, lib.kp_cut_gain_noalloc):
+        g = B.kp_graph(2, -1, 16, 16, 16, 16)
+        assert fn(ctypes.byref(g), ctypes.c_void_p(16), 2, 0.03, ctypes.byref(out), None) == B.KP_ERR_INVALID
+        assert "negative" in B.kp_last_error()
+        g = B.kp_graph(2, 2, 16, None, 16, 16)      # entries without adjncy
+        assert fn(ctypes.byref(g), ctypes.c_void_p(16), 2, 0.03, ctypes.byref(out), None) == B.KP_ERR_INVALID
+        assert "null" in B.kp_last_error()
+        g = B.kp_graph(2, 2, 16, 16, None, 16)      # entries without ewgt
+        assert fn(ctypes.byref(g), ctypes.c_void_p(16), 2, 0.03, ctypes.byref(out), None) == B.KP_ERR_INVALID

@@ -59,6 +59,11 @@ def test_wide_library_refuses_nnz_beyond_the_weight_range():
         assert "2^32" in B.kp_last_error()
         g = B.kp_graph(1, -1, 16, 16, 16, 16)
         assert L.kp_coarsen(ctypes.byref(g), ctypes.byref(o), None, ctypes.byref(h)) == B.KP_ERR_INVALID
+        out = B.kp_cut_gain_out()
+        out.gain, out.target, out.block_w = 16, 16, 16
+        g = B.kp_graph(1, 1 << 32, 16, 16, 16, 16)
+        for fn in (L.kp_cut_gain, L.kp_cut_gain_noalloc):
+            assert fn(ctypes.byref(g), ctypes.c_void_p(16), 2, 0.03, ctypes.byref(out), None) == B.KP_ERR_OVERFLOW
         print("ok")
     """)
     assert out.strip().endswith("ok")
