@@ -416,7 +416,8 @@ kp_status kp_cut_gain_noalloc(const kp_graph *g, const int32_t *part, int32_t k,
  *   *q_nnz    host: the number of directed quotient entries
  * Synchronises the stream.  Errors: KP_ERR_INVALID (k < 1, null arrays, a
  * block id outside [0,k)), KP_ERR_OVERFLOW (*q_nnz > capacity: the entries are
- * not written; retry with larger buffers), KP_ERR_UNSUPPORTED (k > 4096: the
+ * not written; retry with larger buffers; or g->nnz >= 2^32 in the 64-bit
+ * library), KP_ERR_UNSUPPORTED (k > 4096: the
  * accumulator is a dense k x k matrix), KP_ERR_OOM, KP_ERR_CUDA. */
 kp_status kp_quotient_graph(const kp_graph *g, const int32_t *part, int32_t k, int32_t *q_xadj, int32_t *q_adjncy,
                             int64_t *q_ewgt, int64_t capacity, int64_t *q_nnz, kp_stream s);
@@ -430,7 +431,8 @@ kp_status kp_quotient_graph(const kp_graph *g, const int32_t *part, int32_t k, i
  * part: the boundary is the a-b boundary and nodes of other blocks get -2;
  * (-1, -1) means every block.  Synchronises the stream.  Errors:
  * KP_ERR_INVALID (k < 1, depth < 0, a bad pair, null arrays, a block id
- * outside [0,k)), KP_ERR_OOM, KP_ERR_CUDA. */
+ * outside [0,k)), KP_ERR_OVERFLOW (g->nnz >= 2^32 in the 64-bit library),
+ * KP_ERR_OOM, KP_ERR_CUDA. */
 kp_status kp_boundary_band(const kp_graph *g, const int32_t *part, int32_t k, int32_t depth, int32_t pair_a,
                            int32_t pair_b, int32_t *dist, kp_stream s);
 

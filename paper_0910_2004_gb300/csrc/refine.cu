@@ -415,6 +415,7 @@ kp_status check_refine_args(const kp_graph *g, const int32_t *part, int32_t k) {
     if (!g) return set_error(KP_ERR_INVALID, "null argument");
     if (k < 1) return set_error(KP_ERR_INVALID, "k must be >= 1");
     if (g->n < 0 || g->nnz < 0) return set_error(KP_ERR_INVALID, "negative graph size");
+    if ((int64_t)g->nnz >= NNZ_LIMIT) return set_error(KP_ERR_OVERFLOW, "nnz >= 2^32: the edge weights sum to 2^31 or more");
     if (g->n > 0 && (!part || !g->xadj || (g->nnz > 0 && (!g->adjncy || !g->ewgt))))
         return set_error(KP_ERR_INVALID, "null array");
     return KP_OK;

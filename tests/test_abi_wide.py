@@ -64,6 +64,11 @@ def test_wide_library_refuses_nnz_beyond_the_weight_range():
         g = B.kp_graph(1, 1 << 32, 16, 16, 16, 16)
         for fn in (L.kp_cut_gain, L.kp_cut_gain_noalloc):
             assert fn(ctypes.byref(g), ctypes.c_void_p(16), 2, 0.03, ctypes.byref(out), None) == B.KP_ERR_OVERFLOW
+        q_nnz = ctypes.c_int64()
+        assert L.kp_quotient_graph(ctypes.byref(g), ctypes.c_void_p(16), 2, ctypes.c_void_p(16), ctypes.c_void_p(16),
+                                   ctypes.c_void_p(16), 4, ctypes.byref(q_nnz), None) == B.KP_ERR_OVERFLOW
+        assert L.kp_boundary_band(ctypes.byref(g), ctypes.c_void_p(16), 2, 1, -1, -1, ctypes.c_void_p(16),
+                                  None) == B.KP_ERR_OVERFLOW
         print("ok")
     """)
     assert out.strip().endswith("ok")
