@@ -12,13 +12,17 @@
 namespace kp {
 
 namespace {
-thread_local std::string g_last_error;
+// a fixed buffer per thread: reporting an error allocates nothing, so it
+// also works when a host allocation is what failed
+thread_local char g_last_error[2048];
 }
 
-kp_status set_error(kp_status st, const std::string &msg) {
-    g_last_error = msg;
+kp_status set_error(kp_status st, const char *msg) {
+    snprintf(g_last_error, sizeof g_last_error, "%s", msg ? msg : "");
     return st;
 }
+
+kp_status set_error(kp_status st, const std::string &msg) { return set_error(st, msg.c_str()); }
 
 kp_status cuda_error(cudaError_t e, const char *what) {
     cudaGetLastError();   // clear a non-sticky error
@@ -271,7 +275,7 @@ kp_status kp_coarsen(const kp_graph *g, const kp_options *o, kp_stream s, kp_hie
     kp_options def;
     kp_options_default(&def);
     if (o && o->max_levels > 120) return set_error(KP_ERR_UNSUPPORTED, "max_levels above 120");
-    g_last_error.clear();
+    g_last_error[0] = 0;
     KP_GUARD(coarsen_impl(g, o ? o : &def, (cudaStream_t)s, out));
 }
 
@@ -284,7 +288,7 @@ kp_status kp_coarsen_batch(const kp_graph *g, int32_t num_graphs, const int32_t 
     kp_options def;
     kp_options_default(&def);
     if (o && o->max_levels > 120) return set_error(KP_ERR_UNSUPPORTED, "max_levels above 120");
-    g_last_error.clear();
+    g_last_error[0] = 0;
     BatchSpec b;
     b.num_graphs = num_graphs;
     b.node_offsets = node_offsets;
@@ -392,7 +396,7 @@ kp_status kp_pipeline_host(const kp_graph *g, const kp_options *o, int32_t k, do
                                 num_levels, (cudaStream_t)s));
 }
 
-const char *kp_last_error(void) { return g_last_error.c_str(); }
+const char *kp_last_error(void) { return g_last_error; }
 
 const char *kp_version(void) {
     return KP_OFFSET_BITS == 64 ? "kp-gb300 0.1 (sm_103a, 64-bit offsets)" : "kp-gb300 0.1 (sm_103a)";

@@ -38,6 +38,7 @@ constexpr int64_t NNZ_LIMIT = KP_OFFSET_BITS == 64 ? (1ll << 32) : (1ll << 31);
 // ---------------------------------------------------------------------------
 // error state (host)
 // ---------------------------------------------------------------------------
+kp_status set_error(kp_status st, const char *msg);
 kp_status set_error(kp_status st, const std::string &msg);
 kp_status cuda_error(cudaError_t e, const char *what);
 
