@@ -1,5 +1,7 @@
 // Host-compiler stand-ins for the CUDA device builtins the library uses, so
-// that g++ -Wconversion can type-check its device code (never linked or run).
+// that g++ can type-check its device code (-Wconversion) and run its pure
+// integer helpers on the host.  Builtins whose value matters to those helpers
+// are defined by their mathematics; the others are inert.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -31,7 +33,10 @@ inline int __popcll(unsigned long long) { return 0; }
 inline int __ffs(int) { return 0; }
 inline int __clz(int) { return 0; }
 inline int __clzll(long long) { return 0; }
-inline unsigned long long __umul64hi(unsigned long long, unsigned long long) { return 0; }
+// the high 64 bits of the 128-bit product (its definition)
+inline unsigned long long __umul64hi(unsigned long long a, unsigned long long b) {
+    return (unsigned long long)(((unsigned __int128)a * b) >> 64);
+}
 inline double __ull2double_rn(unsigned long long x) { return (double)x; }
 inline size_t __cvta_generic_to_shared(const void *) { return 0; }
 template <class T> T __ldg(const T *p) { return *p; }

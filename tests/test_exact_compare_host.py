@@ -1,0 +1,126 @@
+"""The library's exact rating comparison and tie-break hash, the functions
+every matching decision of the GPU path goes through, compiled by the host
+compiler and run on the CPU (CPU only).
+
+cmp_frac compares two ratings num/den (Section 3.1; a zero denominator is
++infinity, two infinities are equal) by 128-bit cross products, with a
+shortcut of single widening multiplies when all four terms fit 32 bits.  The
+parity graphs keep weights small, so products beyond 64 bits and the switch
+between the two forms are checked here instead: against Python's exact
+fractions on random and boundary cases, in both builds of the function (with
+the shortcut, and the 128-bit form alone as the persistent tail compiles it).
+The hash is checked against the published splitmix64 vectors and the
+oracle's independent implementation."""
+import math
+import os
+import shutil
+import subprocess
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HERE = os.path.join(ROOT, "tests", "hostcc")
+GAMMA = 0x9E3779B97F4A7C15
+
+
+def _cuda_include():
+    for d in (os.environ.get("CUDA_HOME", ""), "/usr/local/cuda"):
+        if d and os.path.exists(os.path.join(d, "include", "cuda_runtime.h")):
+            return os.path.join(d, "include")
+    return None
+
+
+@pytest.fixture(scope="module", params=["shortcut", "wide_only"])
+def harness(request, tmp_path_factory):
+    inc = _cuda_include()
+    if shutil.which("g++") is None or inc is None:
+        pytest.skip("needs g++ and the CUDA headers")
+    exe = str(tmp_path_factory.mktemp("hostcc") / f"exact_compare_{request.param}")
+    cmd = ["g++", "-std=c++17", "-O1", "-Wno-attributes", "-include", os.path.join(HERE, "cuda_stubs.h"),
+           "-I", os.path.join(ROOT, "include"), "-I", os.path.join(ROOT, "paper_0910_2004_gb300", "csrc"),
+           "-I", inc, os.path.join(HERE, "exact_compare.cpp"), "-o", exe]
+    if request.param == "wide_only":
+        cmd.insert(1, "-DKP_FRAC_WIDE_ONLY")
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+
+    def run(lines):
+        out = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=120)
+        assert out.returncode == 0, out.stderr
+        return [int(x) for x in out.stdout.split()]
+
+    return run
+
+
+def rating(num: int, den: int):
+    return math.inf if den == 0 else Fraction(num, den)
+
+
+def expected(a, b, c, d):
+    x, y = rating(a, b), rating(c, d)
+    return (x > y) - (x < y)
+
+
+def cases(seed: int, count: int):
+    """(num, den) pairs the ratings can produce: numerators in [1, 2^62]
+    (expansion*2: omega^2 with omega < 2^31), denominators in [0, 2^62]
+    (products of two node weights below 2^31), mixed with small values and
+    the 32-bit boundary."""
+    rng = np.random.default_rng(seed)
+    edges = [1, 2, 3, (1 << 31) - 1, (1 << 32) - 1, 1 << 32, (1 << 32) + 1, (1 << 62) - 1, 1 << 62]
+    out = []
+    for _ in range(count):
+        pick = []
+        for lo in (1, 0):
+            kind = int(rng.integers(4))
+            if kind == 0:
+                v = int(rng.integers(lo, 1 << 16))
+            elif kind == 1:
+                v = int(rng.integers(lo, 1 << 32))
+            elif kind == 2:
+                v = int(rng.integers(lo, (1 << 62) + 1, dtype=np.uint64))
+            else:
+                v = int(rng.choice(edges))
+            pick.append(max(v, lo))
+        out.append(tuple(pick))
+    return out
+
+
+def test_cmp_frac_equals_exact_fractions(harness):
+    fr = cases(1, 4000)
+    pairs = [(fr[i], fr[i + 1]) for i in range(0, len(fr) - 1, 2)]
+    # equal fractions in other terms (a*k / b*k), near-equal ones, and infinities
+    rng = np.random.default_rng(2)
+    for _ in range(1000):
+        a, b = int(rng.integers(1, 1 << 31)), int(rng.integers(1, 1 << 31))
+        k = int(rng.integers(1, 1 << 31))
+        pairs.append(((a, b), (a * k, b * k)))
+        pairs.append(((a * k, b * k + 1), (a, b)))
+        pairs.append(((a * k + 1, b * k), (a, b)))
+    pairs += [((5, 0), (7, 0)), ((1, 0), ((1 << 62), 1)), (((1 << 62), (1 << 62)), (1, 1)),
+              (((1 << 62), (1 << 62) - 1), ((1 << 62) - 1, (1 << 62) - 2)), (((1 << 32) - 1, 1), (1 << 32, 1))]
+    lines = [f"c {a} {b} {c} {d}" for (a, b), (c, d) in pairs]
+    got = harness(lines)
+    want = [expected(a, b, c, d) for (a, b), (c, d) in pairs]
+    bad = [(p, g, w) for p, g, w in zip(pairs, got, want) if g != w]
+    assert not bad, bad[:5]
+    # antisymmetric
+    got_rev = harness([f"c {c} {d} {a} {b}" for (a, b), (c, d) in pairs])
+    assert got_rev == [-x for x in got]
+
+
+def test_hash_matches_the_published_vectors_and_the_oracle(harness):
+    gold = [l.split() for l in open(os.path.join(ROOT, "tests", "golden", "splitmix64_seed0.txt"))
+            if l.strip() and not l.startswith("#")]
+    got = harness([f"s {(int(i) * GAMMA) % (1 << 64)}" for i, _ in gold])
+    assert got == [int(h, 16) for _, h in gold]
+    rng = np.random.default_rng(3)
+    q = [(int(rng.integers(0, 1 << 63, dtype=np.uint64)) * 2 + int(rng.integers(2)),
+          int(rng.integers(0, 1 << 31)), int(rng.integers(0, 1 << 31))) for _ in range(2000)]
+    q += [(0, 0, 1), (0, 1, 0), ((1 << 64) - 1, (1 << 31) - 1, 0)]
+    got = harness([f"h {s} {u} {v}" for s, u, v in q])
+    assert got == [O.edge_hash(s, u, v) for s, u, v in q]

@@ -2,7 +2,7 @@
 
 The library's device and host sources are compiled by the host compiler
 (g++, syntax only, with stand-ins for the CUDA builtins in
-narrowing/cuda_stubs.h and kernel launches reduced to calls) with
+hostcc/cuda_stubs.h and kernel launches reduced to calls) with
 -Wconversion, in both offset widths: in the 64-bit build (KP_WIDE_OFFSETS)
 every implicit conversion from a 64-bit integer to a 32-bit one is a place
 where a row offset or entry index above 2^31 could be truncated.  Both
@@ -17,7 +17,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_0910_2004_gb300", "csrc")
-STUBS = os.path.join(ROOT, "tests", "narrowing", "cuda_stubs.h")
+STUBS = os.path.join(ROOT, "tests", "hostcc", "cuda_stubs.h")
 NARROW = re.compile(r"conversion from .(long int|long long int|int64_t|kp::eoff|kp_eoff|long unsigned int|"
                     r"long long unsigned int|uint64_t). .*to .(int|int32_t|unsigned int|uint32_t)\b")
 
