@@ -1,12 +1,36 @@
-// Runs the library's exact rating comparison and tie-break hash
-// (paper_0910_2004_gb300/csrc/kp_internal.cuh) on the host, one query per
-// input line:  c a b d e  -> cmp_frac(a, b, d, e) (-1, 0 or 1)
-//              s x        -> splitmix64(x)
-//              h seed u v -> edge_hash(seed, u, v)
+// Runs the library's exact rating comparison, tie-break hash and strict edge
+// order (paper_0910_2004_gb300/csrc/kp_internal.cuh, engine.cuh) on the
+// host, one query per input line:
+//   c a b d e  -> cmp_frac(a, b, d, e) (-1, 0 or 1)
+//   s x        -> splitmix64(x)
+//   h seed u v -> edge_hash(seed, u, v)
+//   b R seed v u1 w1 u2 w2 av a1 a2 -> better() of the candidates {v,u1}
+//                 and {v,u2} of node v under rating R (av, a1, a2: the rating
+//                 attribute of v, u1, u2), both ways round: "x y"
 // Built with g++ and the stand-ins of cuda_stubs.h by tests/test_exact_compare_host.py.
 #include <cstdio>
 
-#include "kp_internal.cuh"
+#include "engine.cuh"
+
+namespace {
+
+template <int R>
+kp::Cand cand(uint64_t seed, int32_t v, int32_t u, int32_t w, int32_t av, int32_t au) {
+    kp::Cand c;
+    kp::rating_ab<R>(w, av, au, c.num, c.den);
+    c.h = kp::edge_hash(seed, v, u);
+    c.u = u;
+    return c;
+}
+
+template <int R>
+void order(uint64_t seed, int32_t v, int32_t u1, int32_t w1, int32_t u2, int32_t w2, int32_t av, int32_t a1,
+           int32_t a2) {
+    const kp::Cand x = cand<R>(seed, v, u1, w1, av, a1), y = cand<R>(seed, v, u2, w2, av, a2);
+    printf("%d %d\n", (int)kp::better(x, y, v), (int)kp::better(y, x, v));
+}
+
+}  // namespace
 
 int main() {
     char op[4];
@@ -24,6 +48,19 @@ int main() {
             int u, v;
             if (scanf("%llu %d %d", &s, &u, &v) != 3) return 2;
             printf("%llu\n", (unsigned long long)kp::edge_hash(s, u, v));
+        } else if (op[0] == 'b') {
+            int r, v, u1, w1, u2, w2, av, a1, a2;
+            unsigned long long seed;
+            if (scanf("%d %llu %d %d %d %d %d %d %d %d", &r, &seed, &v, &u1, &w1, &u2, &w2, &av, &a1, &a2) != 10)
+                return 2;
+            switch (r) {
+            case KP_RATING_EXPANSION_STAR2: order<KP_RATING_EXPANSION_STAR2>(seed, v, u1, w1, u2, w2, av, a1, a2); break;
+            case KP_RATING_INNER_OUTER: order<KP_RATING_INNER_OUTER>(seed, v, u1, w1, u2, w2, av, a1, a2); break;
+            case KP_RATING_WEIGHT: order<KP_RATING_WEIGHT>(seed, v, u1, w1, u2, w2, av, a1, a2); break;
+            case KP_RATING_EXPANSION: order<KP_RATING_EXPANSION>(seed, v, u1, w1, u2, w2, av, a1, a2); break;
+            case KP_RATING_EXPANSION_STAR: order<KP_RATING_EXPANSION_STAR>(seed, v, u1, w1, u2, w2, av, a1, a2); break;
+            default: return 2;
+            }
         } else {
             return 2;
         }

@@ -1,6 +1,6 @@
-"""The library's exact rating comparison and tie-break hash, the functions
-every matching decision of the GPU path goes through, compiled by the host
-compiler and run on the CPU (CPU only).
+"""The library's exact rating comparison, tie-break hash and strict edge
+order, the functions every matching decision of the GPU path goes through,
+compiled by the host compiler and run on the CPU (CPU only).
 
 cmp_frac compares two ratings num/den (Section 3.1; a zero denominator is
 +infinity, two infinities are equal) by 128-bit cross products, with a
@@ -10,7 +10,9 @@ between the two forms are checked here instead: against Python's exact
 fractions on random and boundary cases, in both builds of the function (with
 the shortcut, and the 128-bit form alone as the persistent tail compiles it).
 The hash is checked against the published splitmix64 vectors and the
-oracle's independent implementation."""
+oracle's independent implementation, and the order of two candidate edges
+of a node (rating_ab and better) against the oracle's edge order for all
+five ratings."""
 import math
 import os
 import shutil
@@ -124,3 +126,34 @@ def test_hash_matches_the_published_vectors_and_the_oracle(harness):
     q += [(0, 0, 1), (0, 1, 0), ((1 << 64) - 1, (1 << 31) - 1, 0)]
     got = harness([f"h {s} {u} {v}" for s, u, v in q])
     assert got == [O.edge_hash(s, u, v) for s, u, v in q]
+
+
+RATING_IDS = {"expansion*2": 0, "innerOuter": 1, "weight": 2, "expansion": 3, "expansion*": 4}
+
+
+@pytest.mark.parametrize("rating", list(RATING_IDS))
+def test_candidate_order_equals_the_oracle_edge_order(harness, rating):
+    """Two edges {v,u1}, {v,u2} at a node v: the GPU's candidate order agrees
+    with the oracle's strict order, both ways round.  Small weight and node
+    weight ranges make equal ratings common, so the hash decides many pairs;
+    zero node weights give infinite ratings."""
+    rng = np.random.default_rng(10 + RATING_IDS[rating])
+    n = 64
+    queries, expect = [], []
+    for t in range(3000):
+        wmax = [2, 5, 1 << 20, (1 << 31) - 1][t % 4]
+        vw = rng.integers(0 if t % 3 == 0 else 1, [3, 50, 1 << 15, (1 << 31) - 1][t % 4], size=n).astype(np.int64)
+        v, u1, u2 = (int(x) for x in rng.choice(n, size=3, replace=False))
+        w1, w2 = int(rng.integers(1, wmax + 1)), int(rng.integers(1, wmax + 1))
+        # Out(x) is at least the weight of any edge at x (innerOuter's denominator stays >= 0)
+        out = (max(w1, w2) + rng.integers(0, 1 << 20, size=n)).astype(np.int64)
+        if rating == "innerOuter":
+            out = np.minimum(out, (1 << 31) - 1)
+            attr = out
+        else:
+            attr = vw
+        seed = int(rng.integers(0, 1 << 63, dtype=np.uint64))
+        queries.append(f"b {RATING_IDS[rating]} {seed} {v} {u1} {w1} {u2} {w2} {attr[v]} {attr[u1]} {attr[u2]}")
+        o = O.edge_order(rating, seed, vw.astype(np.int32), out, (v, u1, w1), (v, u2, w2))
+        expect += [int(o == 1), int(o == -1)]
+    assert harness(queries) == expect
