@@ -36,26 +36,31 @@ def _cuda_include():
     return None
 
 
-@pytest.fixture(scope="module", params=["shortcut", "wide_only"])
-def harness(request, tmp_path_factory):
+def host_program(source: str, exe: str, defines=()):
+    """Builds tests/hostcc/<source> with g++ against the library's headers
+    and the stand-ins; returns run(lines) -> the integers it prints."""
     inc = _cuda_include()
     if shutil.which("g++") is None or inc is None:
         pytest.skip("needs g++ and the CUDA headers")
-    exe = str(tmp_path_factory.mktemp("hostcc") / f"exact_compare_{request.param}")
-    cmd = ["g++", "-std=c++17", "-O1", "-Wno-attributes", "-include", os.path.join(HERE, "cuda_stubs.h"),
-           "-I", os.path.join(ROOT, "include"), "-I", os.path.join(ROOT, "paper_0910_2004_gb300", "csrc"),
-           "-I", inc, os.path.join(HERE, "exact_compare.cpp"), "-o", exe]
-    if request.param == "wide_only":
-        cmd.insert(1, "-DKP_FRAC_WIDE_ONLY")
+    cmd = ["g++", "-std=c++17", "-O1", "-Wno-attributes", *[f"-D{d}" for d in defines],
+           "-include", os.path.join(HERE, "cuda_stubs.h"), "-I", os.path.join(ROOT, "include"),
+           "-I", os.path.join(ROOT, "paper_0910_2004_gb300", "csrc"), "-I", inc, os.path.join(HERE, source),
+           "-o", exe]
     r = subprocess.run(cmd, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
 
     def run(lines):
-        out = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=120)
+        out = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, timeout=300)
         assert out.returncode == 0, out.stderr
         return [int(x) for x in out.stdout.split()]
 
     return run
+
+
+@pytest.fixture(scope="module", params=["shortcut", "wide_only"])
+def harness(request, tmp_path_factory):
+    exe = str(tmp_path_factory.mktemp("hostcc") / f"exact_compare_{request.param}")
+    return host_program("exact_compare.cpp", exe, ["KP_FRAC_WIDE_ONLY"] if request.param == "wide_only" else [])
 
 
 def rating(num: int, den: int):
