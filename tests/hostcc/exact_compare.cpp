@@ -7,10 +7,14 @@
 //   b R seed v u1 w1 u2 w2 av a1 a2 -> better() of the candidates {v,u1}
 //                 and {v,u2} of node v under rating R (av, a1, a2: the rating
 //                 attribute of v, u1, u2), both ways round: "x y"
+//   e R seed cur v w s ws acur as av -> eligible_at(): whether cur (attribute
+//                 acur) may offer the edge {cur,v} of weight w to v, whose
+//                 record holds suitor s (-1: none) over an edge of weight ws,
+//                 s's attribute as and v's own av (paper_0910_2004_gb300/csrc/match.cuh)
 // Built with g++ and the stand-ins of cuda_stubs.h by tests/test_exact_compare_host.py.
 #include <cstdio>
 
-#include "engine.cuh"
+#include "match.cuh"
 
 namespace {
 
@@ -21,6 +25,21 @@ kp::Cand cand(uint64_t seed, int32_t v, int32_t u, int32_t w, int32_t av, int32_
     c.h = kp::edge_hash(seed, v, u);
     c.u = u;
     return c;
+}
+
+template <int R>
+void eligible(uint64_t seed, int32_t cur, int32_t v, int32_t w, int32_t s, int32_t ws, int32_t acur, int32_t as,
+              int32_t av) {
+    kp::HashCtx hc;
+    hc.seed = seed;
+    hc.base = 0;
+    kp::Offer so;
+    so.s = s;
+    so.w = ws;
+    so.as = as;
+    so.au = av;
+    kp::Cand cd;
+    printf("%d\n", (int)kp::eligible_at<R>(hc, cur, acur, v, w, so, cd));
 }
 
 template <int R>
@@ -59,6 +78,19 @@ int main() {
             case KP_RATING_WEIGHT: order<KP_RATING_WEIGHT>(seed, v, u1, w1, u2, w2, av, a1, a2); break;
             case KP_RATING_EXPANSION: order<KP_RATING_EXPANSION>(seed, v, u1, w1, u2, w2, av, a1, a2); break;
             case KP_RATING_EXPANSION_STAR: order<KP_RATING_EXPANSION_STAR>(seed, v, u1, w1, u2, w2, av, a1, a2); break;
+            default: return 2;
+            }
+        } else if (op[0] == 'e') {
+            int r, cur, v, w, s, ws, acur, as, av;
+            unsigned long long seed;
+            if (scanf("%d %llu %d %d %d %d %d %d %d %d", &r, &seed, &cur, &v, &w, &s, &ws, &acur, &as, &av) != 10)
+                return 2;
+            switch (r) {
+            case KP_RATING_EXPANSION_STAR2: eligible<KP_RATING_EXPANSION_STAR2>(seed, cur, v, w, s, ws, acur, as, av); break;
+            case KP_RATING_INNER_OUTER: eligible<KP_RATING_INNER_OUTER>(seed, cur, v, w, s, ws, acur, as, av); break;
+            case KP_RATING_WEIGHT: eligible<KP_RATING_WEIGHT>(seed, cur, v, w, s, ws, acur, as, av); break;
+            case KP_RATING_EXPANSION: eligible<KP_RATING_EXPANSION>(seed, cur, v, w, s, ws, acur, as, av); break;
+            case KP_RATING_EXPANSION_STAR: eligible<KP_RATING_EXPANSION_STAR>(seed, cur, v, w, s, ws, acur, as, av); break;
             default: return 2;
             }
         } else {

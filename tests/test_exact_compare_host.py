@@ -1,6 +1,7 @@
-"""The library's exact rating comparison, tie-break hash and strict edge
-order, the functions every matching decision of the GPU path goes through,
-compiled by the host compiler and run on the CPU (CPU only).
+"""The library's exact rating comparison, tie-break hash, strict edge order
+and Suitor eligibility test, the functions every matching decision of the
+GPU path goes through, compiled by the host compiler and run on the CPU (CPU
+only).
 
 cmp_frac compares two ratings num/den (Section 3.1; a zero denominator is
 +infinity, two infinities are equal) by 128-bit cross products, with a
@@ -11,8 +12,10 @@ fractions on random and boundary cases, in both builds of the function (with
 the shortcut, and the 128-bit form alone as the persistent tail compiles it).
 The hash is checked against the published splitmix64 vectors and the
 oracle's independent implementation, and the order of two candidate edges
-of a node (rating_ab and better) against the oracle's edge order for all
-five ratings."""
+of a node (rating_ab and better) and the test whether an edge beats the
+standing offer at its other end (eligible_at, which rebuilds the standing
+edge from the 16-byte offer record and hashes it only on equal ratings)
+against the oracle's edge order for all five ratings."""
 import math
 import os
 import shutil
@@ -139,9 +142,9 @@ RATING_IDS = {"expansion*2": 0, "innerOuter": 1, "weight": 2, "expansion": 3, "e
 @pytest.mark.parametrize("rating", list(RATING_IDS))
 def test_candidate_order_equals_the_oracle_edge_order(harness, rating):
     """Two edges {v,u1}, {v,u2} at a node v: the GPU's candidate order agrees
-    with the oracle's strict order, both ways round.  Small weight and node
-    weight ranges make equal ratings common, so the hash decides many pairs;
-    zero node weights give infinite ratings."""
+    with the oracle's strict order, both ways round.  Small weight, node
+    weight and Out ranges make equal ratings common, so the hash decides many
+    pairs; zero node weights give infinite ratings."""
     rng = np.random.default_rng(10 + RATING_IDS[rating])
     n = 64
     queries, expect = [], []
@@ -151,7 +154,7 @@ def test_candidate_order_equals_the_oracle_edge_order(harness, rating):
         v, u1, u2 = (int(x) for x in rng.choice(n, size=3, replace=False))
         w1, w2 = int(rng.integers(1, wmax + 1)), int(rng.integers(1, wmax + 1))
         # Out(x) is at least the weight of any edge at x (innerOuter's denominator stays >= 0)
-        out = (max(w1, w2) + rng.integers(0, 1 << 20, size=n)).astype(np.int64)
+        out = (max(w1, w2) + rng.integers(0, [3, 50, 1 << 20, 1 << 20][t % 4], size=n)).astype(np.int64)
         if rating == "innerOuter":
             out = np.minimum(out, (1 << 31) - 1)
             attr = out
@@ -161,4 +164,31 @@ def test_candidate_order_equals_the_oracle_edge_order(harness, rating):
         queries.append(f"b {RATING_IDS[rating]} {seed} {v} {u1} {w1} {u2} {w2} {attr[v]} {attr[u1]} {attr[u2]}")
         o = O.edge_order(rating, seed, vw.astype(np.int32), out, (v, u1, w1), (v, u2, w2))
         expect += [int(o == 1), int(o == -1)]
+    assert harness(queries) == expect
+
+
+@pytest.mark.parametrize("rating", list(RATING_IDS))
+def test_suitor_eligibility_equals_the_oracle_edge_order(harness, rating):
+    """cur may offer {cur,v} to v iff v holds no offer or {cur,v} comes before
+    the standing edge {s,v} in the strict order."""
+    rng = np.random.default_rng(20 + RATING_IDS[rating])
+    n = 64
+    queries, expect = [], []
+    for t in range(3000):
+        wmax = [2, 5, 1 << 20, (1 << 31) - 1][t % 4]
+        vw = rng.integers(0 if t % 3 == 0 else 1, [3, 50, 1 << 15, (1 << 31) - 1][t % 4], size=n).astype(np.int64)
+        cur, v, s = (int(x) for x in rng.choice(n, size=3, replace=False))
+        w, ws = int(rng.integers(1, wmax + 1)), int(rng.integers(1, wmax + 1))
+        out = np.minimum(max(w, ws) + rng.integers(0, [3, 50, 1 << 20, 1 << 20][t % 4], size=n),
+                         (1 << 31) - 1).astype(np.int64)
+        attr = out if rating == "innerOuter" else vw
+        seed = int(rng.integers(0, 1 << 63, dtype=np.uint64))
+        none = t % 10 == 0
+        queries.append(f"e {RATING_IDS[rating]} {seed} {cur} {v} {w} {-1 if none else s} {ws} "
+                       f"{attr[cur]} {attr[s]} {attr[v]}")
+        if none:
+            expect.append(1)
+        else:
+            o = O.edge_order(rating, seed, vw.astype(np.int32), out, (cur, v, w), (s, v, ws))
+            expect.append(int(o == 1))
     assert harness(queries) == expect
