@@ -11,9 +11,13 @@
 //                 acur) may offer the edge {cur,v} of weight w to v, whose
 //                 record holds suitor s (-1: none) over an edge of weight ws,
 //                 s's attribute as and v's own av (paper_0910_2004_gb300/csrc/match.cuh)
+//   g R seed x1 y1 w1 ax1 ay1 x2 y2 w2 ax2 ay2 -> gedge_before() of the edges
+//                 {x1,y1} and {x2,y2} (the Global Path Algorithm's order,
+//                 paper_0910_2004_gb300/csrc/gpa.cuh), both ways round: "x y"
 // Built with g++ and the stand-ins of cuda_stubs.h by tests/test_exact_compare_host.py.
 #include <cstdio>
 
+#include "gpa.cuh"
 #include "match.cuh"
 
 namespace {
@@ -40,6 +44,22 @@ void eligible(uint64_t seed, int32_t cur, int32_t v, int32_t w, int32_t s, int32
     so.au = av;
     kp::Cand cd;
     printf("%d\n", (int)kp::eligible_at<R>(hc, cur, acur, v, w, so, cd));
+}
+
+template <int R>
+kp::GEdge gedge(uint64_t seed, int32_t x, int32_t y, int32_t w, int32_t ax, int32_t ay) {
+    kp::GEdge g;
+    kp::rating_ab<R>(w, ax, ay, g.num, g.den);
+    g.h = kp::edge_hash(seed, x, y);
+    g.lo = x < y ? x : y;
+    g.hi = x < y ? y : x;
+    return g;
+}
+
+template <int R>
+void gorder(uint64_t seed, const int32_t *e) {
+    const kp::GEdge a = gedge<R>(seed, e[0], e[1], e[2], e[3], e[4]), b = gedge<R>(seed, e[5], e[6], e[7], e[8], e[9]);
+    printf("%d %d\n", (int)kp::gedge_before(a, b), (int)kp::gedge_before(b, a));
 }
 
 template <int R>
@@ -91,6 +111,20 @@ int main() {
             case KP_RATING_WEIGHT: eligible<KP_RATING_WEIGHT>(seed, cur, v, w, s, ws, acur, as, av); break;
             case KP_RATING_EXPANSION: eligible<KP_RATING_EXPANSION>(seed, cur, v, w, s, ws, acur, as, av); break;
             case KP_RATING_EXPANSION_STAR: eligible<KP_RATING_EXPANSION_STAR>(seed, cur, v, w, s, ws, acur, as, av); break;
+            default: return 2;
+            }
+        } else if (op[0] == 'g') {
+            int r, e[10];
+            unsigned long long seed;
+            if (scanf("%d %llu", &r, &seed) != 2) return 2;
+            for (int i = 0; i < 10; i++)
+                if (scanf("%d", &e[i]) != 1) return 2;
+            switch (r) {
+            case KP_RATING_EXPANSION_STAR2: gorder<KP_RATING_EXPANSION_STAR2>(seed, e); break;
+            case KP_RATING_INNER_OUTER: gorder<KP_RATING_INNER_OUTER>(seed, e); break;
+            case KP_RATING_WEIGHT: gorder<KP_RATING_WEIGHT>(seed, e); break;
+            case KP_RATING_EXPANSION: gorder<KP_RATING_EXPANSION>(seed, e); break;
+            case KP_RATING_EXPANSION_STAR: gorder<KP_RATING_EXPANSION_STAR>(seed, e); break;
             default: return 2;
             }
         } else {

@@ -192,3 +192,32 @@ def test_suitor_eligibility_equals_the_oracle_edge_order(harness, rating):
             o = O.edge_order(rating, seed, vw.astype(np.int32), out, (cur, v, w), (s, v, ws))
             expect.append(int(o == 1))
     assert harness(queries) == expect
+
+
+@pytest.mark.parametrize("rating", list(RATING_IDS))
+def test_gpa_edge_order_equals_the_oracle_edge_order(harness, rating):
+    """The Global Path Algorithm compares edges that need not share a node
+    (gedge_before): the same strict order, both ways round, and an edge is
+    never before itself."""
+    rng = np.random.default_rng(30 + RATING_IDS[rating])
+    n = 40
+    queries, expect = [], []
+    for t in range(3000):
+        wmax = [2, 5, 1 << 20, (1 << 31) - 1][t % 4]
+        vw = rng.integers(0 if t % 3 == 0 else 1, [3, 50, 1 << 15, (1 << 31) - 1][t % 4], size=n).astype(np.int64)
+        x1, y1 = (int(x) for x in rng.choice(n, size=2, replace=False))
+        if t % 7 == 0:
+            x2, y2 = y1, x1                                  # the same edge seen from its other end
+        else:
+            x2, y2 = (int(x) for x in rng.choice(n, size=2, replace=False))
+        w1 = int(rng.integers(1, wmax + 1))
+        w2 = w1 if {x1, y1} == {x2, y2} else int(rng.integers(1, wmax + 1))
+        out = np.minimum(max(w1, w2) + rng.integers(0, [3, 50, 1 << 20, 1 << 20][t % 4], size=n),
+                         (1 << 31) - 1).astype(np.int64)
+        attr = out if rating == "innerOuter" else vw
+        seed = int(rng.integers(0, 1 << 63, dtype=np.uint64))
+        queries.append(f"g {RATING_IDS[rating]} {seed} {x1} {y1} {w1} {attr[x1]} {attr[y1]} "
+                       f"{x2} {y2} {w2} {attr[x2]} {attr[y2]}")
+        o = O.edge_order(rating, seed, vw.astype(np.int32), out, (x1, y1, w1), (x2, y2, w2))
+        expect += [int(o == 1), int(o == -1)]
+    assert harness(queries) == expect
